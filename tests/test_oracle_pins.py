@@ -1,0 +1,403 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage of the paper it pins. None of them re-types the
+oracle's own formulas: they use quadrature, brute force, library routines,
+closed-form consequences (linear exactness, lattice symmetry, an energy
+identity) or values printed in the paper.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_2608_22269_gb300 import scenes as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+# -- Eq. (c2kernel): normalisation and derivative --------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_kernel_integrates_to_one(dim):
+    p = S.default_params(dim, 0.01, 20.0)
+    h = p["h_over_dx"] * p["dx"]
+
+    def w(r):
+        return oracle.kernel(p, np.array([r]))[0][0]
+
+    shell = (lambda r: 2 * math.pi * r) if dim == 2 else (lambda r: 4 * math.pi * r * r)
+    val, _ = integrate.quad(lambda r: w(r) * shell(r), 0.0, 2.0 * h, epsabs=1e-14, epsrel=1e-13)
+    assert abs(val - 1.0) < 1e-10
+    assert w(2.0 * h * 1.0000001) == 0.0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_kernel_derivative_matches_finite_difference(dim):
+    p = S.default_params(dim, 0.01, 20.0)
+    h = p["h_over_dx"] * p["dx"]
+    r = np.linspace(0.05 * h, 1.95 * h, 37)
+    e = 1e-6 * h
+    wp, _ = oracle.kernel(p, r + e)
+    wm, _ = oracle.kernel(p, r - e)
+    _, dw = oracle.kernel(p, r)
+    fd = (wp - wm) / (2 * e)
+    assert np.max(np.abs(fd - dw)) < 1e-6 * np.max(np.abs(dw))
+    assert np.all(dw <= 0)
+
+
+# -- Eqs. (hashid), (ixyz), radix sort, Algorithm 1 ------------------------------------------
+
+def _brute_pairs(x, two_h):
+    """All-pairs neighbour sets by the definition of Algorithm 1 (d <= 2h), with
+    r^2 accumulated left to right and (2h)^2 = (2h)*(2h)."""
+    d, n = x.shape
+    four = two_h * two_h
+    rows = []
+    for i in range(n):
+        r2 = (x[0] - x[0, i]) * (x[0] - x[0, i])
+        r2 = r2 + (x[1] - x[1, i]) * (x[1] - x[1, i])
+        if d == 3:
+            r2 = r2 + (x[2] - x[2, i]) * (x[2] - x[2, i])
+        m = (r2 <= four) & (r2 > 0)
+        m[i] = False
+        rows.append(np.nonzero(m)[0].astype(np.int32))
+    return rows
+
+
+@pytest.mark.parametrize("dim,n", [(2, 1500), (3, 2000)])
+def test_neighbours_equal_brute_force(dim, n):
+    sc = S.random_box(n, dim, side=0.2, dx=0.01, seed=2026 + dim)
+    p = sc.params
+    two_h = 2.0 * (p["h_over_dx"] * p["dx"])
+    row, col = oracle.neighbors(p, sc.x)
+    rowb, colb = oracle.neighbors(p, sc.x, brute=True)
+    assert np.array_equal(row, rowb) and np.array_equal(col, colb)
+    ref = _brute_pairs(sc.x, two_h)
+    for i in range(sc.n):
+        assert np.array_equal(col[row[i]:row[i + 1]], ref[i]), i
+    # the snapped faces / exact-2h pairs are present
+    assert row[-1] > 0
+
+
+def test_cell_keys_and_stable_sort():
+    sc = S.random_box(3000, 3, side=0.2, dx=0.01, seed=11)
+    p = sc.params
+    keys = oracle.cell_keys(p, sc.x)
+    R = 2.0 * (p["h_over_dx"] * p["dx"])
+    nc = [int(math.floor((p["domain_max"][k] - p["domain_min"][k]) / R)) + 1 for k in range(3)]
+    ic = keys % nc[0], (keys // nc[0]) % nc[1], keys // (nc[0] * nc[1])
+    for k in range(3):
+        lo = p["domain_min"][k] + ic[k] * R
+        assert np.all(sc.x[k] >= lo - 1e-15) and np.all(sc.x[k] <= lo + R + 1e-15)
+    perm = oracle.sort_by_key(keys)
+    assert np.array_equal(perm, np.argsort(keys, kind="stable"))
+    with pytest.raises(oracle.OracleError):
+        bad = sc.x.copy()
+        bad[0, 5] = p["domain_max"][0] + 1.0
+        oracle.cell_keys(p, bad)
+
+
+# -- closed-form eigenvalue (Sec. 3) ---------------------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_eigenvalue_closed_form_vs_lapack(dim):
+    rng = np.random.default_rng(5)
+    for trial in range(300):
+        a = rng.normal(size=(dim, dim))
+        m = a @ a.T + 0.01 * np.eye(dim)
+        if trial % 50 == 0:
+            m = np.diag(rng.uniform(0.2, 2.0, size=dim))
+        if trial % 50 == 1:
+            m = np.eye(dim) * 0.8
+        lam = oracle.eig_min_sym(dim, m)
+        ref = np.linalg.eigvalsh(m)[0]
+        assert abs(lam - ref) <= 1e-12 * max(1.0, np.abs(m).max()), (m, lam, ref)
+
+
+# -- Eqs. (parGrad), (renorm), (sph): first-order consistency ----------------------------------
+
+@pytest.mark.parametrize("dim,n_side", [(2, 24), (3, 10)])
+@pytest.mark.parametrize("eos", [0, 1])
+def test_linear_potential_recovered_exactly(dim, n_side, eos):
+    """With U = 0 and phi = a + b.x, the corrected Riemann gradient gives b
+    for every particle whose L is invertible, ordered or disordered (Sec. 2.2.2)."""
+    sc = S.lattice_cloud(dim, n_side, jitter_amount=0.2, seed=7, eos=eos)
+    rng = np.random.default_rng(3)
+    b = rng.normal(size=dim) * 5.0
+    phi = 0.3 + b @ sc.x
+    m = oracle.mass(sc.params, phi)
+    r = oracle.stage_rates(sc.params, sc.x, sc.u, phi, m, sc.type, sc.normal)
+    ok = r["lam"] > 0.05
+    assert ok.sum() > 0.8 * sc.n
+    err = np.abs(-r["dudt"][:, ok] - b[:, None]).max()
+    assert err <= 1e-12 * np.abs(b).max(), err
+
+
+@pytest.mark.parametrize("dim,n_side", [(2, 24), (3, 10)])
+@pytest.mark.parametrize("eos", [0, 1])
+def test_linear_velocity_divergence_exact(dim, n_side, eos):
+    """For U = A x the corrected divergence sum_ab (L^-1)_ab M_ab equals tr A
+    (M = A L for linear U, L symmetric), so Dphi/Dt = -c^2 tr A, with c^2 the
+    EOS slope dp/drho taken here by finite differences of the oracle's EOS."""
+    sc = S.lattice_cloud(dim, n_side, jitter_amount=0.2, seed=9, eos=eos)
+    rng = np.random.default_rng(4)
+    A = rng.normal(size=(dim, dim)) * 0.3
+    u = np.ascontiguousarray(A @ sc.x)
+    phi = np.full(sc.n, 0.7)
+    m = oracle.mass(sc.params, phi)
+    r = oracle.stage_rates(sc.params, sc.x, u, phi, m, sc.type, sc.normal)
+    ok = r["lam"] > 0.05
+    e = 1e-4
+    rho_p, rho_m = oracle.density(sc.params, [0.7 + e])[0], oracle.density(sc.params, [0.7 - e])[0]
+    p_p, p_m = oracle.pressure(sc.params, [0.7 + e])[0], oracle.pressure(sc.params, [0.7 - e])[0]
+    c2 = (p_p - p_m) / (rho_p - rho_m)
+    expect = -c2 * np.trace(A)
+    got = r["dphidt"][ok]
+    assert np.abs(got - expect).max() <= 1e-7 * abs(expect)   # c2 by finite differences
+    assert np.ptp(got) <= 1e-11 * abs(expect)                 # exact: one value for all
+
+
+def test_renormalisation_matrix_on_lattice():
+    """Interior of a square / cubic lattice: L = c I by symmetry, c near 1 and
+    c = tr(L)/d; a sign error in grad W would make L negative (Eq. renorm)."""
+    for dim, n in [(2, 20), (3, 10)]:
+        sc = S.lattice_cloud(dim, n)
+        m = oracle.mass(sc.params, sc.phi)
+        s = oracle.pair_sums(sc.params, sc.x, sc.u, sc.phi, m, sc.type)
+        ctr = np.argmin(((sc.x - sc.x.mean(axis=1, keepdims=True)) ** 2).sum(0))
+        L = s[ctr, :9].reshape(3, 3)[:dim, :dim]
+        c = np.trace(L) / dim
+        assert np.abs(L - c * np.eye(dim)).max() < 1e-13
+        assert 0.9 < c < 1.1
+
+
+# -- Riemann dissipation (Sec. 2.2.2: Pi_i acts like artificial viscosity) ---------------------
+
+@pytest.mark.parametrize("dim,n_side", [(2, 26), (3, 12)])
+def test_riemann_term_dissipates_energy_exactly(dim, n_side):
+    """phi uniform, G = 0, random velocities on deep-interior lattice particles:
+    sum_i m_i U_i . DU_i/Dt equals the pair form
+    -(C0 / (2 c)) sum_(i,j) m V |W'(r_ij)| (U_j.e - U_i.e)^2 <= 0
+    (L = c I for those particles). Pins the factor 2 of Eq. (parGrad), the
+    C0/2 of Eq. (lfsover) and the sign of the interface potential."""
+    sc = S.lattice_cloud(dim, n_side, nu=0.0)
+    p = sc.params
+    h = p["h_over_dx"] * p["dx"]
+    rng = np.random.default_rng(21)
+    ctr = sc.x.mean(axis=1, keepdims=True)
+    half = 0.5 * n_side * p["dx"]
+    deep = np.all(np.abs(sc.x - ctr) < half - 2.5 * h, axis=0)
+    u = np.zeros_like(sc.x)
+    u[:, deep] = rng.normal(size=(dim, deep.sum()))
+    phi = np.zeros(sc.n)
+    m = oracle.mass(p, phi)
+    r = oracle.stage_rates(p, sc.x, u, phi, m, sc.type, sc.normal)
+    lhs = float(np.sum(m * np.sum(u * r["dudt"], axis=0)))
+    s = oracle.pair_sums(p, sc.x, sc.x * 0, phi, m, sc.type)
+    i0 = np.nonzero(deep)[0][0]
+    c = np.trace(s[i0, :9].reshape(3, 3)[:dim, :dim]) / dim
+    row, col = oracle.neighbors(p, sc.x)
+    V = m[0] / p["rho0"]
+    rhs = 0.0
+    for i in range(sc.n):
+        js = col[row[i]:row[i + 1]]
+        rv = sc.x[:, js] - sc.x[:, i:i + 1]
+        rr = np.sqrt((rv * rv).sum(0))
+        e = rv / rr
+        dun = ((u[:, js] - u[:, i:i + 1]) * e).sum(0)
+        _, dw = oracle.kernel(p, rr)
+        rhs += np.sum(m[i] * V * np.abs(dw) * dun * dun)
+    rhs *= -p["c0"] / (2.0 * c)
+    assert lhs < 0
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs), (lhs, rhs)
+
+
+# -- delta-SPH and Laplacian operators on a lattice (Sec. 2.1, 2.3) ---------------------------
+
+@pytest.mark.parametrize("dim,n", [(2, 20), (3, 10)])
+def test_diffusion_and_laplacian_sums_on_quadratic_fields(dim, n):
+    """On a symmetric lattice interior, for phi = k|x - x0|^2 / 2 the delta-SPH
+    sum (without delta h C0) is k tr(L), and for U_x = k|x - x0|^2 / 2 the
+    Laplacian-operator sum is k tr(L) / 2 (odd terms cancel by symmetry when
+    all volumes are equal; the even term is k r^2 times -W'/r). Pins the
+    factor 2 and the 1/r^2."""
+    sc = S.lattice_cloud(dim, n)
+    p = sc.params
+    x0 = sc.x.mean(axis=1, keepdims=True)
+    q = 0.5 * ((sc.x - x0) ** 2).sum(0)
+    k = 3.0
+    m = oracle.mass(p, k * q)                # uniform volumes V = dx^d
+    u = np.zeros_like(sc.x)
+    u[0] = k * q
+    s = oracle.pair_sums(p, sc.x, u, k * q, m, sc.type)
+    ctr = np.argmin(((sc.x - x0) ** 2).sum(0))
+    trL = np.trace(s[ctr, :9].reshape(3, 3)[:dim, :dim])
+    assert abs(s[ctr, 24] - k * trL) < 1e-10 * k * trL
+    assert abs(s[ctr, 28] - 0.5 * k * trL) < 1e-10 * k * trL
+
+
+def test_pairwise_sums_are_antisymmetric():
+    """sum_i V_i sum_j (phi_i + phi_j) grad_i W_ij V_j = 0 and sum_i V_i D_i = 0
+    over all particles: the conservative (TIC) gradient and the delta-SPH
+    diffusion exchange equal and opposite pair terms (Sec. 2.3)."""
+    sc = S.jitter(S.dam_break_2d(dx=0.02), 0.2, seed=3)
+    p = sc.params
+    rng = np.random.default_rng(8)
+    phi = sc.phi + rng.normal(size=sc.n)
+    m = oracle.mass(p, phi)
+    V = m / oracle.density(p, phi)
+    s = oracle.pair_sums(p, sc.x, sc.u, phi, m, sc.type, all_types=True)
+    Csum = (V[:, None] * s[:, 21:23]).sum(0)
+    Cscale = (V[:, None] * np.abs(s[:, 21:23])).sum(0)
+    assert np.all(np.abs(Csum) <= 1e-13 * Cscale)
+    Dsum = (V * s[:, 24]).sum()
+    assert abs(Dsum) <= 1e-13 * (V * np.abs(s[:, 24])).sum()
+
+
+# -- particle shifting (Sec. 2.3) ------------------------------------------------------------
+
+def test_shifting_direction_and_clamp():
+    """Top-row particles of a resting block shift outward (up); a particle
+    displaced from its lattice site shifts back; |dU| <= U_max / 2."""
+    sc = S.lattice_cloud(2, 20, use_pst=1, use_tic=1)
+    p = sc.params
+    x = sc.x.copy()
+    mid = np.argmin(((x - x.mean(axis=1, keepdims=True)) ** 2).sum(0))
+    x[0, mid] += 0.2 * p["dx"]
+    u = np.zeros_like(x)
+    u[0, :] = 0.3
+    m = oracle.mass(p, sc.phi)
+    r = oracle.stage_rates(p, x, u, sc.phi, m, sc.type, sc.normal)
+    assert r["umax"] == pytest.approx(0.3)
+    top = x[1] > x[1].max() - 1e-12
+    assert np.all(r["dushift"][1, top] > 0)
+    assert r["dushift"][0, mid] < 0
+    nrm = np.sqrt((r["dushift"] ** 2).sum(0))
+    assert np.all(nrm <= 0.15 + 1e-15)
+    assert np.isclose(nrm.max(), 0.15)
+
+
+# -- walls (Sec. 2.4) ------------------------------------------------------------------------
+
+def test_dummy_potential_is_hydrostatic_and_velocity_slips():
+    sc = S.topography_tank_2d("gauss", dx=0.01)
+    p = sc.params
+    g = 9.81
+    phi_hs = g * (sc.water_height - sc.x[1])
+    rng = np.random.default_rng(1)
+    u = rng.normal(size=sc.x.shape)
+    phi = sc.phi + 5.0 * (sc.type == 1)      # dummies start wrong on purpose
+    u2, phi2 = oracle.dummy_update(p, sc.x, u, phi, sc.type, sc.normal)
+    dm = sc.type == 1
+    row, col = oracle.neighbors(p, sc.x)
+    has_fluid = np.array([np.any(sc.type[col[row[i]:row[i + 1]]] == 0) for i in range(sc.n)])
+    upd = dm & has_fluid
+    assert upd.sum() > 100
+    assert np.abs(phi2[upd] - phi_hs[upd]).max() <= 1e-14 * g * sc.water_height
+    un = (u2 * sc.normal).sum(0)
+    assert np.abs(un[upd]).max() < 1e-14
+    assert np.all(phi2[dm & ~has_fluid] == phi[dm & ~has_fluid])
+
+
+# -- well-balance (Sec. 2.5 and 4.1) ---------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["flat", "rect", "tri", "gauss"])
+@pytest.mark.parametrize("eos", [0, 1])
+def test_hydrostatic_state_is_a_discrete_equilibrium(kind, eos):
+    """At U = 0 and phi = G.x + |G| H the discrete rates vanish up to rounding:
+    DU/Dt = 0, Dphi/Dt = 0 (stabilisers off, Sec. 4.1)."""
+    sc = S.topography_tank_2d(kind, dx=0.01, width=1.0, eos=eos)
+    p = sc.params
+    m = oracle.mass(p, sc.phi)
+    r = oracle.stage_rates(p, sc.x, sc.u, sc.phi, m, sc.type, sc.normal)
+    f = sc.type == 0
+    assert np.abs(r["dudt"][:, f]).max() <= 1e-12 * 9.81
+    assert np.abs(r["dphidt"][f]).max() == 0.0
+
+
+def _golden():
+    with open(GOLDEN) as fh:
+        return json.load(fh)
+
+
+def test_closed_tank_stays_at_rest_for_200_steps():
+    """No free surface: L2 spurious velocity at the level the paper prints
+    (order 1e-14 to 1e-13), max |U| <= 1e-12."""
+    st = oracle.State(S.hydrostatic_tank_2d(lid=True))
+    st.step(200)
+    l2, um = st.l2_velocity()
+    assert l2 <= _golden()["hydrostatic_l2_wbsph"]["range"][1]
+    assert um <= 1e-12
+
+
+@pytest.mark.parametrize("eos", [0, 1])
+def test_open_tank_stays_at_rest_100_steps(eos):
+    """Free surface, 5,000 fluid particles: max |U| <= 1e-12 for 100 steps.
+    (Beyond that a rounding-seeded free-surface mode of the printed scheme
+    grows; see the reading on free-surface stability.)"""
+    st = oracle.State(S.hydrostatic_tank_2d(eos=eos))
+    st.step(100)
+    l2, um = st.l2_velocity()
+    assert um <= 1e-12
+    assert l2 <= _golden()["hydrostatic_l2_wbsph"]["range"][1]
+
+
+# -- SSP-RK2 and the time step (Sec. 2.3) -----------------------------------------------------
+
+def test_lone_particle_falls_exactly():
+    """A lone fluid particle has L = 0 (lambda_min = 0 < 0.75), so with TIC on its
+    rate is DU/Dt = G; SSP-RK2 integrates constant acceleration exactly:
+    x = x0 + U0 t + G t^2 / 2 for any step sequence. With TIC off L is singular."""
+    p = S.default_params(2, 0.01, 30.0, use_tic=1, domain_min=[-5, -50, 0], domain_max=[5, 5, 1])
+    x = np.array([[0.1], [0.2]])
+    u = np.array([[0.5], [1.0]])
+    sc = S.Scene(p, x, u, np.zeros(1), np.zeros(1, np.uint8), np.zeros((2, 1)))
+    st = oracle.State(sc)
+    st.step(50)
+    t = st.t
+    exp_x = np.array([0.1 + 0.5 * t, 0.2 + 1.0 * t - 0.5 * 9.81 * t * t])
+    assert np.abs(st.x[:, 0] - exp_x).max() < 1e-14
+    assert abs(st.u[1, 0] - (1.0 - 9.81 * t)) < 1e-13
+    p2 = dict(p, use_tic=0)
+    st2 = oracle.State(S.Scene(p2, x, u, np.zeros(1), np.zeros(1, np.uint8), np.zeros((2, 1))))
+    with pytest.raises(oracle.OracleError) as ei:
+        st2.step(1)
+    assert ei.value.code == -5
+
+
+def test_time_step_limits():
+    """dt = CFL min(dx/(C0 + U_max), dx^2/(2 nu), sqrt(2 dx/|G|))."""
+    p = S.default_params(2, 0.01, 30.0)
+    u = np.array([[3.0, 0.0], [4.0, 0.0]])
+    typ = np.zeros(2, np.uint8)
+    assert oracle.time_step(p, u, typ) == pytest.approx(0.2 * 0.01 / 35.0, rel=1e-15)
+    p2 = dict(p, nu=10.0)
+    assert oracle.time_step(p2, u, typ) == pytest.approx(0.2 * 1e-4 / 20.0, rel=1e-15)
+    p3 = dict(p, c0=1e-3, nu=0.0, g=[0.0, -1e6, 0.0])
+    assert oracle.time_step(p3, u * 0, typ) == pytest.approx(0.2 * math.sqrt(2e-2 / 1e6), rel=1e-14)
+
+
+def test_tait_potential_is_enthalpy():
+    """phi(rho) = integral of dp/rho from rho0 (Sec. 2.2.1 with the Tait EOS)."""
+    p = S.default_params(2, 0.01, 22.0, eos=1)
+    phis = [-20.0, -7.5, 2.5, 15.0, 40.0]
+    for ph in phis:
+        grid = np.linspace(0.0, ph, 2001)
+        rho = oracle.density(p, grid)
+        pr = oracle.pressure(p, grid)
+        val = np.trapezoid(np.gradient(pr, grid) / rho, grid)
+        assert abs(val - ph) < 1e-6 * max(1.0, abs(ph))
+    assert oracle.density(p, [0.0])[0] == p["rho0"]
+
+
+def test_results_independent_of_thread_count(monkeypatch):
+    sc = S.jitter(S.dam_break_2d(dx=0.01), 0.1, seed=2)
+    a = oracle.State(sc)
+    a.step(2)
+    b = oracle.State(sc)
+    b.step(2)
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.phi, b.phi)
