@@ -1,0 +1,182 @@
+/*
+ * wbsph.h -- C-ABI of the GB300 (sm_103a) well-balanced WCSPH hot path.
+ *
+ * The library advances a set of SPH particles (fluid and fixed dummy wall
+ * particles) with the well-balanced weakly compressible SPH method of Zhang,
+ * Zhao, Gan and Xu: auxiliary potential phi with rho = rho0 exp(phi/C0^2)
+ * (Sec. 2.2.1, Eq. newEqns), Riemann-based corrected gradient (Eqs. parGrad,
+ * renorm, lfsover), delta-SPH diffusion, particle shifting and tensile
+ * instability control (Sec. 2.3), the final semi-discrete system (Eq. sph),
+ * SSP-RK2 with the three-condition time step (Sec. 2.3), and dummy-particle
+ * slip walls (Sec. 2.4, Eq. phiBn). The neighbour build follows Sec. 3
+ * (Eqs. hashid, ixyz; Algorithm 1): cell key, stable radix sort, reorder.
+ *
+ * Conventions (every function):
+ *  - Return value: WBSPH_OK (0) or a negative wbsph_status. A message for
+ *    the last failure of a handle is available from wbsph_last_error().
+ *  - Arrays are structure-of-arrays: component k of particle i at [k*n + i],
+ *    k < dim. Types: 0 fluid, 1 dummy.
+ *  - Pointers are borrowed for the duration of the call. Host or device
+ *    memory is selected by the `where` argument (WBSPH_HOST / WBSPH_DEVICE);
+ *    device pointers must be on the handle's device.
+ *  - Work is enqueued on the caller's CUDA stream (wbsph_config.cuda_stream,
+ *    NULL = legacy default stream). Only wbsph_sync, the wbsph_get_* calls
+ *    and wbsph_set_particles with host input synchronise that stream.
+ *  - The handle owns its device memory, obtained from the caller's allocator
+ *    callbacks when given, otherwise from cudaMallocAsync on the stream.
+ *  - Device-side failures (particle outside the domain, singular
+ *    renormalisation matrix with TIC off, non-finite value, neighbour list
+ *    overflow) set a status word that is read at the next synchronising call.
+ */
+#ifndef WBSPH_H
+#define WBSPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wbsph_s* wbsph_handle;
+
+typedef enum {
+  WBSPH_OK = 0,
+  WBSPH_E_INVAL = -1,     /* bad argument or configuration */
+  WBSPH_E_NOMEM = -2,     /* device allocation failed */
+  WBSPH_E_CUDA = -3,      /* CUDA runtime error (message in wbsph_last_error) */
+  WBSPH_E_DOMAIN = -4,    /* a particle left [domain_min, domain_max] */
+  WBSPH_E_SINGULAR = -5,  /* renormalisation matrix singular and TIC off */
+  WBSPH_E_NAN = -6,       /* a non-finite rate or state value */
+  WBSPH_E_TIMEOUT = -7,   /* a bounded device-side wait gave up */
+  WBSPH_E_STATE = -8,     /* call out of order (e.g. step before set_particles) */
+  WBSPH_E_CAPACITY = -9,  /* output capacity too small / neighbour list overflow */
+  WBSPH_E_NOSYM = -10     /* feature not built into this library */
+} wbsph_status;
+
+typedef enum { WBSPH_FP64 = 0, WBSPH_MIXED = 1 } wbsph_precision;
+typedef enum { WBSPH_HOST = 0, WBSPH_DEVICE = 1 } wbsph_where;
+
+typedef enum {
+  WBSPH_FIELD_X = 0,       /* dim*n positions */
+  WBSPH_FIELD_U = 1,       /* dim*n velocities */
+  WBSPH_FIELD_PHI = 2,     /* n potentials */
+  WBSPH_FIELD_RHO = 3,     /* n densities from the EOS */
+  WBSPH_FIELD_P = 4,       /* n pressures from the EOS */
+  WBSPH_FIELD_DUDT = 5,    /* dim*n: DU/Dt of the last evaluated stage (fluid; 0 for dummies) */
+  WBSPH_FIELD_DPHIDT = 6,  /* n: Dphi/Dt of the last evaluated stage */
+  WBSPH_FIELD_DUSHIFT = 7, /* dim*n: shifting velocity dU of the last evaluated stage */
+  WBSPH_FIELD_LAMBDA = 8,  /* n: lambda_min(L) of the last evaluated stage */
+  WBSPH_FIELD_MASS = 9,    /* n masses */
+  WBSPH_FIELD_VOL = 10     /* n volumes m/rho of the last evaluated stage */
+} wbsph_field;
+
+/* Optional allocator hooks (e.g. a framework's caching allocator). */
+typedef void* (*wbsph_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*wbsph_free_fn)(void* ptr, void* stream, void* ctx);
+
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  double dx;                /* initial particle spacing */
+  double h_over_dx;         /* smoothing length h = h_over_dx * dx (paper: 1.5, Sec. 2.1) */
+  double rho0;              /* reference density (paper: 1000, Sec. 4) */
+  double c0;                /* artificial sound speed C0 (paper: 30, Sec. 4) */
+  double nu;                /* kinematic viscosity (paper: 1e-4, Sec. 4) */
+  double g[3];              /* body force G */
+  double cfl;               /* CFL number (paper: 0.2, Sec. 2.3) */
+  double delta;             /* delta-SPH coefficient (paper: 0.1, Sec. 2.3) */
+  double pst_R, pst_n;      /* shifting constants R, n (paper: 0.2, 4, Sec. 2.3) */
+  double tic_lambda;        /* surface / TIC threshold on lambda_min (paper: 0.75) */
+  int use_delta, use_pst, use_tic, use_visc;
+  int eos;                  /* 0: linear p = C0^2 (rho - rho0) (Eq. eos-water); 1: Tait */
+  double tait_gamma;        /* Tait exponent (7) */
+  double domain_min[3], domain_max[3]; /* grid extent; particles must stay inside */
+  double force_amp[3];      /* harmonic tank displacement amplitude A: G(t) = G + A w^2 sin(w t) */
+  double force_period;      /* forcing period; <= 0 disables */
+  double fixed_dt;          /* > 0 replaces the adaptive time step */
+  int precision;            /* wbsph_precision */
+  int device;               /* CUDA device ordinal */
+  void* cuda_stream;        /* cudaStream_t owned by the caller; NULL = default stream */
+  wbsph_alloc_fn alloc;     /* NULL: cudaMallocAsync on cuda_stream */
+  wbsph_free_fn free;
+  void* alloc_ctx;
+  double water_height;      /* free-surface height H of the hydrostatic split (mixed path) */
+} wbsph_config;
+
+typedef struct {
+  int64_t n, n_fluid, n_dummy;
+  int64_t ncells;           /* background grid cells (R = 2h) */
+  int64_t grid[3];
+  int64_t steps;            /* steps taken */
+  int64_t launches;         /* kernels launched by this handle so far */
+  int64_t device_bytes;     /* device memory held by the handle */
+  double t, dt;             /* simulated time and last time step (after a sync) */
+} wbsph_stats;
+
+/* Kernel classes timed when profiling is on (CUDA events on the stream). */
+typedef enum {
+  WBSPH_K_KEYS = 0, WBSPH_K_SORT = 1, WBSPH_K_REORDER = 2, WBSPH_K_CELLS = 3,
+  WBSPH_K_PREPASS = 4, WBSPH_K_PAIR = 5, WBSPH_K_UPDATE = 6, WBSPH_K_OTHER = 7,
+  WBSPH_K_COUNT = 8
+} wbsph_kernel_class;
+
+/* Fill *cfg with the paper's constants (Sec. 4) for dimension dim. */
+int wbsph_config_default(wbsph_config* cfg, int dim);
+
+/* Create a handle; validates cfg and copies it. */
+int wbsph_create(const wbsph_config* cfg, wbsph_handle* out);
+
+/* Load n particles (Sec. 2.4: fluid and dummy). x, u, normal: dim*n SoA;
+ * phi: n; mass: n or NULL (then m = rho(phi) dx^dim, the initial density
+ * times the particle volume); type: n bytes (0 fluid, 1 dummy); normal may
+ * be NULL when there are no dummies. Sets t = 0. */
+int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, const double* u,
+                        const double* phi, const double* mass, const uint8_t* type,
+                        const double* normal, int where);
+
+/* Cell key, stable radix sort by key and reorder of all particle data, then
+ * the per-cell index bounds (Sec. 3, Eqs. hashid/ixyz). */
+int wbsph_build_neighbors(wbsph_handle h);
+
+/* One rate evaluation at the current state and time: neighbour build, dummy
+ * update, volumes, pair pass (Eq. sph). State is not advanced. */
+int wbsph_eval_rates(wbsph_handle h);
+
+/* Advance nsteps SSP-RK2 steps (two stages each, neighbours rebuilt per
+ * stage). Asynchronous: errors surface at the next synchronising call. */
+int wbsph_step(wbsph_handle h, int64_t nsteps);
+
+/* Wait for the handle's stream and read the device status word. */
+int wbsph_sync(wbsph_handle h);
+
+/* Copy one field out in the caller's original particle order. */
+int wbsph_get_fields(wbsph_handle h, int field, double* out, int where);
+
+/* Test hook: cell keys in sorted order and the original particle id at each
+ * sorted position, from the last neighbour build (host arrays of n). */
+int wbsph_get_cell_keys(wbsph_handle h, uint32_t* keys_sorted, uint32_t* ids_sorted);
+
+/* Test hook: neighbour lists of every particle (d <= 2h, j != i, r > 0) in
+ * CSR form over original ids, each row ascending. Returns the number of
+ * entries (>= 0) or a negative status; row_ptr has n+1 entries; when cols is
+ * NULL or cap is too small only row_ptr is written (then
+ * WBSPH_E_CAPACITY is returned if cols was given). */
+int64_t wbsph_get_neighbors(wbsph_handle h, int64_t* row_ptr, int32_t* cols, int64_t cap);
+
+int wbsph_get_stats(wbsph_handle h, wbsph_stats* out);
+
+/* Profiling: when on, CUDA events bracket each kernel class on the stream;
+ * wbsph_get_profile returns total milliseconds and launch counts per class
+ * (arrays of WBSPH_K_COUNT) accumulated since the last reset, and
+ * synchronises the stream. */
+int wbsph_set_profiling(wbsph_handle h, int on);
+int wbsph_get_profile(wbsph_handle h, double* ms, int64_t* launches, int reset);
+
+void wbsph_destroy(wbsph_handle h);
+const char* wbsph_last_error(wbsph_handle h);
+const char* wbsph_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -39,7 +39,7 @@ class Config(C.Structure):
                 ("use_visc", C.c_int), ("eos", C.c_int), ("tait_gamma", C.c_double),
                 ("domain_min", C.c_double * 3), ("domain_max", C.c_double * 3),
                 ("force_amp", C.c_double * 3), ("force_period", C.c_double),
-                ("fixed_dt", C.c_double)]
+                ("fixed_dt", C.c_double), ("umax_override", C.c_double)]
 
 
 _lock = threading.Lock()
@@ -96,7 +96,7 @@ def lib():
 def make_config(params: dict) -> Config:
     c = Config()
     for name, _ in Config._fields_:
-        v = params[name]
+        v = params.get(name, -1.0) if name == "umax_override" else params[name]
         if isinstance(v, (list, tuple, np.ndarray)):
             arr = getattr(c, name)
             for k in range(3):
@@ -222,10 +222,12 @@ class Rates(dict):
     pass
 
 
-def stage_rates(params, x, u, phi, m, typ, normal, t=0.0):
+def stage_rates(params, x, u, phi, m, typ, normal, t=0.0, umax=None):
     """One stage of rates at the given state (dummy update applied to
-    copies of u and phi). Returns dict with dudt, dphidt, dushift, lambda,
-    umax, u, phi (after the dummy update)."""
+    copies of u and phi). ``umax`` (optional) replaces the U_max of the
+    shifting term, for rates of a patch cut from a larger scene. Returns
+    dict with dudt, dphidt, dushift, lam, umax, u, phi (after the dummy
+    update)."""
     x, u, phi, m, normal = _f64(x), _f64(u).copy(), _f64(phi).copy(), _f64(m), _f64(normal)
     typ = np.ascontiguousarray(typ, dtype=np.uint8)
     d, n = x.shape
@@ -233,6 +235,7 @@ def stage_rates(params, x, u, phi, m, typ, normal, t=0.0):
     dushift = np.zeros((d, n))
     dphidt = np.zeros(n)
     lam = np.zeros(n)
+    params = dict(params, umax_override=-1.0 if umax is None else float(umax))
     umax = np.zeros(1)
     c = make_config(params)
     _check(lib().orc_stage_rates(C.byref(c), n, _p(x), _p(u), _p(phi), _p(m), _p(typ),

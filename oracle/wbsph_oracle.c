@@ -657,7 +657,7 @@ int orc_stage_rates(const orc_config* c, int64_t n, const double* x, double* u, 
   double* vol = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   if (!vol) { csr_free(&nb); return ORC_E_NOMEM; }
   rc = volumes(c, n, phi, mass, vol);
-  double umax = fluid_umax(c, n, u, type);
+  double umax = c->umax_override >= 0 ? c->umax_override : fluid_umax(c, n, u, type);
   if (umax_out) *umax_out = umax;
   double G[3];
   body_force(c, t, G);
@@ -665,7 +665,7 @@ int orc_stage_rates(const orc_config* c, int64_t n, const double* x, double* u, 
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 256) reduction(min : err)
     for (int64_t i = 0; i < n; ++i) {
-      double a[3], sh[3], dp, lam;
+      double a[3], sh[3], dp = 0.0, lam = 0.0;
       if (type[i] != FLUID) {
         for (int k = 0; k < d; ++k) { dudt[k * n + i] = 0.0; dushift[k * n + i] = 0.0; }
         dphidt[i] = 0.0;
@@ -721,6 +721,7 @@ int orc_step(const orc_config* c, int64_t n, double* x, double* u, double* phi,
              int64_t nsteps, double* dt_last, double* dudt, double* dphidt, double* dushift,
              double* lambda) {
   if (!valid_config(c) || n < 0 || nsteps < 0 || !t) return ORC_E_INVAL;
+  if (c->umax_override >= 0) return ORC_E_INVAL; /* a full step computes U_max itself */
   int d = c->dim;
   size_t nd = (size_t)(n > 0 ? n : 1);
   double* x0 = (double*)malloc(sizeof(double) * nd * d);

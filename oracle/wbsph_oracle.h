@@ -58,6 +58,9 @@ typedef struct {
   double force_amp[3];     /* tank displacement amplitude A (harmonic forcing) */
   double force_period;     /* forcing period T; <= 0 disables the forcing */
   double fixed_dt;         /* > 0 replaces the adaptive time step */
+  double umax_override;    /* >= 0: U_max used by shifting in orc_stage_rates (an input
+                              when rates are evaluated on a patch of a larger scene);
+                              < 0: computed from the particles */
 } orc_config;
 
 /* Number of doubles per particle written by orc_pair_sums:

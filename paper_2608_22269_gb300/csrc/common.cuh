@@ -1,0 +1,117 @@
+// common.cuh -- shared definitions of the sm_103a well-balanced WCSPH kernels.
+//
+// Layout in HBM: structure-of-arrays, one array per component, particles in
+// the order of the last neighbour build (cell-key order). Every per-particle
+// array of the state is double-buffered so that the reorder of Sec. 3 is a
+// gather into the second buffer followed by a pointer swap.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wbsph {
+
+constexpr int kFluid = 0;
+constexpr int kDummy = 1;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+// Device status word bits (read by the host at synchronising calls).
+enum : unsigned {
+  kStatDomain = 1u,     // particle outside the grid
+  kStatSingular = 2u,   // singular renormalisation matrix on the corrected branch
+  kStatNaN = 4u,        // non-finite rate or state
+  kStatOverflow = 8u,   // neighbour list chunk bookkeeping overflow
+  kStatTimeout = 16u    // bounded device wait gave up
+};
+
+// Numerical parameters, derived once on the host from the configuration and
+// passed to kernels by value.
+struct Params {
+  int dim;
+  int eos;              // 0 linear, 1 Tait
+  int use_delta, use_pst, use_tic, use_visc;
+  double dx, h, two_h, four_h2;   // four_h2 = (2h)*(2h), the Algorithm 1 test
+  float prefilter_r2;             // FP32 candidate threshold, >= (2h)^2 plus a rounding margin
+  double alpha;                   // kernel normalisation (Eq. c2kernel)
+  double neg_dwdr_over_r_coef;    // -W'(r)/r = coef * (1 - q/2)^3, coef = 5 alpha / h^2
+  double inv_two_h;               // 1/(2h): (1 - q/2) = 1 - r/(2h)
+  double two_over_h;              // 2q + 1 = 1 + r * 2/h
+  double pst_alpha_over_wdx;      // alpha / W(dx), for W_ij / W(dx)
+  double pst_R, pst_n;
+  double rho0, c0, c0sq, nu, gamma;
+  double delta_h_c0;              // delta * h * C0
+  double tic_lambda;
+  double g[3];
+  double force_amp[3];
+  double omega;                   // 2 pi / period, 0 = no forcing
+  double cfl, fixed_dt;
+  double inv_dx_vol;              // unused placeholder for alignment
+  double domain_min[3], domain_max[3];
+  double R;                       // cell size 2h
+  int nc[3];                      // grid cells per axis
+  int64_t ncells;
+  double water_height;
+};
+
+// Device arrays of one particle-state buffer.
+struct State {
+  double* x;        // dim * n
+  double* u;        // dim * n
+  double* phi;      // n
+  double* x0;       // dim * n: stage-start state y^n (SSP-RK2)
+  double* u0;       // dim * n
+  double* phi0;     // n
+  double* mass;     // n
+  double* normal;   // dim * n
+  uint8_t* type;    // n
+  uint32_t* oid;    // n: original particle id
+};
+
+// Rates and per-stage scratch (not reordered: recomputed every stage).
+struct Work {
+  double* dudt;      // dim * n
+  double* dphidt;    // n
+  double* dushift;   // dim * n
+  double* lambda;    // n
+  double* vol;       // n
+  float4* xf;        // n: FP32 copy of positions (.w unused) for the candidate prefilter
+  uint32_t* key;     // n: sorted cell keys
+  uint32_t* key_alt; // n
+  uint32_t* perm;    // n: source index of each sorted position
+  uint32_t* perm_alt;
+  uint32_t* cell_lb; // ncells + 1: first sorted index with key >= c
+  uint32_t* fluid_list;  // n_fluid: sorted indices of fluid particles
+  uint32_t* block_cnt;   // scratch for scans
+  uint32_t* hist;        // radix histograms
+  unsigned long long* umax_bits;  // [0]: max |U|^2 over fluid (bits of a non-negative double)
+  double* scalars;   // [0] t, [1] dt, [2] U_max of the current stage
+  unsigned* status;  // device status word
+};
+
+__host__ __device__ inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---- launchers (neighbors.cu) ----
+int radix_sort_scratch_words(int64_t n);
+void launch_cell_keys(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
+void launch_radix_sort(const Params& p, Work& w, int64_t n, cudaStream_t st, int* launches);
+void launch_gather(const Params& p, const State& src, const State& dst, const Work& w, int64_t n,
+                   bool with_base, cudaStream_t st);
+void launch_cell_bounds(const Params& p, const Work& w, int64_t n, cudaStream_t st);
+void launch_fluid_list(const State& s, const Work& w, int64_t n, int64_t nblocks_scan,
+                       cudaStream_t st, int* launches);
+void launch_count_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
+                            uint32_t* counts, cudaStream_t st);
+void launch_fill_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
+                           const int64_t* row_ptr_by_oid, int32_t* cols, cudaStream_t st);
+
+// ---- launchers (pair_fp64.cu) ----
+void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int stage2,
+                    cudaStream_t st);
+void launch_time_step(const Params& p, const Work& w, cudaStream_t st);
+void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid,
+                      int stage2, cudaStream_t st);
+void launch_rk_stage(const Params& p, const State& s, const Work& w, int64_t n, int stage,
+                     cudaStream_t st);
+void launch_field(const Params& p, const State& s, const Work& w, int64_t n, int field,
+                  double* out, cudaStream_t st);
+
+}  // namespace wbsph

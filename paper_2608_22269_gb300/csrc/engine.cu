@@ -1,0 +1,637 @@
+// engine.cu -- the C-ABI of include/wbsph.h: handle, device buffers, stage
+// sequencing on the caller's stream, status word, profiling events.
+//
+// One SSP-RK2 step (Sec. 2.3) is enqueued as, per stage s = 1, 2:
+//   keys -> radix sort -> gather (reorder) -> cell bounds -> fluid list   (Sec. 3)
+//   prepass: dummy walls (Sec. 2.4), volumes, U_max
+//   [s = 1] time step from U_max of y^n
+//   fused FP64 pair pass + epilogue (Eq. sph)
+//   RK stage update
+// with no host synchronisation inside a step.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wbsph.h"
+#include "common.cuh"
+
+using namespace wbsph;
+
+namespace wbsph {
+void launch_mass(const Params& p, const double* phi, double* mass, int64_t n, cudaStream_t st);
+int launch_mixed_stage(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
+                       int stage2, cudaStream_t st);
+}
+
+struct ProfEvent {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+struct wbsph_s {
+  wbsph_config cfg;
+  Params P;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0, nf = 0, nd = 0;
+  State A{}, B{};
+  Work W{};
+  std::vector<void*> blocks;
+  int64_t device_bytes = 0;
+  int64_t launches = 0, steps = 0;
+  bool loaded = false;
+  std::string err;
+  bool prof = false;
+  std::vector<ProfEvent> events, pool;
+  double prof_ms[WBSPH_K_COUNT] = {0};
+  int64_t prof_cnt[WBSPH_K_COUNT] = {0};
+};
+
+static const char* kStatusNames[] = {"ok", "invalid argument", "out of device memory",
+                                     "CUDA error", "particle outside the domain",
+                                     "singular renormalisation matrix", "non-finite value",
+                                     "device wait timed out", "call out of order",
+                                     "capacity too small", "feature not built"};
+
+extern "C" const char* wbsph_status_string(int s) {
+  if (s > 0 || s < -10) return "unknown status";
+  return kStatusNames[-s];
+}
+
+static int fail(wbsph_s* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(h, WBSPH_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+static int check_launch(wbsph_s* h, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, WBSPH_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return WBSPH_OK;
+}
+
+// ---- profiling: CUDA events around each kernel class on the stream ----
+static void prof_begin(wbsph_s* h, int cls, ProfEvent* out) {
+  if (!h->prof) return;
+  ProfEvent e;
+  if (!h->pool.empty()) {
+    e = h->pool.back();
+    h->pool.pop_back();
+  } else {
+    cudaEventCreate(&e.a);
+    cudaEventCreate(&e.b);
+  }
+  e.cls = cls;
+  cudaEventRecord(e.a, h->stream);
+  *out = e;
+}
+
+static void prof_end(wbsph_s* h, ProfEvent* e) {
+  if (!h->prof) return;
+  cudaEventRecord(e->b, h->stream);
+  h->events.push_back(*e);
+}
+
+struct ProfScope {
+  wbsph_s* h;
+  ProfEvent e;
+  ProfScope(wbsph_s* h_, int cls) : h(h_) { prof_begin(h, cls, &e); }
+  ~ProfScope() { prof_end(h, &e); }
+};
+
+// ---- allocation ----
+static void* dev_alloc(wbsph_s* h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (h->cfg.alloc) {
+    p = h->cfg.alloc(bytes, (void*)h->stream, h->cfg.alloc_ctx);
+  } else if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) {
+    h->blocks.push_back(p);
+    h->device_bytes += (int64_t)bytes;
+  }
+  return p;
+}
+
+static void free_all(wbsph_s* h) {
+  for (void* p : h->blocks) {
+    if (h->cfg.free) h->cfg.free(p, (void*)h->stream, h->cfg.alloc_ctx);
+    else cudaFreeAsync(p, h->stream);
+  }
+  h->blocks.clear();
+  h->device_bytes = 0;
+  h->A = State{};
+  h->B = State{};
+  h->W = Work{};
+}
+
+// ---- parameters ----
+static const double kPi = 3.14159265358979323846;
+
+static int derive_params(wbsph_s* h) {
+  const wbsph_config& c = h->cfg;
+  Params& p = h->P;
+  memset(&p, 0, sizeof p);
+  p.dim = c.dim;
+  p.eos = c.eos;
+  p.use_delta = c.use_delta;
+  p.use_pst = c.use_pst;
+  p.use_tic = c.use_tic;
+  p.use_visc = c.use_visc;
+  p.dx = c.dx;
+  p.h = c.h_over_dx * c.dx;
+  p.two_h = 2.0 * p.h;
+  p.four_h2 = p.two_h * p.two_h;
+  p.R = p.two_h;
+  p.alpha = c.dim == 2 ? 7.0 / (4.0 * kPi * p.h * p.h) : 21.0 / (16.0 * kPi * p.h * p.h * p.h);
+  p.neg_dwdr_over_r_coef = 5.0 * p.alpha / (p.h * p.h);
+  p.inv_two_h = 1.0 / p.two_h;
+  p.two_over_h = 2.0 / p.h;
+  double q = c.dx / p.h, tq = 1.0 - 0.5 * q;
+  p.pst_alpha_over_wdx = 1.0 / (tq * tq * tq * tq * (2.0 * q + 1.0));
+  p.pst_R = c.pst_R;
+  p.pst_n = c.pst_n;
+  p.rho0 = c.rho0;
+  p.c0 = c.c0;
+  p.c0sq = c.c0 * c.c0;
+  p.nu = c.nu;
+  p.gamma = c.tait_gamma;
+  p.delta_h_c0 = c.delta * p.h * c.c0;
+  p.tic_lambda = c.tic_lambda;
+  for (int k = 0; k < 3; ++k) {
+    p.g[k] = k < c.dim ? c.g[k] : 0.0;
+    p.force_amp[k] = k < c.dim ? c.force_amp[k] : 0.0;
+    p.domain_min[k] = c.domain_min[k];
+    p.domain_max[k] = c.domain_max[k];
+  }
+  p.omega = c.force_period > 0 ? 2.0 * kPi / c.force_period : 0.0;
+  p.cfl = c.cfl;
+  p.fixed_dt = c.fixed_dt;
+  p.water_height = c.water_height;
+  int64_t ncells = 1;
+  for (int k = 0; k < 3; ++k) {
+    int64_t m = 1;
+    if (k < c.dim) m = (int64_t)std::floor((c.domain_max[k] - c.domain_min[k]) / p.R) + 1;
+    if (m < 1 || m > (int64_t)1 << 30) return fail(h, WBSPH_E_INVAL, "grid extent out of range on axis %d", k);
+    p.nc[k] = (int)m;
+    ncells *= m;
+  }
+  if (ncells >= (int64_t)0xFFFFFFFFLL) return fail(h, WBSPH_E_INVAL, "too many grid cells (%lld)", (long long)ncells);
+  p.ncells = ncells;
+  // FP32 prefilter bound: every pair with exact r <= 2h has FP32 distance
+  // below (2h + e)^2 (1 + 16 ulp), e twice the worst coordinate rounding.
+  double X = 0.0;
+  for (int k = 0; k < c.dim; ++k) X = std::max(X, std::max(std::fabs(c.domain_min[k]), std::fabs(c.domain_max[k])));
+  const double u24 = std::ldexp(1.0, -24);
+  double e = 2.0 * std::sqrt((double)c.dim) * (2.0 * X + 2.0 * p.two_h) * u24;
+  double thr = (p.two_h + e) * (p.two_h + e) * (1.0 + 16.0 * u24);
+  float tf = (float)thr;
+  if ((double)tf < thr) tf = std::nextafter(tf, INFINITY);
+  p.prefilter_r2 = tf;
+  return WBSPH_OK;
+}
+
+static int validate(const wbsph_config* c, wbsph_s* h) {
+  if (!c) return fail(h, WBSPH_E_INVAL, "null config");
+  if (c->dim != 2 && c->dim != 3) return fail(h, WBSPH_E_INVAL, "dim must be 2 or 3");
+  if (!(c->dx > 0) || !(c->h_over_dx > 0) || !(c->rho0 > 0) || !(c->c0 > 0))
+    return fail(h, WBSPH_E_INVAL, "dx, h_over_dx, rho0 and c0 must be positive");
+  if (c->nu < 0 || !(c->cfl > 0)) return fail(h, WBSPH_E_INVAL, "nu >= 0 and cfl > 0 required");
+  if (c->eos != 0 && c->eos != 1) return fail(h, WBSPH_E_INVAL, "eos must be 0 or 1");
+  if (c->eos == 1 && !(c->tait_gamma > 1)) return fail(h, WBSPH_E_INVAL, "tait_gamma must exceed 1");
+  if (c->precision != WBSPH_FP64 && c->precision != WBSPH_MIXED)
+    return fail(h, WBSPH_E_INVAL, "unknown precision");
+  for (int k = 0; k < c->dim; ++k)
+    if (!(c->domain_max[k] > c->domain_min[k])) return fail(h, WBSPH_E_INVAL, "empty domain on axis %d", k);
+  if ((c->alloc == nullptr) != (c->free == nullptr))
+    return fail(h, WBSPH_E_INVAL, "alloc and free hooks must be given together");
+  return WBSPH_OK;
+}
+
+extern "C" int wbsph_config_default(wbsph_config* cfg, int dim) {
+  if (!cfg || (dim != 2 && dim != 3)) return WBSPH_E_INVAL;
+  memset(cfg, 0, sizeof *cfg);
+  cfg->dim = dim;
+  cfg->dx = 0.01;
+  cfg->h_over_dx = 1.5;
+  cfg->rho0 = 1000.0;
+  cfg->c0 = 30.0;
+  cfg->nu = 1e-4;
+  cfg->g[dim - 1] = -9.81;
+  cfg->cfl = 0.2;
+  cfg->delta = 0.1;
+  cfg->pst_R = 0.2;
+  cfg->pst_n = 4.0;
+  cfg->tic_lambda = 0.75;
+  cfg->use_delta = cfg->use_pst = cfg->use_tic = cfg->use_visc = 1;
+  cfg->eos = 0;
+  cfg->tait_gamma = 7.0;
+  for (int k = 0; k < 3; ++k) cfg->domain_max[k] = 1.0;
+  cfg->precision = WBSPH_FP64;
+  return WBSPH_OK;
+}
+
+extern "C" int wbsph_create(const wbsph_config* cfg, wbsph_handle* out) {
+  if (!out) return WBSPH_E_INVAL;
+  *out = nullptr;
+  wbsph_s* h = new wbsph_s();
+  int rc = validate(cfg, h);
+  if (rc) { delete h; return rc; }
+  h->cfg = *cfg;
+  h->stream = (cudaStream_t)cfg->cuda_stream;
+  rc = derive_params(h);
+  if (rc) { delete h; return rc; }
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return WBSPH_E_CUDA;
+  }
+  *out = h;
+  return WBSPH_OK;
+}
+
+extern "C" void wbsph_destroy(wbsph_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->cfg.device);
+  free_all(h);
+  cudaStreamSynchronize(h->stream);
+  for (auto& e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (auto& e : h->pool) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  delete h;
+}
+
+extern "C" const char* wbsph_last_error(wbsph_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+static int allocate(wbsph_s* h, int64_t n) {
+  free_all(h);
+  const int d = h->cfg.dim;
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  auto D = [&](size_t cnt) { return (double*)dev_alloc(h, cnt * sizeof(double)); };
+  auto U32 = [&](size_t cnt) { return (uint32_t*)dev_alloc(h, cnt * sizeof(uint32_t)); };
+  for (State* s : {&h->A, &h->B}) {
+    s->x = D(d * nn); s->u = D(d * nn); s->phi = D(nn);
+    s->x0 = D(d * nn); s->u0 = D(d * nn); s->phi0 = D(nn);
+    s->mass = D(nn); s->normal = D(d * nn);
+    s->type = (uint8_t*)dev_alloc(h, nn);
+    s->oid = U32(nn);
+  }
+  Work& w = h->W;
+  w.dudt = D(d * nn); w.dushift = D(d * nn); w.dphidt = D(nn); w.lambda = D(nn); w.vol = D(nn);
+  w.xf = (float4*)dev_alloc(h, nn * sizeof(float4));
+  w.key = U32(nn); w.key_alt = U32(nn); w.perm = U32(nn); w.perm_alt = U32(nn);
+  w.cell_lb = U32((size_t)h->P.ncells + 1);
+  w.fluid_list = U32(nn);
+  w.block_cnt = U32((size_t)div_up((int64_t)nn, 1024) + 1);
+  w.hist = U32((size_t)radix_sort_scratch_words((int64_t)nn));
+  w.umax_bits = (unsigned long long*)dev_alloc(h, 8);
+  w.scalars = D(4);
+  w.status = (unsigned*)dev_alloc(h, sizeof(unsigned));
+  for (void* p : h->blocks)
+    if (!p) return fail(h, WBSPH_E_NOMEM, "device allocation failed");
+  if (h->blocks.size() != 2 * 10 + 17) return fail(h, WBSPH_E_NOMEM, "device allocation failed");
+  return WBSPH_OK;
+}
+
+__global__ void k_iota(uint32_t* a, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (uint32_t)i;
+}
+
+extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, const double* u,
+                                   const double* phi, const double* mass, const uint8_t* type,
+                                   const double* normal, int where) {
+  if (!h) return WBSPH_E_INVAL;
+  if (n < 0 || n > (int64_t)0x7FFFFFFF) return fail(h, WBSPH_E_INVAL, "particle count out of range");
+  if (n > 0 && (!x || !u || !phi || !type)) return fail(h, WBSPH_E_INVAL, "x, u, phi and type are required");
+  if (where != WBSPH_HOST && where != WBSPH_DEVICE) return fail(h, WBSPH_E_INVAL, "bad 'where'");
+  CK(cudaSetDevice(h->cfg.device));
+  const int d = h->cfg.dim;
+  std::vector<uint8_t> ty((size_t)n);
+  cudaMemcpyKind kind = where == WBSPH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (where == WBSPH_HOST) {
+    if (n) memcpy(ty.data(), type, (size_t)n);
+  } else if (n) {
+    CK(cudaMemcpyAsync(ty.data(), type, (size_t)n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  int64_t nf = 0, nd = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (ty[i] == 0) ++nf;
+    else if (ty[i] == 1) ++nd;
+    else return fail(h, WBSPH_E_INVAL, "particle %lld has type %d (0 fluid, 1 dummy)", (long long)i, ty[i]);
+  }
+  if (nd > 0 && !normal) return fail(h, WBSPH_E_INVAL, "dummy particles need normals");
+  h->loaded = false;
+  int rc = allocate(h, n);
+  if (rc) return rc;
+  h->n = n; h->nf = nf; h->nd = nd;
+  size_t vb = (size_t)n * sizeof(double);
+  if (n) {
+    CK(cudaMemcpyAsync(h->A.x, x, d * vb, kind, h->stream));
+    CK(cudaMemcpyAsync(h->A.u, u, d * vb, kind, h->stream));
+    CK(cudaMemcpyAsync(h->A.phi, phi, vb, kind, h->stream));
+    CK(cudaMemcpyAsync(h->A.type, ty.data(), (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    if (normal) CK(cudaMemcpyAsync(h->A.normal, normal, d * vb, kind, h->stream));
+    else CK(cudaMemsetAsync(h->A.normal, 0, d * vb, h->stream));
+    if (mass) CK(cudaMemcpyAsync(h->A.mass, mass, vb, kind, h->stream));
+    else launch_mass(h->P, h->A.phi, h->A.mass, n, h->stream);
+    k_iota<<<(unsigned)div_up(n, 256), 256, 0, h->stream>>>(h->A.oid, n);
+    h->launches += mass ? 1 : 2;
+  }
+  CK(cudaMemsetAsync(h->W.scalars, 0, 4 * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->W.status, 0, sizeof(unsigned), h->stream));
+  CK(cudaMemsetAsync(h->W.umax_bits, 0, 8, h->stream));
+  if (n) {
+    CK(cudaMemsetAsync(h->W.dudt, 0, d * vb, h->stream));
+    CK(cudaMemsetAsync(h->W.dushift, 0, d * vb, h->stream));
+    CK(cudaMemsetAsync(h->W.dphidt, 0, vb, h->stream));
+    CK(cudaMemsetAsync(h->W.lambda, 0, vb, h->stream));
+    CK(cudaMemsetAsync(h->W.vol, 0, vb, h->stream));
+  }
+  rc = check_launch(h, "set_particles");
+  if (rc) return rc;
+  if (where == WBSPH_HOST) CK(cudaStreamSynchronize(h->stream));
+  h->steps = 0;
+  h->loaded = true;
+  return WBSPH_OK;
+}
+
+// Neighbour build for the current positions (stage 2 also carries y^n).
+static int build(wbsph_s* h, bool with_base) {
+  const int64_t n = h->n;
+  if (n == 0) return WBSPH_OK;
+  cudaStream_t st = h->stream;
+  {
+    ProfScope ps(h, WBSPH_K_KEYS);
+    launch_cell_keys(h->P, h->A, h->W, n, st);
+  }
+  int l = 0;
+  {
+    ProfScope ps(h, WBSPH_K_SORT);
+    launch_radix_sort(h->P, h->W, n, st, &l);
+  }
+  {
+    ProfScope ps(h, WBSPH_K_REORDER);
+    launch_gather(h->P, h->A, h->B, h->W, n, with_base, st);
+  }
+  std::swap(h->A, h->B);
+  {
+    ProfScope ps(h, WBSPH_K_CELLS);
+    launch_cell_bounds(h->P, h->W, n, st);
+    launch_fluid_list(h->A, h->W, n, 0, st, &l);
+  }
+  h->launches += 3 + l;
+  return check_launch(h, "neighbour build");
+}
+
+static int rates(wbsph_s* h, int stage2) {
+  const int64_t n = h->n;
+  cudaStream_t st = h->stream;
+  {
+    ProfScope ps(h, WBSPH_K_PREPASS);
+    launch_prepass(h->P, h->A, h->W, n, stage2, st);
+  }
+  if (!stage2) {
+    ProfScope ps(h, WBSPH_K_OTHER);
+    launch_time_step(h->P, h->W, st);
+  }
+  {
+    ProfScope ps(h, WBSPH_K_PAIR);
+    if (h->cfg.precision == WBSPH_MIXED) {
+      int rc = launch_mixed_stage(h->P, h->A, h->W, n, h->nf, stage2, st);
+      if (rc) return fail(h, rc, "mixed path not available in this library");
+    } else {
+      launch_pair_fp64(h->P, h->A, h->W, n, h->nf, stage2, st);
+    }
+  }
+  h->launches += (n ? 1 : 0) + (stage2 ? 0 : 1) + (h->nf ? 1 : 0);
+  return check_launch(h, "stage rates");
+}
+
+extern "C" int wbsph_build_neighbors(wbsph_handle h) {
+  if (!h) return WBSPH_E_INVAL;
+  if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
+  CK(cudaSetDevice(h->cfg.device));
+  return build(h, false);
+}
+
+extern "C" int wbsph_eval_rates(wbsph_handle h) {
+  if (!h) return WBSPH_E_INVAL;
+  if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
+  CK(cudaSetDevice(h->cfg.device));
+  int rc = build(h, false);
+  if (rc) return rc;
+  return rates(h, 0);
+}
+
+extern "C" int wbsph_step(wbsph_handle h, int64_t nsteps) {
+  if (!h) return WBSPH_E_INVAL;
+  if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
+  if (nsteps < 0) return fail(h, WBSPH_E_INVAL, "nsteps < 0");
+  CK(cudaSetDevice(h->cfg.device));
+  for (int64_t s = 0; s < nsteps; ++s) {
+    int rc = build(h, false);
+    if (rc) return rc;
+    rc = rates(h, 0);
+    if (rc) return rc;
+    {
+      ProfScope ps(h, WBSPH_K_UPDATE);
+      launch_rk_stage(h->P, h->A, h->W, h->n, 1, h->stream);
+    }
+    rc = build(h, true);
+    if (rc) return rc;
+    rc = rates(h, 1);
+    if (rc) return rc;
+    {
+      ProfScope ps(h, WBSPH_K_UPDATE);
+      launch_rk_stage(h->P, h->A, h->W, h->n, 2, h->stream);
+    }
+    h->launches += 2;
+    rc = check_launch(h, "step");
+    if (rc) return rc;
+    ++h->steps;
+  }
+  return WBSPH_OK;
+}
+
+static int read_status(wbsph_s* h) {
+  unsigned s = 0;
+  CK(cudaMemcpyAsync(&s, h->W.status, sizeof s, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (!s) return WBSPH_OK;
+  if (s & kStatDomain) return fail(h, WBSPH_E_DOMAIN, "a particle left the domain");
+  if (s & kStatSingular) return fail(h, WBSPH_E_SINGULAR, "singular renormalisation matrix (TIC off)");
+  if (s & kStatNaN) return fail(h, WBSPH_E_NAN, "non-finite rate or state value");
+  if (s & kStatTimeout) return fail(h, WBSPH_E_TIMEOUT, "a bounded device wait gave up");
+  return fail(h, WBSPH_E_CAPACITY, "neighbour list overflow");
+}
+
+extern "C" int wbsph_sync(wbsph_handle h) {
+  if (!h) return WBSPH_E_INVAL;
+  CK(cudaSetDevice(h->cfg.device));
+  CK(cudaStreamSynchronize(h->stream));
+  if (!h->loaded) return WBSPH_OK;
+  return read_status(h);
+}
+
+extern "C" int wbsph_get_fields(wbsph_handle h, int field, double* out, int where) {
+  if (!h) return WBSPH_E_INVAL;
+  if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
+  if (field < 0 || field > WBSPH_FIELD_VOL || !out) return fail(h, WBSPH_E_INVAL, "bad field or output");
+  if (where != WBSPH_HOST && where != WBSPH_DEVICE) return fail(h, WBSPH_E_INVAL, "bad 'where'");
+  CK(cudaSetDevice(h->cfg.device));
+  int rc = read_status(h);
+  if (rc) return rc;
+  const int64_t n = h->n;
+  if (n == 0) return WBSPH_OK;
+  bool vec = field == WBSPH_FIELD_X || field == WBSPH_FIELD_U || field == WBSPH_FIELD_DUDT ||
+             field == WBSPH_FIELD_DUSHIFT;
+  size_t bytes = (size_t)n * (vec ? h->cfg.dim : 1) * sizeof(double);
+  double* tmp = out;
+  void* scratch = nullptr;
+  if (where == WBSPH_HOST) {
+    CK(cudaMallocAsync(&scratch, bytes, h->stream));
+    tmp = (double*)scratch;
+  }
+  launch_field(h->P, h->A, h->W, n, field, tmp, h->stream);
+  h->launches += 1;
+  rc = check_launch(h, "get_fields");
+  if (!rc && where == WBSPH_HOST) {
+    cudaError_t e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) rc = fail(h, WBSPH_E_CUDA, "copy out: %s", cudaGetErrorString(e));
+  }
+  if (scratch) cudaFreeAsync(scratch, h->stream);
+  CK(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+extern "C" int wbsph_get_cell_keys(wbsph_handle h, uint32_t* keys_sorted, uint32_t* ids_sorted) {
+  if (!h) return WBSPH_E_INVAL;
+  if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
+  CK(cudaSetDevice(h->cfg.device));
+  int rc = read_status(h);
+  if (rc) return rc;
+  if (h->n == 0) return WBSPH_OK;
+  if (keys_sorted) CK(cudaMemcpyAsync(keys_sorted, h->W.key, h->n * 4, cudaMemcpyDeviceToHost, h->stream));
+  if (ids_sorted) CK(cudaMemcpyAsync(ids_sorted, h->A.oid, h->n * 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return WBSPH_OK;
+}
+
+extern "C" int64_t wbsph_get_neighbors(wbsph_handle h, int64_t* row_ptr, int32_t* cols, int64_t cap) {
+  if (!h || !row_ptr) return WBSPH_E_INVAL;
+  if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
+  CK(cudaSetDevice(h->cfg.device));
+  const int64_t n = h->n;
+  int rc = build(h, false);
+  if (rc) return rc;
+  rc = read_status(h);
+  if (rc) return rc;
+  row_ptr[0] = 0;
+  if (n == 0) return 0;
+  uint32_t* counts = nullptr;
+  CK(cudaMallocAsync((void**)&counts, n * 4, h->stream));
+  launch_count_neighbors(h->P, h->A, h->W, n, counts, h->stream);
+  std::vector<uint32_t> hc((size_t)n);
+  CK(cudaMemcpyAsync(hc.data(), counts, n * 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  cudaFreeAsync(counts, h->stream);
+  for (int64_t i = 0; i < n; ++i) row_ptr[i + 1] = row_ptr[i] + hc[i];
+  int64_t nnz = row_ptr[n];
+  h->launches += 1;
+  if (!cols) return nnz;
+  if (nnz > cap) return fail(h, WBSPH_E_CAPACITY, "need %lld entries", (long long)nnz);
+  int64_t* drow = nullptr;
+  int32_t* dcol = nullptr;
+  CK(cudaMallocAsync((void**)&drow, (n + 1) * 8, h->stream));
+  CK(cudaMallocAsync((void**)&dcol, (nnz > 0 ? nnz : 1) * 4, h->stream));
+  CK(cudaMemcpyAsync(drow, row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, h->stream));
+  launch_fill_neighbors(h->P, h->A, h->W, n, drow, dcol, h->stream);
+  h->launches += 1;
+  if (nnz) CK(cudaMemcpyAsync(cols, dcol, nnz * 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  cudaFreeAsync(drow, h->stream);
+  cudaFreeAsync(dcol, h->stream);
+  CK(cudaStreamSynchronize(h->stream));
+  for (int64_t i = 0; i < n; ++i) std::sort(cols + row_ptr[i], cols + row_ptr[i + 1]);
+  return nnz;
+}
+
+extern "C" int wbsph_get_stats(wbsph_handle h, wbsph_stats* out) {
+  if (!h || !out) return WBSPH_E_INVAL;
+  memset(out, 0, sizeof *out);
+  out->n = h->n; out->n_fluid = h->nf; out->n_dummy = h->nd;
+  out->ncells = h->P.ncells;
+  for (int k = 0; k < 3; ++k) out->grid[k] = h->P.nc[k];
+  out->steps = h->steps;
+  out->launches = h->launches;
+  out->device_bytes = h->device_bytes;
+  if (h->loaded) {
+    double sc[2] = {0, 0};
+    CK(cudaSetDevice(h->cfg.device));
+    CK(cudaMemcpyAsync(sc, h->W.scalars, sizeof sc, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out->t = sc[0];
+    out->dt = sc[1];
+  }
+  return WBSPH_OK;
+}
+
+extern "C" int wbsph_set_profiling(wbsph_handle h, int on) {
+  if (!h) return WBSPH_E_INVAL;
+  h->prof = on != 0;
+  return WBSPH_OK;
+}
+
+extern "C" int wbsph_get_profile(wbsph_handle h, double* ms, int64_t* launches, int reset) {
+  if (!h) return WBSPH_E_INVAL;
+  CK(cudaSetDevice(h->cfg.device));
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto& e : h->events) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e.a, e.b);
+    h->prof_ms[e.cls] += t;
+    h->prof_cnt[e.cls] += 1;
+    h->pool.push_back(e);
+  }
+  h->events.clear();
+  for (int k = 0; k < WBSPH_K_COUNT; ++k) {
+    if (ms) ms[k] = h->prof_ms[k];
+    if (launches) launches[k] = h->prof_cnt[k];
+    if (reset) { h->prof_ms[k] = 0; h->prof_cnt[k] = 0; }
+  }
+  return WBSPH_OK;
+}
+
+// ---- small kernels owned by the engine ----
+namespace wbsph {
+__global__ void k_mass(Params p, const double* phi, double* mass, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double rho = p.eos == 0 ? p.rho0 * exp(phi[i] / p.c0sq)
+                          : p.rho0 * pow(1.0 + (p.gamma - 1.0) * phi[i] / p.c0sq, 1.0 / (p.gamma - 1.0));
+  double vol = p.dim == 2 ? p.dx * p.dx : p.dx * p.dx * p.dx;
+  mass[i] = rho * vol;
+}
+
+void launch_mass(const Params& p, const double* phi, double* mass, int64_t n, cudaStream_t st) {
+  k_mass<<<(unsigned)div_up(n, 256), 256, 0, st>>>(p, phi, mass, n);
+}
+}  // namespace wbsph

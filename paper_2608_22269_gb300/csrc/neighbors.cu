@@ -1,0 +1,307 @@
+// neighbors.cu -- cell-linked-list neighbour build (Sec. 3, Eqs. hashid and
+// ixyz, Algorithm 1): cell key per particle, stable LSD radix sort of
+// (key, particle index), gather of all particle data into key order, and a
+// lower-bound table giving the sorted index range of any run of cells.
+#include "common.cuh"
+#include "neighbor_iter.cuh"
+
+namespace wbsph {
+
+// ---------------------------------------------------------------------------
+// Cell key (Eqs. hashid, ixyz): i_k = floor((x_k - x_min,k) / R), R = 2h;
+// key = i_x + i_y N_x + i_z N_x N_y. The subtraction and the division are
+// IEEE round-to-nearest (explicit intrinsics) so the keys equal the CPU
+// definition bit for bit.
+// ---------------------------------------------------------------------------
+__global__ void k_cell_keys(Params p, const double* __restrict__ x, int64_t n,
+                            uint32_t* __restrict__ key, unsigned* status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t ic[3] = {0, 0, 0};
+  bool bad = false;
+  for (int k = 0; k < p.dim; ++k) {
+    double xk = x[k * n + i];
+    if (!(xk >= p.domain_min[k] && xk <= p.domain_max[k])) {
+      bad = true;
+      continue;
+    }
+    ic[k] = (int64_t)floor(__ddiv_rn(__dsub_rn(xk, p.domain_min[k]), p.R));
+    if (ic[k] >= p.nc[k]) ic[k] = p.nc[k] - 1;  // unreachable for in-domain x; guards indexing
+  }
+  if (bad) {
+    atomicOr(status, kStatDomain);
+    key[i] = 0;
+    return;
+  }
+  key[i] = (uint32_t)(ic[0] + ic[1] * (int64_t)p.nc[0] + ic[2] * (int64_t)p.nc[0] * p.nc[1]);
+}
+
+void launch_cell_keys(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  k_cell_keys<<<(unsigned)div_up(n, 256), 256, 0, st>>>(p, s.x, n, w.key, w.status);
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of 32-bit keys with 32-bit values, 8-bit digits.
+// Per pass: tile histograms (digit-major table), one exclusive scan of the
+// table, then a scatter that ranks equal digits inside a tile in index order
+// (warp match + per-warp counts), which keeps the sort stable.
+// ---------------------------------------------------------------------------
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int SCAN_THREADS = 1024;
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n,
+                                                          int shift, uint32_t mask,
+                                                          uint32_t* __restrict__ hist, int64_t nblocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = blockIdx.x * (int64_t)RS_TILE;
+#pragma unroll 4
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    int64_t i = base + r * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of `total` 32-bit counts in place, one block.
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_exclusive(uint32_t* data, int64_t total) {
+  __shared__ uint32_t part[SCAN_THREADS];
+  int t = threadIdx.x;
+  int64_t chunk = div_up(total, SCAN_THREADS);
+  int64_t beg = t * chunk, end = beg + chunk < total ? beg + chunk : total;
+  uint32_t s = 0;
+  for (int64_t i = beg; i < end; ++i) s += data[i];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+    uint32_t v = t >= off ? part[t - off] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[t] - s;  // exclusive prefix of this chunk
+  for (int64_t i = beg; i < end; ++i) {
+    uint32_t v = data[i];
+    data[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift,
+    uint32_t mask, const uint32_t* __restrict__ hist, int64_t nblocks) {
+  __shared__ uint32_t offs[256];
+  __shared__ uint32_t wcnt[RS_WARPS][256];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  offs[t] = hist[(int64_t)t * nblocks + blockIdx.x];
+  int64_t base = blockIdx.x * (int64_t)RS_TILE;
+  for (int r = 0; r < RS_ITEMS; ++r) {
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) wcnt[w][t] = 0;
+    __syncthreads();
+    int64_t i = base + r * RS_THREADS + t;
+    bool valid = i < n;
+    uint32_t key = valid ? keys_in[i] : 0u;
+    uint32_t digit = valid ? ((key >> shift) & mask) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, digit);
+    uint32_t rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = offs[digit] + rank;
+      for (int w = 0; w < warp; ++w) pos += wcnt[w][digit];
+      keys_out[pos] = key;
+      vals_out[pos] = vals_in ? vals_in[i] : (uint32_t)i;
+    }
+    __syncthreads();
+    uint32_t add = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) add += wcnt[w][t];
+    offs[t] += add;
+    __syncthreads();
+  }
+}
+
+int radix_sort_scratch_words(int64_t n) { return (int)(256 * div_up(n > 0 ? n : 1, RS_TILE)); }
+
+static int bits_for(int64_t ncells) {
+  int b = 1;
+  while (b < 32 && (int64_t(1) << b) < ncells) ++b;
+  return b;
+}
+
+void launch_radix_sort(const Params& p, Work& w, int64_t n, cudaStream_t st, int* launches) {
+  if (n == 0) return;
+  int64_t nblocks = div_up(n, RS_TILE);
+  int bits = bits_for(p.ncells);
+  const uint32_t* vin = nullptr;
+  for (int shift = 0; shift < bits; shift += 8) {
+    int b = bits - shift < 8 ? bits - shift : 8;
+    uint32_t mask = (1u << b) - 1u;
+    k_radix_hist<<<(unsigned)nblocks, RS_THREADS, 0, st>>>(w.key, n, shift, mask, w.hist, nblocks);
+    k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(w.hist, 256 * nblocks);
+    k_radix_scatter<<<(unsigned)nblocks, RS_THREADS, 0, st>>>(w.key, vin, w.key_alt, w.perm_alt, n,
+                                                             shift, mask, w.hist, nblocks);
+    *launches += 3;
+    uint32_t* tk = w.key; w.key = w.key_alt; w.key_alt = tk;
+    uint32_t* tp = w.perm; w.perm = w.perm_alt; w.perm_alt = tp;
+    vin = w.perm;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reorder (Sec. 3: particles of one cell stored contiguously): gather every
+// per-particle array by the sort permutation; also writes the FP32 position
+// copy used by the candidate prefilter.
+// ---------------------------------------------------------------------------
+__global__ void k_gather(int dim, State src, State dst, const uint32_t* __restrict__ perm, int64_t n,
+                         int with_base, float4* __restrict__ xf) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t j = perm[i];
+  float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = 0; k < dim; ++k) {
+    double xv = src.x[k * n + j];
+    dst.x[k * n + i] = xv;
+    dst.u[k * n + i] = src.u[k * n + j];
+    dst.normal[k * n + i] = src.normal[k * n + j];
+    if (with_base) {
+      dst.x0[k * n + i] = src.x0[k * n + j];
+      dst.u0[k * n + i] = src.u0[k * n + j];
+    }
+    float fv = (float)xv;
+    if (k == 0) f.x = fv; else if (k == 1) f.y = fv; else f.z = fv;
+  }
+  dst.phi[i] = src.phi[j];
+  if (with_base) dst.phi0[i] = src.phi0[j];
+  dst.mass[i] = src.mass[j];
+  dst.type[i] = src.type[j];
+  dst.oid[i] = src.oid[j];
+  xf[i] = f;
+}
+
+void launch_gather(const Params& p, const State& src, const State& dst, const Work& w, int64_t n,
+                   bool with_base, cudaStream_t st) {
+  if (n == 0) return;
+  k_gather<<<(unsigned)div_up(n, 256), 256, 0, st>>>(p.dim, src, dst, w.perm, n, with_base ? 1 : 0,
+                                                     w.xf);
+}
+
+// lb[c] = number of sorted keys < c, for c in [0, ncells]: the particles of
+// cells [a, b] occupy sorted positions [lb[a], lb[b + 1]).
+__global__ void k_cell_lower_bounds(const uint32_t* __restrict__ key, int64_t n, int64_t ncells,
+                                    uint32_t* __restrict__ lb) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c > ncells) return;
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)key[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  lb[c] = (uint32_t)lo;
+}
+
+void launch_cell_bounds(const Params& p, const Work& w, int64_t n, cudaStream_t st) {
+  k_cell_lower_bounds<<<(unsigned)div_up(p.ncells + 1, 256), 256, 0, st>>>(w.key, n, p.ncells,
+                                                                           w.cell_lb);
+}
+
+// ---------------------------------------------------------------------------
+// Ordered compaction of the sorted indices of fluid particles (the pair
+// pass runs over fluid particles only).
+// ---------------------------------------------------------------------------
+constexpr int CMP_THREADS = 1024;
+
+__global__ void __launch_bounds__(CMP_THREADS) k_count_fluid(const uint8_t* __restrict__ type, int64_t n,
+                                                            uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t wsum[CMP_THREADS / 32];
+  int64_t i = blockIdx.x * (int64_t)CMP_THREADS + threadIdx.x;
+  bool f = i < n && type[i] == kFluid;
+  unsigned b = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int k = 0; k < CMP_THREADS / 32; ++k) s += wsum[k];
+    cnt[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(CMP_THREADS) k_write_fluid(const uint8_t* __restrict__ type, int64_t n,
+                                                            const uint32_t* __restrict__ off,
+                                                            uint32_t* __restrict__ list) {
+  __shared__ uint32_t wsum[CMP_THREADS / 32];
+  int64_t i = blockIdx.x * (int64_t)CMP_THREADS + threadIdx.x;
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool f = i < n && type[i] == kFluid;
+  unsigned b = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) wsum[warp] = __popc(b);
+  __syncthreads();
+  uint32_t pos = off[blockIdx.x];
+  for (int k = 0; k < warp; ++k) pos += wsum[k];
+  pos += __popc(b & ((1u << lane) - 1u));
+  if (f) list[pos] = (uint32_t)i;
+}
+
+void launch_fluid_list(const State& s, const Work& w, int64_t n, int64_t nblocks_scan,
+                       cudaStream_t st, int* launches) {
+  if (n == 0) return;
+  int64_t nb = div_up(n, CMP_THREADS);
+  (void)nblocks_scan;
+  k_count_fluid<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, w.block_cnt);
+  k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(w.block_cnt, nb);
+  k_write_fluid<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, w.block_cnt, w.fluid_list);
+  *launches += 3;
+}
+
+// ---------------------------------------------------------------------------
+// Test hook: the neighbour lists themselves (all particle types), with the
+// same candidate enumeration and exact FP64 test as the pair pass.
+// ---------------------------------------------------------------------------
+__global__ void k_count_neighbors(Params p, State s, Work w, int64_t n, uint32_t* counts) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t c = 0;
+  CandidateIter it;
+  it.init(p, w, n, (uint32_t)i);
+  uint32_t j;
+  while (it.next(p, w, j)) {
+    if (exact_neighbor(p, s.x, n, (uint32_t)i, j)) ++c;
+  }
+  counts[s.oid[i]] = c;
+}
+
+__global__ void k_fill_neighbors(Params p, State s, Work w, int64_t n, const int64_t* row_ptr,
+                                 int32_t* cols) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = row_ptr[s.oid[i]];
+  CandidateIter it;
+  it.init(p, w, n, (uint32_t)i);
+  uint32_t j;
+  while (it.next(p, w, j)) {
+    if (exact_neighbor(p, s.x, n, (uint32_t)i, j)) cols[o++] = (int32_t)s.oid[j];
+  }
+}
+
+void launch_count_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
+                            uint32_t* counts, cudaStream_t st) {
+  if (n == 0) return;
+  k_count_neighbors<<<(unsigned)div_up(n, 128), 128, 0, st>>>(p, s, w, n, counts);
+}
+
+void launch_fill_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
+                           const int64_t* row_ptr_by_oid, int32_t* cols, cudaStream_t st) {
+  if (n == 0) return;
+  k_fill_neighbors<<<(unsigned)div_up(n, 128), 128, 0, st>>>(p, s, w, n, row_ptr_by_oid, cols);
+}
+
+}  // namespace wbsph

@@ -1,0 +1,255 @@
+"""Python binding of the C-ABI in ``include/wbsph.h`` (argument marshalling only).
+
+Every step of the hot path runs in the CUDA library ``libwbsph.so`` built
+in-tree by :mod:`paper_2608_22269_gb300.build`; this module only converts
+arguments. PyTorch supplies device memory (through its caching allocator,
+passed to the library as allocation callbacks) and the CUDA stream. There is
+no CPU fallback: if the library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERRORS = {-1: "WBSPH_E_INVAL", -2: "WBSPH_E_NOMEM", -3: "WBSPH_E_CUDA", -4: "WBSPH_E_DOMAIN",
+          -5: "WBSPH_E_SINGULAR", -6: "WBSPH_E_NAN", -7: "WBSPH_E_TIMEOUT", -8: "WBSPH_E_STATE",
+          -9: "WBSPH_E_CAPACITY", -10: "WBSPH_E_NOSYM"}
+FP64, MIXED = 0, 1
+HOST, DEVICE = 0, 1
+FIELDS = {"x": 0, "u": 1, "phi": 2, "rho": 3, "p": 4, "dudt": 5, "dphidt": 6, "dushift": 7,
+          "lambda": 8, "mass": 9, "vol": 10}
+VECTOR_FIELDS = {"x", "u", "dudt", "dushift"}
+KERNEL_CLASSES = ["keys", "sort", "reorder", "cells", "prepass", "pair", "update", "other"]
+
+#: every symbol declared in include/wbsph.h
+SYMBOLS = ["wbsph_config_default", "wbsph_create", "wbsph_set_particles", "wbsph_build_neighbors",
+           "wbsph_eval_rates", "wbsph_step", "wbsph_sync", "wbsph_get_fields",
+           "wbsph_get_cell_keys", "wbsph_get_neighbors", "wbsph_get_stats", "wbsph_set_profiling",
+           "wbsph_get_profile", "wbsph_destroy", "wbsph_last_error", "wbsph_status_string"]
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class Config(C.Structure):
+    _fields_ = [("dim", C.c_int), ("dx", C.c_double), ("h_over_dx", C.c_double),
+                ("rho0", C.c_double), ("c0", C.c_double), ("nu", C.c_double),
+                ("g", C.c_double * 3), ("cfl", C.c_double), ("delta", C.c_double),
+                ("pst_R", C.c_double), ("pst_n", C.c_double), ("tic_lambda", C.c_double),
+                ("use_delta", C.c_int), ("use_pst", C.c_int), ("use_tic", C.c_int),
+                ("use_visc", C.c_int), ("eos", C.c_int), ("tait_gamma", C.c_double),
+                ("domain_min", C.c_double * 3), ("domain_max", C.c_double * 3),
+                ("force_amp", C.c_double * 3), ("force_period", C.c_double),
+                ("fixed_dt", C.c_double), ("precision", C.c_int), ("device", C.c_int),
+                ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p), ("water_height", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_fluid", C.c_int64), ("n_dummy", C.c_int64),
+                ("ncells", C.c_int64), ("grid", C.c_int64 * 3), ("steps", C.c_int64),
+                ("launches", C.c_int64), ("device_bytes", C.c_int64), ("t", C.c_double),
+                ("dt", C.c_double)]
+
+
+class WbsphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libwbsph.so (raises if it is not built; no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        _build.build()
+    L = C.CDLL(path)
+    P, i64, I = C.c_void_p, C.c_int64, C.c_int
+    sig = {
+        "wbsph_config_default": (I, [P, I]),
+        "wbsph_create": (I, [P, P]),
+        "wbsph_set_particles": (I, [P, i64, P, P, P, P, P, P, I]),
+        "wbsph_build_neighbors": (I, [P]),
+        "wbsph_eval_rates": (I, [P]),
+        "wbsph_step": (I, [P, i64]),
+        "wbsph_sync": (I, [P]),
+        "wbsph_get_fields": (I, [P, I, P, I]),
+        "wbsph_get_cell_keys": (I, [P, P, P]),
+        "wbsph_get_neighbors": (i64, [P, P, P, i64]),
+        "wbsph_get_stats": (I, [P, P]),
+        "wbsph_set_profiling": (I, [P, I]),
+        "wbsph_get_profile": (I, [P, P, P, I]),
+        "wbsph_destroy": (None, [P]),
+        "wbsph_last_error": (C.c_char_p, [P]),
+        "wbsph_status_string": (C.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())  # torch tensor
+
+
+def make_config(params: dict, precision: int = FP64, stream=None, device: int = 0,
+                water_height: float = 0.0) -> Config:
+    cfg = Config()
+    load().wbsph_config_default(C.byref(cfg), int(params["dim"]))
+    for name, _ in Config._fields_:
+        if name in params and name not in ("alloc", "free", "alloc_ctx", "cuda_stream"):
+            v = params[name]
+            if isinstance(v, (list, tuple, np.ndarray)):
+                arr = getattr(cfg, name)
+                for k in range(3):
+                    arr[k] = float(v[k]) if k < len(v) else 0.0
+            else:
+                setattr(cfg, name, v)
+    cfg.precision = precision
+    cfg.device = device
+    cfg.cuda_stream = stream
+    cfg.water_height = water_height
+    return cfg
+
+
+class Sim:
+    """One simulation handle. ``params`` is a scene parameter dict; device
+    memory comes from PyTorch's caching allocator on the current stream."""
+
+    def __init__(self, params: dict, precision: int = FP64, water_height: float = 0.0,
+                 device: int = 0, use_torch_allocator: bool = True):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.dim = int(params["dim"])
+        self.device = device
+        self.stream = torch.cuda.current_stream(device)
+        cfg = make_config(params, precision, C.c_void_p(self.stream.cuda_stream), device,
+                          water_height)
+        if use_torch_allocator:
+            def _alloc(size, stream, ctx):
+                return torch.cuda.caching_allocator_alloc(int(size), device, self.stream)
+
+            def _free(ptr, stream, ctx):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._alloc_cb = ALLOC_FN(_alloc)
+            self._free_cb = FREE_FN(_free)
+            cfg.alloc = self._alloc_cb
+            cfg.free = self._free_cb
+        self.cfg = cfg
+        h = C.c_void_p()
+        rc = self.lib.wbsph_create(C.byref(cfg), C.byref(h))
+        if rc != OK:
+            raise WbsphError(rc, self.lib.wbsph_status_string(rc).decode())
+        self.h = h
+        self.n = 0
+
+    def _check(self, rc):
+        if rc < 0:
+            raise WbsphError(int(rc), self.lib.wbsph_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.wbsph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C-ABI calls ------------------------------------------------------------------------
+    def set_particles(self, x, u, phi, type, normal=None, mass=None):
+        """Host numpy arrays or device torch tensors (float64 SoA, uint8 type)."""
+        dev = not isinstance(x, np.ndarray)
+        if not dev:
+            x, u, phi = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, u, phi))
+            type = np.ascontiguousarray(type, dtype=np.uint8)
+            normal = None if normal is None else np.ascontiguousarray(normal, dtype=np.float64)
+            mass = None if mass is None else np.ascontiguousarray(mass, dtype=np.float64)
+        n = int(phi.shape[0])
+        self._keep = (x, u, phi, type, normal, mass)
+        self._check(self.lib.wbsph_set_particles(self.h, n, _ptr(x), _ptr(u), _ptr(phi), _ptr(mass),
+                                                 _ptr(type), _ptr(normal), DEVICE if dev else HOST))
+        self.n = n
+        return self
+
+    def set_scene(self, scene):
+        return self.set_particles(scene.x, scene.u, scene.phi, scene.type, scene.normal)
+
+    def build_neighbors(self):
+        self._check(self.lib.wbsph_build_neighbors(self.h))
+
+    def eval_rates(self):
+        self._check(self.lib.wbsph_eval_rates(self.h))
+
+    def step(self, nsteps=1):
+        self._check(self.lib.wbsph_step(self.h, int(nsteps)))
+
+    def sync(self):
+        self._check(self.lib.wbsph_sync(self.h))
+
+    def get(self, field: str, out=None):
+        """Field in the caller's original order: numpy (host) unless ``out``
+        is a device tensor."""
+        comps = self.dim if field in VECTOR_FIELDS else 1
+        shape = (comps, self.n) if comps > 1 else (self.n,)
+        if out is None:
+            out = np.empty(shape, dtype=np.float64)
+        where = HOST if isinstance(out, np.ndarray) else DEVICE
+        self._check(self.lib.wbsph_get_fields(self.h, FIELDS[field], _ptr(out), where))
+        return out
+
+    def cell_keys(self):
+        k = np.empty(self.n, dtype=np.uint32)
+        ids = np.empty(self.n, dtype=np.uint32)
+        self._check(self.lib.wbsph_get_cell_keys(self.h, _ptr(k), _ptr(ids)))
+        return k, ids
+
+    def neighbors(self):
+        row = np.empty(self.n + 1, dtype=np.int64)
+        nnz = self._check(self.lib.wbsph_get_neighbors(self.h, _ptr(row), None, 0))
+        cols = np.empty(max(nnz, 1), dtype=np.int32)
+        self._check(self.lib.wbsph_get_neighbors(self.h, _ptr(row), _ptr(cols), nnz))
+        return row, cols[:nnz]
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self.lib.wbsph_get_stats(self.h, C.byref(s)))
+        return {k: (list(getattr(s, k)) if k == "grid" else getattr(s, k)) for k, _ in Stats._fields_}
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.wbsph_set_profiling(self.h, int(on)))
+
+    def profile(self, reset=False) -> dict:
+        ms = (C.c_double * 8)()
+        cnt = (C.c_int64 * 8)()
+        self._check(self.lib.wbsph_get_profile(self.h, ms, cnt, int(reset)))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
