@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the well-balanced WCSPH hot path on GB300.
+
+One step = one SSP-RK2 step of the whole path (two stages, each: cell keys,
+radix sort, reorder, cell bounds, dummy/volume prepass, fused pair pass,
+update) over the synthetic scene named by --workload, inputs resident in HBM.
+Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload dam3d|slosh3d] [--precision fp64|mixed]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on the host cores, on a bounded sample of the same workload.
+Multi-GPU runs are independent replicas (weak scaling): the method's single
+domain is not partitioned across GPUs.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (3D, 1.2M and 17.5M particles): FP64 vs mixed vs surrogate at stated error"
+UNIT = "particle-steps/s"
+
+# FP64 flops of one neighbour pair in the fused pair pass with all terms on
+# (an FMA counts 2): distance 8, reciprocal square root (two Newton steps)
+# 12, kernel scalars 7, velocity difference and normal component 10,
+# interface potential 4, L 12, S 6, C 6, M 18 (3D), D 2, Lambda 6, shifting 16.
+FLOPS_PER_PAIR_3D = 110
+FLOPS_PER_PAIR_2D = 74
+# per fluid particle: eigenvalue, 3x3 inverse, contractions and rates
+FLOPS_EPILOGUE_3D = 260
+# measured FP64 FMA throughput of this GB300 (independent DFMA chains,
+# 152 SMs at 1987 MHz): 5.93e11 DFMA/s = 1.186 TFLOP/s
+FP64_PEAK_TFLOPS = 1.186
+
+WORKLOADS = {
+    "dam3d": dict(
+        make=lambda: _scenes().dam_break_3d(dx=0.0084),
+        sample=lambda: _scenes().dam_break_3d(dx=0.0168),
+        desc=("3D dam break: box 3.2x1.0x1.0 m, water column 1.2x1.0x0.6 m, dx=0.0084 m "
+              "(1,208,207 fluid + 498,949 dummy particles in 3 layers), Wendland C2 h=1.3dx, "
+              "c0=10 sqrt(gH), linear EOS, delta-SPH, shifting and TIC on, adaptive dt (CFL 0.2)"),
+        sample_desc="same scene at dx=0.0168 m (1/8 replica: 153,360 fluid + 127,188 dummy)"),
+    "dam3d_s": dict(
+        make=lambda: _scenes().dam_break_3d(dx=0.0126),
+        sample=lambda: _scenes().dam_break_3d(dx=0.0252),
+        desc=("3D dam break as dam3d at dx=0.0126 m (360,240 fluid + 221,996 dummy particles): the profiling "
+              "case, larger than L2"),
+        sample_desc="same scene at dx=0.0252 m"),
+    "slosh3d": dict(
+        make=lambda: _scenes().sloshing_3d(),
+        sample=lambda: _scenes().sloshing_3d(dx=0.0307),
+        desc=("3D sloshing tank 4.0x2.0x2.0 m, depth 1.0 m, dx=0.00769 m (17,576,000 fluid "
+              "particles + dummies), harmonic forcing A=0.01 m, T=1.5 s, delta-SPH, shifting, TIC on"),
+        sample_desc="same tank at dx=0.0307 m (1/64 replica)"),
+}
+
+
+def _scenes():
+    from paper_2608_22269_gb300 import scenes
+    return scenes
+
+
+def algorithmic_bytes_per_particle_step(dim: int) -> int:
+    """HBM bytes the method must move per fluid particle-step (two stages):
+    per stage the build reads positions and writes keys (8d+4), sorts (3
+    passes x 16 B), reorders the state (2 x (16d+18+8d)), the pair pass reads
+    x, U, phi, V of the particle (8(2d+2)) and writes rates (8(2d+2)), the
+    update reads/writes state (2 x 8(2d+1))."""
+    d = dim
+    per_stage = (8 * d + 4) + 48 + 2 * (24 * d + 18) + 16 * (2 * d + 2) + 16 * (2 * d + 1)
+    return 2 * per_stage
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [v.strip() for v in line.split(",")]
+                if len(f) >= 8 and f[0].replace(".", "").isdigit():
+                    rows.append(f)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][1]),
+                "power_w_max": max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit()),
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def profile_traffic(kernel_file: str, key: str):
+    """DRAM traffic per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = data.get(key)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2608_22269_gb300", "csrc", kernel_file)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if ent.get("source_sha") != sha:
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def cpu_baseline(sample_scene, budget_s=12.0, max_steps=20):
+    import oracle
+    st = oracle.State(sample_scene)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps and (steps < 2 or time.perf_counter() - t0 < budget_s):
+        st.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return sample_scene.n_fluid * steps / dt, steps, dt, oracle.num_threads()
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2608_22269_gb300 import wbsph
+
+    world, rank, local = dist_setup()
+    wl = WORKLOADS[args.workload]
+    t_setup = time.perf_counter()
+    scene = wl["make"]()
+    precision = wbsph.MIXED if args.precision == "mixed" else wbsph.FP64
+    sim = wbsph.Sim(scene.params, precision=precision, water_height=scene.water_height,
+                    device=local)
+    sim.set_scene(scene)
+    dim = scene.params["dim"]
+    nf = scene.n_fluid
+    stream = sim.stream
+
+    sim.step(args.warmup)
+    sim.sync()
+    setup_s = time.perf_counter() - t_setup
+
+    # ---- device-resident timed region ----
+    sim.set_profiling(True)
+    sim.profile(reset=True)
+    st0 = sim.stats()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    sim.sync()
+    st1 = sim.stats()
+    prof = sim.profile(reset=True)
+    sim.set_profiling(False)
+    ms_max = max_over_ranks(ms, world)
+    value = nf * args.steps * world / (ms_max / 1e3)
+
+    pair_ms, pair_n = prof["pair"]
+    pairs = st1["pairs"] - st0["pairs"]
+    pairs_per_launch = pairs / max(pair_n, 1)
+    fpp = FLOPS_PER_PAIR_3D if dim == 3 else FLOPS_PER_PAIR_2D
+    flops_launch = pairs_per_launch * fpp + nf * FLOPS_EPILOGUE_3D
+    achieved = flops_launch / (pair_ms / max(pair_n, 1) / 1e3) / 1e12
+    traffic = profile_traffic("pair_fp64.cu", f"pair_fp64_{args.workload}")
+    roofline = {"bound": "alu", "kernel": "k_pair_fp64<%d>" % dim, "achieved": round(achieved, 4),
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "traffic": traffic,
+                "peak_source": "measured FP64 DFMA throughput of this GB300 (profiles/fp64_alu_peak.md)",
+                "pairs_per_launch": int(pairs_per_launch), "flops_per_pair": fpp,
+                "avg_launch_ms": round(pair_ms / max(pair_n, 1), 4),
+                "share_of_step": round(pair_ms / max(sum(v[0] for v in prof.values()), 1e-9), 4)}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6686.1)
+    bytes_ps = algorithmic_bytes_per_particle_step(dim)
+    hbm_frac = value / world * bytes_ps / (hbm * 1e9)
+
+    # ---- end to end through the C-ABI with pinned host buffers ----
+    k_e2e = max(1, min(args.steps, 5))
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hx, hu, hphi = pin(sim.get("x")), pin(sim.get("u")), pin(sim.get("phi"))
+    htype = pin(scene.type)
+    hnormal, hmass = pin(scene.normal), pin(sim.get("mass"))
+    ox = torch.empty_like(hx).pin_memory()
+    ou = torch.empty_like(hu).pin_memory()
+    ophi = torch.empty_like(hphi).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        sim.set_particles(hx, hu, hphi, htype, hnormal, hmass, where=wbsph.HOST)
+        sim.step(1)
+        sim.get("x", ox)
+        sim.get("u", ou)
+        sim.get("phi", ophi)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    h2d = sum(t.numel() * t.element_size() for t in (hx, hu, hphi, htype, hnormal, hmass))
+    d2h = sum(t.numel() * t.element_size() for t in (ox, ou, ophi))
+    e2e = {"value": round(nf * k_e2e * world / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": k_e2e,
+           "api": "wbsph_set_particles(host) + wbsph_step(1) + wbsph_get_fields(x,u,phi -> host)"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "precision": args.precision, "n_fluid": nf,
+                   "n_total": scene.n, "dim": dim,
+                   "l2": f"inputs larger than L2 ({st1['device_bytes'] / 1e9:.2f} GB resident)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "unit_counted": "fluid particles x steps"},
+        "roofline": roofline,
+        "hbm": {"algorithmic_bytes_per_particle_step": bytes_ps, "achieved_gbs": round(value / world * bytes_ps / 1e9, 1),
+                "peak_gbs": hbm, "frac": round(hbm_frac, 5)},
+        "e2e": e2e,
+        "gpu_launches": int(st1["launches"] - st0["launches"]),
+        "clocks": clk.summary(),
+        "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
+        "setup_s": round(setup_s, 1),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = wl["sample"]()
+        v, steps, secs, cores = cpu_baseline(sample)
+        line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{wl['sample_desc']}, {steps} steps in {secs:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    wl = WORKLOADS[args.workload]
+    sample = wl["sample"]()
+    st = oracle.State(sample)
+    st.step(args.warmup)
+    t0 = time.perf_counter()
+    st.step(args.steps)
+    secs = time.perf_counter() - t0
+    v = sample.n_fluid * args.steps / secs
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "precision": "fp64", "sample": wl["sample_desc"]},
+            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": f"{wl['sample_desc']}, {args.steps} timed steps"},
+            "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dam3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

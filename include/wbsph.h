@@ -111,6 +111,7 @@ typedef struct {
   int64_t launches;         /* kernels launched by this handle so far */
   int64_t device_bytes;     /* device memory held by the handle */
   double t, dt;             /* simulated time and last time step (after a sync) */
+  int64_t pairs;            /* neighbour pairs summed by pair passes since set_particles */
 } wbsph_stats;
 
 /* Kernel classes timed when profiling is on (CUDA events on the stream). */

@@ -85,6 +85,9 @@ struct Work {
   unsigned long long* umax_bits;  // [0]: max |U|^2 over fluid (bits of a non-negative double)
   double* scalars;   // [0] t, [1] dt, [2] U_max of the current stage
   unsigned* status;  // device status word
+  unsigned long long* pairs;  // [0]: neighbour pairs summed by pair passes (units of work)
+  float4* packA;     // n: mixed path, (cell-relative offset, phi - phi_hs) in FP32
+  float4* packB;     // n: mixed path, (U, +-V) in FP32
 };
 
 __host__ __device__ inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }

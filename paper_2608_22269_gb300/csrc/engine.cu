@@ -43,6 +43,8 @@ struct wbsph_s {
   int64_t device_bytes = 0;
   int64_t launches = 0, steps = 0;
   bool loaded = false;
+  bool alloc_failed = false;
+  int64_t n_alloc = -1;  // particle count the buffers were sized for
   std::string err;
   bool prof = false;
   std::vector<ProfEvent> events, pool;
@@ -126,6 +128,9 @@ static void* dev_alloc(wbsph_s* h, size_t bytes) {
   if (p) {
     h->blocks.push_back(p);
     h->device_bytes += (int64_t)bytes;
+  } else {
+    cudaGetLastError();
+    h->alloc_failed = true;
   }
   return p;
 }
@@ -137,6 +142,8 @@ static void free_all(wbsph_s* h) {
   }
   h->blocks.clear();
   h->device_bytes = 0;
+  h->alloc_failed = false;
+  h->n_alloc = -1;
   h->A = State{};
   h->B = State{};
   h->W = Work{};
@@ -303,9 +310,13 @@ static int allocate(wbsph_s* h, int64_t n) {
   w.umax_bits = (unsigned long long*)dev_alloc(h, 8);
   w.scalars = D(4);
   w.status = (unsigned*)dev_alloc(h, sizeof(unsigned));
-  for (void* p : h->blocks)
-    if (!p) return fail(h, WBSPH_E_NOMEM, "device allocation failed");
-  if (h->blocks.size() != 2 * 10 + 17) return fail(h, WBSPH_E_NOMEM, "device allocation failed");
+  w.pairs = (unsigned long long*)dev_alloc(h, 8);
+  if (h->cfg.precision == WBSPH_MIXED) {
+    w.packA = (float4*)dev_alloc(h, nn * sizeof(float4));
+    w.packB = (float4*)dev_alloc(h, nn * sizeof(float4));
+  }
+  if (h->alloc_failed) return fail(h, WBSPH_E_NOMEM, "device allocation failed");
+  h->n_alloc = n;
   return WBSPH_OK;
 }
 
@@ -339,7 +350,8 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
   }
   if (nd > 0 && !normal) return fail(h, WBSPH_E_INVAL, "dummy particles need normals");
   h->loaded = false;
-  int rc = allocate(h, n);
+  int rc = WBSPH_OK;
+  if (n != h->n_alloc || h->blocks.empty()) rc = allocate(h, n);  // same n: reuse the buffers
   if (rc) return rc;
   h->n = n; h->nf = nf; h->nd = nd;
   size_t vb = (size_t)n * sizeof(double);
@@ -358,6 +370,7 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
   CK(cudaMemsetAsync(h->W.scalars, 0, 4 * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->W.status, 0, sizeof(unsigned), h->stream));
   CK(cudaMemsetAsync(h->W.umax_bits, 0, 8, h->stream));
+  CK(cudaMemsetAsync(h->W.pairs, 0, 8, h->stream));
   if (n) {
     CK(cudaMemsetAsync(h->W.dudt, 0, d * vb, h->stream));
     CK(cudaMemsetAsync(h->W.dushift, 0, d * vb, h->stream));
@@ -585,11 +598,14 @@ extern "C" int wbsph_get_stats(wbsph_handle h, wbsph_stats* out) {
   out->device_bytes = h->device_bytes;
   if (h->loaded) {
     double sc[2] = {0, 0};
+    unsigned long long pairs = 0;
     CK(cudaSetDevice(h->cfg.device));
     CK(cudaMemcpyAsync(sc, h->W.scalars, sizeof sc, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&pairs, h->W.pairs, 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     out->t = sc[0];
     out->dt = sc[1];
+    out->pairs = (int64_t)pairs;
   }
   return WBSPH_OK;
 }

@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, 3)
   a.D = 0.0;
 
   const bool pst4 = p.use_pst && p.pst_n == 4.0;
+  unsigned npairs = 0;
   CandidateIter it;
   bool done = !active;
   if (active) it.init(p, w, n, i);
@@ -254,6 +255,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, 3)
 #pragma unroll
       for (int c = 1; c < DIM; ++c) r2 = __dadd_rn(r2, __dmul_rn(r[c], r[c]));
       if (!(r2 <= p.four_h2 && r2 > 0.0)) continue;
+      ++npairs;
       double inv_r = rsqrt_nr(r2);
       double rr = r2 * inv_r;
       double t = fma(-rr, p.inv_two_h, 1.0);
@@ -308,6 +310,8 @@ __global__ void __launch_bounds__(PAIR_THREADS, 3)
     }
     __syncwarp();
   }
+  unsigned wp = __reduce_add_sync(0xffffffffu, npairs);
+  if (lane == 0 && wp) atomicAdd(w.pairs, (unsigned long long)wp);
   if (!active) return;
 
   // ---- epilogue (Eq. sph with the TIC switch, K8/K9 of Sec. 3) ----

@@ -54,7 +54,7 @@ class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_fluid", C.c_int64), ("n_dummy", C.c_int64),
                 ("ncells", C.c_int64), ("grid", C.c_int64 * 3), ("steps", C.c_int64),
                 ("launches", C.c_int64), ("device_bytes", C.c_int64), ("t", C.c_double),
-                ("dt", C.c_double)]
+                ("dt", C.c_double), ("pairs", C.c_int64)]
 
 
 class WbsphError(RuntimeError):
@@ -186,10 +186,14 @@ class Sim:
             pass
 
     # -- C-ABI calls ------------------------------------------------------------------------
-    def set_particles(self, x, u, phi, type, normal=None, mass=None):
-        """Host numpy arrays or device torch tensors (float64 SoA, uint8 type)."""
-        dev = not isinstance(x, np.ndarray)
-        if not dev:
+    def set_particles(self, x, u, phi, type, normal=None, mass=None, where=None):
+        """Host numpy arrays, or torch tensors (float64 SoA, uint8 type) on the
+        device or in (pinned) host memory; ``where`` defaults from the arrays."""
+        if where is None:
+            dev = not isinstance(x, np.ndarray) and x.is_cuda
+        else:
+            dev = where == DEVICE
+        if isinstance(x, np.ndarray):
             x, u, phi = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, u, phi))
             type = np.ascontiguousarray(type, dtype=np.uint8)
             normal = None if normal is None else np.ascontiguousarray(normal, dtype=np.float64)
@@ -223,7 +227,7 @@ class Sim:
         shape = (comps, self.n) if comps > 1 else (self.n,)
         if out is None:
             out = np.empty(shape, dtype=np.float64)
-        where = HOST if isinstance(out, np.ndarray) else DEVICE
+        where = HOST if isinstance(out, np.ndarray) or not out.is_cuda else DEVICE
         self._check(self.lib.wbsph_get_fields(self.h, FIELDS[field], _ptr(out), where))
         return out
 
