@@ -173,6 +173,29 @@ int wbsph_get_stats(wbsph_handle h, wbsph_stats* out);
 int wbsph_set_profiling(wbsph_handle h, int on);
 int wbsph_get_profile(wbsph_handle h, double* ms, int64_t* launches, int reset);
 
+/* Cell keys and stable sort without any device allocation. The paper has no
+ * counterpart: this is a variant of the neighbour build's key and radix-sort
+ * kernels for callers that cannot let a library allocate device memory (a
+ * framework that owns the device memory pool, or a loop that cannot afford
+ * the implicit synchronisation of cudaMalloc/cudaFree).
+ * x: device pointer, dim*n SoA positions; keys_sorted, ids_sorted: device
+ * arrays of n, written with the sorted cell keys and, for each sorted
+ * position, the input index (the same result as wbsph_build_neighbors +
+ * wbsph_get_cell_keys on particles loaded in that order). The grid comes
+ * from h's configuration; h needs no wbsph_set_particles, and the handle's
+ * stream is used and synchronised before returning.
+ * Scratch lives in a file-scope device array sized for WBSPH_NOALLOC_MAX_N
+ * particles (4.3 MB, held by every GPU that loads the library until
+ * the process exits); larger n returns WBSPH_E_CAPACITY. The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) for
+ * that device, so make that first call before any stream capture. All calls
+ * share the array: calls that overlap on the GPU (other threads or streams)
+ * race and must be serialised by the caller. Returns WBSPH_E_DOMAIN if a
+ * particle lies outside the domain. */
+#define WBSPH_NOALLOC_MAX_N 524288
+int wbsph_sort_cells_noalloc(wbsph_handle h, const double* x, int64_t n, uint32_t* keys_sorted,
+                             uint32_t* ids_sorted);
+
 void wbsph_destroy(wbsph_handle h);
 const char* wbsph_last_error(wbsph_handle h);
 const char* wbsph_status_string(int status);

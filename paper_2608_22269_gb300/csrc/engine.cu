@@ -651,3 +651,11 @@ void launch_mass(const Params& p, const double* phi, double* mass, int64_t n, cu
   k_mass<<<(unsigned)div_up(n, 256), 256, 0, st>>>(p, phi, mass, n);
 }
 }  // namespace wbsph
+
+// ---- read-only accessors for other translation units of the library ----
+namespace wbsph {
+const Params* handle_params(wbsph_handle h) { return h ? &h->P : nullptr; }
+cudaStream_t handle_stream(wbsph_handle h) { return h ? h->stream : nullptr; }
+int handle_device(wbsph_handle h) { return h ? h->cfg.device : 0; }
+int handle_fail(wbsph_handle h, int code, const char* msg) { return fail(h, code, "%s", msg); }
+}  // namespace wbsph

@@ -30,7 +30,9 @@ KERNEL_CLASSES = ["keys", "sort", "reorder", "cells", "prepass", "pair", "update
 SYMBOLS = ["wbsph_config_default", "wbsph_create", "wbsph_set_particles", "wbsph_build_neighbors",
            "wbsph_eval_rates", "wbsph_step", "wbsph_sync", "wbsph_get_fields",
            "wbsph_get_cell_keys", "wbsph_get_neighbors", "wbsph_get_stats", "wbsph_set_profiling",
-           "wbsph_get_profile", "wbsph_destroy", "wbsph_last_error", "wbsph_status_string"]
+           "wbsph_get_profile", "wbsph_destroy", "wbsph_last_error", "wbsph_status_string",
+           "wbsph_sort_cells_noalloc"]
+NOALLOC_MAX_N = 524288
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -99,6 +101,7 @@ def load(build_if_missing: bool = False):
         "wbsph_destroy": (None, [P]),
         "wbsph_last_error": (C.c_char_p, [P]),
         "wbsph_status_string": (C.c_char_p, [I]),
+        "wbsph_sort_cells_noalloc": (I, [P, P, i64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -248,6 +251,14 @@ class Sim:
         s = Stats()
         self._check(self.lib.wbsph_get_stats(self.h, C.byref(s)))
         return {k: (list(getattr(s, k)) if k == "grid" else getattr(s, k)) for k, _ in Stats._fields_}
+
+    def sort_cells_noalloc(self, x, keys_sorted, ids_sorted):
+        """wbsph_sort_cells_noalloc on device tensors: x (dim, n) float64,
+        keys_sorted / ids_sorted (n,) 32-bit. Allocates no device memory."""
+        n = int(x.shape[1])
+        self._check(self.lib.wbsph_sort_cells_noalloc(self.h, _ptr(x), n, _ptr(keys_sorted),
+                                                      _ptr(ids_sorted)))
+        return keys_sorted, ids_sorted
 
     def set_profiling(self, on=True):
         self._check(self.lib.wbsph_set_profiling(self.h, int(on)))
