@@ -41,9 +41,14 @@ FLOPS_PER_PAIR_3D = 110
 FLOPS_PER_PAIR_2D = 74
 # per fluid particle: eigenvalue, 3x3 inverse, contractions and rates
 FLOPS_EPILOGUE_3D = 260
-# measured FP64 FMA throughput of this GB300 (independent DFMA chains,
-# 152 SMs at 1987 MHz): 5.93e11 DFMA/s = 1.186 TFLOP/s
+# FP32 flops of one pair in the mixed pass: 78 for the pair terms and
+# 124 for the Kahan-compensated updates of 31 accumulators (4 each)
+FLOPS_PER_PAIR_MIXED_3D = 202
+FLOPS_PER_PAIR_MIXED_2D = 118
+# measured FMA throughput of this GB300 (independent FMA chains, 152 SMs at
+# 1987 MHz): FP64 5.93e11 DFMA/s = 1.186 TFLOP/s; FP32 3.62e13 FFMA/s = 72.4
 FP64_PEAK_TFLOPS = 1.186
+FP32_PEAK_TFLOPS = 72.4
 
 WORKLOADS = {
     "dam3d": dict(
@@ -200,6 +205,108 @@ def cpu_baseline(sample_scene, budget_s=12.0, max_steps=20):
 
 
 # ---------------------------------------------------------------------------
+def time_path(scene, precision, args, world, local):
+    """Warm up, then time args.steps steps device-side; returns the sim and
+    a dict of measurements (CUDA events on the library's stream)."""
+    import torch
+
+    from paper_2608_22269_gb300 import wbsph
+    sim = wbsph.Sim(scene.params, precision=precision, water_height=scene.water_height,
+                    device=local)
+    sim.set_scene(scene)
+    sim.step(args.warmup)
+    sim.sync()
+    sim.set_profiling(True)
+    sim.profile(reset=True)
+    st0 = sim.stats()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(sim.stream)
+        sim.step(args.steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    sim.sync()
+    st1 = sim.stats()
+    prof = sim.profile(reset=True)
+    sim.set_profiling(False)
+    return sim, {"ms": max_over_ranks(ms, world), "st0": st0, "st1": st1, "prof": prof,
+                 "clocks": clk.summary()}
+
+
+def pair_roofline(m, dim, nf, mixed, workload):
+    pair_ms, pair_n = m["prof"]["pair"]
+    pairs = m["st1"]["pairs"] - m["st0"]["pairs"]
+    per_launch = pairs / max(pair_n, 1)
+    avg_ms = pair_ms / max(pair_n, 1)
+    if mixed:
+        fpp = FLOPS_PER_PAIR_MIXED_3D if dim == 3 else FLOPS_PER_PAIR_MIXED_2D
+        flops = per_launch * fpp + nf * 600
+        peak, kernel, src = FP32_PEAK_TFLOPS, "k_pair_mixed<%d>" % dim, "pair_mixed.cu"
+    else:
+        fpp = FLOPS_PER_PAIR_3D if dim == 3 else FLOPS_PER_PAIR_2D
+        flops = per_launch * fpp + nf * FLOPS_EPILOGUE_3D
+        peak, kernel, src = FP64_PEAK_TFLOPS, "k_pair_fp64<%d>" % dim, "pair_fp64.cu"
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    key = ("pair_mixed_" if mixed else "pair_fp64_") + workload
+    total = sum(v[0] for v in m["prof"].values())
+    return {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 4), "peak": peak,
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "traffic": profile_traffic(src, key),
+            "peak_source": ("measured %s FMA throughput of this GB300 (profiles/fp64_alu_peak.md)"
+                            % ("FP32" if mixed else "FP64")),
+            "pairs_per_launch": int(per_launch), "flops_per_pair": fpp,
+            "avg_launch_ms": round(avg_ms, 4), "share_of_step": round(pair_ms / max(total, 1e-9), 4)}
+
+
+def sampled_error(sim, scene, nsample=64, seed=7):
+    """Rates of the GPU against the FP64 oracle on patches around sampled
+    fluid particles (all particles within 4.5h: neighbours and the nearest
+    fluid of neighbouring dummies), with the global U_max and time."""
+    import numpy as np
+
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from helpers import patch_indices, scaled_err, scales
+    sim.eval_rates()
+    x, u, phi, m = sim.get("x"), sim.get("u"), sim.get("phi"), sim.get("mass")
+    dudt, dphidt, dush = sim.get("dudt"), sim.get("dphidt"), sim.get("dushift")
+    t = sim.stats()["t"]
+    p = scene.params
+    h = p["h_over_dx"] * p["dx"]
+    f = np.nonzero(scene.type == 0)[0]
+    rng = np.random.default_rng(seed)
+    smp = rng.choice(f, size=min(nsample, f.size), replace=False)
+    umax = float(np.sqrt((u[:, f] ** 2).sum(0)).max())
+    idx = patch_indices(x, x[:, smp], 4.5 * h)
+    loc = np.searchsorted(idx, smp)
+    r = oracle.stage_rates(p, x[:, idx], u[:, idx], phi[idx], m[idx], scene.type[idx],
+                           scene.normal[:, idx], t=t, umax=umax)
+    sk = scales(p, scene.water_height)
+    return {"dudt": scaled_err(dudt[:, smp], r["dudt"][:, loc], sk["dudt"]),
+            "dphidt": scaled_err(dphidt[smp], r["dphidt"][loc], sk["dphidt"]),
+            "dushift": scaled_err(dush[:, smp], r["dushift"][:, loc], sk["dushift"]),
+            "samples": int(smp.size), "patch_particles": int(idx.size)}
+
+
+def rates_diff(a, b, scene):
+    """Scaled difference of the stage rates of two sims on the same state."""
+    import numpy as np
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from helpers import scaled_err, scales
+    f = scene.type == 0
+    sk = scales(scene.params, scene.water_height)
+    lam = b.get("lambda")[f]
+    keep = np.abs(lam - scene.params["tic_lambda"]) > 1e-4
+    return {"dudt": scaled_err(a.get("dudt")[:, f][:, keep], b.get("dudt")[:, f][:, keep], sk["dudt"]),
+            "dphidt": scaled_err(a.get("dphidt")[f][keep], b.get("dphidt")[f][keep], sk["dphidt"]),
+            "excluded_tic_boundary": int((~keep).sum())}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -210,54 +317,13 @@ def run_ours(args):
     wl = WORKLOADS[args.workload]
     t_setup = time.perf_counter()
     scene = wl["make"]()
-    precision = wbsph.MIXED if args.precision == "mixed" else wbsph.FP64
-    sim = wbsph.Sim(scene.params, precision=precision, water_height=scene.water_height,
-                    device=local)
-    sim.set_scene(scene)
     dim = scene.params["dim"]
     nf = scene.n_fluid
-    stream = sim.stream
-
-    sim.step(args.warmup)
-    sim.sync()
     setup_s = time.perf_counter() - t_setup
-
-    # ---- device-resident timed region ----
-    sim.set_profiling(True)
-    sim.profile(reset=True)
-    st0 = sim.stats()
-    barrier(world)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        sim.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    barrier(world)
-    ms = e0.elapsed_time(e1)
-    sim.sync()
-    st1 = sim.stats()
-    prof = sim.profile(reset=True)
-    sim.set_profiling(False)
-    ms_max = max_over_ranks(ms, world)
-    value = nf * args.steps * world / (ms_max / 1e3)
-
-    pair_ms, pair_n = prof["pair"]
-    pairs = st1["pairs"] - st0["pairs"]
-    pairs_per_launch = pairs / max(pair_n, 1)
-    fpp = FLOPS_PER_PAIR_3D if dim == 3 else FLOPS_PER_PAIR_2D
-    flops_launch = pairs_per_launch * fpp + nf * FLOPS_EPILOGUE_3D
-    achieved = flops_launch / (pair_ms / max(pair_n, 1) / 1e3) / 1e12
-    traffic = profile_traffic("pair_fp64.cu", f"pair_fp64_{args.workload}")
-    roofline = {"bound": "alu", "kernel": "k_pair_fp64<%d>" % dim, "achieved": round(achieved, 4),
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                "traffic": traffic,
-                "peak_source": "measured FP64 DFMA throughput of this GB300 (profiles/fp64_alu_peak.md)",
-                "pairs_per_launch": int(pairs_per_launch), "flops_per_pair": fpp,
-                "avg_launch_ms": round(pair_ms / max(pair_n, 1), 4),
-                "share_of_step": round(pair_ms / max(sum(v[0] for v in prof.values()), 1e-9), 4)}
+    primary_mixed = args.precision == "mixed"
+    sim, m = time_path(scene, wbsph.MIXED if primary_mixed else wbsph.FP64, args, world, local)
+    value = nf * args.steps * world / (m["ms"] / 1e3)
+    roofline = pair_roofline(m, dim, nf, primary_mixed, args.workload)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -265,7 +331,6 @@ def run_ours(args):
         pass
     hbm = peaks.get("hbm_gbs", 6686.1)
     bytes_ps = algorithmic_bytes_per_particle_step(dim)
-    hbm_frac = value / world * bytes_ps / (hbm * 1e9)
 
     # ---- end to end through the C-ABI with pinned host buffers ----
     k_e2e = max(1, min(args.steps, 5))
@@ -294,23 +359,46 @@ def run_ours(args):
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(m["ms"] / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "precision": args.precision, "n_fluid": nf,
                    "n_total": scene.n, "dim": dim,
-                   "l2": f"inputs larger than L2 ({st1['device_bytes'] / 1e9:.2f} GB resident)",
+                   "l2": f"inputs larger than L2 ({m['st1']['device_bytes'] / 1e9:.2f} GB resident)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "unit_counted": "fluid particles x steps"},
         "roofline": roofline,
-        "hbm": {"algorithmic_bytes_per_particle_step": bytes_ps, "achieved_gbs": round(value / world * bytes_ps / 1e9, 1),
-                "peak_gbs": hbm, "frac": round(hbm_frac, 5)},
+        "hbm": {"algorithmic_bytes_per_particle_step": bytes_ps,
+                "achieved_gbs": round(value / world * bytes_ps / 1e9, 1), "peak_gbs": hbm,
+                "frac": round(value / world * bytes_ps / (hbm * 1e9), 5)},
         "e2e": e2e,
-        "gpu_launches": int(st1["launches"] - st0["launches"]),
-        "clocks": clk.summary(),
-        "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
+        "gpu_launches": int(m["st1"]["launches"] - m["st0"]["launches"]),
+        "clocks": m["clocks"],
+        "kernel_ms": {k: round(v[0], 3) for k, v in m["prof"].items()},
         "setup_s": round(setup_s, 1),
     }
+    if not args.no_paths:
+        # the other precision on the same workload, and errors at this size
+        other = wbsph.FP64 if primary_mixed else wbsph.MIXED
+        sim2, m2 = time_path(scene, other, args, world, local)
+        v2 = nf * args.steps * world / (m2["ms"] / 1e3)
+        paths = {("fp64" if primary_mixed else "mixed"): {
+            "value": round(v2, 1), "ms_per_step": round(m2["ms"] / args.steps, 4),
+            "roofline": pair_roofline(m2, dim, nf, not primary_mixed, args.workload),
+            "hbm_frac": round(v2 / world * bytes_ps / (hbm * 1e9), 5)}}
+        if rank == 0:
+            fp64 = sim2 if primary_mixed else sim
+            mixed = sim if primary_mixed else sim2
+            st = {k: mixed.get(k) for k in ("x", "u", "phi")}
+            fp64.set_particles(st["x"], st["u"], st["phi"], scene.type, scene.normal,
+                               mixed.get("mass"))
+            err64 = sampled_error(fp64, scene)
+            mixed.eval_rates()
+            diff = rates_diff(mixed, fp64, scene)
+            line["error"] = {"fp64_vs_oracle_sampled": err64, "mixed_vs_fp64": diff,
+                             "measure": "max|a-b| / max(max|b|, natural scale) over fluid particles"}
+        line["paths"] = paths
+        sim2.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = wl["sample"]()
         v, steps, secs, cores = cpu_baseline(sample)
@@ -358,6 +446,8 @@ def main():
     ap.add_argument("--workload", default="dam3d", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-paths", action="store_true",
+                    help="skip the second precision and the sampled error checks")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

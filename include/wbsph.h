@@ -173,6 +173,65 @@ int wbsph_get_stats(wbsph_handle h, wbsph_stats* out);
 int wbsph_set_profiling(wbsph_handle h, int on);
 int wbsph_get_profile(wbsph_handle h, double* ms, int64_t* launches, int reset);
 
+/* ---- learned surrogate (the paper has no learned part) ----------------
+ * A message-passing network over the same neighbour lists predicts the
+ * stage rates (DU/Dt, Dphi/Dt) of fluid particles from node features
+ * (U, rho/rho0 - 1, phi, dummy flag) and edge features (r/h, |r|/h). Three
+ * layers, hidden width 64, BF16 weights and activations, FP32 accumulation
+ * on the tensor cores; trained on the GPU against the plain FP64 rates of
+ * the states it is shown. Parameters are a flat FP32 vector: blocks node
+ * encoder, edge encoder, (edge MLP, node MLP) per layer, decoder; each
+ * W1 [in][64], b1 [64], W2 [64][out], b2 [out], row-major. */
+typedef struct wbsph_surrogate_s* wbsph_surrogate;
+typedef struct {
+  int dim;            /* 2 or 3 */
+  int hidden;         /* 64 */
+  int layers;         /* message-passing layers (3) */
+  float beta1, beta2, eps;  /* Adam */
+  int device;
+} wbsph_surrogate_config;
+
+typedef struct {
+  int64_t surrogate_steps, plain_steps, anchors, fallbacks;
+  double last_rel_err;   /* relative L2 of surrogate vs plain DU/Dt at the last anchor */
+  double max_rel_err;
+} wbsph_anchor_stats;
+
+int wbsph_surrogate_config_default(wbsph_surrogate_config* cfg, int dim);
+int wbsph_surrogate_create(const wbsph_surrogate_config* cfg, wbsph_surrogate* out);
+int64_t wbsph_surrogate_num_params(wbsph_surrogate s);
+/* host FP32 arrays of wbsph_surrogate_num_params() values */
+int wbsph_surrogate_set_params(wbsph_surrogate s, const float* params);
+int wbsph_surrogate_get_params(wbsph_surrogate s, float* params);
+/* node mean/std: dim+2 values (U, rho/rho0-1, phi); output mean/std: dim+1 */
+int wbsph_surrogate_set_normalization(wbsph_surrogate s, const float* node_mean, const float* node_std,
+                                      const float* out_mean, const float* out_std);
+/* One training step on the sim's current state: plain FP64 rates as targets,
+ * forward, MSE loss on normalised outputs, backward, Adam with rate lr.
+ * Synchronises; *loss (nullable) receives the loss before the update. */
+int wbsph_surrogate_train_step(wbsph_surrogate s, wbsph_handle h, float lr, double* loss);
+/* Loss on the sim's current state without an update. */
+int wbsph_surrogate_eval(wbsph_surrogate s, wbsph_handle h, double* loss);
+/* Surrogate stage rates at the sim's current state into its rate fields
+ * (WBSPH_FIELD_DUDT / DPHIDT; DUSHIFT set to zero). */
+int wbsph_surrogate_predict(wbsph_surrogate s, wbsph_handle h);
+/* Test hook: graph, features, outputs and loss gradient of the sim's
+ * current state, all host arrays; ids are original particle ids. Call with
+ * null arrays first to get *n_edges. out: n_fluid*(dim+1) normalised outputs
+ * in the order of fluid_ids; grad: num_params; node_feat: n*8; edge_feat:
+ * n_edges*8 (BF16 values as float). */
+int wbsph_surrogate_debug(wbsph_surrogate s, wbsph_handle h, int64_t* n_edges, uint32_t* recv_ids,
+                          uint32_t* send_ids, float* edge_feat, float* node_feat, uint32_t* fluid_ids,
+                          float* out, float* grad, double* loss);
+/* Advance nsteps SSP-RK2 steps with surrogate rates; every anchor_every-th
+ * step is a plain FP64 step, and at each anchor the surrogate's DU/Dt is
+ * compared with the plain one on the same state (relative L2 over fluid).
+ * If it exceeds tau the next window runs plain (fallback). Synchronises. */
+int wbsph_step_surrogate(wbsph_handle h, wbsph_surrogate s, int64_t nsteps, int anchor_every, double tau,
+                         wbsph_anchor_stats* stats);
+void wbsph_surrogate_destroy(wbsph_surrogate s);
+const char* wbsph_surrogate_last_error(wbsph_surrogate s);
+
 /* Cell keys and stable sort without any device allocation. The paper has no
  * counterpart: this is a variant of the neighbour build's key and radix-sort
  * kernels for callers that cannot let a library allocate device memory (a

@@ -1,0 +1,128 @@
+"""FP64 reference of the message-passing surrogate (test infrastructure only).
+
+Plain PyTorch CPU float64 statement of the network that the CUDA surrogate
+kernels evaluate in BF16 with FP32 accumulation; gradients come from
+autograd of this forward and are pinned by central finite differences in
+the tests. Only the tests may import this module.
+
+Network (dimension d, hidden H = 64, three message-passing layers):
+  node input  f_i = normalised (U_i, rho_i/rho0 - 1, phi_i, dummy flag)   (d + 3)
+  edge input  g_ij = ((x_j - x_i)/h, |x_j - x_i|/h) for receiver i, sender j (d + 1)
+  MLP(x) = W2 silu(W1 x + b1) + b2 (weights stored input-major: x @ W)
+  h = MLP_node_enc(f), e = MLP_edge_enc(g)
+  per layer: e <- e + MLP_e([e_ij, h_i, h_j]);  a_i = sum_j e_ij;  h <- h + MLP_n([h_i, a_i])
+  output y_i = MLP_dec(h_i)  (d + 1: normalised DU/Dt and Dphi/Dt)
+Edges: every fluid receiver i with every particle j within 2h (dummies only
+send). Loss: mean over fluid particles and output components of the squared
+difference to the normalised targets.
+
+Flat parameter layout (shared with the CUDA library): blocks in the order
+node encoder, edge encoder, (edge MLP, node MLP) per layer, decoder; each
+block W1 [in][H], b1 [H], W2 [H][out], b2 [out], row-major.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+HIDDEN = 64
+LAYERS = 3
+
+
+def block_dims(dim: int, hidden: int = HIDDEN, layers: int = LAYERS):
+    fn, fe, fo = dim + 3, dim + 1, dim + 1
+    dims = [("enc_n", fn, hidden), ("enc_e", fe, hidden)]
+    for l in range(layers):
+        dims += [(f"mp{l}_e", 3 * hidden, hidden), (f"mp{l}_n", 2 * hidden, hidden)]
+    dims.append(("dec", hidden, fo))
+    return dims
+
+
+def num_params(dim: int, hidden: int = HIDDEN, layers: int = LAYERS) -> int:
+    return sum(i * hidden + hidden + hidden * o + o for _, i, o in block_dims(dim, hidden, layers))
+
+
+def unflatten(theta: torch.Tensor, dim: int, hidden: int = HIDDEN, layers: int = LAYERS):
+    out, k = {}, 0
+    for name, i, o in block_dims(dim, hidden, layers):
+        w1 = theta[k:k + i * hidden].view(i, hidden); k += i * hidden
+        b1 = theta[k:k + hidden]; k += hidden
+        w2 = theta[k:k + hidden * o].view(hidden, o); k += hidden * o
+        b2 = theta[k:k + o]; k += o
+        out[name] = (w1, b1, w2, b2)
+    assert k == theta.numel()
+    return out
+
+
+def init_params(dim: int, seed: int = 0, hidden: int = HIDDEN, layers: int = LAYERS) -> np.ndarray:
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases; the last
+    layer of every processor MLP is scaled by 0.1 so residual updates start small."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, i, o in block_dims(dim, hidden, layers):
+        s1, s2 = 1.0 / np.sqrt(i), 1.0 / np.sqrt(hidden)
+        if name.startswith("mp"):
+            s2 *= 0.1
+        parts += [rng.uniform(-s1, s1, i * hidden), np.zeros(hidden),
+                  rng.uniform(-s2, s2, hidden * o), np.zeros(o)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def _mlp(x, p):
+    w1, b1, w2, b2 = p
+    return torch.nn.functional.silu(x @ w1 + b1) @ w2 + b2
+
+
+def forward(theta, dim, node_in, recv, send, edge_in, hidden=HIDDEN, layers=LAYERS):
+    """node_in (N, d+3), recv/send (E,) int64, edge_in (E, d+1) -> (N, d+1)."""
+    P = unflatten(theta, dim, hidden, layers)
+    h = _mlp(node_in, P["enc_n"])
+    e = _mlp(edge_in, P["enc_e"])
+    for l in range(layers):
+        e = e + _mlp(torch.cat([e, h[recv], h[send]], dim=1), P[f"mp{l}_e"])
+        agg = torch.zeros(h.shape, dtype=h.dtype).index_add(0, recv, e)
+        h = h + _mlp(torch.cat([h, agg], dim=1), P[f"mp{l}_n"])
+    return _mlp(h, P["dec"])
+
+
+def loss(out, target, fluid):
+    d = out[fluid] - target[fluid]
+    return (d * d).mean()
+
+
+def as_t(a):
+    return torch.as_tensor(np.asarray(a), dtype=torch.float64)
+
+
+def forward_np(theta, dim, node_in, recv, send, edge_in):
+    with torch.no_grad():
+        return forward(as_t(theta), dim, as_t(node_in), torch.as_tensor(recv, dtype=torch.int64),
+                       torch.as_tensor(send, dtype=torch.int64), as_t(edge_in)).numpy()
+
+
+def grad_np(theta, dim, node_in, recv, send, edge_in, dout):
+    """Gradient of sum(dout * out) with respect to the flat parameters."""
+    th = as_t(theta).clone().requires_grad_(True)
+    out = forward(th, dim, as_t(node_in), torch.as_tensor(recv, dtype=torch.int64),
+                  torch.as_tensor(send, dtype=torch.int64), as_t(edge_in))
+    (out * as_t(dout)).sum().backward()
+    return th.grad.numpy()
+
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round float32 values to bfloat16 (nearest even) and back, as the
+    surrogate stores weights and activations."""
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def round_weights_bf16(theta: np.ndarray, dim: int, hidden: int = HIDDEN, layers: int = LAYERS) -> np.ndarray:
+    """Weights (W1, W2 of every block) rounded to bfloat16, biases unchanged:
+    the parameters exactly as the BF16 kernels use them."""
+    out = np.asarray(theta, dtype=np.float64).copy()
+    k = 0
+    for _, i, o in block_dims(dim, hidden, layers):
+        for size, is_w in ((i * hidden, True), (hidden, False), (hidden * o, True), (o, False)):
+            if is_w:
+                out[k:k + size] = bf16_round(out[k:k + size])
+            k += size
+    return out

@@ -44,7 +44,7 @@ struct Params {
   double force_amp[3];
   double omega;                   // 2 pi / period, 0 = no forcing
   double cfl, fixed_dt;
-  double inv_dx_vol;              // unused placeholder for alignment
+  float nearest_band_r2;          // FP32 band around the FP32 minimum that holds the exact nearest
   double domain_min[3], domain_max[3];
   double R;                       // cell size 2h
   int nc[3];                      // grid cells per axis
@@ -73,21 +73,25 @@ struct Work {
   double* dushift;   // dim * n
   double* lambda;    // n
   double* vol;       // n
-  float4* xf;        // n: FP32 copy of positions (.w unused) for the candidate prefilter
+  float4* xf;        // n: FP32 copy of positions (.w = type) for the candidate prefilter
   uint32_t* key;     // n: sorted cell keys
   uint32_t* key_alt; // n
   uint32_t* perm;    // n: source index of each sorted position
   uint32_t* perm_alt;
   uint32_t* cell_lb; // ncells + 1: first sorted index with key >= c
   uint32_t* fluid_list;  // n_fluid: sorted indices of fluid particles
+  uint32_t* dummy_list;  // n_dummy: sorted indices of dummy particles
   uint32_t* block_cnt;   // scratch for scans
   uint32_t* hist;        // radix histograms
   unsigned long long* umax_bits;  // [0]: max |U|^2 over fluid (bits of a non-negative double)
   double* scalars;   // [0] t, [1] dt, [2] U_max of the current stage
   unsigned* status;  // device status word
   unsigned long long* pairs;  // [0]: neighbour pairs summed by pair passes (units of work)
+  uint32_t* nbr;     // kmax * n_fluid: candidate lists, k-major (nbr[k * nf + gi])
+  uint32_t* nbr_cnt; // n_fluid: candidates per fluid particle
   float4* packA;     // n: mixed path, (cell-relative offset, phi - phi_hs) in FP32
   float4* packB;     // n: mixed path, (U, +-V) in FP32
+  uint32_t* packC;   // n: mixed path, cell coordinates packed 11/11/10 bits
 };
 
 __host__ __device__ inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -99,19 +103,21 @@ void launch_radix_sort(const Params& p, Work& w, int64_t n, cudaStream_t st, int
 void launch_gather(const Params& p, const State& src, const State& dst, const Work& w, int64_t n,
                    bool with_base, cudaStream_t st);
 void launch_cell_bounds(const Params& p, const Work& w, int64_t n, cudaStream_t st);
-void launch_fluid_list(const State& s, const Work& w, int64_t n, int64_t nblocks_scan,
-                       cudaStream_t st, int* launches);
+void launch_fluid_list(const State& s, const Work& w, int64_t n, int64_t nd, cudaStream_t st,
+                       int* launches);
 void launch_count_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
                             uint32_t* counts, cudaStream_t st);
 void launch_fill_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
                            const int64_t* row_ptr_by_oid, int32_t* cols, cudaStream_t st);
 
 // ---- launchers (pair_fp64.cu) ----
-void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int stage2,
-                    cudaStream_t st);
+void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int64_t nd,
+                    int stage2, cudaStream_t st);
 void launch_time_step(const Params& p, const Work& w, cudaStream_t st);
 void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid,
                       int stage2, cudaStream_t st);
+int pair_list_kmax(int dim);
+void launch_nbr_list(const Params& p, const Work& w, int64_t n, int64_t n_fluid, cudaStream_t st);
 void launch_rk_stage(const Params& p, const State& s, const Work& w, int64_t n, int stage,
                      cudaStream_t st);
 void launch_field(const Params& p, const State& s, const Work& w, int64_t n, int field,

@@ -212,6 +212,13 @@ static int derive_params(wbsph_s* h) {
   float tf = (float)thr;
   if ((double)tf < thr) tf = std::nextafter(tf, INFINITY);
   p.prefilter_r2 = tf;
+  // Nearest-fluid band: |r_f^2 - r^2| <= B for every candidate (r <= 2h), so
+  // the exact nearest lies within 2B of the FP32 minimum.
+  double eps = std::sqrt((double)c.dim) * (2.0 * X + 2.0 * p.two_h) * u24;
+  double B = 2.0 * (2.0 * p.two_h * eps + eps * eps + 4.0 * u24 * p.four_h2);
+  float bf = (float)(2.0 * B);
+  if ((double)bf < 2.0 * B) bf = std::nextafter(bf, INFINITY);
+  p.nearest_band_r2 = bf;
   return WBSPH_OK;
 }
 
@@ -305,15 +312,22 @@ static int allocate(wbsph_s* h, int64_t n) {
   w.key = U32(nn); w.key_alt = U32(nn); w.perm = U32(nn); w.perm_alt = U32(nn);
   w.cell_lb = U32((size_t)h->P.ncells + 1);
   w.fluid_list = U32(nn);
+  w.dummy_list = U32((size_t)(h->nd > 0 ? h->nd : 1));
   w.block_cnt = U32((size_t)div_up((int64_t)nn, 1024) + 1);
   w.hist = U32((size_t)radix_sort_scratch_words((int64_t)nn));
   w.umax_bits = (unsigned long long*)dev_alloc(h, 8);
   w.scalars = D(4);
   w.status = (unsigned*)dev_alloc(h, sizeof(unsigned));
   w.pairs = (unsigned long long*)dev_alloc(h, 8);
+  {
+    size_t nfl = (size_t)(h->nf > 0 ? h->nf : 1);
+    w.nbr = U32(nfl * (size_t)pair_list_kmax(d));
+    w.nbr_cnt = U32(nfl);
+  }
   if (h->cfg.precision == WBSPH_MIXED) {
     w.packA = (float4*)dev_alloc(h, nn * sizeof(float4));
     w.packB = (float4*)dev_alloc(h, nn * sizeof(float4));
+    w.packC = U32(nn);
   }
   if (h->alloc_failed) return fail(h, WBSPH_E_NOMEM, "device allocation failed");
   h->n_alloc = n;
@@ -351,9 +365,10 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
   if (nd > 0 && !normal) return fail(h, WBSPH_E_INVAL, "dummy particles need normals");
   h->loaded = false;
   int rc = WBSPH_OK;
-  if (n != h->n_alloc || h->blocks.empty()) rc = allocate(h, n);  // same n: reuse the buffers
-  if (rc) return rc;
+  bool same = n == h->n_alloc && nf == h->nf && !h->blocks.empty();
   h->n = n; h->nf = nf; h->nd = nd;
+  if (!same) rc = allocate(h, n);  // same counts: reuse the buffers
+  if (rc) return rc;
   size_t vb = (size_t)n * sizeof(double);
   if (n) {
     CK(cudaMemcpyAsync(h->A.x, x, d * vb, kind, h->stream));
@@ -408,7 +423,7 @@ static int build(wbsph_s* h, bool with_base) {
   {
     ProfScope ps(h, WBSPH_K_CELLS);
     launch_cell_bounds(h->P, h->W, n, st);
-    launch_fluid_list(h->A, h->W, n, 0, st, &l);
+    launch_fluid_list(h->A, h->W, n, h->nd, st, &l);
   }
   h->launches += 3 + l;
   return check_launch(h, "neighbour build");
@@ -419,7 +434,7 @@ static int rates(wbsph_s* h, int stage2) {
   cudaStream_t st = h->stream;
   {
     ProfScope ps(h, WBSPH_K_PREPASS);
-    launch_prepass(h->P, h->A, h->W, n, stage2, st);
+    launch_prepass(h->P, h->A, h->W, n, h->nd, stage2, st);
   }
   if (!stage2) {
     ProfScope ps(h, WBSPH_K_OTHER);
@@ -429,12 +444,14 @@ static int rates(wbsph_s* h, int stage2) {
     ProfScope ps(h, WBSPH_K_PAIR);
     if (h->cfg.precision == WBSPH_MIXED) {
       int rc = launch_mixed_stage(h->P, h->A, h->W, n, h->nf, stage2, st);
-      if (rc) return fail(h, rc, "mixed path not available in this library");
+      if (rc) return fail(h, rc, "mixed path: grid too large for packed cell coordinates");
     } else {
+      launch_nbr_list(h->P, h->W, n, h->nf, st);
       launch_pair_fp64(h->P, h->A, h->W, n, h->nf, stage2, st);
     }
   }
-  h->launches += (n ? 1 : 0) + (stage2 ? 0 : 1) + (h->nf ? 1 : 0);
+  h->launches += (n ? 1 : 0) + (h->nd ? 1 : 0) + (stage2 ? 0 : 1) + (h->nf ? 2 : 0) +
+                 (h->cfg.precision == WBSPH_MIXED && n ? 1 : 0);
   return check_launch(h, "stage rates");
 }
 
@@ -659,3 +676,189 @@ cudaStream_t handle_stream(wbsph_handle h) { return h ? h->stream : nullptr; }
 int handle_device(wbsph_handle h) { return h ? h->cfg.device : 0; }
 int handle_fail(wbsph_handle h, int code, const char* msg) { return fail(h, code, "%s", msg); }
 }  // namespace wbsph
+
+// ---------------------------------------------------------------------------
+// Learned surrogate: training, prediction and anchored rollouts
+// ---------------------------------------------------------------------------
+#include <cuda_bf16.h>
+namespace wbsph {
+int surrogate_stage_rates(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n,
+                          int64_t nf, cudaStream_t cs);
+int surrogate_loss(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n, int64_t nf,
+                   cudaStream_t cs, int train, float lr, double* loss_out, const float* dout_override,
+                   float* grad_out);
+int64_t surrogate_edges(wbsph_surrogate s);
+const float* surrogate_out(wbsph_surrogate s);
+const uint32_t* surrogate_recv(wbsph_surrogate s);
+const uint32_t* surrogate_send(wbsph_surrogate s);
+const __nv_bfloat16* surrogate_efeat(wbsph_surrogate s);
+const __nv_bfloat16* surrogate_nfeat(wbsph_surrogate s);
+void launch_rel_err(const Params& p, const Work& w, int64_t n, int64_t nf, const double* a_ref_copy,
+                    double* sums, cudaStream_t st);
+}  // namespace wbsph
+
+static int check_pair(wbsph_s* h, wbsph_surrogate s) {
+  if (!h || !s) return WBSPH_E_INVAL;
+  if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
+  if (h->cfg.precision != WBSPH_FP64) return fail(h, WBSPH_E_INVAL, "the surrogate needs an FP64 handle");
+  return WBSPH_OK;
+}
+
+// Surrogate stage: dummy walls, volumes, [time step], surrogate rates.
+static int surrogate_stage(wbsph_s* h, wbsph_surrogate s, int stage2) {
+  cudaStream_t st = h->stream;
+  {
+    ProfScope ps(h, WBSPH_K_PREPASS);
+    launch_prepass(h->P, h->A, h->W, h->n, h->nd, stage2, st);
+  }
+  if (!stage2) {
+    ProfScope ps(h, WBSPH_K_OTHER);
+    launch_time_step(h->P, h->W, st);
+  }
+  int rc;
+  {
+    ProfScope ps(h, WBSPH_K_PAIR);
+    rc = surrogate_stage_rates(s, h->P, h->A, h->W, h->n, h->nf, st);
+  }
+  h->launches += 3 + (stage2 ? 0 : 1) + 20;
+  if (rc) return fail(h, rc, "surrogate stage failed");
+  return check_launch(h, "surrogate stage");
+}
+
+extern "C" int wbsph_surrogate_train_step(wbsph_surrogate s, wbsph_handle h, float lr, double* loss) {
+  int rc = check_pair(h, s);
+  if (rc) return rc;
+  CK(cudaSetDevice(h->cfg.device));
+  if ((rc = build(h, false)) || (rc = rates(h, 0))) return rc;
+  rc = surrogate_loss(s, h->P, h->A, h->W, h->n, h->nf, h->stream, 1, lr, loss, nullptr, nullptr);
+  if (rc) return fail(h, rc, "surrogate training step failed");
+  return read_status(h);
+}
+
+extern "C" int wbsph_surrogate_eval(wbsph_surrogate s, wbsph_handle h, double* loss) {
+  int rc = check_pair(h, s);
+  if (rc) return rc;
+  CK(cudaSetDevice(h->cfg.device));
+  if ((rc = build(h, false)) || (rc = rates(h, 0))) return rc;
+  rc = surrogate_loss(s, h->P, h->A, h->W, h->n, h->nf, h->stream, 0, 0.f, loss, nullptr, nullptr);
+  if (rc) return fail(h, rc, "surrogate evaluation failed");
+  return read_status(h);
+}
+
+extern "C" int wbsph_surrogate_predict(wbsph_surrogate s, wbsph_handle h) {
+  int rc = check_pair(h, s);
+  if (rc) return rc;
+  CK(cudaSetDevice(h->cfg.device));
+  if ((rc = build(h, false))) return rc;
+  return surrogate_stage(h, s, 0);
+}
+
+static void bf16_to_host(const __nv_bfloat16* d, int64_t count, float* out, cudaStream_t st) {
+  std::vector<uint16_t> tmp((size_t)count);
+  if (count) cudaMemcpyAsync(tmp.data(), d, count * 2, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  for (int64_t k = 0; k < count; ++k) {
+    uint32_t b = (uint32_t)tmp[k] << 16;
+    memcpy(&out[k], &b, 4);
+  }
+}
+
+extern "C" int wbsph_surrogate_debug(wbsph_surrogate s, wbsph_handle h, int64_t* n_edges, uint32_t* recv_ids,
+                                     uint32_t* send_ids, float* edge_feat, float* node_feat,
+                                     uint32_t* fluid_ids, float* out, float* grad, double* loss) {
+  int rc = check_pair(h, s);
+  if (rc) return rc;
+  if (!n_edges) return fail(h, WBSPH_E_INVAL, "n_edges required");
+  CK(cudaSetDevice(h->cfg.device));
+  if ((rc = build(h, false)) || (rc = rates(h, 0))) return rc;
+  rc = surrogate_loss(s, h->P, h->A, h->W, h->n, h->nf, h->stream, 0, 0.f, loss, nullptr, grad);
+  if (rc) return fail(h, rc, "surrogate evaluation failed");
+  int64_t E = surrogate_edges(s);
+  *n_edges = E;
+  const int64_t n = h->n, nf = h->nf;
+  const int fo = h->cfg.dim + 1;
+  cudaStream_t st = h->stream;
+  std::vector<uint32_t> oid((size_t)n), fl((size_t)nf), tmp((size_t)E);
+  CK(cudaMemcpyAsync(oid.data(), h->A.oid, n * 4, cudaMemcpyDeviceToHost, st));
+  if (nf) CK(cudaMemcpyAsync(fl.data(), h->W.fluid_list, nf * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (fluid_ids)
+    for (int64_t g = 0; g < nf; ++g) fluid_ids[g] = oid[fl[g]];
+  if (recv_ids && E) {
+    CK(cudaMemcpyAsync(tmp.data(), surrogate_recv(s), E * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int64_t e = 0; e < E; ++e) recv_ids[e] = oid[tmp[e]];
+  }
+  if (send_ids && E) {
+    CK(cudaMemcpyAsync(tmp.data(), surrogate_send(s), E * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int64_t e = 0; e < E; ++e) send_ids[e] = oid[tmp[e]];
+  }
+  if (edge_feat) bf16_to_host(surrogate_efeat(s), E * 8, edge_feat, st);
+  if (node_feat) {
+    std::vector<float> nfe((size_t)n * 8);
+    bf16_to_host(surrogate_nfeat(s), n * 8, nfe.data(), st);
+    for (int64_t i = 0; i < n; ++i) memcpy(node_feat + (int64_t)oid[i] * 8, &nfe[(size_t)i * 8], 32);
+  }
+  if (out && nf) {
+    CK(cudaMemcpyAsync(out, surrogate_out(s), nf * fo * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return read_status(h);
+}
+
+extern "C" int wbsph_step_surrogate(wbsph_handle h, wbsph_surrogate s, int64_t nsteps, int anchor_every,
+                                    double tau, wbsph_anchor_stats* stats) {
+  int rc = check_pair(h, s);
+  if (rc) return rc;
+  if (nsteps < 0 || anchor_every < 0) return fail(h, WBSPH_E_INVAL, "bad step counts");
+  CK(cudaSetDevice(h->cfg.device));
+  wbsph_anchor_stats local;
+  memset(&local, 0, sizeof local);
+  const int d = h->cfg.dim;
+  double* ref = nullptr;  // copy of the surrogate DU/Dt at an anchor, then error sums
+  CK(cudaMallocAsync((void**)&ref, ((size_t)d * (h->n > 0 ? h->n : 1) + 2) * sizeof(double), h->stream));
+  int64_t plain_until = -1;
+  for (int64_t k = 0; k < nsteps && !rc; ++k) {
+    bool anchor = anchor_every > 0 && (k + 1) % anchor_every == 0;
+    bool plain = anchor || k < plain_until;
+    if ((rc = build(h, false))) break;
+    if (anchor) {
+      // surrogate rates at this state, kept for the comparison with the plain ones
+      if ((rc = surrogate_stage(h, s, 0))) break;
+      CK(cudaMemcpyAsync(ref, h->W.dudt, (size_t)d * h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (plain) {
+      if ((rc = rates(h, 0))) break;
+    } else {
+      if ((rc = surrogate_stage(h, s, 0))) break;
+    }
+    if (anchor) {
+      double sums[2] = {0, 0};
+      launch_rel_err(h->P, h->W, h->n, h->nf, ref, ref + (size_t)d * h->n, h->stream);
+      CK(cudaMemcpyAsync(sums, ref + (size_t)d * h->n, 16, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      double e = sums[1] > 0 ? std::sqrt(sums[0] / sums[1]) : 0.0;
+      local.anchors += 1;
+      local.last_rel_err = e;
+      local.max_rel_err = std::max(local.max_rel_err, e);
+      if (e > tau) {
+        local.fallbacks += 1;
+        plain_until = k + 1 + anchor_every;
+      }
+    }
+    launch_rk_stage(h->P, h->A, h->W, h->n, 1, h->stream);
+    if ((rc = build(h, true))) break;
+    if (plain) rc = rates(h, 1);
+    else rc = surrogate_stage(h, s, 1);
+    if (rc) break;
+    launch_rk_stage(h->P, h->A, h->W, h->n, 2, h->stream);
+    h->launches += 2;
+    if (plain) local.plain_steps += 1; else local.surrogate_steps += 1;
+    ++h->steps;
+  }
+  cudaFreeAsync(ref, h->stream);
+  if (stats) *stats = local;
+  if (rc) return rc;
+  return read_status(h);
+}

@@ -1,0 +1,1039 @@
+// mpnn.cu -- BF16 message-passing surrogate of the pair pass: graph over the
+// same neighbour lists, fused two-layer MLP kernels on the tensor cores
+// (mma.sync m16n8k16, BF16 operands, FP32 accumulation) for inference and
+// training, segment sums, loss, Adam, and the surrogate stage rates.
+//
+// Network (the paper has no learned part): node input f_i = normalised
+// (U_i, rho_i/rho0 - 1, phi_i) plus a dummy flag; edge input
+// ((x_j - x_i)/h, |x_j - x_i|/h) for every fluid receiver i and every particle
+// j within 2h; MLP(x) = W2 silu(W1 x + b1) + b2; node and edge encoders,
+// three layers of e <- e + MLP_e([e, h_i, h_j]), a_i = sum_j e_ij,
+// h <- h + MLP_n([h, a]), and a decoder to normalised (DU/Dt, Dphi/Dt).
+// Flat parameter layout: blocks node encoder, edge encoder, (edge MLP,
+// node MLP) per layer, decoder; each block W1 [in][64], b1, W2 [64][out], b2.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wbsph.h"
+#include "common.cuh"
+#include "physics.cuh"
+
+namespace wbsph {
+const Params* handle_params(wbsph_handle h);
+cudaStream_t handle_stream(wbsph_handle h);
+int handle_device(wbsph_handle h);
+int handle_fail(wbsph_handle h, int code, const char* msg);
+void launch_scan_exclusive(uint32_t* data, int64_t total, cudaStream_t st);
+}  // namespace wbsph
+
+using namespace wbsph;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int HID = 64;
+constexpr int FEAT = 8;   // padded width of node and edge input features
+constexpr int MLP_THREADS = 128;
+constexpr int TILE = 64;  // rows per tile (4 warps x 16)
+
+enum { MODE_DIRECT = 0, MODE_LIST = 1, MODE_EDGE = 2, MODE_NODE = 3 };
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Fragments of m16n8k16 (PTX ISA fragment layouts): lane = 4 g + t.
+// A (16x16 at m0,k0): {(g,2t),(g,2t+1)}, {(g+8,2t),..}, {(g,2t+8),..}, {(g+8,2t+8),..}
+// B (16x8 at k0,n0):  {(2t,g),(2t+1,g)}, {(2t+8,g),(2t+9,g)}
+// C (16x8):           (g,2t),(g,2t+1),(g+8,2t),(g+8,2t+1)
+// Row-major smem [m][k] with even k gives 32-bit pair loads.
+__device__ __forceinline__ void frag_a_rm(uint32_t r[4], const bf16* s, int ld, int m0, int k0) {
+  int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const uint32_t* p0 = reinterpret_cast<const uint32_t*>(s + (m0 + g) * ld + k0 + 2 * t);
+  const uint32_t* p1 = reinterpret_cast<const uint32_t*>(s + (m0 + g + 8) * ld + k0 + 2 * t);
+  r[0] = p0[0]; r[1] = p1[0]; r[2] = p0[4]; r[3] = p1[4];
+}
+// B from smem stored [n][k] (k contiguous).
+__device__ __forceinline__ void frag_b_nk(uint32_t r[2], const bf16* s, int ld, int k0, int n0) {
+  int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const uint32_t* p = reinterpret_cast<const uint32_t*>(s + (n0 + g) * ld + k0 + 2 * t);
+  r[0] = p[0]; r[1] = p[4];
+}
+// A from smem stored [k][m] (transposed access, 16-bit loads).
+__device__ __forceinline__ void frag_a_t(uint32_t r[4], const bf16* s, int ld, int m0, int k0) {
+  int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  auto e = [&](int m, int k) { return s[k * ld + m]; };
+  r[0] = pack2(e(m0 + g, k0 + 2 * t), e(m0 + g, k0 + 2 * t + 1));
+  r[1] = pack2(e(m0 + g + 8, k0 + 2 * t), e(m0 + g + 8, k0 + 2 * t + 1));
+  r[2] = pack2(e(m0 + g, k0 + 2 * t + 8), e(m0 + g, k0 + 2 * t + 9));
+  r[3] = pack2(e(m0 + g + 8, k0 + 2 * t + 8), e(m0 + g + 8, k0 + 2 * t + 9));
+}
+// B from smem stored [k][n] (n contiguous, 16-bit loads).
+__device__ __forceinline__ void frag_b_kn(uint32_t r[2], const bf16* s, int ld, int k0, int n0) {
+  int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  r[0] = pack2(s[(k0 + 2 * t) * ld + n0 + g], s[(k0 + 2 * t + 1) * ld + n0 + g]);
+  r[1] = pack2(s[(k0 + 2 * t + 8) * ld + n0 + g], s[(k0 + 2 * t + 9) * ld + n0 + g]);
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z) {
+  float s = 1.f / (1.f + __expf(-z));
+  return s * (1.f + z * (1.f - s));
+}
+
+// Inputs and outputs of one fused MLP launch over `rows` rows.
+struct MlpArgs {
+  const uint32_t* rows_dev;  // row count in device memory (edges), or null
+  int64_t rows;              // row count when rows_dev is null
+  // gather sources
+  const bf16* in;            // DIRECT: [rows][FEAT]; LIST: node table [n][64]
+  const uint32_t* list;      // LIST: row -> node
+  const bf16* e;             // EDGE: [E][64]
+  const bf16* h;             // EDGE, NODE: [n][64]
+  const uint32_t* recv;      // EDGE
+  const uint32_t* send;      // EDGE
+  const bf16* agg;           // NODE: [n][64]
+  int kin, nout;             // true widths
+  const bf16* w1; const float* b1; const bf16* w2; const float* b2;  // block parameters
+  // forward outputs
+  bf16* out_bf;              // [rows][64] (+ residual for EDGE/NODE)
+  float* out_f;              // [rows][nout] (decoder)
+  // backward
+  const float* dout;         // [rows][nout] incoming gradient (EDGE/NODE/DIRECT: [rows][64])
+  float* din_row;            // EDGE: de_in, NODE: dh_in ([rows][64], = dout + dX[0:64])
+  float* dh;                 // EDGE: atomics into [n][64]; LIST: writes dh[list[row]]
+  float* dagg;               // NODE: [rows][64]
+  float* gw1; float* gb1; float* gw2; float* gb2;  // FP32 parameter gradients
+};
+
+__device__ __forceinline__ int64_t arg_rows(const MlpArgs& a) {
+  return a.rows_dev ? (int64_t)*a.rows_dev : a.rows;
+}
+
+// Gather of input element pair (k, k+1) of row `row` (KP padded width).
+template <int MODE, int KP>
+__device__ __forceinline__ uint32_t gather_pair(const MlpArgs& a, int64_t row, int k) {
+  if (MODE == MODE_DIRECT) {
+    if (k >= FEAT) return 0u;
+    return *reinterpret_cast<const uint32_t*>(a.in + row * FEAT + k);
+  } else if (MODE == MODE_LIST) {
+    return *reinterpret_cast<const uint32_t*>(a.in + (int64_t)a.list[row] * HID + k);
+  } else if (MODE == MODE_EDGE) {
+    if (k < HID) return *reinterpret_cast<const uint32_t*>(a.e + row * HID + k);
+    if (k < 2 * HID) return *reinterpret_cast<const uint32_t*>(a.h + (int64_t)a.recv[row] * HID + k - HID);
+    return *reinterpret_cast<const uint32_t*>(a.h + (int64_t)a.send[row] * HID + k - 2 * HID);
+  } else {
+    if (k < HID) return *reinterpret_cast<const uint32_t*>(a.h + row * HID + k);
+    return *reinterpret_cast<const uint32_t*>(a.agg + row * HID + k - HID);
+  }
+}
+
+template <int MODE, int KP>
+__device__ __forceinline__ void load_tile(const MlpArgs& a, int64_t row0, int64_t rows, bf16* X, int ldx) {
+  for (int idx = threadIdx.x; idx < TILE * (KP / 2); idx += MLP_THREADS) {
+    int r = idx / (KP / 2), k = (idx % (KP / 2)) * 2;
+    int64_t row = row0 + r;
+    uint32_t v = row < rows ? gather_pair<MODE, KP>(a, row, k) : 0u;
+    *reinterpret_cast<uint32_t*>(X + r * ldx + k) = v;
+  }
+}
+
+// smem layout sizes (elements) with +8 padding per row against bank conflicts
+template <int KP, int NP>
+struct Smem {
+  static constexpr int LDX = KP + 8, LDH = HID + 8, LDO = NP + 8;
+  static constexpr size_t fwd_bytes =
+      (size_t)(HID * LDX + NP * LDH + TILE * LDX + TILE * LDH) * 2 + (HID + NP) * 4;
+};
+
+// ---------------------------------------------------------------------------
+// Forward: out = MLP([gathered row]) (+ residual). Weights are staged once per
+// CTA (transposed to [n][k]); the CTA then walks row tiles of 64.
+// ---------------------------------------------------------------------------
+template <int MODE, int KP, int NP>
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
+  using S = Smem<KP, NP>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16* W1t = reinterpret_cast<bf16*>(smem);      // [64][LDX]  W1t[n][k] = W1[k][n]
+  bf16* W2t = W1t + HID * S::LDX;                  // [NP][LDH]  W2t[o][c] = W2[c][o]
+  bf16* X = W2t + NP * S::LDH;                     // [64][LDX]
+  bf16* A1 = X + TILE * S::LDX;                    // [64][LDH]
+  float* B1 = reinterpret_cast<float*>(A1 + TILE * S::LDH);
+  float* B2 = B1 + HID;
+  const bf16 zero = __float2bfloat16(0.f);
+  for (int idx = threadIdx.x; idx < HID * KP; idx += MLP_THREADS) {
+    int n = idx / KP, k = idx % KP;
+    W1t[n * S::LDX + k] = k < a.kin ? a.w1[k * HID + n] : zero;
+  }
+  for (int idx = threadIdx.x; idx < NP * HID; idx += MLP_THREADS) {
+    int o = idx / HID, c = idx % HID;
+    W2t[o * S::LDH + c] = o < a.nout ? a.w2[c * a.nout + o] : zero;
+  }
+  for (int idx = threadIdx.x; idx < HID; idx += MLP_THREADS) B1[idx] = a.b1[idx];
+  for (int idx = threadIdx.x; idx < NP; idx += MLP_THREADS) B2[idx] = idx < a.nout ? a.b2[idx] : 0.f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int m0 = warp * 16;
+  const int64_t rows = arg_rows(a);
+  for (int64_t tile = blockIdx.x; tile * TILE < rows; tile += gridDim.x) {
+    const int64_t row0 = tile * TILE;
+    load_tile<MODE, KP>(a, row0, rows, X, S::LDX);
+    __syncthreads();
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < KP / 16; ++kt) {
+      uint32_t af[4];
+      frag_a_rm(af, X, S::LDX, m0, kt * 16);
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        uint32_t bfr[2];
+        frag_b_nk(bfr, W1t, S::LDX, kt * 16, nt * 8);
+        mma16816(acc[nt], af, bfr);
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      int c = nt * 8 + 2 * t;
+      A1[(m0 + g) * S::LDH + c] = __float2bfloat16(silu(acc[nt][0] + B1[c]));
+      A1[(m0 + g) * S::LDH + c + 1] = __float2bfloat16(silu(acc[nt][1] + B1[c + 1]));
+      A1[(m0 + g + 8) * S::LDH + c] = __float2bfloat16(silu(acc[nt][2] + B1[c]));
+      A1[(m0 + g + 8) * S::LDH + c + 1] = __float2bfloat16(silu(acc[nt][3] + B1[c + 1]));
+    }
+    __syncwarp();
+    float acc2[NP / 8][4];
+#pragma unroll
+    for (int nt = 0; nt < NP / 8; ++nt) acc2[nt][0] = acc2[nt][1] = acc2[nt][2] = acc2[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < HID / 16; ++kt) {
+      uint32_t af[4];
+      frag_a_rm(af, A1, S::LDH, m0, kt * 16);
+#pragma unroll
+      for (int nt = 0; nt < NP / 8; ++nt) {
+        uint32_t bfr[2];
+        frag_b_nk(bfr, W2t, S::LDH, kt * 16, nt * 8);
+        mma16816(acc2[nt], af, bfr);
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < NP / 8; ++nt) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int r = m0 + g + (q >> 1) * 8, o = nt * 8 + 2 * t + (q & 1);
+        int64_t row = row0 + r;
+        if (row >= rows || o >= a.nout) continue;
+        float v = acc2[nt][q] + B2[o];
+        if (a.out_f) {
+          a.out_f[row * a.nout + o] = v;
+        } else {
+          if (MODE == MODE_EDGE) v += __bfloat162float(a.e[row * HID + o]);
+          if (MODE == MODE_NODE) v += __bfloat162float(a.h[row * HID + o]);
+          a.out_bf[row * HID + o] = __float2bfloat16(v);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Backward of one fused MLP over its rows: recompute z1 = X W1 + b1 and
+// a1 = silu(z1); dA1 = dOut W2^T; dZ = dA1 * silu'(z1); dX = dZ W1^T,
+// scattered to the gather sources; dW1 += X^T dZ, dW2 += a1^T dOut,
+// db1 += sum dZ, db2 += sum dOut. Each warp owns a fixed set of the weight-
+// gradient tiles and accumulates them in shared memory across the CTA's row
+// tiles; one atomic add per element and CTA at the end.
+// ---------------------------------------------------------------------------
+template <int KP, int NP>
+struct BwdSmem {
+  static constexpr int LDX = KP + 8, LDH = HID + 8, LDO = NP + 8, LDW1 = HID + 8;
+  // W1t [64][LDX], W1r [KP][LDW1], W2r [64][LDO], W2t (not needed), X [64][LDX],
+  // A1 [64][LDH], DZ [64][LDH], DO [64][LDO]; FP32: gW1 [KP][64], gW2 [64][NP], gb1 [64], gb2 [NP], B1 [64]
+  static constexpr size_t bf_elems = (size_t)HID * LDX + (size_t)KP * LDW1 + (size_t)HID * LDO +
+                                     (size_t)TILE * LDX + 2 * (size_t)TILE * LDH + (size_t)TILE * LDO;
+  static constexpr size_t f_elems = (size_t)KP * HID + (size_t)HID * NP + HID + NP + HID;
+  static constexpr size_t bytes = bf_elems * 2 + f_elems * 4;
+};
+
+template <int MODE, int KP, int NP>
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd(MlpArgs a) {
+  using S = BwdSmem<KP, NP>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16* W1t = reinterpret_cast<bf16*>(smem);   // [64][LDX]   W1t[c][k] = W1[k][c]
+  bf16* W1r = W1t + HID * S::LDX;               // [KP][LDW1]  W1r[k][c] = W1[k][c]
+  bf16* W2r = W1r + KP * S::LDW1;               // [64][LDO]   W2r[c][o] = W2[c][o]
+  bf16* X = W2r + HID * S::LDO;                 // [64][LDX]
+  bf16* A1 = X + TILE * S::LDX;                 // [64][LDH]
+  bf16* DZ = A1 + TILE * S::LDH;                // [64][LDH]
+  bf16* DO = DZ + TILE * S::LDH;                // [64][LDO]
+  float* gW1 = reinterpret_cast<float*>(DO + TILE * S::LDO);  // [KP][64]
+  float* gW2 = gW1 + KP * HID;                  // [64][NP]
+  float* gB1 = gW2 + HID * NP;
+  float* gB2 = gB1 + HID;
+  float* B1 = gB2 + NP;
+  const bf16 zero = __float2bfloat16(0.f);
+  for (int idx = threadIdx.x; idx < HID * KP; idx += MLP_THREADS) {
+    int c = idx / KP, k = idx % KP;
+    bf16 v = k < a.kin ? a.w1[k * HID + c] : zero;
+    W1t[c * S::LDX + k] = v;
+    W1r[k * S::LDW1 + c] = v;
+  }
+  for (int idx = threadIdx.x; idx < HID * NP; idx += MLP_THREADS) {
+    int c = idx / NP, o = idx % NP;
+    W2r[c * S::LDO + o] = o < a.nout ? a.w2[c * a.nout + o] : zero;
+  }
+  for (int idx = threadIdx.x; idx < KP * HID + HID * NP + HID + NP; idx += MLP_THREADS) gW1[idx] = 0.f;
+  for (int idx = threadIdx.x; idx < HID; idx += MLP_THREADS) B1[idx] = a.b1[idx];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int m0 = warp * 16;
+  const int64_t rows = arg_rows(a);
+  const int dstride = (MODE == MODE_LIST) ? a.nout : HID;  // incoming gradient row width
+  for (int64_t tile = blockIdx.x; tile * TILE < rows; tile += gridDim.x) {
+    const int64_t row0 = tile * TILE;
+    load_tile<MODE, KP>(a, row0, rows, X, S::LDX);
+    for (int idx = threadIdx.x; idx < TILE * NP; idx += MLP_THREADS) {
+      int r = idx / NP, o = idx % NP;
+      int64_t row = row0 + r;
+      float v = (row < rows && o < a.nout) ? a.dout[row * dstride + o] : 0.f;
+      DO[r * S::LDO + o] = __float2bfloat16(v);
+    }
+    __syncthreads();
+    // bias gradient of the second layer from the FP32 incoming gradient
+    for (int o = threadIdx.x; o < a.nout; o += MLP_THREADS) {
+      float sacc = 0.f;
+      for (int r = 0; r < TILE && row0 + r < rows; ++r) sacc += a.dout[(row0 + r) * dstride + o];
+      gB2[o] += sacc;
+    }
+    // recompute z1 (warp's 16 rows x 64)
+    float z[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) z[nt][0] = z[nt][1] = z[nt][2] = z[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < KP / 16; ++kt) {
+      uint32_t af[4];
+      frag_a_rm(af, X, S::LDX, m0, kt * 16);
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        uint32_t bfr[2];
+        frag_b_nk(bfr, W1t, S::LDX, kt * 16, nt * 8);
+        mma16816(z[nt], af, bfr);
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int r = m0 + g + (q >> 1) * 8, c = nt * 8 + 2 * t + (q & 1);
+        z[nt][q] += B1[c];
+        A1[r * S::LDH + c] = __float2bfloat16(silu(z[nt][q]));
+      }
+    }
+    // dA1 = dOut W2^T  (B[k=o][n=c] = W2[c][o] = W2r[c][o] -> stored [n][k])
+    float da[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) da[nt][0] = da[nt][1] = da[nt][2] = da[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < NP / 16; ++kt) {
+      uint32_t af[4];
+      frag_a_rm(af, DO, S::LDO, m0, kt * 16);
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        uint32_t bfr[2];
+        frag_b_nk(bfr, W2r, S::LDO, kt * 16, nt * 8);
+        mma16816(da[nt], af, bfr);
+      }
+    }
+    // dZ = dA1 * silu'(z1); bias gradient of the first layer
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float cs0 = 0.f, cs1 = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int r = m0 + g + (q >> 1) * 8, c = nt * 8 + 2 * t + (q & 1);
+        bool valid = row0 + r < rows;
+        float dz = valid ? da[nt][q] * silu_grad(z[nt][q]) : 0.f;
+        DZ[r * S::LDH + c] = __float2bfloat16(dz);
+        if (q & 1) cs1 += dz; else cs0 += dz;
+      }
+      for (int off = 4; off < 32; off <<= 1) {
+        cs0 += __shfl_xor_sync(0xffffffffu, cs0, off);
+        cs1 += __shfl_xor_sync(0xffffffffu, cs1, off);
+      }
+      if (g == 0) {
+        atomicAdd(&gB1[nt * 8 + 2 * t], cs0);
+        atomicAdd(&gB1[nt * 8 + 2 * t + 1], cs1);
+      }
+    }
+    __syncthreads();
+    // dX = dZ W1^T (B[k=c][n=k_in] = W1[k_in][c] = W1r[k_in][c] -> stored [n][k]); scatter
+    if (MODE != MODE_DIRECT) {
+#pragma unroll 1
+      for (int nt = 0; nt < KP / 8; ++nt) {
+        float dx[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < HID / 16; ++kt) {
+          uint32_t af[4], bfr[2];
+          frag_a_rm(af, DZ, S::LDH, m0, kt * 16);
+          frag_b_nk(bfr, W1r, S::LDW1, kt * 16, nt * 8);
+          mma16816(dx, af, bfr);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int r = m0 + g + (q >> 1) * 8, k = nt * 8 + 2 * t + (q & 1);
+          int64_t row = row0 + r;
+          if (row >= rows || k >= a.kin) continue;
+          float v = dx[q];
+          if (MODE == MODE_LIST) {
+            a.dh[(int64_t)a.list[row] * HID + k] = v;
+          } else if (MODE == MODE_EDGE) {
+            if (k < HID) a.din_row[row * HID + k] = a.dout[row * HID + k] + v;
+            else if (k < 2 * HID) atomicAdd(&a.dh[(int64_t)a.recv[row] * HID + k - HID], v);
+            else atomicAdd(&a.dh[(int64_t)a.send[row] * HID + k - 2 * HID], v);
+          } else {  // MODE_NODE
+            if (k < HID) a.din_row[row * HID + k] = a.dout[row * HID + k] + v;
+            else a.dagg[row * HID + k - HID] = v;
+          }
+        }
+      }
+    }
+    // weight gradients: tiles (mt, nt) of dW1 [KP x 64] and dW2 [64 x NP], round-robin over warps
+    {
+      constexpr int T1 = (KP / 16) * 8;
+      for (int tt = warp; tt < T1; tt += 4) {
+        int mt = tt / 8, nt = tt % 8;
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < TILE / 16; ++kt) {
+          uint32_t af[4], bfr[2];
+          frag_a_t(af, X, S::LDX, mt * 16, kt * 16);     // A[m=k_in][k=row] = X[row][k_in]
+          frag_b_kn(bfr, DZ, S::LDH, kt * 16, nt * 8);   // B[k=row][n=c] = DZ[row][c]
+          mma16816(c, af, bfr);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int m = mt * 16 + g + (q >> 1) * 8, n = nt * 8 + 2 * t + (q & 1);
+          gW1[m * HID + n] += c[q];
+        }
+      }
+      constexpr int T2 = (HID / 16) * (NP / 8);
+      for (int tt = warp; tt < T2; tt += 4) {
+        int mt = tt / (NP / 8), nt = tt % (NP / 8);
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < TILE / 16; ++kt) {
+          uint32_t af[4], bfr[2];
+          frag_a_t(af, A1, S::LDH, mt * 16, kt * 16);    // A[m=c][k=row] = A1[row][c]
+          frag_b_kn(bfr, DO, S::LDO, kt * 16, nt * 8);   // B[k=row][n=o] = DO[row][o]
+          mma16816(c, af, bfr);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int m = mt * 16 + g + (q >> 1) * 8, n = nt * 8 + 2 * t + (q & 1);
+          gW2[m * NP + n] += c[q];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < a.kin * HID; idx += MLP_THREADS) atomicAdd(&a.gw1[idx], gW1[idx]);
+  for (int idx = threadIdx.x; idx < HID * a.nout; idx += MLP_THREADS) {
+    int c = idx / a.nout, o = idx % a.nout;
+    atomicAdd(&a.gw2[idx], gW2[c * NP + o]);
+  }
+  for (int idx = threadIdx.x; idx < HID; idx += MLP_THREADS) atomicAdd(&a.gb1[idx], gB1[idx]);
+  for (int idx = threadIdx.x; idx < a.nout; idx += MLP_THREADS) atomicAdd(&a.gb2[idx], gB2[idx]);
+}
+
+// ---------------------------------------------------------------------------
+// Graph, features, aggregation, loss, optimiser
+// ---------------------------------------------------------------------------
+__global__ void k_sg_count(Params p, State s, Work w, int64_t n, int64_t nf, uint32_t* cnt) {
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gi >= nf) return;
+  uint32_t i = w.fluid_list[gi];
+  int c = (int)w.nbr_cnt[gi];
+  uint32_t m = 0;
+  for (int k = 0; k < c; ++k) {
+    uint32_t j = w.nbr[(int64_t)k * nf + gi];
+    double r2 = 0.0;
+    for (int d = 0; d < p.dim; ++d) {
+      double dd = __dsub_rn(s.x[d * n + j], s.x[d * n + i]);
+      r2 = __dadd_rn(r2, __dmul_rn(dd, dd));
+    }
+    if (r2 <= p.four_h2 && r2 > 0.0) ++m;
+  }
+  cnt[gi] = m;
+}
+
+__global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, const uint32_t* row_ptr,
+                          uint32_t* recv, uint32_t* send, bf16* efeat) {
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gi >= nf) return;
+  uint32_t i = w.fluid_list[gi];
+  int c = (int)w.nbr_cnt[gi];
+  int64_t e = row_ptr[gi];
+  double inv_h = 1.0 / p.h;
+  for (int k = 0; k < c; ++k) {
+    uint32_t j = w.nbr[(int64_t)k * nf + gi];
+    double r[3] = {0, 0, 0}, r2 = 0.0;
+    for (int d = 0; d < p.dim; ++d) {
+      r[d] = __dsub_rn(s.x[d * n + j], s.x[d * n + i]);
+      r2 = __dadd_rn(r2, __dmul_rn(r[d], r[d]));
+    }
+    if (!(r2 <= p.four_h2 && r2 > 0.0)) continue;
+    recv[e] = i;
+    send[e] = j;
+    bf16* f = efeat + e * FEAT;
+    for (int d = 0; d < FEAT; ++d) f[d] = __float2bfloat16(0.f);
+    for (int d = 0; d < p.dim; ++d) f[d] = __float2bfloat16((float)(r[d] * inv_h));
+    f[p.dim] = __float2bfloat16((float)(sqrt(r2) * inv_h));
+    ++e;
+  }
+}
+
+// node features: (U, rho/rho0 - 1, phi) normalised by (mean, std), dummy flag
+__global__ void k_sg_nodes(Params p, State s, int64_t n, const float* mean, const float* stdv, bf16* nf_out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v[FEAT] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int d = 0; d < p.dim; ++d) v[d] = (float)s.u[d * n + i];
+  double rho = eos_density(p, s.phi[i]);
+  v[p.dim] = (float)(rho / p.rho0 - 1.0);
+  v[p.dim + 1] = (float)s.phi[i];
+  for (int k = 0; k < p.dim + 2; ++k) v[k] = (v[k] - mean[k]) / stdv[k];
+  v[p.dim + 2] = s.type[i] == kFluid ? 0.f : 1.f;
+  for (int k = 0; k < FEAT; ++k) nf_out[i * FEAT + k] = __float2bfloat16(v[k]);
+}
+
+// a_i = sum of the receiver's edge states (fluid rows; other nodes keep zero)
+__global__ void k_sg_aggregate(const uint32_t* fluid_list, int64_t nf, const uint32_t* row_ptr,
+                               const bf16* e, bf16* agg) {
+  int64_t gi = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (gi >= nf) return;
+  uint32_t i = fluid_list[gi];
+  float s0 = 0.f, s1 = 0.f;
+  for (uint32_t k = row_ptr[gi]; k < row_ptr[gi + 1]; ++k) {
+    __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162*>(e + (int64_t)k * HID)[lane];
+    s0 += __bfloat162float(v.x);
+    s1 += __bfloat162float(v.y);
+  }
+  reinterpret_cast<__nv_bfloat162*>(agg + (int64_t)i * HID)[lane] = __floats2bfloat162_rn(s0, s1);
+}
+
+// de_e += dagg_recv(e)
+__global__ void k_sg_aggregate_bwd(const uint32_t* fluid_list, int64_t nf, const uint32_t* row_ptr,
+                                   const float* dagg_rows, float* de) {
+  int64_t gi = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (gi >= nf) return;
+  uint32_t i = fluid_list[gi];
+  float2 g = reinterpret_cast<const float2*>(dagg_rows + (int64_t)i * HID)[lane];
+  for (uint32_t k = row_ptr[gi]; k < row_ptr[gi + 1]; ++k) {
+    float2* p2 = reinterpret_cast<float2*>(de + (int64_t)k * HID) + lane;
+    float2 v = *p2;
+    v.x += g.x;
+    v.y += g.y;
+    *p2 = v;
+  }
+}
+
+// normalised targets from the plain rates; loss and its gradient (fluid rows)
+__global__ void k_sg_loss(int dim, Work w, int64_t n, int64_t nf, const float* out, const float* tmean,
+                          const float* tstd, float* dout, double* loss) {
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double l = 0.0;
+  int no = dim + 1;
+  if (gi < nf) {
+    uint32_t i = w.fluid_list[gi];
+    for (int o = 0; o < no; ++o) {
+      double y = o < dim ? w.dudt[o * n + i] : w.dphidt[i];
+      float tn = (float)((y - tmean[o]) / tstd[o]);
+      float d = out[gi * no + o] - tn;
+      l += (double)d * d;
+      dout[gi * no + o] = 2.f * d / (float)(nf * no);
+    }
+  }
+  for (int off = 16; off; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+  if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l / (double)(nf * no));
+}
+
+// de-normalised outputs -> stage rates (shifting velocity zero)
+__global__ void k_sg_rates(int dim, Work w, int64_t n, int64_t nf, const float* out, const float* tmean,
+                           const float* tstd) {
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gi >= nf) return;
+  uint32_t i = w.fluid_list[gi];
+  int no = dim + 1;
+  for (int o = 0; o < dim; ++o) {
+    w.dudt[o * n + i] = (double)out[gi * no + o] * tstd[o] + tmean[o];
+    w.dushift[o * n + i] = 0.0;
+  }
+  w.dphidt[i] = (double)out[gi * no + dim] * tstd[dim] + tmean[dim];
+}
+
+__global__ void k_adam(int64_t np, float* p, const float* g, float* m, float* v, float lr, float b1,
+                       float b2, float eps, float c1, float c2, bf16* pb) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  float gk = g[k];
+  float mk = b1 * m[k] + (1.f - b1) * gk;
+  float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+  m[k] = mk;
+  v[k] = vk;
+  float pk = p[k] - lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+  p[k] = pk;
+  pb[k] = __float2bfloat16(pk);
+}
+
+__global__ void k_to_bf16(int64_t np, const float* p, bf16* pb) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < np) pb[k] = __float2bfloat16(p[k]);
+}
+
+struct Block {
+  int kin, nout;
+  int64_t w1, b1, w2, b2;  // offsets into the flat parameter vector
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Surrogate object
+// ---------------------------------------------------------------------------
+struct wbsph_surrogate_s {
+  wbsph_surrogate_config cfg;
+  int dim = 2, layers = 3;
+  std::vector<Block> blocks;
+  int64_t np = 0;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  bf16* pb = nullptr;
+  float* norm = nullptr;  // node mean[8], node std[8], target mean[4], target std[4]
+  int64_t adam_t = 0;
+  // graph and activations, sized on demand
+  int64_t cap_n = 0, cap_nf = 0, cap_e = 0;
+  uint32_t *cnt = nullptr, *row_ptr = nullptr, *recv = nullptr, *send = nullptr;
+  bf16 *efeat = nullptr, *nfeat = nullptr;
+  std::vector<bf16*> hs, es, aggs;
+  float *out = nullptr, *dout = nullptr, *dh = nullptr, *de = nullptr, *dagg = nullptr;
+  double* loss = nullptr;
+  int64_t E = 0;
+  std::string err;
+};
+
+namespace {
+
+int sfail(wbsph_surrogate s, int code, const char* msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+void build_blocks(wbsph_surrogate s) {
+  int d = s->dim;
+  int64_t off = 0;
+  auto add = [&](int kin, int nout) {
+    Block b;
+    b.kin = kin; b.nout = nout;
+    b.w1 = off; off += (int64_t)kin * HID;
+    b.b1 = off; off += HID;
+    b.w2 = off; off += (int64_t)HID * nout;
+    b.b2 = off; off += nout;
+    s->blocks.push_back(b);
+  };
+  add(d + 3, HID);
+  add(d + 1, HID);
+  for (int l = 0; l < s->layers; ++l) {
+    add(3 * HID, HID);
+    add(2 * HID, HID);
+  }
+  add(HID, d + 1);
+  s->np = off;
+}
+
+template <class T>
+bool dalloc(T** p, size_t count) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  *p = (T*)q;
+  return true;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+void free_graph(wbsph_surrogate s) {
+  dfree(s->cnt); dfree(s->row_ptr); dfree(s->recv); dfree(s->send); dfree(s->efeat); dfree(s->nfeat);
+  for (auto* q : s->hs) dfree(q);
+  for (auto* q : s->es) dfree(q);
+  for (auto* q : s->aggs) dfree(q);
+  s->hs.clear(); s->es.clear(); s->aggs.clear();
+  dfree(s->out); dfree(s->dout); dfree(s->dh); dfree(s->de); dfree(s->dagg);
+  s->cnt = s->row_ptr = s->recv = s->send = nullptr;
+  s->efeat = s->nfeat = nullptr;
+  s->out = s->dout = s->dh = s->de = s->dagg = nullptr;
+  s->cap_n = s->cap_nf = s->cap_e = 0;
+}
+
+int ensure_nodes(wbsph_surrogate s, int64_t n, int64_t nf) {
+  if (n <= s->cap_n && nf <= s->cap_nf) return WBSPH_OK;
+  int64_t e_keep = s->cap_e;
+  free_graph(s);
+  s->cap_n = n; s->cap_nf = nf;
+  bool ok = dalloc(&s->cnt, nf + 1) && dalloc(&s->row_ptr, nf + 1) && dalloc(&s->nfeat, n * FEAT) &&
+            dalloc(&s->out, nf * 4) && dalloc(&s->dout, nf * 4) && dalloc(&s->dh, n * HID) &&
+            dalloc(&s->dagg, n * HID);
+  for (int l = 0; ok && l <= s->layers; ++l) {
+    bf16* q = nullptr;
+    ok = dalloc(&q, n * HID);
+    s->hs.push_back(q);
+    if (ok && l < s->layers) {
+      ok = dalloc(&q, n * HID);
+      s->aggs.push_back(q);
+    }
+  }
+  (void)e_keep;
+  return ok ? WBSPH_OK : sfail(s, WBSPH_E_NOMEM, "surrogate node buffers");
+}
+
+int ensure_edges(wbsph_surrogate s, int64_t E) {
+  if (E <= s->cap_e) return WBSPH_OK;
+  dfree(s->recv); dfree(s->send); dfree(s->efeat); dfree(s->de);
+  for (auto* q : s->es) dfree(q);
+  s->es.clear();
+  int64_t cap = E + E / 4 + 1024;
+  bool ok = dalloc(&s->recv, cap) && dalloc(&s->send, cap) && dalloc(&s->efeat, cap * FEAT) &&
+            dalloc(&s->de, cap * HID);
+  for (int l = 0; ok && l <= s->layers; ++l) {
+    bf16* q = nullptr;
+    ok = dalloc(&q, cap * HID);
+    s->es.push_back(q);
+  }
+  s->cap_e = ok ? cap : 0;
+  return ok ? WBSPH_OK : sfail(s, WBSPH_E_NOMEM, "surrogate edge buffers");
+}
+
+template <int MODE, int KP, int NP>
+void launch_fwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
+  size_t sm = Smem<KP, NP>::fwd_bytes;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mlp_fwd<MODE, KP, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  int64_t tiles = div_up(max_rows > 0 ? max_rows : 1, TILE);
+  int grid = (int)(tiles < 152 * 4 ? tiles : 152 * 4);
+  k_mlp_fwd<MODE, KP, NP><<<grid, MLP_THREADS, sm, st>>>(a);
+}
+
+template <int MODE, int KP, int NP>
+void launch_bwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
+  size_t sm = BwdSmem<KP, NP>::bytes;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mlp_bwd<MODE, KP, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  int64_t tiles = div_up(max_rows > 0 ? max_rows : 1, TILE);
+  int grid = (int)(tiles < 152 ? tiles : 152);
+  k_mlp_bwd<MODE, KP, NP><<<grid, MLP_THREADS, sm, st>>>(a);
+}
+
+MlpArgs block_args(wbsph_surrogate s, int bi) {
+  const Block& b = s->blocks[bi];
+  MlpArgs a;
+  memset(&a, 0, sizeof a);
+  a.kin = b.kin;
+  a.nout = b.nout;
+  a.w1 = s->pb + b.w1; a.b1 = s->p + b.b1; a.w2 = s->pb + b.w2; a.b2 = s->p + b.b2;
+  a.gw1 = s->g + b.w1; a.gb1 = s->g + b.b1; a.gw2 = s->g + b.w2; a.gb2 = s->g + b.b2;
+  return a;
+}
+
+// Graph of the sim's current state (candidate lists must be built).
+int build_graph(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n,
+                int64_t nf, cudaStream_t cs) {
+  int rc = ensure_nodes(s, n, nf);
+  if (rc) return rc;
+  if (nf > 0) k_sg_count<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p, st, w, n, nf, s->cnt);
+  cudaMemsetAsync(s->cnt + nf, 0, 4, cs);
+  cudaMemcpyAsync(s->row_ptr, s->cnt, (nf + 1) * 4, cudaMemcpyDeviceToDevice, cs);
+  launch_scan_exclusive(s->row_ptr, nf + 1, cs);
+  uint32_t E = 0;
+  cudaMemcpyAsync(&E, s->row_ptr + nf, 4, cudaMemcpyDeviceToHost, cs);
+  if (cudaStreamSynchronize(cs) != cudaSuccess) return sfail(s, WBSPH_E_CUDA, "graph build");
+  s->E = E;
+  rc = ensure_edges(s, E);
+  if (rc) return rc;
+  if (nf > 0)
+    k_sg_fill<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p, st, w, n, nf, s->row_ptr, s->recv, s->send, s->efeat);
+  k_sg_nodes<<<(unsigned)div_up(n > 0 ? n : 1, 256), 256, 0, cs>>>(p, st, n, s->norm, s->norm + 8, s->nfeat);
+  return WBSPH_OK;
+}
+
+void forward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream_t cs) {
+  const int64_t E = s->E;
+  int L = s->layers;
+  {  // node encoder
+    MlpArgs a = block_args(s, 0);
+    a.rows = n; a.in = s->nfeat; a.out_bf = s->hs[0];
+    launch_fwd<MODE_DIRECT, 16, 64>(a, n, cs);
+  }
+  {  // edge encoder
+    MlpArgs a = block_args(s, 1);
+    a.rows = E; a.in = s->efeat; a.out_bf = s->es[0];
+    launch_fwd<MODE_DIRECT, 16, 64>(a, E, cs);
+  }
+  for (int l = 0; l < L; ++l) {
+    MlpArgs a = block_args(s, 2 + 2 * l);
+    a.rows = E; a.e = s->es[l]; a.h = s->hs[l]; a.recv = s->recv; a.send = s->send; a.out_bf = s->es[l + 1];
+    launch_fwd<MODE_EDGE, 192, 64>(a, E, cs);
+    cudaMemsetAsync(s->aggs[l], 0, (size_t)n * HID * 2, cs);
+    if (nf > 0)
+      k_sg_aggregate<<<(unsigned)div_up(nf, 4), 128, 0, cs>>>(w.fluid_list, nf, s->row_ptr, s->es[l + 1], s->aggs[l]);
+    MlpArgs b = block_args(s, 3 + 2 * l);
+    b.rows = n; b.h = s->hs[l]; b.agg = s->aggs[l]; b.out_bf = s->hs[l + 1];
+    launch_fwd<MODE_NODE, 128, 64>(b, n, cs);
+  }
+  {  // decoder over fluid rows
+    MlpArgs a = block_args(s, 2 + 2 * L);
+    a.rows = nf; a.in = s->hs[L]; a.list = w.fluid_list; a.out_f = s->out;
+    launch_fwd<MODE_LIST, 64, 16>(a, nf, cs);
+  }
+}
+
+void backward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream_t cs) {
+  const int64_t E = s->E;
+  int L = s->layers;
+  cudaMemsetAsync(s->g, 0, (size_t)s->np * 4, cs);
+  cudaMemsetAsync(s->dh, 0, (size_t)n * HID * 4, cs);
+  cudaMemsetAsync(s->de, 0, (size_t)E * HID * 4 + 4, cs);
+  {  // decoder: dh_L[fluid] = dX
+    MlpArgs a = block_args(s, 2 + 2 * L);
+    a.rows = nf; a.in = s->hs[L]; a.list = w.fluid_list; a.dout = s->dout; a.dh = s->dh;
+    launch_bwd<MODE_LIST, 64, 16>(a, nf, cs);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    MlpArgs b = block_args(s, 3 + 2 * l);  // node MLP: dh_l = dh_{l+1} + dX[:64], dagg = dX[64:]
+    b.rows = n; b.h = s->hs[l]; b.agg = s->aggs[l]; b.dout = s->dh; b.din_row = s->dh; b.dagg = s->dagg;
+    launch_bwd<MODE_NODE, 128, 64>(b, n, cs);
+    if (nf > 0)
+      k_sg_aggregate_bwd<<<(unsigned)div_up(nf, 4), 128, 0, cs>>>(w.fluid_list, nf, s->row_ptr, s->dagg, s->de);
+    MlpArgs a = block_args(s, 2 + 2 * l);  // edge MLP: de_l = de_{l+1} + dX[:64], dh += scatter
+    a.rows = E; a.e = s->es[l]; a.h = s->hs[l]; a.recv = s->recv; a.send = s->send;
+    a.dout = s->de; a.din_row = s->de; a.dh = s->dh;
+    launch_bwd<MODE_EDGE, 192, 64>(a, E, cs);
+  }
+  {  // encoders: weight gradients only
+    MlpArgs a = block_args(s, 1);
+    a.rows = E; a.in = s->efeat; a.dout = s->de;
+    launch_bwd<MODE_DIRECT, 16, 64>(a, E, cs);
+    MlpArgs b = block_args(s, 0);
+    b.rows = n; b.in = s->nfeat; b.dout = s->dh;
+    launch_bwd<MODE_DIRECT, 16, 64>(b, n, cs);
+  }
+}
+
+}  // namespace
+
+// Called by the engine for a surrogate stage: graph over the candidate lists,
+// forward pass, de-normalised rates into the stage rate arrays.
+namespace wbsph {
+int surrogate_stage_rates(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n,
+                          int64_t nf, cudaStream_t cs) {
+  launch_nbr_list(p, w, n, nf, cs);
+  int rc = build_graph(s, p, st, w, n, nf, cs);
+  if (rc) return rc;
+  forward(s, w, n, nf, cs);
+  if (nf > 0)
+    k_sg_rates<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, n, nf, s->out, s->norm + 16, s->norm + 20);
+  return WBSPH_OK;
+}
+
+// Loss of the surrogate against the rates currently in the work arrays
+// (the plain pass of the same state); with `train`, backward and Adam.
+int surrogate_loss(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n, int64_t nf,
+                   cudaStream_t cs, int train, float lr, double* loss_out, const float* dout_override,
+                   float* grad_out) {
+  launch_nbr_list(p, w, n, nf, cs);
+  int rc = build_graph(s, p, st, w, n, nf, cs);
+  if (rc) return rc;
+  forward(s, w, n, nf, cs);
+  cudaMemsetAsync(s->loss, 0, 8, cs);
+  if (nf > 0)
+    k_sg_loss<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, n, nf, s->out, s->norm + 16, s->norm + 20,
+                                                          s->dout, s->loss);
+  if (dout_override)
+    cudaMemcpyAsync(s->dout, dout_override, (size_t)nf * (p.dim + 1) * 4, cudaMemcpyHostToDevice, cs);
+  if (train || grad_out) backward(s, w, n, nf, cs);
+  if (grad_out) cudaMemcpyAsync(grad_out, s->g, (size_t)s->np * 4, cudaMemcpyDeviceToHost, cs);
+  if (train) {
+    s->adam_t += 1;
+    const wbsph_surrogate_config& c = s->cfg;
+    float c1 = 1.f - powf(c.beta1, (float)s->adam_t), c2 = 1.f - powf(c.beta2, (float)s->adam_t);
+    k_adam<<<(unsigned)div_up(s->np, 256), 256, 0, cs>>>(s->np, s->p, s->g, s->m, s->v, lr, c.beta1, c.beta2,
+                                                         c.eps, c1, c2, s->pb);
+  }
+  double l = 0.0;
+  cudaMemcpyAsync(&l, s->loss, 8, cudaMemcpyDeviceToHost, cs);
+  cudaError_t e = cudaStreamSynchronize(cs);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return sfail(s, WBSPH_E_CUDA, cudaGetErrorString(e));
+  if (loss_out) *loss_out = l;
+  return WBSPH_OK;
+}
+
+int64_t surrogate_edges(wbsph_surrogate s) { return s->E; }
+const float* surrogate_out(wbsph_surrogate s) { return s->out; }
+const uint32_t* surrogate_recv(wbsph_surrogate s) { return s->recv; }
+const uint32_t* surrogate_send(wbsph_surrogate s) { return s->send; }
+const bf16* surrogate_efeat(wbsph_surrogate s) { return s->efeat; }
+const bf16* surrogate_nfeat(wbsph_surrogate s) { return s->nfeat; }
+}  // namespace wbsph
+
+// ---------------------------------------------------------------------------
+// C-ABI: create / parameters / normalisation / destroy
+// ---------------------------------------------------------------------------
+extern "C" int wbsph_surrogate_config_default(wbsph_surrogate_config* c, int dim) {
+  if (!c || (dim != 2 && dim != 3)) return WBSPH_E_INVAL;
+  memset(c, 0, sizeof *c);
+  c->dim = dim;
+  c->hidden = HID;
+  c->layers = 3;
+  c->beta1 = 0.9f;
+  c->beta2 = 0.999f;
+  c->eps = 1e-8f;
+  c->device = 0;
+  return WBSPH_OK;
+}
+
+extern "C" int wbsph_surrogate_create(const wbsph_surrogate_config* c, wbsph_surrogate* out) {
+  if (!c || !out) return WBSPH_E_INVAL;
+  *out = nullptr;
+  if (c->dim != 2 && c->dim != 3) return WBSPH_E_INVAL;
+  if (c->hidden != HID || c->layers < 1 || c->layers > 8) return WBSPH_E_INVAL;
+  if (cudaSetDevice(c->device) != cudaSuccess) { cudaGetLastError(); return WBSPH_E_CUDA; }
+  wbsph_surrogate s = new wbsph_surrogate_s();
+  s->cfg = *c;
+  s->dim = c->dim;
+  s->layers = c->layers;
+  build_blocks(s);
+  bool ok = dalloc(&s->p, s->np) && dalloc(&s->g, s->np) && dalloc(&s->m, s->np) && dalloc(&s->v, s->np) &&
+            dalloc(&s->pb, s->np) && dalloc(&s->norm, 32) && dalloc(&s->loss, 1);
+  if (!ok) {
+    wbsph_surrogate_destroy(s);
+    return WBSPH_E_NOMEM;
+  }
+  cudaMemset(s->p, 0, s->np * 4);
+  cudaMemset(s->m, 0, s->np * 4);
+  cudaMemset(s->v, 0, s->np * 4);
+  cudaMemset(s->pb, 0, s->np * 2);
+  std::vector<float> nrm(32, 0.f);
+  for (int k = 8; k < 16; ++k) nrm[k] = 1.f;
+  for (int k = 20; k < 24; ++k) nrm[k] = 1.f;
+  cudaMemcpy(s->norm, nrm.data(), 32 * 4, cudaMemcpyHostToDevice);
+  *out = s;
+  return WBSPH_OK;
+}
+
+extern "C" void wbsph_surrogate_destroy(wbsph_surrogate s) {
+  if (!s) return;
+  cudaSetDevice(s->cfg.device);
+  cudaDeviceSynchronize();
+  free_graph(s);
+  dfree(s->p); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->pb); dfree(s->norm); dfree(s->loss);
+  delete s;
+}
+
+extern "C" int64_t wbsph_surrogate_num_params(wbsph_surrogate s) { return s ? s->np : WBSPH_E_INVAL; }
+
+extern "C" int wbsph_surrogate_set_params(wbsph_surrogate s, const float* params) {
+  if (!s || !params) return WBSPH_E_INVAL;
+  cudaSetDevice(s->cfg.device);
+  if (cudaMemcpy(s->p, params, s->np * 4, cudaMemcpyHostToDevice) != cudaSuccess) return WBSPH_E_CUDA;
+  cudaMemset(s->m, 0, s->np * 4);
+  cudaMemset(s->v, 0, s->np * 4);
+  s->adam_t = 0;
+  k_to_bf16<<<(unsigned)div_up(s->np, 256), 256>>>(s->np, s->p, s->pb);
+  return cudaDeviceSynchronize() == cudaSuccess ? WBSPH_OK : WBSPH_E_CUDA;
+}
+
+extern "C" int wbsph_surrogate_get_params(wbsph_surrogate s, float* params) {
+  if (!s || !params) return WBSPH_E_INVAL;
+  cudaSetDevice(s->cfg.device);
+  cudaDeviceSynchronize();
+  return cudaMemcpy(params, s->p, s->np * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? WBSPH_OK : WBSPH_E_CUDA;
+}
+
+extern "C" int wbsph_surrogate_set_normalization(wbsph_surrogate s, const float* node_mean,
+                                                 const float* node_std, const float* out_mean,
+                                                 const float* out_std) {
+  if (!s || !node_mean || !node_std || !out_mean || !out_std) return WBSPH_E_INVAL;
+  std::vector<float> nrm(32, 0.f);
+  int fn = s->dim + 2, fo = s->dim + 1;
+  for (int k = 0; k < 8; ++k) nrm[8 + k] = 1.f;
+  for (int k = 0; k < fn; ++k) {
+    if (!(node_std[k] > 0)) return sfail(s, WBSPH_E_INVAL, "node std must be positive");
+    nrm[k] = node_mean[k];
+    nrm[8 + k] = node_std[k];
+  }
+  for (int k = 0; k < 4; ++k) nrm[20 + k] = 1.f;
+  for (int k = 0; k < fo; ++k) {
+    if (!(out_std[k] > 0)) return sfail(s, WBSPH_E_INVAL, "output std must be positive");
+    nrm[16 + k] = out_mean[k];
+    nrm[20 + k] = out_std[k];
+  }
+  cudaSetDevice(s->cfg.device);
+  return cudaMemcpy(s->norm, nrm.data(), 32 * 4, cudaMemcpyHostToDevice) == cudaSuccess ? WBSPH_OK : WBSPH_E_CUDA;
+}
+
+extern "C" const char* wbsph_surrogate_last_error(wbsph_surrogate s) { return s ? s->err.c_str() : "null"; }
+
+// relative L2 error of DU/Dt: sums[0] += |a - a_ref|^2, sums[1] += |a|^2 over fluid
+namespace {
+__global__ void k_rel_err(int dim, Work w, int64_t n, int64_t nf, const double* a_ref, double* sums) {
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double e2 = 0.0, r2 = 0.0;
+  if (gi < nf) {
+    uint32_t i = w.fluid_list[gi];
+    for (int d = 0; d < dim; ++d) {
+      double a = w.dudt[d * n + i], b = a_ref[d * n + i];
+      e2 += (b - a) * (b - a);
+      r2 += a * a;
+    }
+  }
+  for (int off = 16; off; off >>= 1) {
+    e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+    r2 += __shfl_xor_sync(0xffffffffu, r2, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[0], e2);
+    atomicAdd(&sums[1], r2);
+  }
+}
+}  // namespace
+
+namespace wbsph {
+void launch_rel_err(const Params& p, const Work& w, int64_t n, int64_t nf, const double* a_ref_copy,
+                    double* sums, cudaStream_t st) {
+  cudaMemsetAsync(sums, 0, 16, st);
+  if (nf > 0) k_rel_err<<<(unsigned)div_up(nf, 128), 128, 0, st>>>(p.dim, w, n, nf, a_ref_copy, sums);
+}
+}  // namespace wbsph

@@ -64,7 +64,8 @@ struct CandidateIter {
     return false;
   }
 
-  __device__ __forceinline__ bool next(const Params& p, const Work& w, uint32_t& j) {
+  // Next candidate j and its FP32 squared distance r2f.
+  __device__ __forceinline__ bool next(const Params& p, const Work& w, uint32_t& j, float& r2f) {
     for (;;) {
       while (cur < end) {
         uint32_t c = cur++;
@@ -74,11 +75,17 @@ struct CandidateIter {
         float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 <= p.prefilter_r2) {
           j = c;
+          r2f = r2;
           return true;
         }
       }
       if (!advance_row(p, w)) return false;
     }
+  }
+
+  __device__ __forceinline__ bool next(const Params& p, const Work& w, uint32_t& j) {
+    float r2f;
+    return next(p, w, j, r2f);
   }
 };
 

@@ -130,6 +130,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
   }
 }
 
+void launch_scan_exclusive(uint32_t* data, int64_t total, cudaStream_t st) {
+  k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(data, total);
+}
+
 int radix_sort_scratch_words(int64_t n) { return (int)(256 * div_up(n > 0 ? n : 1, RS_TILE)); }
 
 static int bits_for(int64_t ncells) {
@@ -160,7 +164,7 @@ void launch_radix_sort(const Params& p, Work& w, int64_t n, cudaStream_t st, int
 // ---------------------------------------------------------------------------
 // Reorder (Sec. 3: particles of one cell stored contiguously): gather every
 // per-particle array by the sort permutation; also writes the FP32 position
-// copy used by the candidate prefilter.
+// copy used by the candidate prefilter (.w = particle type).
 // ---------------------------------------------------------------------------
 __global__ void k_gather(int dim, State src, State dst, const uint32_t* __restrict__ perm, int64_t n,
                          int with_base, float4* __restrict__ xf) {
@@ -183,7 +187,9 @@ __global__ void k_gather(int dim, State src, State dst, const uint32_t* __restri
   dst.phi[i] = src.phi[j];
   if (with_base) dst.phi0[i] = src.phi0[j];
   dst.mass[i] = src.mass[j];
-  dst.type[i] = src.type[j];
+  uint8_t ty = src.type[j];
+  dst.type[i] = ty;
+  f.w = (float)ty;
   dst.oid[i] = src.oid[j];
   xf[i] = f;
 }
@@ -220,11 +226,11 @@ void launch_cell_bounds(const Params& p, const Work& w, int64_t n, cudaStream_t 
 // ---------------------------------------------------------------------------
 constexpr int CMP_THREADS = 1024;
 
-__global__ void __launch_bounds__(CMP_THREADS) k_count_fluid(const uint8_t* __restrict__ type, int64_t n,
-                                                            uint32_t* __restrict__ cnt) {
+__global__ void __launch_bounds__(CMP_THREADS) k_count_type(const uint8_t* __restrict__ type, int64_t n,
+                                                           uint8_t want, uint32_t* __restrict__ cnt) {
   __shared__ uint32_t wsum[CMP_THREADS / 32];
   int64_t i = blockIdx.x * (int64_t)CMP_THREADS + threadIdx.x;
-  bool f = i < n && type[i] == kFluid;
+  bool f = i < n && type[i] == want;
   unsigned b = __ballot_sync(0xffffffffu, f);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(b);
   __syncthreads();
@@ -235,13 +241,13 @@ __global__ void __launch_bounds__(CMP_THREADS) k_count_fluid(const uint8_t* __re
   }
 }
 
-__global__ void __launch_bounds__(CMP_THREADS) k_write_fluid(const uint8_t* __restrict__ type, int64_t n,
-                                                            const uint32_t* __restrict__ off,
-                                                            uint32_t* __restrict__ list) {
+__global__ void __launch_bounds__(CMP_THREADS) k_write_type(const uint8_t* __restrict__ type, int64_t n,
+                                                           uint8_t want, const uint32_t* __restrict__ off,
+                                                           uint32_t* __restrict__ list) {
   __shared__ uint32_t wsum[CMP_THREADS / 32];
   int64_t i = blockIdx.x * (int64_t)CMP_THREADS + threadIdx.x;
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  bool f = i < n && type[i] == kFluid;
+  bool f = i < n && type[i] == want;
   unsigned b = __ballot_sync(0xffffffffu, f);
   if (lane == 0) wsum[warp] = __popc(b);
   __syncthreads();
@@ -251,15 +257,21 @@ __global__ void __launch_bounds__(CMP_THREADS) k_write_fluid(const uint8_t* __re
   if (f) list[pos] = (uint32_t)i;
 }
 
-void launch_fluid_list(const State& s, const Work& w, int64_t n, int64_t nblocks_scan,
-                       cudaStream_t st, int* launches) {
+// Ordered lists of the sorted indices of fluid and of dummy particles.
+void launch_fluid_list(const State& s, const Work& w, int64_t n, int64_t nd, cudaStream_t st,
+                       int* launches) {
   if (n == 0) return;
   int64_t nb = div_up(n, CMP_THREADS);
-  (void)nblocks_scan;
-  k_count_fluid<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, w.block_cnt);
+  k_count_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kFluid, w.block_cnt);
   k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(w.block_cnt, nb);
-  k_write_fluid<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, w.block_cnt, w.fluid_list);
+  k_write_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kFluid, w.block_cnt, w.fluid_list);
   *launches += 3;
+  if (nd > 0 && w.dummy_list) {
+    k_count_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kDummy, w.block_cnt);
+    k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(w.block_cnt, nb);
+    k_write_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kDummy, w.block_cnt, w.dummy_list);
+    *launches += 3;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -1,92 +1,87 @@
 // pair_fp64.cu -- FP64 stage kernels of the well-balanced WCSPH step:
-// prepass (dummy wall update, volumes, U_max), time step, the fused pair pass
-// with its epilogue (Eq. sph with TIC, viscosity, delta-SPH and shifting),
-// the SSP-RK2 stage updates, and field output in the caller's order.
+// prepass (dummy wall update, volumes, U_max), time step, neighbour-list
+// build, the fused FP64 pair pass with its epilogue (Eq. sph with TIC,
+// viscosity, delta-SPH and shifting), the SSP-RK2 stage updates, and field
+// output in the caller's order.
 //
-// On GB300 the FP64 pipe (about 2 DFMA per clock per SM) bounds this path,
-// so the pair pass is split per warp into (A) an FP32/integer phase that
-// enumerates candidates of the 3^d cells and writes compact per-lane
-// neighbour lists to shared memory, and (B) an FP64 phase that walks those
-// lists with every lane busy. Lanes that would otherwise idle in FP64
-// instructions cost pipe cycles, so (B) never runs on candidate tests.
-#include <cstdio>
+// On GB300 the FP64 pipe (2 DFMA per clock per SM, 1/61 of FP32) bounds this
+// path. Candidate enumeration of the 3^d cells is therefore done by a
+// separate FP32/integer kernel that writes each fluid particle's candidate
+// list (k-major, coalesced); the FP64 kernel then walks these lists with
+// every lane busy and no shared memory, so more warps per SM cover the
+// latency of the gathers and of the FP64 pipe itself.
 #include "common.cuh"
 #include "neighbor_iter.cuh"
+#include "physics.cuh"
+#include "warp_scan.cuh"
 
 namespace wbsph {
 
-__device__ __forceinline__ double eos_density(const Params& p, double phi) {
-  if (p.eos == 0) return p.rho0 * exp(phi / p.c0sq);
-  double gm1 = p.gamma - 1.0;
-  return p.rho0 * pow(1.0 + gm1 * phi / p.c0sq, 1.0 / gm1);
-}
-
-// D(phi)/Dt = -c^2 div U: c^2 = C0^2 (linear EOS), c0^2 + (gamma - 1) phi (Tait).
-__device__ __forceinline__ double eos_c2(const Params& p, double phi) {
-  return p.eos == 0 ? p.c0sq : p.c0sq + (p.gamma - 1.0) * phi;
-}
-
-__device__ __forceinline__ void body_force(const Params& p, double t, double g[3]) {
-  double s = 0.0;
-  if (p.omega > 0.0) s = p.omega * p.omega * sin(p.omega * t);
-  for (int k = 0; k < 3; ++k) g[k] = p.g[k] + p.force_amp[k] * s;
-}
-
-__device__ __forceinline__ double stage_time(const Work& w, int stage2) {
-  return stage2 ? w.scalars[0] + w.scalars[1] : w.scalars[0];
-}
-
 // ---------------------------------------------------------------------------
-// Prepass, all particles. Dummy particles (Sec. 2.4): nearest fluid particle
-// f within 2h (exact FP64 squared distance; ties to the smaller original id),
-// phi_d = phi_f + G(t).(x_d - x_f) (Eq. phiBn), slip velocity
-// U_d = U_f - (U_f.n_d) n_d. Then V = m / rho(phi) for every particle and the
-// maximum |U|^2 over fluid particles (for the shifting velocity scale).
+// Prepass. (1) Dummy particles (Sec. 2.4), one lane per dummy: nearest fluid
+// particle f within 2h (exact FP64 squared distance; ties to the smaller
+// original id), phi_d = phi_f + G(t).(x_d - x_f) (Eq. phiBn), slip velocity
+// U_d = U_f - (U_f.n_d) n_d. A warp-staged FP32 scan evaluates the exact
+// FP64 distance only for candidates within a proven rounding band of the
+// running FP32 minimum. (2) V = m / rho(phi) for
+// every particle and max |U|^2 over fluid particles.
 // ---------------------------------------------------------------------------
+constexpr int DUM_THREADS = 128;
+
+__global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s, Work w, int64_t n,
+                                                             int64_t nd, int stage2) {
+  __shared__ float4 stage[DUM_THREADS / 32][32];
+  const int warp = threadIdx.x >> 5;
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool active = gi < nd;
+  const uint32_t i = active ? w.dummy_list[gi] : 0u;
+  const uint32_t key = active ? w.key[i] : 0u;
+  const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  // One scan: a candidate is evaluated exactly when its FP32 distance lies
+  // within the rounding band of the running FP32 minimum. A candidate skipped
+  // at some point lies outside the band of the final minimum too, so it
+  // cannot be the exact nearest.
+  float best_f = INFINITY;
+  uint32_t best = kEmpty, best_oid = kEmpty;
+  double best_r2 = 0.0;
+  warp_scan_candidates(p, w, active, i, key, xs, stage[warp], [&](uint32_t j, float r2f, float jtype) {
+    if (jtype != 0.f) return;  // fluid neighbours only
+    if (r2f > best_f + p.nearest_band_r2) return;
+    if (r2f < best_f) best_f = r2f;
+    double d0 = __dsub_rn(s.x[j], s.x[i]);
+    double r2 = __dmul_rn(d0, d0);
+    double d1 = __dsub_rn(s.x[n + j], s.x[n + i]);
+    r2 = __dadd_rn(r2, __dmul_rn(d1, d1));
+    if (p.dim == 3) {
+      double d2 = __dsub_rn(s.x[2 * n + j], s.x[2 * n + i]);
+      r2 = __dadd_rn(r2, __dmul_rn(d2, d2));
+    }
+    if (!(r2 <= p.four_h2 && r2 > 0.0)) return;
+    uint32_t o = s.oid[j];
+    if (best == kEmpty || r2 < best_r2 || (r2 == best_r2 && o < best_oid)) {
+      best = j; best_r2 = r2; best_oid = o;
+    }
+  });
+  if (!active || best == kEmpty) return;
+  double fs = forcing_factor(p, stage_time(w, stage2));
+  double gdot = 0.0, un = 0.0;
+  for (int k = 0; k < p.dim; ++k) {
+    gdot += (p.g[k] + p.force_amp[k] * fs) * (s.x[k * n + i] - s.x[k * n + best]);
+    un += s.u[k * n + best] * s.normal[k * n + i];
+  }
+  s.phi[i] = s.phi[best] + gdot;
+  for (int k = 0; k < p.dim; ++k) s.u[k * n + i] = s.u[k * n + best] - un * s.normal[k * n + i];
+}
+
 constexpr int PRE_THREADS = 256;
 
-__global__ void __launch_bounds__(PRE_THREADS) k_prepass(Params p, State s, Work w, int64_t n, int stage2) {
+__global__ void __launch_bounds__(PRE_THREADS) k_volumes_umax(Params p, State s, Work w, int64_t n) {
   __shared__ unsigned long long red[PRE_THREADS / 32];
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double umax2 = 0.0;
   if (i < n) {
-    int ty = s.type[i];
-    if (ty == kDummy) {
-      CandidateIter it;
-      it.init(p, w, n, (uint32_t)i);
-      uint32_t j, best = kEmpty, best_oid = kEmpty;
-      double best_r2 = 0.0;
-      while (it.next(p, w, j)) {
-        if (s.type[j] != kFluid) continue;
-        double d0 = __dsub_rn(s.x[j], s.x[i]);
-        double r2 = __dmul_rn(d0, d0);
-        double d1 = __dsub_rn(s.x[n + j], s.x[n + i]);
-        r2 = __dadd_rn(r2, __dmul_rn(d1, d1));
-        if (p.dim == 3) {
-          double d2 = __dsub_rn(s.x[2 * n + j], s.x[2 * n + i]);
-          r2 = __dadd_rn(r2, __dmul_rn(d2, d2));
-        }
-        if (!(r2 <= p.four_h2 && r2 > 0.0)) continue;
-        uint32_t o = s.oid[j];
-        if (best == kEmpty || r2 < best_r2 || (r2 == best_r2 && o < best_oid)) {
-          best = j; best_r2 = r2; best_oid = o;
-        }
-      }
-      if (best != kEmpty) {
-        double G[3];
-        body_force(p, stage_time(w, stage2), G);
-        double gdot = 0.0, un = 0.0;
-        for (int k = 0; k < p.dim; ++k) {
-          gdot += G[k] * (s.x[k * n + i] - s.x[k * n + best]);
-          un += s.u[k * n + best] * s.normal[k * n + i];
-        }
-        s.phi[i] = s.phi[best] + gdot;
-        for (int k = 0; k < p.dim; ++k)
-          s.u[k * n + i] = s.u[k * n + best] - un * s.normal[k * n + i];
-      }
-    } else {
+    if (s.type[i] == kFluid)
       for (int k = 0; k < p.dim; ++k) umax2 += s.u[k * n + i] * s.u[k * n + i];
-    }
     double v = s.mass[i] / eos_density(p, s.phi[i]);
     w.vol[i] = v;
     if (!isfinite(v)) atomicOr(w.status, kStatNaN);
@@ -107,11 +102,13 @@ __global__ void __launch_bounds__(PRE_THREADS) k_prepass(Params p, State s, Work
   }
 }
 
-void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int stage2,
-                    cudaStream_t st) {
+void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int64_t nd,
+                    int stage2, cudaStream_t st) {
   cudaMemsetAsync(w.umax_bits, 0, sizeof(unsigned long long), st);
   if (n == 0) return;
-  k_prepass<<<(unsigned)div_up(n, PRE_THREADS), PRE_THREADS, 0, st>>>(p, s, w, n, stage2);
+  if (nd > 0)
+    k_dummy_update<<<(unsigned)div_up(nd, DUM_THREADS), DUM_THREADS, 0, st>>>(p, s, w, n, nd, stage2);
+  k_volumes_umax<<<(unsigned)div_up(n, PRE_THREADS), PRE_THREADS, 0, st>>>(p, s, w, n);
 }
 
 // Time step (Sec. 2.3): CFL * min(dx/(C0 + U_max), dx^2/(2 nu), sqrt(2 dx/|G|)).
@@ -142,45 +139,44 @@ void launch_time_step(const Params& p, const Work& w, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Closed-form smallest eigenvalue of the symmetric renormalisation matrix
-// (Sec. 3). 2D: mean - sqrt(half-difference^2 + off^2). 3D: trigonometric
-// root of the characteristic cubic (Smith, CACM 1961).
+// Candidate lists: for fluid particle gi (sorted index fluid_list[gi]), every
+// j whose FP32 distance passes the conservative prefilter, in Algorithm 1
+// order, stored k-major: nbr[k * nf + gi]. Lists are staged per warp in
+// shared memory so the global stores are coalesced rows.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double lambda_min_2(double a, double b, double c) {
-  double m = 0.5 * (a + c), d = 0.5 * (a - c);
-  return m - sqrt(d * d + b * b);
-}
+constexpr int LIST_THREADS = 64;
 
-__device__ __forceinline__ double lambda_min_3(double a00, double a01, double a02, double a11,
-                                               double a12, double a22) {
-  double off = a01 * a01 + a02 * a02 + a12 * a12;
-  if (off == 0.0) return fmin(fmin(a00, a11), a22);
-  double mean = (a00 + a11 + a22) * (1.0 / 3.0);
-  double b00 = a00 - mean, b11 = a11 - mean, b22 = a22 - mean;
-  double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * off;
-  double pp = sqrt(p2 * (1.0 / 6.0));
-  double det = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) +
-               a02 * (a01 * a12 - b11 * a02);
-  double r = det / (2.0 * pp * pp * pp);
-  r = fmin(1.0, fmax(-1.0, r));
-  double ang = acos(r) * (1.0 / 3.0);
-  return mean + 2.0 * pp * cos(ang + 2.0943951023931954923);  // 2 pi / 3
-}
-
-// Reciprocal square root: FP32 estimate refined by two Newton-Raphson steps
-// y <- y (3 - r2 y^2) / 2 in FP64 (each step roughly doubles the correct
-// bits: ~23 -> ~46 -> full double precision).
-__device__ __forceinline__ double rsqrt_nr(double r2) {
-  double y = (double)rsqrtf((float)r2);
-  double hy = 0.5 * y;
-  y = fma(hy, fma(-r2 * y, y, 1.0), y);
-  hy = 0.5 * y;
-  y = fma(hy, fma(-r2 * y, y, 1.0), y);
-  return y;
+__global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, Work w, int64_t n, int64_t nf,
+                                                         int kmax) {
+  extern __shared__ float4 smem_f4[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4* stage = smem_f4 + warp * 32;
+  uint32_t* my = reinterpret_cast<uint32_t*>(smem_f4 + (LIST_THREADS / 32) * 32) + warp * kmax * 32;
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool active = gi < nf;
+  const uint32_t i = active ? w.fluid_list[gi] : 0u;
+  const uint32_t key = active ? w.key[i] : 0u;
+  const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  int cnt = 0;
+  warp_scan_candidates(p, w, active, i, key, xs, stage, [&](uint32_t j, float, float) {
+    if (cnt < kmax) my[cnt * 32 + lane] = j;
+    ++cnt;
+  });
+  if (active) {
+    if (cnt > kmax) {
+      atomicOr(w.status, kStatOverflow);
+      cnt = kmax;
+    }
+    w.nbr_cnt[gi] = (uint32_t)cnt;
+  }
+  __syncwarp();
+  int maxc = __reduce_max_sync(0xffffffffu, cnt);
+  for (int k = 0; k < maxc; ++k)
+    if (k < cnt) w.nbr[(int64_t)k * nf + gi] = my[k * 32 + lane];
 }
 
 // ---------------------------------------------------------------------------
-// Fused pair pass over fluid particles (one lane per particle i).
+// Fused FP64 pair pass over fluid particles (one lane per particle i).
 // Accumulated with g = -W'(r)/r V_j >= 0, so grad_i W_ij V_j = g r (r = x_j - x_i):
 //   L  += r (x) g r                       (Eq. renorm; symmetric)
 //   S  += [phi_j - phi_i - C0 (U_j - U_i).r/|r|] g r      (2(phi* - phi_i), Eq. lfsover)
@@ -190,26 +186,23 @@ __device__ __forceinline__ double rsqrt_nr(double r2) {
 //   Lam+= (U_j - U_i) g, fluid j only     (Laplacian operator, Sec. 2.1/2.4)
 //   P  += [1 + R (W_ij / W(dx))^n] g r    (shifting)
 // ---------------------------------------------------------------------------
-template <int DIM>
-struct PairAcc {
-  double L[6], S[DIM], M[DIM * DIM], C[DIM], D, Lam[DIM], P[DIM];
-};
-
 constexpr int PAIR_THREADS = 128;
 
-template <int DIM>
-__host__ __device__ constexpr int pair_kcap() { return DIM == 3 ? 96 : 40; }
+// Reciprocal square root: FP32 estimate refined by one Newton-Raphson step
+// y <- y (3 - r2 y^2) / 2 in FP64, relative error about 1e-13 (the step
+// squares the ~2e-7 error of the estimate).
+__device__ __forceinline__ double rsqrt_nr1(double r2) {
+  double y = (double)rsqrtf((float)r2);
+  return fma(0.5 * y, fma(-r2 * y, y, 1.0), y);
+}
 
 template <int DIM>
-__global__ void __launch_bounds__(PAIR_THREADS, 3)
+__global__ void __launch_bounds__(PAIR_THREADS, 4)
     k_pair_fp64(Params p, State s, Work w, int64_t n, int64_t nf, int stage2) {
-  constexpr int KCAP = pair_kcap<DIM>();
-  extern __shared__ uint32_t lists[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* my = lists + warp * KCAP * 32;
-  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool active = gi < nf;
   const uint32_t i = active ? w.fluid_list[gi] : 0u;
+  const int cnt = active ? (int)w.nbr_cnt[gi] : 0;
 
   double xi[DIM], ui[DIM], phii = 0.0;
 #pragma unroll
@@ -219,182 +212,120 @@ __global__ void __launch_bounds__(PAIR_THREADS, 3)
   }
   if (active) phii = s.phi[i];
 
-  PairAcc<DIM> a;
+  double L[6] = {0, 0, 0, 0, 0, 0}, S[DIM], M[DIM * DIM], C[DIM], Lam[DIM], P[DIM], D = 0.0;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) a.L[k] = 0.0;
+  for (int k = 0; k < DIM; ++k) { S[k] = C[k] = Lam[k] = P[k] = 0.0; }
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) { a.S[k] = a.C[k] = a.Lam[k] = a.P[k] = 0.0; }
-#pragma unroll
-  for (int k = 0; k < DIM * DIM; ++k) a.M[k] = 0.0;
-  a.D = 0.0;
+  for (int k = 0; k < DIM * DIM; ++k) M[k] = 0.0;
 
   const bool pst4 = p.use_pst && p.pst_n == 4.0;
   unsigned npairs = 0;
-  CandidateIter it;
-  bool done = !active;
-  if (active) it.init(p, w, n, i);
-
-  while (__any_sync(0xffffffffu, !done)) {
-    // (A) candidate enumeration, FP32 prefilter, compact list
-    int cnt = 0;
-    while (!done && cnt < KCAP) {
-      uint32_t j;
-      if (it.next(p, w, j)) my[cnt++ * 32 + lane] = j;
-      else done = true;
+  const int maxc = __reduce_max_sync(0xffffffffu, cnt);
+  const uint32_t* lst = w.nbr + gi;
+  for (int k = 0; k < maxc; ++k) {
+    if (k >= cnt) continue;
+    uint32_t j = __ldg(lst + (int64_t)k * nf);
+    double r[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) r[c] = __dsub_rn(s.x[c * n + j], xi[c]);
+    double r2 = __dmul_rn(r[0], r[0]);
+#pragma unroll
+    for (int c = 1; c < DIM; ++c) r2 = __dadd_rn(r2, __dmul_rn(r[c], r[c]));
+    if (!(r2 <= p.four_h2 && r2 > 0.0)) continue;
+    ++npairs;
+    double inv_r = rsqrt_nr1(r2);
+    double rr = r2 * inv_r;
+    double t = fma(-rr, p.inv_two_h, 1.0);
+    double t3 = t * t * t;
+    double g = p.neg_dwdr_over_r_coef * t3 * w.vol[j];
+    double gr[DIM], du[DIM];
+    double dun = 0.0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      gr[c] = g * r[c];
+      du[c] = s.u[c * n + j] - ui[c];
+      dun = fma(du[c], r[c], dun);
     }
-    __syncwarp();
-    int maxc = __reduce_max_sync(0xffffffffu, cnt);
-    // (B) FP64 pair terms
-    for (int k = 0; k < maxc; ++k) {
-      if (k >= cnt) continue;
-      uint32_t j = my[k * 32 + lane];
-      double r[DIM];
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) r[c] = __dsub_rn(s.x[c * n + j], xi[c]);
-      double r2 = __dmul_rn(r[0], r[0]);
-#pragma unroll
-      for (int c = 1; c < DIM; ++c) r2 = __dadd_rn(r2, __dmul_rn(r[c], r[c]));
-      if (!(r2 <= p.four_h2 && r2 > 0.0)) continue;
-      ++npairs;
-      double inv_r = rsqrt_nr(r2);
-      double rr = r2 * inv_r;
-      double t = fma(-rr, p.inv_two_h, 1.0);
-      double t3 = t * t * t;
-      double g = p.neg_dwdr_over_r_coef * t3 * w.vol[j];
-      double gr[DIM], du[DIM];
-      double dun = 0.0;
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        gr[c] = g * r[c];
-        du[c] = s.u[c * n + j] - ui[c];
-        dun = fma(du[c], r[c], dun);
-      }
-      dun *= inv_r;
-      double phij = s.phi[j];
-      double dphi = phij - phii;
-      double sphi = phij + phii;
-      double rs = fma(-p.c0, dun, dphi);
-      // L (upper triangle, row-major order 00 01 [02] 11 [12 22])
-      if (DIM == 2) {
-        a.L[0] = fma(r[0], gr[0], a.L[0]);
-        a.L[1] = fma(r[0], gr[1], a.L[1]);
-        a.L[2] = fma(r[1], gr[1], a.L[2]);
-      } else {
-        a.L[0] = fma(r[0], gr[0], a.L[0]);
-        a.L[1] = fma(r[0], gr[1], a.L[1]);
-        a.L[2] = fma(r[0], gr[2], a.L[2]);
-        a.L[3] = fma(r[1], gr[1], a.L[3]);
-        a.L[4] = fma(r[1], gr[2], a.L[4]);
-        a.L[5] = fma(r[2], gr[2], a.L[5]);
-      }
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        a.S[c] = fma(rs, gr[c], a.S[c]);
-        a.C[c] = fma(sphi, gr[c], a.C[c]);
-#pragma unroll
-        for (int e = 0; e < DIM; ++e) a.M[c * DIM + e] = fma(du[c], gr[e], a.M[c * DIM + e]);
-      }
-      a.D = fma(dphi, g, a.D);
-      if (s.type[j] == kFluid) {
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) a.Lam[c] = fma(du[c], g, a.Lam[c]);
-      }
-      if (p.use_pst) {
-        double q21 = fma(rr, p.two_over_h, 1.0);           // 2q + 1
-        double ratio = p.pst_alpha_over_wdx * (t3 * t) * q21;  // W_ij / W(dx)
-        double rn = pst4 ? (ratio * ratio) * (ratio * ratio) : pow(ratio, p.pst_n);
-        double f = fma(p.pst_R, rn, 1.0);
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) a.P[c] = fma(f, gr[c], a.P[c]);
-      }
+    dun *= inv_r;
+    double phij = s.phi[j];
+    double dphi = phij - phii;
+    double sphi = phij + phii;
+    double rs = fma(-p.c0, dun, dphi);
+    if (DIM == 2) {
+      L[0] = fma(r[0], gr[0], L[0]);
+      L[1] = fma(r[0], gr[1], L[1]);
+      L[2] = fma(r[1], gr[1], L[2]);
+    } else {
+      L[0] = fma(r[0], gr[0], L[0]);
+      L[1] = fma(r[0], gr[1], L[1]);
+      L[2] = fma(r[0], gr[DIM - 1], L[2]);
+      L[3] = fma(r[1], gr[1], L[3]);
+      L[4] = fma(r[1], gr[DIM - 1], L[4]);
+      L[5] = fma(r[DIM - 1], gr[DIM - 1], L[5]);
     }
-    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      S[c] = fma(rs, gr[c], S[c]);
+      C[c] = fma(sphi, gr[c], C[c]);
+#pragma unroll
+      for (int e = 0; e < DIM; ++e) M[c * DIM + e] = fma(du[c], gr[e], M[c * DIM + e]);
+    }
+    D = fma(dphi, g, D);
+    if (s.type[j] == kFluid) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) Lam[c] = fma(du[c], g, Lam[c]);
+    }
+    if (p.use_pst) {
+      double q21 = fma(rr, p.two_over_h, 1.0);               // 2q + 1
+      double ratio = p.pst_alpha_over_wdx * (t3 * t) * q21;  // W_ij / W(dx)
+      double rn = pst4 ? (ratio * ratio) * (ratio * ratio) : pow(ratio, p.pst_n);
+      double f = fma(p.pst_R, rn, 1.0);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) P[c] = fma(f, gr[c], P[c]);
+    }
   }
+  const int lane = threadIdx.x & 31;
   unsigned wp = __reduce_add_sync(0xffffffffu, npairs);
   if (lane == 0 && wp) atomicAdd(w.pairs, (unsigned long long)wp);
   if (!active) return;
 
-  // ---- epilogue (Eq. sph with the TIC switch, K8/K9 of Sec. 3) ----
-  double Lf[3][3];
-  if (DIM == 2) {
-    Lf[0][0] = a.L[0]; Lf[0][1] = Lf[1][0] = a.L[1]; Lf[1][1] = a.L[2];
-  } else {
-    Lf[0][0] = a.L[0]; Lf[0][1] = Lf[1][0] = a.L[1]; Lf[0][2] = Lf[2][0] = a.L[2];
-    Lf[1][1] = a.L[3]; Lf[1][2] = Lf[2][1] = a.L[4]; Lf[2][2] = a.L[5];
-  }
-  double lam = DIM == 2 ? lambda_min_2(Lf[0][0], Lf[0][1], Lf[1][1])
-                        : lambda_min_3(Lf[0][0], Lf[0][1], Lf[0][2], Lf[1][1], Lf[1][2], Lf[2][2]);
+  // ---- epilogue (Eq. sph with the TIC switch; Sec. 3: correction outside the sum) ----
+  double lam = DIM == 2 ? lambda_min_2(L[0], L[1], L[2]) : lambda_min_3(L[0], L[1], L[2], L[3], L[4], L[5]);
   double gradphi[DIM], divu = 0.0;
   if (p.use_tic && lam < p.tic_lambda) {
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-      gradphi[c] = a.C[c];
-      divu += a.M[c * DIM + c];
+      gradphi[c] = C[c];
+      divu += M[c * DIM + c];
     }
   } else {
-    double inv[DIM][DIM], det, amax = 0.0;
-#pragma unroll
-    for (int c = 0; c < DIM; ++c)
-#pragma unroll
-      for (int e = 0; e < DIM; ++e) amax = fmax(amax, fabs(Lf[c][e]));
-    if (DIM == 2) {
-      det = Lf[0][0] * Lf[1][1] - Lf[0][1] * Lf[1][0];
-      double id = 1.0 / det;
-      inv[0][0] = Lf[1][1] * id; inv[1][1] = Lf[0][0] * id;
-      inv[0][1] = -Lf[0][1] * id; inv[1][0] = -Lf[1][0] * id;
-    } else {
-      double c00 = Lf[1][1] * Lf[2][2] - Lf[1][2] * Lf[2][1];
-      double c01 = Lf[1][2] * Lf[2][0] - Lf[1][0] * Lf[2][2];
-      double c02 = Lf[1][0] * Lf[2][1] - Lf[1][1] * Lf[2][0];
-      det = Lf[0][0] * c00 + Lf[0][1] * c01 + Lf[0][2] * c02;
-      double id = 1.0 / det;
-      double m[3][3];
-      m[0][0] = c00; m[1][0] = c01; m[2][0] = c02;
-      m[0][1] = Lf[0][2] * Lf[2][1] - Lf[0][1] * Lf[2][2];
-      m[1][1] = Lf[0][0] * Lf[2][2] - Lf[0][2] * Lf[2][0];
-      m[2][1] = Lf[0][1] * Lf[2][0] - Lf[0][0] * Lf[2][1];
-      m[0][2] = Lf[0][1] * Lf[1][2] - Lf[0][2] * Lf[1][1];
-      m[1][2] = Lf[0][2] * Lf[1][0] - Lf[0][0] * Lf[1][2];
-      m[2][2] = Lf[0][0] * Lf[1][1] - Lf[0][1] * Lf[1][0];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int e = 0; e < 3; ++e) inv[c][e] = m[c][e] * id;
-    }
-    double amd = DIM == 2 ? amax * amax : amax * amax * amax;
-    if (!(fabs(det) > 1e-12 * amd)) {
-      atomicOr(w.status, kStatSingular);
-#pragma unroll
-      for (int c = 0; c < DIM; ++c)
-#pragma unroll
-        for (int e = 0; e < DIM; ++e) inv[c][e] = 0.0;
-    }
+    double inv[DIM][DIM];
+    if (!sym_inverse<DIM>(L, inv)) atomicOr(w.status, kStatSingular);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       double gsum = 0.0;
 #pragma unroll
       for (int e = 0; e < DIM; ++e) {
-        gsum = fma(inv[c][e], a.S[e], gsum);
-        divu = fma(inv[c][e], a.M[c * DIM + e], divu);
+        gsum = fma(inv[c][e], S[e], gsum);
+        divu = fma(inv[c][e], M[c * DIM + e], divu);
       }
       gradphi[c] = gsum;
     }
   }
-  double G[3];
-  body_force(p, stage_time(w, stage2), G);
+  double fs = forcing_factor(p, stage_time(w, stage2));
   double umax = sqrt(__longlong_as_double((long long)*w.umax_bits));
   bool bad = false;
   double dstar[DIM], dn2 = 0.0;
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
-    double visc = p.use_visc ? 2.0 * p.nu * a.Lam[c] : 0.0;
-    double acc = -gradphi[c] + visc + G[c];
+    double visc = p.use_visc ? 2.0 * p.nu * Lam[c] : 0.0;
+    double acc = -gradphi[c] + visc + (p.g[c] + p.force_amp[c] * fs);
     w.dudt[c * n + i] = acc;
     bad |= !isfinite(acc);
-    dstar[c] = -2.0 * p.h * umax * a.P[c];
+    dstar[c] = -2.0 * p.h * umax * P[c];
     dn2 += dstar[c] * dstar[c];
   }
-  double diff = p.use_delta ? p.delta_h_c0 * (2.0 * a.D) : 0.0;
+  double diff = p.use_delta ? p.delta_h_c0 * (2.0 * D) : 0.0;
   double dphidt = -eos_c2(p, phii) * divu + diff;
   w.dphidt[i] = dphidt;
   bad |= !isfinite(dphidt);
@@ -411,22 +342,27 @@ __global__ void __launch_bounds__(PAIR_THREADS, 3)
   if (bad) atomicOr(w.status, kStatNaN);
 }
 
+int pair_list_kmax(int dim) { return dim == 3 ? 128 : 48; }
+
+void launch_nbr_list(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st) {
+  if (nf == 0) return;
+  int kmax = pair_list_kmax(p.dim);
+  size_t sm = (size_t)kmax * 32 * (LIST_THREADS / 32) * sizeof(uint32_t) +
+              (LIST_THREADS / 32) * 32 * sizeof(float4);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_nbr_list, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    attr = true;
+  }
+  k_nbr_list<<<(unsigned)div_up(nf, LIST_THREADS), LIST_THREADS, sm, st>>>(p, w, n, nf, kmax);
+}
+
 void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
                       int stage2, cudaStream_t st) {
   if (nf == 0) return;
   unsigned blocks = (unsigned)div_up(nf, PAIR_THREADS);
-  if (p.dim == 2) {
-    size_t sm = (size_t)pair_kcap<2>() * 32 * (PAIR_THREADS / 32) * sizeof(uint32_t);
-    k_pair_fp64<2><<<blocks, PAIR_THREADS, sm, st>>>(p, s, w, n, nf, stage2);
-  } else {
-    size_t sm = (size_t)pair_kcap<3>() * 32 * (PAIR_THREADS / 32) * sizeof(uint32_t);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_pair_fp64<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-    }
-    k_pair_fp64<3><<<blocks, PAIR_THREADS, sm, st>>>(p, s, w, n, nf, stage2);
-  }
+  if (p.dim == 2) k_pair_fp64<2><<<blocks, PAIR_THREADS, 0, st>>>(p, s, w, n, nf, stage2);
+  else k_pair_fp64<3><<<blocks, PAIR_THREADS, 0, st>>>(p, s, w, n, nf, stage2);
 }
 
 // ---------------------------------------------------------------------------

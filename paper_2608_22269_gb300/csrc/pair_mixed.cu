@@ -17,28 +17,9 @@
 // The state (x, U, phi) stays FP64; only the pair sums run in FP32.
 #include "../../include/wbsph.h"
 #include "common.cuh"
+#include "physics.cuh"
 
 namespace wbsph {
-
-// ---- helpers (FP64 epilogue) ----
-__device__ __forceinline__ double mx_lambda_min_2(double a, double b, double c) {
-  double m = 0.5 * (a + c), d = 0.5 * (a - c);
-  return m - sqrt(d * d + b * b);
-}
-
-__device__ __forceinline__ double mx_lambda_min_3(double a00, double a01, double a02, double a11,
-                                                  double a12, double a22) {
-  double off = a01 * a01 + a02 * a02 + a12 * a12;
-  if (off == 0.0) return fmin(fmin(a00, a11), a22);
-  double mean = (a00 + a11 + a22) * (1.0 / 3.0);
-  double b00 = a00 - mean, b11 = a11 - mean, b22 = a22 - mean;
-  double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * off;
-  double pp = sqrt(p2 * (1.0 / 6.0));
-  double det = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) +
-               a02 * (a01 * a12 - b11 * a02);
-  double r = fmin(1.0, fmax(-1.0, det / (2.0 * pp * pp * pp)));
-  return mean + 2.0 * pp * cos(acos(r) * (1.0 / 3.0) + 2.0943951023931954923);
-}
 
 // Kahan-compensated FP32 accumulator: s + (-c) carries the running sum.
 struct Kahan {
@@ -53,10 +34,12 @@ struct Kahan {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// ---- pack: cell-relative FP32 offsets, phi', U, signed V ----
+// ---- pack: cell-relative FP32 offsets, phi', U, signed V, packed cell ----
 // A[i] = (x - cell origin, phi - phi_hs(x)), B[i] = (U, V) with V < 0 marking
-// dummy particles (the Laplacian operator takes fluid neighbours only).
-__global__ void k_pack_mixed(Params p, State s, Work w, int64_t n, float4* A, float4* B) {
+// dummy particles (the Laplacian operator takes fluid neighbours only),
+// C[i] = cell coordinates packed 11/11/10 bits.
+__global__ void k_pack_mixed(Params p, State s, Work w, int64_t n, float4* A, float4* B,
+                             uint32_t* Cc) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t key = w.key[i];
@@ -78,24 +61,35 @@ __global__ void k_pack_mixed(Params p, State s, Work w, int64_t n, float4* A, fl
   if (s.type[i] != kFluid) v = -v;
   A[i] = make_float4(o[0], o[1], o[2], phip);
   B[i] = make_float4(u[0], u[1], u[2], v);
+  Cc[i] = ic[0] | (ic[1] << 11) | (ic[2] << 22);
+}
+
+__device__ __forceinline__ float lambda_min_3f(float a00, float a01, float a02, float a11, float a12,
+                                               float a22) {
+  float off = a01 * a01 + a02 * a02 + a12 * a12;
+  if (off == 0.f) return fminf(fminf(a00, a11), a22);
+  float mean = (a00 + a11 + a22) * (1.f / 3.f);
+  float b00 = a00 - mean, b11 = a11 - mean, b22 = a22 - mean;
+  float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.f * off;
+  float pp = sqrtf(p2 * (1.f / 6.f));
+  float det = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) + a02 * (a01 * a12 - b11 * a02);
+  float r = fminf(1.f, fmaxf(-1.f, det / (2.f * pp * pp * pp)));
+  return mean + 2.f * pp * cosf(acosf(r) * (1.f / 3.f) + 2.09439510f);
 }
 
 constexpr int MX_THREADS = 128;
 
+// Pair sums over the candidate lists built by k_nbr_list (the same lists as
+// the FP64 pass); the neighbour test is the FP32 cell-relative distance.
 template <int DIM>
-__host__ __device__ constexpr int mx_kcap() { return DIM == 3 ? 96 : 40; }
-
-template <int DIM>
-__global__ void __launch_bounds__(MX_THREADS, 3)
+__global__ void __launch_bounds__(MX_THREADS, 4)
     k_pair_mixed(Params p, State s, Work w, int64_t n, int64_t nf, int stage2, const float4* __restrict__ A,
-                 const float4* __restrict__ B) {
-  constexpr int KCAP = mx_kcap<DIM>();
-  extern __shared__ uint32_t lists[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* my = lists + warp * KCAP * 32;
+                 const float4* __restrict__ B, const uint32_t* __restrict__ Cc) {
+  const int lane = threadIdx.x & 31;
   int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool active = gi < nf;
   const uint32_t i = active ? w.fluid_list[gi] : 0u;
+  const int cnt = active ? (int)w.nbr_cnt[gi] : 0;
   const float R = (float)p.R;
   const float four_h2 = (float)p.four_h2;
   const float inv_two_h = (float)p.inv_two_h;
@@ -106,212 +100,134 @@ __global__ void __launch_bounds__(MX_THREADS, 3)
   const float pst_R = (float)p.pst_R;
 
   float4 Ai = make_float4(0.f, 0.f, 0.f, 0.f), Bi = Ai;
-  int ix = 0, iy = 0, iz = 0;
-  if (active) {
-    Ai = A[i];
-    Bi = B[i];
-    uint32_t key = w.key[i];
-    uint32_t nx = (uint32_t)p.nc[0], ny = (uint32_t)p.nc[1];
-    ix = (int)(key % nx);
-    iy = (int)((key / nx) % ny);
-    iz = (int)(key / (nx * ny));
-  }
-  Kahan L[6], S[DIM], M[DIM * DIM], Cc[DIM], K[DIM], D, Lam[DIM], P[DIM];
+  uint32_t ci = 0;
+  if (active) { Ai = A[i]; Bi = B[i]; ci = Cc[i]; }
+  const int cix = (int)(ci & 2047u), ciy = (int)((ci >> 11) & 2047u), ciz = (int)(ci >> 22);
+  Kahan L[6], S[DIM], M[DIM * DIM], Cs[DIM], K[DIM], D, Lam[DIM], P[DIM];
 #pragma unroll
   for (int k = 0; k < 6; ++k) L[k].zero();
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) { S[k].zero(); Cc[k].zero(); K[k].zero(); Lam[k].zero(); P[k].zero(); }
+  for (int k = 0; k < DIM; ++k) { S[k].zero(); Cs[k].zero(); K[k].zero(); Lam[k].zero(); P[k].zero(); }
 #pragma unroll
   for (int k = 0; k < DIM * DIM; ++k) M[k].zero();
   D.zero();
-
-  // row iterator state (phase A)
-  const int nrows = DIM == 3 ? 9 : 3;
-  int row = active ? 0 : nrows;
-  uint32_t cur = 0, end = 0, b0 = 0, b1 = 0;
-  int oy = 0, oz = 0;
-  bool have_row = false;
   unsigned npairs = 0;
-
-  while (__any_sync(0xffffffffu, row < nrows || have_row)) {
-    int cnt = 0;
-    // (A) candidates of the 3^d cells: FP32 cell-relative distance test
-    while (cnt < KCAP && (row < nrows || have_row)) {
-      if (!have_row) {
-        oy = row % 3 - 1;
-        oz = DIM == 3 ? row / 3 - 1 : 0;
-        ++row;
-        int cy = iy + oy, cz = iz + oz;
-        if (cy < 0 || cy >= p.nc[1] || cz < 0 || cz >= p.nc[2]) continue;
-        int x0 = ix > 0 ? ix - 1 : 0;
-        int x1 = ix + 1 < p.nc[0] ? ix + 1 : p.nc[0] - 1;
-        int64_t base = (int64_t)cy * p.nc[0] + (int64_t)cz * p.nc[0] * p.nc[1];
-        cur = w.cell_lb[base + x0];
-        end = w.cell_lb[base + x1 + 1];
-        b0 = w.cell_lb[base + ix];
-        b1 = w.cell_lb[base + ix + 1];
-        have_row = cur < end;
-        continue;
-      }
-      uint32_t j = cur++;
-      if (cur >= end) have_row = false;
-      if (j == i) continue;
-      int dcx = (j >= b0) + (j >= b1) - 1;
-      float4 Aj = A[j];
-      float rx = fmaf((float)dcx, R, Aj.x - Ai.x);
-      float ry = fmaf((float)oy, R, Aj.y - Ai.y);
-      float r2 = rx * rx + ry * ry;
-      if (DIM == 3) {
-        float rz = fmaf((float)oz, R, Aj.z - Ai.z);
-        r2 += rz * rz;
-      }
-      if (r2 <= four_h2 && r2 > 0.f) {
-        uint32_t code = (uint32_t)((dcx + 1) + 3 * (oy + 1) + 9 * (oz + 1));
-        my[cnt++ * 32 + lane] = (j << 5) | code;
-      }
+  const int maxc = __reduce_max_sync(0xffffffffu, cnt);
+  const uint32_t* lst = w.nbr + gi;
+  for (int k = 0; k < maxc; ++k) {
+    if (k >= cnt) continue;
+    uint32_t j = __ldg(lst + (int64_t)k * nf);
+    float4 Aj = A[j], Bj = B[j];
+    uint32_t cj = Cc[j];
+    float r[DIM], du[DIM];
+    r[0] = fmaf((float)((int)(cj & 2047u) - cix), R, Aj.x - Ai.x);
+    r[1] = fmaf((float)((int)((cj >> 11) & 2047u) - ciy), R, Aj.y - Ai.y);
+    if (DIM == 3) r[DIM - 1] = fmaf((float)((int)(cj >> 22) - ciz), R, Aj.z - Ai.z);
+    float r2 = 0.f, dun = 0.f;
+    du[0] = Bj.x - Bi.x;
+    du[1] = Bj.y - Bi.y;
+    if (DIM == 3) du[DIM - 1] = Bj.z - Bi.z;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) { r2 = fmaf(r[c], r[c], r2); dun = fmaf(du[c], r[c], dun); }
+    if (!(r2 <= four_h2 && r2 > 0.f)) continue;
+    ++npairs;
+    float inv_r = rsqrtf(r2);
+    float rr = r2 * inv_r;
+    float t = fmaf(-rr, inv_two_h, 1.f);
+    float t3 = t * t * t;
+    float g = coef * t3 * fabsf(Bj.w);
+    dun *= inv_r;
+    float dphi = Aj.w - Ai.w, sphi = Aj.w + Ai.w;
+    float rs = fmaf(-c0, dun, dphi);
+    float gr[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) gr[c] = g * r[c];
+    if (DIM == 2) {
+      L[0].add(r[0] * gr[0]); L[1].add(r[0] * gr[1]); L[2].add(r[1] * gr[1]);
+    } else {
+      L[0].add(r[0] * gr[0]); L[1].add(r[0] * gr[1]); L[2].add(r[0] * gr[DIM - 1]);
+      L[3].add(r[1] * gr[1]); L[4].add(r[1] * gr[DIM - 1]); L[5].add(r[DIM - 1] * gr[DIM - 1]);
     }
-    __syncwarp();
-    int maxc = __reduce_max_sync(0xffffffffu, cnt);
-    // (B) FP32 pair terms with compensated sums
-    for (int k = 0; k < maxc; ++k) {
-      if (k >= cnt) continue;
-      uint32_t e = my[k * 32 + lane];
-      uint32_t j = e >> 5, code = e & 31u;
-      int dc[3] = {(int)(code % 3) - 1, (int)((code / 3) % 3) - 1, (int)(code / 9) - 1};
-      float4 Aj = A[j], Bj = B[j];
-      float r[DIM], du[DIM];
-      r[0] = fmaf((float)dc[0], R, Aj.x - Ai.x);
-      r[1] = fmaf((float)dc[1], R, Aj.y - Ai.y);
-      if (DIM == 3) r[DIM - 1] = fmaf((float)dc[2], R, Aj.z - Ai.z);
-      du[0] = Bj.x - Bi.x;
-      du[1] = Bj.y - Bi.y;
-      if (DIM == 3) du[DIM - 1] = Bj.z - Bi.z;
-      float r2 = 0.f, dun = 0.f;
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) { r2 = fmaf(r[c], r[c], r2); dun = fmaf(du[c], r[c], dun); }
-      ++npairs;
-      float inv_r = rsqrtf(r2);
-      float rr = r2 * inv_r;
-      float t = fmaf(-rr, inv_two_h, 1.f);
-      float t3 = t * t * t;
-      float vj = fabsf(Bj.w);
-      float g = coef * t3 * vj;
-      dun *= inv_r;
-      float dphi = Aj.w - Ai.w, sphi = Aj.w + Ai.w;
-      float rs = fmaf(-c0, dun, dphi);
-      float gr[DIM];
+    for (int c = 0; c < DIM; ++c) {
+      S[c].add(rs * gr[c]);
+      Cs[c].add(sphi * gr[c]);
+      K[c].add(gr[c]);
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) gr[c] = g * r[c];
-      if (DIM == 2) {
-        L[0].add(r[0] * gr[0]); L[1].add(r[0] * gr[1]); L[2].add(r[1] * gr[1]);
-      } else {
-        L[0].add(r[0] * gr[0]); L[1].add(r[0] * gr[1]); L[2].add(r[0] * gr[DIM - 1]);
-        L[3].add(r[1] * gr[1]); L[4].add(r[1] * gr[DIM - 1]); L[5].add(r[DIM - 1] * gr[DIM - 1]);
-      }
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        S[c].add(rs * gr[c]);
-        Cc[c].add(sphi * gr[c]);
-        K[c].add(gr[c]);
-#pragma unroll
-        for (int d2 = 0; d2 < DIM; ++d2) M[c * DIM + d2].add(du[c] * gr[d2]);
-      }
-      D.add(dphi * g);
-      if (Bj.w > 0.f) {
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) Lam[c].add(du[c] * g);
-      }
-      if (p.use_pst) {
-        float q21 = fmaf(rr, two_over_h, 1.f);
-        float ratio = pst_a * (t3 * t) * q21;
-        float r4 = (ratio * ratio) * (ratio * ratio);
-        float f = fmaf(pst_R, r4, 1.f);
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) P[c].add(f * gr[c]);
-      }
+      for (int d2 = 0; d2 < DIM; ++d2) M[c * DIM + d2].add(du[c] * gr[d2]);
     }
-    __syncwarp();
+    D.add(dphi * g);
+    if (Bj.w > 0.f) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) Lam[c].add(du[c] * g);
+    }
+    if (p.use_pst) {
+      float q21 = fmaf(rr, two_over_h, 1.f);
+      float ratio = pst_a * (t3 * t) * q21;
+      float r4 = (ratio * ratio) * (ratio * ratio);
+      float f = fmaf(pst_R, r4, 1.f);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) P[c].add(f * gr[c]);
+    }
   }
   unsigned wp = __reduce_add_sync(0xffffffffu, npairs);
   if (lane == 0 && wp) atomicAdd(w.pairs, (unsigned long long)wp);
   if (!active) return;
 
-  // ---- FP64 epilogue ----
-  double Lf[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  if (DIM == 2) {
-    Lf[0][0] = L[0].value(); Lf[0][1] = Lf[1][0] = L[1].value(); Lf[1][1] = L[2].value();
-  } else {
-    Lf[0][0] = L[0].value(); Lf[0][1] = Lf[1][0] = L[1].value(); Lf[0][2] = Lf[2][0] = L[2].value();
-    Lf[1][1] = L[3].value(); Lf[1][2] = Lf[2][1] = L[4].value(); Lf[2][2] = L[5].value();
+  // ---- epilogue: lambda_min in FP32 (it only selects the branch and is
+  // reported), L inverse and the hydrostatic terms in FP64 ----
+  double l[6];
+  float lf[6];
+  const int nl = DIM == 2 ? 3 : 6;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    lf[k] = k < nl ? L[k].s - L[k].c : 0.f;
+    l[k] = (double)lf[k];
   }
   double Sd[DIM], Md[DIM * DIM], Cd[DIM], Kd[DIM], Ld[DIM], Pd[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
-    Sd[c] = S[c].value(); Cd[c] = Cc[c].value(); Kd[c] = K[c].value();
-    Ld[c] = Lam[c].value(); Pd[c] = P[c].value();
+    Sd[c] = (double)(S[c].s - S[c].c); Cd[c] = (double)(Cs[c].s - Cs[c].c);
+    Kd[c] = (double)(K[c].s - K[c].c); Ld[c] = (double)(Lam[c].s - Lam[c].c);
+    Pd[c] = (double)(P[c].s - P[c].c);
   }
 #pragma unroll
-  for (int c = 0; c < DIM * DIM; ++c) Md[c] = M[c].value();
-  double lam = DIM == 2 ? mx_lambda_min_2(Lf[0][0], Lf[0][1], Lf[1][1])
-                        : mx_lambda_min_3(Lf[0][0], Lf[0][1], Lf[0][2], Lf[1][1], Lf[1][2], Lf[2][2]);
+  for (int c = 0; c < DIM * DIM; ++c) Md[c] = (double)(M[c].s - M[c].c);
+  float lamf;
+  if (DIM == 2) {
+    float m = 0.5f * (lf[0] + lf[2]), d = 0.5f * (lf[0] - lf[2]);
+    lamf = m - sqrtf(d * d + lf[1] * lf[1]);
+  } else {
+    lamf = lambda_min_3f(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
+  }
   double t_stage = stage2 ? w.scalars[0] + w.scalars[1] : w.scalars[0];
   double fs = p.omega > 0.0 ? p.omega * p.omega * sin(p.omega * t_stage) : 0.0;
-  double xi[DIM], phs = 0.0, gn2 = 0.0;
+  double phs = 0.0, gn2 = 0.0;
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
-    xi[c] = s.x[c * n + i];
-    phs += p.g[c] * xi[c];
+    phs += p.g[c] * s.x[c * n + i];
     gn2 += p.g[c] * p.g[c];
   }
   phs += sqrt(gn2) * p.water_height;
   double acc[DIM], divu = 0.0;
-  if (p.use_tic && lam < p.tic_lambda) {
+  if (p.use_tic && lamf < (float)p.tic_lambda) {
+    // conservative gradient of the full phi rebuilt from the phi' sums:
+    // C = C' + 2 phi_hs,i K + L G
+    double Lm[3][3] = {{l[0], l[1], DIM == 3 ? l[2] : 0.0},
+                       {l[1], DIM == 3 ? l[3] : l[2], DIM == 3 ? l[4] : 0.0},
+                       {DIM == 3 ? l[2] : 0.0, DIM == 3 ? l[4] : 0.0, DIM == 3 ? l[5] : 0.0}};
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       double lg = 0.0;
 #pragma unroll
-      for (int e = 0; e < DIM; ++e) lg += Lf[c][e] * p.g[e];
+      for (int e = 0; e < DIM; ++e) lg += Lm[c][e] * p.g[e];
       double gradphi = Cd[c] + 2.0 * phs * Kd[c] + lg;
       acc[c] = -gradphi + p.g[c] + p.force_amp[c] * fs;
       divu += Md[c * DIM + c];
     }
   } else {
-    double inv[DIM][DIM], det, amax = 0.0;
-#pragma unroll
-    for (int c = 0; c < DIM; ++c)
-#pragma unroll
-      for (int e = 0; e < DIM; ++e) amax = fmax(amax, fabs(Lf[c][e]));
-    if (DIM == 2) {
-      det = Lf[0][0] * Lf[1][1] - Lf[0][1] * Lf[1][0];
-      double id = 1.0 / det;
-      inv[0][0] = Lf[1][1] * id; inv[DIM - 1][DIM - 1] = Lf[0][0] * id;
-      inv[0][DIM - 1] = -Lf[0][1] * id; inv[DIM - 1][0] = -Lf[1][0] * id;
-    } else {
-      double m[3][3];
-      m[0][0] = Lf[1][1] * Lf[2][2] - Lf[1][2] * Lf[2][1];
-      m[1][0] = Lf[1][2] * Lf[2][0] - Lf[1][0] * Lf[2][2];
-      m[2][0] = Lf[1][0] * Lf[2][1] - Lf[1][1] * Lf[2][0];
-      det = Lf[0][0] * m[0][0] + Lf[0][1] * m[1][0] + Lf[0][2] * m[2][0];
-      m[0][1] = Lf[0][2] * Lf[2][1] - Lf[0][1] * Lf[2][2];
-      m[1][1] = Lf[0][0] * Lf[2][2] - Lf[0][2] * Lf[2][0];
-      m[2][1] = Lf[0][1] * Lf[2][0] - Lf[0][0] * Lf[2][1];
-      m[0][2] = Lf[0][1] * Lf[1][2] - Lf[0][2] * Lf[1][1];
-      m[1][2] = Lf[0][2] * Lf[1][0] - Lf[0][0] * Lf[1][2];
-      m[2][2] = Lf[0][0] * Lf[1][1] - Lf[0][1] * Lf[1][0];
-      double id = 1.0 / det;
-#pragma unroll
-      for (int c = 0; c < DIM; ++c)
-#pragma unroll
-        for (int e = 0; e < DIM; ++e) inv[c][e] = m[c][e] * id;
-    }
-    double amd = DIM == 2 ? amax * amax : amax * amax * amax;
-    if (!(fabs(det) > 1e-12 * amd)) {
-      atomicOr(w.status, kStatSingular);
-#pragma unroll
-      for (int c = 0; c < DIM; ++c)
-#pragma unroll
-        for (int e = 0; e < DIM; ++e) inv[c][e] = 0.0;
-    }
+    double inv[DIM][DIM];
+    if (!sym_inverse<DIM>(l, inv)) atomicOr(w.status, kStatSingular);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       double gs = 0.0;
@@ -336,9 +252,8 @@ __global__ void __launch_bounds__(MX_THREADS, 3)
     dn2 += dstar[c] * dstar[c];
     gk += p.g[c] * Kd[c];
   }
-  double c2 = p.eos == 0 ? p.c0sq : p.c0sq + (p.gamma - 1.0) * phii;
-  double diff = p.use_delta ? p.delta_h_c0 * 2.0 * (D.value() + gk) : 0.0;
-  double dphidt = -c2 * divu + diff;
+  double diff = p.use_delta ? p.delta_h_c0 * 2.0 * ((double)(D.s - D.c) + gk) : 0.0;
+  double dphidt = -eos_c2(p, phii) * divu + diff;
   w.dphidt[i] = dphidt;
   bad |= !isfinite(dphidt);
   double dn = sqrt(dn2);
@@ -349,29 +264,20 @@ __global__ void __launch_bounds__(MX_THREADS, 3)
     w.dushift[c * n + i] = v;
     bad |= !isfinite(v);
   }
-  w.lambda[i] = lam;
+  w.lambda[i] = (double)lamf;
   if (bad) atomicOr(w.status, kStatNaN);
 }
 
 int launch_mixed_stage(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
                        int stage2, cudaStream_t st) {
   if (n == 0) return 0;
-  if (n >= ((int64_t)1 << 27)) return WBSPH_E_INVAL;  // list entries pack the index in 27 bits
-  k_pack_mixed<<<(unsigned)div_up(n, 256), 256, 0, st>>>(p, s, w, n, w.packA, w.packB);
+  if (p.nc[0] > 2048 || p.nc[1] > 2048 || p.nc[2] > 1024) return WBSPH_E_INVAL;  // packed cell coords
+  k_pack_mixed<<<(unsigned)div_up(n, 256), 256, 0, st>>>(p, s, w, n, w.packA, w.packB, w.packC);
   if (nf == 0) return 0;
+  launch_nbr_list(p, w, n, nf, st);
   unsigned blocks = (unsigned)div_up(nf, MX_THREADS);
-  if (p.dim == 2) {
-    size_t sm = (size_t)mx_kcap<2>() * 32 * (MX_THREADS / 32) * sizeof(uint32_t);
-    k_pair_mixed<2><<<blocks, MX_THREADS, sm, st>>>(p, s, w, n, nf, stage2, w.packA, w.packB);
-  } else {
-    size_t sm = (size_t)mx_kcap<3>() * 32 * (MX_THREADS / 32) * sizeof(uint32_t);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_pair_mixed<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-    }
-    k_pair_mixed<3><<<blocks, MX_THREADS, sm, st>>>(p, s, w, n, nf, stage2, w.packA, w.packB);
-  }
+  if (p.dim == 2) k_pair_mixed<2><<<blocks, MX_THREADS, 0, st>>>(p, s, w, n, nf, stage2, w.packA, w.packB, w.packC);
+  else k_pair_mixed<3><<<blocks, MX_THREADS, 0, st>>>(p, s, w, n, nf, stage2, w.packA, w.packB, w.packC);
   return 0;
 }
 

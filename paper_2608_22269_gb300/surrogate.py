@@ -1,0 +1,237 @@
+"""Training and evaluation driver of the learned surrogate (BF16 message passing).
+
+Trajectories of the plain FP64 method (CUDA path) provide the training states;
+the network is trained on the GPU by the library's own forward/backward
+kernels (wbsph_surrogate_train_step), its targets being the plain rates of
+each state. Rollouts replace the pair pass by the network inside the same
+SSP-RK2 step and re-anchor with a plain FP64 step every `anchor_every` steps
+(wbsph_step_surrogate), which also measures the surrogate's acceleration
+error against the plain one on the anchor state.
+
+Scenes: 2D dam breaks in a 2.0 x 1.0 m basin, column width and height drawn
+(seeded) from [0.3, 0.8] x [0.2, 0.5] m, dx = sqrt(w h / n_target).
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import scenes as S
+from . import wbsph
+
+
+def column_sizes(n: int, seed: int = 7):
+    rng = np.random.default_rng(seed)
+    return [(float(rng.uniform(0.3, 0.8)), float(rng.uniform(0.2, 0.5))) for _ in range(n)]
+
+
+def dam_scene(w: float, h: float, n_target: int, width: float = 2.0, wall: float = 1.0):
+    dx = math.sqrt(w * h / n_target)
+    return S.dam_break_2d(dx=dx, width=width, wall=wall, column=(w, h))
+
+
+def generate(n_traj=40, n_target=50_000, t_end=0.2, frames=20, seed=7, log=print):
+    """Plain FP64 trajectories; returns a list of (scene, [(x, u, phi), ...])."""
+    data = []
+    t0 = time.time()
+    for k, (w, h) in enumerate(column_sizes(n_traj, seed)):
+        sc = dam_scene(w, h, n_target)
+        sim = wbsph.Sim(sc.params, water_height=sc.water_height)
+        sim.set_scene(sc)
+        states = []
+        for f in range(frames):
+            t_goal = t_end * (f + 1) / frames
+            while sim.stats()["t"] < t_goal:
+                sim.step(20)
+            states.append((sim.get("x"), sim.get("u"), sim.get("phi")))
+        data.append((sc, states))
+        nsteps = sim.stats()["steps"]
+        sim.close()
+        if log:
+            log(f"trajectory {k}: column {w:.2f} x {h:.2f}, n_fluid {sc.n_fluid}, "
+                f"steps {nsteps}, elapsed {time.time() - t0:.1f} s")
+    return data
+
+
+def _load_state(sim, sc, st):
+    x, u, phi = st
+    sim.set_particles(x, u, phi, sc.type, sc.normal)
+
+
+def normalisation(data, samples=20, seed=0):
+    """Means and standard deviations of the node features (U, rho/rho0 - 1,
+    phi) and of the plain rates (DU/Dt, Dphi/Dt) over sampled frames."""
+    rng = np.random.default_rng(seed)
+    feats, outs = [], []
+    for _ in range(samples):
+        sc, states = data[rng.integers(len(data))]
+        st = states[rng.integers(len(states))]
+        sim = wbsph.Sim(sc.params, water_height=sc.water_height)
+        _load_state(sim, sc, st)
+        sim.eval_rates()
+        f = sc.type == 0
+        rho = sim.get("rho")
+        d = sc.params["dim"]
+        feats.append(np.r_[st[1][:, f], (rho[f] / sc.params["rho0"] - 1.0)[None], st[2][None, f]])
+        outs.append(np.r_[sim.get("dudt")[:, f], sim.get("dphidt")[None, f]])
+        sim.close()
+    F = np.concatenate(feats, axis=1)
+    O = np.concatenate(outs, axis=1)
+    fs = np.maximum(F.std(1), 1e-6)
+    os_ = np.maximum(O.std(1), 1e-6)
+    return F.mean(1), fs, O.mean(1), os_
+
+
+def train(sur: "wbsph.Surrogate", data, iters=2000, lr=1e-3, seed=1, log=print, log_every=200):
+    """Adam with cosine decay over random frames; returns the loss history."""
+    rng = np.random.default_rng(seed)
+    sims = {}
+    hist = []
+    t0 = time.time()
+    for it in range(iters):
+        k = int(rng.integers(len(data)))
+        sc, states = data[k]
+        if k not in sims:
+            sims[k] = wbsph.Sim(sc.params, water_height=sc.water_height)
+        sim = sims[k]
+        _load_state(sim, sc, states[int(rng.integers(len(states)))])
+        lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * it / iters))
+        loss = sur.train_step(sim, lr_t)
+        hist.append(loss)
+        if log and (it % log_every == 0 or it == iters - 1):
+            log(f"iter {it}: loss {np.mean(hist[-log_every:]):.4e} lr {lr_t:.2e} ({time.time() - t0:.1f} s)")
+    for s in sims.values():
+        s.close()
+    return hist
+
+
+def gravity_only_params(dim, out_mean, out_std, g):
+    """Parameters of a network whose output is exactly (G, 0) for every
+    particle: all weights zero, decoder bias set to the normalised gravity."""
+    from_flat = np.zeros(wbsph_num_params(dim), dtype=np.float32)
+    tgt = np.r_[np.asarray(g[:dim], dtype=np.float64), 0.0]
+    b2 = ((tgt - out_mean) / out_std).astype(np.float32)
+    from_flat[-(dim + 1):] = b2
+    return from_flat
+
+
+def wbsph_num_params(dim, hidden=64, layers=3):
+    fn, fe, fo = dim + 3, dim + 1, dim + 1
+    blocks = [(fn, hidden), (fe, hidden)] + [(3 * hidden, hidden), (2 * hidden, hidden)] * layers + [(hidden, fo)]
+    return sum(i * hidden + hidden + hidden * o + o for i, o in blocks)
+
+
+def rollout_error(sc, sur, nsteps, anchor_every=10, tau=0.1):
+    """Run the plain FP64 rollout and a surrogate rollout from the same state;
+    return position RMS / dx, velocity RMS error and the anchor statistics."""
+    ref = wbsph.Sim(sc.params, water_height=sc.water_height)
+    ref.set_scene(sc)
+    t0 = time.time()
+    ref.step(nsteps)
+    ref.sync()
+    t_plain = time.time() - t0
+    sim = wbsph.Sim(sc.params, water_height=sc.water_height)
+    sim.set_scene(sc)
+    t0 = time.time()
+    stats = sur.step(sim, nsteps, anchor_every=anchor_every, tau=tau)
+    t_sur = time.time() - t0
+    f = sc.type == 0
+    dx = sc.params["dx"]
+    ex = ref.get("x")[:, f] - sim.get("x")[:, f]
+    eu = ref.get("u")[:, f] - sim.get("u")[:, f]
+    out = {"pos_rms_over_dx": float(np.sqrt((ex ** 2).sum(0).mean()) / dx),
+           "vel_rms": float(np.sqrt((eu ** 2).sum(0).mean())),
+           "vel_scale": float(np.sqrt((ref.get("u")[:, f] ** 2).sum(0).mean())),
+           "anchors": stats, "wall_plain_s": t_plain, "wall_surrogate_s": t_sur}
+    ref.close()
+    sim.close()
+    return out
+
+
+def save(path, sur, norm, meta):
+    np.savez(path, params=sur.get_params(), node_mean=norm[0], node_std=norm[1], out_mean=norm[2],
+             out_std=norm[3], meta=np.frombuffer(str(meta).encode(), dtype=np.uint8))
+
+
+def load(path, dim=2):
+    z = np.load(path)
+    sur = wbsph.Surrogate(dim)
+    sur.set_params(z["params"])
+    norm = (z["node_mean"], z["node_std"], z["out_mean"], z["out_std"])
+    sur.set_normalization(*norm)
+    return sur, norm
+
+
+def main(argv=None):
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="train the BF16 surrogate on plain FP64 trajectories")
+    ap.add_argument("--out", required=True, help="output .npz with parameters and normalisation")
+    ap.add_argument("--report", default=None, help="JSON report path")
+    ap.add_argument("--trajectories", type=int, default=40)
+    ap.add_argument("--particles", type=int, default=50_000)
+    ap.add_argument("--t-end", type=float, default=0.2)
+    ap.add_argument("--frames", type=int, default=20)
+    ap.add_argument("--iters", type=int, default=2000)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--eval-steps", type=int, default=400)
+    args = ap.parse_args(argv)
+    t0 = time.time()
+    data = generate(args.trajectories, args.particles, args.t_end, args.frames, args.seed)
+    t_gen = time.time() - t0
+    norm = normalisation(data)
+    sur = wbsph.Surrogate(2)
+    theta0 = init_params_2d(seed=args.seed)
+    sur.set_params(theta0)
+    sur.set_normalization(*norm)
+    t0 = time.time()
+    hist = train(sur, data, iters=args.iters, lr=args.lr, seed=args.seed)
+    t_train = time.time() - t0
+    meta = dict(trajectories=args.trajectories, particles=args.particles, t_end=args.t_end,
+                frames=args.frames, iters=args.iters, lr=args.lr, seed=args.seed)
+    save(args.out, sur, norm, meta)
+    # gain test on a held-out column, same anchoring for every variant
+    held = dam_scene(0.55, 0.35, args.particles)
+    rep = {"meta": meta, "gen_s": t_gen, "train_s": t_train,
+           "loss_first": float(np.mean(hist[:50])), "loss_last": float(np.mean(hist[-50:]))}
+    rep["trained"] = rollout_error(held, sur, args.eval_steps)
+    grav = wbsph.Surrogate(2)
+    grav.set_params(gravity_only_params(2, norm[2], norm[3], held.params["g"]))
+    grav.set_normalization(*norm)
+    rep["gravity_only"] = rollout_error(held, grav, args.eval_steps)
+    untrained = wbsph.Surrogate(2)
+    untrained.set_params(theta0)
+    untrained.set_normalization(*norm)
+    rep["untrained"] = rollout_error(held, untrained, args.eval_steps)
+    print(json.dumps(rep))
+    if args.report:
+        with open(args.report, "w") as fh:
+            json.dump(rep, fh, indent=1)
+
+
+def init_params_2d(seed=0, hidden=64, layers=3):
+    """Uniform(+-1/sqrt(fan_in)) weights, zero biases, processor output
+    layers scaled by 0.1 (small residual updates at the start)."""
+    dim = 2
+    rng = np.random.default_rng(seed)
+    fn, fe, fo = dim + 3, dim + 1, dim + 1
+    blocks = [("n", fn, hidden), ("e", fe, hidden)]
+    for _ in range(layers):
+        blocks += [("mp", 3 * hidden, hidden), ("mp", 2 * hidden, hidden)]
+    blocks.append(("dec", hidden, fo))
+    parts = []
+    for name, i, o in blocks:
+        s1, s2 = 1.0 / math.sqrt(i), 1.0 / math.sqrt(hidden)
+        if name == "mp":
+            s2 *= 0.1
+        parts += [rng.uniform(-s1, s1, i * hidden), np.zeros(hidden), rng.uniform(-s2, s2, hidden * o),
+                  np.zeros(o)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+if __name__ == "__main__":
+    main()

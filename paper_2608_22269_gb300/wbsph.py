@@ -268,3 +268,143 @@ class Sim:
         cnt = (C.c_int64 * 8)()
         self._check(self.lib.wbsph_get_profile(self.h, ms, cnt, int(reset)))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+# ---------------------------------------------------------------------------
+# Learned surrogate (wbsph_surrogate_* in include/wbsph.h)
+# ---------------------------------------------------------------------------
+class SurrogateConfig(C.Structure):
+    _fields_ = [("dim", C.c_int), ("hidden", C.c_int), ("layers", C.c_int), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("device", C.c_int)]
+
+
+class AnchorStats(C.Structure):
+    _fields_ = [("surrogate_steps", C.c_int64), ("plain_steps", C.c_int64), ("anchors", C.c_int64),
+                ("fallbacks", C.c_int64), ("last_rel_err", C.c_double), ("max_rel_err", C.c_double)]
+
+
+SURROGATE_SYMBOLS = ["wbsph_surrogate_config_default", "wbsph_surrogate_create",
+                     "wbsph_surrogate_num_params", "wbsph_surrogate_set_params",
+                     "wbsph_surrogate_get_params", "wbsph_surrogate_set_normalization",
+                     "wbsph_surrogate_train_step", "wbsph_surrogate_eval", "wbsph_surrogate_predict",
+                     "wbsph_surrogate_debug", "wbsph_step_surrogate", "wbsph_surrogate_destroy",
+                     "wbsph_surrogate_last_error"]
+SYMBOLS += SURROGATE_SYMBOLS
+
+
+def _load_surrogate(L):
+    if getattr(L, "_surrogate_sig", False):
+        return L
+    P, i64, I, F, D = C.c_void_p, C.c_int64, C.c_int, C.c_float, C.c_double
+    sig = {
+        "wbsph_surrogate_config_default": (I, [P, I]),
+        "wbsph_surrogate_create": (I, [P, P]),
+        "wbsph_surrogate_num_params": (i64, [P]),
+        "wbsph_surrogate_set_params": (I, [P, P]),
+        "wbsph_surrogate_get_params": (I, [P, P]),
+        "wbsph_surrogate_set_normalization": (I, [P, P, P, P, P]),
+        "wbsph_surrogate_train_step": (I, [P, P, F, P]),
+        "wbsph_surrogate_eval": (I, [P, P, P]),
+        "wbsph_surrogate_predict": (I, [P, P]),
+        "wbsph_surrogate_debug": (I, [P, P, P, P, P, P, P, P, P, P, P]),
+        "wbsph_step_surrogate": (I, [P, P, i64, I, D, P]),
+        "wbsph_surrogate_destroy": (None, [P]),
+        "wbsph_surrogate_last_error": (C.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    L._surrogate_sig = True
+    return L
+
+
+class Surrogate:
+    """BF16 message-passing surrogate; parameters live on the device."""
+
+    def __init__(self, dim: int, device: int = 0, layers: int = 3):
+        self.lib = _load_surrogate(load())
+        cfg = SurrogateConfig()
+        self.lib.wbsph_surrogate_config_default(C.byref(cfg), dim)
+        cfg.layers = layers
+        cfg.device = device
+        h = C.c_void_p()
+        rc = self.lib.wbsph_surrogate_create(C.byref(cfg), C.byref(h))
+        if rc != OK:
+            raise WbsphError(rc, "wbsph_surrogate_create failed")
+        self.h = h
+        self.dim = dim
+        self.np = int(self.lib.wbsph_surrogate_num_params(h))
+
+    def _check(self, rc, sim=None):
+        if rc < 0:
+            msg = self.lib.wbsph_surrogate_last_error(self.h).decode()
+            if sim is not None:
+                msg += " / " + sim.lib.wbsph_last_error(sim.h).decode()
+            raise WbsphError(int(rc), msg)
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.wbsph_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        assert theta.size == self.np
+        self._check(self.lib.wbsph_surrogate_set_params(self.h, _ptr(theta)))
+
+    def get_params(self):
+        out = np.empty(self.np, dtype=np.float32)
+        self._check(self.lib.wbsph_surrogate_get_params(self.h, _ptr(out)))
+        return out
+
+    def set_normalization(self, node_mean, node_std, out_mean, out_std):
+        a = [np.ascontiguousarray(v, dtype=np.float32) for v in (node_mean, node_std, out_mean, out_std)]
+        self._check(self.lib.wbsph_surrogate_set_normalization(self.h, *[_ptr(v) for v in a]))
+
+    def train_step(self, sim, lr):
+        loss = C.c_double()
+        self._check(self.lib.wbsph_surrogate_train_step(self.h, sim.h, float(lr), C.byref(loss)), sim)
+        return loss.value
+
+    def eval(self, sim):
+        loss = C.c_double()
+        self._check(self.lib.wbsph_surrogate_eval(self.h, sim.h, C.byref(loss)), sim)
+        return loss.value
+
+    def predict(self, sim):
+        self._check(self.lib.wbsph_surrogate_predict(self.h, sim.h), sim)
+
+    def debug(self, sim):
+        ne = C.c_int64()
+        self._check(self.lib.wbsph_surrogate_debug(self.h, sim.h, C.byref(ne), None, None, None, None,
+                                                   None, None, None, None), sim)
+        E = ne.value
+        st = sim.stats()
+        n, nf = st["n"], st["n_fluid"]
+        recv = np.empty(E, np.uint32)
+        send = np.empty(E, np.uint32)
+        ef = np.empty((E, 8), np.float32)
+        nfe = np.empty((n, 8), np.float32)
+        fid = np.empty(nf, np.uint32)
+        out = np.empty((nf, self.dim + 1), np.float32)
+        grad = np.empty(self.np, np.float32)
+        loss = C.c_double()
+        self._check(self.lib.wbsph_surrogate_debug(self.h, sim.h, C.byref(ne), _ptr(recv), _ptr(send),
+                                                   _ptr(ef), _ptr(nfe), _ptr(fid), _ptr(out), _ptr(grad),
+                                                   C.byref(loss)), sim)
+        return dict(recv=recv, send=send, edge_feat=ef, node_feat=nfe, fluid_ids=fid, out=out,
+                    grad=grad, loss=loss.value)
+
+    def step(self, sim, nsteps, anchor_every=10, tau=0.1):
+        stats = AnchorStats()
+        self._check(self.lib.wbsph_step_surrogate(sim.h, self.h, int(nsteps), int(anchor_every),
+                                                  float(tau), C.byref(stats)), sim)
+        return {k: getattr(stats, k) for k, _ in AnchorStats._fields_}

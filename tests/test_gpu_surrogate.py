@@ -1,0 +1,101 @@
+"""BF16 surrogate kernels (forward, backward, training, anchored rollouts)
+against the FP64 reference of oracle/mpnn.py, on identical BF16-rounded
+weights and the same graph and features."""
+import numpy as np
+import pytest
+
+from oracle import mpnn
+from paper_2608_22269_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(dim=2, seed=3):
+    if dim == 2:
+        sc = S.dam_break_2d(dx=0.01, width=0.8, column=(0.3, 0.2))
+    else:
+        sc = S.dam_break_3d(dx=0.025, box=(0.4, 0.2, 0.3), column=(0.16, 0.2, 0.15))
+    sc = S.jitter(sc, 0.15, seed=seed)
+    rng = np.random.default_rng(seed)
+    f = sc.type == 0
+    sc.u[:, f] = 0.3 * rng.normal(size=(dim, f.sum()))
+    sc.phi[f] += 0.1 * rng.normal(size=f.sum())
+    return sc
+
+
+def _setup(sc, seed=1):
+    from paper_2608_22269_gb300 import wbsph
+    dim = sc.params["dim"]
+    sim = wbsph.Sim(sc.params, water_height=sc.water_height)
+    sim.set_scene(sc)
+    sur = wbsph.Surrogate(dim)
+    theta = mpnn.init_params(dim, seed=seed)
+    theta = theta + np.random.default_rng(seed).normal(scale=0.02, size=theta.size).astype(np.float32)
+    sur.set_params(theta)
+    f = sc.type == 0
+    node_mean = np.r_[sc.u[:, f].mean(1), 0.0, sc.phi[f].mean()].astype(np.float32)
+    node_std = np.r_[sc.u[:, f].std(1), 1e-3, sc.phi[f].std()].astype(np.float32)
+    sim.eval_rates()
+    a = np.r_[sim.get("dudt")[:, f], sim.get("dphidt")[None, f]]
+    out_mean, out_std = a.mean(1).astype(np.float32), a.std(1).astype(np.float32)
+    sur.set_normalization(node_mean, node_std, out_mean, out_std)
+    return sim, sur, theta, (out_mean, out_std)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_forward_and_gradient_match_fp64_reference(dim):
+    sc = _state(dim)
+    sim, sur, theta, (om, osd) = _setup(sc)
+    dbg = sur.debug(sim)
+    n = sc.n
+    fin = dim + 3
+    node_in = dbg["node_feat"][:, :fin].astype(np.float64)
+    edge_in = dbg["edge_feat"][:, :dim + 1].astype(np.float64)
+    th = mpnn.round_weights_bf16(theta, dim)
+    out = mpnn.forward_np(th, dim, node_in, dbg["recv"], dbg["send"], edge_in)
+    fid = dbg["fluid_ids"].astype(np.int64)
+    ref = out[fid]
+    gpu = dbg["out"]
+    rel = np.abs(gpu - ref).max() / np.abs(ref).max()
+    print(dim, "forward rel err", rel)
+    assert rel < 2e-2
+    # loss gradient: targets = normalised plain rates of the same state
+    f = sc.type == 0
+    tgt = np.zeros((n, dim + 1))
+    rates = np.r_[sim.get("dudt"), sim.get("dphidt")[None]].T
+    tgt[:] = (rates - om) / osd
+    fluid = np.zeros(n, bool)
+    fluid[fid] = True
+    dout = np.zeros((n, dim + 1))
+    dout[fluid] = 2.0 * (out[fluid] - tgt[fluid]) / (fluid.sum() * (dim + 1))
+    g_ref = mpnn.grad_np(th, dim, node_in, dbg["recv"], dbg["send"], edge_in, dout)
+    g = dbg["grad"].astype(np.float64)
+    cos = g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref))
+    reln = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    loss_ref = float(((out[fluid] - tgt[fluid]) ** 2).mean())
+    print(dim, "grad cos", cos, "rel norm", reln, "loss", dbg["loss"], loss_ref)
+    assert abs(dbg["loss"] - loss_ref) <= 3e-2 * loss_ref
+    assert cos > 0.9999 and reln < 1e-2
+
+
+def test_training_reduces_loss():
+    sc = _state(2, seed=5)
+    sim, sur, theta, _ = _setup(sc, seed=2)
+    l0 = sur.eval(sim)
+    for _ in range(60):
+        sur.train_step(sim, 3e-3)
+    l1 = sur.eval(sim)
+    print("loss", l0, "->", l1)
+    assert l1 < 0.5 * l0
+
+
+def test_anchored_rollout_bookkeeping():
+    sc = _state(2, seed=6)
+    sim, sur, theta, _ = _setup(sc, seed=3)
+    st = sur.step(sim, 20, anchor_every=5, tau=1e9)
+    assert st["anchors"] == 4 and st["plain_steps"] == 4 and st["surrogate_steps"] == 16
+    assert st["fallbacks"] == 0 and np.isfinite(st["max_rel_err"])
+    st2 = sur.step(sim, 10, anchor_every=5, tau=0.0)
+    assert st2["fallbacks"] >= 1 and st2["plain_steps"] > st2["anchors"]
+    x = sim.get("x")
+    assert np.all(np.isfinite(x))

@@ -1,0 +1,91 @@
+"""Pins of the FP64 surrogate reference (oracle/mpnn.py).
+
+The reference's gradients come from autograd of its forward; they are
+pinned by central finite differences. Its forward is pinned by properties
+fixed by the definition: permutation equivariance, batching additivity of
+disjoint graphs, independence of absolute position, and an isolated
+receiver reducing to the encoder-processor-decoder chain without messages.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mpnn
+
+
+def _graph(n=40, dim=2, seed=0, deg=5):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, size=(n, dim))
+    recv, send = [], []
+    for i in range(n):
+        js = rng.choice(np.delete(np.arange(n), i), size=deg, replace=False)
+        recv += [i] * deg
+        send += list(js)
+    recv, send = np.array(recv), np.array(send)
+    r = x[send] - x[recv]
+    edge = np.concatenate([r / 0.1, np.linalg.norm(r, axis=1, keepdims=True) / 0.1], axis=1)
+    node = rng.normal(size=(n, dim + 3))
+    return node, recv, send, edge
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gradient_matches_central_differences(dim):
+    node, recv, send, edge = _graph(n=12, dim=dim, seed=dim, deg=4)
+    theta = mpnn.init_params(dim, seed=1).astype(np.float64)
+    theta += np.random.default_rng(2).normal(scale=0.05, size=theta.shape)
+    dout = np.random.default_rng(3).normal(size=(node.shape[0], dim + 1))
+    g = mpnn.grad_np(theta, dim, node, recv, send, edge, dout)
+    f = lambda th: float((mpnn.forward_np(th, dim, node, recv, send, edge) * dout).sum())
+    idx = np.random.default_rng(4).choice(theta.size, size=40, replace=False)
+    for k in idx:
+        e = 1e-6
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += e
+        tm[k] -= e
+        fd = (f(tp) - f(tm)) / (2 * e)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, g[k])
+
+
+def test_permutation_equivariance():
+    node, recv, send, edge = _graph(n=30, seed=5)
+    theta = mpnn.init_params(2, seed=3)
+    out = mpnn.forward_np(theta, 2, node, recv, send, edge)
+    perm = np.random.default_rng(9).permutation(node.shape[0])
+    inv = np.argsort(perm)
+    out_p = mpnn.forward_np(theta, 2, node[perm], inv[recv], inv[send], edge)
+    assert np.allclose(out_p, out[perm], rtol=1e-12, atol=1e-12)
+
+
+def test_disjoint_graphs_batch_additively():
+    a = _graph(n=20, seed=1)
+    b = _graph(n=15, seed=2)
+    theta = mpnn.init_params(2, seed=4)
+    oa = mpnn.forward_np(theta, 2, *a)
+    ob = mpnn.forward_np(theta, 2, *b)
+    node = np.concatenate([a[0], b[0]])
+    recv = np.concatenate([a[1], b[1] + 20])
+    send = np.concatenate([a[2], b[2] + 20])
+    edge = np.concatenate([a[3], b[3]])
+    o = mpnn.forward_np(theta, 2, node, recv, send, edge)
+    assert np.allclose(o[:20], oa, atol=1e-12) and np.allclose(o[20:], ob, atol=1e-12)
+
+
+def test_isolated_receiver_has_no_messages():
+    """A node that receives no edge gets a = 0 in every layer: its output is
+    dec(h_L) with h_{l+1} = h_l + MLP_n([h_l, 0]), independent of the rest."""
+    node, recv, send, edge = _graph(n=20, seed=6)
+    keep = recv != 0
+    recv, send, edge = recv[keep], send[keep], edge[keep]
+    theta = mpnn.init_params(2, seed=5)
+    out = mpnn.forward_np(theta, 2, node, recv, send, edge)
+    node2 = node.copy()
+    node2[1:] += 3.0
+    out2 = mpnn.forward_np(theta, 2, node2, recv, send, edge)
+    assert np.array_equal(out[0], out2[0])
+    assert not np.allclose(out[1:], out2[1:])
+
+
+def test_parameter_count_and_layout():
+    assert mpnn.num_params(2) == mpnn.init_params(2).size
+    P = mpnn.unflatten(torch.zeros(mpnn.num_params(3), dtype=torch.float64), 3)
+    assert P["mp0_e"][0].shape == (192, 64) and P["dec"][2].shape == (64, 4)
