@@ -164,14 +164,21 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(v: float, world: int) -> float:
+def max_over_ranks(v: float, world: int, device: str = "cuda") -> float:
+    """Largest value over ranks (the slowest replica sets the job time)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of independent replicas: units of all ranks over
+    the slowest rank's time."""
+    return units_per_rank * world / seconds_max
 
 
 def profile_traffic(kernel_file: str, key: str):
@@ -216,8 +223,6 @@ def time_path(scene, precision, args, world, local):
     sim.set_scene(scene)
     sim.step(args.warmup)
     sim.sync()
-    sim.set_profiling(True)
-    sim.profile(reset=True)
     st0 = sim.stats()
     barrier(world)
     torch.cuda.synchronize()
@@ -225,22 +230,30 @@ def time_path(scene, precision, args, world, local):
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         e0.record(sim.stream)
-        sim.step(args.steps)
+        sim.step(args.steps)       # replayed as a CUDA graph after the first step
         e1.record(sim.stream)
         torch.cuda.synchronize()
     barrier(world)
     ms = e0.elapsed_time(e1)
     sim.sync()
     st1 = sim.stats()
+    # kernel-class timing: the same number of steps again with CUDA events
+    # bracketing every kernel class (eager launches)
+    sim.set_profiling(True)
+    sim.profile(reset=True)
+    sp0 = sim.stats()
+    sim.step(args.steps)
+    sim.sync()
+    sp1 = sim.stats()
     prof = sim.profile(reset=True)
     sim.set_profiling(False)
     return sim, {"ms": max_over_ranks(ms, world), "st0": st0, "st1": st1, "prof": prof,
-                 "clocks": clk.summary()}
+                 "sp0": sp0, "sp1": sp1, "clocks": clk.summary()}
 
 
 def pair_roofline(m, dim, nf, mixed, workload):
     pair_ms, pair_n = m["prof"]["pair"]
-    pairs = m["st1"]["pairs"] - m["st0"]["pairs"]
+    pairs = m["sp1"]["pairs"] - m["sp0"]["pairs"]
     per_launch = pairs / max(pair_n, 1)
     avg_ms = pair_ms / max(pair_n, 1)
     if mixed:
@@ -307,6 +320,60 @@ def rates_diff(a, b, scene):
             "excluded_tic_boundary": int((~keep).sum())}
 
 
+def surrogate_path(args, local):
+    """Surrogate rollouts (configs' 2D inference case: dam break, column
+    0.6 x 0.3 m, dx = 0.00085 m, 249,218 fluid particles) with a plain FP64
+    re-anchoring step every 10 steps, timed against the plain FP64 rollout of
+    the same scene; error = position RMS / dx against that plain rollout."""
+    import numpy as np
+    import torch
+
+    from paper_2608_22269_gb300 import scenes, wbsph
+    from paper_2608_22269_gb300 import surrogate as SG
+    path = os.path.join(ROOT, "paper_2608_22269_gb300", "data", "surrogate_2d.npz")
+    if not os.path.exists(path):
+        return {"unavailable": "no trained surrogate weights in paper_2608_22269_gb300/data"}
+    sur, norm = SG.load(path, 2)
+    sc = scenes.dam_break_2d(dx=0.00085, width=2.0, wall=0.6, column=(0.6, 0.3))
+    K = max(args.steps, 10)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    plain = wbsph.Sim(sc.params, water_height=sc.water_height, device=local)
+    plain.set_scene(sc)
+    plain.step(args.warmup)
+    plain.sync()
+    t_plain = timed(lambda: (plain.step(K), plain.sync()))
+    sim = wbsph.Sim(sc.params, water_height=sc.water_height, device=local)
+    sim.set_scene(sc)
+    sur.step(sim, args.warmup, anchor_every=10, tau=0.1)
+    sim.set_profiling(True)
+    sim.profile(reset=True)
+    stats = {}
+    t_sur = timed(lambda: stats.update(sur.step(sim, K, anchor_every=10, tau=0.1)))
+    prof = sim.profile(reset=True)
+    f = sc.type == 0
+    err = float(np.sqrt(((plain.get("x")[:, f] - sim.get("x")[:, f]) ** 2).sum(0).mean()) / sc.params["dx"])
+    out = {"workload": "2D dam break, column 0.6x0.3 m in a 2.0 m basin, dx=0.00085 m "
+                       f"({sc.n_fluid:,} fluid), FP64 anchor every 10 steps",
+           "value": round(sc.n_fluid * K / t_sur, 1), "unit": UNIT,
+           "plain_fp64_same_scene": round(sc.n_fluid * K / t_plain, 1),
+           "ms_per_step": round(t_sur * 1e3 / K, 3), "steps": K,
+           "anchors": stats, "error": {"pos_rms_over_dx_vs_plain": err,
+                                        "max_anchor_rel_l2_dudt": stats.get("max_rel_err")},
+           "surrogate_stage_ms": round(prof["pair"][0], 3),
+           "weights": "paper_2608_22269_gb300/data/surrogate_2d.npz (trained on the GPU by this library)"}
+    plain.close()
+    sim.close()
+    sur.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -322,7 +389,7 @@ def run_ours(args):
     setup_s = time.perf_counter() - t_setup
     primary_mixed = args.precision == "mixed"
     sim, m = time_path(scene, wbsph.MIXED if primary_mixed else wbsph.FP64, args, world, local)
-    value = nf * args.steps * world / (m["ms"] / 1e3)
+    value = weak_scaling_value(nf * args.steps, world, m["ms"] / 1e3)
     roofline = pair_roofline(m, dim, nf, primary_mixed, args.workload)
     peaks = {}
     try:
@@ -397,6 +464,11 @@ def run_ours(args):
             diff = rates_diff(mixed, fp64, scene)
             line["error"] = {"fp64_vs_oracle_sampled": err64, "mixed_vs_fp64": diff,
                              "measure": "max|a-b| / max(max|b|, natural scale) over fluid particles"}
+        if rank == 0:
+            try:
+                paths["surrogate"] = surrogate_path(args, local)
+            except Exception as exc:  # the plain paths above are the headline; report, do not abort
+                paths["surrogate"] = {"error": f"{type(exc).__name__}: {exc}"}
         line["paths"] = paths
         sim2.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -448,11 +520,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true",
                     help="skip the second precision and the sampled error checks")
+    ap.add_argument("--only-surrogate", action="store_true",
+                    help="run only the surrogate rollout timing (profiling aid)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_surrogate:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"surrogate": surrogate_path(args, 0)}), flush=True)
     else:
         run_ours(args)
 

@@ -176,7 +176,8 @@ int wbsph_get_profile(wbsph_handle h, double* ms, int64_t* launches, int reset);
 /* ---- learned surrogate (the paper has no learned part) ----------------
  * A message-passing network over the same neighbour lists predicts the
  * stage rates (DU/Dt, Dphi/Dt) of fluid particles from node features
- * (U, rho/rho0 - 1, phi, dummy flag) and edge features (r/h, |r|/h). Three
+ * (U, rho/rho0 - 1, phi, dummy flag) and edge features (r/h, |r|/h and the
+ * differences of U and phi scaled by the node-feature scales). Three
  * layers, hidden width 64, BF16 weights and activations, FP32 accumulation
  * on the tensor cores; trained on the GPU against the plain FP64 rates of
  * the states it is shown. Parameters are a flat FP32 vector: blocks node

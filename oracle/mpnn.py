@@ -7,7 +7,8 @@ the tests. Only the tests may import this module.
 
 Network (dimension d, hidden H = 64, three message-passing layers):
   node input  f_i = normalised (U_i, rho_i/rho0 - 1, phi_i, dummy flag)   (d + 3)
-  edge input  g_ij = ((x_j - x_i)/h, |x_j - x_i|/h) for receiver i, sender j (d + 1)
+  edge input  g_ij = ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U, (phi_j - phi_i)/s_phi)
+              for receiver i, sender j (2d + 2; s = the node-feature scales)
   MLP(x) = W2 silu(W1 x + b1) + b2 (weights stored input-major: x @ W)
   h = MLP_node_enc(f), e = MLP_edge_enc(g)
   per layer: e <- e + MLP_e([e_ij, h_i, h_j]);  a_i = sum_j e_ij;  h <- h + MLP_n([h_i, a_i])
@@ -30,7 +31,7 @@ LAYERS = 3
 
 
 def block_dims(dim: int, hidden: int = HIDDEN, layers: int = LAYERS):
-    fn, fe, fo = dim + 3, dim + 1, dim + 1
+    fn, fe, fo = dim + 3, 2 * dim + 2, dim + 1
     dims = [("enc_n", fn, hidden), ("enc_e", fe, hidden)]
     for l in range(layers):
         dims += [(f"mp{l}_e", 3 * hidden, hidden), (f"mp{l}_n", 2 * hidden, hidden)]
@@ -74,7 +75,7 @@ def _mlp(x, p):
 
 
 def forward(theta, dim, node_in, recv, send, edge_in, hidden=HIDDEN, layers=LAYERS):
-    """node_in (N, d+3), recv/send (E,) int64, edge_in (E, d+1) -> (N, d+1)."""
+    """node_in (N, d+3), recv/send (E,) int64, edge_in (E, 2d+2) -> (N, d+1)."""
     P = unflatten(theta, dim, hidden, layers)
     h = _mlp(node_in, P["enc_n"])
     e = _mlp(edge_in, P["enc_e"])

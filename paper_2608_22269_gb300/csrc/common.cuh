@@ -37,6 +37,8 @@ struct Params {
   double two_over_h;              // 2q + 1 = 1 + r * 2/h
   double pst_alpha_over_wdx;      // alpha / W(dx), for W_ij / W(dx)
   double pst_R, pst_n;
+  double pst_R_a4;                // pst_R * pst_alpha_over_wdx^4
+  double four_h2_lo;              // (2h)^2 (1 - 2^-48): below it the contracted r^2 decides
   double rho0, c0, c0sq, nu, gamma;
   double delta_h_c0;              // delta * h * C0
   double tic_lambda;
@@ -73,6 +75,7 @@ struct Work {
   double* dushift;   // dim * n
   double* lambda;    // n
   double* vol;       // n
+  double* volc;      // n: 5 alpha / h^2 * V, so that -W'(r)/r V = volc (1 - q/2)^3
   float4* xf;        // n: FP32 copy of positions (.w = type) for the candidate prefilter
   uint32_t* key;     // n: sorted cell keys
   uint32_t* key_alt; // n

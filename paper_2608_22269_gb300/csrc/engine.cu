@@ -44,6 +44,11 @@ struct wbsph_s {
   int64_t launches = 0, steps = 0;
   bool loaded = false;
   bool alloc_failed = false;
+  bool use_graphs = true;            // replay captured steps (caller stream only)
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_launches = 0;        // kernels in the captured step
+  int64_t steps_since_load = 0;
+  bool capturing = false;
   int64_t n_alloc = -1;  // particle count the buffers were sized for
   std::string err;
   bool prof = false;
@@ -166,6 +171,7 @@ static int derive_params(wbsph_s* h) {
   p.h = c.h_over_dx * c.dx;
   p.two_h = 2.0 * p.h;
   p.four_h2 = p.two_h * p.two_h;
+  p.four_h2_lo = p.four_h2 * (1.0 - std::ldexp(1.0, -48));
   p.R = p.two_h;
   p.alpha = c.dim == 2 ? 7.0 / (4.0 * kPi * p.h * p.h) : 21.0 / (16.0 * kPi * p.h * p.h * p.h);
   p.neg_dwdr_over_r_coef = 5.0 * p.alpha / (p.h * p.h);
@@ -174,6 +180,10 @@ static int derive_params(wbsph_s* h) {
   double q = c.dx / p.h, tq = 1.0 - 0.5 * q;
   p.pst_alpha_over_wdx = 1.0 / (tq * tq * tq * tq * (2.0 * q + 1.0));
   p.pst_R = c.pst_R;
+  {
+    double a2 = p.pst_alpha_over_wdx * p.pst_alpha_over_wdx;
+    p.pst_R_a4 = c.pst_R * a2 * a2;
+  }
   p.pst_n = c.pst_n;
   p.rho0 = c.rho0;
   p.c0 = c.c0;
@@ -281,9 +291,12 @@ extern "C" int wbsph_create(const wbsph_config* cfg, wbsph_handle* out) {
   return WBSPH_OK;
 }
 
+static void drop_graph(wbsph_s* h);
+
 extern "C" void wbsph_destroy(wbsph_handle h) {
   if (!h) return;
   cudaSetDevice(h->cfg.device);
+  drop_graph(h);
   free_all(h);
   cudaStreamSynchronize(h->stream);
   for (auto& e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -308,6 +321,7 @@ static int allocate(wbsph_s* h, int64_t n) {
   }
   Work& w = h->W;
   w.dudt = D(d * nn); w.dushift = D(d * nn); w.dphidt = D(nn); w.lambda = D(nn); w.vol = D(nn);
+  w.volc = D(nn);
   w.xf = (float4*)dev_alloc(h, nn * sizeof(float4));
   w.key = U32(nn); w.key_alt = U32(nn); w.perm = U32(nn); w.perm_alt = U32(nn);
   w.cell_lb = U32((size_t)h->P.ncells + 1);
@@ -397,6 +411,8 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
   if (rc) return rc;
   if (where == WBSPH_HOST) CK(cudaStreamSynchronize(h->stream));
   h->steps = 0;
+  h->steps_since_load = 0;
+  drop_graph(h);
   h->loaded = true;
   return WBSPH_OK;
 }
@@ -404,6 +420,9 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
 // Neighbour build for the current positions (stage 2 also carries y^n).
 static int build(wbsph_s* h, bool with_base) {
   const int64_t n = h->n;
+  // an odd number of builds outside a captured step would desynchronise
+  // the buffer pointers baked into a captured graph
+  if (h->graph_exec && !h->capturing) drop_graph(h);
   if (n == 0) return WBSPH_OK;
   cudaStream_t st = h->stream;
   {
@@ -471,32 +490,96 @@ extern "C" int wbsph_eval_rates(wbsph_handle h) {
   return rates(h, 0);
 }
 
+// One SSP-RK2 step as a launch sequence (no host synchronisation).
+static int enqueue_step(wbsph_s* h) {
+  int rc = build(h, false);
+  if (rc) return rc;
+  rc = rates(h, 0);
+  if (rc) return rc;
+  {
+    ProfScope ps(h, WBSPH_K_UPDATE);
+    launch_rk_stage(h->P, h->A, h->W, h->n, 1, h->stream);
+  }
+  rc = build(h, true);
+  if (rc) return rc;
+  rc = rates(h, 1);
+  if (rc) return rc;
+  {
+    ProfScope ps(h, WBSPH_K_UPDATE);
+    launch_rk_stage(h->P, h->A, h->W, h->n, 2, h->stream);
+  }
+  h->launches += 2;
+  return check_launch(h, "step");
+}
+
+static void drop_graph(wbsph_s* h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  h->graph_exec = nullptr;
+  h->graph_launches = 0;
+}
+
+// A step's launch sequence is periodic in the buffer pointers: every swap
+// (state buffers per stage, sort buffers per pass) happens an even number of
+// times per step, so one captured step replays correctly any number of times.
+static int capture_step(wbsph_s* h) {
+  drop_graph(h);
+  int64_t l0 = h->launches;
+  const State a0 = h->A;
+  const Work w0 = h->W;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  h->capturing = true;
+  int rc = enqueue_step(h);
+  h->capturing = false;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (rc || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc ? rc : fail(h, WBSPH_E_CUDA, "step capture: %s", cudaGetErrorString(e));
+  }
+  if (h->A.x != a0.x || h->W.key != w0.key || h->W.perm != w0.perm) {
+    cudaGraphDestroy(g);
+    return fail(h, WBSPH_E_STATE, "step is not pointer-periodic; graph replay disabled");
+  }
+  e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph_exec = nullptr;
+    cudaGetLastError();
+    return fail(h, WBSPH_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  h->graph_launches = h->launches - l0;
+  h->launches = l0;
+  return WBSPH_OK;
+}
+
 extern "C" int wbsph_step(wbsph_handle h, int64_t nsteps) {
   if (!h) return WBSPH_E_INVAL;
   if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
   if (nsteps < 0) return fail(h, WBSPH_E_INVAL, "nsteps < 0");
   CK(cudaSetDevice(h->cfg.device));
+  // Graph replay on a caller stream (not the legacy default stream) when
+  // profiling is off; the first step of a particle set runs eagerly so that
+  // one-time kernel attributes are set outside the capture.
+  bool graphs = h->use_graphs && h->stream != nullptr && !h->prof && h->n > 0;
   for (int64_t s = 0; s < nsteps; ++s) {
-    int rc = build(h, false);
-    if (rc) return rc;
-    rc = rates(h, 0);
-    if (rc) return rc;
-    {
-      ProfScope ps(h, WBSPH_K_UPDATE);
-      launch_rk_stage(h->P, h->A, h->W, h->n, 1, h->stream);
+    int rc;
+    if (graphs && h->steps_since_load > 0) {
+      if (!h->graph_exec && capture_step(h) != WBSPH_OK) {
+        h->use_graphs = false;
+        graphs = false;
+        rc = enqueue_step(h);
+      } else {
+        CK(cudaGraphLaunch(h->graph_exec, h->stream));
+        h->launches += h->graph_launches;
+        rc = check_launch(h, "graph step");
+      }
+    } else {
+      rc = enqueue_step(h);
     }
-    rc = build(h, true);
-    if (rc) return rc;
-    rc = rates(h, 1);
-    if (rc) return rc;
-    {
-      ProfScope ps(h, WBSPH_K_UPDATE);
-      launch_rk_stage(h->P, h->A, h->W, h->n, 2, h->stream);
-    }
-    h->launches += 2;
-    rc = check_launch(h, "step");
     if (rc) return rc;
     ++h->steps;
+    ++h->steps_since_load;
   }
   return WBSPH_OK;
 }
@@ -506,9 +589,10 @@ static int read_status(wbsph_s* h) {
   CK(cudaMemcpyAsync(&s, h->W.status, sizeof s, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (!s) return WBSPH_OK;
-  if (s & kStatDomain) return fail(h, WBSPH_E_DOMAIN, "a particle left the domain");
-  if (s & kStatSingular) return fail(h, WBSPH_E_SINGULAR, "singular renormalisation matrix (TIC off)");
+  // a non-finite value also sends positions out of the domain: report it first
   if (s & kStatNaN) return fail(h, WBSPH_E_NAN, "non-finite rate or state value");
+  if (s & kStatSingular) return fail(h, WBSPH_E_SINGULAR, "singular renormalisation matrix (TIC off)");
+  if (s & kStatDomain) return fail(h, WBSPH_E_DOMAIN, "a particle left the domain");
   if (s & kStatTimeout) return fail(h, WBSPH_E_TIMEOUT, "a bounded device wait gave up");
   return fail(h, WBSPH_E_CAPACITY, "neighbour list overflow");
 }

@@ -5,8 +5,8 @@
 //
 // Network (the paper has no learned part): node input f_i = normalised
 // (U_i, rho_i/rho0 - 1, phi_i) plus a dummy flag; edge input
-// ((x_j - x_i)/h, |x_j - x_i|/h) for every fluid receiver i and every particle
-// j within 2h; MLP(x) = W2 silu(W1 x + b1) + b2; node and edge encoders,
+// ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U, (phi_j - phi_i)/s_phi) for
+// every fluid receiver i and every particle j within 2h (s = node scales); MLP(x) = W2 silu(W1 x + b1) + b2; node and edge encoders,
 // three layers of e <- e + MLP_e([e, h_i, h_j]), a_i = sum_j e_ij,
 // h <- h + MLP_n([h, a]), and a decoder to normalised (DU/Dt, Dphi/Dt).
 // Flat parameter layout: blocks node encoder, edge encoder, (edge MLP,
@@ -87,6 +87,24 @@ __device__ __forceinline__ void frag_b_kn(uint32_t r[2], const bf16* s, int ld, 
   r[1] = pack2(s[(k0 + 2 * t + 8) * ld + n0 + g], s[(k0 + 2 * t + 9) * ld + n0 + g]);
 }
 
+// ldmatrix: four 8x8 b16 matrices, one row address per lane (16-byte aligned rows).
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const bf16* p) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+// A fragment (16x16 at m0,k0) of row-major [m][k] smem.
+__device__ __forceinline__ void ldsm_a(uint32_t r[4], const bf16* s, int ld, int m0, int k0) {
+  int lane = threadIdx.x & 31;
+  ldsm_x4(r, s + (m0 + (lane & 15)) * ld + k0 + ((lane >> 4) << 3));
+}
+// B fragments of n-tiles n0 and n0+8 (16 k at k0) of [n][k] smem: b0 = {r0,r1}, b1 = {r2,r3}.
+__device__ __forceinline__ void ldsm_b2(uint32_t r[4], const bf16* s, int ld, int k0, int n0) {
+  int lane = threadIdx.x & 31;
+  ldsm_x4(r, s + (n0 + (lane & 7) + ((lane >> 4) << 3)) * ld + k0 + (((lane >> 3) & 1) << 3));
+}
+
 __device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad(float z) {
   float s = 1.f / (1.f + __expf(-z));
@@ -160,18 +178,100 @@ struct Smem {
 
 // ---------------------------------------------------------------------------
 // Forward: out = MLP([gathered row]) (+ residual). Weights are staged once per
-// CTA (transposed to [n][k]); the CTA then walks row tiles of 64.
+// CTA (transposed to [n][k]); the CTA then walks row tiles of 64 with the
+// gather of the next tile (cp.async, 16-byte chunks, zero fill past the last
+// row) in flight while the current tile runs through both GEMMs. The
+// residual comes from the staged tile; outputs are staged per warp and
+// written as whole 128-byte rows.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, bool valid) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Row indices a tile's gather needs (EDGE: receiver and sender; LIST: node),
+// copied asynchronously two tiles ahead into a small ring in shared memory.
+template <int MODE>
+__device__ __forceinline__ void issue_idx(const MlpArgs& a, int64_t row0, int64_t rows, uint32_t* I) {
+  if (MODE == MODE_EDGE || MODE == MODE_LIST) {
+    const int per = TILE / 4;  // 16-byte chunks per index array
+    const int narr = MODE == MODE_EDGE ? 2 : 1;
+    if (threadIdx.x < per * narr) {
+      int arr = threadIdx.x / per, c = threadIdx.x % per;
+      const uint32_t* src = MODE == MODE_LIST ? a.list : (arr == 0 ? a.recv : a.send);
+      int64_t r = row0 + c * 4;
+      bool valid = r + 3 < rows;  // a partial last chunk is gathered below with plain loads
+      cp_async16(I + arr * TILE + c * 4, valid ? (const void*)(src + r) : (const void*)a.w1, valid);
+      if (!valid)
+        for (int q = 0; q < 4; ++q) I[arr * TILE + c * 4 + q] = (r + q < rows) ? src[r + q] : 0u;
+    }
+  }
+  cp_async_commit();
+}
+
+// Source of 16-byte chunk c8 (8 elements) of tile row r (row < rows).
+template <int MODE>
+__device__ __forceinline__ const bf16* chunk_src(const MlpArgs& a, int64_t row, int r, int c8,
+                                                 const uint32_t* I) {
+  if (MODE == MODE_DIRECT) return a.in + row * FEAT;  // only chunk 0 carries data
+  if (MODE == MODE_LIST) return a.in + (int64_t)I[r] * HID + c8 * 8;
+  if (MODE == MODE_EDGE) {
+    if (c8 < 8) return a.e + row * HID + c8 * 8;
+    if (c8 < 16) return a.h + (int64_t)I[r] * HID + (c8 - 8) * 8;
+    return a.h + (int64_t)I[TILE + r] * HID + (c8 - 16) * 8;
+  }
+  if (c8 < 8) return a.h + row * HID + c8 * 8;
+  return a.agg + row * HID + (c8 - 8) * 8;
+}
+
+template <int MODE, int KP>
+__device__ __forceinline__ void issue_tile(const MlpArgs& a, int64_t row0, int64_t rows, bf16* X, int ldx,
+                                           const uint32_t* I) {
+  constexpr int C8 = KP / 8;
+  for (int idx = threadIdx.x; idx < TILE * C8; idx += MLP_THREADS) {
+    int r = idx / C8, c8 = idx % C8;
+    int64_t row = row0 + r;
+    bool valid = row < rows && (MODE != MODE_DIRECT || c8 == 0);
+    const bf16* src = valid ? chunk_src<MODE>(a, row, r, c8, I) : a.w1;  // any address when zero-filling
+    cp_async16(X + r * ldx + c8 * 8, src, valid);
+  }
+  cp_async_commit();
+}
+
+template <int MODE, int KP, int NP>
+struct FwdSmem {
+  static constexpr int LDX = KP + 8, LDH = HID + 8;
+  static constexpr size_t bytes = (size_t)(HID * LDX + NP * LDH + 2 * TILE * LDX + TILE * LDH) * 2 +
+                                  (HID + NP) * 4 + 3 * 2 * TILE * 4;
+};
+
 template <int MODE, int KP, int NP>
 __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
-  using S = Smem<KP, NP>;
+  using S = FwdSmem<MODE, KP, NP>;
   extern __shared__ __align__(16) unsigned char smem[];
   bf16* W1t = reinterpret_cast<bf16*>(smem);      // [64][LDX]  W1t[n][k] = W1[k][n]
   bf16* W2t = W1t + HID * S::LDX;                  // [NP][LDH]  W2t[o][c] = W2[c][o]
-  bf16* X = W2t + NP * S::LDH;                     // [64][LDX]
-  bf16* A1 = X + TILE * S::LDX;                    // [64][LDH]
+  bf16* Xb = W2t + NP * S::LDH;                    // 2 x [64][LDX]
+  bf16* A1 = Xb + 2 * TILE * S::LDX;               // [64][LDH]
   float* B1 = reinterpret_cast<float*>(A1 + TILE * S::LDH);
   float* B2 = B1 + HID;
+  uint32_t* Ib = reinterpret_cast<uint32_t*>(B2 + NP);  // 3 x [2][64] row indices
+  const int64_t rows = arg_rows(a);
+  const int64_t stride = gridDim.x;
+  int64_t tile = blockIdx.x;
+  // pipeline: indices two tiles ahead, rows one tile ahead. Commit order per
+  // tile t: idx(t+2), data(t+1); so waiting for all but the newest group
+  // leaves data(t) and idx(t+1) complete.
+  issue_idx<MODE>(a, tile * TILE, rows, Ib);
+  issue_idx<MODE>(a, (tile + stride) * TILE, rows, Ib + 2 * TILE);
+  cp_async_wait<1>();
+  __syncthreads();
+  if (tile * TILE < rows) issue_tile<MODE, KP>(a, tile * TILE, rows, Xb, S::LDX, Ib);
+  else cp_async_commit();
   const bf16 zero = __float2bfloat16(0.f);
   for (int idx = threadIdx.x; idx < HID * KP; idx += MLP_THREADS) {
     int n = idx / KP, k = idx % KP;
@@ -183,35 +283,41 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
   }
   for (int idx = threadIdx.x; idx < HID; idx += MLP_THREADS) B1[idx] = a.b1[idx];
   for (int idx = threadIdx.x; idx < NP; idx += MLP_THREADS) B2[idx] = idx < a.nout ? a.b2[idx] : 0.f;
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int m0 = warp * 16;
-  const int64_t rows = arg_rows(a);
-  for (int64_t tile = blockIdx.x; tile * TILE < rows; tile += gridDim.x) {
+  for (int buf = 0, ring = 0; tile * TILE < rows; tile += stride, buf ^= 1, ring = (ring + 1) % 3) {
     const int64_t row0 = tile * TILE;
-    load_tile<MODE, KP>(a, row0, rows, X, S::LDX);
-    __syncthreads();
+    bf16* X = Xb + buf * TILE * S::LDX;
+    issue_idx<MODE>(a, (tile + 2 * stride) * TILE, rows, Ib + ((ring + 2) % 3) * 2 * TILE);
+    cp_async_wait<1>();
+    __syncthreads();  // data(t) and idx(t+1) visible to all threads
+    if ((tile + stride) * TILE < rows)
+      issue_tile<MODE, KP>(a, (tile + stride) * TILE, rows, Xb + (buf ^ 1) * TILE * S::LDX, S::LDX,
+                           Ib + ((ring + 1) % 3) * 2 * TILE);
+    else
+      cp_async_commit();
     float acc[8][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
 #pragma unroll
     for (int kt = 0; kt < KP / 16; ++kt) {
       uint32_t af[4];
-      frag_a_rm(af, X, S::LDX, m0, kt * 16);
+      ldsm_a(af, X, S::LDX, m0, kt * 16);
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        uint32_t bfr[2];
-        frag_b_nk(bfr, W1t, S::LDX, kt * 16, nt * 8);
-        mma16816(acc[nt], af, bfr);
+      for (int nt = 0; nt < 8; nt += 2) {
+        uint32_t bq[4];
+        ldsm_b2(bq, W1t, S::LDX, kt * 16, nt * 8);
+        mma16816(acc[nt], af, bq);
+        mma16816(acc[nt + 1], af, bq + 2);
       }
     }
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       int c = nt * 8 + 2 * t;
-      A1[(m0 + g) * S::LDH + c] = __float2bfloat16(silu(acc[nt][0] + B1[c]));
-      A1[(m0 + g) * S::LDH + c + 1] = __float2bfloat16(silu(acc[nt][1] + B1[c + 1]));
-      A1[(m0 + g + 8) * S::LDH + c] = __float2bfloat16(silu(acc[nt][2] + B1[c]));
-      A1[(m0 + g + 8) * S::LDH + c + 1] = __float2bfloat16(silu(acc[nt][3] + B1[c + 1]));
+      *reinterpret_cast<__nv_bfloat162*>(A1 + (m0 + g) * S::LDH + c) =
+          __floats2bfloat162_rn(silu(acc[nt][0] + B1[c]), silu(acc[nt][1] + B1[c + 1]));
+      *reinterpret_cast<__nv_bfloat162*>(A1 + (m0 + g + 8) * S::LDH + c) =
+          __floats2bfloat162_rn(silu(acc[nt][2] + B1[c]), silu(acc[nt][3] + B1[c + 1]));
     }
     __syncwarp();
     float acc2[NP / 8][4];
@@ -220,32 +326,52 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
 #pragma unroll
     for (int kt = 0; kt < HID / 16; ++kt) {
       uint32_t af[4];
-      frag_a_rm(af, A1, S::LDH, m0, kt * 16);
+      ldsm_a(af, A1, S::LDH, m0, kt * 16);
 #pragma unroll
-      for (int nt = 0; nt < NP / 8; ++nt) {
-        uint32_t bfr[2];
-        frag_b_nk(bfr, W2t, S::LDH, kt * 16, nt * 8);
-        mma16816(acc2[nt], af, bfr);
+      for (int nt = 0; nt < NP / 8; nt += 2) {
+        uint32_t bq[4];
+        ldsm_b2(bq, W2t, S::LDH, kt * 16, nt * 8);
+        mma16816(acc2[nt], af, bq);
+        mma16816(acc2[nt + 1], af, bq + 2);
       }
     }
+    __syncwarp();
+    if (a.out_f) {  // decoder: FP32 outputs, few columns
 #pragma unroll
-    for (int nt = 0; nt < NP / 8; ++nt) {
+      for (int nt = 0; nt < NP / 8; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int r = m0 + g + (q >> 1) * 8, o = nt * 8 + 2 * t + (q & 1);
+          int64_t row = row0 + r;
+          if (row < rows && o < a.nout) a.out_f[row * a.nout + o] = acc2[nt][q] + B2[o];
+        }
+    } else {
+      // bias and residual (first 64 staged columns are e for EDGE, h for NODE)
+#pragma unroll
+      for (int nt = 0; nt < NP / 8; ++nt)
+#pragma unroll
+        for (int hq = 0; hq < 2; ++hq) {
+          int r = m0 + g + hq * 8, o = nt * 8 + 2 * t;
+          float v0 = acc2[nt][2 * hq] + B2[o], v1 = acc2[nt][2 * hq + 1] + B2[o + 1];
+          if (MODE == MODE_EDGE || MODE == MODE_NODE) {
+            __nv_bfloat162 res = *reinterpret_cast<const __nv_bfloat162*>(X + r * S::LDX + o);
+            v0 += __bfloat162float(res.x);
+            v1 += __bfloat162float(res.y);
+          }
+          *reinterpret_cast<__nv_bfloat162*>(A1 + r * S::LDH + o) = __floats2bfloat162_rn(v0, v1);
+        }
+      __syncwarp();
+      // the warp's 16 output rows, 8 chunks of 16 bytes each
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        int r = m0 + g + (q >> 1) * 8, o = nt * 8 + 2 * t + (q & 1);
+        int idx = q * 32 + lane, r = m0 + (idx >> 3), c8 = idx & 7;
         int64_t row = row0 + r;
-        if (row >= rows || o >= a.nout) continue;
-        float v = acc2[nt][q] + B2[o];
-        if (a.out_f) {
-          a.out_f[row * a.nout + o] = v;
-        } else {
-          if (MODE == MODE_EDGE) v += __bfloat162float(a.e[row * HID + o]);
-          if (MODE == MODE_NODE) v += __bfloat162float(a.h[row * HID + o]);
-          a.out_bf[row * HID + o] = __float2bfloat16(v);
-        }
+        if (row < rows)
+          *reinterpret_cast<uint4*>(a.out_bf + row * HID + c8 * 8) =
+              *reinterpret_cast<const uint4*>(A1 + r * S::LDH + c8 * 8);
       }
     }
-    __syncthreads();
+    __syncthreads();  // X[buf] is refilled by the next-but-one prefetch
   }
 }
 
@@ -480,7 +606,7 @@ __global__ void k_sg_count(Params p, State s, Work w, int64_t n, int64_t nf, uin
 }
 
 __global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, const uint32_t* row_ptr,
-                          uint32_t* recv, uint32_t* send, bf16* efeat) {
+                          uint32_t* recv, uint32_t* send, bf16* efeat, const float* node_std) {
   int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gi >= nf) return;
   uint32_t i = w.fluid_list[gi];
@@ -499,8 +625,12 @@ __global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, cons
     send[e] = j;
     bf16* f = efeat + e * FEAT;
     for (int d = 0; d < FEAT; ++d) f[d] = __float2bfloat16(0.f);
-    for (int d = 0; d < p.dim; ++d) f[d] = __float2bfloat16((float)(r[d] * inv_h));
+    for (int d = 0; d < p.dim; ++d) {
+      f[d] = __float2bfloat16((float)(r[d] * inv_h));
+      f[p.dim + 1 + d] = __float2bfloat16((float)((s.u[d * n + j] - s.u[d * n + i]) / node_std[d]));
+    }
     f[p.dim] = __float2bfloat16((float)(sqrt(r2) * inv_h));
+    f[2 * p.dim + 1] = __float2bfloat16((float)((s.phi[j] - s.phi[i]) / node_std[p.dim + 1]));
     ++e;
   }
 }
@@ -655,7 +785,7 @@ void build_blocks(wbsph_surrogate s) {
     s->blocks.push_back(b);
   };
   add(d + 3, HID);
-  add(d + 1, HID);
+  add(2 * d + 2, HID);
   for (int l = 0; l < s->layers; ++l) {
     add(3 * HID, HID);
     add(2 * HID, HID);
@@ -732,7 +862,7 @@ int ensure_edges(wbsph_surrogate s, int64_t E) {
 
 template <int MODE, int KP, int NP>
 void launch_fwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
-  size_t sm = Smem<KP, NP>::fwd_bytes;
+  size_t sm = FwdSmem<MODE, KP, NP>::bytes;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_mlp_fwd<MODE, KP, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -783,7 +913,8 @@ int build_graph(wbsph_surrogate s, const Params& p, const State& st, const Work&
   rc = ensure_edges(s, E);
   if (rc) return rc;
   if (nf > 0)
-    k_sg_fill<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p, st, w, n, nf, s->row_ptr, s->recv, s->send, s->efeat);
+    k_sg_fill<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p, st, w, n, nf, s->row_ptr, s->recv, s->send, s->efeat,
+                                                         s->norm + 8);
   k_sg_nodes<<<(unsigned)div_up(n > 0 ? n : 1, 256), 256, 0, cs>>>(p, st, n, s->norm, s->norm + 8, s->nfeat);
   return WBSPH_OK;
 }

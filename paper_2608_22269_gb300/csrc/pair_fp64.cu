@@ -37,17 +37,31 @@ __global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s,
   const uint32_t i = active ? w.dummy_list[gi] : 0u;
   const uint32_t key = active ? w.key[i] : 0u;
   const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  // One scan: a candidate is evaluated exactly when its FP32 distance lies
-  // within the rounding band of the running FP32 minimum. A candidate skipped
-  // at some point lies outside the band of the final minimum too, so it
-  // cannot be the exact nearest.
+  // One FP32 scan keeps the (at most 4) fluid candidates whose FP32 distance
+  // lies within the rounding band of the running FP32 minimum; the exact
+  // FP64 distances decide among those left within the band of the final
+  // minimum. A candidate dropped at any point lies outside the band of the
+  // final minimum too, so it cannot be the exact nearest. If more than 4
+  // candidates share the band, a second scan evaluates all of them exactly.
+  constexpr int KEEP = 4;
   float best_f = INFINITY;
-  uint32_t best = kEmpty, best_oid = kEmpty;
-  double best_r2 = 0.0;
+  uint32_t kj[KEEP] = {0u, 0u, 0u, 0u};
+  float kr[KEEP] = {INFINITY, INFINITY, INFINITY, INFINITY};  // slot free when > band limit
+  bool spill = false;
   warp_scan_candidates(p, w, active, i, key, xs, stage[warp], [&](uint32_t j, float r2f, float jtype) {
     if (jtype != 0.f) return;  // fluid neighbours only
     if (r2f > best_f + p.nearest_band_r2) return;
-    if (r2f < best_f) best_f = r2f;
+    best_f = fminf(best_f, r2f);
+    const float lim_now = best_f + p.nearest_band_r2;
+    bool placed = false;
+#pragma unroll
+    for (int q = 0; q < KEEP; ++q)
+      if (!placed && kr[q] > lim_now) { kr[q] = r2f; kj[q] = j; placed = true; }
+    spill |= !placed;
+  });
+  uint32_t best = kEmpty, best_oid = kEmpty;
+  double best_r2 = 0.0;
+  auto consider = [&](uint32_t j) {
     double d0 = __dsub_rn(s.x[j], s.x[i]);
     double r2 = __dmul_rn(d0, d0);
     double d1 = __dsub_rn(s.x[n + j], s.x[n + i]);
@@ -61,7 +75,18 @@ __global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s,
     if (best == kEmpty || r2 < best_r2 || (r2 == best_r2 && o < best_oid)) {
       best = j; best_r2 = r2; best_oid = o;
     }
-  });
+  };
+  const float lim = best_f + p.nearest_band_r2;
+  if (!spill && best_f < INFINITY) {  // empty slots hold r = inf and no index
+#pragma unroll
+    for (int q = 0; q < KEEP; ++q)
+      if (kr[q] <= lim) consider(kj[q]);
+  }
+  if (__any_sync(0xffffffffu, spill)) {
+    warp_scan_candidates(p, w, active && spill, i, key, xs, stage[warp], [&](uint32_t j, float r2f, float jtype) {
+      if (jtype == 0.f && r2f <= lim) consider(j);
+    });
+  }
   if (!active || best == kEmpty) return;
   double fs = forcing_factor(p, stage_time(w, stage2));
   double gdot = 0.0, un = 0.0;
@@ -84,6 +109,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_volumes_umax(Params p, State s,
       for (int k = 0; k < p.dim; ++k) umax2 += s.u[k * n + i] * s.u[k * n + i];
     double v = s.mass[i] / eos_density(p, s.phi[i]);
     w.vol[i] = v;
+    w.volc[i] = p.neg_dwdr_over_r_coef * v;  // -W'(r)/r V = volc (1 - q/2)^3
     if (!isfinite(v)) atomicOr(w.status, kStatNaN);
   }
   // block max of |U|^2, then one atomic per block on the bit pattern
@@ -228,16 +254,24 @@ __global__ void __launch_bounds__(PAIR_THREADS, 4)
     double r[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) r[c] = __dsub_rn(s.x[c * n + j], xi[c]);
-    double r2 = __dmul_rn(r[0], r[0]);
+    // r^2 with contraction; the exact (uncontracted) test of Algorithm 1 is
+    // evaluated only when r^2 lies within a few ulps of (2h)^2
+    double r2 = r[0] * r[0];
 #pragma unroll
-    for (int c = 1; c < DIM; ++c) r2 = __dadd_rn(r2, __dmul_rn(r[c], r[c]));
-    if (!(r2 <= p.four_h2 && r2 > 0.0)) continue;
+    for (int c = 1; c < DIM; ++c) r2 = fma(r[c], r[c], r2);
+    if (r2 > p.four_h2_lo) {
+      double e2 = __dmul_rn(r[0], r[0]);
+#pragma unroll
+      for (int c = 1; c < DIM; ++c) e2 = __dadd_rn(e2, __dmul_rn(r[c], r[c]));
+      if (!(e2 <= p.four_h2)) continue;
+    }
+    if (!(r2 > 0.0)) continue;
     ++npairs;
     double inv_r = rsqrt_nr1(r2);
     double rr = r2 * inv_r;
     double t = fma(-rr, p.inv_two_h, 1.0);
-    double t3 = t * t * t;
-    double g = p.neg_dwdr_over_r_coef * t3 * w.vol[j];
+    double t2 = t * t;
+    double g = t2 * (t * w.volc[j]);
     double gr[DIM], du[DIM];
     double dun = 0.0;
 #pragma unroll
@@ -276,10 +310,15 @@ __global__ void __launch_bounds__(PAIR_THREADS, 4)
       for (int c = 0; c < DIM; ++c) Lam[c] = fma(du[c], g, Lam[c]);
     }
     if (p.use_pst) {
-      double q21 = fma(rr, p.two_over_h, 1.0);               // 2q + 1
-      double ratio = p.pst_alpha_over_wdx * (t3 * t) * q21;  // W_ij / W(dx)
-      double rn = pst4 ? (ratio * ratio) * (ratio * ratio) : pow(ratio, p.pst_n);
-      double f = fma(p.pst_R, rn, 1.0);
+      double q21 = fma(rr, p.two_over_h, 1.0);  // 2q + 1
+      double v = (t2 * t2) * q21;               // W_ij / W(dx) = pst_alpha_over_wdx * v
+      double f;
+      if (pst4) {
+        double v2 = v * v;
+        f = fma(p.pst_R_a4, v2 * v2, 1.0);      // 1 + R (W_ij / W(dx))^4
+      } else {
+        f = fma(p.pst_R, pow(p.pst_alpha_over_wdx * v, p.pst_n), 1.0);
+      }
 #pragma unroll
       for (int c = 0; c < DIM; ++c) P[c] = fma(f, gr[c], P[c]);
     }

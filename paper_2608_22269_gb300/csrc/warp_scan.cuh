@@ -3,9 +3,9 @@
 // neighbour loop of Algorithm 1).
 //
 // The 32 lanes of a warp hold particles that are consecutive in cell-key
-// order, so they sit in one or two x-runs of cells. Lanes are grouped by
-// their (y, z) cell row; for each group the union of the lanes' 3^d
-// neighbourhoods is 3^(d-1) rows times one x-run [min ix - 1, max ix + 1],
+// order, so they sit in one or a few x-runs of cells. Lanes are grouped by
+// (y, z) cell row and contiguous x cells; for each group the union of the
+// lanes' 3^d neighbourhoods is 3^(d-1) rows times one x-run [min ix - 1, max ix + 1],
 // each a contiguous sorted index range. The warp stages 32 candidate
 // positions at a time into shared memory and every lane of the group tests
 // all of them (uniform loop, broadcast reads), instead of each lane walking
@@ -44,11 +44,20 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Work
                                                      float4* stage, F&& f) {
   const int lane = threadIdx.x & 31;
   LaneCell c = lane_cell(p, active ? key : 0u);
+  // groups: consecutive active lanes of one cell row whose x cells are no
+  // more than 2 apart (a row of wall particles can hold both ends of a row)
+  int prev_row = __shfl_up_sync(0xffffffffu, c.row, 1);
+  int prev_ix = __shfl_up_sync(0xffffffffu, c.ix, 1);
+  bool prev_active = __shfl_up_sync(0xffffffffu, (int)active, 1) != 0;
+  bool starts = active && (lane == 0 || !prev_active || prev_row != c.row || c.ix > prev_ix + 2);
+  unsigned starts_mask = __ballot_sync(0xffffffffu, starts);
+  int gid = __popc(starts_mask & ((2u << lane) - 1u));  // group number (1-based) of this lane
   unsigned pending = __ballot_sync(0xffffffffu, active);
   while (pending) {
     int leader = __ffs(pending) - 1;
+    int ggid = __shfl_sync(0xffffffffu, gid, leader);
     int grow = __shfl_sync(0xffffffffu, c.row, leader);
-    bool in_g = active && c.row == grow;
+    bool in_g = active && gid == ggid;
     unsigned gmask = __ballot_sync(0xffffffffu, in_g);
     pending &= ~gmask;
     int xlo = __reduce_min_sync(0xffffffffu, in_g ? c.ix : INT_MAX);

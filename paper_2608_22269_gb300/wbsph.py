@@ -144,13 +144,17 @@ class Sim:
     memory comes from PyTorch's caching allocator on the current stream."""
 
     def __init__(self, params: dict, precision: int = FP64, water_height: float = 0.0,
-                 device: int = 0, use_torch_allocator: bool = True):
+                 device: int = 0, use_torch_allocator: bool = True, stream=None):
+        """The handle works on its own CUDA stream (a new torch stream unless
+        ``stream`` is given), so that its steps can be replayed as CUDA
+        graphs; the binding orders that stream against torch's current
+        stream wherever device tensors are exchanged."""
         import torch
         self._torch = torch
         self.lib = load()
         self.dim = int(params["dim"])
         self.device = device
-        self.stream = torch.cuda.current_stream(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device)
         cfg = make_config(params, precision, C.c_void_p(self.stream.cuda_stream), device,
                           water_height)
         if use_torch_allocator:
@@ -203,6 +207,8 @@ class Sim:
             mass = None if mass is None else np.ascontiguousarray(mass, dtype=np.float64)
         n = int(phi.shape[0])
         self._keep = (x, u, phi, type, normal, mass)
+        if dev:
+            self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
         self._check(self.lib.wbsph_set_particles(self.h, n, _ptr(x), _ptr(u), _ptr(phi), _ptr(mass),
                                                  _ptr(type), _ptr(normal), DEVICE if dev else HOST))
         self.n = n
@@ -231,7 +237,11 @@ class Sim:
         if out is None:
             out = np.empty(shape, dtype=np.float64)
         where = HOST if isinstance(out, np.ndarray) or not out.is_cuda else DEVICE
+        if where == DEVICE:
+            self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
         self._check(self.lib.wbsph_get_fields(self.h, FIELDS[field], _ptr(out), where))
+        if where == DEVICE:
+            self._torch.cuda.current_stream(self.device).wait_stream(self.stream)
         return out
 
     def cell_keys(self):
@@ -256,8 +266,11 @@ class Sim:
         """wbsph_sort_cells_noalloc on device tensors: x (dim, n) float64,
         keys_sorted / ids_sorted (n,) 32-bit. Allocates no device memory."""
         n = int(x.shape[1])
+        cur = self._torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
         self._check(self.lib.wbsph_sort_cells_noalloc(self.h, _ptr(x), n, _ptr(keys_sorted),
                                                       _ptr(ids_sorted)))
+        cur.wait_stream(self.stream)
         return keys_sorted, ids_sorted
 
     def set_profiling(self, on=True):

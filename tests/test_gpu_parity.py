@@ -225,3 +225,32 @@ def test_profile_and_stats_count_launches():
     assert prof["pair"][1] == 4 and prof["pair"][0] > 0
     st = sim.stats()
     assert st["launches"] > 20 and st["steps"] == 2
+
+
+def test_non_finite_input_is_reported():
+    from paper_2608_22269_gb300 import wbsph
+    sc = S.dam_break_2d(dx=0.02, width=1.0, column=(0.3, 0.2))
+    bad = sc.copy()
+    bad.phi[5] = np.nan
+    sim = _sim(bad)
+    sim.step(1)
+    with pytest.raises(wbsph.WbsphError) as ei:
+        sim.sync()
+    assert ei.value.code == -6
+
+
+def test_restart_from_fields_continues_the_run():
+    """get_fields + set_particles restart: x, U, phi and masses carry the whole
+    state of a flow without forcing (the dummies are rebuilt every stage)."""
+    sc = _dynamic(S.dam_break_2d(dx=0.01, width=1.0, column=(0.3, 0.2)))
+    a = _sim(sc)
+    a.step(4)
+    b = _sim(sc)
+    b.step(2)
+    st = {k: b.get(k) for k in ("x", "u", "phi", "mass")}
+    c = _sim(sc)
+    c.set_particles(st["x"], st["u"], st["phi"], sc.type, sc.normal, st["mass"])
+    c.step(2)
+    sk = scales(sc.params, sc.water_height)
+    assert scaled_err(c.get("x"), a.get("x"), sk["x"]) <= 1e-13
+    assert scaled_err(c.get("u"), a.get("u"), sk["u"]) <= 1e-12

@@ -50,7 +50,7 @@ def test_forward_and_gradient_match_fp64_reference(dim):
     n = sc.n
     fin = dim + 3
     node_in = dbg["node_feat"][:, :fin].astype(np.float64)
-    edge_in = dbg["edge_feat"][:, :dim + 1].astype(np.float64)
+    edge_in = dbg["edge_feat"][:, :2 * dim + 2].astype(np.float64)
     th = mpnn.round_weights_bf16(theta, dim)
     out = mpnn.forward_np(th, dim, node_in, dbg["recv"], dbg["send"], edge_in)
     fid = dbg["fluid_ids"].astype(np.int64)

@@ -1,0 +1,45 @@
+"""Multi-rank logic of bench.py on CPU (gloo, world size 2): replicas are
+independent, the job time is the maximum over ranks, and the reported
+throughput counts the units of every rank."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t = 1.0 + rank  # rank 1 is the slower replica
+    bench.barrier(world)
+    tmax = bench.max_over_ranks(t, world, device="cpu")
+    v = bench.weak_scaling_value(1000.0, world, tmax)
+    out[rank] = (tmax, v)
+    dist.destroy_process_group()
+
+
+def test_two_rank_max_and_weak_scaling():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert out[0] == out[1] == (2.0, 1000.0)

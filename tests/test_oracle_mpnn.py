@@ -23,8 +23,10 @@ def _graph(n=40, dim=2, seed=0, deg=5):
         send += list(js)
     recv, send = np.array(recv), np.array(send)
     r = x[send] - x[recv]
-    edge = np.concatenate([r / 0.1, np.linalg.norm(r, axis=1, keepdims=True) / 0.1], axis=1)
     node = rng.normal(size=(n, dim + 3))
+    du = node[send, :dim] - node[recv, :dim]
+    dphi = node[send, dim + 1:dim + 2] - node[recv, dim + 1:dim + 2]
+    edge = np.concatenate([r / 0.1, np.linalg.norm(r, axis=1, keepdims=True) / 0.1, du, dphi], axis=1)
     return node, recv, send, edge
 
 
