@@ -118,7 +118,8 @@ typedef struct {
 typedef enum {
   WBSPH_K_KEYS = 0, WBSPH_K_SORT = 1, WBSPH_K_REORDER = 2, WBSPH_K_CELLS = 3,
   WBSPH_K_PREPASS = 4, WBSPH_K_PAIR = 5, WBSPH_K_UPDATE = 6, WBSPH_K_OTHER = 7,
-  WBSPH_K_COUNT = 8
+  WBSPH_K_NLIST = 8, /* candidate lists of the pair pass (k_nbr_list) */
+  WBSPH_K_COUNT = 9
 } wbsph_kernel_class;
 
 /* Fill *cfg with the paper's constants (Sec. 4) for dimension dim. */

@@ -23,8 +23,9 @@ using namespace wbsph;
 
 namespace wbsph {
 void launch_mass(const Params& p, const double* phi, double* mass, int64_t n, cudaStream_t st);
-int launch_mixed_stage(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
-                       int stage2, cudaStream_t st);
+int launch_pack_mixed(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
+void launch_pair_mixed(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
+                       cudaStream_t st);
 }
 
 struct ProfEvent {
@@ -459,15 +460,20 @@ static int rates(wbsph_s* h, int stage2) {
     ProfScope ps(h, WBSPH_K_OTHER);
     launch_time_step(h->P, h->W, st);
   }
+  const bool mixed = h->cfg.precision == WBSPH_MIXED;
+  if (mixed) {
+    ProfScope ps(h, WBSPH_K_PREPASS);
+    int rc = launch_pack_mixed(h->P, h->A, h->W, n, st);
+    if (rc) return fail(h, rc, "mixed path: grid too large for packed cell coordinates");
+  }
+  {
+    ProfScope ps(h, WBSPH_K_NLIST);
+    launch_nbr_list(h->P, h->W, n, h->nf, st);
+  }
   {
     ProfScope ps(h, WBSPH_K_PAIR);
-    if (h->cfg.precision == WBSPH_MIXED) {
-      int rc = launch_mixed_stage(h->P, h->A, h->W, n, h->nf, stage2, st);
-      if (rc) return fail(h, rc, "mixed path: grid too large for packed cell coordinates");
-    } else {
-      launch_nbr_list(h->P, h->W, n, h->nf, st);
-      launch_pair_fp64(h->P, h->A, h->W, n, h->nf, stage2, st);
-    }
+    if (mixed) launch_pair_mixed(h->P, h->A, h->W, n, h->nf, stage2, st);
+    else launch_pair_fp64(h->P, h->A, h->W, n, h->nf, stage2, st);
   }
   h->launches += (n ? 1 : 0) + (h->nd ? 1 : 0) + (stage2 ? 0 : 1) + (h->nf ? 2 : 0) +
                  (h->cfg.precision == WBSPH_MIXED && n ? 1 : 0);

@@ -43,9 +43,12 @@ void launch_cell_keys(const Params& p, const State& s, const Work& w, int64_t n,
 
 // ---------------------------------------------------------------------------
 // Stable LSD radix sort of 32-bit keys with 32-bit values, 8-bit digits.
-// Per pass: tile histograms (digit-major table), one exclusive scan of the
-// table, then a scatter that ranks equal digits inside a tile in index order
-// (warp match + per-warp counts), which keeps the sort stable.
+// Per pass: tile histograms (digit-major table: row d holds digit d's count
+// in every tile), an exclusive scan of every row by its own block plus the
+// row totals, then a scatter that adds the exclusive scan of the 256 row
+// totals (done in shared memory by every scatter block) and ranks equal
+// digits inside a tile in index order (warp match + per-warp counts), which
+// keeps the sort stable.
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
@@ -93,15 +96,65 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_exclusive(uint32_t* data,
   }
 }
 
+// Exclusive scan of each digit row of the histogram table in place (block
+// d scans row d, RS_THREADS entries per round, coalesced); totals[d] gets the
+// row's sum. Rows of digits above `mask` are all zero and are skipped.
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scan_rows(uint32_t* __restrict__ hist, int64_t nblocks,
+                                                               uint32_t* __restrict__ totals) {
+  __shared__ uint32_t wsum[RS_WARPS];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint32_t* row = hist + (int64_t)blockIdx.x * nblocks;
+  uint32_t carry = 0;
+  for (int64_t c0 = 0; c0 < nblocks; c0 += RS_THREADS) {
+    int64_t i = c0 + t;
+    uint32_t v = i < nblocks ? row[i] : 0u;
+    uint32_t inc = v;  // inclusive warp scan
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += o;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0, all = 0;
+#pragma unroll
+    for (int k = 0; k < RS_WARPS; ++k) {
+      uint32_t x = wsum[k];
+      wpre += k < warp ? x : 0u;
+      all += x;
+    }
+    if (i < nblocks) row[i] = carry + wpre + inc - v;
+    carry += all;
+    __syncthreads();
+  }
+  if (t == 0) totals[blockIdx.x] = carry;
+}
+
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift,
-    uint32_t mask, const uint32_t* __restrict__ hist, int64_t nblocks) {
+    uint32_t mask, const uint32_t* __restrict__ hist, int64_t nblocks,
+    const uint32_t* __restrict__ totals) {
   __shared__ uint32_t offs[256];
   __shared__ uint32_t wcnt[RS_WARPS][256];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  offs[t] = hist[(int64_t)t * nblocks + blockIdx.x];
+  {
+    // digit base = exclusive scan of the row totals (digits above mask: 0)
+    uint32_t v = t <= (int)mask ? totals[t] : 0u;
+    uint32_t inc = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += o;
+    }
+    if (lane == 31) wcnt[0][warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int k = 0; k < warp; ++k) wpre += wcnt[0][k];
+    offs[t] = wpre + inc - v + (t <= (int)mask ? hist[(int64_t)t * nblocks + blockIdx.x] : 0u);
+    __syncthreads();
+  }
   int64_t base = blockIdx.x * (int64_t)RS_TILE;
   for (int r = 0; r < RS_ITEMS; ++r) {
 #pragma unroll
@@ -134,7 +187,8 @@ void launch_scan_exclusive(uint32_t* data, int64_t total, cudaStream_t st) {
   k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(data, total);
 }
 
-int radix_sort_scratch_words(int64_t n) { return (int)(256 * div_up(n > 0 ? n : 1, RS_TILE)); }
+// histogram table (256 rows x tiles) followed by the 256 row totals
+int radix_sort_scratch_words(int64_t n) { return (int)(256 * div_up(n > 0 ? n : 1, RS_TILE) + 256); }
 
 static int bits_for(int64_t ncells) {
   int b = 1;
@@ -150,10 +204,11 @@ void launch_radix_sort(const Params& p, Work& w, int64_t n, cudaStream_t st, int
   for (int shift = 0; shift < bits; shift += 8) {
     int b = bits - shift < 8 ? bits - shift : 8;
     uint32_t mask = (1u << b) - 1u;
+    uint32_t* totals = w.hist + 256 * nblocks;
     k_radix_hist<<<(unsigned)nblocks, RS_THREADS, 0, st>>>(w.key, n, shift, mask, w.hist, nblocks);
-    k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(w.hist, 256 * nblocks);
+    k_radix_scan_rows<<<mask + 1u, RS_THREADS, 0, st>>>(w.hist, nblocks, totals);
     k_radix_scatter<<<(unsigned)nblocks, RS_THREADS, 0, st>>>(w.key, vin, w.key_alt, w.perm_alt, n,
-                                                             shift, mask, w.hist, nblocks);
+                                                             shift, mask, w.hist, nblocks, totals);
     *launches += 3;
     uint32_t* tk = w.key; w.key = w.key_alt; w.key_alt = tk;
     uint32_t* tp = w.perm; w.perm = w.perm_alt; w.perm_alt = tp;

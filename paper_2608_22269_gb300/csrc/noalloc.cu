@@ -27,7 +27,7 @@ namespace {
 
 constexpr int64_t kMaxN = WBSPH_NOALLOC_MAX_N;
 constexpr int64_t kTile = 4096;  // keys per radix tile (256 threads x 16)
-constexpr int64_t kHistWords = 256 * ((kMaxN + kTile - 1) / kTile);
+constexpr int64_t kHistWords = 256 * ((kMaxN + kTile - 1) / kTile) + 256;  // table + row totals
 // layout (32-bit words): [keys kMaxN][ids kMaxN][histograms kHistWords][status 64]
 constexpr int64_t kScratchWords = 2 * kMaxN + kHistWords + 64;
 

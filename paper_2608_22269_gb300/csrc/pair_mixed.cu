@@ -78,11 +78,14 @@ __device__ __forceinline__ float lambda_min_3f(float a00, float a01, float a02, 
 }
 
 constexpr int MX_THREADS = 128;
+#ifndef WBSPH_MX_MIN_BLOCKS
+#define WBSPH_MX_MIN_BLOCKS 3  // resident blocks per SM the register budget is sized for
+#endif
 
 // Pair sums over the candidate lists built by k_nbr_list (the same lists as
 // the FP64 pass); the neighbour test is the FP32 cell-relative distance.
 template <int DIM>
-__global__ void __launch_bounds__(MX_THREADS, 4)
+__global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
     k_pair_mixed(Params p, State s, Work w, int64_t n, int64_t nf, int stage2, const float4* __restrict__ A,
                  const float4* __restrict__ B, const uint32_t* __restrict__ Cc) {
   const int lane = threadIdx.x & 31;
@@ -114,11 +117,24 @@ __global__ void __launch_bounds__(MX_THREADS, 4)
   unsigned npairs = 0;
   const int maxc = __reduce_max_sync(0xffffffffu, cnt);
   const uint32_t* lst = w.nbr + gi;
+  // software pipeline: the packed data of entry k + 1 and the index of
+  // entry k + 2 are loaded while entry k is summed (the loop is latency
+  // bound on these dependent gathers, not on the FP32 pipe)
+  float4 An = make_float4(0.f, 0.f, 0.f, 0.f), Bn = An;
+  uint32_t cn = 0, jnn = 0;
+  if (cnt > 0) {
+    uint32_t j0 = __ldg(lst);
+    An = A[j0]; Bn = B[j0]; cn = Cc[j0];
+  }
+  if (cnt > 1) jnn = __ldg(lst + nf);
   for (int k = 0; k < maxc; ++k) {
     if (k >= cnt) continue;
-    uint32_t j = __ldg(lst + (int64_t)k * nf);
-    float4 Aj = A[j], Bj = B[j];
-    uint32_t cj = Cc[j];
+    const float4 Aj = An, Bj = Bn;
+    const uint32_t cj = cn;
+    if (k + 1 < cnt) {
+      An = A[jnn]; Bn = B[jnn]; cn = Cc[jnn];
+      if (k + 2 < cnt) jnn = __ldg(lst + (int64_t)(k + 2) * nf);
+    }
     float r[DIM], du[DIM];
     r[0] = fmaf((float)((int)(cj & 2047u) - cix), R, Aj.x - Ai.x);
     r[1] = fmaf((float)((int)((cj >> 11) & 2047u) - ciy), R, Aj.y - Ai.y);
@@ -268,17 +284,22 @@ __global__ void __launch_bounds__(MX_THREADS, 4)
   if (bad) atomicOr(w.status, kStatNaN);
 }
 
-int launch_mixed_stage(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
-                       int stage2, cudaStream_t st) {
+// Packed FP32 copies of the stage state (k_pack_mixed); fails when the
+// grid is too large for the packed cell coordinates (11/11/10 bits).
+int launch_pack_mixed(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st) {
   if (n == 0) return 0;
-  if (p.nc[0] > 2048 || p.nc[1] > 2048 || p.nc[2] > 1024) return WBSPH_E_INVAL;  // packed cell coords
+  if (p.nc[0] > 2048 || p.nc[1] > 2048 || p.nc[2] > 1024) return WBSPH_E_INVAL;
   k_pack_mixed<<<(unsigned)div_up(n, 256), 256, 0, st>>>(p, s, w, n, w.packA, w.packB, w.packC);
-  if (nf == 0) return 0;
-  launch_nbr_list(p, w, n, nf, st);
+  return 0;
+}
+
+// Pair sums over the candidate lists of k_nbr_list (built before this).
+void launch_pair_mixed(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
+                       cudaStream_t st) {
+  if (n == 0 || nf == 0) return;
   unsigned blocks = (unsigned)div_up(nf, MX_THREADS);
   if (p.dim == 2) k_pair_mixed<2><<<blocks, MX_THREADS, 0, st>>>(p, s, w, n, nf, stage2, w.packA, w.packB, w.packC);
   else k_pair_mixed<3><<<blocks, MX_THREADS, 0, st>>>(p, s, w, n, nf, stage2, w.packA, w.packB, w.packC);
-  return 0;
 }
 
 }  // namespace wbsph

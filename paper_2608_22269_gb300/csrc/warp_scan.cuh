@@ -74,16 +74,26 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Work
         uint32_t beg = w.cell_lb[base + x0], end = w.cell_lb[base + x1 + 1];
         for (uint32_t c0 = beg; c0 < end; c0 += 32) {
           uint32_t idx = c0 + lane;
-          if (idx < end) stage[lane] = __ldg(&w.xf[idx]);
+          // slots past the run hold a point at infinity, which no test passes
+          stage[lane] = idx < end ? __ldg(&w.xf[idx]) : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
           __syncwarp();
-          int m = end - c0 < 32u ? (int)(end - c0) : 32;
           if (in_g) {
-            for (int k = 0; k < m; ++k) {
+            // independent tests of all 32 staged candidates, then the hits in order
+            unsigned hits = 0u;
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
               float4 q = stage[k];
               float dx = q.x - xs.x, dy = q.y - xs.y, dz = q.z - xs.z;
               float r2 = dx * dx + dy * dy + dz * dz;
-              uint32_t j = c0 + k;
-              if (r2 <= p.prefilter_r2 && j != self) f(j, r2, q.w);
+              hits |= (r2 <= p.prefilter_r2 ? 1u : 0u) << k;
+            }
+            if (self - c0 < 32u) hits &= ~(1u << (self - c0));
+            while (hits) {
+              int k = __ffs(hits) - 1;
+              hits &= hits - 1u;
+              float4 q = stage[k];
+              float dx = q.x - xs.x, dy = q.y - xs.y, dz = q.z - xs.z;
+              f(c0 + k, dx * dx + dy * dy + dz * dz, q.w);
             }
           }
           __syncwarp();

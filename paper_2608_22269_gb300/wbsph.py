@@ -24,7 +24,7 @@ HOST, DEVICE = 0, 1
 FIELDS = {"x": 0, "u": 1, "phi": 2, "rho": 3, "p": 4, "dudt": 5, "dphidt": 6, "dushift": 7,
           "lambda": 8, "mass": 9, "vol": 10}
 VECTOR_FIELDS = {"x", "u", "dudt", "dushift"}
-KERNEL_CLASSES = ["keys", "sort", "reorder", "cells", "prepass", "pair", "update", "other"]
+KERNEL_CLASSES = ["keys", "sort", "reorder", "cells", "prepass", "pair", "update", "other", "nlist"]
 
 #: every symbol declared in include/wbsph.h
 SYMBOLS = ["wbsph_config_default", "wbsph_create", "wbsph_set_particles", "wbsph_build_neighbors",
@@ -277,8 +277,8 @@ class Sim:
         self._check(self.lib.wbsph_set_profiling(self.h, int(on)))
 
     def profile(self, reset=False) -> dict:
-        ms = (C.c_double * 8)()
-        cnt = (C.c_int64 * 8)()
+        ms = (C.c_double * len(KERNEL_CLASSES))()
+        cnt = (C.c_int64 * len(KERNEL_CLASSES))()
         self._check(self.lib.wbsph_get_profile(self.h, ms, cnt, int(reset)))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
 

@@ -60,3 +60,14 @@ def test_create_rejects_bad_configs_without_a_gpu(lib):
     cfg.domain_max[0] = cfg.domain_min[0]
     assert L.wbsph_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
     assert L.wbsph_step(None, 1) == -1
+
+
+def test_binding_kernel_classes_match_the_header():
+    """The profile arrays the binding passes hold WBSPH_K_COUNT entries, in
+    the order of the wbsph_kernel_class enum."""
+    from paper_2608_22269_gb300 import wbsph
+    src = open(os.path.join(ROOT, "include", "wbsph.h")).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"WBSPH_K_(\w+)\s*=\s*(\d+)", src))
+    count = enum.pop("COUNT")
+    assert len(wbsph.KERNEL_CLASSES) == count
+    assert sorted(enum, key=enum.get) == [k.upper() for k in wbsph.KERNEL_CLASSES]

@@ -223,6 +223,7 @@ def test_profile_and_stats_count_launches():
     sim.step(2)
     prof = sim.profile(reset=True)
     assert prof["pair"][1] == 4 and prof["pair"][0] > 0
+    assert prof["nlist"][1] == 4 and prof["nlist"][0] > 0
     st = sim.stats()
     assert st["launches"] > 20 and st["steps"] == 2
 
