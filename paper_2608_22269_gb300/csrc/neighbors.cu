@@ -4,6 +4,7 @@
 // lower-bound table giving the sorted index range of any run of cells.
 #include "common.cuh"
 #include "neighbor_iter.cuh"
+#include "warp_scan.cuh"
 
 namespace wbsph {
 
@@ -331,44 +332,58 @@ void launch_fluid_list(const State& s, const Work& w, int64_t n, int64_t nd, cud
 
 // ---------------------------------------------------------------------------
 // Test hook: the neighbour lists themselves (all particle types), with the
-// same candidate enumeration and exact FP64 test as the pair pass.
+// same warp-cooperative candidate enumeration (warp_scan_candidates) as the
+// pair pass and the exact FP64 test of Algorithm 1.
 // ---------------------------------------------------------------------------
-__global__ void k_count_neighbors(Params p, State s, Work w, int64_t n, uint32_t* counts) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+template <int DIM>
+__global__ void __launch_bounds__(128) k_count_neighbors(Params p, State s, Work w, int64_t n,
+                                                        uint32_t* counts) {
+  __shared__ float4 stage[4][32];
+  __shared__ uint32_t sidx[4][32];
+  const int warp = threadIdx.x >> 5;
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool active = gi < n;
+  const uint32_t i = active ? (uint32_t)gi : 0u;
+  const uint32_t key = active ? w.key[i] : 0u;
+  const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t c = 0;
-  CandidateIter it;
-  it.init(p, w, n, (uint32_t)i);
-  uint32_t j;
-  while (it.next(p, w, j)) {
-    if (exact_neighbor(p, s.x, n, (uint32_t)i, j)) ++c;
-  }
-  counts[s.oid[i]] = c;
+  warp_scan_candidates<DIM>(p, w, active, i, key, xs, stage[warp], sidx[warp], [&](uint32_t j, float, float) {
+    if (exact_neighbor(p, s.x, n, i, j)) ++c;
+  });
+  if (active) counts[s.oid[i]] = c;
 }
 
-__global__ void k_fill_neighbors(Params p, State s, Work w, int64_t n, const int64_t* row_ptr,
-                                 int32_t* cols) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t o = row_ptr[s.oid[i]];
-  CandidateIter it;
-  it.init(p, w, n, (uint32_t)i);
-  uint32_t j;
-  while (it.next(p, w, j)) {
-    if (exact_neighbor(p, s.x, n, (uint32_t)i, j)) cols[o++] = (int32_t)s.oid[j];
-  }
+template <int DIM>
+__global__ void __launch_bounds__(128) k_fill_neighbors(Params p, State s, Work w, int64_t n,
+                                                       const int64_t* row_ptr, int32_t* cols) {
+  __shared__ float4 stage[4][32];
+  __shared__ uint32_t sidx[4][32];
+  const int warp = threadIdx.x >> 5;
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool active = gi < n;
+  const uint32_t i = active ? (uint32_t)gi : 0u;
+  const uint32_t key = active ? w.key[i] : 0u;
+  const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  int64_t o = active ? row_ptr[s.oid[i]] : 0;
+  warp_scan_candidates<DIM>(p, w, active, i, key, xs, stage[warp], sidx[warp], [&](uint32_t j, float, float) {
+    if (exact_neighbor(p, s.x, n, i, j)) cols[o++] = (int32_t)s.oid[j];
+  });
 }
 
 void launch_count_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
                             uint32_t* counts, cudaStream_t st) {
   if (n == 0) return;
-  k_count_neighbors<<<(unsigned)div_up(n, 128), 128, 0, st>>>(p, s, w, n, counts);
+  unsigned blocks = (unsigned)div_up(n, 128);
+  if (p.dim == 3) k_count_neighbors<3><<<blocks, 128, 0, st>>>(p, s, w, n, counts);
+  else k_count_neighbors<2><<<blocks, 128, 0, st>>>(p, s, w, n, counts);
 }
 
 void launch_fill_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
                            const int64_t* row_ptr_by_oid, int32_t* cols, cudaStream_t st) {
   if (n == 0) return;
-  k_fill_neighbors<<<(unsigned)div_up(n, 128), 128, 0, st>>>(p, s, w, n, row_ptr_by_oid, cols);
+  unsigned blocks = (unsigned)div_up(n, 128);
+  if (p.dim == 3) k_fill_neighbors<3><<<blocks, 128, 0, st>>>(p, s, w, n, row_ptr_by_oid, cols);
+  else k_fill_neighbors<2><<<blocks, 128, 0, st>>>(p, s, w, n, row_ptr_by_oid, cols);
 }
 
 }  // namespace wbsph

@@ -28,9 +28,11 @@ namespace wbsph {
 // ---------------------------------------------------------------------------
 constexpr int DUM_THREADS = 128;
 
+template <int DIM>
 __global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s, Work w, int64_t n,
                                                              int64_t nd, int stage2) {
   __shared__ float4 stage[DUM_THREADS / 32][32];
+  __shared__ uint32_t sidx[DUM_THREADS / 32][32];
   const int warp = threadIdx.x >> 5;
   int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool active = gi < nd;
@@ -48,7 +50,8 @@ __global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s,
   uint32_t kj[KEEP] = {0u, 0u, 0u, 0u};
   float kr[KEEP] = {INFINITY, INFINITY, INFINITY, INFINITY};  // slot free when > band limit
   bool spill = false;
-  warp_scan_candidates(p, w, active, i, key, xs, stage[warp], [&](uint32_t j, float r2f, float jtype) {
+  warp_scan_candidates<DIM>(p, w, active, i, key, xs, stage[warp], sidx[warp],
+                            [&](uint32_t j, float r2f, float jtype) {
     if (jtype != 0.f) return;  // fluid neighbours only
     if (r2f > best_f + p.nearest_band_r2) return;
     best_f = fminf(best_f, r2f);
@@ -83,7 +86,8 @@ __global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s,
       if (kr[q] <= lim) consider(kj[q]);
   }
   if (__any_sync(0xffffffffu, spill)) {
-    warp_scan_candidates(p, w, active && spill, i, key, xs, stage[warp], [&](uint32_t j, float r2f, float jtype) {
+    warp_scan_candidates<DIM>(p, w, active && spill, i, key, xs, stage[warp], sidx[warp],
+                              [&](uint32_t j, float r2f, float jtype) {
       if (jtype == 0.f && r2f <= lim) consider(j);
     });
   }
@@ -132,8 +136,11 @@ void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, i
                     int stage2, cudaStream_t st) {
   cudaMemsetAsync(w.umax_bits, 0, sizeof(unsigned long long), st);
   if (n == 0) return;
-  if (nd > 0)
-    k_dummy_update<<<(unsigned)div_up(nd, DUM_THREADS), DUM_THREADS, 0, st>>>(p, s, w, n, nd, stage2);
+  if (nd > 0) {
+    unsigned blocks = (unsigned)div_up(nd, DUM_THREADS);
+    if (p.dim == 3) k_dummy_update<3><<<blocks, DUM_THREADS, 0, st>>>(p, s, w, n, nd, stage2);
+    else k_dummy_update<2><<<blocks, DUM_THREADS, 0, st>>>(p, s, w, n, nd, stage2);
+  }
   k_volumes_umax<<<(unsigned)div_up(n, PRE_THREADS), PRE_THREADS, 0, st>>>(p, s, w, n);
 }
 
@@ -172,20 +179,25 @@ void launch_time_step(const Params& p, const Work& w, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 constexpr int LIST_THREADS = 64;
 
+template <int DIM>
 __global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, Work w, int64_t n, int64_t nf,
-                                                         int kmax) {
+                                                         int kmax, int ks) {
   extern __shared__ float4 smem_f4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4* stage = smem_f4 + warp * 32;
-  uint32_t* my = reinterpret_cast<uint32_t*>(smem_f4 + (LIST_THREADS / 32) * 32) + warp * kmax * 32;
+  uint32_t* sidx = reinterpret_cast<uint32_t*>(smem_f4 + (LIST_THREADS / 32) * 32) + warp * 32;
+  uint32_t* my = reinterpret_cast<uint32_t*>(smem_f4 + (LIST_THREADS / 32) * 32) + LIST_THREADS +
+                 warp * ks * 32;
   int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool active = gi < nf;
   const uint32_t i = active ? w.fluid_list[gi] : 0u;
   const uint32_t key = active ? w.key[i] : 0u;
   const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   int cnt = 0;
-  warp_scan_candidates(p, w, active, i, key, xs, stage, [&](uint32_t j, float, float) {
-    if (cnt < kmax) my[cnt * 32 + lane] = j;
+  warp_scan_candidates<DIM>(p, w, active, i, key, xs, stage, sidx, [&](uint32_t j, float, float) {
+    // the first ks entries are staged; the rare ones beyond go straight out
+    if (cnt < ks) my[cnt * 32 + lane] = j;
+    else if (cnt < kmax) w.nbr[(int64_t)cnt * nf + gi] = j;
     ++cnt;
   });
   if (active) {
@@ -196,9 +208,10 @@ __global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, Work w, int
     w.nbr_cnt[gi] = (uint32_t)cnt;
   }
   __syncwarp();
-  int maxc = __reduce_max_sync(0xffffffffu, cnt);
+  const int staged = cnt < ks ? cnt : ks;
+  int maxc = __reduce_max_sync(0xffffffffu, staged);
   for (int k = 0; k < maxc; ++k)
-    if (k < cnt) w.nbr[(int64_t)k * nf + gi] = my[k * 32 + lane];
+    if (k < staged) w.nbr[(int64_t)k * nf + gi] = my[k * 32 + lane];
 }
 
 // ---------------------------------------------------------------------------
@@ -383,17 +396,32 @@ __global__ void __launch_bounds__(PAIR_THREADS, 4)
 
 int pair_list_kmax(int dim) { return dim == 3 ? 128 : 48; }
 
+// List entries per lane staged in shared memory (the rest are stored
+// directly, uncoalesced): 80 holds the candidates of most particles of 3D
+// lattices at h = 1.3 dx (about 75) and leaves room for 20 resident warps
+// per SM, which this latency-bound kernel needs more than coalesced stores
+// of the few entries beyond.
+#ifndef WBSPH_LIST_STAGE_3D
+#define WBSPH_LIST_STAGE_3D 80
+#endif
+static int pair_list_stage(int dim) { return dim == 3 ? WBSPH_LIST_STAGE_3D : 48; }
+
 void launch_nbr_list(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st) {
   if (nf == 0) return;
   int kmax = pair_list_kmax(p.dim);
-  size_t sm = (size_t)kmax * 32 * (LIST_THREADS / 32) * sizeof(uint32_t) +
-              (LIST_THREADS / 32) * 32 * sizeof(float4);
+  int ks = pair_list_stage(p.dim);
+  if (ks > kmax) ks = kmax;
+  size_t sm = (size_t)ks * 32 * (LIST_THREADS / 32) * sizeof(uint32_t) +
+              (LIST_THREADS / 32) * 32 * (sizeof(float4) + sizeof(uint32_t));
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_nbr_list, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_nbr_list<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_nbr_list<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     attr = true;
   }
-  k_nbr_list<<<(unsigned)div_up(nf, LIST_THREADS), LIST_THREADS, sm, st>>>(p, w, n, nf, kmax);
+  unsigned blocks = (unsigned)div_up(nf, LIST_THREADS);
+  if (p.dim == 3) k_nbr_list<3><<<blocks, LIST_THREADS, sm, st>>>(p, w, n, nf, kmax, ks);
+  else k_nbr_list<2><<<blocks, LIST_THREADS, sm, st>>>(p, w, n, nf, kmax, ks);
 }
 
 void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,

@@ -190,25 +190,14 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
   if (lane == 0 && wp) atomicAdd(w.pairs, (unsigned long long)wp);
   if (!active) return;
 
-  // ---- epilogue: lambda_min in FP32 (it only selects the branch and is
-  // reported), L inverse and the hydrostatic terms in FP64 ----
-  double l[6];
+  // ---- epilogue. FP64: L^-1 (adjugate) and its contractions with S' and M,
+  // the hydrostatic rebuild of the TIC branch and the continuity terms.
+  // FP32: lambda_min (selects the branch), the viscous and shifting parts
+  // (their pair sums are FP32-accurate, so FP64 arithmetic would add nothing).
   float lf[6];
   const int nl = DIM == 2 ? 3 : 6;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    lf[k] = k < nl ? L[k].s - L[k].c : 0.f;
-    l[k] = (double)lf[k];
-  }
-  double Sd[DIM], Md[DIM * DIM], Cd[DIM], Kd[DIM], Ld[DIM], Pd[DIM];
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) {
-    Sd[c] = (double)(S[c].s - S[c].c); Cd[c] = (double)(Cs[c].s - Cs[c].c);
-    Kd[c] = (double)(K[c].s - K[c].c); Ld[c] = (double)(Lam[c].s - Lam[c].c);
-    Pd[c] = (double)(P[c].s - P[c].c);
-  }
-#pragma unroll
-  for (int c = 0; c < DIM * DIM; ++c) Md[c] = (double)(M[c].s - M[c].c);
+  for (int k = 0; k < 6; ++k) lf[k] = k < nl ? L[k].s - L[k].c : 0.f;
   float lamf;
   if (DIM == 2) {
     float m = 0.5f * (lf[0] + lf[2]), d = 0.5f * (lf[0] - lf[2]);
@@ -216,73 +205,112 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
   } else {
     lamf = lambda_min_3f(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
   }
-  double t_stage = stage2 ? w.scalars[0] + w.scalars[1] : w.scalars[0];
-  double fs = p.omega > 0.0 ? p.omega * p.omega * sin(p.omega * t_stage) : 0.0;
-  double phs = 0.0, gn2 = 0.0;
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) {
-    phs += p.g[c] * s.x[c * n + i];
-    gn2 += p.g[c] * p.g[c];
-  }
-  phs += sqrt(gn2) * p.water_height;
+  double fs = 0.0;
+  if (p.omega > 0.0) fs = forcing_factor(p, stage2 ? w.scalars[0] + w.scalars[1] : w.scalars[0]);
   double acc[DIM], divu = 0.0;
   if (p.use_tic && lamf < (float)p.tic_lambda) {
     // conservative gradient of the full phi rebuilt from the phi' sums:
-    // C = C' + 2 phi_hs,i K + L G
-    double Lm[3][3] = {{l[0], l[1], DIM == 3 ? l[2] : 0.0},
-                       {l[1], DIM == 3 ? l[3] : l[2], DIM == 3 ? l[4] : 0.0},
-                       {DIM == 3 ? l[2] : 0.0, DIM == 3 ? l[4] : 0.0, DIM == 3 ? l[5] : 0.0}};
+    // C = C' + 2 phi_hs,i K + L G, phi_hs,i = G.x_i + |G| H
+    double phs = 0.0, gn2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      phs += p.g[c] * s.x[c * n + i];
+      gn2 += p.g[c] * p.g[c];
+    }
+    phs += sqrt(gn2) * p.water_height;
+    const double l00 = lf[0], l01 = lf[1], l11 = DIM == 3 ? lf[3] : lf[2];
+    const double l02 = DIM == 3 ? lf[2] : 0.0, l12 = DIM == 3 ? lf[4] : 0.0, l22 = DIM == 3 ? lf[5] : 0.0;
+    const double Lm[3][3] = {{l00, l01, l02}, {l01, l11, l12}, {l02, l12, l22}};
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       double lg = 0.0;
 #pragma unroll
       for (int e = 0; e < DIM; ++e) lg += Lm[c][e] * p.g[e];
-      double gradphi = Cd[c] + 2.0 * phs * Kd[c] + lg;
+      double gradphi = (double)(Cs[c].s - Cs[c].c) + 2.0 * phs * (double)(K[c].s - K[c].c) + lg;
       acc[c] = -gradphi + p.g[c] + p.force_amp[c] * fs;
-      divu += Md[c * DIM + c];
+      divu += (double)(M[c * DIM + c].s - M[c * DIM + c].c);
     }
   } else {
-    double inv[DIM][DIM];
-    if (!sym_inverse<DIM>(l, inv)) atomicOr(w.status, kStatSingular);
+    // L^-1 = adj(L) / det(L); the FP32 sums are exact in FP64, and so is
+    // max |L_ab| taken in FP32 for the singularity test |det| <= 1e-12 max^d
+    float amax = 0.f;
+#pragma unroll
+    for (int k = 0; k < nl; ++k) amax = fmaxf(amax, fabsf(lf[k]));
+    double adj[DIM][DIM], det;
+    if (DIM == 2) {
+      const double a = lf[0], b = lf[1], c = lf[2];
+      det = a * c - b * b;
+      adj[0][0] = c;
+      adj[DIM - 1][DIM - 1] = a;
+      adj[0][DIM - 1] = adj[DIM - 1][0] = -b;
+    } else {
+      const double a00 = lf[0], a01 = lf[1], a02 = lf[2], a11 = lf[3], a12 = lf[4], a22 = lf[5];
+      double m[3][3];
+      m[0][0] = a11 * a22 - a12 * a12;
+      m[0][1] = a12 * a02 - a01 * a22;
+      m[0][2] = a01 * a12 - a11 * a02;
+      m[1][1] = a00 * a22 - a02 * a02;
+      m[1][2] = a02 * a01 - a00 * a12;
+      m[2][2] = a00 * a11 - a01 * a01;
+      m[1][0] = m[0][1]; m[2][0] = m[0][2]; m[2][1] = m[1][2];
+      det = a00 * m[0][0] + a01 * m[0][1] + a02 * m[0][2];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) adj[r % DIM][c % DIM] = m[r][c];
+    }
+    const double am = (double)amax;
+    const double lim = DIM == 2 ? 1e-12 * am * am : 1e-12 * am * am * am;
+    const bool ok = fabs(det) > lim;
+    if (!ok) atomicOr(w.status, kStatSingular);
+    const double id = ok ? 1.0 / det : 0.0;
+    double Sd[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) Sd[c] = (double)(S[c].s - S[c].c);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       double gs = 0.0;
 #pragma unroll
       for (int e = 0; e < DIM; ++e) {
-        gs = fma(inv[c][e], Sd[e], gs);
-        divu = fma(inv[c][e], Md[c * DIM + e], divu);
+        gs = fma(adj[c][e], Sd[e], gs);
+        divu = fma(adj[c][e], (double)(M[c * DIM + e].s - M[c * DIM + e].c), divu);
       }
-      acc[c] = -gs + p.force_amp[c] * fs;   // -(L^-1 S' + G) + G(t)
+      acc[c] = -gs * id + p.force_amp[c] * fs;   // -(L^-1 S' + G) + G(t)
     }
+    divu *= id;
   }
-  double umax = sqrt(__longlong_as_double((long long)*w.umax_bits));
-  double phii = s.phi[i];
-  bool bad = false;
-  double dstar[DIM], dn2 = 0.0, gk = 0.0;
+  const float umax = sqrtf((float)__longlong_as_double((long long)*w.umax_bits));
+  const double phii = s.phi[i];
+  const float two_nu = (float)(2.0 * p.nu), m2h = (float)(-2.0 * p.h);
+  unsigned bad = 0u;
+  float dstar[DIM], dn2 = 0.f;
+  double gk = 0.0;
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
-    double a = acc[c] + (p.use_visc ? 2.0 * p.nu * Ld[c] : 0.0);
+    double a = acc[c];
+    if (p.use_visc) a += (double)(two_nu * (Lam[c].s - Lam[c].c));
     w.dudt[c * n + i] = a;
-    bad |= !isfinite(a);
-    dstar[c] = -2.0 * p.h * umax * Pd[c];
-    dn2 += dstar[c] * dstar[c];
-    gk += p.g[c] * Kd[c];
+    bad |= ((unsigned)__double2hiint(a) & 0x7ff00000u) == 0x7ff00000u ? 1u : 0u;
+    dstar[c] = m2h * umax * (P[c].s - P[c].c);
+    dn2 = fmaf(dstar[c], dstar[c], dn2);
+    gk += p.g[c] * (double)(K[c].s - K[c].c);
   }
   double diff = p.use_delta ? p.delta_h_c0 * 2.0 * ((double)(D.s - D.c) + gk) : 0.0;
   double dphidt = -eos_c2(p, phii) * divu + diff;
   w.dphidt[i] = dphidt;
-  bad |= !isfinite(dphidt);
-  double dn = sqrt(dn2);
-  double scale = (p.use_pst && dn > 0.0) ? fmin(dn, 0.5 * umax) / dn : 0.0;
+  bad |= ((unsigned)__double2hiint(dphidt) & 0x7ff00000u) == 0x7ff00000u ? 1u : 0u;
+  const float dn = sqrtf(dn2);
+  const float scale = (p.use_pst && dn > 0.f) ? fminf(dn, 0.5f * umax) / dn : 0.f;
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
-    double v = dstar[c] * scale;
-    w.dushift[c * n + i] = v;
-    bad |= !isfinite(v);
+    float v = dstar[c] * scale;
+    w.dushift[c * n + i] = (double)v;
+    bad |= isfinite(v) ? 0u : 1u;
   }
   w.lambda[i] = (double)lamf;
   if (bad) atomicOr(w.status, kStatNaN);
 }
+
 
 // Packed FP32 copies of the stage state (k_pack_mixed); fails when the
 // grid is too large for the packed cell coordinates (11/11/10 bits).

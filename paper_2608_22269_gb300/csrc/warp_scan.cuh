@@ -34,14 +34,64 @@ __device__ __forceinline__ LaneCell lane_cell(const Params& p, uint32_t key) {
   return c;
 }
 
+// Paired FP32 arithmetic (two lanes of a 64-bit register, round to nearest):
+// the candidate tests run two candidates per instruction.
+__device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi) {
+  unsigned long long d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void f32x2_unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f32x2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f32x2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f32x2_fma(unsigned long long a, unsigned long long b,
+                                                        unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Sorted index of position q of the group's flattened candidate stream:
+// rows r = 0..nrows-1 hold [beg_r, beg_r + len_r), incl_r = len_0 + ... + len_r.
+template <int NR>
+__device__ __forceinline__ uint32_t flat_candidate(uint32_t q, const uint32_t (&beg)[NR],
+                                                   const uint32_t (&incl)[NR]) {
+  uint32_t idx = 0, lo = 0;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (q >= lo && q < incl[r]) idx = beg[r] + (q - lo);
+    lo = incl[r];
+  }
+  return idx;
+}
+
 // f(j, r2f, type_j) is called for every candidate j != self of the lane's
 // particle with FP32 squared distance r2f <= prefilter_r2 (type_j from the .w
-// component of the FP32 position copy). `stage` holds 32 float4 of
-// this warp. All 32 lanes must call this function together.
-template <class F>
+// component of the FP32 position copy). `stage` holds 32 float4 and `sidx`
+// 32 indices of this warp; the positions are staged as four arrays of 32
+// (x, y, z, type) so that pairs of candidates load as one 64-bit word. All
+// 32 lanes must call this function together.
+//
+// Per group the 3^(d-1) row ranges are fetched by one lane each, scanned
+// into one flattened candidate stream (rows in (z, y) order, each in sorted
+// order), and the stream is staged 32 at a time with the next 32 loaded
+// into registers while the current ones are tested: no partially filled
+// batches at row ends, and the gather latency overlaps the tests.
+template <int DIM, class F>
 __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Work& w, bool active,
                                                      uint32_t self, uint32_t key, float4 xs,
-                                                     float4* stage, F&& f) {
+                                                     float4* stage, uint32_t* sidx, F&& f) {
+  constexpr int NR = DIM == 3 ? 9 : 3;
   const int lane = threadIdx.x & 31;
   LaneCell c = lane_cell(p, active ? key : 0u);
   // groups: consecutive active lanes of one cell row whose x cells are no
@@ -53,6 +103,7 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Work
   unsigned starts_mask = __ballot_sync(0xffffffffu, starts);
   int gid = __popc(starts_mask & ((2u << lane) - 1u));  // group number (1-based) of this lane
   unsigned pending = __ballot_sync(0xffffffffu, active);
+  const float4 far = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
   while (pending) {
     int leader = __ffs(pending) - 1;
     int ggid = __shfl_sync(0xffffffffu, gid, leader);
@@ -65,40 +116,73 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Work
     int gy = grow % p.nc[1], gz = grow / p.nc[1];
     int x0 = xlo > 0 ? xlo - 1 : 0;
     int x1 = xhi + 1 < p.nc[0] ? xhi + 1 : p.nc[0] - 1;
-    int z0 = p.dim == 3 ? gz - 1 : 0, z1 = p.dim == 3 ? gz + 1 : 0;
-    for (int cz = z0; cz <= z1; ++cz) {
-      if (cz < 0 || cz >= p.nc[2]) continue;
-      for (int cy = gy - 1; cy <= gy + 1; ++cy) {
-        if (cy < 0 || cy >= p.nc[1]) continue;
+    // lane r < NR: row r = (cz, cy) = (gz - 1 + r / 3, gy - 1 + r % 3) in 3D
+    uint32_t rb = 0, rl = 0;
+    if (lane < NR) {
+      int cy = gy - 1 + lane % 3;
+      int cz = DIM == 3 ? gz - 1 + lane / 3 : 0;
+      if (cy >= 0 && cy < p.nc[1] && cz >= 0 && cz < p.nc[2]) {
         int64_t base = (int64_t)cy * p.nc[0] + (int64_t)cz * p.nc[0] * p.nc[1];
-        uint32_t beg = w.cell_lb[base + x0], end = w.cell_lb[base + x1 + 1];
-        for (uint32_t c0 = beg; c0 < end; c0 += 32) {
-          uint32_t idx = c0 + lane;
-          // slots past the run hold a point at infinity, which no test passes
-          stage[lane] = idx < end ? __ldg(&w.xf[idx]) : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-          __syncwarp();
-          if (in_g) {
-            // independent tests of all 32 staged candidates, then the hits in order
-            unsigned hits = 0u;
+        rb = w.cell_lb[base + x0];
+        rl = w.cell_lb[base + x1 + 1] - rb;
+      }
+    }
+    uint32_t inc = rl;
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+      uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += o;
+    }
+    uint32_t beg[NR], incl[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      beg[r] = __shfl_sync(0xffffffffu, rb, r);
+      incl[r] = __shfl_sync(0xffffffffu, inc, r);
+    }
+    const uint32_t total = incl[NR - 1];
+    uint32_t nidx = flat_candidate<NR>((uint32_t)lane, beg, incl);
+    float4 nxt = (uint32_t)lane < total ? __ldg(&w.xf[nidx]) : far;
+    float* sx = reinterpret_cast<float*>(stage);  // [x 32][y 32][z 32][type 32]
+    const unsigned long long px = f32x2_pack(xs.x, xs.x), py = f32x2_pack(xs.y, xs.y),
+                             pz = f32x2_pack(xs.z, xs.z);
+    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+      // slots past the stream hold a point at infinity, which no test passes
+      sx[lane] = nxt.x;
+      sx[32 + lane] = nxt.y;
+      sx[64 + lane] = nxt.z;
+      sx[96 + lane] = nxt.w;
+      sidx[lane] = nidx;
+      __syncwarp();
+      const uint32_t q = c0 + 32 + (uint32_t)lane;
+      if (c0 + 32 < total) {
+        nidx = flat_candidate<NR>(q, beg, incl);
+        nxt = q < total ? __ldg(&w.xf[nidx]) : far;
+      }
+      if (in_g) {
+        // independent tests of all 32 staged candidates, then the hits in order
+        unsigned hits = 0u;
+        const unsigned long long* s2 = reinterpret_cast<const unsigned long long*>(sx);
 #pragma unroll 8
-            for (int k = 0; k < 32; ++k) {
-              float4 q = stage[k];
-              float dx = q.x - xs.x, dy = q.y - xs.y, dz = q.z - xs.z;
-              float r2 = dx * dx + dy * dy + dz * dz;
-              hits |= (r2 <= p.prefilter_r2 ? 1u : 0u) << k;
-            }
-            if (self - c0 < 32u) hits &= ~(1u << (self - c0));
-            while (hits) {
-              int k = __ffs(hits) - 1;
-              hits &= hits - 1u;
-              float4 q = stage[k];
-              float dx = q.x - xs.x, dy = q.y - xs.y, dz = q.z - xs.z;
-              f(c0 + k, dx * dx + dy * dy + dz * dz, q.w);
-            }
-          }
-          __syncwarp();
+        for (int k = 0; k < 16; ++k) {
+          unsigned long long dx = f32x2_sub(s2[k], px);
+          unsigned long long dy = f32x2_sub(s2[16 + k], py);
+          unsigned long long dz = f32x2_sub(s2[32 + k], pz);
+          unsigned long long r2 = f32x2_fma(dz, dz, f32x2_fma(dy, dy, f32x2_mul(dx, dx)));
+          float r2a, r2b;
+          f32x2_unpack(r2, r2a, r2b);
+          hits |= (r2a <= p.prefilter_r2 ? 1u : 0u) << (2 * k);
+          hits |= (r2b <= p.prefilter_r2 ? 1u : 0u) << (2 * k + 1);
+        }
+        while (hits) {
+          int k = __ffs(hits) - 1;
+          hits &= hits - 1u;
+          uint32_t j = sidx[k];
+          if (j == self) continue;
+          float dx = sx[k] - xs.x, dy = sx[32 + k] - xs.y, dz = sx[64 + k] - xs.z;
+          f(j, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), sx[96 + k]);
         }
       }
+      __syncwarp();
     }
   }
 }

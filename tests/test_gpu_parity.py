@@ -93,6 +93,18 @@ def test_stage_rates_match_oracle(name, make):
     _compare_rates(sc, sim, name)
 
 
+def test_long_candidate_lists_match_oracle():
+    """h = 1.48 dx in 3D gives 90 to 110 neighbours per particle: list
+    entries past the shared-memory staging depth take the direct-store path
+    of the candidate-list kernel."""
+    sc = _dynamic(S.dam_break_3d(dx=0.02, box=(0.4, 0.2, 0.3), column=(0.16, 0.2, 0.14),
+                                 h_over_dx=1.48))
+    sim = _sim(sc)
+    row, _ = sim.neighbors()
+    assert np.diff(row).max() > 100
+    _compare_rates(sc, sim, "h1.48")
+
+
 @pytest.mark.parametrize("name,make", SMALL)
 @pytest.mark.parametrize("nsteps", [1, 3])
 def test_fields_after_steps_match_oracle(name, make, nsteps):
