@@ -40,7 +40,7 @@ constexpr int FEAT = 8;   // padded width of node and edge input features
 constexpr int MLP_THREADS = 128;
 constexpr int TILE = 64;  // rows per tile (4 warps x 16)
 
-enum { MODE_DIRECT = 0, MODE_LIST = 1, MODE_EDGE = 2, MODE_NODE = 3 };
+enum { MODE_DIRECT = 0, MODE_LIST = 1, MODE_EDGE = 2, MODE_NODE = 3, MODE_SPLIT = 4 };
 
 __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
@@ -123,6 +123,7 @@ struct MlpArgs {
   const uint32_t* recv;      // EDGE
   const uint32_t* send;      // EDGE
   const bf16* agg;           // NODE: [n][64]
+  const bf16* proj;          // SPLIT: [n][128] node projections h W1[64:128] | h W1[128:192]
   int kin, nout;             // true widths
   const bf16* w1; const float* b1; const bf16* w2; const float* b2;  // block parameters
   // forward outputs
@@ -197,9 +198,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // copied asynchronously two tiles ahead into a small ring in shared memory.
 template <int MODE>
 __device__ __forceinline__ void issue_idx(const MlpArgs& a, int64_t row0, int64_t rows, uint32_t* I) {
-  if (MODE == MODE_EDGE || MODE == MODE_LIST) {
+  if (MODE == MODE_EDGE || MODE == MODE_SPLIT || MODE == MODE_LIST) {
     const int per = TILE / 4;  // 16-byte chunks per index array
-    const int narr = MODE == MODE_EDGE ? 2 : 1;
+    const int narr = MODE == MODE_LIST ? 1 : 2;
     if (threadIdx.x < per * narr) {
       int arr = threadIdx.x / per, c = threadIdx.x % per;
       const uint32_t* src = MODE == MODE_LIST ? a.list : (arr == 0 ? a.recv : a.send);
@@ -219,6 +220,11 @@ __device__ __forceinline__ const bf16* chunk_src(const MlpArgs& a, int64_t row, 
                                                  const uint32_t* I) {
   if (MODE == MODE_DIRECT) return a.in + row * FEAT;  // only chunk 0 carries data
   if (MODE == MODE_LIST) return a.in + (int64_t)I[r] * HID + c8 * 8;
+  if (MODE == MODE_SPLIT) {
+    if (c8 < 8) return a.e + row * HID + c8 * 8;
+    if (c8 < 16) return a.proj + (int64_t)I[r] * 2 * HID + (c8 - 8) * 8;
+    return a.proj + (int64_t)I[TILE + r] * 2 * HID + HID + (c8 - 16) * 8;
+  }
   if (MODE == MODE_EDGE) {
     if (c8 < 8) return a.e + row * HID + c8 * 8;
     if (c8 < 16) return a.h + (int64_t)I[r] * HID + (c8 - 8) * 8;
@@ -272,9 +278,12 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
   __syncthreads();
   if (tile * TILE < rows) issue_tile<MODE, KP>(a, tile * TILE, rows, Xb, S::LDX, Ib);
   else cp_async_commit();
+  // SPLIT: only the first 64 inputs (the edge state) go through the GEMM;
+  // the receiver and sender parts arrive as node projections
+  constexpr int KG = MODE == MODE_SPLIT ? HID : KP;
   const bf16 zero = __float2bfloat16(0.f);
-  for (int idx = threadIdx.x; idx < HID * KP; idx += MLP_THREADS) {
-    int n = idx / KP, k = idx % KP;
+  for (int idx = threadIdx.x; idx < HID * KG; idx += MLP_THREADS) {
+    int n = idx / KG, k = idx % KG;
     W1t[n * S::LDX + k] = k < a.kin ? a.w1[k * HID + n] : zero;
   }
   for (int idx = threadIdx.x; idx < NP * HID; idx += MLP_THREADS) {
@@ -300,7 +309,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
 #pragma unroll
-    for (int kt = 0; kt < KP / 16; ++kt) {
+    for (int kt = 0; kt < KG / 16; ++kt) {
       uint32_t af[4];
       ldsm_a(af, X, S::LDX, m0, kt * 16);
 #pragma unroll
@@ -314,10 +323,20 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       int c = nt * 8 + 2 * t;
+      float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+      if (MODE == MODE_SPLIT) {  // + h_recv W1r + h_send W1s from the staged projections
+        const bf16* x0 = X + (m0 + g) * S::LDX + HID + c;
+        const bf16* x1 = X + (m0 + g + 8) * S::LDX + HID + c;
+        float2 r0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(x0));
+        float2 s0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(x0 + HID));
+        float2 r1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(x1));
+        float2 s1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(x1 + HID));
+        p0 = r0.x + s0.x; p1 = r0.y + s0.y; p2 = r1.x + s1.x; p3 = r1.y + s1.y;
+      }
       *reinterpret_cast<__nv_bfloat162*>(A1 + (m0 + g) * S::LDH + c) =
-          __floats2bfloat162_rn(silu(acc[nt][0] + B1[c]), silu(acc[nt][1] + B1[c + 1]));
+          __floats2bfloat162_rn(silu(acc[nt][0] + B1[c] + p0), silu(acc[nt][1] + B1[c + 1] + p1));
       *reinterpret_cast<__nv_bfloat162*>(A1 + (m0 + g + 8) * S::LDH + c) =
-          __floats2bfloat162_rn(silu(acc[nt][2] + B1[c]), silu(acc[nt][3] + B1[c + 1]));
+          __floats2bfloat162_rn(silu(acc[nt][2] + B1[c] + p2), silu(acc[nt][3] + B1[c + 1] + p3));
     }
     __syncwarp();
     float acc2[NP / 8][4];
@@ -353,7 +372,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
         for (int hq = 0; hq < 2; ++hq) {
           int r = m0 + g + hq * 8, o = nt * 8 + 2 * t;
           float v0 = acc2[nt][2 * hq] + B2[o], v1 = acc2[nt][2 * hq + 1] + B2[o + 1];
-          if (MODE == MODE_EDGE || MODE == MODE_NODE) {
+          if (MODE == MODE_EDGE || MODE == MODE_SPLIT || MODE == MODE_NODE) {
             __nv_bfloat162 res = *reinterpret_cast<const __nv_bfloat162*>(X + r * S::LDX + o);
             v0 += __bfloat162float(res.x);
             v1 += __bfloat162float(res.y);
@@ -372,6 +391,71 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
       }
     }
     __syncthreads();  // X[buf] is refilled by the next-but-one prefetch
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Node projections for the split edge MLP. The first layer of the edge MLP
+// acts on [e_ij, h_i, h_j], so z1 = e_ij W1e + h_i W1r + h_j W1s + b1 with
+// W1 = [W1e; W1r; W1s] (64 rows each): the two node terms are computed once
+// per node here, P_i = [h_i W1r | h_i W1s] (BF16, FP32 accumulation), and
+// the edge kernel gathers them instead of h, leaving a 64-wide GEMM per edge.
+// ---------------------------------------------------------------------------
+constexpr int PJ_LD = HID + 8, PJ_LDO = 2 * HID + 8;
+
+__global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restrict__ h, int64_t n,
+                                                           const bf16* __restrict__ w1, bf16* __restrict__ P) {
+  __shared__ __align__(16) bf16 Bt[2 * HID * PJ_LD];  // Bt[o][k] = W1[64 + k][o] | W1[128 + k][o - 64]
+  __shared__ __align__(16) bf16 At[TILE * PJ_LD];
+  __shared__ __align__(16) bf16 Ot[TILE * PJ_LDO];
+  for (int idx = threadIdx.x; idx < 2 * HID * HID; idx += MLP_THREADS) {
+    int o = idx / HID, k = idx % HID;
+    Bt[o * PJ_LD + k] = w1[(int64_t)(HID + (o >= HID ? HID : 0) + k) * HID + (o % HID)];
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int m0 = warp * 16;
+  for (int64_t tile = blockIdx.x; tile * TILE < n; tile += gridDim.x) {
+    const int64_t row0 = tile * TILE;
+    __syncthreads();  // Bt staged / At and Ot free
+    for (int idx = threadIdx.x; idx < TILE * (HID / 8); idx += MLP_THREADS) {
+      int r = idx / (HID / 8), c8 = idx % (HID / 8);
+      int64_t row = row0 + r;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (row < n) v = *reinterpret_cast<const uint4*>(h + row * HID + c8 * 8);
+      *reinterpret_cast<uint4*>(At + r * PJ_LD + c8 * 8) = v;
+    }
+    __syncthreads();
+    float acc[16][4];
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < HID / 16; ++kt) {
+      uint32_t af[4];
+      ldsm_a(af, At, PJ_LD, m0, kt * 16);
+#pragma unroll
+      for (int nt = 0; nt < 16; nt += 2) {
+        uint32_t bq[4];
+        ldsm_b2(bq, Bt, PJ_LD, kt * 16, nt * 8);
+        mma16816(acc[nt], af, bq);
+        mma16816(acc[nt + 1], af, bq + 2);
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) {
+      int c = nt * 8 + 2 * t;
+      *reinterpret_cast<__nv_bfloat162*>(Ot + (m0 + g) * PJ_LDO + c) = __floats2bfloat162_rn(acc[nt][0], acc[nt][1]);
+      *reinterpret_cast<__nv_bfloat162*>(Ot + (m0 + g + 8) * PJ_LDO + c) =
+          __floats2bfloat162_rn(acc[nt][2], acc[nt][3]);
+    }
+    __syncwarp();
+    // the warp's 16 rows of 256 bytes, 16-byte chunks
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int idx = q * 32 + lane, r = m0 + (idx >> 4), c16 = idx & 15;
+      int64_t row = row0 + r;
+      if (row < n)
+        *reinterpret_cast<uint4*>(P + row * 2 * HID + c16 * 8) = *reinterpret_cast<const uint4*>(Ot + r * PJ_LDO + c16 * 8);
+    }
   }
 }
 
@@ -612,25 +696,41 @@ __global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, cons
   uint32_t i = w.fluid_list[gi];
   int c = (int)w.nbr_cnt[gi];
   int64_t e = row_ptr[gi];
-  double inv_h = 1.0 / p.h;
+  const float inv_h = (float)(1.0 / p.h);
+  float inv_su[3] = {0.f, 0.f, 0.f};
+  for (int d = 0; d < p.dim; ++d) inv_su[d] = 1.f / node_std[d];
+  const float inv_sphi = 1.f / node_std[p.dim + 1];
+  double xi[3] = {0, 0, 0};
+  float ui[3] = {0.f, 0.f, 0.f};
+  for (int d = 0; d < p.dim; ++d) {
+    xi[d] = s.x[d * n + i];
+    ui[d] = (float)s.u[d * n + i];
+  }
+  const float phii = (float)s.phi[i];
   for (int k = 0; k < c; ++k) {
     uint32_t j = w.nbr[(int64_t)k * nf + gi];
     double r[3] = {0, 0, 0}, r2 = 0.0;
     for (int d = 0; d < p.dim; ++d) {
-      r[d] = __dsub_rn(s.x[d * n + j], s.x[d * n + i]);
+      r[d] = __dsub_rn(s.x[d * n + j], xi[d]);
       r2 = __dadd_rn(r2, __dmul_rn(r[d], r[d]));
     }
     if (!(r2 <= p.four_h2 && r2 > 0.0)) continue;
     recv[e] = i;
     send[e] = j;
-    bf16* f = efeat + e * FEAT;
-    for (int d = 0; d < FEAT; ++d) f[d] = __float2bfloat16(0.f);
+    // features (r/h, |r|/h, dU/s_U, dphi/s_phi), zero padded to 8, one 16-byte store
+    float f[FEAT] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int d = 0; d < p.dim; ++d) {
-      f[d] = __float2bfloat16((float)(r[d] * inv_h));
-      f[p.dim + 1 + d] = __float2bfloat16((float)((s.u[d * n + j] - s.u[d * n + i]) / node_std[d]));
+      f[d] = (float)r[d] * inv_h;
+      f[p.dim + 1 + d] = ((float)s.u[d * n + j] - ui[d]) * inv_su[d];
     }
-    f[p.dim] = __float2bfloat16((float)(sqrt(r2) * inv_h));
-    f[2 * p.dim + 1] = __float2bfloat16((float)((s.phi[j] - s.phi[i]) / node_std[p.dim + 1]));
+    f[p.dim] = sqrtf((float)r2) * inv_h;
+    f[2 * p.dim + 1] = ((float)s.phi[j] - phii) * inv_sphi;
+    uint4 v;
+    v.x = pack2(__float2bfloat16(f[0]), __float2bfloat16(f[1]));
+    v.y = pack2(__float2bfloat16(f[2]), __float2bfloat16(f[3]));
+    v.z = pack2(__float2bfloat16(f[4]), __float2bfloat16(f[5]));
+    v.w = pack2(__float2bfloat16(f[6]), __float2bfloat16(f[7]));
+    *reinterpret_cast<uint4*>(efeat + e * FEAT) = v;
     ++e;
   }
 }
@@ -757,7 +857,7 @@ struct wbsph_surrogate_s {
   // graph and activations, sized on demand
   int64_t cap_n = 0, cap_nf = 0, cap_e = 0;
   uint32_t *cnt = nullptr, *row_ptr = nullptr, *recv = nullptr, *send = nullptr;
-  bf16 *efeat = nullptr, *nfeat = nullptr;
+  bf16 *efeat = nullptr, *nfeat = nullptr, *proj = nullptr;
   std::vector<bf16*> hs, es, aggs;
   float *out = nullptr, *dout = nullptr, *dh = nullptr, *de = nullptr, *dagg = nullptr;
   double* loss = nullptr;
@@ -811,6 +911,8 @@ void dfree(void* p) {
 
 void free_graph(wbsph_surrogate s) {
   dfree(s->cnt); dfree(s->row_ptr); dfree(s->recv); dfree(s->send); dfree(s->efeat); dfree(s->nfeat);
+  dfree(s->proj);
+  s->proj = nullptr;
   for (auto* q : s->hs) dfree(q);
   for (auto* q : s->es) dfree(q);
   for (auto* q : s->aggs) dfree(q);
@@ -824,12 +926,11 @@ void free_graph(wbsph_surrogate s) {
 
 int ensure_nodes(wbsph_surrogate s, int64_t n, int64_t nf) {
   if (n <= s->cap_n && nf <= s->cap_nf) return WBSPH_OK;
-  int64_t e_keep = s->cap_e;
   free_graph(s);
   s->cap_n = n; s->cap_nf = nf;
   bool ok = dalloc(&s->cnt, nf + 1) && dalloc(&s->row_ptr, nf + 1) && dalloc(&s->nfeat, n * FEAT) &&
             dalloc(&s->out, nf * 4) && dalloc(&s->dout, nf * 4) && dalloc(&s->dh, n * HID) &&
-            dalloc(&s->dagg, n * HID);
+            dalloc(&s->dagg, n * HID) && dalloc(&s->proj, n * 2 * HID);
   for (int l = 0; ok && l <= s->layers; ++l) {
     bf16* q = nullptr;
     ok = dalloc(&q, n * HID);
@@ -839,7 +940,6 @@ int ensure_nodes(wbsph_surrogate s, int64_t n, int64_t nf) {
       s->aggs.push_back(q);
     }
   }
-  (void)e_keep;
   return ok ? WBSPH_OK : sfail(s, WBSPH_E_NOMEM, "surrogate node buffers");
 }
 
@@ -932,10 +1032,12 @@ void forward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream
     a.rows = E; a.in = s->efeat; a.out_bf = s->es[0];
     launch_fwd<MODE_DIRECT, 16, 64>(a, E, cs);
   }
+  const int pgrid = (int)(div_up(n > 0 ? n : 1, TILE) < 152 * 4 ? div_up(n > 0 ? n : 1, TILE) : 152 * 4);
   for (int l = 0; l < L; ++l) {
     MlpArgs a = block_args(s, 2 + 2 * l);
-    a.rows = E; a.e = s->es[l]; a.h = s->hs[l]; a.recv = s->recv; a.send = s->send; a.out_bf = s->es[l + 1];
-    launch_fwd<MODE_EDGE, 192, 64>(a, E, cs);
+    k_node_proj<<<pgrid, MLP_THREADS, 0, cs>>>(s->hs[l], n, a.w1, s->proj);
+    a.rows = E; a.e = s->es[l]; a.proj = s->proj; a.recv = s->recv; a.send = s->send; a.out_bf = s->es[l + 1];
+    launch_fwd<MODE_SPLIT, 192, 64>(a, E, cs);
     cudaMemsetAsync(s->aggs[l], 0, (size_t)n * HID * 2, cs);
     if (nf > 0)
       k_sg_aggregate<<<(unsigned)div_up(nf, 4), 128, 0, cs>>>(w.fluid_list, nf, s->row_ptr, s->es[l + 1], s->aggs[l]);

@@ -4,6 +4,7 @@ weights and the same graph and features."""
 import numpy as np
 import pytest
 
+import oracle
 from oracle import mpnn
 from paper_2608_22269_gb300 import scenes as S
 
@@ -76,6 +77,35 @@ def test_forward_and_gradient_match_fp64_reference(dim):
     print(dim, "grad cos", cos, "rel norm", reln, "loss", dbg["loss"], loss_ref)
     assert abs(dbg["loss"] - loss_ref) <= 3e-2 * loss_ref
     assert cos > 0.9999 and reln < 1e-2
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_graph_and_edge_features_follow_the_positions(dim):
+    """Edges: every fluid receiver with every particle within 2h, the exact
+    neighbour sets of the oracle; edge features recomputed in FP64 from the
+    positions, velocities and potentials agree to BF16 precision."""
+    sc = _state(dim)
+    sim, sur, theta, _ = _setup(sc)
+    dbg = sur.debug(sim)
+    row, col = oracle.neighbors(sc.params, sc.x)
+    f = sc.type == 0
+    ref = {(i, int(j)) for i in np.nonzero(f)[0] for j in col[row[i]:row[i + 1]]}
+    got = list(zip(dbg["recv"].tolist(), dbg["send"].tolist()))
+    assert len(got) == len(ref) and set(got) == ref
+    recv, send = dbg["recv"].astype(np.int64), dbg["send"].astype(np.int64)
+    h = sc.params["h_over_dx"] * sc.params["dx"]
+    su = sc.u[:, f].std(1)
+    sphi = sc.phi[f].std()
+    # U and phi after the stage's dummy update (wall particles take theirs
+    # from the nearest fluid particle before the graph is built)
+    u, phi = sim.get("u"), sim.get("phi")
+    r = sc.x[:, send] - sc.x[:, recv]
+    want = np.r_[r / h, np.sqrt((r ** 2).sum(0))[None] / h,
+                 (u[:, send] - u[:, recv]) / su[:, None],
+                 (phi[send] - phi[recv])[None] / sphi].T
+    ef = dbg["edge_feat"][:, :2 * dim + 2]
+    assert np.all(np.abs(ef - want) <= 8e-3 * np.maximum(1.0, np.abs(want)))
+    assert np.all(dbg["edge_feat"][:, 2 * dim + 2:] == 0.0)
 
 
 def test_training_reduces_loss():
