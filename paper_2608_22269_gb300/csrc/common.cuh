@@ -52,6 +52,7 @@ struct Params {
   int nc[3];                      // grid cells per axis
   int64_t ncells;
   double water_height;
+  double phs0;  // |G| H: hydrostatic potential at height zero (phi_hs = G.x + |G| H)
 };
 
 // Device arrays of one particle-state buffer.

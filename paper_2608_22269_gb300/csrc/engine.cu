@@ -203,6 +203,7 @@ static int derive_params(wbsph_s* h) {
   p.cfl = c.cfl;
   p.fixed_dt = c.fixed_dt;
   p.water_height = c.water_height;
+  p.phs0 = std::sqrt(c.g[0] * c.g[0] + c.g[1] * c.g[1] + c.g[2] * c.g[2]) * c.water_height;
   int64_t ncells = 1;
   for (int k = 0; k < 3; ++k) {
     int64_t m = 1;
@@ -810,7 +811,10 @@ static int surrogate_stage(wbsph_s* h, wbsph_surrogate s, int stage2) {
     ProfScope ps(h, WBSPH_K_PAIR);
     rc = surrogate_stage_rates(s, h->P, h->A, h->W, h->n, h->nf, st);
   }
-  h->launches += 3 + (stage2 ? 0 : 1) + 20;
+  // prepass (dummy update, volumes), time step, and the surrogate stage's 21
+  // kernels: candidate lists, graph count/scan/fill, node features, two
+  // encoders, 3 x (node projections, edge MLP, aggregation, node MLP), decoder, rates
+  h->launches += (h->n ? (h->nd ? 2 : 1) : 0) + (stage2 ? 0 : 1) + (h->nf ? 21 : 0);
   if (rc) return fail(h, rc, "surrogate stage failed");
   return check_launch(h, "surrogate stage");
 }

@@ -47,15 +47,13 @@ __global__ void k_pack_mixed(Params p, State s, Work w, int64_t n, float4* A, fl
   uint32_t ic[3] = {key % nx, (key / nx) % ny, key / (nx * ny)};
   float o[3] = {0.f, 0.f, 0.f};
   float u[3] = {0.f, 0.f, 0.f};
-  double phs = 0.0, gn2 = 0.0;
+  double phs = p.phs0;
   for (int k = 0; k < p.dim; ++k) {
     double xk = s.x[k * n + i];
     o[k] = (float)(xk - (p.domain_min[k] + (double)ic[k] * p.R));
     u[k] = (float)s.u[k * n + i];
-    phs += p.g[k] * xk;
-    gn2 += p.g[k] * p.g[k];
+    if (p.g[k] != 0.0) phs = fma(p.g[k], xk, phs);
   }
-  phs += sqrt(gn2) * p.water_height;
   float phip = (float)(s.phi[i] - phs);
   float v = (float)w.vol[i];
   if (s.type[i] != kFluid) v = -v;
@@ -211,13 +209,10 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
   if (p.use_tic && lamf < (float)p.tic_lambda) {
     // conservative gradient of the full phi rebuilt from the phi' sums:
     // C = C' + 2 phi_hs,i K + L G, phi_hs,i = G.x_i + |G| H
-    double phs = 0.0, gn2 = 0.0;
+    double phs = p.phs0;
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      phs += p.g[c] * s.x[c * n + i];
-      gn2 += p.g[c] * p.g[c];
-    }
-    phs += sqrt(gn2) * p.water_height;
+    for (int c = 0; c < DIM; ++c)
+      if (p.g[c] != 0.0) phs = fma(p.g[c], s.x[c * n + i], phs);
     const double l00 = lf[0], l01 = lf[1], l11 = DIM == 3 ? lf[3] : lf[2];
     const double l02 = DIM == 3 ? lf[2] : 0.0, l12 = DIM == 3 ? lf[4] : 0.0, l22 = DIM == 3 ? lf[5] : 0.0;
     const double Lm[3][3] = {{l00, l01, l02}, {l01, l11, l12}, {l02, l12, l22}};
