@@ -460,6 +460,245 @@ __global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restric
 }
 
 // ---------------------------------------------------------------------------
+// Edge MLP of a message-passing layer on the 5th-generation tensor cores
+// (tcgen05). Per tile of 128 edges:
+//   z1 = e W1e + P_recv + P_send + b1    (64 x 64 GEMM, node terms from k_node_proj)
+//   e' = e + silu(z1) W2 + b2            (64 x 64 GEMM)
+// Operands sit in shared memory in the K-major 128-byte-swizzled layout the
+// tensor core reads through matrix descriptors (row r of 64 BF16 = 128 B at
+// r * 128, 16-byte chunk c stored at chunk c ^ (r % 8); 8-row groups 1024 B
+// apart); the FP32 accumulator lives in tensor memory (TMEM, 64 columns, lane
+// = tile row) and is read back by the warp that owns those 32 lanes. One
+// thread issues the MMAs and their commit to an mbarrier; every wait on the
+// mbarrier is bounded and a timeout is reported through the error word.
+// ---------------------------------------------------------------------------
+constexpr int TC_ROWS = 128;
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_TILE_BYTES = TC_ROWS * 128;        // 128 rows x 64 BF16
+constexpr size_t TC_SMEM_BYTES = 1024 + 3 * TC_TILE_BYTES + 2 * 8192 + 2 * 64 * 4 + 64;
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
+
+// instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16,
+// both K-major, N = 64, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 B apart (the leading-dimension offset is unused in this layout)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// byte offset of 16-byte chunk c of row r in the swizzled layout
+__device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// bounded wait for the mbarrier phase `parity`; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restrict__ e_in, bf16* __restrict__ e_out,
+                                                           int64_t E, const uint32_t* __restrict__ recv,
+                                                           const uint32_t* __restrict__ send,
+                                                           const bf16* __restrict__ P, const bf16* __restrict__ w1,
+                                                           const float* __restrict__ b1g, const bf16* __restrict__ w2,
+                                                           const float* __restrict__ b2g, unsigned* err) {
+  extern __shared__ unsigned char tc_raw[];
+  unsigned char* base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);  // 1024-byte aligned
+  unsigned char* A = base;                          // e tile, then the output tile
+  unsigned char* PR = base + TC_TILE_BYTES;         // receiver projections, then silu(z1)
+  unsigned char* PS = base + 2 * TC_TILE_BYTES;     // sender projections
+  unsigned char* B1 = base + 3 * TC_TILE_BYTES;     // W1e^T [n][k]
+  unsigned char* B2 = B1 + 8192;                    // W2^T [n][k]
+  float* b1 = reinterpret_cast<float*>(B2 + 8192);
+  float* b2 = b1 + 64;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(b2 + 64);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+
+  // weights (K-major swizzled), biases, barrier, tensor memory
+  for (int idx = t; idx < 64 * 64; idx += TC_THREADS) {
+    int n = idx >> 6, k = idx & 63;
+    uint32_t off = sw128(n, k >> 3) + (k & 7) * 2;
+    *reinterpret_cast<bf16*>(B1 + off) = w1[k * HID + n];
+    *reinterpret_cast<bf16*>(B2 + off) = w2[k * HID + n];
+  }
+  if (t < 64) { b1[t] = b1g[t]; b2[t] = b2g[t]; }
+  const uint32_t mb = smem_u32(mbar);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(smem_u32(tslot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint64_t dA = tc_desc(smem_u32(A)), dPR = tc_desc(smem_u32(PR));
+  const uint64_t dB1 = tc_desc(smem_u32(B1)), dB2 = tc_desc(smem_u32(B2));
+  uint32_t phase = 0;
+  bool ok = true;
+
+  for (int64_t tile = blockIdx.x; ok && tile * TC_ROWS < E; tile += gridDim.x) {
+    const int64_t row0 = tile * TC_ROWS;
+    // ---- loads: row t of the e tile and of both projection tiles ----
+    {
+      const int64_t row = row0 + t;
+      const bool valid = row < E;
+      const uint32_t rv = valid ? recv[row] : 0u, sd = valid ? send[row] : 0u;
+      const bf16* se = e_in + (valid ? row : 0) * HID;
+      const bf16* sr = P + (int64_t)rv * 2 * HID;
+      const bf16* ss = P + (int64_t)sd * 2 * HID + HID;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        cp_async16(A + sw128(t, c), se + c * 8, valid);
+        cp_async16(PR + sw128(t, c), sr + c * 8, valid);
+        cp_async16(PS + sw128(t, c), ss + c * 8, valid);
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+      fence_async_smem();  // the e tile is read by the tensor core
+    }
+    tc_fence_before();
+    __syncthreads();
+    // ---- z1 = e W1e ----
+    if (t == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tc_mma(tmem, dA + 2 * k, dB1 + 2 * k, k > 0);
+      tc_commit(mb);
+    }
+    bool w_ok = mbar_wait(mb, phase);
+    phase ^= 1u;
+    if (!__syncthreads_and(w_ok)) { ok = false; break; }
+    tc_fence_after();
+    // ---- silu(z1 + b1 + P_recv + P_send) -> PR (BF16, swizzled) ----
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float v[16];
+      tc_ld16(t_lane + q * 16, v);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * q + h;
+        uint4 pr = *reinterpret_cast<const uint4*>(PR + sw128(t, c));
+        uint4 ps = *reinterpret_cast<const uint4*>(PS + sw128(t, c));
+        const __nv_bfloat162* r2 = reinterpret_cast<const __nv_bfloat162*>(&pr);
+        const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(&ps);
+        uint4 o;
+        uint32_t* o32 = reinterpret_cast<uint32_t*>(&o);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int col = c * 8 + 2 * j;
+          float2 fr = __bfloat1622float2(r2[j]), fs = __bfloat1622float2(s2[j]);
+          float z0 = v[h * 8 + 2 * j] + b1[col] + fr.x + fs.x;
+          float z1 = v[h * 8 + 2 * j + 1] + b1[col + 1] + fr.y + fs.y;
+          __nv_bfloat162 a2 = __floats2bfloat162_rn(silu(z0), silu(z1));
+          o32[j] = *reinterpret_cast<uint32_t*>(&a2);
+        }
+        *reinterpret_cast<uint4*>(PR + sw128(t, c)) = o;
+      }
+    }
+    fence_async_smem();  // silu(z1) is read by the tensor core
+    tc_fence_before();
+    __syncthreads();
+    // ---- z2 = silu(z1) W2 (same TMEM columns) ----
+    if (t == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tc_mma(tmem, dPR + 2 * k, dB2 + 2 * k, k > 0);
+      tc_commit(mb);
+    }
+    w_ok = mbar_wait(mb, phase);
+    phase ^= 1u;
+    if (!__syncthreads_and(w_ok)) { ok = false; break; }
+    tc_fence_after();
+    // ---- e' = e + z2 + b2, in place into the e tile ----
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float v[16];
+      tc_ld16(t_lane + q * 16, v);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * q + h;
+        uint4 ev = *reinterpret_cast<const uint4*>(A + sw128(t, c));
+        const __nv_bfloat162* e2 = reinterpret_cast<const __nv_bfloat162*>(&ev);
+        uint4 o;
+        uint32_t* o32 = reinterpret_cast<uint32_t*>(&o);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int col = c * 8 + 2 * j;
+          float2 fe = __bfloat1622float2(e2[j]);
+          __nv_bfloat162 a2 = __floats2bfloat162_rn(v[h * 8 + 2 * j] + b2[col] + fe.x,
+                                                    v[h * 8 + 2 * j + 1] + b2[col + 1] + fe.y);
+          o32[j] = *reinterpret_cast<uint32_t*>(&a2);
+        }
+        *reinterpret_cast<uint4*>(A + sw128(t, c)) = o;
+      }
+    }
+    __syncwarp();
+    // ---- the warp's 32 output rows, 4 whole rows (512 B) per store instruction ----
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const int r = warp * 32 + it * 4 + (lane >> 3), c = lane & 7;
+      const int64_t row = row0 + r;
+      if (row < E)
+        *reinterpret_cast<uint4*>(e_out + row * HID + c * 8) = *reinterpret_cast<const uint4*>(A + sw128(r, c));
+    }
+    __syncwarp();
+  }
+  if (!ok && t == 0) atomicOr(err, (unsigned)kStatTimeout);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Backward of one fused MLP over its rows: recompute z1 = X W1 + b1 and
 // a1 = silu(z1); dA1 = dOut W2^T; dZ = dA1 * silu'(z1); dX = dZ W1^T,
 // scattered to the gather sources; dW1 += X^T dZ, dW2 += a1^T dOut,
@@ -986,6 +1225,25 @@ void launch_bwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
   k_mlp_bwd<MODE, KP, NP><<<grid, MLP_THREADS, sm, st>>>(a);
 }
 
+// Edge MLP of one layer on tcgen05: persistent CTAs, 3 per SM (67 KB of
+// shared memory and 64 TMEM columns each).
+void launch_edge_tc(const bf16* e_in, bf16* e_out, int64_t E, const uint32_t* recv, const uint32_t* send,
+                    const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
+  if (E <= 0) return;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_edge_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES);
+    if (sms <= 0) sms = 152;
+  }
+  int64_t tiles = div_up(E, TC_ROWS);
+  int grid = (int)(tiles < 3 * sms ? tiles : 3 * sms);
+  k_edge_mlp_tc<<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(e_in, e_out, E, recv, send, P, blk.w1, blk.b1, blk.w2,
+                                                        blk.b2, status);
+}
+
 MlpArgs block_args(wbsph_surrogate s, int bi) {
   const Block& b = s->blocks[bi];
   MlpArgs a;
@@ -1036,8 +1294,7 @@ void forward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream
   for (int l = 0; l < L; ++l) {
     MlpArgs a = block_args(s, 2 + 2 * l);
     k_node_proj<<<pgrid, MLP_THREADS, 0, cs>>>(s->hs[l], n, a.w1, s->proj);
-    a.rows = E; a.e = s->es[l]; a.proj = s->proj; a.recv = s->recv; a.send = s->send; a.out_bf = s->es[l + 1];
-    launch_fwd<MODE_SPLIT, 192, 64>(a, E, cs);
+    launch_edge_tc(s->es[l], s->es[l + 1], E, s->recv, s->send, s->proj, a, w.status, cs);
     cudaMemsetAsync(s->aggs[l], 0, (size_t)n * HID * 2, cs);
     if (nf > 0)
       k_sg_aggregate<<<(unsigned)div_up(nf, 4), 128, 0, cs>>>(w.fluid_list, nf, s->row_ptr, s->es[l + 1], s->aggs[l]);
