@@ -40,7 +40,7 @@ constexpr int FEAT = 8;   // padded width of node and edge input features
 constexpr int MLP_THREADS = 128;
 constexpr int TILE = 64;  // rows per tile (4 warps x 16)
 
-enum { MODE_DIRECT = 0, MODE_LIST = 1, MODE_EDGE = 2, MODE_NODE = 3, MODE_SPLIT = 4 };
+enum { MODE_DIRECT = 0, MODE_LIST = 1, MODE_EDGE = 2, MODE_NODE = 3 };
 
 __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
@@ -123,7 +123,6 @@ struct MlpArgs {
   const uint32_t* recv;      // EDGE
   const uint32_t* send;      // EDGE
   const bf16* agg;           // NODE: [n][64]
-  const bf16* proj;          // SPLIT: [n][128] node projections h W1[64:128] | h W1[128:192]
   int kin, nout;             // true widths
   const bf16* w1; const float* b1; const bf16* w2; const float* b2;  // block parameters
   // forward outputs
@@ -198,7 +197,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // copied asynchronously two tiles ahead into a small ring in shared memory.
 template <int MODE>
 __device__ __forceinline__ void issue_idx(const MlpArgs& a, int64_t row0, int64_t rows, uint32_t* I) {
-  if (MODE == MODE_EDGE || MODE == MODE_SPLIT || MODE == MODE_LIST) {
+  if (MODE == MODE_EDGE || MODE == MODE_LIST) {
     const int per = TILE / 4;  // 16-byte chunks per index array
     const int narr = MODE == MODE_LIST ? 1 : 2;
     if (threadIdx.x < per * narr) {
@@ -220,11 +219,6 @@ __device__ __forceinline__ const bf16* chunk_src(const MlpArgs& a, int64_t row, 
                                                  const uint32_t* I) {
   if (MODE == MODE_DIRECT) return a.in + row * FEAT;  // only chunk 0 carries data
   if (MODE == MODE_LIST) return a.in + (int64_t)I[r] * HID + c8 * 8;
-  if (MODE == MODE_SPLIT) {
-    if (c8 < 8) return a.e + row * HID + c8 * 8;
-    if (c8 < 16) return a.proj + (int64_t)I[r] * 2 * HID + (c8 - 8) * 8;
-    return a.proj + (int64_t)I[TILE + r] * 2 * HID + HID + (c8 - 16) * 8;
-  }
   if (MODE == MODE_EDGE) {
     if (c8 < 8) return a.e + row * HID + c8 * 8;
     if (c8 < 16) return a.h + (int64_t)I[r] * HID + (c8 - 8) * 8;
@@ -278,12 +272,9 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
   __syncthreads();
   if (tile * TILE < rows) issue_tile<MODE, KP>(a, tile * TILE, rows, Xb, S::LDX, Ib);
   else cp_async_commit();
-  // SPLIT: only the first 64 inputs (the edge state) go through the GEMM;
-  // the receiver and sender parts arrive as node projections
-  constexpr int KG = MODE == MODE_SPLIT ? HID : KP;
   const bf16 zero = __float2bfloat16(0.f);
-  for (int idx = threadIdx.x; idx < HID * KG; idx += MLP_THREADS) {
-    int n = idx / KG, k = idx % KG;
+  for (int idx = threadIdx.x; idx < HID * KP; idx += MLP_THREADS) {
+    int n = idx / KP, k = idx % KP;
     W1t[n * S::LDX + k] = k < a.kin ? a.w1[k * HID + n] : zero;
   }
   for (int idx = threadIdx.x; idx < NP * HID; idx += MLP_THREADS) {
@@ -309,7 +300,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
 #pragma unroll
-    for (int kt = 0; kt < KG / 16; ++kt) {
+    for (int kt = 0; kt < KP / 16; ++kt) {
       uint32_t af[4];
       ldsm_a(af, X, S::LDX, m0, kt * 16);
 #pragma unroll
@@ -323,20 +314,10 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       int c = nt * 8 + 2 * t;
-      float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-      if (MODE == MODE_SPLIT) {  // + h_recv W1r + h_send W1s from the staged projections
-        const bf16* x0 = X + (m0 + g) * S::LDX + HID + c;
-        const bf16* x1 = X + (m0 + g + 8) * S::LDX + HID + c;
-        float2 r0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(x0));
-        float2 s0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(x0 + HID));
-        float2 r1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(x1));
-        float2 s1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(x1 + HID));
-        p0 = r0.x + s0.x; p1 = r0.y + s0.y; p2 = r1.x + s1.x; p3 = r1.y + s1.y;
-      }
       *reinterpret_cast<__nv_bfloat162*>(A1 + (m0 + g) * S::LDH + c) =
-          __floats2bfloat162_rn(silu(acc[nt][0] + B1[c] + p0), silu(acc[nt][1] + B1[c + 1] + p1));
+          __floats2bfloat162_rn(silu(acc[nt][0] + B1[c]), silu(acc[nt][1] + B1[c + 1]));
       *reinterpret_cast<__nv_bfloat162*>(A1 + (m0 + g + 8) * S::LDH + c) =
-          __floats2bfloat162_rn(silu(acc[nt][2] + B1[c] + p2), silu(acc[nt][3] + B1[c + 1] + p3));
+          __floats2bfloat162_rn(silu(acc[nt][2] + B1[c]), silu(acc[nt][3] + B1[c + 1]));
     }
     __syncwarp();
     float acc2[NP / 8][4];
@@ -372,7 +353,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
         for (int hq = 0; hq < 2; ++hq) {
           int r = m0 + g + hq * 8, o = nt * 8 + 2 * t;
           float v0 = acc2[nt][2 * hq] + B2[o], v1 = acc2[nt][2 * hq + 1] + B2[o + 1];
-          if (MODE == MODE_EDGE || MODE == MODE_SPLIT || MODE == MODE_NODE) {
+          if (MODE == MODE_EDGE || MODE == MODE_NODE) {
             __nv_bfloat162 res = *reinterpret_cast<const __nv_bfloat162*>(X + r * S::LDX + o);
             v0 += __bfloat162float(res.x);
             v1 += __bfloat162float(res.y);
@@ -398,13 +379,14 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
 // Node projections for the split edge MLP. The first layer of the edge MLP
 // acts on [e_ij, h_i, h_j], so z1 = e_ij W1e + h_i W1r + h_j W1s + b1 with
 // W1 = [W1e; W1r; W1s] (64 rows each): the two node terms are computed once
-// per node here, P_i = [h_i W1r | h_i W1s] (BF16, FP32 accumulation), and
+// per node here, P_i = [h_i W1r + b1 | h_i W1s] (BF16, FP32 accumulation), and
 // the edge kernel gathers them instead of h, leaving a 64-wide GEMM per edge.
 // ---------------------------------------------------------------------------
 constexpr int PJ_LD = HID + 8, PJ_LDO = 2 * HID + 8;
 
 __global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restrict__ h, int64_t n,
-                                                           const bf16* __restrict__ w1, bf16* __restrict__ P) {
+                                                           const bf16* __restrict__ w1, const float* __restrict__ b1,
+                                                           bf16* __restrict__ P) {
   __shared__ __align__(16) bf16 Bt[2 * HID * PJ_LD];  // Bt[o][k] = W1[64 + k][o] | W1[128 + k][o - 64]
   __shared__ __align__(16) bf16 At[TILE * PJ_LD];
   __shared__ __align__(16) bf16 Ot[TILE * PJ_LDO];
@@ -443,9 +425,12 @@ __global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restric
 #pragma unroll
     for (int nt = 0; nt < 16; ++nt) {
       int c = nt * 8 + 2 * t;
-      *reinterpret_cast<__nv_bfloat162*>(Ot + (m0 + g) * PJ_LDO + c) = __floats2bfloat162_rn(acc[nt][0], acc[nt][1]);
+      // the first-layer bias rides on the receiver half
+      const float c0 = nt < 8 ? __ldg(b1 + c) : 0.f, c1 = nt < 8 ? __ldg(b1 + c + 1) : 0.f;
+      *reinterpret_cast<__nv_bfloat162*>(Ot + (m0 + g) * PJ_LDO + c) =
+          __floats2bfloat162_rn(acc[nt][0] + c0, acc[nt][1] + c1);
       *reinterpret_cast<__nv_bfloat162*>(Ot + (m0 + g + 8) * PJ_LDO + c) =
-          __floats2bfloat162_rn(acc[nt][2], acc[nt][3]);
+          __floats2bfloat162_rn(acc[nt][2] + c0, acc[nt][3] + c1);
     }
     __syncwarp();
     // the warp's 16 rows of 256 bytes, 16-byte chunks
@@ -475,7 +460,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restric
 constexpr int TC_ROWS = 128;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TILE_BYTES = TC_ROWS * 128;        // 128 rows x 64 BF16
-constexpr size_t TC_SMEM_BYTES = 1024 + 3 * TC_TILE_BYTES + 2 * 8192 + 2 * 64 * 4 + 64;
+constexpr size_t TC_SMEM_BYTES = 1024 + 5 * TC_TILE_BYTES + 2 * 8192 + 64 * 4 + 64;  // 2 load sets, A1, W
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16,
@@ -535,33 +520,41 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+// silu(z) = z sigmoid(z) = z (1 + tanh(z / 2)) / 2 with the hardware tanh
+// approximation (one special-function op instead of an exponential and a
+// reciprocal; absolute error ~1e-3 |z|, below the BF16 rounding of the result)
+__device__ __forceinline__ float silu_tanh(float z) {
+  float h = 0.5f * z, th;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(h));
+  return fmaf(h, th, h);
+}
+
 __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restrict__ e_in, bf16* __restrict__ e_out,
                                                            int64_t E, const uint32_t* __restrict__ recv,
                                                            const uint32_t* __restrict__ send,
                                                            const bf16* __restrict__ P, const bf16* __restrict__ w1,
-                                                           const float* __restrict__ b1g, const bf16* __restrict__ w2,
+                                                           const bf16* __restrict__ w2,
                                                            const float* __restrict__ b2g, unsigned* err) {
   extern __shared__ unsigned char tc_raw[];
   unsigned char* base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);  // 1024-byte aligned
-  unsigned char* A = base;                          // e tile, then the output tile
-  unsigned char* PR = base + TC_TILE_BYTES;         // receiver projections, then silu(z1)
-  unsigned char* PS = base + 2 * TC_TILE_BYTES;     // sender projections
-  unsigned char* B1 = base + 3 * TC_TILE_BYTES;     // W1e^T [n][k]
-  unsigned char* B2 = B1 + 8192;                    // W2^T [n][k]
-  float* b1 = reinterpret_cast<float*>(B2 + 8192);
-  float* b2 = b1 + 64;
+  // two load sets {e tile, sender projections}, then silu(z1), W1e^T, W2^T
+  unsigned char* SET = base;                        // set s: e at s * 32 KB, PS at s * 32 KB + 16 KB
+  unsigned char* A1 = base + 4 * TC_TILE_BYTES;
+  unsigned char* B1 = base + 5 * TC_TILE_BYTES;
+  unsigned char* B2 = B1 + 8192;
+  float* b2 = reinterpret_cast<float*>(B2 + 8192);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(b2 + 64);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
-  // weights (K-major swizzled), biases, barrier, tensor memory
+  // weights (K-major swizzled), bias, barrier, tensor memory
   for (int idx = t; idx < 64 * 64; idx += TC_THREADS) {
     int n = idx >> 6, k = idx & 63;
     uint32_t off = sw128(n, k >> 3) + (k & 7) * 2;
     *reinterpret_cast<bf16*>(B1 + off) = w1[k * HID + n];
     *reinterpret_cast<bf16*>(B2 + off) = w2[k * HID + n];
   }
-  if (t < 64) { b1[t] = b1g[t]; b2[t] = b2g[t]; }
+  if (t < 64) b2[t] = b2g[t];
   const uint32_t mb = smem_u32(mbar);
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
@@ -577,45 +570,71 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
-  const uint64_t dA = tc_desc(smem_u32(A)), dPR = tc_desc(smem_u32(PR));
-  const uint64_t dB1 = tc_desc(smem_u32(B1)), dB2 = tc_desc(smem_u32(B2));
+  const uint64_t dA1 = tc_desc(smem_u32(A1)), dB1 = tc_desc(smem_u32(B1)), dB2 = tc_desc(smem_u32(B2));
+  const int64_t ntiles = div_up(E, TC_ROWS);
+
+  // gather of row t of a tile into load set `set`: e row and sender projection
+  auto issue = [&](int64_t tile, int set, uint32_t sd) {
+    const int64_t row = tile * TC_ROWS + t;
+    const bool valid = tile < ntiles && row < E;
+    const bf16* se = e_in + (valid ? row : 0) * HID;
+    const bf16* ss = P + (int64_t)(valid ? sd : 0u) * 2 * HID + HID;
+    unsigned char* Ae = SET + set * 2 * TC_TILE_BYTES;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      cp_async16(Ae + sw128(t, c), se + c * 8, valid);
+      cp_async16(Ae + TC_TILE_BYTES + sw128(t, c), ss + c * 8, valid);
+    }
+    cp_async_commit();
+  };
+  auto index_of = [&](const uint32_t* a, int64_t tile) -> uint32_t {
+    const int64_t row = tile * TC_ROWS + t;
+    return (tile < ntiles && row < E) ? __ldg(a + row) : 0u;
+  };
+
+  int64_t tile = blockIdx.x;
+  const int64_t stride = gridDim.x;
+  // indices: receiver of the current tile, sender of the next tile, both one tile ahead
+  uint32_t rv_cur = index_of(recv, tile);
+  issue(tile, 0, index_of(send, tile));
+  uint32_t sd_next = index_of(send, tile + stride);
+  uint32_t rv_next = index_of(recv, tile + stride);
   uint32_t phase = 0;
   bool ok = true;
 
-  for (int64_t tile = blockIdx.x; ok && tile * TC_ROWS < E; tile += gridDim.x) {
+  for (int it = 0; tile < ntiles; ++it, tile += stride) {
+    const int cur = it & 1;
     const int64_t row0 = tile * TC_ROWS;
-    // ---- loads: row t of the e tile and of both projection tiles ----
-    {
-      const int64_t row = row0 + t;
-      const bool valid = row < E;
-      const uint32_t rv = valid ? recv[row] : 0u, sd = valid ? send[row] : 0u;
-      const bf16* se = e_in + (valid ? row : 0) * HID;
-      const bf16* sr = P + (int64_t)rv * 2 * HID;
-      const bf16* ss = P + (int64_t)sd * 2 * HID + HID;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        cp_async16(A + sw128(t, c), se + c * 8, valid);
-        cp_async16(PR + sw128(t, c), sr + c * 8, valid);
-        cp_async16(PS + sw128(t, c), ss + c * 8, valid);
-      }
-      cp_async_commit();
-      cp_async_wait<0>();
-      fence_async_smem();  // the e tile is read by the tensor core
-    }
+    unsigned char* A = SET + cur * 2 * TC_TILE_BYTES;
+    unsigned char* PS = A + TC_TILE_BYTES;
+    cp_async_wait<0>();
+    fence_async_smem();  // the e tile is read by the tensor core
     tc_fence_before();
     __syncthreads();
     // ---- z1 = e W1e ----
     if (t == 0) {
       tc_fence_after();
+      const uint64_t dA = tc_desc(smem_u32(A));
 #pragma unroll
       for (int k = 0; k < 4; ++k) tc_mma(tmem, dA + 2 * k, dB1 + 2 * k, k > 0);
       tc_commit(mb);
     }
+    // next tile's gathers overlap this tile's two GEMMs and epilogues
+    issue(tile + stride, cur ^ 1, sd_next);
+    const uint32_t rv = rv_cur;
+    rv_cur = rv_next;
+    sd_next = index_of(send, tile + 2 * stride);
+    rv_next = index_of(recv, tile + 2 * stride);
+    // receiver projections (+ b1) of this row: consecutive rows share receivers
+    uint4 pr[8];
+    const uint4* prg = reinterpret_cast<const uint4*>(P + (int64_t)rv * 2 * HID);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) pr[c] = __ldg(prg + c);
     bool w_ok = mbar_wait(mb, phase);
     phase ^= 1u;
     if (!__syncthreads_and(w_ok)) { ok = false; break; }
     tc_fence_after();
-    // ---- silu(z1 + b1 + P_recv + P_send) -> PR (BF16, swizzled) ----
+    // ---- silu(z1 + P_recv + P_send) -> A1 (BF16, swizzled) ----
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       float v[16];
@@ -623,22 +642,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = 2 * q + h;
-        uint4 pr = *reinterpret_cast<const uint4*>(PR + sw128(t, c));
         uint4 ps = *reinterpret_cast<const uint4*>(PS + sw128(t, c));
-        const __nv_bfloat162* r2 = reinterpret_cast<const __nv_bfloat162*>(&pr);
+        const __nv_bfloat162* r2 = reinterpret_cast<const __nv_bfloat162*>(&pr[c]);
         const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(&ps);
         uint4 o;
         uint32_t* o32 = reinterpret_cast<uint32_t*>(&o);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int col = c * 8 + 2 * j;
           float2 fr = __bfloat1622float2(r2[j]), fs = __bfloat1622float2(s2[j]);
-          float z0 = v[h * 8 + 2 * j] + b1[col] + fr.x + fs.x;
-          float z1 = v[h * 8 + 2 * j + 1] + b1[col + 1] + fr.y + fs.y;
-          __nv_bfloat162 a2 = __floats2bfloat162_rn(silu(z0), silu(z1));
+          __nv_bfloat162 a2 = __floats2bfloat162_rn(silu_tanh(v[h * 8 + 2 * j] + fr.x + fs.x),
+                                                    silu_tanh(v[h * 8 + 2 * j + 1] + fr.y + fs.y));
           o32[j] = *reinterpret_cast<uint32_t*>(&a2);
         }
-        *reinterpret_cast<uint4*>(PR + sw128(t, c)) = o;
+        *reinterpret_cast<uint4*>(A1 + sw128(t, c)) = o;
       }
     }
     fence_async_smem();  // silu(z1) is read by the tensor core
@@ -648,7 +664,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     if (t == 0) {
       tc_fence_after();
 #pragma unroll
-      for (int k = 0; k < 4; ++k) tc_mma(tmem, dPR + 2 * k, dB2 + 2 * k, k > 0);
+      for (int k = 0; k < 4; ++k) tc_mma(tmem, dA1 + 2 * k, dB2 + 2 * k, k > 0);
       tc_commit(mb);
     }
     w_ok = mbar_wait(mb, phase);
@@ -681,14 +697,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     __syncwarp();
     // ---- the warp's 32 output rows, 4 whole rows (512 B) per store instruction ----
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
-      const int r = warp * 32 + it * 4 + (lane >> 3), c = lane & 7;
+    for (int k = 0; k < 8; ++k) {
+      const int r = warp * 32 + k * 4 + (lane >> 3), c = lane & 7;
       const int64_t row = row0 + r;
       if (row < E)
         *reinterpret_cast<uint4*>(e_out + row * HID + c * 8) = *reinterpret_cast<const uint4*>(A + sw128(r, c));
     }
     __syncwarp();
   }
+  cp_async_wait<0>();  // gathers issued for tiles past the end
   if (!ok && t == 0) atomicOr(err, (unsigned)kStatTimeout);
   tc_fence_before();
   __syncthreads();
@@ -1225,7 +1242,7 @@ void launch_bwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
   k_mlp_bwd<MODE, KP, NP><<<grid, MLP_THREADS, sm, st>>>(a);
 }
 
-// Edge MLP of one layer on tcgen05: persistent CTAs, 3 per SM (67 KB of
+// Edge MLP of one layer on tcgen05: persistent CTAs, 2 per SM (99 KB of
 // shared memory and 64 TMEM columns each).
 void launch_edge_tc(const bf16* e_in, bf16* e_out, int64_t E, const uint32_t* recv, const uint32_t* send,
                     const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
@@ -1239,9 +1256,9 @@ void launch_edge_tc(const bf16* e_in, bf16* e_out, int64_t E, const uint32_t* re
     if (sms <= 0) sms = 152;
   }
   int64_t tiles = div_up(E, TC_ROWS);
-  int grid = (int)(tiles < 3 * sms ? tiles : 3 * sms);
-  k_edge_mlp_tc<<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(e_in, e_out, E, recv, send, P, blk.w1, blk.b1, blk.w2,
-                                                        blk.b2, status);
+  int grid = (int)(tiles < 2 * sms ? tiles : 2 * sms);
+  k_edge_mlp_tc<<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(e_in, e_out, E, recv, send, P, blk.w1, blk.w2, blk.b2,
+                                                        status);
 }
 
 MlpArgs block_args(wbsph_surrogate s, int bi) {
@@ -1293,7 +1310,7 @@ void forward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream
   const int pgrid = (int)(div_up(n > 0 ? n : 1, TILE) < 152 * 4 ? div_up(n > 0 ? n : 1, TILE) : 152 * 4);
   for (int l = 0; l < L; ++l) {
     MlpArgs a = block_args(s, 2 + 2 * l);
-    k_node_proj<<<pgrid, MLP_THREADS, 0, cs>>>(s->hs[l], n, a.w1, s->proj);
+    k_node_proj<<<pgrid, MLP_THREADS, 0, cs>>>(s->hs[l], n, a.w1, a.b1, s->proj);
     launch_edge_tc(s->es[l], s->es[l + 1], E, s->recv, s->send, s->proj, a, w.status, cs);
     cudaMemsetAsync(s->aggs[l], 0, (size_t)n * HID * 2, cs);
     if (nf > 0)
