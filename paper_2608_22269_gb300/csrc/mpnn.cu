@@ -28,6 +28,8 @@ cudaStream_t handle_stream(wbsph_handle h);
 int handle_device(wbsph_handle h);
 int handle_fail(wbsph_handle h, int code, const char* msg);
 void launch_scan_exclusive(uint32_t* data, int64_t total, cudaStream_t st);
+void launch_scan_exclusive_chunked(uint32_t* data, int64_t total, uint32_t* scratch, cudaStream_t st);
+int scan_scratch_words(int64_t total);
 }  // namespace wbsph
 
 using namespace wbsph;
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restric
 constexpr int TC_ROWS = 128;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TILE_BYTES = TC_ROWS * 128;        // 128 rows x 64 BF16
-constexpr size_t TC_SMEM_BYTES = 1024 + 5 * TC_TILE_BYTES + 2 * 8192 + 64 * 4 + 64;  // 2 load sets, A1, W
+constexpr size_t TC_SMEM_BYTES = 1024 + 5 * TC_TILE_BYTES + 2 * 8192 + 2 * 64 * 4 + 64;  // 2 load sets, A1, W
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16,
@@ -529,10 +531,15 @@ __device__ __forceinline__ float silu_tanh(float z) {
   return fmaf(h, th, h);
 }
 
+// ENC: the same kernel runs an encoder MLP on rows of 8 BF16 input features
+// (K = 16, zero padded): z1 = f W1 + b1, out = silu(z1) W2 + b2, no
+// projections, no residual.
+template <bool ENC>
 __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restrict__ e_in, bf16* __restrict__ e_out,
                                                            int64_t E, const uint32_t* __restrict__ recv,
                                                            const uint32_t* __restrict__ send,
                                                            const bf16* __restrict__ P, const bf16* __restrict__ w1,
+                                                           int kin, const float* __restrict__ b1g,
                                                            const bf16* __restrict__ w2,
                                                            const float* __restrict__ b2g, unsigned* err) {
   extern __shared__ unsigned char tc_raw[];
@@ -543,7 +550,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   unsigned char* B1 = base + 5 * TC_TILE_BYTES;
   unsigned char* B2 = B1 + 8192;
   float* b2 = reinterpret_cast<float*>(B2 + 8192);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(b2 + 64);
+  float* b1 = b2 + 64;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(b1 + 64);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
@@ -551,10 +559,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   for (int idx = t; idx < 64 * 64; idx += TC_THREADS) {
     int n = idx >> 6, k = idx & 63;
     uint32_t off = sw128(n, k >> 3) + (k & 7) * 2;
-    *reinterpret_cast<bf16*>(B1 + off) = w1[k * HID + n];
+    *reinterpret_cast<bf16*>(B1 + off) = k < kin ? w1[k * HID + n] : __float2bfloat16(0.f);
     *reinterpret_cast<bf16*>(B2 + off) = w2[k * HID + n];
   }
-  if (t < 64) b2[t] = b2g[t];
+  if (t < 64) {
+    b2[t] = b2g[t];
+    b1[t] = ENC ? b1g[t] : 0.f;
+  }
   const uint32_t mb = smem_u32(mbar);
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
@@ -577,19 +588,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   auto issue = [&](int64_t tile, int set, uint32_t sd) {
     const int64_t row = tile * TC_ROWS + t;
     const bool valid = tile < ntiles && row < E;
-    const bf16* se = e_in + (valid ? row : 0) * HID;
-    const bf16* ss = P + (int64_t)(valid ? sd : 0u) * 2 * HID + HID;
     unsigned char* Ae = SET + set * 2 * TC_TILE_BYTES;
+    if (ENC) {  // 8 features, then zeros up to K = 16
+      cp_async16(Ae + sw128(t, 0), e_in + (valid ? row : 0) * FEAT, valid);
+      cp_async16(Ae + sw128(t, 1), e_in, false);
+    } else {
+      const bf16* se = e_in + (valid ? row : 0) * HID;
+      const bf16* ss = P + (int64_t)(valid ? sd : 0u) * 2 * HID + HID;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      cp_async16(Ae + sw128(t, c), se + c * 8, valid);
-      cp_async16(Ae + TC_TILE_BYTES + sw128(t, c), ss + c * 8, valid);
+      for (int c = 0; c < 8; ++c) {
+        cp_async16(Ae + sw128(t, c), se + c * 8, valid);
+        cp_async16(Ae + TC_TILE_BYTES + sw128(t, c), ss + c * 8, valid);
+      }
     }
     cp_async_commit();
   };
   auto index_of = [&](const uint32_t* a, int64_t tile) -> uint32_t {
     const int64_t row = tile * TC_ROWS + t;
-    return (tile < ntiles && row < E) ? __ldg(a + row) : 0u;
+    return (!ENC && tile < ntiles && row < E) ? __ldg(a + row) : 0u;
   };
 
   int64_t tile = blockIdx.x;
@@ -616,7 +632,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
       tc_fence_after();
       const uint64_t dA = tc_desc(smem_u32(A));
 #pragma unroll
-      for (int k = 0; k < 4; ++k) tc_mma(tmem, dA + 2 * k, dB1 + 2 * k, k > 0);
+      for (int k = 0; k < (ENC ? 1 : 4); ++k) tc_mma(tmem, dA + 2 * k, dB1 + 2 * k, k > 0);
       tc_commit(mb);
     }
     // next tile's gathers overlap this tile's two GEMMs and epilogues
@@ -627,9 +643,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     rv_next = index_of(recv, tile + 2 * stride);
     // receiver projections (+ b1) of this row: consecutive rows share receivers
     uint4 pr[8];
-    const uint4* prg = reinterpret_cast<const uint4*>(P + (int64_t)rv * 2 * HID);
+    if (!ENC) {
+      const uint4* prg = reinterpret_cast<const uint4*>(P + (int64_t)rv * 2 * HID);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) pr[c] = __ldg(prg + c);
+      for (int c = 0; c < 8; ++c) pr[c] = __ldg(prg + c);
+    }
     bool w_ok = mbar_wait(mb, phase);
     phase ^= 1u;
     if (!__syncthreads_and(w_ok)) { ok = false; break; }
@@ -642,17 +660,27 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = 2 * q + h;
-        uint4 ps = *reinterpret_cast<const uint4*>(PS + sw128(t, c));
-        const __nv_bfloat162* r2 = reinterpret_cast<const __nv_bfloat162*>(&pr[c]);
-        const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(&ps);
         uint4 o;
         uint32_t* o32 = reinterpret_cast<uint32_t*>(&o);
+        if (ENC) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float2 fr = __bfloat1622float2(r2[j]), fs = __bfloat1622float2(s2[j]);
-          __nv_bfloat162 a2 = __floats2bfloat162_rn(silu_tanh(v[h * 8 + 2 * j] + fr.x + fs.x),
-                                                    silu_tanh(v[h * 8 + 2 * j + 1] + fr.y + fs.y));
-          o32[j] = *reinterpret_cast<uint32_t*>(&a2);
+          for (int j = 0; j < 4; ++j) {
+            const int col = c * 8 + 2 * j;
+            __nv_bfloat162 a2 = __floats2bfloat162_rn(silu_tanh(v[h * 8 + 2 * j] + b1[col]),
+                                                      silu_tanh(v[h * 8 + 2 * j + 1] + b1[col + 1]));
+            o32[j] = *reinterpret_cast<uint32_t*>(&a2);
+          }
+        } else {
+          uint4 ps = *reinterpret_cast<const uint4*>(PS + sw128(t, c));
+          const __nv_bfloat162* r2 = reinterpret_cast<const __nv_bfloat162*>(&pr[c]);
+          const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(&ps);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float2 fr = __bfloat1622float2(r2[j]), fs = __bfloat1622float2(s2[j]);
+            __nv_bfloat162 a2 = __floats2bfloat162_rn(silu_tanh(v[h * 8 + 2 * j] + fr.x + fs.x),
+                                                      silu_tanh(v[h * 8 + 2 * j + 1] + fr.y + fs.y));
+            o32[j] = *reinterpret_cast<uint32_t*>(&a2);
+          }
         }
         *reinterpret_cast<uint4*>(A1 + sw128(t, c)) = o;
       }
@@ -679,7 +707,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = 2 * q + h;
-        uint4 ev = *reinterpret_cast<const uint4*>(A + sw128(t, c));
+        uint4 ev = make_uint4(0u, 0u, 0u, 0u);  // residual (none for an encoder)
+        if (!ENC) ev = *reinterpret_cast<const uint4*>(A + sw128(t, c));
         const __nv_bfloat162* e2 = reinterpret_cast<const __nv_bfloat162*>(&ev);
         uint4 o;
         uint32_t* o32 = reinterpret_cast<uint32_t*>(&o);
@@ -1112,7 +1141,7 @@ struct wbsph_surrogate_s {
   int64_t adam_t = 0;
   // graph and activations, sized on demand
   int64_t cap_n = 0, cap_nf = 0, cap_e = 0;
-  uint32_t *cnt = nullptr, *row_ptr = nullptr, *recv = nullptr, *send = nullptr;
+  uint32_t *cnt = nullptr, *row_ptr = nullptr, *recv = nullptr, *send = nullptr, *scan_tmp = nullptr;
   bf16 *efeat = nullptr, *nfeat = nullptr, *proj = nullptr;
   std::vector<bf16*> hs, es, aggs;
   float *out = nullptr, *dout = nullptr, *dh = nullptr, *de = nullptr, *dagg = nullptr;
@@ -1167,8 +1196,9 @@ void dfree(void* p) {
 
 void free_graph(wbsph_surrogate s) {
   dfree(s->cnt); dfree(s->row_ptr); dfree(s->recv); dfree(s->send); dfree(s->efeat); dfree(s->nfeat);
-  dfree(s->proj);
+  dfree(s->proj); dfree(s->scan_tmp);
   s->proj = nullptr;
+  s->scan_tmp = nullptr;
   for (auto* q : s->hs) dfree(q);
   for (auto* q : s->es) dfree(q);
   for (auto* q : s->aggs) dfree(q);
@@ -1186,7 +1216,8 @@ int ensure_nodes(wbsph_surrogate s, int64_t n, int64_t nf) {
   s->cap_n = n; s->cap_nf = nf;
   bool ok = dalloc(&s->cnt, nf + 1) && dalloc(&s->row_ptr, nf + 1) && dalloc(&s->nfeat, n * FEAT) &&
             dalloc(&s->out, nf * 4) && dalloc(&s->dout, nf * 4) && dalloc(&s->dh, n * HID) &&
-            dalloc(&s->dagg, n * HID) && dalloc(&s->proj, n * 2 * HID);
+            dalloc(&s->dagg, n * HID) && dalloc(&s->proj, n * 2 * HID) &&
+            dalloc(&s->scan_tmp, (size_t)scan_scratch_words(nf + 1));
   for (int l = 0; ok && l <= s->layers; ++l) {
     bf16* q = nullptr;
     ok = dalloc(&q, n * HID);
@@ -1242,23 +1273,29 @@ void launch_bwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
   k_mlp_bwd<MODE, KP, NP><<<grid, MLP_THREADS, sm, st>>>(a);
 }
 
-// Edge MLP of one layer on tcgen05: persistent CTAs, 2 per SM (99 KB of
-// shared memory and 64 TMEM columns each).
-void launch_edge_tc(const bf16* e_in, bf16* e_out, int64_t E, const uint32_t* recv, const uint32_t* send,
-                    const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
-  if (E <= 0) return;
+template <bool ENC>
+void launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, const uint32_t* send,
+               const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
+  if (rows <= 0) return;
   static int sms = 0;
   if (!sms) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_edge_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES);
+    cudaFuncSetAttribute(k_edge_mlp_tc<ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES);
     if (sms <= 0) sms = 152;
   }
-  int64_t tiles = div_up(E, TC_ROWS);
+  int64_t tiles = div_up(rows, TC_ROWS);
   int grid = (int)(tiles < 2 * sms ? tiles : 2 * sms);
-  k_edge_mlp_tc<<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(e_in, e_out, E, recv, send, P, blk.w1, blk.w2, blk.b2,
-                                                        status);
+  k_edge_mlp_tc<ENC><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(in, out, rows, recv, send, P, blk.w1, blk.kin, blk.b1,
+                                                              blk.w2, blk.b2, status);
+}
+
+// Edge MLP of one layer on tcgen05: persistent CTAs, 2 per SM (99 KB of
+// shared memory and 64 TMEM columns each).
+void launch_edge_tc(const bf16* e_in, bf16* e_out, int64_t E, const uint32_t* recv, const uint32_t* send,
+                    const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
+  launch_tc<false>(e_in, e_out, E, recv, send, P, blk, status, st);
 }
 
 MlpArgs block_args(wbsph_surrogate s, int bi) {
@@ -1280,7 +1317,7 @@ int build_graph(wbsph_surrogate s, const Params& p, const State& st, const Work&
   if (nf > 0) k_sg_count<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p, st, w, n, nf, s->cnt);
   cudaMemsetAsync(s->cnt + nf, 0, 4, cs);
   cudaMemcpyAsync(s->row_ptr, s->cnt, (nf + 1) * 4, cudaMemcpyDeviceToDevice, cs);
-  launch_scan_exclusive(s->row_ptr, nf + 1, cs);
+  launch_scan_exclusive_chunked(s->row_ptr, nf + 1, s->scan_tmp, cs);
   uint32_t E = 0;
   cudaMemcpyAsync(&E, s->row_ptr + nf, 4, cudaMemcpyDeviceToHost, cs);
   if (cudaStreamSynchronize(cs) != cudaSuccess) return sfail(s, WBSPH_E_CUDA, "graph build");
@@ -1297,16 +1334,9 @@ int build_graph(wbsph_surrogate s, const Params& p, const State& st, const Work&
 void forward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream_t cs) {
   const int64_t E = s->E;
   int L = s->layers;
-  {  // node encoder
-    MlpArgs a = block_args(s, 0);
-    a.rows = n; a.in = s->nfeat; a.out_bf = s->hs[0];
-    launch_fwd<MODE_DIRECT, 16, 64>(a, n, cs);
-  }
-  {  // edge encoder
-    MlpArgs a = block_args(s, 1);
-    a.rows = E; a.in = s->efeat; a.out_bf = s->es[0];
-    launch_fwd<MODE_DIRECT, 16, 64>(a, E, cs);
-  }
+  // node and edge encoders (tcgen05, K = 16)
+  launch_tc<true>(s->nfeat, s->hs[0], n, nullptr, nullptr, nullptr, block_args(s, 0), w.status, cs);
+  launch_tc<true>(s->efeat, s->es[0], E, nullptr, nullptr, nullptr, block_args(s, 1), w.status, cs);
   const int pgrid = (int)(div_up(n > 0 ? n : 1, TILE) < 152 * 4 ? div_up(n > 0 ? n : 1, TILE) : 152 * 4);
   for (int l = 0; l < L; ++l) {
     MlpArgs a = block_args(s, 2 + 2 * l);

@@ -188,6 +188,78 @@ void launch_scan_exclusive(uint32_t* data, int64_t total, cudaStream_t st) {
   k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(data, total);
 }
 
+// ---------------------------------------------------------------------------
+// Exclusive scan of a long array by chunks of SCAN_CHUNK: chunk sums, one
+// scan of the sums, then each chunk scanned in place from its offset.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_PER;
+
+// inclusive scan of one value per thread over the block; *total = block sum
+__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* wsum, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    uint32_t o = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane >= off) v += o;
+  }
+  if (lane == 31) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < SCAN_THREADS / 32 ? wsum[lane] : 0u;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t o = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += o;
+    }
+    wsum[lane] = w;  // inclusive warp-total prefix
+  }
+  __syncthreads();
+  if (total) *total = wsum[SCAN_THREADS / 32 - 1];
+  return v + (warp > 0 ? wsum[warp - 1] : 0u);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_chunk_sums(const uint32_t* __restrict__ data, int64_t total,
+                                                            uint32_t* __restrict__ sums) {
+  __shared__ uint32_t wsum[32];
+  const int64_t b0 = blockIdx.x * (int64_t)SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_PER;
+  uint32_t v = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER; ++k) v += b0 + k < total ? data[b0 + k] : 0u;
+  uint32_t tot;
+  block_inclusive_scan(v, wsum, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_chunk_scan(uint32_t* __restrict__ data, int64_t total,
+                                                            const uint32_t* __restrict__ offs) {
+  __shared__ uint32_t wsum[32];
+  const int64_t b0 = blockIdx.x * (int64_t)SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_PER;
+  uint32_t x[SCAN_PER], v = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER; ++k) {
+    x[k] = b0 + k < total ? data[b0 + k] : 0u;
+    v += x[k];
+  }
+  uint32_t run = block_inclusive_scan(v, wsum, nullptr) - v + offs[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_PER; ++k) {
+    if (b0 + k < total) data[b0 + k] = run;
+    run += x[k];
+  }
+}
+
+int scan_scratch_words(int64_t total) { return (int)div_up(total > 0 ? total : 1, SCAN_CHUNK); }
+
+// In-place exclusive scan of `total` counts; scratch holds scan_scratch_words(total) words.
+void launch_scan_exclusive_chunked(uint32_t* data, int64_t total, uint32_t* scratch, cudaStream_t st) {
+  if (total <= 0) return;
+  const int64_t nb = div_up(total, SCAN_CHUNK);
+  k_chunk_sums<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(data, total, scratch);
+  k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(scratch, nb);
+  k_chunk_scan<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(data, total, scratch);
+}
+
 // histogram table (256 rows x tiles) followed by the 256 row totals
 int radix_sort_scratch_words(int64_t n) { return (int)(256 * div_up(n > 0 ? n : 1, RS_TILE) + 256); }
 
