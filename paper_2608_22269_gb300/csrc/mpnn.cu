@@ -613,6 +613,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   // indices: receiver of the current tile, sender of the next tile, both one tile ahead
   uint32_t rv_cur = index_of(recv, tile);
   issue(tile, 0, index_of(send, tile));
+  // receiver projections (+ b1) of this thread's row, loaded one tile ahead
+  // (consecutive rows share receivers, so these mostly hit in L1/L2)
+  uint4 pr[8];
+  auto load_pr = [&](uint32_t rv) {
+    if (!ENC) {
+      const uint4* prg = reinterpret_cast<const uint4*>(P + (int64_t)rv * 2 * HID);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) pr[c] = __ldg(prg + c);
+    }
+  };
+  load_pr(rv_cur);
   uint32_t sd_next = index_of(send, tile + stride);
   uint32_t rv_next = index_of(recv, tile + stride);
   uint32_t phase = 0;
@@ -637,17 +648,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     }
     // next tile's gathers overlap this tile's two GEMMs and epilogues
     issue(tile + stride, cur ^ 1, sd_next);
-    const uint32_t rv = rv_cur;
     rv_cur = rv_next;
     sd_next = index_of(send, tile + 2 * stride);
     rv_next = index_of(recv, tile + 2 * stride);
-    // receiver projections (+ b1) of this row: consecutive rows share receivers
-    uint4 pr[8];
-    if (!ENC) {
-      const uint4* prg = reinterpret_cast<const uint4*>(P + (int64_t)rv * 2 * HID);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) pr[c] = __ldg(prg + c);
-    }
     bool w_ok = mbar_wait(mb, phase);
     phase ^= 1u;
     if (!__syncthreads_and(w_ok)) { ok = false; break; }
@@ -688,6 +691,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     fence_async_smem();  // silu(z1) is read by the tensor core
     tc_fence_before();
     __syncthreads();
+    load_pr(rv_cur);  // next tile's receiver projections
     // ---- z2 = silu(z1) W2 (same TMEM columns) ----
     if (t == 0) {
       tc_fence_after();
