@@ -454,15 +454,16 @@ __global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restric
 // Operands sit in shared memory in the K-major 128-byte-swizzled layout the
 // tensor core reads through matrix descriptors (row r of 64 BF16 = 128 B at
 // r * 128, 16-byte chunk c stored at chunk c ^ (r % 8); 8-row groups 1024 B
-// apart); the FP32 accumulator lives in tensor memory (TMEM, 64 columns, lane
-// = tile row) and is read back by the warp that owns those 32 lanes. One
-// thread issues the MMAs and their commit to an mbarrier; every wait on the
-// mbarrier is bounded and a timeout is reported through the error word.
+// apart); the FP32 accumulators live in tensor memory (TMEM, 64 columns per
+// tile in flight, lane = tile row) and are read back by the warp that owns
+// those 32 lanes. One thread issues the MMAs and their commit to an
+// mbarrier; every wait on an mbarrier is bounded and a timeout is reported
+// through the error word.
 // ---------------------------------------------------------------------------
 constexpr int TC_ROWS = 128;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TILE_BYTES = TC_ROWS * 128;        // 128 rows x 64 BF16
-constexpr size_t TC_SMEM_BYTES = 1024 + 5 * TC_TILE_BYTES + 2 * 8192 + 2 * 64 * 4 + 64;  // 2 load sets, A1, W
+constexpr size_t TC_SMEM_BYTES = 1024 + 4 * TC_TILE_BYTES + 2 * 8192 + 2 * 64 * 4 + 64;  // 2 slots, W, biases
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16,
@@ -534,6 +535,13 @@ __device__ __forceinline__ float silu_tanh(float z) {
 // ENC: the same kernel runs an encoder MLP on rows of 8 BF16 input features
 // (K = 16, zero padded): z1 = f W1 + b1, out = silu(z1) W2 + b2, no
 // projections, no residual.
+//
+// Pipeline over the CTA's tiles, two slots s (tile parity), each with its
+// own e tile, sender-projection tile (which then holds silu(z1)), TMEM
+// accumulator (64 columns) and mbarrier. Iteration i runs: epilogue 1 of tile
+// i, MMA2 of tile i issued, MMA1 of tile i+1 issued (its gathers arrived
+// during iteration i-1), epilogue 2 and store of tile i, gathers of tile i+2
+// into slot s. So each tile's GEMMs run while the other tile's epilogues do.
 template <bool ENC>
 __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restrict__ e_in, bf16* __restrict__ e_out,
                                                            int64_t E, const uint32_t* __restrict__ recv,
@@ -544,18 +552,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
                                                            const float* __restrict__ b2g, unsigned* err) {
   extern __shared__ unsigned char tc_raw[];
   unsigned char* base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);  // 1024-byte aligned
-  // two load sets {e tile, sender projections}, then silu(z1), W1e^T, W2^T
-  unsigned char* SET = base;                        // set s: e at s * 32 KB, PS at s * 32 KB + 16 KB
-  unsigned char* A1 = base + 4 * TC_TILE_BYTES;
-  unsigned char* B1 = base + 5 * TC_TILE_BYTES;
-  unsigned char* B2 = B1 + 8192;
+  // slot s: e tile at s * 32 KB, sender projections / silu(z1) at s * 32 KB + 16 KB
+  unsigned char* B1 = base + 4 * TC_TILE_BYTES;  // W1e^T [n][k]
+  unsigned char* B2 = B1 + 8192;                 // W2^T [n][k]
   float* b2 = reinterpret_cast<float*>(B2 + 8192);
   float* b1 = b2 + 64;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(b1 + 64);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(b1 + 64);  // one per slot
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  auto Et = [&](int sl) { return base + sl * 2 * TC_TILE_BYTES; };
+  auto Pt = [&](int sl) { return base + sl * 2 * TC_TILE_BYTES + TC_TILE_BYTES; };
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
-  // weights (K-major swizzled), bias, barrier, tensor memory
+  // weights (K-major swizzled), biases, barriers, tensor memory
   for (int idx = t; idx < 64 * 64; idx += TC_THREADS) {
     int n = idx >> 6, k = idx & 63;
     uint32_t off = sw128(n, k >> 3) + (k & 7) * 2;
@@ -566,39 +574,46 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     b2[t] = b2g[t];
     b1[t] = ENC ? b1g[t] : 0.f;
   }
-  const uint32_t mb = smem_u32(mbar);
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(smem_u32(tslot))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(smem_u32(tslot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
+  const uint32_t tmem = *tslot;  // slot s accumulator: columns 64 s .. 64 s + 63
   const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
-  const uint64_t dA1 = tc_desc(smem_u32(A1)), dB1 = tc_desc(smem_u32(B1)), dB2 = tc_desc(smem_u32(B2));
+  const uint64_t dB1 = tc_desc(smem_u32(B1)), dB2 = tc_desc(smem_u32(B2));
   const int64_t ntiles = div_up(E, TC_ROWS);
+  const int64_t stride = gridDim.x;
 
-  // gather of row t of a tile into load set `set`: e row and sender projection
-  auto issue = [&](int64_t tile, int set, uint32_t sd) {
-    const int64_t row = tile * TC_ROWS + t;
-    const bool valid = tile < ntiles && row < E;
-    unsigned char* Ae = SET + set * 2 * TC_TILE_BYTES;
-    if (ENC) {  // 8 features, then zeros up to K = 16
+  // gathers of tile `tile` into slot `sl`: e rows (or features) and sender
+  // projections of the warp's 32 rows. Edge rows: lane l moves 16-byte chunk
+  // l % 8 of row 4 k + l / 8, so each instruction covers 4 whole rows
+  // (512 contiguous bytes of e); `sd` is the sender of this thread's row.
+  auto issue = [&](int64_t tile, int sl, uint32_t sd) {
+    unsigned char* Ae = Et(sl);
+    if (ENC) {  // row t: 8 features, then zeros up to K = 16
+      const int64_t row = tile * TC_ROWS + t;
+      const bool valid = tile < ntiles && row < E;
       cp_async16(Ae + sw128(t, 0), e_in + (valid ? row : 0) * FEAT, valid);
       cp_async16(Ae + sw128(t, 1), e_in, false);
     } else {
-      const bf16* se = e_in + (valid ? row : 0) * HID;
-      const bf16* ss = P + (int64_t)(valid ? sd : 0u) * 2 * HID + HID;
+      const int c = lane & 7;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        cp_async16(Ae + sw128(t, c), se + c * 8, valid);
-        cp_async16(Ae + TC_TILE_BYTES + sw128(t, c), ss + c * 8, valid);
+      for (int k = 0; k < 8; ++k) {
+        const int rl = k * 4 + (lane >> 3), r = warp * 32 + rl;
+        const uint32_t sdr = __shfl_sync(0xffffffffu, sd, rl);
+        const int64_t row = tile * TC_ROWS + r;
+        const bool valid = tile < ntiles && row < E;
+        cp_async16(Ae + sw128(r, c), e_in + (valid ? row : 0) * HID + c * 8, valid);
+        cp_async16(Pt(sl) + sw128(r, c), P + (int64_t)(valid ? sdr : 0u) * 2 * HID + HID + c * 8, valid);
       }
     }
     cp_async_commit();
@@ -607,14 +622,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     const int64_t row = tile * TC_ROWS + t;
     return (!ENC && tile < ntiles && row < E) ? __ldg(a + row) : 0u;
   };
-
-  int64_t tile = blockIdx.x;
-  const int64_t stride = gridDim.x;
-  // indices: receiver of the current tile, sender of the next tile, both one tile ahead
-  uint32_t rv_cur = index_of(recv, tile);
-  issue(tile, 0, index_of(send, tile));
-  // receiver projections (+ b1) of this thread's row, loaded one tile ahead
-  // (consecutive rows share receivers, so these mostly hit in L1/L2)
+  // receiver projections (+ b1) of this thread's row, in registers, one tile ahead
   uint4 pr[8];
   auto load_pr = [&](uint32_t rv) {
     if (!ENC) {
@@ -623,43 +631,53 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
       for (int c = 0; c < 8; ++c) pr[c] = __ldg(prg + c);
     }
   };
-  load_pr(rv_cur);
-  uint32_t sd_next = index_of(send, tile + stride);
-  uint32_t rv_next = index_of(recv, tile + stride);
-  uint32_t phase = 0;
+  auto mma1 = [&](int sl) {  // z1 = e W1e into slot sl's accumulator
+    tc_fence_after();
+    const uint64_t dA = tc_desc(smem_u32(Et(sl)));
+#pragma unroll
+    for (int k = 0; k < (ENC ? 1 : 4); ++k) tc_mma(tmem + 64 * sl, dA + 2 * k, dB1 + 2 * k, k > 0);
+    tc_commit(smem_u32(mbar + sl));
+  };
+  auto mma2 = [&](int sl) {  // z2 = silu(z1) W2, same columns
+    tc_fence_after();
+    const uint64_t dA = tc_desc(smem_u32(Pt(sl)));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tc_mma(tmem + 64 * sl, dA + 2 * k, dB2 + 2 * k, k > 0);
+    tc_commit(smem_u32(mbar + sl));
+  };
+  uint32_t phases = 0u;  // bit sl: parity of slot sl's next mbarrier phase
+  auto wait_slot = [&](int sl) -> bool {  // bounded; every thread gets the CTA's verdict
+    bool w_ok = mbar_wait(smem_u32(mbar + sl), (phases >> sl) & 1u);
+    phases ^= 1u << sl;
+    return __syncthreads_and(w_ok) != 0;
+  };
+
+  int64_t tile = blockIdx.x;
+  // prologue: gathers of the first two tiles, MMA1 of the first
+  issue(tile, 0, index_of(send, tile));
+  issue(tile + stride, 1, index_of(send, tile + stride));
+  load_pr(index_of(recv, tile));
+  uint32_t rv_n1 = index_of(recv, tile + stride);      // receiver indices of the next tile
+  uint32_t sd_n2 = index_of(send, tile + 2 * stride);  // sender indices two tiles ahead
+  cp_async_wait<1>();
+  fence_async_smem();  // the e tile is read by the tensor core
+  tc_fence_before();
+  __syncthreads();
+  if (tile < ntiles && t == 0) mma1(0);
   bool ok = true;
 
   for (int it = 0; tile < ntiles; ++it, tile += stride) {
-    const int cur = it & 1;
+    const int s = it & 1;
     const int64_t row0 = tile * TC_ROWS;
-    unsigned char* A = SET + cur * 2 * TC_TILE_BYTES;
-    unsigned char* PS = A + TC_TILE_BYTES;
-    cp_async_wait<0>();
-    fence_async_smem();  // the e tile is read by the tensor core
-    tc_fence_before();
-    __syncthreads();
-    // ---- z1 = e W1e ----
-    if (t == 0) {
-      tc_fence_after();
-      const uint64_t dA = tc_desc(smem_u32(A));
-#pragma unroll
-      for (int k = 0; k < (ENC ? 1 : 4); ++k) tc_mma(tmem, dA + 2 * k, dB1 + 2 * k, k > 0);
-      tc_commit(mb);
-    }
-    // next tile's gathers overlap this tile's two GEMMs and epilogues
-    issue(tile + stride, cur ^ 1, sd_next);
-    rv_cur = rv_next;
-    sd_next = index_of(send, tile + 2 * stride);
-    rv_next = index_of(recv, tile + 2 * stride);
-    bool w_ok = mbar_wait(mb, phase);
-    phase ^= 1u;
-    if (!__syncthreads_and(w_ok)) { ok = false; break; }
+    unsigned char* A = Et(s);
+    unsigned char* PS = Pt(s);
+    if (!wait_slot(s)) { ok = false; break; }  // MMA1 of this tile
     tc_fence_after();
-    // ---- silu(z1 + P_recv + P_send) -> A1 (BF16, swizzled) ----
+    // ---- silu(z1 + P_recv + P_send) (or + b1) -> PS, in place, BF16 swizzled ----
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       float v[16];
-      tc_ld16(t_lane + q * 16, v);
+      tc_ld16(t_lane + 64 * s + q * 16, v);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = 2 * q + h;
@@ -685,29 +703,30 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
             o32[j] = *reinterpret_cast<uint32_t*>(&a2);
           }
         }
-        *reinterpret_cast<uint4*>(A1 + sw128(t, c)) = o;
+        *reinterpret_cast<uint4*>(PS + sw128(t, c)) = o;
       }
     }
     fence_async_smem();  // silu(z1) is read by the tensor core
     tc_fence_before();
     __syncthreads();
-    load_pr(rv_cur);  // next tile's receiver projections
-    // ---- z2 = silu(z1) W2 (same TMEM columns) ----
-    if (t == 0) {
-      tc_fence_after();
-#pragma unroll
-      for (int k = 0; k < 4; ++k) tc_mma(tmem, dA1 + 2 * k, dB2 + 2 * k, k > 0);
-      tc_commit(mb);
+    if (t == 0) mma2(s);
+    load_pr(rv_n1);  // next tile's receiver projections
+    rv_n1 = index_of(recv, tile + 2 * stride);
+    // ---- MMA1 of the next tile (its gathers were issued an iteration ago) ----
+    if (tile + stride < ntiles) {
+      cp_async_wait<0>();
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (t == 0) mma1(s ^ 1);
     }
-    w_ok = mbar_wait(mb, phase);
-    phase ^= 1u;
-    if (!__syncthreads_and(w_ok)) { ok = false; break; }
+    if (!wait_slot(s)) { ok = false; break; }  // MMA2 of this tile
     tc_fence_after();
     // ---- e' = e + z2 + b2, in place into the e tile ----
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       float v[16];
-      tc_ld16(t_lane + q * 16, v);
+      tc_ld16(t_lane + 64 * s + q * 16, v);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = 2 * q + h;
@@ -737,6 +756,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
         *reinterpret_cast<uint4*>(e_out + row * HID + c * 8) = *reinterpret_cast<const uint4*>(A + sw128(r, c));
     }
     __syncwarp();
+    // ---- gathers of the tile after next into this slot (its e and silu(z1) tiles are free) ----
+    issue(tile + 2 * stride, s, sd_n2);
+    sd_n2 = index_of(send, tile + 3 * stride);
   }
   cp_async_wait<0>();  // gathers issued for tiles past the end
   if (!ok && t == 0) atomicOr(err, (unsigned)kStatTimeout);
@@ -744,7 +766,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem) : "memory");
   }
 }
 
@@ -1295,8 +1317,8 @@ void launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, co
                                                               blk.w2, blk.b2, status);
 }
 
-// Edge MLP of one layer on tcgen05: persistent CTAs, 2 per SM (99 KB of
-// shared memory and 64 TMEM columns each).
+// Edge MLP of one layer on tcgen05: persistent CTAs, 2 per SM (83 KB of
+// shared memory and 128 TMEM columns each).
 void launch_edge_tc(const bf16* e_in, bf16* e_out, int64_t E, const uint32_t* recv, const uint32_t* send,
                     const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
   launch_tc<false>(e_in, e_out, E, recv, send, P, blk, status, st);
