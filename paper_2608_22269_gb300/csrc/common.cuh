@@ -38,7 +38,6 @@ struct Params {
   double pst_alpha_over_wdx;      // alpha / W(dx), for W_ij / W(dx)
   double pst_R, pst_n;
   double pst_R_a4;                // pst_R * pst_alpha_over_wdx^4
-  double four_h2_lo;              // (2h)^2 (1 - 2^-48): below it the contracted r^2 decides
   double rho0, c0, c0sq, nu, gamma;
   double delta_h_c0;              // delta * h * C0
   double tic_lambda;
@@ -47,6 +46,7 @@ struct Params {
   double omega;                   // 2 pi / period, 0 = no forcing
   double cfl, fixed_dt;
   float nearest_band_r2;          // FP32 band around the FP32 minimum that holds the exact nearest
+  float inner_r2;                 // FP32 r^2 at or below it (and > 0): an exact neighbour, no FP64 test
   double domain_min[3], domain_max[3];
   double R;                       // cell size 2h
   int nc[3];                      // grid cells per axis
@@ -121,7 +121,8 @@ void launch_time_step(const Params& p, const Work& w, cudaStream_t st);
 void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid,
                       int stage2, cudaStream_t st);
 int pair_list_kmax(int dim);
-void launch_nbr_list(const Params& p, const Work& w, int64_t n, int64_t n_fluid, cudaStream_t st);
+void launch_nbr_list(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid, cudaStream_t st,
+                     bool exact);
 void launch_rk_stage(const Params& p, const State& s, const Work& w, int64_t n, int stage,
                      cudaStream_t st);
 void launch_field(const Params& p, const State& s, const Work& w, int64_t n, int field,

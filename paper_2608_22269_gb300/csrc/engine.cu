@@ -172,7 +172,6 @@ static int derive_params(wbsph_s* h) {
   p.h = c.h_over_dx * c.dx;
   p.two_h = 2.0 * p.h;
   p.four_h2 = p.two_h * p.two_h;
-  p.four_h2_lo = p.four_h2 * (1.0 - std::ldexp(1.0, -48));
   p.R = p.two_h;
   p.alpha = c.dim == 2 ? 7.0 / (4.0 * kPi * p.h * p.h) : 21.0 / (16.0 * kPi * p.h * p.h * p.h);
   p.neg_dwdr_over_r_coef = 5.0 * p.alpha / (p.h * p.h);
@@ -231,6 +230,12 @@ static int derive_params(wbsph_s* h) {
   float bf = (float)(2.0 * B);
   if ((double)bf < 2.0 * B) bf = std::nextafter(bf, INFINITY);
   p.nearest_band_r2 = bf;
+  // Inner bound: FP32 r^2 <= (2h)^2 - 2B implies exact r^2 <= (2h)^2, so only
+  // candidates above it (a relative band of ~1e-4 in r^2) need the FP64 test.
+  double inner = p.four_h2 - 2.0 * B;
+  float inf32 = (float)inner;
+  if ((double)inf32 > inner) inf32 = std::nextafter(inf32, -INFINITY);
+  p.inner_r2 = inf32 > 0.f ? inf32 : 0.f;
   return WBSPH_OK;
 }
 
@@ -469,7 +474,7 @@ static int rates(wbsph_s* h, int stage2) {
   }
   {
     ProfScope ps(h, WBSPH_K_NLIST);
-    launch_nbr_list(h->P, h->W, n, h->nf, st);
+    launch_nbr_list(h->P, h->A, h->W, n, h->nf, st, !mixed);
   }
   {
     ProfScope ps(h, WBSPH_K_PAIR);
@@ -811,10 +816,11 @@ static int surrogate_stage(wbsph_s* h, wbsph_surrogate s, int stage2) {
     ProfScope ps(h, WBSPH_K_PAIR);
     rc = surrogate_stage_rates(s, h->P, h->A, h->W, h->n, h->nf, st);
   }
-  // prepass (dummy update, volumes), time step, and the surrogate stage's 21
-  // kernels: candidate lists, graph count/scan/fill, node features, two
-  // encoders, 3 x (node projections, edge MLP, aggregation, node MLP), decoder, rates
-  h->launches += (h->n ? (h->nd ? 2 : 1) : 0) + (stage2 ? 0 : 1) + (h->nf ? 21 : 0);
+  // prepass (dummy update, volumes), time step, and the surrogate stage's 22
+  // kernels: neighbour lists, row-pointer scan (3), graph fill, node features,
+  // two encoders, 3 x (node projections, edge MLP, aggregation, node MLP),
+  // decoder, rates
+  h->launches += (h->n ? (h->nd ? 2 : 1) : 0) + (stage2 ? 0 : 1) + (h->nf ? 22 : 0);
   if (rc) return fail(h, rc, "surrogate stage failed");
   return check_launch(h, "surrogate stage");
 }

@@ -982,24 +982,6 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd(MlpArgs a) {
 // ---------------------------------------------------------------------------
 // Graph, features, aggregation, loss, optimiser
 // ---------------------------------------------------------------------------
-__global__ void k_sg_count(Params p, State s, Work w, int64_t n, int64_t nf, uint32_t* cnt) {
-  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gi >= nf) return;
-  uint32_t i = w.fluid_list[gi];
-  int c = (int)w.nbr_cnt[gi];
-  uint32_t m = 0;
-  for (int k = 0; k < c; ++k) {
-    uint32_t j = w.nbr[(int64_t)k * nf + gi];
-    double r2 = 0.0;
-    for (int d = 0; d < p.dim; ++d) {
-      double dd = __dsub_rn(s.x[d * n + j], s.x[d * n + i]);
-      r2 = __dadd_rn(r2, __dmul_rn(dd, dd));
-    }
-    if (r2 <= p.four_h2 && r2 > 0.0) ++m;
-  }
-  cnt[gi] = m;
-}
-
 __global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, const uint32_t* row_ptr,
                           uint32_t* recv, uint32_t* send, bf16* efeat, const float* node_std) {
   int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1020,12 +1002,11 @@ __global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, cons
   const float phii = (float)s.phi[i];
   for (int k = 0; k < c; ++k) {
     uint32_t j = w.nbr[(int64_t)k * nf + gi];
-    double r[3] = {0, 0, 0}, r2 = 0.0;
+    double r[3] = {0, 0, 0}, r2 = 0.0;  // every list entry is an exact neighbour
     for (int d = 0; d < p.dim; ++d) {
       r[d] = __dsub_rn(s.x[d * n + j], xi[d]);
-      r2 = __dadd_rn(r2, __dmul_rn(r[d], r[d]));
+      r2 = fma(r[d], r[d], r2);
     }
-    if (!(r2 <= p.four_h2 && r2 > 0.0)) continue;
     recv[e] = i;
     send[e] = j;
     // features (r/h, |r|/h, dU/s_U, dphi/s_phi), zero padded to 8, one 16-byte store
@@ -1167,7 +1148,7 @@ struct wbsph_surrogate_s {
   int64_t adam_t = 0;
   // graph and activations, sized on demand
   int64_t cap_n = 0, cap_nf = 0, cap_e = 0;
-  uint32_t *cnt = nullptr, *row_ptr = nullptr, *recv = nullptr, *send = nullptr, *scan_tmp = nullptr;
+  uint32_t *row_ptr = nullptr, *recv = nullptr, *send = nullptr, *scan_tmp = nullptr;
   bf16 *efeat = nullptr, *nfeat = nullptr, *proj = nullptr;
   std::vector<bf16*> hs, es, aggs;
   float *out = nullptr, *dout = nullptr, *dh = nullptr, *de = nullptr, *dagg = nullptr;
@@ -1221,7 +1202,7 @@ void dfree(void* p) {
 }
 
 void free_graph(wbsph_surrogate s) {
-  dfree(s->cnt); dfree(s->row_ptr); dfree(s->recv); dfree(s->send); dfree(s->efeat); dfree(s->nfeat);
+  dfree(s->row_ptr); dfree(s->recv); dfree(s->send); dfree(s->efeat); dfree(s->nfeat);
   dfree(s->proj); dfree(s->scan_tmp);
   s->proj = nullptr;
   s->scan_tmp = nullptr;
@@ -1230,7 +1211,7 @@ void free_graph(wbsph_surrogate s) {
   for (auto* q : s->aggs) dfree(q);
   s->hs.clear(); s->es.clear(); s->aggs.clear();
   dfree(s->out); dfree(s->dout); dfree(s->dh); dfree(s->de); dfree(s->dagg);
-  s->cnt = s->row_ptr = s->recv = s->send = nullptr;
+  s->row_ptr = s->recv = s->send = nullptr;
   s->efeat = s->nfeat = nullptr;
   s->out = s->dout = s->dh = s->de = s->dagg = nullptr;
   s->cap_n = s->cap_nf = s->cap_e = 0;
@@ -1240,7 +1221,7 @@ int ensure_nodes(wbsph_surrogate s, int64_t n, int64_t nf) {
   if (n <= s->cap_n && nf <= s->cap_nf) return WBSPH_OK;
   free_graph(s);
   s->cap_n = n; s->cap_nf = nf;
-  bool ok = dalloc(&s->cnt, nf + 1) && dalloc(&s->row_ptr, nf + 1) && dalloc(&s->nfeat, n * FEAT) &&
+  bool ok = dalloc(&s->row_ptr, nf + 1) && dalloc(&s->nfeat, n * FEAT) &&
             dalloc(&s->out, nf * 4) && dalloc(&s->dout, nf * 4) && dalloc(&s->dh, n * HID) &&
             dalloc(&s->dagg, n * HID) && dalloc(&s->proj, n * 2 * HID) &&
             dalloc(&s->scan_tmp, (size_t)scan_scratch_words(nf + 1));
@@ -1340,9 +1321,9 @@ int build_graph(wbsph_surrogate s, const Params& p, const State& st, const Work&
                 int64_t nf, cudaStream_t cs) {
   int rc = ensure_nodes(s, n, nf);
   if (rc) return rc;
-  if (nf > 0) k_sg_count<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p, st, w, n, nf, s->cnt);
-  cudaMemsetAsync(s->cnt + nf, 0, 4, cs);
-  cudaMemcpyAsync(s->row_ptr, s->cnt, (nf + 1) * 4, cudaMemcpyDeviceToDevice, cs);
+  // edges of receiver gi = its neighbour list (exact neighbours, built by k_nbr_list)
+  if (nf > 0) cudaMemcpyAsync(s->row_ptr, w.nbr_cnt, nf * 4, cudaMemcpyDeviceToDevice, cs);
+  cudaMemsetAsync(s->row_ptr + nf, 0, 4, cs);
   launch_scan_exclusive_chunked(s->row_ptr, nf + 1, s->scan_tmp, cs);
   uint32_t E = 0;
   cudaMemcpyAsync(&E, s->row_ptr + nf, 4, cudaMemcpyDeviceToHost, cs);
@@ -1421,7 +1402,7 @@ void backward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStrea
 namespace wbsph {
 int surrogate_stage_rates(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n,
                           int64_t nf, cudaStream_t cs) {
-  launch_nbr_list(p, w, n, nf, cs);
+  launch_nbr_list(p, st, w, n, nf, cs, true);
   int rc = build_graph(s, p, st, w, n, nf, cs);
   if (rc) return rc;
   forward(s, w, n, nf, cs);
@@ -1435,7 +1416,7 @@ int surrogate_stage_rates(wbsph_surrogate s, const Params& p, const State& st, c
 int surrogate_loss(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n, int64_t nf,
                    cudaStream_t cs, int train, float lr, double* loss_out, const float* dout_override,
                    float* grad_out) {
-  launch_nbr_list(p, w, n, nf, cs);
+  launch_nbr_list(p, st, w, n, nf, cs, true);
   int rc = build_graph(s, p, st, w, n, nf, cs);
   if (rc) return rc;
   forward(s, w, n, nf, cs);

@@ -172,15 +172,21 @@ void launch_time_step(const Params& p, const Work& w, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Candidate lists: for fluid particle gi (sorted index fluid_list[gi]), every
-// j whose FP32 distance passes the conservative prefilter, in Algorithm 1
-// order, stored k-major: nbr[k * nf + gi]. Lists are staged per warp in
-// shared memory so the global stores are coalesced rows.
+// Neighbour lists: for fluid particle gi (sorted index fluid_list[gi]), in
+// Algorithm 1 order, stored k-major: nbr[k * nf + gi].
+//  EXACT (FP64 path, surrogate graph): every j != i with exact r <= 2h
+//    (Algorithm 1's test). The FP32 distance of the warp scan decides for
+//    candidates inside the inner bound; the rest of the candidates that pass
+//    the conservative prefilter (a thin band near 2h) take the exact FP64 test.
+//  otherwise (mixed path): every candidate that passes the FP32 prefilter;
+//    the mixed pair pass applies its own FP32 test.
+// Lists are staged per warp in shared memory so the global stores are
+// coalesced rows.
 // ---------------------------------------------------------------------------
 constexpr int LIST_THREADS = 64;
 
-template <int DIM>
-__global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, Work w, int64_t n, int64_t nf,
+template <int DIM, bool EXACT>
+__global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, State s, Work w, int64_t n, int64_t nf,
                                                          int kmax, int ks) {
   extern __shared__ float4 smem_f4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -193,13 +199,36 @@ __global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, Work w, int
   const uint32_t i = active ? w.fluid_list[gi] : 0u;
   const uint32_t key = active ? w.key[i] : 0u;
   const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  int cnt = 0;
-  warp_scan_candidates<DIM>(p, w, active, i, key, xs, stage, sidx, [&](uint32_t j, float, float) {
+  int cnt = 0, nband = 0;
+  constexpr uint32_t kBand = 0x80000000u;  // entry still needs the exact test
+  warp_scan_candidates<DIM>(p, w, active, i, key, xs, stage, sidx, [&](uint32_t j, float r2f, float) {
+    // neighbour test of Algorithm 1: FP32 decides inside the inner bound;
+    // candidates in the rounding band near 2h (and at r_f = 0) are flagged
+    // for the exact FP64 test below
+    const bool band = EXACT && !(r2f > 0.f && r2f <= p.inner_r2);
+    nband += band ? 1 : 0;
+    const uint32_t v = j | (band ? kBand : 0u);
     // the first ks entries are staged; the rare ones beyond go straight out
-    if (cnt < ks) my[cnt * 32 + lane] = j;
-    else if (cnt < kmax) w.nbr[(int64_t)cnt * nf + gi] = j;
+    if (cnt < ks) my[cnt * 32 + lane] = v;
+    else if (cnt < kmax) w.nbr[(int64_t)cnt * nf + gi] = v;
     ++cnt;
   });
+  if (EXACT && nband > 0) {  // rare: exact test of the flagged entries, compacting in order
+    const int m = cnt < kmax ? cnt : kmax;
+    int kept = 0;
+    for (int k = 0; k < m; ++k) {
+      uint32_t v = k < ks ? my[k * 32 + lane] : w.nbr[(int64_t)k * nf + gi];
+      if (v & kBand) {
+        v &= ~kBand;
+        if (!exact_neighbor(p, s.x, n, i, v)) continue;
+      }
+      if (kept < ks) my[kept * 32 + lane] = v;
+      else w.nbr[(int64_t)kept * nf + gi] = v;
+      ++kept;
+    }
+    if (cnt > kmax) atomicOr(w.status, kStatOverflow);
+    cnt = kept;
+  }
   if (active) {
     if (cnt > kmax) {
       atomicOr(w.status, kStatOverflow);
@@ -228,11 +257,20 @@ __global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, Work w, int
 constexpr int PAIR_THREADS = 128;
 
 // Reciprocal square root: FP32 estimate refined by one Newton-Raphson step
-// y <- y (3 - r2 y^2) / 2 in FP64, relative error about 1e-13 (the step
-// squares the ~2e-7 error of the estimate).
+// y <- y + (y/2)(1 - r2 y^2) in FP64, relative error about 1e-13 (the step
+// squares the ~2e-7 error of the estimate). The FP64 <-> FP32 moves are done
+// on the IEEE fields with integer instructions, keeping the FP64 pipe for
+// the pair sums: r2 (positive, FP32 normal range) is truncated to FP32 by
+// rebiasing the exponent (1023 -> 127) and keeping the top 23 mantissa bits;
+// y and y/2 are widened exactly the other way.
 __device__ __forceinline__ double rsqrt_nr1(double r2) {
-  double y = (double)rsqrtf((float)r2);
-  return fma(0.5 * y, fma(-r2 * y, y, 1.0), y);
+  constexpr unsigned kRebias = (1023u - 127u) << 20;
+  const unsigned hi = (unsigned)__double2hiint(r2), lo = (unsigned)__double2loint(r2);
+  const unsigned fb = ((hi - kRebias) << 3) | (lo >> 29);
+  const unsigned yb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
+  const double y = __hiloint2double((int)((yb >> 3) + kRebias), (int)(yb << 29));
+  const double hy = __hiloint2double((int)((yb >> 3) + kRebias - (1u << 20)), (int)(yb << 29));
+  return fma(hy, fma(-r2 * y, y, 1.0), y);
 }
 
 template <int DIM>
@@ -264,21 +302,13 @@ __global__ void __launch_bounds__(PAIR_THREADS, 4)
   for (int k = 0; k < maxc; ++k) {
     if (k >= cnt) continue;
     uint32_t j = __ldg(lst + (int64_t)k * nf);
+    // every list entry is an exact neighbour (k_nbr_list applies the test)
     double r[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) r[c] = __dsub_rn(s.x[c * n + j], xi[c]);
-    // r^2 with contraction; the exact (uncontracted) test of Algorithm 1 is
-    // evaluated only when r^2 lies within a few ulps of (2h)^2
     double r2 = r[0] * r[0];
 #pragma unroll
     for (int c = 1; c < DIM; ++c) r2 = fma(r[c], r[c], r2);
-    if (r2 > p.four_h2_lo) {
-      double e2 = __dmul_rn(r[0], r[0]);
-#pragma unroll
-      for (int c = 1; c < DIM; ++c) e2 = __dadd_rn(e2, __dmul_rn(r[c], r[c]));
-      if (!(e2 <= p.four_h2)) continue;
-    }
-    if (!(r2 > 0.0)) continue;
     ++npairs;
     double inv_r = rsqrt_nr1(r2);
     double rr = r2 * inv_r;
@@ -406,7 +436,8 @@ int pair_list_kmax(int dim) { return dim == 3 ? 128 : 48; }
 #endif
 static int pair_list_stage(int dim) { return dim == 3 ? WBSPH_LIST_STAGE_3D : 48; }
 
-void launch_nbr_list(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st) {
+void launch_nbr_list(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, cudaStream_t st,
+                     bool exact) {
   if (nf == 0) return;
   int kmax = pair_list_kmax(p.dim);
   int ks = pair_list_stage(p.dim);
@@ -415,13 +446,20 @@ void launch_nbr_list(const Params& p, const Work& w, int64_t n, int64_t nf, cuda
               (LIST_THREADS / 32) * 32 * (sizeof(float4) + sizeof(uint32_t));
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_nbr_list<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_nbr_list<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_nbr_list<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_nbr_list<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_nbr_list<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_nbr_list<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     attr = true;
   }
   unsigned blocks = (unsigned)div_up(nf, LIST_THREADS);
-  if (p.dim == 3) k_nbr_list<3><<<blocks, LIST_THREADS, sm, st>>>(p, w, n, nf, kmax, ks);
-  else k_nbr_list<2><<<blocks, LIST_THREADS, sm, st>>>(p, w, n, nf, kmax, ks);
+  if (p.dim == 3) {
+    if (exact) k_nbr_list<3, true><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
+    else k_nbr_list<3, false><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
+  } else {
+    if (exact) k_nbr_list<2, true><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
+    else k_nbr_list<2, false><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
+  }
 }
 
 void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
     if (DIM == 3) du[DIM - 1] = Bj.z - Bi.z;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) { r2 = fmaf(r[c], r[c], r2); dun = fmaf(du[c], r[c], dun); }
-    if (!(r2 <= four_h2 && r2 > 0.f)) continue;
+    if (!(r2 <= four_h2 && r2 > 0.f)) continue;  // the neighbour test in FP32
     ++npairs;
     float inv_r = rsqrtf(r2);
     float rr = r2 * inv_r;
