@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restric
 constexpr int TC_ROWS = 128;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TILE_BYTES = TC_ROWS * 128;        // 128 rows x 64 BF16
-constexpr size_t TC_SMEM_BYTES = 1024 + 4 * TC_TILE_BYTES + 2 * 8192 + 2 * 64 * 4 + 64;  // 2 slots, W, biases
+constexpr size_t TC_SMEM_BYTES = 1024 + 4 * TC_TILE_BYTES + 3 * 8192 + 2 * 64 * 4 + 64;  // 2 slots, W, biases
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16,
@@ -532,9 +532,11 @@ __device__ __forceinline__ float silu_tanh(float z) {
   return fmaf(h, th, h);
 }
 
-// ENC: the same kernel runs an encoder MLP on rows of 8 BF16 input features
-// (K = 16, zero padded): z1 = f W1 + b1, out = silu(z1) W2 + b2, no
-// projections, no residual.
+// Modes. TC_EDGE: the edge MLP above. TC_ENC: an encoder MLP on rows of 8
+// BF16 input features (K = 16, zero padded): z1 = f W1 + b1,
+// out = silu(z1) W2 + b2, no projections, no residual. TC_NODE: the node MLP
+// of a layer, h' = h + silu([h, a] W1 + b1) W2 + b2 (K = 128: the h tile and
+// the aggregate tile are the two 64-wide K blocks of the first GEMM).
 //
 // Pipeline over the CTA's tiles, two slots s (tile parity), each with its
 // own e tile, sender-projection tile (which then holds silu(z1)), TMEM
@@ -542,7 +544,9 @@ __device__ __forceinline__ float silu_tanh(float z) {
 // i, MMA2 of tile i issued, MMA1 of tile i+1 issued (its gathers arrived
 // during iteration i-1), epilogue 2 and store of tile i, gathers of tile i+2
 // into slot s. So each tile's GEMMs run while the other tile's epilogues do.
-template <bool ENC>
+enum { TC_EDGE = 0, TC_ENC = 1, TC_NODE = 2 };
+
+template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restrict__ e_in, bf16* __restrict__ e_out,
                                                            int64_t E, const uint32_t* __restrict__ recv,
                                                            const uint32_t* __restrict__ send,
@@ -550,12 +554,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
                                                            int kin, const float* __restrict__ b1g,
                                                            const bf16* __restrict__ w2,
                                                            const float* __restrict__ b2g, unsigned* err) {
+  constexpr bool ENC = MODE == TC_ENC, NODE = MODE == TC_NODE, EDGE = MODE == TC_EDGE;
   extern __shared__ unsigned char tc_raw[];
   unsigned char* base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);  // 1024-byte aligned
-  // slot s: e tile at s * 32 KB, sender projections / silu(z1) at s * 32 KB + 16 KB
-  unsigned char* B1 = base + 4 * TC_TILE_BYTES;  // W1e^T [n][k]
+  // slot s: e (or h) tile at s * 32 KB; sender projections (or aggregates),
+  // then silu(z1), at s * 32 KB + 16 KB
+  unsigned char* B1 = base + 4 * TC_TILE_BYTES;  // W1[0:64]^T [n][k]
   unsigned char* B2 = B1 + 8192;                 // W2^T [n][k]
-  float* b2 = reinterpret_cast<float*>(B2 + 8192);
+  unsigned char* B1b = B2 + 8192;                // W1[64:128]^T [n][k] (node MLP)
+  float* b2 = reinterpret_cast<float*>(B1b + 8192);
   float* b1 = b2 + 64;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(b1 + 64);  // one per slot
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
@@ -569,10 +576,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     uint32_t off = sw128(n, k >> 3) + (k & 7) * 2;
     *reinterpret_cast<bf16*>(B1 + off) = k < kin ? w1[k * HID + n] : __float2bfloat16(0.f);
     *reinterpret_cast<bf16*>(B2 + off) = w2[k * HID + n];
+    if (NODE) *reinterpret_cast<bf16*>(B1b + off) = w1[(HID + k) * HID + n];
   }
   if (t < 64) {
     b2[t] = b2g[t];
-    b1[t] = ENC ? b1g[t] : 0.f;
+    b1[t] = EDGE ? 0.f : b1g[t];  // the edge MLP's b1 rides on the receiver projections
   }
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
@@ -589,7 +597,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   tc_fence_after();
   const uint32_t tmem = *tslot;  // slot s accumulator: columns 64 s .. 64 s + 63
   const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
-  const uint64_t dB1 = tc_desc(smem_u32(B1)), dB2 = tc_desc(smem_u32(B2));
+  const uint64_t dB1 = tc_desc(smem_u32(B1)), dB2 = tc_desc(smem_u32(B2)), dB1b = tc_desc(smem_u32(B1b));
   const int64_t ntiles = div_up(E, TC_ROWS);
   const int64_t stride = gridDim.x;
 
@@ -613,29 +621,36 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
         const int64_t row = tile * TC_ROWS + r;
         const bool valid = tile < ntiles && row < E;
         cp_async16(Ae + sw128(r, c), e_in + (valid ? row : 0) * HID + c * 8, valid);
-        cp_async16(Pt(sl) + sw128(r, c), P + (int64_t)(valid ? sdr : 0u) * 2 * HID + HID + c * 8, valid);
+        const bf16* src2 = NODE ? P + (valid ? row : 0) * HID + c * 8
+                                : P + (int64_t)(valid ? sdr : 0u) * 2 * HID + HID + c * 8;
+        cp_async16(Pt(sl) + sw128(r, c), src2, valid);
       }
     }
     cp_async_commit();
   };
   auto index_of = [&](const uint32_t* a, int64_t tile) -> uint32_t {
     const int64_t row = tile * TC_ROWS + t;
-    return (!ENC && tile < ntiles && row < E) ? __ldg(a + row) : 0u;
+    return (EDGE && tile < ntiles && row < E) ? __ldg(a + row) : 0u;
   };
   // receiver projections (+ b1) of this thread's row, in registers, one tile ahead
   uint4 pr[8];
   auto load_pr = [&](uint32_t rv) {
-    if (!ENC) {
+    if (EDGE) {
       const uint4* prg = reinterpret_cast<const uint4*>(P + (int64_t)rv * 2 * HID);
 #pragma unroll
       for (int c = 0; c < 8; ++c) pr[c] = __ldg(prg + c);
     }
   };
-  auto mma1 = [&](int sl) {  // z1 = e W1e into slot sl's accumulator
+  auto mma1 = [&](int sl) {  // z1 = e W1e (or f W1, or [h, a] W1) into slot sl's accumulator
     tc_fence_after();
     const uint64_t dA = tc_desc(smem_u32(Et(sl)));
 #pragma unroll
     for (int k = 0; k < (ENC ? 1 : 4); ++k) tc_mma(tmem + 64 * sl, dA + 2 * k, dB1 + 2 * k, k > 0);
+    if (NODE) {  // second K block: the aggregates
+      const uint64_t dA2 = tc_desc(smem_u32(Pt(sl)));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tc_mma(tmem + 64 * sl, dA2 + 2 * k, dB1b + 2 * k, 1u);
+    }
     tc_commit(smem_u32(mbar + sl));
   };
   auto mma2 = [&](int sl) {  // z2 = silu(z1) W2, same columns
@@ -683,7 +698,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
         const int c = 2 * q + h;
         uint4 o;
         uint32_t* o32 = reinterpret_cast<uint32_t*>(&o);
-        if (ENC) {
+        if (!EDGE) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int col = c * 8 + 2 * j;
@@ -1280,7 +1295,7 @@ void launch_bwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
   k_mlp_bwd<MODE, KP, NP><<<grid, MLP_THREADS, sm, st>>>(a);
 }
 
-template <bool ENC>
+template <int MODE>
 void launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, const uint32_t* send,
                const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
   if (rows <= 0) return;
@@ -1289,12 +1304,12 @@ void launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, co
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_edge_mlp_tc<ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES);
+    cudaFuncSetAttribute(k_edge_mlp_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES);
     if (sms <= 0) sms = 152;
   }
   int64_t tiles = div_up(rows, TC_ROWS);
   int grid = (int)(tiles < 2 * sms ? tiles : 2 * sms);
-  k_edge_mlp_tc<ENC><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(in, out, rows, recv, send, P, blk.w1, blk.kin, blk.b1,
+  k_edge_mlp_tc<MODE><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(in, out, rows, recv, send, P, blk.w1, blk.kin, blk.b1,
                                                               blk.w2, blk.b2, status);
 }
 
@@ -1302,7 +1317,7 @@ void launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, co
 // shared memory and 128 TMEM columns each).
 void launch_edge_tc(const bf16* e_in, bf16* e_out, int64_t E, const uint32_t* recv, const uint32_t* send,
                     const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
-  launch_tc<false>(e_in, e_out, E, recv, send, P, blk, status, st);
+  launch_tc<TC_EDGE>(e_in, e_out, E, recv, send, P, blk, status, st);
 }
 
 MlpArgs block_args(wbsph_surrogate s, int bi) {
@@ -1342,8 +1357,8 @@ void forward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream
   const int64_t E = s->E;
   int L = s->layers;
   // node and edge encoders (tcgen05, K = 16)
-  launch_tc<true>(s->nfeat, s->hs[0], n, nullptr, nullptr, nullptr, block_args(s, 0), w.status, cs);
-  launch_tc<true>(s->efeat, s->es[0], E, nullptr, nullptr, nullptr, block_args(s, 1), w.status, cs);
+  launch_tc<TC_ENC>(s->nfeat, s->hs[0], n, nullptr, nullptr, nullptr, block_args(s, 0), w.status, cs);
+  launch_tc<TC_ENC>(s->efeat, s->es[0], E, nullptr, nullptr, nullptr, block_args(s, 1), w.status, cs);
   const int pgrid = (int)(div_up(n > 0 ? n : 1, TILE) < 152 * 4 ? div_up(n > 0 ? n : 1, TILE) : 152 * 4);
   for (int l = 0; l < L; ++l) {
     MlpArgs a = block_args(s, 2 + 2 * l);
@@ -1352,9 +1367,9 @@ void forward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream
     cudaMemsetAsync(s->aggs[l], 0, (size_t)n * HID * 2, cs);
     if (nf > 0)
       k_sg_aggregate<<<(unsigned)div_up(nf, 4), 128, 0, cs>>>(w.fluid_list, nf, s->row_ptr, s->es[l + 1], s->aggs[l]);
-    MlpArgs b = block_args(s, 3 + 2 * l);
-    b.rows = n; b.h = s->hs[l]; b.agg = s->aggs[l]; b.out_bf = s->hs[l + 1];
-    launch_fwd<MODE_NODE, 128, 64>(b, n, cs);
+    // node MLP (tcgen05): h_{l+1} = h_l + MLP_n([h_l, a_l])
+    launch_tc<TC_NODE>(s->hs[l], s->hs[l + 1], n, nullptr, nullptr, s->aggs[l], block_args(s, 3 + 2 * l),
+                       w.status, cs);
   }
   {  // decoder over fluid rows
     MlpArgs a = block_args(s, 2 + 2 * L);
