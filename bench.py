@@ -333,6 +333,22 @@ def surrogate_flops_per_stage(dim, n, nf, E, hidden=64, layers=3):
     return enc + layers * per_layer + dec
 
 
+def surrogate_bytes_per_stage(n, nf, E, hidden=64, layers=3):
+    """Algorithmic HBM bytes of one surrogate stage (BF16 activations): the
+    graph fill (list entry read, receiver/sender/features written), node and
+    edge encoders (8 features in, a 64-wide row out), per layer the node
+    projections (h in, 128-wide row out), the edge MLP (edge state in and
+    out; the gathered projections are L2 traffic), the aggregation (edge
+    states in, a row out) and the node MLP (h and aggregate in, h out), and
+    the decoder on fluid rows."""
+    row = 2 * hidden
+    fill = E * (4 + 8 + 16)
+    enc = (n + E) * (16 + row)
+    per_layer = n * (row + 2 * row) + E * 2 * row + (E * row + n * row) + n * 3 * row
+    dec = nf * (row + 16)
+    return fill + enc + layers * per_layer + dec
+
+
 def surrogate_path(args, local):
     """Surrogate rollouts (configs' 2D inference case: dam break, column
     0.6 x 0.3 m, dx = 0.00085 m, 249,218 fluid particles) with a plain FP64
@@ -391,6 +407,13 @@ def surrogate_path(args, local):
     except (OSError, ValueError, KeyError):
         pass
     achieved = flops / (stage_ms / 1e3) / 1e12
+    sbytes = surrogate_bytes_per_stage(n, nf, E)
+    hbm_peak = 6686.1
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, ValueError, KeyError):
+        pass
+    gbs = sbytes / (stage_ms / 1e3) / 1e9
     fb_sim = wbsph.Sim(sc.params, water_height=sc.water_height, device=local)
     fb_sim.set_scene(sc)
     fb = sur.step(fb_sim, K, anchor_every=10, tau=0.1)
@@ -407,6 +430,9 @@ def surrogate_path(args, local):
                         "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                         "frac": round(achieved / peak, 4), "traffic": None,
                         "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"},
+           "hbm": {"algorithmic_bytes_per_stage": int(sbytes), "achieved_gbs": round(gbs, 1),
+                   "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4),
+                   "note": "the stage is bound by data movement: ~45 FLOP/B against a ~290 FLOP/B ridge"},
            "with_fallback_tau_0.1": fb,
            "weights": "paper_2608_22269_gb300/data/surrogate_2d.npz (trained on the GPU by this library)"}
     for o in (plain, sim, fb_sim, sur):
