@@ -369,33 +369,45 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
   if (where != WBSPH_HOST && where != WBSPH_DEVICE) return fail(h, WBSPH_E_INVAL, "bad 'where'");
   CK(cudaSetDevice(h->cfg.device));
   const int d = h->cfg.dim;
-  std::vector<uint8_t> ty((size_t)n);
   cudaMemcpyKind kind = where == WBSPH_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  if (where == WBSPH_HOST) {
-    if (n) memcpy(ty.data(), type, (size_t)n);
-  } else if (n) {
-    CK(cudaMemcpyAsync(ty.data(), type, (size_t)n, cudaMemcpyDeviceToHost, h->stream));
+  // types are counted on the host (branch-free, vectorisable); device input
+  // is read back first
+  std::vector<uint8_t> ty_copy;
+  const uint8_t* ty = type;
+  if (where == WBSPH_DEVICE && n) {
+    ty_copy.resize((size_t)n);
+    CK(cudaMemcpyAsync(ty_copy.data(), type, (size_t)n, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    ty = ty_copy.data();
   }
-  int64_t nf = 0, nd = 0;
+  int64_t nf = 0, nd = 0, bad = 0;
   for (int64_t i = 0; i < n; ++i) {
-    if (ty[i] == 0) ++nf;
-    else if (ty[i] == 1) ++nd;
-    else return fail(h, WBSPH_E_INVAL, "particle %lld has type %d (0 fluid, 1 dummy)", (long long)i, ty[i]);
+    const uint8_t v = ty[i];
+    nf += v == 0;
+    nd += v == 1;
+    bad += v > 1;
+  }
+  if (bad) {
+    int64_t i = 0;
+    while (ty[i] <= 1) ++i;
+    return fail(h, WBSPH_E_INVAL, "particle %lld has type %d (0 fluid, 1 dummy)", (long long)i, ty[i]);
   }
   if (nd > 0 && !normal) return fail(h, WBSPH_E_INVAL, "dummy particles need normals");
   h->loaded = false;
   int rc = WBSPH_OK;
-  bool same = n == h->n_alloc && nf == h->nf && !h->blocks.empty();
+  bool same = n == h->n_alloc && nf == h->nf && nd == h->nd && !h->blocks.empty();
   h->n = n; h->nf = nf; h->nd = nd;
-  if (!same) rc = allocate(h, n);  // same counts: reuse the buffers
+  if (!same) {
+    drop_graph(h);           // buffers move: a captured step is stale
+    rc = allocate(h, n);     // same counts: reuse the buffers and the captured step
+  }
   if (rc) return rc;
   size_t vb = (size_t)n * sizeof(double);
   if (n) {
     CK(cudaMemcpyAsync(h->A.x, x, d * vb, kind, h->stream));
     CK(cudaMemcpyAsync(h->A.u, u, d * vb, kind, h->stream));
     CK(cudaMemcpyAsync(h->A.phi, phi, vb, kind, h->stream));
-    CK(cudaMemcpyAsync(h->A.type, ty.data(), (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->A.type, type, (size_t)n, kind, h->stream));
     if (normal) CK(cudaMemcpyAsync(h->A.normal, normal, d * vb, kind, h->stream));
     else CK(cudaMemsetAsync(h->A.normal, 0, d * vb, h->stream));
     if (mass) CK(cudaMemcpyAsync(h->A.mass, mass, vb, kind, h->stream));
@@ -419,7 +431,6 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
   if (where == WBSPH_HOST) CK(cudaStreamSynchronize(h->stream));
   h->steps = 0;
   h->steps_since_load = 0;
-  drop_graph(h);
   h->loaded = true;
   return WBSPH_OK;
 }
@@ -571,12 +582,14 @@ extern "C" int wbsph_step(wbsph_handle h, int64_t nsteps) {
   if (nsteps < 0) return fail(h, WBSPH_E_INVAL, "nsteps < 0");
   CK(cudaSetDevice(h->cfg.device));
   // Graph replay on a caller stream (not the legacy default stream) when
-  // profiling is off; the first step of a particle set runs eagerly so that
-  // one-time kernel attributes are set outside the capture.
+  // profiling is off. The first step of a handle runs eagerly, so that
+  // one-time kernel attributes are set outside the capture; the captured step
+  // survives set_particles with unchanged counts (same buffers; whole steps
+  // leave the double-buffer pointers where the capture found them).
   bool graphs = h->use_graphs && h->stream != nullptr && !h->prof && h->n > 0;
   for (int64_t s = 0; s < nsteps; ++s) {
     int rc;
-    if (graphs && h->steps_since_load > 0) {
+    if (graphs && (h->graph_exec || h->steps_since_load > 0)) {
       if (!h->graph_exec && capture_step(h) != WBSPH_OK) {
         h->use_graphs = false;
         graphs = false;
