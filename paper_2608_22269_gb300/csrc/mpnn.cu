@@ -11,7 +11,9 @@
 // h <- h + MLP_n([h, a]), and a decoder to normalised (DU/Dt, Dphi/Dt).
 // Flat parameter layout: blocks node encoder, edge encoder, (edge MLP,
 // node MLP) per layer, decoder; each block W1 [in][64], b1, W2 [64][out], b2.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstring>
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restric
 constexpr int TC_ROWS = 128;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TILE_BYTES = TC_ROWS * 128;        // 128 rows x 64 BF16
-constexpr size_t TC_SMEM_BYTES = 1024 + 4 * TC_TILE_BYTES + 3 * 8192 + 2 * 64 * 4 + 64;  // 2 slots, W, biases
+constexpr size_t TC_SMEM_BYTES = 1024 + 4 * TC_TILE_BYTES + 3 * 8192 + 2 * 64 * 4 + 64;  // 2 slots, W, biases, barriers
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16,
@@ -523,6 +525,27 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+// TMA: 2D tile load into shared memory, completing on an mbarrier with a
+// byte count; 2D tile store from shared memory in a bulk group.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(src)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_read_wait() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_store_wait() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 // silu(z) = z sigmoid(z) = z (1 + tanh(z / 2)) / 2 with the hardware tanh
 // approximation (one special-function op instead of an exponential and a
 // reciprocal; absolute error ~1e-3 |z|, below the BF16 rounding of the result)
@@ -553,7 +576,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
                                                            const bf16* __restrict__ P, const bf16* __restrict__ w1,
                                                            int kin, const float* __restrict__ b1g,
                                                            const bf16* __restrict__ w2,
-                                                           const float* __restrict__ b2g, unsigned* err) {
+                                                           const float* __restrict__ b2g, unsigned* err,
+                                                           const __grid_constant__ CUtensorMap tm_a,
+                                                           const __grid_constant__ CUtensorMap tm_b,
+                                                           const __grid_constant__ CUtensorMap tm_out) {
+  // tm_a: rows of e_in (edge, node: h) and tm_b: rows of the aggregates (node),
+  // tm_out: rows of e_out; [rows][64] BF16, 128-row boxes, 128-byte swizzle.
+  // The encoder mode (8-feature rows) gathers and stores with plain loads.
   constexpr bool ENC = MODE == TC_ENC, NODE = MODE == TC_NODE, EDGE = MODE == TC_EDGE;
   extern __shared__ unsigned char tc_raw[];
   unsigned char* base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);  // 1024-byte aligned
@@ -564,8 +593,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   unsigned char* B1b = B2 + 8192;                // W1[64:128]^T [n][k] (node MLP)
   float* b2 = reinterpret_cast<float*>(B1b + 8192);
   float* b1 = b2 + 64;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(b1 + 64);  // one per slot
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(b1 + 64);  // MMA completion, one per slot
+  uint64_t* lbar = mbar + 2;                               // TMA tile arrival, one per slot
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 4);
   auto Et = [&](int sl) { return base + sl * 2 * TC_TILE_BYTES; };
   auto Pt = [&](int sl) { return base + sl * 2 * TC_TILE_BYTES + TC_TILE_BYTES; };
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -583,8 +613,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     b1[t] = EDGE ? 0.f : b1g[t];  // the edge MLP's b1 rides on the receiver projections
   }
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + 1)) : "memory");
+    for (int k = 0; k < 4; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + k)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -613,17 +643,25 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
       cp_async16(Ae + sw128(t, 0), e_in + (valid ? row : 0) * FEAT, valid);
       cp_async16(Ae + sw128(t, 1), e_in, false);
     } else {
-      const int c = lane & 7;
+      // e (or h) tile, and the aggregate tile of a node MLP, by TMA (rows past
+      // the end read as zeros); the store of the tile held here before must
+      // have finished reading it
+      if (t == 0 && tile < ntiles) {
+        tma_store_read_wait();
+        mbar_expect_tx(smem_u32(lbar + sl), NODE ? 2 * TC_TILE_BYTES : TC_TILE_BYTES);
+        tma_load_2d(smem_u32(Ae), &tm_a, 0, (int)(tile * TC_ROWS), smem_u32(lbar + sl));
+        if (NODE) tma_load_2d(smem_u32(Pt(sl)), &tm_b, 0, (int)(tile * TC_ROWS), smem_u32(lbar + sl));
+      }
+      if (EDGE) {  // sender projections: lane l moves chunk l % 8 of row 4 k + l / 8
+        const int c = lane & 7;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int rl = k * 4 + (lane >> 3), r = warp * 32 + rl;
-        const uint32_t sdr = __shfl_sync(0xffffffffu, sd, rl);
-        const int64_t row = tile * TC_ROWS + r;
-        const bool valid = tile < ntiles && row < E;
-        cp_async16(Ae + sw128(r, c), e_in + (valid ? row : 0) * HID + c * 8, valid);
-        const bf16* src2 = NODE ? P + (valid ? row : 0) * HID + c * 8
-                                : P + (int64_t)(valid ? sdr : 0u) * 2 * HID + HID + c * 8;
-        cp_async16(Pt(sl) + sw128(r, c), src2, valid);
+        for (int k = 0; k < 8; ++k) {
+          const int rl = k * 4 + (lane >> 3), r = warp * 32 + rl;
+          const uint32_t sdr = __shfl_sync(0xffffffffu, sd, rl);
+          const int64_t row = tile * TC_ROWS + r;
+          const bool valid = tile < ntiles && row < E;
+          cp_async16(Pt(sl) + sw128(r, c), P + (int64_t)(valid ? sdr : 0u) * 2 * HID + HID + c * 8, valid);
+        }
       }
     }
     cp_async_commit();
@@ -660,10 +698,23 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     for (int k = 0; k < 4; ++k) tc_mma(tmem + 64 * sl, dA + 2 * k, dB2 + 2 * k, k > 0);
     tc_commit(smem_u32(mbar + sl));
   };
-  uint32_t phases = 0u;  // bit sl: parity of slot sl's next mbarrier phase
+  uint32_t phases = 0u;  // bit b: parity of mbarrier b's next phase (0, 1: MMA; 2, 3: TMA)
   auto wait_slot = [&](int sl) -> bool {  // bounded; every thread gets the CTA's verdict
     bool w_ok = mbar_wait(smem_u32(mbar + sl), (phases >> sl) & 1u);
     phases ^= 1u << sl;
+    return __syncthreads_and(w_ok) != 0;
+  };
+  // this thread's gathers of slot sl are complete and the slot's TMA tiles
+  // have arrived (bounded wait); followed by a CTA barrier
+  auto wait_loads = [&](int sl, int pending_groups) -> bool {
+    if (pending_groups) cp_async_wait<1>(); else cp_async_wait<0>();
+    bool w_ok = true;
+    if (!ENC) {
+      w_ok = mbar_wait(smem_u32(lbar + sl), (phases >> (2 + sl)) & 1u);
+      phases ^= 1u << (2 + sl);
+    }
+    fence_async_smem();  // gathered tiles are read by the tensor core
+    tc_fence_before();
     return __syncthreads_and(w_ok) != 0;
   };
 
@@ -674,12 +725,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   load_pr(index_of(recv, tile));
   uint32_t rv_n1 = index_of(recv, tile + stride);      // receiver indices of the next tile
   uint32_t sd_n2 = index_of(send, tile + 2 * stride);  // sender indices two tiles ahead
-  cp_async_wait<1>();
-  fence_async_smem();  // the e tile is read by the tensor core
-  tc_fence_before();
-  __syncthreads();
-  if (tile < ntiles && t == 0) mma1(0);
   bool ok = true;
+  if (tile < ntiles) {
+    ok = wait_loads(0, 1);
+    if (ok && t == 0) mma1(0);
+  }
 
   for (int it = 0; tile < ntiles; ++it, tile += stride) {
     const int s = it & 1;
@@ -729,10 +779,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     rv_n1 = index_of(recv, tile + 2 * stride);
     // ---- MMA1 of the next tile (its gathers were issued an iteration ago) ----
     if (tile + stride < ntiles) {
-      cp_async_wait<0>();
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
+      if (!wait_loads(s ^ 1, 0)) { ok = false; break; }
       if (t == 0) mma1(s ^ 1);
     }
     if (!wait_slot(s)) { ok = false; break; }  // MMA2 of this tile
@@ -761,21 +808,28 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
         *reinterpret_cast<uint4*>(A + sw128(t, c)) = o;
       }
     }
-    __syncwarp();
-    // ---- the warp's 32 output rows, 4 whole rows (512 B) per store instruction ----
+    if (ENC) {
+      __syncwarp();
+      // the warp's 32 output rows, 4 whole rows (512 B) per store instruction
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int r = warp * 32 + k * 4 + (lane >> 3), c = lane & 7;
-      const int64_t row = row0 + r;
-      if (row < E)
-        *reinterpret_cast<uint4*>(e_out + row * HID + c * 8) = *reinterpret_cast<const uint4*>(A + sw128(r, c));
+      for (int k = 0; k < 8; ++k) {
+        const int r = warp * 32 + k * 4 + (lane >> 3), c = lane & 7;
+        const int64_t row = row0 + r;
+        if (row < E)
+          *reinterpret_cast<uint4*>(e_out + row * HID + c * 8) = *reinterpret_cast<const uint4*>(A + sw128(r, c));
+      }
+      __syncwarp();
+    } else {  // the whole tile by one TMA store (rows past the end are not written)
+      fence_async_smem();
+      __syncthreads();
+      if (t == 0) tma_store_2d(&tm_out, 0, (int)row0, smem_u32(A));
     }
-    __syncwarp();
     // ---- gathers of the tile after next into this slot (its e and silu(z1) tiles are free) ----
     issue(tile + 2 * stride, s, sd_n2);
     sd_n2 = index_of(send, tile + 3 * stride);
   }
   cp_async_wait<0>();  // gathers issued for tiles past the end
+  if (t == 0) tma_store_wait();
   if (!ok && t == 0) atomicOr(err, (unsigned)kStatTimeout);
   tc_fence_before();
   __syncthreads();
@@ -1295,10 +1349,46 @@ void launch_bwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
   k_mlp_bwd<MODE, KP, NP><<<grid, MLP_THREADS, sm, st>>>(a);
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
+// query (no link-time dependency on libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// TMA map of a [rows][64] BF16 row-major array: 128-row boxes, 128-byte swizzle
+// (the tensor core's K-major operand layout), zero fill past the last row.
+static bool rows_map(CUtensorMap* m, const bf16* base, int64_t rows) {
+  auto fn = tensor_map_encoder();
+  if (!fn || rows <= 0 || rows > 0x7FFFFFFF) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)HID, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)HID * sizeof(bf16)};
+  cuuint32_t box[2] = {(cuuint32_t)HID, (cuuint32_t)TC_ROWS};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// in: rows of e (edge), 8-feature rows (encoder) or h (node); P: projections
+// (edge) or aggregates (node); out: [rows][64]. Returns false when a TMA map
+// cannot be built (the caller reports it).
 template <int MODE>
-void launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, const uint32_t* send,
+bool launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, const uint32_t* send,
                const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
-  if (rows <= 0) return;
+  if (rows <= 0) return true;
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -1307,17 +1397,26 @@ void launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, co
     cudaFuncSetAttribute(k_edge_mlp_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES);
     if (sms <= 0) sms = 152;
   }
+  CUtensorMap ma, mb, mo;
+  memset(&ma, 0, sizeof ma);
+  memset(&mb, 0, sizeof mb);
+  memset(&mo, 0, sizeof mo);
+  if (MODE != TC_ENC) {
+    if (!rows_map(&ma, in, rows) || !rows_map(&mo, out, rows)) return false;
+    if (MODE == TC_NODE && !rows_map(&mb, P, rows)) return false;
+  }
   int64_t tiles = div_up(rows, TC_ROWS);
   int grid = (int)(tiles < 2 * sms ? tiles : 2 * sms);
-  k_edge_mlp_tc<MODE><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(in, out, rows, recv, send, P, blk.w1, blk.kin, blk.b1,
-                                                              blk.w2, blk.b2, status);
+  k_edge_mlp_tc<MODE><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(in, out, rows, recv, send, P, blk.w1, blk.kin,
+                                                               blk.b1, blk.w2, blk.b2, status, ma, mb, mo);
+  return true;
 }
 
 // Edge MLP of one layer on tcgen05: persistent CTAs, 2 per SM (83 KB of
 // shared memory and 128 TMEM columns each).
-void launch_edge_tc(const bf16* e_in, bf16* e_out, int64_t E, const uint32_t* recv, const uint32_t* send,
+bool launch_edge_tc(const bf16* e_in, bf16* e_out, int64_t E, const uint32_t* recv, const uint32_t* send,
                     const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
-  launch_tc<TC_EDGE>(e_in, e_out, E, recv, send, P, blk, status, st);
+  return launch_tc<TC_EDGE>(e_in, e_out, E, recv, send, P, blk, status, st);
 }
 
 MlpArgs block_args(wbsph_surrogate s, int bi) {
@@ -1353,29 +1452,33 @@ int build_graph(wbsph_surrogate s, const Params& p, const State& st, const Work&
   return WBSPH_OK;
 }
 
-void forward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream_t cs) {
+int forward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream_t cs) {
   const int64_t E = s->E;
   int L = s->layers;
   // node and edge encoders (tcgen05, K = 16)
+  const char* tma_err = "TMA tensor map of the surrogate activations could not be built";
   launch_tc<TC_ENC>(s->nfeat, s->hs[0], n, nullptr, nullptr, nullptr, block_args(s, 0), w.status, cs);
   launch_tc<TC_ENC>(s->efeat, s->es[0], E, nullptr, nullptr, nullptr, block_args(s, 1), w.status, cs);
   const int pgrid = (int)(div_up(n > 0 ? n : 1, TILE) < 152 * 4 ? div_up(n > 0 ? n : 1, TILE) : 152 * 4);
   for (int l = 0; l < L; ++l) {
     MlpArgs a = block_args(s, 2 + 2 * l);
     k_node_proj<<<pgrid, MLP_THREADS, 0, cs>>>(s->hs[l], n, a.w1, a.b1, s->proj);
-    launch_edge_tc(s->es[l], s->es[l + 1], E, s->recv, s->send, s->proj, a, w.status, cs);
+    if (!launch_edge_tc(s->es[l], s->es[l + 1], E, s->recv, s->send, s->proj, a, w.status, cs))
+      return sfail(s, WBSPH_E_CUDA, tma_err);
     cudaMemsetAsync(s->aggs[l], 0, (size_t)n * HID * 2, cs);
     if (nf > 0)
       k_sg_aggregate<<<(unsigned)div_up(nf, 4), 128, 0, cs>>>(w.fluid_list, nf, s->row_ptr, s->es[l + 1], s->aggs[l]);
     // node MLP (tcgen05): h_{l+1} = h_l + MLP_n([h_l, a_l])
-    launch_tc<TC_NODE>(s->hs[l], s->hs[l + 1], n, nullptr, nullptr, s->aggs[l], block_args(s, 3 + 2 * l),
-                       w.status, cs);
+    if (!launch_tc<TC_NODE>(s->hs[l], s->hs[l + 1], n, nullptr, nullptr, s->aggs[l], block_args(s, 3 + 2 * l),
+                       w.status, cs))
+      return sfail(s, WBSPH_E_CUDA, tma_err);
   }
   {  // decoder over fluid rows
     MlpArgs a = block_args(s, 2 + 2 * L);
     a.rows = nf; a.in = s->hs[L]; a.list = w.fluid_list; a.out_f = s->out;
     launch_fwd<MODE_LIST, 64, 16>(a, nf, cs);
   }
+  return WBSPH_OK;
 }
 
 void backward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream_t cs) {
@@ -1420,7 +1523,7 @@ int surrogate_stage_rates(wbsph_surrogate s, const Params& p, const State& st, c
   launch_nbr_list(p, st, w, n, nf, cs, true);
   int rc = build_graph(s, p, st, w, n, nf, cs);
   if (rc) return rc;
-  forward(s, w, n, nf, cs);
+  if ((rc = forward(s, w, n, nf, cs))) return rc;
   if (nf > 0)
     k_sg_rates<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, n, nf, s->out, s->norm + 16, s->norm + 20);
   return WBSPH_OK;
@@ -1434,7 +1537,7 @@ int surrogate_loss(wbsph_surrogate s, const Params& p, const State& st, const Wo
   launch_nbr_list(p, st, w, n, nf, cs, true);
   int rc = build_graph(s, p, st, w, n, nf, cs);
   if (rc) return rc;
-  forward(s, w, n, nf, cs);
+  if ((rc = forward(s, w, n, nf, cs))) return rc;
   cudaMemsetAsync(s->loss, 0, 8, cs);
   if (nf > 0)
     k_sg_loss<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, n, nf, s->out, s->norm + 16, s->norm + 20,
