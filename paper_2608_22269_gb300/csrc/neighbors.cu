@@ -299,12 +299,15 @@ __global__ void k_gather(int dim, State src, State dst, const uint32_t* __restri
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int64_t j = perm[i];
+  const uint8_t ty = src.type[j];
   float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int k = 0; k < dim; ++k) {
     double xv = src.x[k * n + j];
     dst.x[k * n + i] = xv;
     dst.u[k * n + i] = src.u[k * n + j];
-    dst.normal[k * n + i] = src.normal[k * n + j];
+    // wall normals are read for dummy particles only (the dummy update);
+    // fluid entries of the normal array are left as they are
+    if (ty != kFluid) dst.normal[k * n + i] = src.normal[k * n + j];
     if (with_base) {
       dst.x0[k * n + i] = src.x0[k * n + j];
       dst.u0[k * n + i] = src.u0[k * n + j];
@@ -315,7 +318,6 @@ __global__ void k_gather(int dim, State src, State dst, const uint32_t* __restri
   dst.phi[i] = src.phi[j];
   if (with_base) dst.phi0[i] = src.phi0[j];
   dst.mass[i] = src.mass[j];
-  uint8_t ty = src.type[j];
   dst.type[i] = ty;
   f.w = (float)ty;
   dst.oid[i] = src.oid[j];
