@@ -257,6 +257,15 @@ const char* wbsph_surrogate_last_error(wbsph_surrogate s);
 int wbsph_sort_cells_noalloc(wbsph_handle h, const double* x, int64_t n, uint32_t* keys_sorted,
                              uint32_t* ids_sorted);
 
+/* Check of the bounded device waits (failure detection without a GPU fault):
+ * launches one thread that waits, with at most `limit` polls, on an mbarrier
+ * that nothing arrives on, the same bounded wait the surrogate's tcgen05
+ * kernels use for their MMA and TMA completions. When the limit runs out the
+ * thread sets the status word and returns; the call then synchronises and
+ * returns WBSPH_E_TIMEOUT (the status stays set until the next
+ * wbsph_set_particles). The context stays usable. Requires loaded particles. */
+int wbsph_test_bounded_wait(wbsph_handle h, int64_t limit);
+
 void wbsph_destroy(wbsph_handle h);
 const char* wbsph_last_error(wbsph_handle h);
 const char* wbsph_status_string(int status);

@@ -24,6 +24,7 @@ using namespace wbsph;
 namespace wbsph {
 void launch_mass(const Params& p, const double* phi, double* mass, int64_t n, cudaStream_t st);
 int launch_pack_mixed(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
+void launch_wait_probe(unsigned* status, uint32_t limit, cudaStream_t st);
 void launch_pair_mixed(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
                        cudaStream_t st);
 }
@@ -620,6 +621,17 @@ static int read_status(wbsph_s* h) {
   if (s & kStatDomain) return fail(h, WBSPH_E_DOMAIN, "a particle left the domain");
   if (s & kStatTimeout) return fail(h, WBSPH_E_TIMEOUT, "a bounded device wait gave up");
   return fail(h, WBSPH_E_CAPACITY, "neighbour list overflow");
+}
+
+extern "C" int wbsph_test_bounded_wait(wbsph_handle h, int64_t limit) {
+  if (!h) return WBSPH_E_INVAL;
+  if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
+  if (limit < 1 || limit > (int64_t)0xFFFFFFFF) return fail(h, WBSPH_E_INVAL, "limit out of range");
+  CK(cudaSetDevice(h->cfg.device));
+  launch_wait_probe(h->W.status, (uint32_t)limit, h->stream);
+  int rc = check_launch(h, "wait probe");
+  if (rc) return rc;
+  return read_status(h);
 }
 
 extern "C" int wbsph_sync(wbsph_handle h) {

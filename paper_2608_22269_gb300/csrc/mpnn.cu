@@ -512,8 +512,8 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
 }
 
 // bounded wait for the mbarrier phase `parity`; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit = TC_WAIT_LIMIT) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -545,6 +545,16 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int 
 }
 __device__ __forceinline__ void tma_store_read_wait() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 __device__ __forceinline__ void tma_store_wait() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
+// Check of the bounded wait itself: one thread waits on an mbarrier that
+// nothing arrives on; when the limit runs out it reports a timeout through the
+// status word, as the MLP kernels do, and the kernel ends normally.
+__global__ void k_wait_probe(unsigned* status, uint32_t limit) {
+  __shared__ uint64_t bar;
+  const uint32_t mb = smem_u32(&bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+  if (!mbar_wait(mb, 0u, limit)) atomicOr(status, (unsigned)kStatTimeout);
+}
 
 // silu(z) = z sigmoid(z) = z (1 + tanh(z / 2)) / 2 with the hardware tanh
 // approximation (one special-function op instead of an exponential and a
@@ -1563,6 +1573,10 @@ int surrogate_loss(wbsph_surrogate s, const Params& p, const State& st, const Wo
 }
 
 int64_t surrogate_edges(wbsph_surrogate s) { return s->E; }
+
+void launch_wait_probe(unsigned* status, uint32_t limit, cudaStream_t st) {
+  k_wait_probe<<<1, 1, 0, st>>>(status, limit);
+}
 const float* surrogate_out(wbsph_surrogate s) { return s->out; }
 const uint32_t* surrogate_recv(wbsph_surrogate s) { return s->recv; }
 const uint32_t* surrogate_send(wbsph_surrogate s) { return s->send; }

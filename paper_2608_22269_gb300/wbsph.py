@@ -31,7 +31,7 @@ SYMBOLS = ["wbsph_config_default", "wbsph_create", "wbsph_set_particles", "wbsph
            "wbsph_eval_rates", "wbsph_step", "wbsph_sync", "wbsph_get_fields",
            "wbsph_get_cell_keys", "wbsph_get_neighbors", "wbsph_get_stats", "wbsph_set_profiling",
            "wbsph_get_profile", "wbsph_destroy", "wbsph_last_error", "wbsph_status_string",
-           "wbsph_sort_cells_noalloc"]
+           "wbsph_sort_cells_noalloc", "wbsph_test_bounded_wait"]
 NOALLOC_MAX_N = 524288
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = False):
         "wbsph_last_error": (C.c_char_p, [P]),
         "wbsph_status_string": (C.c_char_p, [I]),
         "wbsph_sort_cells_noalloc": (I, [P, P, i64, P, P]),
+        "wbsph_test_bounded_wait": (I, [P, i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -272,6 +273,11 @@ class Sim:
                                                       _ptr(ids_sorted)))
         cur.wait_stream(self.stream)
         return keys_sorted, ids_sorted
+
+    def test_bounded_wait(self, limit=4096):
+        """Run the bounded-wait check (wbsph_test_bounded_wait); raises
+        WbsphError(WBSPH_E_TIMEOUT) when the wait gave up as designed."""
+        self._check(self.lib.wbsph_test_bounded_wait(self.h, int(limit)))
 
     def set_profiling(self, on=True):
         self._check(self.lib.wbsph_set_profiling(self.h, int(on)))

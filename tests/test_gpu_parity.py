@@ -267,3 +267,22 @@ def test_restart_from_fields_continues_the_run():
     sk = scales(sc.params, sc.water_height)
     assert scaled_err(c.get("x"), a.get("x"), sk["x"]) <= 1e-13
     assert scaled_err(c.get("u"), a.get("u"), sk["u"]) <= 1e-12
+
+
+def test_bounded_device_wait_reports_timeout_and_context_survives():
+    """A device wait that nothing satisfies gives up after its limit and
+    reports WBSPH_E_TIMEOUT through the status word (no trap, no fault); the
+    same handle then reloads and steps normally."""
+    from paper_2608_22269_gb300 import wbsph
+    sc = S.dam_break_2d(dx=0.02, width=1.0, column=(0.3, 0.2))
+    sim = _sim(sc)
+    with pytest.raises(wbsph.WbsphError) as ei:
+        sim.test_bounded_wait(4096)
+    assert ei.value.code == -7
+    sim.set_scene(sc)
+    sim.step(2)
+    sim.sync()
+    st = oracle.State(sc)
+    st.step(2)
+    sk = scales(sc.params, sc.water_height)
+    assert scaled_err(sim.get("x"), st.x, sk["x"]) <= TOL
