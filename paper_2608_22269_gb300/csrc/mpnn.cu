@@ -1061,6 +1061,17 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd(MlpArgs a) {
 // ---------------------------------------------------------------------------
 // Graph, features, aggregation, loss, optimiser
 // ---------------------------------------------------------------------------
+// FP32 value of a double by truncating its IEEE fields with integer
+// instructions (magnitudes below 2^-126 give zero; no infinities arise
+// here). Feature inputs are rounded to BF16 afterwards, so truncation is
+// immaterial, and the FP64 pipe stays free.
+__device__ __forceinline__ float d2f_fields(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (e <= 1023u - 127u) return 0.f;
+  return __uint_as_float((hi & 0x80000000u) | ((e - (1023u - 127u)) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
 __global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, const uint32_t* row_ptr,
                           uint32_t* recv, uint32_t* send, bf16* efeat, const float* node_std) {
   int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1072,30 +1083,28 @@ __global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, cons
   float inv_su[3] = {0.f, 0.f, 0.f};
   for (int d = 0; d < p.dim; ++d) inv_su[d] = 1.f / node_std[d];
   const float inv_sphi = 1.f / node_std[p.dim + 1];
-  double xi[3] = {0, 0, 0};
+  // relative positions from the FP32 position copy (BF16 features need no
+  // FP64 difference), velocities and potentials narrowed on the fields
+  const float4 xi = w.xf[i];
   float ui[3] = {0.f, 0.f, 0.f};
-  for (int d = 0; d < p.dim; ++d) {
-    xi[d] = s.x[d * n + i];
-    ui[d] = (float)s.u[d * n + i];
-  }
-  const float phii = (float)s.phi[i];
+  for (int d = 0; d < p.dim; ++d) ui[d] = d2f_fields(s.u[d * n + i]);
+  const float phii = d2f_fields(s.phi[i]);
   for (int k = 0; k < c; ++k) {
-    uint32_t j = w.nbr[(int64_t)k * nf + gi];
-    double r[3] = {0, 0, 0}, r2 = 0.0;  // every list entry is an exact neighbour
-    for (int d = 0; d < p.dim; ++d) {
-      r[d] = __dsub_rn(s.x[d * n + j], xi[d]);
-      r2 = fma(r[d], r[d], r2);
-    }
+    uint32_t j = w.nbr[(int64_t)k * nf + gi];  // every list entry is an exact neighbour
+    const float4 xj = __ldg(&w.xf[j]);
+    const float r[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
     recv[e] = i;
     send[e] = j;
     // features (r/h, |r|/h, dU/s_U, dphi/s_phi), zero padded to 8, one 16-byte store
     float f[FEAT] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float r2 = 0.f;
     for (int d = 0; d < p.dim; ++d) {
-      f[d] = (float)r[d] * inv_h;
-      f[p.dim + 1 + d] = ((float)s.u[d * n + j] - ui[d]) * inv_su[d];
+      f[d] = r[d] * inv_h;
+      r2 = fmaf(r[d], r[d], r2);
+      f[p.dim + 1 + d] = (d2f_fields(s.u[d * n + j]) - ui[d]) * inv_su[d];
     }
-    f[p.dim] = sqrtf((float)r2) * inv_h;
-    f[2 * p.dim + 1] = ((float)s.phi[j] - phii) * inv_sphi;
+    f[p.dim] = sqrtf(r2) * inv_h;
+    f[2 * p.dim + 1] = (d2f_fields(s.phi[j]) - phii) * inv_sphi;
     uint4 v;
     v.x = pack2(__float2bfloat16(f[0]), __float2bfloat16(f[1]));
     v.y = pack2(__float2bfloat16(f[2]), __float2bfloat16(f[3]));
