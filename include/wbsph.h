@@ -151,7 +151,13 @@ int wbsph_step(wbsph_handle h, int64_t nsteps);
 /* Wait for the handle's stream and read the device status word. */
 int wbsph_sync(wbsph_handle h);
 
-/* Copy one field out in the caller's original particle order. */
+/* Copy one field out in the caller's original particle order: out holds
+ * dim*n (x, U, DU/Dt, shift velocity; SoA) or n doubles, on the host
+ * (where = WBSPH_HOST, pageable or pinned) or the device (WBSPH_DEVICE).
+ * Synchronises the handle's stream once and reads the status word in the
+ * same synchronisation: if a step since the last check set an error (NaN,
+ * domain, singular, overflow, timeout) that code is returned and the
+ * contents of out are unspecified. */
 int wbsph_get_fields(wbsph_handle h, int field, double* out, int where);
 
 /* Test hook: cell keys in sorted order and the original particle id at each

@@ -57,6 +57,8 @@ struct wbsph_s {
   std::vector<ProfEvent> events, pool;
   double prof_ms[WBSPH_K_COUNT] = {0};
   int64_t prof_cnt[WBSPH_K_COUNT] = {0};
+  double* field_tmp = nullptr;       // device: a field in the caller's order, on its way to the host
+  unsigned* status_host = nullptr;   // pinned host copy of the status word
 };
 
 static const char* kStatusNames[] = {"ok", "invalid argument", "out of device memory",
@@ -307,6 +309,7 @@ extern "C" void wbsph_destroy(wbsph_handle h) {
   drop_graph(h);
   free_all(h);
   cudaStreamSynchronize(h->stream);
+  if (h->status_host) cudaFreeHost(h->status_host);
   for (auto& e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto& e : h->pool) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   delete h;
@@ -346,6 +349,7 @@ static int allocate(wbsph_s* h, int64_t n) {
     w.nbr = U32(nfl * (size_t)pair_list_kmax(d));
     w.nbr_cnt = U32(nfl);
   }
+  h->field_tmp = D(d * nn);
   if (h->cfg.precision == WBSPH_MIXED) {
     w.packA = (float4*)dev_alloc(h, nn * sizeof(float4));
     w.packB = (float4*)dev_alloc(h, nn * sizeof(float4));
@@ -610,10 +614,17 @@ extern "C" int wbsph_step(wbsph_handle h, int64_t nsteps) {
   return WBSPH_OK;
 }
 
+// Status bits -> status code (the copy of the word must have landed).
+static int decode_status(wbsph_s* h, unsigned s);
+
 static int read_status(wbsph_s* h) {
-  unsigned s = 0;
-  CK(cudaMemcpyAsync(&s, h->W.status, sizeof s, cudaMemcpyDeviceToHost, h->stream));
+  if (!h->status_host) CK(cudaMallocHost((void**)&h->status_host, sizeof(unsigned)));
+  CK(cudaMemcpyAsync(h->status_host, h->W.status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return decode_status(h, *h->status_host);
+}
+
+static int decode_status(wbsph_s* h, unsigned s) {
   if (!s) return WBSPH_OK;
   // a non-finite value also sends positions out of the domain: report it first
   if (s & kStatNaN) return fail(h, WBSPH_E_NAN, "non-finite rate or state value");
@@ -648,29 +659,23 @@ extern "C" int wbsph_get_fields(wbsph_handle h, int field, double* out, int wher
   if (field < 0 || field > WBSPH_FIELD_VOL || !out) return fail(h, WBSPH_E_INVAL, "bad field or output");
   if (where != WBSPH_HOST && where != WBSPH_DEVICE) return fail(h, WBSPH_E_INVAL, "bad 'where'");
   CK(cudaSetDevice(h->cfg.device));
-  int rc = read_status(h);
-  if (rc) return rc;
   const int64_t n = h->n;
-  if (n == 0) return WBSPH_OK;
+  if (n == 0) return read_status(h);
+  if (!h->status_host) CK(cudaMallocHost((void**)&h->status_host, sizeof(unsigned)));
   bool vec = field == WBSPH_FIELD_X || field == WBSPH_FIELD_U || field == WBSPH_FIELD_DUDT ||
              field == WBSPH_FIELD_DUSHIFT;
   size_t bytes = (size_t)n * (vec ? h->cfg.dim : 1) * sizeof(double);
-  double* tmp = out;
-  void* scratch = nullptr;
-  if (where == WBSPH_HOST) {
-    CK(cudaMallocAsync(&scratch, bytes, h->stream));
-    tmp = (double*)scratch;
-  }
+  // field in the caller's order, copy out and the status word, then one
+  // synchronisation: the output is valid only when the status is clean
+  double* tmp = where == WBSPH_HOST ? h->field_tmp : out;
   launch_field(h->P, h->A, h->W, n, field, tmp, h->stream);
   h->launches += 1;
-  rc = check_launch(h, "get_fields");
-  if (!rc && where == WBSPH_HOST) {
-    cudaError_t e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
-    if (e != cudaSuccess) rc = fail(h, WBSPH_E_CUDA, "copy out: %s", cudaGetErrorString(e));
-  }
-  if (scratch) cudaFreeAsync(scratch, h->stream);
+  int rc = check_launch(h, "get_fields");
+  if (rc) return rc;
+  if (where == WBSPH_HOST) CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->status_host, h->W.status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  return rc;
+  return decode_status(h, *h->status_host);
 }
 
 extern "C" int wbsph_get_cell_keys(wbsph_handle h, uint32_t* keys_sorted, uint32_t* ids_sorted) {
