@@ -75,6 +75,7 @@ struct Work {
   double* dphidt;    // n
   double* dushift;   // dim * n
   double* lambda;    // n
+  double* Lmat;      // 3n (2D) or 6n (3D): L of the last FP64 pair pass (upper triangle, SoA)
   double* vol;       // n
   double* volc;      // n: 5 alpha / h^2 * V, so that -W'(r)/r V = volc (1 - q/2)^3
   float4* xf;        // n: FP32 copy of positions (.w = type) for the candidate prefilter
@@ -121,6 +122,7 @@ void launch_time_step(const Params& p, const Work& w, cudaStream_t st);
 void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid,
                       int stage2, cudaStream_t st);
 int pair_list_kmax(int dim);
+void launch_lambda_fp64(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st);
 void launch_nbr_list(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid, cudaStream_t st,
                      bool exact);
 void launch_rk_stage(const Params& p, const State& s, const Work& w, int64_t n, int stage,

@@ -333,6 +333,7 @@ static int allocate(wbsph_s* h, int64_t n) {
   Work& w = h->W;
   w.dudt = D(d * nn); w.dushift = D(d * nn); w.dphidt = D(nn); w.lambda = D(nn); w.vol = D(nn);
   w.volc = D(nn);
+  w.Lmat = D((size_t)(d == 3 ? 6 : 3) * nn);
   w.xf = (float4*)dev_alloc(h, nn * sizeof(float4));
   w.key = U32(nn); w.key_alt = U32(nn); w.perm = U32(nn); w.perm_alt = U32(nn);
   w.cell_lb = U32((size_t)h->P.ncells + 1);
@@ -429,6 +430,7 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
     CK(cudaMemsetAsync(h->W.dushift, 0, d * vb, h->stream));
     CK(cudaMemsetAsync(h->W.dphidt, 0, vb, h->stream));
     CK(cudaMemsetAsync(h->W.lambda, 0, vb, h->stream));
+    CK(cudaMemsetAsync(h->W.Lmat, 0, (d == 3 ? 6 : 3) * vb, h->stream));
     CK(cudaMemsetAsync(h->W.vol, 0, vb, h->stream));
   }
   rc = check_launch(h, "set_particles");
@@ -668,6 +670,11 @@ extern "C" int wbsph_get_fields(wbsph_handle h, int field, double* out, int wher
   // field in the caller's order, copy out and the status word, then one
   // synchronisation: the output is valid only when the status is clean
   double* tmp = where == WBSPH_HOST ? h->field_tmp : out;
+  if (field == WBSPH_FIELD_LAMBDA && h->cfg.precision != WBSPH_MIXED) {
+    // the FP64 pass stores L; lambda_min is formed here, in FP64
+    launch_lambda_fp64(h->P, h->W, n, h->nf, h->stream);
+    h->launches += 1;
+  }
   launch_field(h->P, h->A, h->W, n, field, tmp, h->stream);
   h->launches += 1;
   int rc = check_launch(h, "get_fields");

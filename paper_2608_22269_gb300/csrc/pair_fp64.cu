@@ -372,9 +372,29 @@ __global__ void __launch_bounds__(PAIR_THREADS, 4)
   if (!active) return;
 
   // ---- epilogue (Eq. sph with the TIC switch; Sec. 3: correction outside the sum) ----
-  double lam = DIM == 2 ? lambda_min_2(L[0], L[1], L[2]) : lambda_min_3(L[0], L[1], L[2], L[3], L[4], L[5]);
+  // The switch needs only lambda_min < threshold: the FP32 closed form
+  // decides unless it lies within 0.05 of the threshold (its error is below
+  // 1e-2 even where two eigenvalues meet), where the FP64 closed form decides.
+  // The lambda_min field itself is formed in FP64 from the stored L when it
+  // is read (k_lambda_fp64).
+  bool tic_branch = false;
+  if (p.use_tic) {
+    const float lf = DIM == 2 ? lambda_min_2f((float)L[0], (float)L[1], (float)L[2])
+                              : lambda_min_3f((float)L[0], (float)L[1], (float)L[2], (float)L[3], (float)L[4],
+                                              (float)L[5]);
+    const float tl = (float)p.tic_lambda;
+    if (fabsf(lf - tl) > 0.05f) {
+      tic_branch = lf < tl;
+    } else {
+      const double lam = DIM == 2 ? lambda_min_2(L[0], L[1], L[2])
+                                  : lambda_min_3(L[0], L[1], L[2], L[3], L[4], L[5]);
+      tic_branch = lam < p.tic_lambda;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < (DIM == 2 ? 3 : 6); ++k) w.Lmat[k * n + i] = L[k];
   double gradphi[DIM], divu = 0.0;
-  if (p.use_tic && lam < p.tic_lambda) {
+  if (tic_branch) {
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       gradphi[c] = C[c];
@@ -420,8 +440,23 @@ __global__ void __launch_bounds__(PAIR_THREADS, 4)
     w.dushift[c * n + i] = v;
     bad |= !isfinite(v);
   }
-  w.lambda[i] = lam;
   if (bad) atomicOr(w.status, kStatNaN);
+}
+
+// lambda_min(L) of the last FP64 pair pass, from the stored L (fluid rows;
+// dummies keep zero).
+__global__ void k_lambda_fp64(Params p, Work w, int64_t n, int64_t nf) {
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gi >= nf) return;
+  const uint32_t i = w.fluid_list[gi];
+  const double* L = w.Lmat;
+  w.lambda[i] = p.dim == 2 ? lambda_min_2(L[i], L[n + i], L[2 * n + i])
+                           : lambda_min_3(L[i], L[n + i], L[2 * n + i], L[3 * n + i], L[4 * n + i], L[5 * n + i]);
+}
+
+void launch_lambda_fp64(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st) {
+  if (nf == 0) return;
+  k_lambda_fp64<<<(unsigned)div_up(nf, 256), 256, 0, st>>>(p, w, n, nf);
 }
 
 int pair_list_kmax(int dim) { return dim == 3 ? 128 : 48; }

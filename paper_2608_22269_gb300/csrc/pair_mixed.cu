@@ -62,18 +62,6 @@ __global__ void k_pack_mixed(Params p, State s, Work w, int64_t n, float4* A, fl
   Cc[i] = ic[0] | (ic[1] << 11) | (ic[2] << 22);
 }
 
-__device__ __forceinline__ float lambda_min_3f(float a00, float a01, float a02, float a11, float a12,
-                                               float a22) {
-  float off = a01 * a01 + a02 * a02 + a12 * a12;
-  if (off == 0.f) return fminf(fminf(a00, a11), a22);
-  float mean = (a00 + a11 + a22) * (1.f / 3.f);
-  float b00 = a00 - mean, b11 = a11 - mean, b22 = a22 - mean;
-  float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.f * off;
-  float pp = sqrtf(p2 * (1.f / 6.f));
-  float det = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) + a02 * (a01 * a12 - b11 * a02);
-  float r = fminf(1.f, fmaxf(-1.f, det / (2.f * pp * pp * pp)));
-  return mean + 2.f * pp * cosf(acosf(r) * (1.f / 3.f) + 2.09439510f);
-}
 
 constexpr int MX_THREADS = 128;
 #ifndef WBSPH_MX_MIN_BLOCKS

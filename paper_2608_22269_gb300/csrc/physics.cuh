@@ -50,6 +50,25 @@ __device__ __forceinline__ double lambda_min_3(double a00, double a01, double a0
   return mean + 2.0 * pp * cos(acos(r) * (1.0 / 3.0) + 2.0943951023931954923);  // + 2 pi / 3
 }
 
+// FP32 forms of the same closed forms (branch selection and the mixed path).
+__device__ __forceinline__ float lambda_min_2f(float a, float b, float c) {
+  float m = 0.5f * (a + c), d = 0.5f * (a - c);
+  return m - sqrtf(d * d + b * b);
+}
+
+__device__ __forceinline__ float lambda_min_3f(float a00, float a01, float a02, float a11, float a12,
+                                               float a22) {
+  float off = a01 * a01 + a02 * a02 + a12 * a12;
+  if (off == 0.f) return fminf(fminf(a00, a11), a22);
+  float mean = (a00 + a11 + a22) * (1.f / 3.f);
+  float b00 = a00 - mean, b11 = a11 - mean, b22 = a22 - mean;
+  float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.f * off;
+  float pp = sqrtf(p2 * (1.f / 6.f));
+  float det = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) + a02 * (a01 * a12 - b11 * a02);
+  float r = fminf(1.f, fmaxf(-1.f, det / (2.f * pp * pp * pp)));
+  return mean + 2.f * pp * cosf(acosf(r) * (1.f / 3.f) + 2.09439510f);
+}
+
 // Inverse of the symmetric L (upper triangle l[]: 2D 00 01 11; 3D 00 01 02
 // 11 12 22) by the adjugate. Returns false (inverse zeroed) when
 // |det| <= 1e-12 max|L_ab|^d, the singularity test of the corrected branch.
