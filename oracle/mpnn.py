@@ -86,6 +86,46 @@ def forward(theta, dim, node_in, recv, send, edge_in, hidden=HIDDEN, layers=LAYE
     return _mlp(h, P["dec"])
 
 
+def graph_and_features(params, x, u, phi, typ, node_mean, node_std, row=None, col=None):
+    """Edges and network inputs of a particle state, by the definitions above.
+
+    u and phi are the stage's values (wall particles after their update from
+    the nearest fluid particle); row/col is the oracle's neighbour CSR of x
+    (computed here when None). Receivers are the fluid particles in ascending
+    index, each with its neighbours within 2h in ascending index as senders.
+    Node inputs: (U, rho/rho0 - 1, phi) minus node_mean over node_std, then the
+    dummy flag; edge inputs: ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U,
+    (phi_j - phi_i)/s_phi) with s the node_std entries. Both are rounded to
+    BF16, the precision the network reads them in. Returns recv, send (int64),
+    node_in (N, d + 3) and edge_in (E, 2d + 2) as float64."""
+    from . import oracle as O
+    d = int(params["dim"])
+    x = np.asarray(x, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    typ = np.asarray(typ)
+    mean = np.asarray(node_mean, dtype=np.float64)
+    std = np.asarray(node_std, dtype=np.float64)
+    if row is None:
+        row, col = O.neighbors(params, x)
+    fl = np.nonzero(typ == 0)[0]
+    cnt = (row[fl + 1] - row[fl]).astype(np.int64)
+    E = int(cnt.sum())
+    recv = np.repeat(fl, cnt).astype(np.int64)
+    start = np.repeat(row[fl], cnt)
+    within = np.arange(E, dtype=np.int64) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    send = np.asarray(col, dtype=np.int64)[start + within]
+    h = params["h_over_dx"] * params["dx"]
+    rho = O.density(params, phi)
+    raw = np.r_[u[:d], (rho / params["rho0"] - 1.0)[None], phi[None]]
+    node_in = np.c_[((raw - mean[:d + 2, None]) / std[:d + 2, None]).T, (typ != 0).astype(np.float64)]
+    r = x[:d, send] - x[:d, recv]
+    edge_in = np.c_[(r / h).T, np.sqrt((r * r).sum(axis=0)) / h,
+                    ((u[:d, send] - u[:d, recv]) / std[:d, None]).T, (phi[send] - phi[recv]) / std[d + 1]]
+    return (recv, send, bf16_round(node_in).astype(np.float64),
+            bf16_round(edge_in).astype(np.float64))
+
+
 def loss(out, target, fluid):
     d = out[fluid] - target[fluid]
     return (d * d).mean()

@@ -1,0 +1,239 @@
+"""Parity at the full sizes the benchmark runs, on sampled outputs.
+
+Workloads (each built by the scene generator, then put out of equilibrium by
+a seeded perturbation: jittered positions, random velocities, potential
+noise):
+- 3D dam break, 1,208,207 fluid + 498,949 dummy particles (dx = 0.0084);
+- 3D sloshing tank, 17,576,000 fluid particles + dummies (dx = 0.00769),
+  the largest size;
+- 2D dam break, 249,218 fluid particles (dx = 0.00085);
+- 2D Gaussian-bump tank, about 250k fluid particles (dx = 0.002) with
+  delta-SPH, shifting and TIC on.
+
+The GPU runs the whole scene through the C-ABI, in the launch configuration
+of the benchmark (the SSP-RK2 step replayed from its captured CUDA graph).
+The oracle computes the sampled particles from a patch cut around them:
+every particle within 4h per axis for one stage (the neighbours within 2h
+and, for each neighbouring dummy, the fluid particles within 2h of it) and
+within 8h plus a margin for one step (two stages). Global inputs of a patch
+are computed by the oracle from the whole scene: U_max of the stage and the
+time step. The shifting term needs U_max of the second stage, which only the
+whole scene fixes, so the step checks run with shifting off; the stage
+checks cover it.
+
+Bit-exact: cell keys and sort order of the whole scene; neighbour rows of
+the sampled particles. Within 1e-12 of the natural scale: FP64 rates and
+fields. The mixed path and the surrogate are held to the tolerances of their
+small-size tests.
+"""
+import types
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_22269_gb300 import scenes as S
+from tests.helpers import dynamic, patch_indices, sample_fluid, scaled_err, scales
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+MIXED_TOL = 2e-5
+
+FULL = {
+    "dam3d_1.2M": lambda: S.dam_break_3d(dx=0.0084),
+    "slosh3d_17.6M": lambda: S.sloshing_3d(),
+    "dam2d_249k": lambda: S.dam_break_2d(dx=0.00085, width=2.0, wall=0.6, column=(0.6, 0.3)),
+    "gauss2d_250k": lambda: S.topography_tank_2d("gauss", dx=0.002, use_delta=1, use_pst=1, use_tic=1),
+}
+_cache = {}
+
+
+def _scene(name, **override):
+    """The perturbed full-size scene (cached per name; overrides give a copy
+    with changed parameters)."""
+    if name not in _cache:
+        _cache.clear()  # hold one full-size scene at a time
+        _cache[name] = dynamic(FULL[name](), seed=5, amp=0.3)
+    sc = _cache[name]
+    if override:
+        sc = sc.copy()
+        sc.params.update(override)
+    return sc
+
+
+def _sim(sc, precision=0):
+    from paper_2608_22269_gb300 import wbsph
+    sim = wbsph.Sim(sc.params, precision=precision, water_height=sc.water_height)
+    sim.set_scene(sc)
+    return sim
+
+
+def _h(p):
+    return p["h_over_dx"] * p["dx"]
+
+
+def _umax(sc):
+    """U_max over fluid of the whole scene, by the oracle."""
+    st = oracle.State(sc)
+    return st.l2_velocity()[1]
+
+
+def _patch(sc, smp, reach):
+    idx = patch_indices(sc.x, sc.x[:, smp], reach)
+    return idx, np.searchsorted(idx, smp)
+
+
+def _stage_oracle(sc, smp, umax, t=0.0):
+    p = sc.params
+    idx, loc = _patch(sc, smp, 4.0 * _h(p) + 0.05 * p["dx"])
+    m = oracle.mass(p, sc.phi[idx])
+    r = oracle.stage_rates(p, sc.x[:, idx], sc.u[:, idx], sc.phi[idx], m, sc.type[idx],
+                           sc.normal[:, idx], t=t, umax=umax)
+    return idx, loc, r
+
+
+@pytest.mark.parametrize("name", sorted(FULL))
+def test_full_size_keys_and_sort_order_bitexact(name):
+    sc = _scene(name)
+    sim = _sim(sc)
+    sim.build_neighbors()
+    keys, ids = sim.cell_keys()
+    ok = oracle.cell_keys(sc.params, sc.x)
+    perm = oracle.sort_by_key(ok)
+    assert np.array_equal(keys, ok[perm])
+    assert np.array_equal(ids, perm)
+    sim.close()
+
+
+@pytest.mark.parametrize("name", ["dam3d_1.2M", "dam2d_249k", "gauss2d_250k"])
+def test_full_size_neighbour_rows_bitexact(name):
+    """Neighbour rows of sampled particles (fluid and dummy) against the
+    oracle's search on the patch of 2h around them."""
+    sc = _scene(name)
+    sim = _sim(sc)
+    row, col = sim.neighbors()
+    rng = np.random.default_rng(3)
+    smp = np.unique(np.r_[sample_fluid(sc, 96, seed=4),
+                          rng.choice(np.nonzero(sc.type != 0)[0], 32, replace=False)])
+    p = sc.params
+    idx, loc = _patch(sc, smp, 2.0 * _h(p) + 0.05 * p["dx"])
+    orow, ocol = oracle.neighbors(p, sc.x[:, idx])
+    for i, li in zip(smp, loc):
+        want = np.sort(idx[ocol[orow[li]:orow[li + 1]]])
+        assert np.array_equal(col[row[i]:row[i + 1]], want), i
+    sim.close()
+
+
+@pytest.mark.parametrize("name", sorted(FULL))
+def test_full_size_stage_rates_sampled(name):
+    sc = _scene(name)
+    sim = _sim(sc)
+    sim.eval_rates()
+    smp = sample_fluid(sc, 64)
+    idx, loc, r = _stage_oracle(sc, smp, _umax(sc))
+    sk = scales(sc.params, sc.water_height)
+    errs = {
+        "dudt": scaled_err(sim.get("dudt")[:, smp], r["dudt"][:, loc], sk["dudt"]),
+        "dphidt": scaled_err(sim.get("dphidt")[smp], r["dphidt"][loc], sk["dphidt"]),
+        "dushift": scaled_err(sim.get("dushift")[:, smp], r["dushift"][:, loc], sk["dushift"]),
+        "lambda": scaled_err(sim.get("lambda")[smp], r["lam"][loc], 1.0),
+    }
+    # wall particles within 2h of a sample: their U and phi after the update
+    # from the nearest fluid particle
+    h2 = (2.0 * _h(sc.params)) ** 2
+    d = idx[sc.type[idx] != 0]
+    near = np.zeros(d.size, bool)
+    for c in sc.x[:, smp].T:
+        near |= ((sc.x[:, d] - c[:, None]) ** 2).sum(0) <= h2
+    dl = np.searchsorted(idx, d[near])
+    if dl.size:
+        errs["u_dummy"] = scaled_err(sim.get("u")[:, d[near]], r["u"][:, dl], sk["u"])
+        errs["phi_dummy"] = scaled_err(sim.get("phi")[d[near]], r["phi"][dl], sk["phi"])
+    print(name, "samples", smp.size, "patch", idx.size, "dummies", int(near.sum()), errs)
+    for k, v in errs.items():
+        assert v <= TOL, (k, v)
+    sim.close()
+
+
+@pytest.mark.parametrize("name", sorted(FULL))
+def test_full_size_step_sampled(name):
+    """One SSP-RK2 step replayed from the captured CUDA graph: a first step
+    captures it, the state is reloaded (same counts, so the graph is kept)
+    and the second step replays it. Shifting off (see the module note)."""
+    sc = _scene(name, use_pst=0)
+    p = sc.params
+    sim = _sim(sc)
+    sim.step(1)
+    sim.set_scene(sc)
+    sim.step(1)
+    dt = oracle.time_step(p, sc.u, sc.type)
+    st = sim.stats()
+    assert abs(st["dt"] - dt) <= 4e-16 * dt
+    smp = sample_fluid(sc, 24, seed=12)
+    idx, loc = _patch(sc, smp, 8.0 * _h(p) + 0.5 * p["dx"])
+    sub = types.SimpleNamespace(params=dict(p, fixed_dt=dt), x=sc.x[:, idx], u=sc.u[:, idx],
+                                phi=sc.phi[idx], type=sc.type[idx], normal=sc.normal[:, idx])
+    ref = oracle.State(sub).step(1)
+    sk = scales(p, sc.water_height)
+    errs = {"x": scaled_err(sim.get("x")[:, smp], ref.x[:, loc], sk["x"]),
+            "u": scaled_err(sim.get("u")[:, smp], ref.u[:, loc], sk["u"]),
+            "phi": scaled_err(sim.get("phi")[smp], ref.phi[loc], sk["phi"])}
+    print(name, "samples", smp.size, "patch", idx.size, errs)
+    for k, v in errs.items():
+        assert v <= TOL, (k, v)
+    sim.close()
+
+
+@pytest.mark.parametrize("name", ["dam3d_1.2M", "slosh3d_17.6M", "gauss2d_250k"])
+def test_full_size_mixed_rates_sampled(name):
+    from paper_2608_22269_gb300 import wbsph
+    sc = _scene(name)
+    sim = _sim(sc, wbsph.MIXED)
+    sim.eval_rates()
+    smp = sample_fluid(sc, 64)
+    idx, loc, r = _stage_oracle(sc, smp, _umax(sc))
+    keep = np.abs(r["lam"][loc] - sc.params["tic_lambda"]) > 1e-4  # TIC branch may flip in FP32
+    s, l = smp[keep], loc[keep]
+    sk = scales(sc.params, sc.water_height)
+    errs = {"dudt": scaled_err(sim.get("dudt")[:, s], r["dudt"][:, l], sk["dudt"]),
+            "dphidt": scaled_err(sim.get("dphidt")[s], r["dphidt"][l], sk["dphidt"]),
+            "dushift": scaled_err(sim.get("dushift")[:, s], r["dushift"][:, l], sk["dushift"])}
+    print(name, "mixed", "samples", s.size, errs)
+    for k, v in errs.items():
+        assert v <= MIXED_TOL, (k, v)
+    sim.close()
+
+
+def test_full_size_surrogate_sampled():
+    """Surrogate rates at 249,218 fluid particles (the committed trained
+    network, through the same predict call as the rollouts) against the FP64
+    reference network on patches: three message-passing layers reach three
+    neighbour hops (6h), so every particle within 6h per axis of a sample,
+    with the oracle's wall update of the whole scene."""
+    import os
+
+    from oracle import mpnn
+    from paper_2608_22269_gb300 import surrogate as SG
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    z = np.load(os.path.join(root, "paper_2608_22269_gb300", "data", "surrogate_2d.npz"))
+    sur, norm = SG.load(os.path.join(root, "paper_2608_22269_gb300", "data", "surrogate_2d.npz"), 2)
+    nm, ns, om, osd = (np.asarray(a, dtype=np.float32) for a in norm)
+    sc = _scene("dam2d_249k")
+    p = sc.params
+    sim = _sim(sc)
+    sur.predict(sim)
+    dudt, dphidt = sim.get("dudt"), sim.get("dphidt")
+    u, phi = oracle.dummy_update(p, sc.x, sc.u, sc.phi, sc.type, sc.normal, 0.0)
+    smp = sample_fluid(sc, 32, seed=21)
+    idx, loc = _patch(sc, smp, 6.0 * _h(p) + 0.05 * p["dx"])
+    recv, send, node_in, edge_in = mpnn.graph_and_features(p, sc.x[:, idx], u[:, idx], phi[idx],
+                                                           sc.type[idx], nm, ns)
+    th = mpnn.round_weights_bf16(z["params"], 2)
+    out = mpnn.forward_np(th, 2, node_in, recv, send, edge_in)[loc]
+    ref = out * osd + om
+    gpu = np.c_[dudt[:, smp].T, dphidt[smp]]
+    rel = np.abs(gpu - ref).max(axis=0) / np.abs(ref).max(axis=0)
+    print("surrogate full size: samples", smp.size, "patch", idx.size, "edges", recv.size, "rel", rel)
+    assert np.all(rel < 2e-2)
+    sur.close()
+    sim.close()

@@ -1,6 +1,8 @@
 """BF16 surrogate kernels (forward, backward, training, anchored rollouts)
 against the FP64 reference of oracle/mpnn.py, on identical BF16-rounded
-weights and the same graph and features."""
+weights. The reference builds its own graph and features from the same
+host state (oracle neighbour search, wall update and EOS), and its targets
+and normalisation come from the oracle's stage rates."""
 import numpy as np
 import pytest
 
@@ -25,6 +27,10 @@ def _state(dim=2, seed=3, dx2=0.01):
 
 
 def _setup(sc, seed=1):
+    """Sim and network of a state. The normalisation comes from the oracle's
+    stage rates of the same state (host inputs only); returns the sim, the
+    surrogate, the FP32 parameters, the output normalisation and the oracle
+    rates (with the dummies' updated U and phi)."""
     from paper_2608_22269_gb300 import wbsph
     dim = sc.params["dim"]
     sim = wbsph.Sim(sc.params, water_height=sc.water_height)
@@ -36,40 +42,40 @@ def _setup(sc, seed=1):
     f = sc.type == 0
     node_mean = np.r_[sc.u[:, f].mean(1), 0.0, sc.phi[f].mean()].astype(np.float32)
     node_std = np.r_[sc.u[:, f].std(1), 1e-3, sc.phi[f].std()].astype(np.float32)
-    sim.eval_rates()
-    a = np.r_[sim.get("dudt")[:, f], sim.get("dphidt")[None, f]]
+    r = oracle.stage_rates(sc.params, sc.x, sc.u, sc.phi, oracle.mass(sc.params, sc.phi), sc.type,
+                           sc.normal)
+    a = np.r_[r["dudt"][:, f], r["dphidt"][None, f]]
     out_mean, out_std = a.mean(1).astype(np.float32), a.std(1).astype(np.float32)
     sur.set_normalization(node_mean, node_std, out_mean, out_std)
-    return sim, sur, theta, (out_mean, out_std)
+    return sim, sur, theta, (node_mean, node_std, out_mean, out_std), r
 
 
 @pytest.mark.parametrize("dim", [2, 3])
 def test_forward_and_gradient_match_fp64_reference(dim):
+    """GPU forward and loss gradient against the FP64 reference run on the
+    oracle's own graph and features of the same state, with the oracle's
+    rates as targets."""
     sc = _state(dim)
-    sim, sur, theta, (om, osd) = _setup(sc)
+    sim, sur, theta, (nm, ns, om, osd), r = _setup(sc)
     dbg = sur.debug(sim)
     n = sc.n
-    fin = dim + 3
-    node_in = dbg["node_feat"][:, :fin].astype(np.float64)
-    edge_in = dbg["edge_feat"][:, :2 * dim + 2].astype(np.float64)
+    recv, send, node_in, edge_in = mpnn.graph_and_features(sc.params, sc.x, r["u"], r["phi"], sc.type,
+                                                           nm, ns)
     th = mpnn.round_weights_bf16(theta, dim)
-    out = mpnn.forward_np(th, dim, node_in, dbg["recv"], dbg["send"], edge_in)
+    out = mpnn.forward_np(th, dim, node_in, recv, send, edge_in)
     fid = dbg["fluid_ids"].astype(np.int64)
     ref = out[fid]
     gpu = dbg["out"]
     rel = np.abs(gpu - ref).max() / np.abs(ref).max()
     print(dim, "forward rel err", rel)
     assert rel < 2e-2
-    # loss gradient: targets = normalised plain rates of the same state
-    f = sc.type == 0
-    tgt = np.zeros((n, dim + 1))
-    rates = np.r_[sim.get("dudt"), sim.get("dphidt")[None]].T
-    tgt[:] = (rates - om) / osd
+    # loss gradient: targets = normalised oracle rates of the same state
+    tgt = (np.r_[r["dudt"], r["dphidt"][None]].T - om) / osd
     fluid = np.zeros(n, bool)
     fluid[fid] = True
     dout = np.zeros((n, dim + 1))
     dout[fluid] = 2.0 * (out[fluid] - tgt[fluid]) / (fluid.sum() * (dim + 1))
-    g_ref = mpnn.grad_np(th, dim, node_in, dbg["recv"], dbg["send"], edge_in, dout)
+    g_ref = mpnn.grad_np(th, dim, node_in, recv, send, edge_in, dout)
     g = dbg["grad"].astype(np.float64)
     cos = g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref))
     reln = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
@@ -87,32 +93,27 @@ def test_graph_and_edge_features_follow_the_positions(dim, dx2):
     15,000-fluid case spans several chunks of the row-pointer scan and
     hundreds of 128-edge tiles."""
     sc = _state(dim, dx2=dx2)
-    sim, sur, theta, _ = _setup(sc)
+    sim, sur, theta, (nm, ns, _, _), r = _setup(sc)
     dbg = sur.debug(sim)
-    row, col = oracle.neighbors(sc.params, sc.x)
-    f = sc.type == 0
-    ref = {(i, int(j)) for i in np.nonzero(f)[0] for j in col[row[i]:row[i + 1]]}
+    recv, send, node_in, edge_in = mpnn.graph_and_features(sc.params, sc.x, r["u"], r["phi"], sc.type,
+                                                           nm, ns)
+    ref = dict(zip(zip(recv.tolist(), send.tolist()), range(recv.size)))
     got = list(zip(dbg["recv"].tolist(), dbg["send"].tolist()))
-    assert len(got) == len(ref) and set(got) == ref
-    recv, send = dbg["recv"].astype(np.int64), dbg["send"].astype(np.int64)
-    h = sc.params["h_over_dx"] * sc.params["dx"]
-    su = sc.u[:, f].std(1)
-    sphi = sc.phi[f].std()
-    # U and phi after the stage's dummy update (wall particles take theirs
-    # from the nearest fluid particle before the graph is built)
-    u, phi = sim.get("u"), sim.get("phi")
-    r = sc.x[:, send] - sc.x[:, recv]
-    want = np.r_[r / h, np.sqrt((r ** 2).sum(0))[None] / h,
-                 (u[:, send] - u[:, recv]) / su[:, None],
-                 (phi[send] - phi[recv])[None] / sphi].T
+    assert len(got) == len(ref) and set(got) == set(ref)
+    # features of each GPU edge against the oracle's (both BF16; U and phi of
+    # wall particles after the stage's update from the nearest fluid particle)
+    want = edge_in[[ref[e] for e in got]]
     ef = dbg["edge_feat"][:, :2 * dim + 2]
     assert np.all(np.abs(ef - want) <= 8e-3 * np.maximum(1.0, np.abs(want)))
     assert np.all(dbg["edge_feat"][:, 2 * dim + 2:] == 0.0)
+    # node features, all particles in the caller's order
+    nfe = dbg["node_feat"][:, :dim + 3]
+    assert np.all(np.abs(nfe - node_in) <= 8e-3 * np.maximum(1.0, np.abs(node_in)))
 
 
 def test_training_reduces_loss():
     sc = _state(2, seed=5)
-    sim, sur, theta, _ = _setup(sc, seed=2)
+    sim, sur, theta, _, _ = _setup(sc, seed=2)
     l0 = sur.eval(sim)
     for _ in range(60):
         sur.train_step(sim, 3e-3)
@@ -123,7 +124,7 @@ def test_training_reduces_loss():
 
 def test_anchored_rollout_bookkeeping():
     sc = _state(2, seed=6)
-    sim, sur, theta, _ = _setup(sc, seed=3)
+    sim, sur, theta, _, _ = _setup(sc, seed=3)
     st = sur.step(sim, 20, anchor_every=5, tau=1e9)
     assert st["anchors"] == 4 and st["plain_steps"] == 4 and st["surrogate_steps"] == 16
     assert st["fallbacks"] == 0 and np.isfinite(st["max_rel_err"])

@@ -91,3 +91,34 @@ def test_parameter_count_and_layout():
     assert mpnn.num_params(2) == mpnn.init_params(2).size
     P = mpnn.unflatten(torch.zeros(mpnn.num_params(3), dtype=torch.float64), 3)
     assert P["mp0_e"][0].shape == (192, 64) and P["dec"][2].shape == (64, 4)
+
+
+def test_graph_and_features_by_hand():
+    """Receivers are the fluid particles, senders everything within 2h; the
+    features follow their definitions, worked out by hand for four particles
+    (h = 0.13): fluid 0 at (0.5, 0.5), fluid 1 at (0.6, 0.5), a dummy 2 at
+    (0.5, 0.3) and fluid 3 at (0.9, 0.5), out of everyone's reach."""
+    import math
+
+    from paper_2608_22269_gb300 import scenes as S
+    p = S.default_params(2, dx=0.1, c0=10.0)
+    x = np.array([[0.5, 0.6, 0.5, 0.9], [0.5, 0.5, 0.3, 0.5]])
+    u = np.array([[0.1, -0.2, 0.05, 0.0], [0.3, 0.0, -0.1, 0.0]])
+    phi = np.array([2.0, 1.5, 4.0, 0.0])
+    typ = np.array([0, 0, 1, 0], dtype=np.uint8)
+    mean = np.array([0.1, -0.1, 0.0, 1.0], dtype=np.float32)
+    std = np.array([0.5, 0.25, 0.001, 2.0], dtype=np.float32)
+    recv, send, node_in, edge_in = mpnn.graph_and_features(p, x, u, phi, typ, mean, std)
+    assert recv.tolist() == [0, 0, 1, 1] and send.tolist() == [1, 2, 0, 2]
+    h = 0.13
+    m, sd = mean.astype(np.float64), std.astype(np.float64)  # the FP32 values the library holds
+    for k in range(4):
+        rho = 1000.0 * math.exp(phi[k] / 100.0)  # linear EOS, C0 = 10
+        want = [(u[0, k] - m[0]) / sd[0], (u[1, k] - m[1]) / sd[1], (rho / 1000.0 - 1.0) / sd[2],
+                (phi[k] - m[3]) / sd[3], 1.0 if k == 2 else 0.0]
+        assert np.array_equal(node_in[k], mpnn.bf16_round(np.array(want)).astype(np.float64))
+    for e, (i, j) in enumerate([(0, 1), (0, 2), (1, 0), (1, 2)]):
+        rx, ry = x[0, j] - x[0, i], x[1, j] - x[1, i]
+        want = [rx / h, ry / h, math.hypot(rx, ry) / h, (u[0, j] - u[0, i]) / sd[0],
+                (u[1, j] - u[1, i]) / sd[1], (phi[j] - phi[i]) / sd[3]]
+        assert np.allclose(edge_in[e], mpnn.bf16_round(np.array(want)), rtol=0, atol=1e-12), e
