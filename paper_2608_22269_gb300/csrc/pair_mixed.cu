@@ -65,8 +65,29 @@ __global__ void k_pack_mixed(Params p, State s, Work w, int64_t n, float4* A, fl
 
 constexpr int MX_THREADS = 128;
 #ifndef WBSPH_MX_MIN_BLOCKS
-#define WBSPH_MX_MIN_BLOCKS 3  // resident blocks per SM the register budget is sized for
+#define WBSPH_MX_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for
 #endif
+#ifndef WBSPH_MX_RING
+#define WBSPH_MX_RING 2  // list entries of each lane in flight (shared-memory ring)
+#endif
+constexpr int MX_RING = WBSPH_MX_RING;
+
+// Asynchronous global -> shared copies (cp.async, cached in L1), one group
+// per list entry; a thread waits only for its own groups.
+__device__ __forceinline__ void mx_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void mx_cp4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void mx_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void mx_wait_ring() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(MX_RING - 1) : "memory");
+}
 
 // Pair sums over the candidate lists built by k_nbr_list (the same lists as
 // the FP64 pass); the neighbour test is the FP32 cell-relative distance.
@@ -103,24 +124,32 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
   unsigned npairs = 0;
   const int maxc = __reduce_max_sync(0xffffffffu, cnt);
   const uint32_t* lst = w.nbr + gi;
-  // software pipeline: the packed data of entry k + 1 and the index of
-  // entry k + 2 are loaded while entry k is summed (the loop is latency
-  // bound on these dependent gathers, not on the FP32 pipe)
-  float4 An = make_float4(0.f, 0.f, 0.f, 0.f), Bn = An;
-  uint32_t cn = 0, jnn = 0;
-  if (cnt > 0) {
-    uint32_t j0 = __ldg(lst);
-    An = A[j0]; Bn = B[j0]; cn = Cc[j0];
+  // The packed data of list entry k + 1 is gathered (cp.async into this
+  // lane's slot of a shared-memory ring) while entry k is summed: the loop is
+  // latency bound on these dependent gathers, and the ring holds them without
+  // registers, which leaves room for four resident blocks per SM.
+  __shared__ float4 ringA[MX_RING * MX_THREADS];
+  __shared__ float4 ringB[MX_RING * MX_THREADS];
+  __shared__ uint32_t ringC[MX_RING * MX_THREADS];
+  const int t = threadIdx.x;
+  auto fetch = [&](int k, uint32_t j) {  // entry k (< cnt), neighbour j, into slot k % MX_RING
+    const int q = (k % MX_RING) * MX_THREADS + t;
+    mx_cp16(&ringA[q], A + j);
+    mx_cp16(&ringB[q], B + j);
+    mx_cp4(&ringC[q], Cc + j);
+  };
+#pragma unroll
+  for (int k = 0; k < MX_RING; ++k) {  // one group per entry (empty past the list)
+    if (k < cnt) fetch(k, __ldg(lst + (int64_t)k * nf));
+    mx_commit();
   }
-  if (cnt > 1) jnn = __ldg(lst + nf);
+  uint32_t jn = MX_RING < cnt ? __ldg(lst + (int64_t)MX_RING * nf) : 0u;  // next entry to fetch
   for (int k = 0; k < maxc; ++k) {
     if (k >= cnt) continue;
-    const float4 Aj = An, Bj = Bn;
-    const uint32_t cj = cn;
-    if (k + 1 < cnt) {
-      An = A[jnn]; Bn = B[jnn]; cn = Cc[jnn];
-      if (k + 2 < cnt) jnn = __ldg(lst + (int64_t)(k + 2) * nf);
-    }
+    mx_wait_ring();  // entry k's group has landed; the later ones may still be in flight
+    const int q = (k % MX_RING) * MX_THREADS + t;
+    const float4 Aj = ringA[q], Bj = ringB[q];
+    const uint32_t cj = ringC[q];
     float r[DIM], du[DIM];
     r[0] = fmaf((float)((int)(cj & 2047u) - cix), R, Aj.x - Ai.x);
     r[1] = fmaf((float)((int)((cj >> 11) & 2047u) - ciy), R, Aj.y - Ai.y);
@@ -131,15 +160,23 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
     if (DIM == 3) du[DIM - 1] = Bj.z - Bi.z;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) { r2 = fmaf(r[c], r[c], r2); dun = fmaf(du[c], r[c], dun); }
+    const float Bjw = Bj.w, Ajw = Aj.w;
+    // the slot is refilled with entry k + MX_RING only after the values read
+    // from it (two 16-byte and one 4-byte shared load) have been used above
+    if (k + MX_RING < cnt) {
+      fetch(k + MX_RING, jn);
+      if (k + MX_RING + 1 < cnt) jn = __ldg(lst + (int64_t)(k + MX_RING + 1) * nf);
+    }
+    mx_commit();
     if (!(r2 <= four_h2 && r2 > 0.f)) continue;  // the neighbour test in FP32
     ++npairs;
     float inv_r = rsqrtf(r2);
     float rr = r2 * inv_r;
     float t = fmaf(-rr, inv_two_h, 1.f);
     float t3 = t * t * t;
-    float g = coef * t3 * fabsf(Bj.w);
+    float g = coef * t3 * fabsf(Bjw);
     dun *= inv_r;
-    float dphi = Aj.w - Ai.w, sphi = Aj.w + Ai.w;
+    float dphi = Ajw - Ai.w, sphi = Ajw + Ai.w;
     float rs = fmaf(-c0, dun, dphi);
     float gr[DIM];
 #pragma unroll
@@ -159,7 +196,7 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
       for (int d2 = 0; d2 < DIM; ++d2) M[c * DIM + d2].add(du[c] * gr[d2]);
     }
     D.add(dphi * g);
-    if (Bj.w > 0.f) {
+    if (Bjw > 0.f) {
 #pragma unroll
       for (int c = 0; c < DIM; ++c) Lam[c].add(du[c] * g);
     }
