@@ -85,6 +85,9 @@ struct Work {
   uint32_t* perm_alt;
   uint32_t* cell_lb; // ncells + 1: first sorted index with key >= c
   uint32_t* fluid_list;  // n_fluid: sorted indices of fluid particles
+  float4* xff;           // n_fluid: xf of the fluid particles, in fluid_list order
+  uint32_t* fkey;        // n_fluid: their cell keys
+  uint32_t* fcell_lb;    // ncells + 1: first fluid_list position with key >= c
   uint32_t* dummy_list;  // n_dummy: sorted indices of dummy particles
   uint32_t* block_cnt;   // scratch for scans
   uint32_t* hist;        // radix histograms
@@ -108,16 +111,17 @@ void launch_radix_sort(const Params& p, Work& w, int64_t n, cudaStream_t st, int
 void launch_gather(const Params& p, const State& src, const State& dst, const Work& w, int64_t n,
                    bool with_base, cudaStream_t st);
 void launch_cell_bounds(const Params& p, const Work& w, int64_t n, cudaStream_t st);
-void launch_fluid_list(const State& s, const Work& w, int64_t n, int64_t nd, cudaStream_t st,
-                       int* launches);
+void launch_fluid_list(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int64_t nd,
+                       cudaStream_t st, int* launches);
 void launch_count_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
                             uint32_t* counts, cudaStream_t st);
 void launch_fill_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
                            const int64_t* row_ptr_by_oid, int32_t* cols, cudaStream_t st);
 
 // ---- launchers (pair_fp64.cu) ----
+// Dummy walls, then (volumes = true) V = m / rho and U_max of the stage.
 void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int64_t nd,
-                    int stage2, cudaStream_t st);
+                    int stage2, cudaStream_t st, bool volumes = true);
 void launch_time_step(const Params& p, const Work& w, cudaStream_t st);
 void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid,
                       int stage2, cudaStream_t st);

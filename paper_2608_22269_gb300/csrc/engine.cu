@@ -23,7 +23,7 @@ using namespace wbsph;
 
 namespace wbsph {
 void launch_mass(const Params& p, const double* phi, double* mass, int64_t n, cudaStream_t st);
-int launch_pack_mixed(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
+int launch_prepass_mixed(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
 void launch_wait_probe(unsigned* status, uint32_t limit, cudaStream_t st);
 void launch_pair_mixed(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
                        cudaStream_t st);
@@ -339,6 +339,12 @@ static int allocate(wbsph_s* h, int64_t n) {
   w.cell_lb = U32((size_t)h->P.ncells + 1);
   w.fluid_list = U32(nn);
   w.dummy_list = U32((size_t)(h->nd > 0 ? h->nd : 1));
+  if (h->nd > 0) {
+    const size_t nfl = (size_t)(h->nf > 0 ? h->nf : 1);
+    w.xff = (float4*)dev_alloc(h, nfl * sizeof(float4));
+    w.fkey = U32(nfl);
+    w.fcell_lb = U32((size_t)h->P.ncells + 1);
+  }
   w.block_cnt = U32((size_t)div_up((int64_t)nn, 1024) + 1);
   w.hist = U32((size_t)radix_sort_scratch_words((int64_t)nn));
   w.umax_bits = (unsigned long long*)dev_alloc(h, 8);
@@ -467,7 +473,7 @@ static int build(wbsph_s* h, bool with_base) {
   {
     ProfScope ps(h, WBSPH_K_CELLS);
     launch_cell_bounds(h->P, h->W, n, st);
-    launch_fluid_list(h->A, h->W, n, h->nd, st, &l);
+    launch_fluid_list(h->P, h->A, h->W, n, h->nf, h->nd, st, &l);
   }
   h->launches += 3 + l;
   return check_launch(h, "neighbour build");
@@ -476,19 +482,20 @@ static int build(wbsph_s* h, bool with_base) {
 static int rates(wbsph_s* h, int stage2) {
   const int64_t n = h->n;
   cudaStream_t st = h->stream;
+  const bool mixed = h->cfg.precision == WBSPH_MIXED;
   {
+    // dummy walls, then V and U_max (FP64 path) or V, U_max and the packed
+    // FP32 copies in one kernel (mixed path)
     ProfScope ps(h, WBSPH_K_PREPASS);
-    launch_prepass(h->P, h->A, h->W, n, h->nd, stage2, st);
+    launch_prepass(h->P, h->A, h->W, n, h->nd, stage2, st, !mixed);
+    if (mixed) {
+      int rc = launch_prepass_mixed(h->P, h->A, h->W, n, st);
+      if (rc) return fail(h, rc, "mixed path: grid too large for packed cell coordinates");
+    }
   }
   if (!stage2) {
     ProfScope ps(h, WBSPH_K_OTHER);
     launch_time_step(h->P, h->W, st);
-  }
-  const bool mixed = h->cfg.precision == WBSPH_MIXED;
-  if (mixed) {
-    ProfScope ps(h, WBSPH_K_PREPASS);
-    int rc = launch_pack_mixed(h->P, h->A, h->W, n, st);
-    if (rc) return fail(h, rc, "mixed path: grid too large for packed cell coordinates");
   }
   {
     ProfScope ps(h, WBSPH_K_NLIST);
@@ -499,8 +506,7 @@ static int rates(wbsph_s* h, int stage2) {
     if (mixed) launch_pair_mixed(h->P, h->A, h->W, n, h->nf, stage2, st);
     else launch_pair_fp64(h->P, h->A, h->W, n, h->nf, stage2, st);
   }
-  h->launches += (n ? 1 : 0) + (h->nd ? 1 : 0) + (stage2 ? 0 : 1) + (h->nf ? 2 : 0) +
-                 (h->cfg.precision == WBSPH_MIXED && n ? 1 : 0);
+  h->launches += (n ? 1 : 0) + (h->nd ? 1 : 0) + (stage2 ? 0 : 1) + (h->nf ? 2 : 0);
   return check_launch(h, "stage rates");
 }
 

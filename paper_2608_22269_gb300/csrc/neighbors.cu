@@ -373,7 +373,10 @@ __global__ void __launch_bounds__(CMP_THREADS) k_count_type(const uint8_t* __res
 
 __global__ void __launch_bounds__(CMP_THREADS) k_write_type(const uint8_t* __restrict__ type, int64_t n,
                                                            uint8_t want, const uint32_t* __restrict__ off,
-                                                           uint32_t* __restrict__ list) {
+                                                           uint32_t* __restrict__ list,
+                                                           const float4* __restrict__ xf, float4* xf_out,
+                                                           const uint32_t* __restrict__ key,
+                                                           uint32_t* key_out) {
   __shared__ uint32_t wsum[CMP_THREADS / 32];
   int64_t i = blockIdx.x * (int64_t)CMP_THREADS + threadIdx.x;
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -384,23 +387,36 @@ __global__ void __launch_bounds__(CMP_THREADS) k_write_type(const uint8_t* __res
   uint32_t pos = off[blockIdx.x];
   for (int k = 0; k < warp; ++k) pos += wsum[k];
   pos += __popc(b & ((1u << lane) - 1u));
-  if (f) list[pos] = (uint32_t)i;
+  if (f) {
+    list[pos] = (uint32_t)i;
+    if (xf_out) {  // compacted copies for scans over this type only
+      xf_out[pos] = xf[i];
+      key_out[pos] = key[i];
+    }
+  }
 }
 
-// Ordered lists of the sorted indices of fluid and of dummy particles.
-void launch_fluid_list(const State& s, const Work& w, int64_t n, int64_t nd, cudaStream_t st,
-                       int* launches) {
+// Ordered lists of the sorted indices of fluid and of dummy particles. With
+// dummies present, the fluid particles also get compacted positions and keys
+// and their own cell lower bounds: the dummy update scans fluid candidates
+// only (the nearest fluid particle is all it looks for).
+void launch_fluid_list(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int64_t nd,
+                       cudaStream_t st, int* launches) {
   if (n == 0) return;
   int64_t nb = div_up(n, CMP_THREADS);
+  const bool compact = nd > 0 && w.dummy_list;
   k_count_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kFluid, w.block_cnt);
   k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(w.block_cnt, nb);
-  k_write_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kFluid, w.block_cnt, w.fluid_list);
+  k_write_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kFluid, w.block_cnt, w.fluid_list,
+                                                      w.xf, compact ? w.xff : nullptr, w.key, w.fkey);
   *launches += 3;
-  if (nd > 0 && w.dummy_list) {
+  if (compact) {
+    k_cell_lower_bounds<<<(unsigned)div_up(p.ncells + 1, 256), 256, 0, st>>>(w.fkey, nf, p.ncells, w.fcell_lb);
     k_count_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kDummy, w.block_cnt);
     k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(w.block_cnt, nb);
-    k_write_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kDummy, w.block_cnt, w.dummy_list);
-    *launches += 3;
+    k_write_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kDummy, w.block_cnt, w.dummy_list,
+                                                        nullptr, nullptr, nullptr, nullptr);
+    *launches += 4;
   }
 }
 
@@ -421,7 +437,7 @@ __global__ void __launch_bounds__(128) k_count_neighbors(Params p, State s, Work
   const uint32_t key = active ? w.key[i] : 0u;
   const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t c = 0;
-  warp_scan_candidates<DIM>(p, w, active, i, key, xs, stage[warp], sidx[warp], [&](uint32_t j, float, float) {
+  warp_scan_candidates<DIM>(p, all_particles(w), active, i, key, xs, stage[warp], sidx[warp], [&](uint32_t j, float, float) {
     if (exact_neighbor(p, s.x, n, i, j)) ++c;
   });
   if (active) counts[s.oid[i]] = c;
@@ -439,7 +455,7 @@ __global__ void __launch_bounds__(128) k_fill_neighbors(Params p, State s, Work 
   const uint32_t key = active ? w.key[i] : 0u;
   const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   int64_t o = active ? row_ptr[s.oid[i]] : 0;
-  warp_scan_candidates<DIM>(p, w, active, i, key, xs, stage[warp], sidx[warp], [&](uint32_t j, float, float) {
+  warp_scan_candidates<DIM>(p, all_particles(w), active, i, key, xs, stage[warp], sidx[warp], [&](uint32_t j, float, float) {
     if (exact_neighbor(p, s.x, n, i, j)) cols[o++] = (int32_t)s.oid[j];
   });
 }

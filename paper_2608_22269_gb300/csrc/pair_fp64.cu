@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s,
   uint32_t kj[KEEP] = {0u, 0u, 0u, 0u};
   float kr[KEEP] = {INFINITY, INFINITY, INFINITY, INFINITY};  // slot free when > band limit
   bool spill = false;
-  warp_scan_candidates<DIM>(p, w, active, i, key, xs, stage[warp], sidx[warp],
+  warp_scan_candidates<DIM>(p, fluid_particles(w), active, i, key, xs, stage[warp], sidx[warp],
                             [&](uint32_t j, float r2f, float jtype) {
     if (jtype != 0.f) return;  // fluid neighbours only
     if (r2f > best_f + p.nearest_band_r2) return;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s,
       if (kr[q] <= lim) consider(kj[q]);
   }
   if (__any_sync(0xffffffffu, spill)) {
-    warp_scan_candidates<DIM>(p, w, active && spill, i, key, xs, stage[warp], sidx[warp],
+    warp_scan_candidates<DIM>(p, fluid_particles(w), active && spill, i, key, xs, stage[warp], sidx[warp],
                               [&](uint32_t j, float r2f, float jtype) {
       if (jtype == 0.f && r2f <= lim) consider(j);
     });
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_volumes_umax(Params p, State s,
 }
 
 void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int64_t nd,
-                    int stage2, cudaStream_t st) {
+                    int stage2, cudaStream_t st, bool volumes) {
   cudaMemsetAsync(w.umax_bits, 0, sizeof(unsigned long long), st);
   if (n == 0) return;
   if (nd > 0) {
@@ -141,7 +141,7 @@ void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, i
     if (p.dim == 3) k_dummy_update<3><<<blocks, DUM_THREADS, 0, st>>>(p, s, w, n, nd, stage2);
     else k_dummy_update<2><<<blocks, DUM_THREADS, 0, st>>>(p, s, w, n, nd, stage2);
   }
-  k_volumes_umax<<<(unsigned)div_up(n, PRE_THREADS), PRE_THREADS, 0, st>>>(p, s, w, n);
+  if (volumes) k_volumes_umax<<<(unsigned)div_up(n, PRE_THREADS), PRE_THREADS, 0, st>>>(p, s, w, n);
 }
 
 // Time step (Sec. 2.3): CFL * min(dx/(C0 + U_max), dx^2/(2 nu), sqrt(2 dx/|G|)).
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, State s, Wo
   const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   int cnt = 0, nband = 0;
   constexpr uint32_t kBand = 0x80000000u;  // entry still needs the exact test
-  warp_scan_candidates<DIM>(p, w, active, i, key, xs, stage, sidx, [&](uint32_t j, float r2f, float) {
+  warp_scan_candidates<DIM>(p, all_particles(w), active, i, key, xs, stage, sidx, [&](uint32_t j, float r2f, float) {
     // neighbour test of Algorithm 1: FP32 decides inside the inner bound;
     // candidates in the rounding band near 2h (and at r_f = 0) are flagged
     // for the exact FP64 test below

@@ -75,6 +75,17 @@ __device__ __forceinline__ uint32_t flat_candidate(uint32_t q, const uint32_t (&
   return idx;
 }
 
+// Where candidates come from: cell lower bounds `lb` (ncells + 1 entries,
+// the first position with key >= c) over an array of candidates in key
+// order, their FP32 positions `xf` (.w = type) and, when `map` is not null,
+// the sorted particle index of each position (candidates = a compacted
+// subset such as the fluid particles); otherwise the position is the index.
+struct CandSource {
+  const uint32_t* lb;
+  const float4* xf;
+  const uint32_t* map;
+};
+
 // f(j, r2f, type_j) is called for every candidate j != self of the lane's
 // particle with FP32 squared distance r2f <= prefilter_r2 (type_j from the .w
 // component of the FP32 position copy). `stage` holds 32 float4 and `sidx`
@@ -83,12 +94,12 @@ __device__ __forceinline__ uint32_t flat_candidate(uint32_t q, const uint32_t (&
 // 32 lanes must call this function together.
 //
 // Per group the 3^(d-1) row ranges are fetched by one lane each, scanned
-// into one flattened candidate stream (rows in (z, y) order, each in sorted
+// into one flattened candidate stream (rows in (z, y) order, each in key
 // order), and the stream is staged 32 at a time with the next 32 loaded
 // into registers while the current ones are tested: no partially filled
 // batches at row ends, and the gather latency overlaps the tests.
 template <int DIM, class F>
-__device__ __forceinline__ void warp_scan_candidates(const Params& p, const Work& w, bool active,
+__device__ __forceinline__ void warp_scan_candidates(const Params& p, const CandSource& src, bool active,
                                                      uint32_t self, uint32_t key, float4 xs,
                                                      float4* stage, uint32_t* sidx, F&& f) {
   constexpr int NR = DIM == 3 ? 9 : 3;
@@ -123,8 +134,8 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Work
       int cz = DIM == 3 ? gz - 1 + lane / 3 : 0;
       if (cy >= 0 && cy < p.nc[1] && cz >= 0 && cz < p.nc[2]) {
         int64_t base = (int64_t)cy * p.nc[0] + (int64_t)cz * p.nc[0] * p.nc[1];
-        rb = w.cell_lb[base + x0];
-        rl = w.cell_lb[base + x1 + 1] - rb;
+        rb = src.lb[base + x0];
+        rl = src.lb[base + x1 + 1] - rb;
       }
     }
     uint32_t inc = rl;
@@ -141,7 +152,9 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Work
     }
     const uint32_t total = incl[NR - 1];
     uint32_t nidx = flat_candidate<NR>((uint32_t)lane, beg, incl);
-    float4 nxt = (uint32_t)lane < total ? __ldg(&w.xf[nidx]) : far;
+    const bool has0 = (uint32_t)lane < total;
+    float4 nxt = has0 ? __ldg(&src.xf[nidx]) : far;
+    uint32_t nj = (src.map && has0) ? __ldg(&src.map[nidx]) : nidx;
     float* sx = reinterpret_cast<float*>(stage);  // [x 32][y 32][z 32][type 32]
     const unsigned long long px = f32x2_pack(xs.x, xs.x), py = f32x2_pack(xs.y, xs.y),
                              pz = f32x2_pack(xs.z, xs.z);
@@ -151,12 +164,14 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Work
       sx[32 + lane] = nxt.y;
       sx[64 + lane] = nxt.z;
       sx[96 + lane] = nxt.w;
-      sidx[lane] = nidx;
+      sidx[lane] = nj;
       __syncwarp();
       const uint32_t q = c0 + 32 + (uint32_t)lane;
       if (c0 + 32 < total) {
         nidx = flat_candidate<NR>(q, beg, incl);
-        nxt = q < total ? __ldg(&w.xf[nidx]) : far;
+        const bool has = q < total;
+        nxt = has ? __ldg(&src.xf[nidx]) : far;
+        nj = (src.map && has) ? __ldg(&src.map[nidx]) : nidx;
       }
       if (in_g) {
         // independent tests of all 32 staged candidates, then the hits in order
@@ -185,6 +200,14 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Work
       __syncwarp();
     }
   }
+}
+
+// Candidates = all particles in sorted order.
+__device__ __forceinline__ CandSource all_particles(const Work& w) { return CandSource{w.cell_lb, w.xf, nullptr}; }
+
+// Candidates = the fluid particles (compacted in sorted order).
+__device__ __forceinline__ CandSource fluid_particles(const Work& w) {
+  return CandSource{w.fcell_lb, w.xff, w.fluid_list};
 }
 
 }  // namespace wbsph
