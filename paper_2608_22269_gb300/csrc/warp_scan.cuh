@@ -156,8 +156,12 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Cand
     float4 nxt = has0 ? __ldg(&src.xf[nidx]) : far;
     uint32_t nj = (src.map && has0) ? __ldg(&src.map[nidx]) : nidx;
     float* sx = reinterpret_cast<float*>(stage);  // [x 32][y 32][z 32][type 32]
-    const unsigned long long px = f32x2_pack(xs.x, xs.x), py = f32x2_pack(xs.y, xs.y),
-                             pz = f32x2_pack(xs.z, xs.z);
+    // a lane whose own position is not finite tests against -inf: every
+    // candidate then fails, as it would fail an ordered comparison with NaN
+    const bool fin = isfinite(xs.x) && isfinite(xs.y) && isfinite(xs.z);
+    const float qx = fin ? xs.x : -INFINITY, qy = fin ? xs.y : -INFINITY, qz = fin ? xs.z : -INFINITY;
+    const unsigned long long px = f32x2_pack(qx, qx), py = f32x2_pack(qy, qy), pz = f32x2_pack(qz, qz);
+    const unsigned long long pre2 = f32x2_pack(p.prefilter_r2, p.prefilter_r2);
     for (uint32_t c0 = 0; c0 < total; c0 += 32) {
       // slots past the stream hold a point at infinity, which no test passes
       sx[lane] = nxt.x;
@@ -174,20 +178,31 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Cand
         nj = (src.map && has) ? __ldg(&src.map[nidx]) : nidx;
       }
       if (in_g) {
-        // independent tests of all 32 staged candidates, then the hits in order
-        unsigned hits = 0u;
-        const unsigned long long* s2 = reinterpret_cast<const unsigned long long*>(sx);
-#pragma unroll 8
-        for (int k = 0; k < 16; ++k) {
-          unsigned long long dx = f32x2_sub(s2[k], px);
-          unsigned long long dy = f32x2_sub(s2[16 + k], py);
-          unsigned long long dz = f32x2_sub(s2[32 + k], pz);
-          unsigned long long r2 = f32x2_fma(dz, dz, f32x2_fma(dy, dy, f32x2_mul(dx, dx)));
-          float r2a, r2b;
-          f32x2_unpack(r2, r2a, r2b);
-          hits |= (r2a <= p.prefilter_r2 ? 1u : 0u) << (2 * k);
-          hits |= (r2b <= p.prefilter_r2 ? 1u : 0u) << (2 * k + 1);
+        // independent tests of all 32 staged candidates, then the hits in
+        // order. Four candidates per 16-byte broadcast load, two per paired
+        // instruction; candidate k fails r2 <= prefilter_r2 exactly when the
+        // difference prefilter_r2 - r2 is negative (it is never rounded to
+        // zero), so its sign bit is shifted into bit k of the miss mask.
+        unsigned miss = 0u;
+        const ulonglong2* s4 = reinterpret_cast<const ulonglong2*>(sx);
+#pragma unroll
+        for (int g = 7; g >= 0; --g) {
+          const ulonglong2 X = s4[g], Y = s4[8 + g], Z = s4[16 + g];
+          unsigned long long d[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {  // h = 0: candidates 4g, 4g + 1; h = 1: 4g + 2, 4g + 3
+            unsigned long long dx = f32x2_sub(h ? X.y : X.x, px);
+            unsigned long long dy = f32x2_sub(h ? Y.y : Y.x, py);
+            unsigned long long dz = f32x2_sub(h ? Z.y : Z.x, pz);
+            unsigned long long r2 = f32x2_fma(dz, dz, f32x2_fma(dy, dy, f32x2_mul(dx, dx)));
+            d[h] = f32x2_sub(pre2, r2);
+          }
+          miss = __funnelshift_l((unsigned)(d[1] >> 32), miss, 1);
+          miss = __funnelshift_l((unsigned)d[1], miss, 1);
+          miss = __funnelshift_l((unsigned)(d[0] >> 32), miss, 1);
+          miss = __funnelshift_l((unsigned)d[0], miss, 1);
         }
+        unsigned hits = ~miss;
         while (hits) {
           int k = __ffs(hits) - 1;
           hits &= hits - 1u;
