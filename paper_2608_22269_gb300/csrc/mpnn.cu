@@ -465,7 +465,14 @@ __global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restric
 constexpr int TC_ROWS = 128;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TILE_BYTES = TC_ROWS * 128;        // 128 rows x 64 BF16
-constexpr size_t TC_SMEM_BYTES = 1024 + 4 * TC_TILE_BYTES + 3 * 8192 + 2 * 64 * 4 + 64;  // 2 slots, W, biases, barriers
+#ifndef WBSPH_TC_SLOTS
+#define WBSPH_TC_SLOTS 2
+#endif
+// tiles in flight per CTA (operand slots of 2 x 16 KB each)
+constexpr int TC_SLOTS = WBSPH_TC_SLOTS;
+static_assert(TC_SLOTS >= 2 && TC_SLOTS <= 8, "slot count");
+constexpr size_t TC_SMEM_BYTES =
+    1024 + 2 * TC_SLOTS * TC_TILE_BYTES + 3 * 8192 + 2 * 64 * 4 + 128;  // slots, W, biases, barriers
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16,
@@ -498,17 +505,26 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
+// all 64 FP32 columns of this thread's TMEM lane in one load and one wait
+__device__ __forceinline__ void tc_ld64(uint32_t taddr, float v[64]) {
+  uint32_t r[64];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // bounded wait for the mbarrier phase `parity`; false on timeout
@@ -571,16 +587,21 @@ __device__ __forceinline__ float silu_tanh(float z) {
 // of a layer, h' = h + silu([h, a] W1 + b1) W2 + b2 (K = 128: the h tile and
 // the aggregate tile are the two 64-wide K blocks of the first GEMM).
 //
-// Pipeline over the CTA's tiles, two slots s (tile parity), each with its
-// own e tile, sender-projection tile (which then holds silu(z1)), TMEM
-// accumulator (64 columns) and mbarrier. Iteration i runs: epilogue 1 of tile
-// i, MMA2 of tile i issued, MMA1 of tile i+1 issued (its gathers arrived
-// during iteration i-1), epilogue 2 and store of tile i, gathers of tile i+2
-// into slot s. So each tile's GEMMs run while the other tile's epilogues do.
+// Pipeline over the CTA's tiles: TC_SLOTS operand slots (tile i in slot
+// i % TC_SLOTS), each with its own e tile, sender-projection tile (which
+// then holds silu(z1)) and TMA mbarrier, and two TMEM accumulators of 64
+// columns with their MMA mbarriers (tile i in accumulator i % 2). Iteration
+// i runs: epilogue 1 of tile i, MMA2 of tile i issued, MMA1 of tile i+1
+// issued (its loads were issued TC_SLOTS - 1 iterations earlier), epilogue
+// 2 and store of tile i, loads of tile i + TC_SLOTS into tile i's slot. So
+// each tile's GEMMs run while the other tile's epilogues do, and the loads
+// of TC_SLOTS - 1 tiles are in flight.
+// (The explicit minimum of one block lets the compiler keep the edge mode's
+// receiver projections and accumulator values in registers without spills.)
 enum { TC_EDGE = 0, TC_ENC = 1, TC_NODE = 2 };
 
 template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restrict__ e_in, bf16* __restrict__ e_out,
+__global__ void __launch_bounds__(TC_THREADS, 1) k_edge_mlp_tc(const bf16* __restrict__ e_in, bf16* __restrict__ e_out,
                                                            int64_t E, const uint32_t* __restrict__ recv,
                                                            const uint32_t* __restrict__ send,
                                                            const bf16* __restrict__ P, const bf16* __restrict__ w1,
@@ -598,14 +619,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   unsigned char* base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);  // 1024-byte aligned
   // slot s: e (or h) tile at s * 32 KB; sender projections (or aggregates),
   // then silu(z1), at s * 32 KB + 16 KB
-  unsigned char* B1 = base + 4 * TC_TILE_BYTES;  // W1[0:64]^T [n][k]
+  unsigned char* B1 = base + 2 * TC_SLOTS * TC_TILE_BYTES;  // W1[0:64]^T [n][k]
   unsigned char* B2 = B1 + 8192;                 // W2^T [n][k]
   unsigned char* B1b = B2 + 8192;                // W1[64:128]^T [n][k] (node MLP)
   float* b2 = reinterpret_cast<float*>(B1b + 8192);
   float* b1 = b2 + 64;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(b1 + 64);  // MMA completion, one per slot
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(b1 + 64);  // MMA completion, one per accumulator
   uint64_t* lbar = mbar + 2;                               // TMA tile arrival, one per slot
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 4);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(lbar + TC_SLOTS);
   auto Et = [&](int sl) { return base + sl * 2 * TC_TILE_BYTES; };
   auto Pt = [&](int sl) { return base + sl * 2 * TC_TILE_BYTES + TC_TILE_BYTES; };
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -623,7 +644,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     b1[t] = EDGE ? 0.f : b1g[t];  // the edge MLP's b1 rides on the receiver projections
   }
   if (t == 0) {
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 2 + TC_SLOTS; ++k)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + k)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -689,35 +710,39 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
       for (int c = 0; c < 8; ++c) pr[c] = __ldg(prg + c);
     }
   };
-  auto mma1 = [&](int sl) {  // z1 = e W1e (or f W1, or [h, a] W1) into slot sl's accumulator
+  // accumulator ac (TMEM columns 64 ac .. 64 ac + 63) of the tile in slot sl
+  auto mma1 = [&](int sl, int ac) {  // z1 = e W1e (or f W1, or [h, a] W1)
     tc_fence_after();
     const uint64_t dA = tc_desc(smem_u32(Et(sl)));
 #pragma unroll
-    for (int k = 0; k < (ENC ? 1 : 4); ++k) tc_mma(tmem + 64 * sl, dA + 2 * k, dB1 + 2 * k, k > 0);
+    for (int k = 0; k < (ENC ? 1 : 4); ++k) tc_mma(tmem + 64 * ac, dA + 2 * k, dB1 + 2 * k, k > 0);
     if (NODE) {  // second K block: the aggregates
       const uint64_t dA2 = tc_desc(smem_u32(Pt(sl)));
 #pragma unroll
-      for (int k = 0; k < 4; ++k) tc_mma(tmem + 64 * sl, dA2 + 2 * k, dB1b + 2 * k, 1u);
+      for (int k = 0; k < 4; ++k) tc_mma(tmem + 64 * ac, dA2 + 2 * k, dB1b + 2 * k, 1u);
     }
-    tc_commit(smem_u32(mbar + sl));
+    tc_commit(smem_u32(mbar + ac));
   };
-  auto mma2 = [&](int sl) {  // z2 = silu(z1) W2, same columns
+  auto mma2 = [&](int sl, int ac) {  // z2 = silu(z1) W2, same columns
     tc_fence_after();
     const uint64_t dA = tc_desc(smem_u32(Pt(sl)));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) tc_mma(tmem + 64 * sl, dA + 2 * k, dB2 + 2 * k, k > 0);
-    tc_commit(smem_u32(mbar + sl));
+    for (int k = 0; k < 4; ++k) tc_mma(tmem + 64 * ac, dA + 2 * k, dB2 + 2 * k, k > 0);
+    tc_commit(smem_u32(mbar + ac));
   };
-  uint32_t phases = 0u;  // bit b: parity of mbarrier b's next phase (0, 1: MMA; 2, 3: TMA)
-  auto wait_slot = [&](int sl) -> bool {  // bounded; every thread gets the CTA's verdict
-    bool w_ok = mbar_wait(smem_u32(mbar + sl), (phases >> sl) & 1u);
-    phases ^= 1u << sl;
+  // bit b: parity of mbarrier b's next phase (0, 1: MMA per accumulator;
+  // 2 + s: TMA arrival of slot s)
+  uint32_t phases = 0u;
+  auto wait_slot = [&](int ac) -> bool {  // bounded; every thread gets the CTA's verdict
+    bool w_ok = mbar_wait(smem_u32(mbar + ac), (phases >> ac) & 1u);
+    phases ^= 1u << ac;
     return __syncthreads_and(w_ok) != 0;
   };
   // this thread's gathers of slot sl are complete and the slot's TMA tiles
-  // have arrived (bounded wait); followed by a CTA barrier
-  auto wait_loads = [&](int sl, int pending_groups) -> bool {
-    if (pending_groups) cp_async_wait<1>(); else cp_async_wait<0>();
+  // have arrived (bounded wait); followed by a CTA barrier. In the prologue
+  // all TC_SLOTS slots are in flight, later TC_SLOTS - 1 of them.
+  auto wait_loads = [&](int sl, bool prologue) -> bool {
+    if (prologue) cp_async_wait<TC_SLOTS - 1>(); else cp_async_wait<TC_SLOTS - 2>();
     bool w_ok = true;
     if (!ENC) {
       w_ok = mbar_wait(smem_u32(lbar + sl), (phases >> (2 + sl)) & 1u);
@@ -729,41 +754,42 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
   };
 
   int64_t tile = blockIdx.x;
-  // prologue: gathers of the first two tiles, MMA1 of the first
-  issue(tile, 0, index_of(send, tile));
-  issue(tile + stride, 1, index_of(send, tile + stride));
+  // prologue: gathers of the first TC_SLOTS tiles, MMA1 of the first
+#pragma unroll
+  for (int q = 0; q < TC_SLOTS; ++q) issue(tile + q * stride, q, index_of(send, tile + q * stride));
   load_pr(index_of(recv, tile));
-  uint32_t rv_n1 = index_of(recv, tile + stride);      // receiver indices of the next tile
-  uint32_t sd_n2 = index_of(send, tile + 2 * stride);  // sender indices two tiles ahead
+  uint32_t rv_n1 = index_of(recv, tile + stride);                // receiver indices of the next tile
+  uint32_t sd_nx = index_of(send, tile + TC_SLOTS * stride);     // senders of the next tile to gather
   bool ok = true;
   if (tile < ntiles) {
-    ok = wait_loads(0, 1);
-    if (ok && t == 0) mma1(0);
+    ok = wait_loads(0, true);
+    if (ok && t == 0) mma1(0, 0);
   }
 
   for (int it = 0; tile < ntiles; ++it, tile += stride) {
-    const int s = it & 1;
+    const int ac = it & 1;              // accumulator of this tile
+    const int sl = it % TC_SLOTS;       // operand slot of this tile
+    const int sn = (it + 1) % TC_SLOTS; // and of the next one
     const int64_t row0 = tile * TC_ROWS;
-    unsigned char* A = Et(s);
-    unsigned char* PS = Pt(s);
-    if (!wait_slot(s)) { ok = false; break; }  // MMA1 of this tile
+    unsigned char* A = Et(sl);
+    unsigned char* PS = Pt(sl);
+    if (!wait_slot(ac)) { ok = false; break; }  // MMA1 of this tile
     tc_fence_after();
     // ---- silu(z1 + P_recv + P_send) (or + b1) -> PS, in place, BF16 swizzled ----
+    {
+      float va[64];
+      tc_ld64(t_lane + 64 * ac, va);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float v[16];
-      tc_ld16(t_lane + 64 * s + q * 16, v);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = 2 * q + h;
+      for (int c = 0; c < 8; ++c) {
+        const float* v = va + 8 * c;
         uint4 o;
         uint32_t* o32 = reinterpret_cast<uint32_t*>(&o);
         if (!EDGE) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int col = c * 8 + 2 * j;
-            __nv_bfloat162 a2 = __floats2bfloat162_rn(silu_tanh(v[h * 8 + 2 * j] + b1[col]),
-                                                      silu_tanh(v[h * 8 + 2 * j + 1] + b1[col + 1]));
+            __nv_bfloat162 a2 = __floats2bfloat162_rn(silu_tanh(v[2 * j] + b1[col]),
+                                                      silu_tanh(v[2 * j + 1] + b1[col + 1]));
             o32[j] = *reinterpret_cast<uint32_t*>(&a2);
           }
         } else {
@@ -773,8 +799,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             float2 fr = __bfloat1622float2(r2[j]), fs = __bfloat1622float2(s2[j]);
-            __nv_bfloat162 a2 = __floats2bfloat162_rn(silu_tanh(v[h * 8 + 2 * j] + fr.x + fs.x),
-                                                      silu_tanh(v[h * 8 + 2 * j + 1] + fr.y + fs.y));
+            __nv_bfloat162 a2 = __floats2bfloat162_rn(silu_tanh(v[2 * j] + fr.x + fs.x),
+                                                      silu_tanh(v[2 * j + 1] + fr.y + fs.y));
             o32[j] = *reinterpret_cast<uint32_t*>(&a2);
           }
         }
@@ -784,24 +810,23 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
     fence_async_smem();  // silu(z1) is read by the tensor core
     tc_fence_before();
     __syncthreads();
-    if (t == 0) mma2(s);
+    if (t == 0) mma2(sl, ac);
     load_pr(rv_n1);  // next tile's receiver projections
     rv_n1 = index_of(recv, tile + 2 * stride);
-    // ---- MMA1 of the next tile (its gathers were issued an iteration ago) ----
+    // ---- MMA1 of the next tile (its gathers were issued TC_SLOTS - 1 iterations ago) ----
     if (tile + stride < ntiles) {
-      if (!wait_loads(s ^ 1, 0)) { ok = false; break; }
-      if (t == 0) mma1(s ^ 1);
+      if (!wait_loads(sn, false)) { ok = false; break; }
+      if (t == 0) mma1(sn, ac ^ 1);
     }
-    if (!wait_slot(s)) { ok = false; break; }  // MMA2 of this tile
+    if (!wait_slot(ac)) { ok = false; break; }  // MMA2 of this tile
     tc_fence_after();
     // ---- e' = e + z2 + b2, in place into the e tile ----
+    {
+      float va[64];
+      tc_ld64(t_lane + 64 * ac, va);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float v[16];
-      tc_ld16(t_lane + 64 * s + q * 16, v);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = 2 * q + h;
+      for (int c = 0; c < 8; ++c) {
+        const float* v = va + 8 * c;
         uint4 ev = make_uint4(0u, 0u, 0u, 0u);  // residual (none for an encoder)
         if (!ENC) ev = *reinterpret_cast<const uint4*>(A + sw128(t, c));
         const __nv_bfloat162* e2 = reinterpret_cast<const __nv_bfloat162*>(&ev);
@@ -811,8 +836,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
         for (int j = 0; j < 4; ++j) {
           const int col = c * 8 + 2 * j;
           float2 fe = __bfloat1622float2(e2[j]);
-          __nv_bfloat162 a2 = __floats2bfloat162_rn(v[h * 8 + 2 * j] + b2[col] + fe.x,
-                                                    v[h * 8 + 2 * j + 1] + b2[col + 1] + fe.y);
+          __nv_bfloat162 a2 = __floats2bfloat162_rn(v[2 * j] + b2[col] + fe.x,
+                                                    v[2 * j + 1] + b2[col + 1] + fe.y);
           o32[j] = *reinterpret_cast<uint32_t*>(&a2);
         }
         *reinterpret_cast<uint4*>(A + sw128(t, c)) = o;
@@ -834,9 +859,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_edge_mlp_tc(const bf16* __restri
       __syncthreads();
       if (t == 0) tma_store_2d(&tm_out, 0, (int)row0, smem_u32(A));
     }
-    // ---- gathers of the tile after next into this slot (its e and silu(z1) tiles are free) ----
-    issue(tile + 2 * stride, s, sd_n2);
-    sd_n2 = index_of(send, tile + 3 * stride);
+    // ---- gathers of the tile TC_SLOTS ahead into this slot (its e and silu(z1) tiles are free) ----
+    issue(tile + TC_SLOTS * stride, sl, sd_nx);
+    sd_nx = index_of(send, tile + (TC_SLOTS + 1) * stride);
   }
   cp_async_wait<0>();  // gathers issued for tiles past the end
   if (t == 0) tma_store_wait();
@@ -1072,35 +1097,65 @@ __device__ __forceinline__ float d2f_fields(double x) {
   return __uint_as_float((hi & 0x80000000u) | ((e - (1023u - 127u)) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
 }
 
+// Edges and edge features. A warp covers the receivers g0 .. g0 + 31 and
+// the contiguous range of their edges; lane l takes edges l, l + 32, ... of
+// that range, finds its receiver by a binary search over the lanes' row
+// starts, and receives the receiver's data by shuffle: every store of
+// recv, send and the 16-byte feature rows is coalesced.
 __global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, const uint32_t* row_ptr,
                           uint32_t* recv, uint32_t* send, bf16* efeat, const float* node_std) {
-  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gi >= nf) return;
-  uint32_t i = w.fluid_list[gi];
-  int c = (int)w.nbr_cnt[gi];
-  int64_t e = row_ptr[gi];
+  const int lane = threadIdx.x & 31;
+  const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane;
+  if (g0 >= nf) return;  // whole warps leave together
+  const int64_t gl = g0 + lane;
+  const uint32_t start = row_ptr[gl < nf ? gl : nf];  // row_ptr holds nf + 1 entries
+  const uint32_t e_end = __shfl_sync(0xffffffffu, start, 31) +
+                         (g0 + 31 < nf ? w.nbr_cnt[g0 + 31] : 0u);  // end of the last receiver's row
+  const uint32_t e_beg = __shfl_sync(0xffffffffu, start, 0);
   const float inv_h = (float)(1.0 / p.h);
   float inv_su[3] = {0.f, 0.f, 0.f};
   for (int d = 0; d < p.dim; ++d) inv_su[d] = 1.f / node_std[d];
   const float inv_sphi = 1.f / node_std[p.dim + 1];
-  // relative positions from the FP32 position copy (BF16 features need no
-  // FP64 difference), velocities and potentials narrowed on the fields
-  const float4 xi = w.xf[i];
-  float ui[3] = {0.f, 0.f, 0.f};
-  for (int d = 0; d < p.dim; ++d) ui[d] = d2f_fields(s.u[d * n + i]);
-  const float phii = d2f_fields(s.phi[i]);
-  for (int k = 0; k < c; ++k) {
-    uint32_t j = w.nbr[(int64_t)k * nf + gi];  // every list entry is an exact neighbour
+  // this lane's receiver: FP32 position, velocity and potential narrowed on
+  // the IEEE fields (BF16 features need no FP64 arithmetic)
+  uint32_t i_l = 0u;
+  float4 x_l = make_float4(0.f, 0.f, 0.f, 0.f);
+  float u_l[3] = {0.f, 0.f, 0.f}, phi_l = 0.f;
+  if (gl < nf) {
+    i_l = w.fluid_list[gl];
+    x_l = w.xf[i_l];
+    for (int d = 0; d < p.dim; ++d) u_l[d] = d2f_fields(s.u[d * n + i_l]);
+    phi_l = d2f_fields(s.phi[i_l]);
+  }
+  for (uint32_t e0 = e_beg; e0 < e_end; e0 += 32) {
+    const uint32_t e = e0 + (uint32_t)lane;
+    // receiver lane r: the last lane whose row starts at or before e
+    int r = 0;
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {
+      const uint32_t st_c = __shfl_sync(0xffffffffu, start, r + step);
+      if (r + step < 32 && g0 + r + step < nf && st_c <= e) r += step;
+    }
+    const uint32_t i = __shfl_sync(0xffffffffu, i_l, r);
+    const float xi = __shfl_sync(0xffffffffu, x_l.x, r), yi = __shfl_sync(0xffffffffu, x_l.y, r),
+                zi = __shfl_sync(0xffffffffu, x_l.z, r);
+    float ui[3];
+    for (int d = 0; d < 3; ++d) ui[d] = __shfl_sync(0xffffffffu, u_l[d], r);
+    const float phii = __shfl_sync(0xffffffffu, phi_l, r);
+    const uint32_t st_r = __shfl_sync(0xffffffffu, start, r);
+    if (e >= e_end) continue;
+    const uint32_t k = e - st_r;
+    const uint32_t j = w.nbr[(int64_t)k * nf + g0 + r];  // every list entry is an exact neighbour
     const float4 xj = __ldg(&w.xf[j]);
-    const float r[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
+    const float rv[3] = {xj.x - xi, xj.y - yi, xj.z - zi};
     recv[e] = i;
     send[e] = j;
     // features (r/h, |r|/h, dU/s_U, dphi/s_phi), zero padded to 8, one 16-byte store
     float f[FEAT] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float r2 = 0.f;
     for (int d = 0; d < p.dim; ++d) {
-      f[d] = r[d] * inv_h;
-      r2 = fmaf(r[d], r[d], r2);
+      f[d] = rv[d] * inv_h;
+      r2 = fmaf(rv[d], rv[d], r2);
       f[p.dim + 1 + d] = (d2f_fields(s.u[d * n + j]) - ui[d]) * inv_su[d];
     }
     f[p.dim] = sqrtf(r2) * inv_h;
@@ -1110,8 +1165,7 @@ __global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, cons
     v.y = pack2(__float2bfloat16(f[2]), __float2bfloat16(f[3]));
     v.z = pack2(__float2bfloat16(f[4]), __float2bfloat16(f[5]));
     v.w = pack2(__float2bfloat16(f[6]), __float2bfloat16(f[7]));
-    *reinterpret_cast<uint4*>(efeat + e * FEAT) = v;
-    ++e;
+    *reinterpret_cast<uint4*>(efeat + (int64_t)e * FEAT) = v;
   }
 }
 
@@ -1408,12 +1462,20 @@ template <int MODE>
 bool launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, const uint32_t* send,
                const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
   if (rows <= 0) return true;
-  static int sms = 0;
+  static int sms = 0, per_sm = 1;
   if (!sms) {
-    int dev = 0;
+    int dev = 0, smem_sm = 0, reserved = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     cudaFuncSetAttribute(k_edge_mlp_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES);
+    // all of the unified L1/shared storage as shared memory; the persistent
+    // grid holds as many CTAs per SM as their shared memory allows (two with
+    // two slots), at most four (their TMEM columns then fill the 512)
+    cudaFuncSetAttribute(k_edge_mlp_tc<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    per_sm = smem_sm > 0 ? smem_sm / (int)(TC_SMEM_BYTES + (size_t)reserved) : 1;
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
     if (sms <= 0) sms = 152;
   }
   CUtensorMap ma, mb, mo;
@@ -1425,7 +1487,7 @@ bool launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, co
     if (MODE == TC_NODE && !rows_map(&mb, P, rows)) return false;
   }
   int64_t tiles = div_up(rows, TC_ROWS);
-  int grid = (int)(tiles < 2 * sms ? tiles : 2 * sms);
+  int grid = (int)(tiles < (int64_t)per_sm * sms ? tiles : (int64_t)per_sm * sms);
   k_edge_mlp_tc<MODE><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(in, out, rows, recv, send, P, blk.w1, blk.kin,
                                                                blk.b1, blk.w2, blk.b2, status, ma, mb, mo);
   return true;
