@@ -1,248 +1,17 @@
-// pair_fp64.cu -- FP64 stage kernels of the well-balanced WCSPH step:
-// prepass (dummy wall update, volumes, U_max), time step, neighbour-list
-// build, the fused FP64 pair pass with its epilogue (Eq. sph with TIC,
-// viscosity, delta-SPH and shifting), the SSP-RK2 stage updates, and field
-// output in the caller's order.
+// pair_fp64.cu -- the fused FP64 pair pass of the well-balanced WCSPH step
+// and its epilogue (Eq. sph with TIC, viscosity, delta-SPH and shifting),
+// and lambda_min of the stored renormalisation matrices.
 //
 // On GB300 the FP64 pipe (2 DFMA per clock per SM, 1/61 of FP32) bounds this
 // path. Candidate enumeration of the 3^d cells is therefore done by a
-// separate FP32/integer kernel that writes each fluid particle's candidate
-// list (k-major, coalesced); the FP64 kernel then walks these lists with
-// every lane busy and no shared memory, so more warps per SM cover the
-// latency of the gathers and of the FP64 pipe itself.
+// separate FP32/integer kernel that writes each fluid particle's neighbour
+// list (k-major, coalesced; lists.cu); the FP64 kernel then walks these
+// lists with every lane busy and no shared memory, so more warps per SM
+// cover the latency of the gathers and of the FP64 pipe itself.
 #include "common.cuh"
-#include "neighbor_iter.cuh"
 #include "physics.cuh"
-#include "warp_scan.cuh"
 
 namespace wbsph {
-
-// ---------------------------------------------------------------------------
-// Prepass. (1) Dummy particles (Sec. 2.4), one lane per dummy: nearest fluid
-// particle f within 2h (exact FP64 squared distance; ties to the smaller
-// original id), phi_d = phi_f + G(t).(x_d - x_f) (Eq. phiBn), slip velocity
-// U_d = U_f - (U_f.n_d) n_d. A warp-staged FP32 scan evaluates the exact
-// FP64 distance only for candidates within a proven rounding band of the
-// running FP32 minimum. (2) V = m / rho(phi) for
-// every particle and max |U|^2 over fluid particles.
-// ---------------------------------------------------------------------------
-constexpr int DUM_THREADS = 128;
-
-template <int DIM>
-__global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s, Work w, int64_t n,
-                                                             int64_t nd, int stage2) {
-  __shared__ float4 stage[DUM_THREADS / 32][32];
-  __shared__ uint32_t sidx[DUM_THREADS / 32][32];
-  const int warp = threadIdx.x >> 5;
-  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool active = gi < nd;
-  const uint32_t i = active ? w.dummy_list[gi] : 0u;
-  const uint32_t key = active ? w.key[i] : 0u;
-  const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  // One FP32 scan keeps the (at most 4) fluid candidates whose FP32 distance
-  // lies within the rounding band of the running FP32 minimum; the exact
-  // FP64 distances decide among those left within the band of the final
-  // minimum. A candidate dropped at any point lies outside the band of the
-  // final minimum too, so it cannot be the exact nearest. If more than 4
-  // candidates share the band, a second scan evaluates all of them exactly.
-  constexpr int KEEP = 4;
-  float best_f = INFINITY;
-  uint32_t kj[KEEP] = {0u, 0u, 0u, 0u};
-  float kr[KEEP] = {INFINITY, INFINITY, INFINITY, INFINITY};  // slot free when > band limit
-  bool spill = false;
-  warp_scan_candidates<DIM>(p, fluid_particles(w), active, i, key, xs, stage[warp], sidx[warp],
-                            [&](uint32_t j, float r2f, float jtype) {
-    if (jtype != 0.f) return;  // fluid neighbours only
-    if (r2f > best_f + p.nearest_band_r2) return;
-    best_f = fminf(best_f, r2f);
-    const float lim_now = best_f + p.nearest_band_r2;
-    bool placed = false;
-#pragma unroll
-    for (int q = 0; q < KEEP; ++q)
-      if (!placed && kr[q] > lim_now) { kr[q] = r2f; kj[q] = j; placed = true; }
-    spill |= !placed;
-  });
-  uint32_t best = kEmpty, best_oid = kEmpty;
-  double best_r2 = 0.0;
-  auto consider = [&](uint32_t j) {
-    double d0 = __dsub_rn(s.x[j], s.x[i]);
-    double r2 = __dmul_rn(d0, d0);
-    double d1 = __dsub_rn(s.x[n + j], s.x[n + i]);
-    r2 = __dadd_rn(r2, __dmul_rn(d1, d1));
-    if (p.dim == 3) {
-      double d2 = __dsub_rn(s.x[2 * n + j], s.x[2 * n + i]);
-      r2 = __dadd_rn(r2, __dmul_rn(d2, d2));
-    }
-    if (!(r2 <= p.four_h2 && r2 > 0.0)) return;
-    uint32_t o = s.oid[j];
-    if (best == kEmpty || r2 < best_r2 || (r2 == best_r2 && o < best_oid)) {
-      best = j; best_r2 = r2; best_oid = o;
-    }
-  };
-  const float lim = best_f + p.nearest_band_r2;
-  if (!spill && best_f < INFINITY) {  // empty slots hold r = inf and no index
-#pragma unroll
-    for (int q = 0; q < KEEP; ++q)
-      if (kr[q] <= lim) consider(kj[q]);
-  }
-  if (__any_sync(0xffffffffu, spill)) {
-    warp_scan_candidates<DIM>(p, fluid_particles(w), active && spill, i, key, xs, stage[warp], sidx[warp],
-                              [&](uint32_t j, float r2f, float jtype) {
-      if (jtype == 0.f && r2f <= lim) consider(j);
-    });
-  }
-  if (!active || best == kEmpty) return;
-  double fs = forcing_factor(p, stage_time(w, stage2));
-  double gdot = 0.0, un = 0.0;
-  for (int k = 0; k < p.dim; ++k) {
-    gdot += (p.g[k] + p.force_amp[k] * fs) * (s.x[k * n + i] - s.x[k * n + best]);
-    un += s.u[k * n + best] * s.normal[k * n + i];
-  }
-  s.phi[i] = s.phi[best] + gdot;
-  for (int k = 0; k < p.dim; ++k) s.u[k * n + i] = s.u[k * n + best] - un * s.normal[k * n + i];
-}
-
-constexpr int PRE_THREADS = 256;
-
-__global__ void __launch_bounds__(PRE_THREADS) k_volumes_umax(Params p, State s, Work w, int64_t n) {
-  __shared__ unsigned long long red[PRE_THREADS / 32];
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double umax2 = 0.0;
-  if (i < n) {
-    if (s.type[i] == kFluid)
-      for (int k = 0; k < p.dim; ++k) umax2 += s.u[k * n + i] * s.u[k * n + i];
-    double v = s.mass[i] / eos_density(p, s.phi[i]);
-    w.vol[i] = v;
-    w.volc[i] = p.neg_dwdr_over_r_coef * v;  // -W'(r)/r V = volc (1 - q/2)^3
-    if (!isfinite(v)) atomicOr(w.status, kStatNaN);
-  }
-  // block max of |U|^2, then one atomic per block on the bit pattern
-  // (non-negative doubles order like their unsigned 64-bit patterns)
-  unsigned long long b = __double_as_longlong(umax2);
-  for (int off = 16; off; off >>= 1) {
-    unsigned long long o = __shfl_xor_sync(0xffffffffu, b, off);
-    b = o > b ? o : b;
-  }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long m = 0;
-    for (int k = 0; k < PRE_THREADS / 32; ++k) m = red[k] > m ? red[k] : m;
-    if (m) atomicMax(w.umax_bits, m);
-  }
-}
-
-void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int64_t nd,
-                    int stage2, cudaStream_t st, bool volumes) {
-  cudaMemsetAsync(w.umax_bits, 0, sizeof(unsigned long long), st);
-  if (n == 0) return;
-  if (nd > 0) {
-    unsigned blocks = (unsigned)div_up(nd, DUM_THREADS);
-    if (p.dim == 3) k_dummy_update<3><<<blocks, DUM_THREADS, 0, st>>>(p, s, w, n, nd, stage2);
-    else k_dummy_update<2><<<blocks, DUM_THREADS, 0, st>>>(p, s, w, n, nd, stage2);
-  }
-  if (volumes) k_volumes_umax<<<(unsigned)div_up(n, PRE_THREADS), PRE_THREADS, 0, st>>>(p, s, w, n);
-}
-
-// Time step (Sec. 2.3): CFL * min(dx/(C0 + U_max), dx^2/(2 nu), sqrt(2 dx/|G|)).
-__global__ void k_time_step(Params p, Work w) {
-  double umax = sqrt(__longlong_as_double((long long)*w.umax_bits));
-  double dt;
-  if (p.fixed_dt > 0) {
-    dt = p.fixed_dt;
-  } else {
-    double t = p.dx / (p.c0 + umax);
-    if (p.nu > 0) {
-      double td = p.dx * p.dx / (2.0 * p.nu);
-      if (td < t) t = td;
-    }
-    double g2 = 0.0;
-    for (int k = 0; k < p.dim; ++k) g2 += p.g[k] * p.g[k];
-    if (g2 > 0) {
-      double tg = sqrt(2.0 * p.dx / sqrt(g2));
-      if (tg < t) t = tg;
-    }
-    dt = p.cfl * t;
-  }
-  w.scalars[1] = dt;
-}
-
-void launch_time_step(const Params& p, const Work& w, cudaStream_t st) {
-  k_time_step<<<1, 1, 0, st>>>(p, w);
-}
-
-// ---------------------------------------------------------------------------
-// Neighbour lists: for fluid particle gi (sorted index fluid_list[gi]), in
-// Algorithm 1 order, stored k-major: nbr[k * nf + gi].
-//  EXACT (FP64 path, surrogate graph): every j != i with exact r <= 2h
-//    (Algorithm 1's test). The FP32 distance of the warp scan decides for
-//    candidates inside the inner bound; the rest of the candidates that pass
-//    the conservative prefilter (a thin band near 2h) take the exact FP64 test.
-//  otherwise (mixed path): every candidate that passes the FP32 prefilter;
-//    the mixed pair pass applies its own FP32 test.
-// Lists are staged per warp in shared memory so the global stores are
-// coalesced rows.
-// ---------------------------------------------------------------------------
-constexpr int LIST_THREADS = 64;
-
-template <int DIM, bool EXACT>
-__global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, State s, Work w, int64_t n, int64_t nf,
-                                                         int kmax, int ks) {
-  extern __shared__ float4 smem_f4[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4* stage = smem_f4 + warp * 32;
-  uint32_t* sidx = reinterpret_cast<uint32_t*>(smem_f4 + (LIST_THREADS / 32) * 32) + warp * 32;
-  uint32_t* my = reinterpret_cast<uint32_t*>(smem_f4 + (LIST_THREADS / 32) * 32) + LIST_THREADS +
-                 warp * ks * 32;
-  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool active = gi < nf;
-  const uint32_t i = active ? w.fluid_list[gi] : 0u;
-  const uint32_t key = active ? w.key[i] : 0u;
-  const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  int cnt = 0, nband = 0;
-  constexpr uint32_t kBand = 0x80000000u;  // entry still needs the exact test
-  warp_scan_candidates<DIM>(p, all_particles(w), active, i, key, xs, stage, sidx, [&](uint32_t j, float r2f, float) {
-    // neighbour test of Algorithm 1: FP32 decides inside the inner bound;
-    // candidates in the rounding band near 2h (and at r_f = 0) are flagged
-    // for the exact FP64 test below
-    const bool band = EXACT && !(r2f > 0.f && r2f <= p.inner_r2);
-    nband += band ? 1 : 0;
-    const uint32_t v = j | (band ? kBand : 0u);
-    // the first ks entries are staged; the rare ones beyond go straight out
-    if (cnt < ks) my[cnt * 32 + lane] = v;
-    else if (cnt < kmax) w.nbr[(int64_t)cnt * nf + gi] = v;
-    ++cnt;
-  });
-  if (EXACT && nband > 0) {  // rare: exact test of the flagged entries, compacting in order
-    const int m = cnt < kmax ? cnt : kmax;
-    int kept = 0;
-    for (int k = 0; k < m; ++k) {
-      uint32_t v = k < ks ? my[k * 32 + lane] : w.nbr[(int64_t)k * nf + gi];
-      if (v & kBand) {
-        v &= ~kBand;
-        if (!exact_neighbor(p, s.x, n, i, v)) continue;
-      }
-      if (kept < ks) my[kept * 32 + lane] = v;
-      else w.nbr[(int64_t)kept * nf + gi] = v;
-      ++kept;
-    }
-    if (cnt > kmax) atomicOr(w.status, kStatOverflow);
-    cnt = kept;
-  }
-  if (active) {
-    if (cnt > kmax) {
-      atomicOr(w.status, kStatOverflow);
-      cnt = kmax;
-    }
-    w.nbr_cnt[gi] = (uint32_t)cnt;
-  }
-  __syncwarp();
-  const int staged = cnt < ks ? cnt : ks;
-  int maxc = __reduce_max_sync(0xffffffffu, staged);
-  for (int k = 0; k < maxc; ++k)
-    if (k < staged) w.nbr[(int64_t)k * nf + gi] = my[k * 32 + lane];
-}
-
 // ---------------------------------------------------------------------------
 // Fused FP64 pair pass over fluid particles (one lane per particle i).
 // Accumulated with g = -W'(r)/r V_j >= 0, so grad_i W_ij V_j = g r (r = x_j - x_i):
@@ -459,131 +228,12 @@ void launch_lambda_fp64(const Params& p, const Work& w, int64_t n, int64_t nf, c
   k_lambda_fp64<<<(unsigned)div_up(nf, 256), 256, 0, st>>>(p, w, n, nf);
 }
 
-int pair_list_kmax(int dim) { return dim == 3 ? 128 : 48; }
-
-// List entries per lane staged in shared memory (the rest are stored
-// directly, uncoalesced): 80 holds the candidates of most particles of 3D
-// lattices at h = 1.3 dx (about 75) and leaves room for 20 resident warps
-// per SM, which this latency-bound kernel needs more than coalesced stores
-// of the few entries beyond.
-#ifndef WBSPH_LIST_STAGE_3D
-#define WBSPH_LIST_STAGE_3D 80
-#endif
-static int pair_list_stage(int dim) { return dim == 3 ? WBSPH_LIST_STAGE_3D : 48; }
-
-void launch_nbr_list(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, cudaStream_t st,
-                     bool exact) {
-  if (nf == 0) return;
-  int kmax = pair_list_kmax(p.dim);
-  int ks = pair_list_stage(p.dim);
-  if (ks > kmax) ks = kmax;
-  size_t sm = (size_t)ks * 32 * (LIST_THREADS / 32) * sizeof(uint32_t) +
-              (LIST_THREADS / 32) * 32 * (sizeof(float4) + sizeof(uint32_t));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_nbr_list<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_nbr_list<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_nbr_list<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_nbr_list<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    attr = true;
-  }
-  unsigned blocks = (unsigned)div_up(nf, LIST_THREADS);
-  if (p.dim == 3) {
-    if (exact) k_nbr_list<3, true><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
-    else k_nbr_list<3, false><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
-  } else {
-    if (exact) k_nbr_list<2, true><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
-    else k_nbr_list<2, false><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
-  }
-}
-
 void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
                       int stage2, cudaStream_t st) {
   if (nf == 0) return;
   unsigned blocks = (unsigned)div_up(nf, PAIR_THREADS);
   if (p.dim == 2) k_pair_fp64<2><<<blocks, PAIR_THREADS, 0, st>>>(p, s, w, n, nf, stage2);
   else k_pair_fp64<3><<<blocks, PAIR_THREADS, 0, st>>>(p, s, w, n, nf, stage2);
-}
-
-// ---------------------------------------------------------------------------
-// SSP-RK2 stages (Sec. 2.3), fluid particles; dummies stay fixed.
-//   stage 1: y0 = y;  y = y0 + dt F(y0);  x = x0 + dt (U0 + dU0)
-//   stage 2: y = y0/2 + (y1 + dt F(y1))/2; x = x0/2 + (x1 + dt (U1 + dU1))/2
-// Stage 2 also advances t by dt (one thread, after every reader of t).
-// ---------------------------------------------------------------------------
-__global__ void k_rk_stage(Params p, State s, Work w, int64_t n, int stage) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double dt = w.scalars[1];
-  if (stage == 2 && i == 0) w.scalars[0] = w.scalars[0] + dt;
-  if (i >= n) return;
-  bool fluid = s.type[i] == kFluid;
-  if (stage == 1) {
-    for (int k = 0; k < p.dim; ++k) {
-      double x0 = s.x[k * n + i], u0 = s.u[k * n + i];
-      s.x0[k * n + i] = x0;
-      s.u0[k * n + i] = u0;
-      if (fluid) {
-        s.x[k * n + i] = x0 + dt * (u0 + w.dushift[k * n + i]);
-        s.u[k * n + i] = u0 + dt * w.dudt[k * n + i];
-      }
-    }
-    double ph0 = s.phi[i];
-    s.phi0[i] = ph0;
-    if (fluid) s.phi[i] = ph0 + dt * w.dphidt[i];
-  } else if (fluid) {
-    for (int k = 0; k < p.dim; ++k) {
-      double x1 = s.x[k * n + i], u1 = s.u[k * n + i];
-      s.x[k * n + i] = 0.5 * s.x0[k * n + i] + 0.5 * (x1 + dt * (u1 + w.dushift[k * n + i]));
-      s.u[k * n + i] = 0.5 * s.u0[k * n + i] + 0.5 * (u1 + dt * w.dudt[k * n + i]);
-    }
-    s.phi[i] = 0.5 * s.phi0[i] + 0.5 * (s.phi[i] + dt * w.dphidt[i]);
-  }
-}
-
-void launch_rk_stage(const Params& p, const State& s, const Work& w, int64_t n, int stage,
-                     cudaStream_t st) {
-  k_rk_stage<<<(unsigned)div_up(n > 0 ? n : 1, 256), 256, 0, st>>>(p, s, w, n, stage);
-}
-
-// ---------------------------------------------------------------------------
-// Field output in original order: out[k n + oid[i]] = field[k n + i].
-// ---------------------------------------------------------------------------
-__global__ void k_field(Params p, State s, Work w, int64_t n, int field, double* out) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t o = s.oid[i];
-  const double* src = nullptr;
-  int comps = 1;
-  switch (field) {
-    case 0: src = s.x; comps = p.dim; break;
-    case 1: src = s.u; comps = p.dim; break;
-    case 2: src = s.phi; break;
-    case 5: src = w.dudt; comps = p.dim; break;
-    case 6: src = w.dphidt; break;
-    case 7: src = w.dushift; comps = p.dim; break;
-    case 8: src = w.lambda; break;
-    case 9: src = s.mass; break;
-    case 10: src = w.vol; break;
-    default: break;
-  }
-  if (field == 3 || field == 4) {
-    double rho = eos_density(p, s.phi[i]);
-    double v = rho;
-    if (field == 4) {
-      v = p.eos == 0 ? p.c0sq * (rho - p.rho0)
-                     : p.rho0 * p.c0sq / p.gamma * (pow(rho / p.rho0, p.gamma) - 1.0);
-    }
-    out[o] = v;
-    return;
-  }
-  if (!src) return;
-  for (int k = 0; k < comps; ++k) out[k * n + o] = src[k * n + i];
-}
-
-void launch_field(const Params& p, const State& s, const Work& w, int64_t n, int field,
-                  double* out, cudaStream_t st) {
-  if (n == 0) return;
-  k_field<<<(unsigned)div_up(n, 256), 256, 0, st>>>(p, s, w, n, field, out);
 }
 
 }  // namespace wbsph

@@ -34,91 +34,6 @@ struct Kahan {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// FP32 value of a finite double, rounded to nearest (ties away from zero) on
-// its IEEE fields with integer instructions, so that the FP64 pipe only
-// does the arithmetic that needs it; magnitudes below 2^-126 give zero.
-__device__ __forceinline__ float mx_d2f(double x) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  b = (b & 0x7FFFFFFFFFFFFFFFull) + (1ull << 28);  // half of the 29 dropped bits; a carry renormalises
-  const unsigned e = (unsigned)(b >> 52);
-  if (e <= 1023u - 127u) return 0.f;
-  return __uint_as_float(sign | ((e - (1023u - 127u)) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
-}
-
-// exponent field of a double is all ones: infinity or NaN
-__device__ __forceinline__ bool mx_nonfinite(double x) {
-  return ((unsigned)__double2hiint(x) & 0x7FF00000u) == 0x7FF00000u;
-}
-
-// ---- prepass of the mixed path, per particle (after the dummy update) ----
-// U_max^2 over fluid particles (FP64, for the time step and shifting); the
-// volume V = m / rho(phi) in FP32 (it only enters the FP32 pair sums); and the
-// packed FP32 copies read by the pair pass:
-//   A[i] = (x - cell origin, phi - phi_hs(x)), B[i] = (U, V) with V < 0 marking
-//   dummy particles (the Laplacian operator takes fluid neighbours only),
-//   C[i] = cell coordinates packed 11/11/10 bits.
-// w.vol receives V widened to FP64.
-constexpr int MXP_THREADS = 256;
-
-__global__ void __launch_bounds__(MXP_THREADS) k_prepass_mixed(Params p, State s, Work w, int64_t n, float4* A,
-                                                               float4* B, uint32_t* Cc) {
-  __shared__ unsigned long long red[MXP_THREADS / 32];
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double umax2 = 0.0;
-  if (i < n) {
-    const bool fluid = s.type[i] == kFluid;
-    const uint32_t key = w.key[i];
-    const uint32_t nx = (uint32_t)p.nc[0], ny = (uint32_t)p.nc[1];
-    const uint32_t ic[3] = {key % nx, (key / nx) % ny, key / (nx * ny)};
-    float o[3] = {0.f, 0.f, 0.f};
-    float u[3] = {0.f, 0.f, 0.f};
-    double phs = p.phs0;
-    bool bad = false;
-    for (int k = 0; k < p.dim; ++k) {
-      const double xk = s.x[k * n + i], uk = s.u[k * n + i];
-      bad |= mx_nonfinite(xk) | mx_nonfinite(uk);
-      o[k] = mx_d2f(xk - (p.domain_min[k] + (double)ic[k] * p.R));
-      u[k] = mx_d2f(uk);
-      if (fluid) umax2 = fma(uk, uk, umax2);
-      if (p.g[k] != 0.0) phs = fma(p.g[k], xk, phs);
-    }
-    const double phi = s.phi[i];
-    bad |= mx_nonfinite(phi);
-    const float phif = mx_d2f(phi);
-    // rho / rho0 = exp(phi / C0^2) (linear EOS) or (1 + (gamma-1) phi / c0^2)^(1/(gamma-1)) (Tait)
-    const float inv_c0sq = (float)(1.0 / p.c0sq);
-    float inv_rel;
-    if (p.eos == 0) {
-      inv_rel = expf(-phif * inv_c0sq);
-    } else {
-      const float gm1 = (float)(p.gamma - 1.0);
-      inv_rel = powf(fmaf(gm1 * phif, inv_c0sq, 1.f), -1.f / gm1);
-    }
-    float v = mx_d2f(s.mass[i]) * (float)(1.0 / p.rho0) * inv_rel;
-    bad |= !isfinite(v);
-    if (bad) atomicOr(w.status, kStatNaN);
-    w.vol[i] = (double)v;
-    A[i] = make_float4(o[0], o[1], o[2], mx_d2f(phi - phs));
-    B[i] = make_float4(u[0], u[1], u[2], fluid ? v : -v);
-    Cc[i] = ic[0] | (ic[1] << 11) | (ic[2] << 22);
-  }
-  // block max of |U|^2, one atomic per block on the bit pattern
-  unsigned long long b = (unsigned long long)__double_as_longlong(umax2);
-  for (int off = 16; off; off >>= 1) {
-    unsigned long long q = __shfl_xor_sync(0xffffffffu, b, off);
-    b = q > b ? q : b;
-  }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long m = 0;
-    for (int k = 0; k < MXP_THREADS / 32; ++k) m = red[k] > m ? red[k] : m;
-    if (m) atomicMax(w.umax_bits, m);
-  }
-}
-
-
 constexpr int MX_THREADS = 128;
 #ifndef WBSPH_MX_MIN_BLOCKS
 #define WBSPH_MX_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for
@@ -387,16 +302,6 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
   if (bad) atomicOr(w.status, kStatNaN);
 }
 
-
-// Mixed prepass (after the dummy update, which resets U_max); fails when the
-// grid is too large for the packed cell coordinates (11/11/10 bits).
-int launch_prepass_mixed(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st) {
-  if (n == 0) return 0;
-  if (p.nc[0] > 2048 || p.nc[1] > 2048 || p.nc[2] > 1024) return WBSPH_E_INVAL;
-  k_prepass_mixed<<<(unsigned)div_up(n, MXP_THREADS), MXP_THREADS, 0, st>>>(p, s, w, n, w.packA, w.packB,
-                                                                            w.packC);
-  return 0;
-}
 
 // Pair sums over the candidate lists of k_nbr_list (built before this).
 void launch_pair_mixed(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,

@@ -1,0 +1,259 @@
+// prepass.cu -- per-stage work before the pair pass: the dummy wall update
+// (Sec. 2.4), particle volumes and U_max, the time step (Sec. 2.3), and the
+// packed FP32 copies of the mixed path.
+#include "../../include/wbsph.h"
+#include "common.cuh"
+#include "neighbor_iter.cuh"
+#include "physics.cuh"
+#include "warp_scan.cuh"
+
+namespace wbsph {
+// ---------------------------------------------------------------------------
+// Prepass. (1) Dummy particles (Sec. 2.4), one lane per dummy: nearest fluid
+// particle f within 2h (exact FP64 squared distance; ties to the smaller
+// original id), phi_d = phi_f + G(t).(x_d - x_f) (Eq. phiBn), slip velocity
+// U_d = U_f - (U_f.n_d) n_d. A warp-staged FP32 scan evaluates the exact
+// FP64 distance only for candidates within a proven rounding band of the
+// running FP32 minimum. (2) V = m / rho(phi) for
+// every particle and max |U|^2 over fluid particles.
+// ---------------------------------------------------------------------------
+constexpr int DUM_THREADS = 128;
+
+template <int DIM>
+__global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s, Work w, int64_t n,
+                                                             int64_t nd, int stage2) {
+  __shared__ float4 stage[DUM_THREADS / 32][32];
+  __shared__ uint32_t sidx[DUM_THREADS / 32][32];
+  const int warp = threadIdx.x >> 5;
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool active = gi < nd;
+  const uint32_t i = active ? w.dummy_list[gi] : 0u;
+  const uint32_t key = active ? w.key[i] : 0u;
+  const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  // One FP32 scan keeps the (at most 4) fluid candidates whose FP32 distance
+  // lies within the rounding band of the running FP32 minimum; the exact
+  // FP64 distances decide among those left within the band of the final
+  // minimum. A candidate dropped at any point lies outside the band of the
+  // final minimum too, so it cannot be the exact nearest. If more than 4
+  // candidates share the band, a second scan evaluates all of them exactly.
+  constexpr int KEEP = 4;
+  float best_f = INFINITY;
+  uint32_t kj[KEEP] = {0u, 0u, 0u, 0u};
+  float kr[KEEP] = {INFINITY, INFINITY, INFINITY, INFINITY};  // slot free when > band limit
+  bool spill = false;
+  warp_scan_candidates<DIM>(p, fluid_particles(w), active, i, key, xs, stage[warp], sidx[warp],
+                            [&](uint32_t j, float r2f, float jtype) {
+    if (jtype != 0.f) return;  // fluid neighbours only
+    if (r2f > best_f + p.nearest_band_r2) return;
+    best_f = fminf(best_f, r2f);
+    const float lim_now = best_f + p.nearest_band_r2;
+    bool placed = false;
+#pragma unroll
+    for (int q = 0; q < KEEP; ++q)
+      if (!placed && kr[q] > lim_now) { kr[q] = r2f; kj[q] = j; placed = true; }
+    spill |= !placed;
+  });
+  uint32_t best = kEmpty, best_oid = kEmpty;
+  double best_r2 = 0.0;
+  auto consider = [&](uint32_t j) {
+    double d0 = __dsub_rn(s.x[j], s.x[i]);
+    double r2 = __dmul_rn(d0, d0);
+    double d1 = __dsub_rn(s.x[n + j], s.x[n + i]);
+    r2 = __dadd_rn(r2, __dmul_rn(d1, d1));
+    if (p.dim == 3) {
+      double d2 = __dsub_rn(s.x[2 * n + j], s.x[2 * n + i]);
+      r2 = __dadd_rn(r2, __dmul_rn(d2, d2));
+    }
+    if (!(r2 <= p.four_h2 && r2 > 0.0)) return;
+    uint32_t o = s.oid[j];
+    if (best == kEmpty || r2 < best_r2 || (r2 == best_r2 && o < best_oid)) {
+      best = j; best_r2 = r2; best_oid = o;
+    }
+  };
+  const float lim = best_f + p.nearest_band_r2;
+  if (!spill && best_f < INFINITY) {  // empty slots hold r = inf and no index
+#pragma unroll
+    for (int q = 0; q < KEEP; ++q)
+      if (kr[q] <= lim) consider(kj[q]);
+  }
+  if (__any_sync(0xffffffffu, spill)) {
+    warp_scan_candidates<DIM>(p, fluid_particles(w), active && spill, i, key, xs, stage[warp], sidx[warp],
+                              [&](uint32_t j, float r2f, float jtype) {
+      if (jtype == 0.f && r2f <= lim) consider(j);
+    });
+  }
+  if (!active || best == kEmpty) return;
+  double fs = forcing_factor(p, stage_time(w, stage2));
+  double gdot = 0.0, un = 0.0;
+  for (int k = 0; k < p.dim; ++k) {
+    gdot += (p.g[k] + p.force_amp[k] * fs) * (s.x[k * n + i] - s.x[k * n + best]);
+    un += s.u[k * n + best] * s.normal[k * n + i];
+  }
+  s.phi[i] = s.phi[best] + gdot;
+  for (int k = 0; k < p.dim; ++k) s.u[k * n + i] = s.u[k * n + best] - un * s.normal[k * n + i];
+}
+
+constexpr int PRE_THREADS = 256;
+
+__global__ void __launch_bounds__(PRE_THREADS) k_volumes_umax(Params p, State s, Work w, int64_t n) {
+  __shared__ unsigned long long red[PRE_THREADS / 32];
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double umax2 = 0.0;
+  if (i < n) {
+    if (s.type[i] == kFluid)
+      for (int k = 0; k < p.dim; ++k) umax2 += s.u[k * n + i] * s.u[k * n + i];
+    double v = s.mass[i] / eos_density(p, s.phi[i]);
+    w.vol[i] = v;
+    w.volc[i] = p.neg_dwdr_over_r_coef * v;  // -W'(r)/r V = volc (1 - q/2)^3
+    if (!isfinite(v)) atomicOr(w.status, kStatNaN);
+  }
+  // block max of |U|^2, then one atomic per block on the bit pattern
+  // (non-negative doubles order like their unsigned 64-bit patterns)
+  unsigned long long b = __double_as_longlong(umax2);
+  for (int off = 16; off; off >>= 1) {
+    unsigned long long o = __shfl_xor_sync(0xffffffffu, b, off);
+    b = o > b ? o : b;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = 0;
+    for (int k = 0; k < PRE_THREADS / 32; ++k) m = red[k] > m ? red[k] : m;
+    if (m) atomicMax(w.umax_bits, m);
+  }
+}
+
+void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int64_t nd,
+                    int stage2, cudaStream_t st, bool volumes) {
+  cudaMemsetAsync(w.umax_bits, 0, sizeof(unsigned long long), st);
+  if (n == 0) return;
+  if (nd > 0) {
+    unsigned blocks = (unsigned)div_up(nd, DUM_THREADS);
+    if (p.dim == 3) k_dummy_update<3><<<blocks, DUM_THREADS, 0, st>>>(p, s, w, n, nd, stage2);
+    else k_dummy_update<2><<<blocks, DUM_THREADS, 0, st>>>(p, s, w, n, nd, stage2);
+  }
+  if (volumes) k_volumes_umax<<<(unsigned)div_up(n, PRE_THREADS), PRE_THREADS, 0, st>>>(p, s, w, n);
+}
+
+// Time step (Sec. 2.3): CFL * min(dx/(C0 + U_max), dx^2/(2 nu), sqrt(2 dx/|G|)).
+__global__ void k_time_step(Params p, Work w) {
+  double umax = sqrt(__longlong_as_double((long long)*w.umax_bits));
+  double dt;
+  if (p.fixed_dt > 0) {
+    dt = p.fixed_dt;
+  } else {
+    double t = p.dx / (p.c0 + umax);
+    if (p.nu > 0) {
+      double td = p.dx * p.dx / (2.0 * p.nu);
+      if (td < t) t = td;
+    }
+    double g2 = 0.0;
+    for (int k = 0; k < p.dim; ++k) g2 += p.g[k] * p.g[k];
+    if (g2 > 0) {
+      double tg = sqrt(2.0 * p.dx / sqrt(g2));
+      if (tg < t) t = tg;
+    }
+    dt = p.cfl * t;
+  }
+  w.scalars[1] = dt;
+}
+
+void launch_time_step(const Params& p, const Work& w, cudaStream_t st) {
+  k_time_step<<<1, 1, 0, st>>>(p, w);
+}
+
+// FP32 value of a finite double, rounded to nearest (ties away from zero) on
+// its IEEE fields with integer instructions, so that the FP64 pipe only
+// does the arithmetic that needs it; magnitudes below 2^-126 give zero.
+__device__ __forceinline__ float mx_d2f(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  b = (b & 0x7FFFFFFFFFFFFFFFull) + (1ull << 28);  // half of the 29 dropped bits; a carry renormalises
+  const unsigned e = (unsigned)(b >> 52);
+  if (e <= 1023u - 127u) return 0.f;
+  return __uint_as_float(sign | ((e - (1023u - 127u)) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+}
+
+// exponent field of a double is all ones: infinity or NaN
+__device__ __forceinline__ bool mx_nonfinite(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7FF00000u) == 0x7FF00000u;
+}
+
+// ---- prepass of the mixed path, per particle (after the dummy update) ----
+// U_max^2 over fluid particles (FP64, for the time step and shifting); the
+// volume V = m / rho(phi) in FP32 (it only enters the FP32 pair sums); and the
+// packed FP32 copies read by the pair pass:
+//   A[i] = (x - cell origin, phi - phi_hs(x)), B[i] = (U, V) with V < 0 marking
+//   dummy particles (the Laplacian operator takes fluid neighbours only),
+//   C[i] = cell coordinates packed 11/11/10 bits.
+// w.vol receives V widened to FP64.
+constexpr int MXP_THREADS = 256;
+
+__global__ void __launch_bounds__(MXP_THREADS) k_prepass_mixed(Params p, State s, Work w, int64_t n, float4* A,
+                                                               float4* B, uint32_t* Cc) {
+  __shared__ unsigned long long red[MXP_THREADS / 32];
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double umax2 = 0.0;
+  if (i < n) {
+    const bool fluid = s.type[i] == kFluid;
+    const uint32_t key = w.key[i];
+    const uint32_t nx = (uint32_t)p.nc[0], ny = (uint32_t)p.nc[1];
+    const uint32_t ic[3] = {key % nx, (key / nx) % ny, key / (nx * ny)};
+    float o[3] = {0.f, 0.f, 0.f};
+    float u[3] = {0.f, 0.f, 0.f};
+    double phs = p.phs0;
+    bool bad = false;
+    for (int k = 0; k < p.dim; ++k) {
+      const double xk = s.x[k * n + i], uk = s.u[k * n + i];
+      bad |= mx_nonfinite(xk) | mx_nonfinite(uk);
+      o[k] = mx_d2f(xk - (p.domain_min[k] + (double)ic[k] * p.R));
+      u[k] = mx_d2f(uk);
+      if (fluid) umax2 = fma(uk, uk, umax2);
+      if (p.g[k] != 0.0) phs = fma(p.g[k], xk, phs);
+    }
+    const double phi = s.phi[i];
+    bad |= mx_nonfinite(phi);
+    const float phif = mx_d2f(phi);
+    // rho / rho0 = exp(phi / C0^2) (linear EOS) or (1 + (gamma-1) phi / c0^2)^(1/(gamma-1)) (Tait)
+    const float inv_c0sq = (float)(1.0 / p.c0sq);
+    float inv_rel;
+    if (p.eos == 0) {
+      inv_rel = expf(-phif * inv_c0sq);
+    } else {
+      const float gm1 = (float)(p.gamma - 1.0);
+      inv_rel = powf(fmaf(gm1 * phif, inv_c0sq, 1.f), -1.f / gm1);
+    }
+    float v = mx_d2f(s.mass[i]) * (float)(1.0 / p.rho0) * inv_rel;
+    bad |= !isfinite(v);
+    if (bad) atomicOr(w.status, kStatNaN);
+    w.vol[i] = (double)v;
+    A[i] = make_float4(o[0], o[1], o[2], mx_d2f(phi - phs));
+    B[i] = make_float4(u[0], u[1], u[2], fluid ? v : -v);
+    Cc[i] = ic[0] | (ic[1] << 11) | (ic[2] << 22);
+  }
+  // block max of |U|^2, one atomic per block on the bit pattern
+  unsigned long long b = (unsigned long long)__double_as_longlong(umax2);
+  for (int off = 16; off; off >>= 1) {
+    unsigned long long q = __shfl_xor_sync(0xffffffffu, b, off);
+    b = q > b ? q : b;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = 0;
+    for (int k = 0; k < MXP_THREADS / 32; ++k) m = red[k] > m ? red[k] : m;
+    if (m) atomicMax(w.umax_bits, m);
+  }
+}
+
+// Mixed prepass (after the dummy update, which resets U_max); fails when the
+// grid is too large for the packed cell coordinates (11/11/10 bits).
+int launch_prepass_mixed(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st) {
+  if (n == 0) return 0;
+  if (p.nc[0] > 2048 || p.nc[1] > 2048 || p.nc[2] > 1024) return WBSPH_E_INVAL;
+  k_prepass_mixed<<<(unsigned)div_up(n, MXP_THREADS), MXP_THREADS, 0, st>>>(p, s, w, n, w.packA, w.packB,
+                                                                            w.packC);
+  return 0;
+}
+
+}  // namespace wbsph
