@@ -32,26 +32,42 @@ def dam_scene(w: float, h: float, n_target: int, width: float = 2.0, wall: float
     return S.dam_break_2d(dx=dx, width=width, wall=wall, column=(w, h))
 
 
-def generate(n_traj=40, n_target=50_000, t_end=0.2, frames=20, seed=7, log=print):
-    """Plain FP64 trajectories; returns a list of (scene, [(x, u, phi), ...])."""
-    data = []
+def generate(n_traj=40, n_target=50_000, t_end=0.2, frames=20, seed=7, log=print, concurrent=8):
+    """Plain FP64 trajectories; returns a list of (scene, [(x, u, phi), ...]).
+
+    Each trajectory advances in chunks of 20 steps and records a frame at
+    the first chunk end past each of the frame times t_end (f + 1) / frames.
+    A 50k-particle step leaves most of the GPU idle, so `concurrent`
+    trajectories run at once, each on its own stream, advanced in lockstep
+    (the frames are the same as one at a time)."""
+    sizes = column_sizes(n_traj, seed)
+    data = [None] * n_traj
     t0 = time.time()
-    for k, (w, h) in enumerate(column_sizes(n_traj, seed)):
-        sc = dam_scene(w, h, n_target)
-        sim = wbsph.Sim(sc.params, water_height=sc.water_height)
-        sim.set_scene(sc)
-        states = []
-        for f in range(frames):
-            t_goal = t_end * (f + 1) / frames
-            while sim.stats()["t"] < t_goal:
-                sim.step(20)
-            states.append((sim.get("x"), sim.get("u"), sim.get("phi")))
-        data.append((sc, states))
-        nsteps = sim.stats()["steps"]
-        sim.close()
-        if log:
-            log(f"trajectory {k}: column {w:.2f} x {h:.2f}, n_fluid {sc.n_fluid}, "
-                f"steps {nsteps}, elapsed {time.time() - t0:.1f} s")
+    for b0 in range(0, n_traj, concurrent):
+        batch = []
+        for k in range(b0, min(b0 + concurrent, n_traj)):
+            sc = dam_scene(*sizes[k], n_target)
+            sim = wbsph.Sim(sc.params, water_height=sc.water_height)
+            sim.set_scene(sc)
+            batch.append({"k": k, "sc": sc, "sim": sim, "states": []})
+        live = list(batch)
+        while live:
+            for b in live:
+                b["sim"].step(20)  # enqueued on the trajectory's own stream
+            for b in live:
+                if b["sim"].stats()["t"] >= t_end * (len(b["states"]) + 1) / frames:
+                    b["states"].append((b["sim"].get("x"), b["sim"].get("u"), b["sim"].get("phi")))
+            done = [b for b in live if len(b["states"]) == frames]
+            live = [b for b in live if len(b["states"]) < frames]
+            for b in done:
+                sc, sim = b["sc"], b["sim"]
+                data[b["k"]] = (sc, b["states"])
+                nsteps = sim.stats()["steps"]
+                sim.close()
+                if log:
+                    w, h = sizes[b["k"]]
+                    log(f"trajectory {b['k']}: column {w:.2f} x {h:.2f}, n_fluid {sc.n_fluid}, "
+                        f"steps {nsteps}, elapsed {time.time() - t0:.1f} s")
     return data
 
 
