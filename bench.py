@@ -199,7 +199,7 @@ def profile_traffic(kernel_file: str, key: str):
     return ent.get("bytes_per_launch")
 
 
-def cpu_baseline(sample_scene, budget_s=12.0, max_steps=20):
+def cpu_baseline(sample_scene, budget_s=12.0, max_steps=500):
     import oracle
     st = oracle.State(sample_scene)
     t0 = time.perf_counter()

@@ -195,9 +195,11 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--eval-steps", type=int, default=400)
+    ap.add_argument("--concurrent", type=int, default=8, help="trajectories generated at once")
     args = ap.parse_args(argv)
     t0 = time.time()
-    data = generate(args.trajectories, args.particles, args.t_end, args.frames, args.seed)
+    data = generate(args.trajectories, args.particles, args.t_end, args.frames, args.seed,
+                    concurrent=args.concurrent)
     t_gen = time.time() - t0
     norm = normalisation(data)
     sur = wbsph.Surrogate(2)
