@@ -49,6 +49,12 @@ struct Params {
   float inner_r2;                 // FP32 r^2 at or below it (and > 0): an exact neighbour, no FP64 test
   double domain_min[3], domain_max[3];
   double R;                       // cell size 2h
+  // cell keys: FP32 estimate of (x - min)/R, trusted where its fractional
+  // part is more than key_margin from a cell boundary (exact FP64 otherwise)
+  float key_min_f[3];             // domain_min rounded to FP32
+  float key_inv_R_f;              // 1/R rounded to FP32
+  float key_margin[3];            // twice the bound on |estimate - FP64 quotient|, per axis
+  long long key_lo[3], key_hi[3]; // order-preserving integer images of domain_min, domain_max
   int nc[3];                      // grid cells per axis
   int64_t ncells;
   double water_height;

@@ -161,6 +161,15 @@ static void free_all(wbsph_s* h) {
 // ---- parameters ----
 static const double kPi = 3.14159265358979323846;
 
+// Integer image of a double that orders like the value (-0 maps to +0, NaN
+// outside the images of all numbers); the same map as the cell-key kernel's.
+static long long ordered_bits(double v) {
+  long long b;
+  memcpy(&b, &v, 8);
+  if (b == (long long)0x8000000000000000ULL) b = 0;
+  return b < 0 ? b ^ 0x7FFFFFFFFFFFFFFFLL : b;
+}
+
 static int derive_params(wbsph_s* h) {
   const wbsph_config& c = h->cfg;
   Params& p = h->P;
@@ -216,6 +225,24 @@ static int derive_params(wbsph_s* h) {
   }
   if (ncells >= (int64_t)0xFFFFFFFFLL) return fail(h, WBSPH_E_INVAL, "too many grid cells (%lld)", (long long)ncells);
   p.ncells = ncells;
+  // Cell keys. With x in [min, max] on axis k, A = max(|min|, |max|), the
+  // FP32 estimate qf = (fl32(x) - fl32(min)) * fl32(1/R), with fl32(x) the
+  // truncation of x (relative error below 2^-23) and every FP32 operation
+  // rounded to nearest, differs from the FP64 quotient fl64(fl64(x - min)/R)
+  // by less than 1.6 A 2^-23 / R + 3.1 N 2^-24 + N 2^-50 (N = cells on the
+  // axis, the largest quotient); twice that is the margin. An estimate whose
+  // fractional part lies within the margin of 0 or 1 takes the exact path.
+  p.key_inv_R_f = (float)(1.0 / p.R);
+  for (int k = 0; k < 3; ++k) {
+    p.key_lo[k] = ordered_bits(c.domain_min[k]);
+    p.key_hi[k] = ordered_bits(c.domain_max[k]);
+    p.key_min_f[k] = (float)c.domain_min[k];
+    double A = std::max(std::fabs(c.domain_min[k]), std::fabs(c.domain_max[k]));
+    double N = (double)p.nc[k];
+    double E = 1.6 * A * std::ldexp(1.0, -23) / p.R + 3.1 * N * std::ldexp(1.0, -24) + N * std::ldexp(1.0, -50);
+    double m = 2.0 * E;
+    p.key_margin[k] = m < 0.25 ? (float)m * 1.001f : 0.5f;  // 0.5: always exact
+  }
   // FP32 prefilter bound: every pair with exact r <= 2h has FP32 distance
   // below (2h + e)^2 (1 + 16 ulp), e twice the worst coordinate rounding.
   double X = 0.0;

@@ -10,10 +10,24 @@ namespace wbsph {
 
 // ---------------------------------------------------------------------------
 // Cell key (Eqs. hashid, ixyz): i_k = floor((x_k - x_min,k) / R), R = 2h;
-// key = i_x + i_y N_x + i_z N_x N_y. The subtraction and the division are
-// IEEE round-to-nearest (explicit intrinsics) so the keys equal the CPU
-// definition bit for bit.
+// key = i_x + i_y N_x + i_z N_x N_y, with the subtraction and the division
+// IEEE round-to-nearest in FP64 as the CPU definition has them. Almost every
+// particle gets floor of an FP32 estimate of the quotient: its error bound
+// (derived with the margin on the host) keeps the FP64 quotient on the same
+// side of every integer when the estimate's fractional part is more than
+// the margin from 0 and 1; the rest take the FP64 subtraction and division.
+// Either way the key equals the definition bit for bit.
 // ---------------------------------------------------------------------------
+// FP32 value of a double with its mantissa truncated (relative error below
+// 2^-23), on the IEEE fields with integer instructions; magnitudes below
+// 2^-126 give zero. The input is finite.
+__device__ __forceinline__ float key_d2f_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (e <= 1023u - 127u) return 0.f;
+  return __uint_as_float((hi & 0x80000000u) | ((e - (1023u - 127u)) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
 __global__ void k_cell_keys(Params p, const double* __restrict__ x, int64_t n,
                             uint32_t* __restrict__ key, unsigned* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -22,11 +36,21 @@ __global__ void k_cell_keys(Params p, const double* __restrict__ x, int64_t n,
   bool bad = false;
   for (int k = 0; k < p.dim; ++k) {
     double xk = x[k * n + i];
-    if (!(xk >= p.domain_min[k] && xk <= p.domain_max[k])) {
+    // min <= x <= max, compared on order-preserving integer images (-0 as
+    // +0; NaN falls outside), which keeps the FP64 pipe free
+    long long b = __double_as_longlong(xk);
+    if (b == (long long)0x8000000000000000ULL) b = 0;
+    b = b < 0 ? b ^ 0x7FFFFFFFFFFFFFFFLL : b;
+    if (!(b >= p.key_lo[k] && b <= p.key_hi[k])) {
       bad = true;
       continue;
     }
-    ic[k] = (int64_t)floor(__ddiv_rn(__dsub_rn(xk, p.domain_min[k]), p.R));
+    const float qf = (key_d2f_trunc(xk) - p.key_min_f[k]) * p.key_inv_R_f;
+    const float fl = floorf(qf), fr = qf - fl;
+    if (fr > p.key_margin[k] && fr < 1.f - p.key_margin[k])
+      ic[k] = (int64_t)fl;
+    else
+      ic[k] = (int64_t)floor(__ddiv_rn(__dsub_rn(xk, p.domain_min[k]), p.R));
     if (ic[k] >= p.nc[k]) ic[k] = p.nc[k] - 1;  // unreachable for in-domain x; guards indexing
   }
   if (bad) {

@@ -1,9 +1,11 @@
 """Host-side checks of the C-ABI library: it builds for sm_103a, loads, and
-exports every function that include/wbsph.h declares (no compute calls)."""
+exports every function that include/wbsph.h declares (no compute calls);
+and the error bound that the cell-key kernel's FP32 fast path relies on."""
 import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -71,3 +73,38 @@ def test_binding_kernel_classes_match_the_header():
     count = enum.pop("COUNT")
     assert len(wbsph.KERNEL_CLASSES) == count
     assert sorted(enum, key=enum.get) == [k.upper() for k in wbsph.KERNEL_CLASSES]
+
+
+def _trunc32(x):
+    """FP32 value of doubles with the mantissa truncated to 23 bits."""
+    b = np.asarray(x, dtype=np.float64).view(np.uint64) & np.uint64(0xFFFFFFFFE0000000)
+    return b.view(np.float64).astype(np.float32)
+
+
+@pytest.mark.parametrize("lo,hi,R", [(0.0, 3.2, 0.02184), (-0.03, 4.03, 0.02), (-1.5, 2.0, 0.0044),
+                                     (0.0, 0.2, 0.026)])
+def test_cell_key_estimate_error_bound(lo, hi, R):
+    """The cell-key kernel trusts floor of an FP32 estimate of (x - min)/R
+    when its fractional part is more than 2E from 0 and 1, with
+    E = 1.6 A 2^-23 / R + 3.1 N 2^-24 + N 2^-50 (A = max(|min|, |max|), N the
+    cells on the axis). The estimate, emulated operation by operation, stays
+    within E of the FP64 quotient of the definition, on random positions and
+    on positions next to every cell boundary."""
+    rng = np.random.default_rng(1)
+    N = int(np.floor((hi - lo) / R)) + 1
+    A = max(abs(lo), abs(hi))
+    E = 1.6 * A * 2.0 ** -23 / R + 3.1 * N * 2.0 ** -24 + N * 2.0 ** -50
+    bounds = lo + np.arange(N) * R
+    near = np.concatenate([bounds, np.nextafter(bounds, -np.inf), np.nextafter(bounds, np.inf),
+                           bounds + R * 1e-9, bounds - R * 1e-9])
+    x = np.concatenate([rng.uniform(lo, hi, 200_000), near])
+    x = x[(x >= lo) & (x <= hi)]
+    q64 = (x - lo) / R  # IEEE FP64 subtraction then division, as the definition
+    qf = (_trunc32(x) - np.float32(lo)) * np.float32(1.0 / R)  # float32 arithmetic, round to nearest
+    err = np.abs(qf.astype(np.float64) - q64)
+    assert err.max() <= E, (err.max(), E)
+    # and where the estimate is trusted, it gives the definition's cell
+    fr = qf - np.floor(qf)
+    m = np.float32(2 * E * 1.001)
+    ok = (fr > m) & (fr < 1 - m)
+    assert np.array_equal(np.floor(qf[ok]).astype(np.int64), np.floor(q64[ok]).astype(np.int64))

@@ -104,3 +104,34 @@ def test_mixed_3d_hydrostatic_box_rates_vanish():
     sim.eval_rates()
     f = sc.type == 0
     assert np.abs(sim.get("dudt")[:, f]).max() <= 1e-12 * 9.81
+
+
+def test_mixed_lone_particle_falls_exactly():
+    """A lone fluid particle has no neighbours: its renormalisation matrix is
+    zero, the TIC branch takes the conservative gradient (zero), and the
+    mixed path's FP64 epilogue gives DU/Dt = G exactly, so the SSP-RK2 step
+    reproduces the free fall to rounding."""
+    p = S.default_params(2, 0.01, 30.0, use_tic=1, domain_min=[-5, -20, 0], domain_max=[5, 5, 1])
+    sc = S.Scene(p, np.array([[0.1], [0.2]]), np.array([[0.5], [1.0]]), np.zeros(1),
+                 np.zeros(1, np.uint8), np.zeros((2, 1)))
+    sim = _sim(sc)
+    sim.step(50)
+    t = sim.stats()["t"]
+    x = sim.get("x")[:, 0]
+    assert abs(x[0] - (0.1 + 0.5 * t)) < 1e-14
+    assert abs(x[1] - (0.2 + t - 0.5 * 9.81 * t * t)) < 1e-13
+
+
+def test_mixed_rejects_grids_beyond_its_packed_cell_coordinates():
+    """The mixed path packs cell coordinates in 11/11/10 bits: a grid with
+    more than 2048 cells on an axis is refused at the first step with
+    WBSPH_E_INVAL (the FP64 path has no such limit)."""
+    from paper_2608_22269_gb300 import wbsph
+    p = S.default_params(2, 0.01, 30.0, domain_min=[-5, -50, 0], domain_max=[5, 5, 1])
+    sc = S.Scene(p, np.array([[0.1], [0.2]]), np.zeros((2, 1)), np.zeros(1), np.zeros(1, np.uint8),
+                 np.zeros((2, 1)))
+    assert int(np.floor(55.0 / (2 * 1.3 * 0.01))) + 1 > 2048
+    sim = _sim(sc)
+    with pytest.raises(wbsph.WbsphError) as ei:
+        sim.step(1)
+    assert ei.value.code == -1

@@ -286,3 +286,24 @@ def test_bounded_device_wait_reports_timeout_and_context_survives():
     st.step(2)
     sk = scales(sc.params, sc.water_height)
     assert scaled_err(sim.get("x"), st.x, sk["x"]) <= TOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_wall_particles_only(precision):
+    """No fluid at all: the dummy update finds no fluid within 2h and leaves
+    every wall particle as it is, the pair passes have no rows, and time
+    still advances with U_max = 0 (FP64 and mixed paths)."""
+    sc = S.dam_break_2d(dx=0.02, width=1.0, column=(0.3, 0.2))
+    walls = sc.type != 0
+    only = S.Scene(dict(sc.params), sc.x[:, walls].copy(), sc.u[:, walls].copy(), sc.phi[walls].copy(),
+                   sc.type[walls].copy(), sc.normal[:, walls].copy())
+    sim = _sim(only, precision)
+    sim.step(2)
+    sim.sync()
+    st = sim.stats()
+    assert st["n_fluid"] == 0 and st["n"] == int(walls.sum())
+    assert np.array_equal(sim.get("x"), only.x)
+    assert np.array_equal(sim.get("u"), only.u)
+    assert np.array_equal(sim.get("phi"), only.phi)
+    dt = oracle.time_step(only.params, only.u, only.type)
+    assert st["t"] == pytest.approx(2 * dt, rel=1e-15)
