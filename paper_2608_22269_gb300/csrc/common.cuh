@@ -106,6 +106,8 @@ struct Work {
   float4* packA;     // n: mixed path, (cell-relative offset, phi - phi_hs) in FP32
   float4* packB;     // n: mixed path, (U, +-V) in FP32
   uint32_t* packC;   // n: mixed path, cell coordinates packed 11/11/10 bits
+  double* cell_origin;  // mixed path: domain_min[k] + i R for the cells of axis k, axes one after
+                        // another (nc[0] + nc[1] + nc[2] entries)
 };
 
 __host__ __device__ inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }

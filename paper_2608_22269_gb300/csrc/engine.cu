@@ -388,6 +388,16 @@ static int allocate(wbsph_s* h, int64_t n) {
     w.packA = (float4*)dev_alloc(h, nn * sizeof(float4));
     w.packB = (float4*)dev_alloc(h, nn * sizeof(float4));
     w.packC = U32(nn);
+    const size_t no = (size_t)h->P.nc[0] + h->P.nc[1] + h->P.nc[2];
+    w.cell_origin = D(no);
+    if (w.cell_origin) {
+      std::vector<double> org;
+      org.reserve(no);
+      for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < h->P.nc[k]; ++i) org.push_back(h->P.domain_min[k] + (double)i * h->P.R);
+      CK(cudaMemcpyAsync(w.cell_origin, org.data(), no * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      CK(cudaStreamSynchronize(h->stream));  // the host vector goes out of scope
+    }
   }
   if (h->alloc_failed) return fail(h, WBSPH_E_NOMEM, "device allocation failed");
   h->n_alloc = n;

@@ -174,6 +174,15 @@ __device__ __forceinline__ float mx_d2f(double x) {
   return __uint_as_float(sign | ((e - (1023u - 127u)) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
 }
 
+// FP64 value of a positive normal float (V), widened exactly on the IEEE
+// fields; zero and anything else non-normal gives zero.
+__device__ __forceinline__ double mx_f2d(float v) {
+  const unsigned b = __float_as_uint(v), e = (b >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return 0.0;
+  return __hiloint2double((int)((b & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((b & 0x7FFFFFu) >> 3)),
+                          (int)(b << 29));
+}
+
 // exponent field of a double is all ones: infinity or NaN
 __device__ __forceinline__ bool mx_nonfinite(double x) {
   return ((unsigned)__double2hiint(x) & 0x7FF00000u) == 0x7FF00000u;
@@ -203,10 +212,12 @@ __global__ void __launch_bounds__(MXP_THREADS) k_prepass_mixed(Params p, State s
     float u[3] = {0.f, 0.f, 0.f};
     double phs = p.phs0;
     bool bad = false;
+    const double* org = w.cell_origin;  // origins of axis 0, then 1, then 2
     for (int k = 0; k < p.dim; ++k) {
       const double xk = s.x[k * n + i], uk = s.u[k * n + i];
       bad |= mx_nonfinite(xk) | mx_nonfinite(uk);
-      o[k] = mx_d2f(xk - (p.domain_min[k] + (double)ic[k] * p.R));
+      o[k] = mx_d2f(xk - __ldg(org + ic[k]));  // x - (domain_min + i R)
+      org += p.nc[k];
       u[k] = mx_d2f(uk);
       if (fluid) umax2 = fma(uk, uk, umax2);
       if (p.g[k] != 0.0) phs = fma(p.g[k], xk, phs);
@@ -226,7 +237,7 @@ __global__ void __launch_bounds__(MXP_THREADS) k_prepass_mixed(Params p, State s
     float v = mx_d2f(s.mass[i]) * (float)(1.0 / p.rho0) * inv_rel;
     bad |= !isfinite(v);
     if (bad) atomicOr(w.status, kStatNaN);
-    w.vol[i] = (double)v;
+    w.vol[i] = mx_f2d(v);
     A[i] = make_float4(o[0], o[1], o[2], mx_d2f(phi - phs));
     B[i] = make_float4(u[0], u[1], u[2], fluid ? v : -v);
     Cc[i] = ic[0] | (ic[1] << 11) | (ic[2] << 22);
