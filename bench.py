@@ -319,24 +319,34 @@ def surrogate_bytes_per_stage(n, nf, E, hidden=64, layers=3):
     return fill + enc + layers * per_layer + dec
 
 
-def surrogate_path(args, local):
-    """Surrogate rollouts (configs' 2D inference case: dam break, column
-    0.6 x 0.3 m, dx = 0.00085 m, 249,218 fluid particles) with a plain FP64
-    re-anchoring step every 10 steps, timed against the plain FP64 rollout of
-    the same scene; error = position RMS / dx against that plain rollout.
-    The timed rollout keeps the surrogate between anchors (tau = inf); the
-    fallback rule (tau = 0.1: a window whose anchor error exceeds tau runs
-    plain) is reported from a second, untimed rollout."""
+def surrogate_path(args, local, dim=2):
+    """Surrogate rollouts with a plain FP64 re-anchoring step every 10 steps,
+    timed against the plain FP64 rollout of the same scene; error = position
+    RMS / dx against that plain rollout. 2D: the configs' inference case (dam
+    break, column 0.6 x 0.3 m, dx = 0.00085 m, 249,218 fluid particles). 3D:
+    the 3D dam break of the headline (1,208,207 fluid particles) with the
+    network trained on its half-size replicas. The timed rollout keeps the
+    surrogate between anchors (tau = inf); the fallback rule (tau = 0.1: a
+    window whose anchor error exceeds tau runs plain) is reported from a
+    second, untimed rollout."""
     import numpy as np
     import torch
 
     from paper_2608_22269_gb300 import scenes, wbsph
     from paper_2608_22269_gb300 import surrogate as SG
-    path = os.path.join(ROOT, "paper_2608_22269_gb300", "data", "surrogate_2d.npz")
+    name = "surrogate_2d.npz" if dim == 2 else "surrogate_3d.npz"
+    path = os.path.join(ROOT, "paper_2608_22269_gb300", "data", name)
     if not os.path.exists(path):
-        return {"unavailable": "no trained surrogate weights in paper_2608_22269_gb300/data"}
-    sur, norm = SG.load(path, 2)
-    sc = scenes.dam_break_2d(dx=0.00085, width=2.0, wall=0.6, column=(0.6, 0.3))
+        return {"unavailable": f"no trained {dim}D surrogate weights in paper_2608_22269_gb300/data"}
+    sur, norm = SG.load(path, dim)
+    if dim == 2:
+        sc = scenes.dam_break_2d(dx=0.00085, width=2.0, wall=0.6, column=(0.6, 0.3))
+        desc = ("2D dam break, column 0.6x0.3 m in a 2.0 m basin, dx=0.00085 m "
+                f"({sc.n_fluid:,} fluid), FP64 anchor every 10 steps, no fallback (tau = inf)")
+    else:
+        sc = scenes.dam_break_3d(dx=0.0084)
+        desc = ("3D dam break, box 3.2x1.0x1.0 m, column 1.2x1.0x0.6 m, dx=0.0084 m "
+                f"({sc.n_fluid:,} fluid), FP64 anchor every 10 steps, no fallback (tau = inf)")
     K = max(args.steps, 10)
     inf = float("inf")
 
@@ -365,12 +375,11 @@ def surrogate_path(args, local):
     # one surrogate stage alone: graph build and network, CUDA events in the library
     st = sim.stats()
     n, nf = st["n"], st["n_fluid"]
-    dbg = sur.debug(sim)
-    E = len(dbg["recv"])
+    E = sur.edges(sim)
     sim.profile(reset=True)
     sur.predict(sim)
     stage_ms = sim.profile(reset=True)["pair"][0]
-    flops = surrogate_flops_per_stage(2, n, nf, E)
+    flops = surrogate_flops_per_stage(dim, n, nf, E)
     peak = 1925.2
     try:
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
@@ -387,8 +396,7 @@ def surrogate_path(args, local):
     fb_sim = wbsph.Sim(sc.params, water_height=sc.water_height, device=local)
     fb_sim.set_scene(sc)
     fb = sur.step(fb_sim, K, anchor_every=10, tau=0.1)
-    out = {"workload": "2D dam break, column 0.6x0.3 m in a 2.0 m basin, dx=0.00085 m "
-                       f"({sc.n_fluid:,} fluid), FP64 anchor every 10 steps, no fallback (tau = inf)",
+    out = {"workload": desc,
            "value": round(sc.n_fluid * K / t_sur, 1), "unit": UNIT,
            "plain_fp64_same_scene": round(sc.n_fluid * K / t_plain, 1),
            "ms_per_step": round(t_sur * 1e3 / K, 3), "steps": K,
@@ -404,7 +412,7 @@ def surrogate_path(args, local):
                    "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4),
                    "note": "the stage is bound by data movement: ~45 FLOP/B against a ~290 FLOP/B ridge"},
            "with_fallback_tau_0.1": fb,
-           "weights": "paper_2608_22269_gb300/data/surrogate_2d.npz (trained on the GPU by this library)"}
+           "weights": f"paper_2608_22269_gb300/data/{name} (trained on the GPU by this library)"}
     for o in (plain, sim, fb_sim, sur):
         o.close()
     return out
@@ -502,10 +510,11 @@ def run_ours(args):
                              "fp64_vs_oracle": "within 1e-12 (tests/test_gpu_fullsize.py samples this workload)",
                              "measure": "max|a-b| / max(max|b|, natural scale) over fluid particles"}
         if rank == 0:
-            try:
-                paths["surrogate"] = surrogate_path(args, local)
-            except Exception as exc:  # the plain paths above are the headline; report, do not abort
-                paths["surrogate"] = {"error": f"{type(exc).__name__}: {exc}"}
+            for key, dim in (("surrogate", 2), ("surrogate_3d", 3)):
+                try:
+                    paths[key] = surrogate_path(args, local, dim)
+                except Exception as exc:  # the plain paths above are the headline; report, do not abort
+                    paths[key] = {"error": f"{type(exc).__name__}: {exc}"}
         line["paths"] = paths
         sim2.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -556,9 +565,11 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true",
-                    help="skip the second precision and the sampled error checks")
+                    help="skip the second precision and the surrogate paths")
     ap.add_argument("--only-surrogate", action="store_true",
                     help="run only the surrogate rollout timing (profiling aid)")
+    ap.add_argument("--surrogate-dim", type=int, default=2, choices=(2, 3),
+                    help="with --only-surrogate: the 2D or the 3D surrogate case")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -567,7 +578,8 @@ def main():
     elif args.only_surrogate:
         import torch
         torch.cuda.set_device(0)
-        print(json.dumps({"surrogate": surrogate_path(args, 0)}), flush=True)
+        key = "surrogate" if args.surrogate_dim == 2 else "surrogate_3d"
+        print(json.dumps({key: surrogate_path(args, 0, args.surrogate_dim)}), flush=True)
     else:
         run_ours(args)
 

@@ -9,7 +9,10 @@ SSP-RK2 step and re-anchor with a plain FP64 step every `anchor_every` steps
 error against the plain one on the anchor state.
 
 Scenes: 2D dam breaks in a 2.0 x 1.0 m basin, column width and height drawn
-(seeded) from [0.3, 0.8] x [0.2, 0.5] m, dx = sqrt(w h / n_target).
+(seeded) from [0.3, 0.8] x [0.2, 0.5] m, dx = sqrt(w h / n_target); in 3D,
+dam breaks in the 1.6 x 0.5 x 0.5 m box (the 3D dam break halved along every
+axis) at its dx = 0.0084 m, column length and height from the same draws
+with the height mapped to [0.2, 0.35] m.
 """
 from __future__ import annotations
 
@@ -27,26 +30,36 @@ def column_sizes(n: int, seed: int = 7):
     return [(float(rng.uniform(0.3, 0.8)), float(rng.uniform(0.2, 0.5))) for _ in range(n)]
 
 
+def dam_scene_3d(w: float, h: float, dx: float = 0.0084):
+    """3D dam break in the 1.6 x 0.5 x 0.5 m box: a column w long, 0.5 m wide
+    and 0.2 + (h - 0.2) / 2 m high (h from the 2D draws)."""
+    return S.dam_break_3d(dx=dx, box=(1.6, 0.5, 0.5), column=(w, 0.5, 0.2 + 0.5 * (h - 0.2)))
+
+
 def dam_scene(w: float, h: float, n_target: int, width: float = 2.0, wall: float = 1.0):
     dx = math.sqrt(w * h / n_target)
     return S.dam_break_2d(dx=dx, width=width, wall=wall, column=(w, h))
 
 
-def generate(n_traj=40, n_target=50_000, t_end=0.2, frames=20, seed=7, log=print, concurrent=8):
+def generate(n_traj=40, n_target=50_000, t_end=0.2, frames=20, seed=7, log=print, concurrent=8, scene_fn=None):
     """Plain FP64 trajectories; returns a list of (scene, [(x, u, phi), ...]).
 
     Each trajectory advances in chunks of 20 steps and records a frame at
     the first chunk end past each of the frame times t_end (f + 1) / frames.
     A 50k-particle step leaves most of the GPU idle, so `concurrent`
     trajectories run at once, each on its own stream, advanced in lockstep
-    (the frames are the same as one at a time)."""
+    (the frames are the same as one at a time). scene_fn(w, h) builds a
+    scene from a column draw (default: the 2D dam break with n_target fluid
+    particles)."""
+    if scene_fn is None:
+        scene_fn = lambda w, h: dam_scene(w, h, n_target)  # noqa: E731
     sizes = column_sizes(n_traj, seed)
     data = [None] * n_traj
     t0 = time.time()
     for b0 in range(0, n_traj, concurrent):
         batch = []
         for k in range(b0, min(b0 + concurrent, n_traj)):
-            sc = dam_scene(*sizes[k], n_target)
+            sc = scene_fn(*sizes[k])
             sim = wbsph.Sim(sc.params, water_height=sc.water_height)
             sim.set_scene(sc)
             batch.append({"k": k, "sc": sc, "sim": sim, "states": []})
@@ -187,42 +200,49 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="train the BF16 surrogate on plain FP64 trajectories")
     ap.add_argument("--out", required=True, help="output .npz with parameters and normalisation")
     ap.add_argument("--report", default=None, help="JSON report path")
-    ap.add_argument("--trajectories", type=int, default=24)
+    ap.add_argument("--trajectories", type=int, default=200)
     ap.add_argument("--particles", type=int, default=50_000)
     ap.add_argument("--t-end", type=float, default=0.2)
     ap.add_argument("--frames", type=int, default=20)
-    ap.add_argument("--iters", type=int, default=8000)
-    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--iters", type=int, default=30000)
+    ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--eval-steps", type=int, default=400)
-    ap.add_argument("--concurrent", type=int, default=8, help="trajectories generated at once")
+    ap.add_argument("--concurrent", type=int, default=16, help="trajectories generated at once")
+    ap.add_argument("--dim", type=int, default=2, choices=(2, 3))
+    ap.add_argument("--dx3", type=float, default=0.0084, help="particle spacing of the 3D scenes")
     args = ap.parse_args(argv)
+    dim = args.dim
+    if dim == 2:
+        scene_fn = lambda w, h: dam_scene(w, h, args.particles)  # noqa: E731
+    else:
+        scene_fn = lambda w, h: dam_scene_3d(w, h, args.dx3)  # noqa: E731
     t0 = time.time()
     data = generate(args.trajectories, args.particles, args.t_end, args.frames, args.seed,
-                    concurrent=args.concurrent)
+                    concurrent=args.concurrent, scene_fn=scene_fn)
     t_gen = time.time() - t0
     norm = normalisation(data)
-    sur = wbsph.Surrogate(2)
-    theta0 = init_params_2d(seed=args.seed)
+    sur = wbsph.Surrogate(dim)
+    theta0 = init_params(dim, seed=args.seed)
     sur.set_params(theta0)
     sur.set_normalization(*norm)
     t0 = time.time()
     hist = train(sur, data, iters=args.iters, lr=args.lr, seed=args.seed)
     t_train = time.time() - t0
-    meta = dict(trajectories=args.trajectories, particles=args.particles, t_end=args.t_end,
+    meta = dict(dim=dim, trajectories=args.trajectories, particles=args.particles, dx3=args.dx3, t_end=args.t_end,
                 frames=args.frames, iters=args.iters, lr=args.lr, seed=args.seed)
     save(args.out, sur, norm, meta)
     # gain test on a held-out column, same anchoring for every variant
-    held = dam_scene(0.55, 0.35, args.particles)
+    held = scene_fn(0.55, 0.35)
     rep = {"meta": meta, "gen_s": t_gen, "train_s": t_train,
            "loss_first": float(np.mean(hist[:50])), "loss_last": float(np.mean(hist[-50:]))}
     inf = float("inf")
     rep["trained"] = rollout_error(held, sur, args.eval_steps, tau=inf)
-    grav = wbsph.Surrogate(2)
-    grav.set_params(gravity_only_params(2, norm[2], norm[3], held.params["g"]))
+    grav = wbsph.Surrogate(dim)
+    grav.set_params(gravity_only_params(dim, norm[2], norm[3], held.params["g"]))
     grav.set_normalization(*norm)
     rep["gravity_only"] = rollout_error(held, grav, args.eval_steps, tau=inf)
-    untrained = wbsph.Surrogate(2)
+    untrained = wbsph.Surrogate(dim)
     untrained.set_params(theta0)
     untrained.set_normalization(*norm)
     rep["untrained"] = rollout_error(held, untrained, args.eval_steps, tau=inf)
@@ -234,9 +254,13 @@ def main(argv=None):
 
 
 def init_params_2d(seed=0, hidden=64, layers=3):
+    """init_params in 2D."""
+    return init_params(2, seed, hidden, layers)
+
+
+def init_params(dim, seed=0, hidden=64, layers=3):
     """Uniform(+-1/sqrt(fan_in)) weights, zero biases, processor output
     layers scaled by 0.1 (small residual updates at the start)."""
-    dim = 2
     rng = np.random.default_rng(seed)
     fn, fe, fo = dim + 3, 2 * dim + 2, dim + 1
     blocks = [("n", fn, hidden), ("e", fe, hidden)]

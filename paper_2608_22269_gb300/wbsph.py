@@ -401,6 +401,14 @@ class Surrogate:
     def predict(self, sim):
         self._check(self.lib.wbsph_surrogate_predict(self.h, sim.h), sim)
 
+    def edges(self, sim):
+        """Number of graph edges (fluid receivers and their neighbours) at the
+        sim's current state."""
+        ne = C.c_int64()
+        self._check(self.lib.wbsph_surrogate_debug(self.h, sim.h, C.byref(ne), None, None, None, None,
+                                                   None, None, None, None), sim)
+        return ne.value
+
     def debug(self, sim):
         ne = C.c_int64()
         self._check(self.lib.wbsph_surrogate_debug(self.h, sim.h, C.byref(ne), None, None, None, None,
