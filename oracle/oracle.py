@@ -39,7 +39,11 @@ class Config(C.Structure):
                 ("use_visc", C.c_int), ("eos", C.c_int), ("tait_gamma", C.c_double),
                 ("domain_min", C.c_double * 3), ("domain_max", C.c_double * 3),
                 ("force_amp", C.c_double * 3), ("force_period", C.c_double),
-                ("fixed_dt", C.c_double), ("umax_override", C.c_double)]
+                ("fixed_dt", C.c_double), ("umax_override", C.c_double),
+                ("scheme", C.c_int), ("art_alpha", C.c_double)]
+
+# parameters with defaults when a parameter set does not name them
+_DEFAULTS = {"umax_override": -1.0, "scheme": 0, "art_alpha": 0.02}
 
 
 _lock = threading.Lock()
@@ -96,7 +100,7 @@ def lib():
 def make_config(params: dict) -> Config:
     c = Config()
     for name, _ in Config._fields_:
-        v = params.get(name, -1.0) if name == "umax_override" else params[name]
+        v = params.get(name, _DEFAULTS[name]) if name in _DEFAULTS else params[name]
         if isinstance(v, (list, tuple, np.ndarray)):
             arr = getattr(c, name)
             for k in range(3):

@@ -42,6 +42,8 @@ static int valid_config(const orc_config* c) {
   if (c->eos == 1 && !(c->tait_gamma > 1)) return 0;
   for (int k = 0; k < c->dim; ++k)
     if (!(c->domain_max[k] > c->domain_min[k])) return 0;
+  if (c->scheme != 0 && c->scheme != 1) return 0;
+  if (c->scheme == 1 && (c->use_delta || c->use_pst || c->use_tic || c->art_alpha < 0)) return 0;
   return 1;
 }
 
@@ -531,6 +533,67 @@ static void pair_sums_one(const orc_config* c, int64_t n, const double* x, const
   memcpy(out + 28, Lam, sizeof Lam);
 }
 
+/* ---------------------------------------------------------------------------
+ * Conventional WCSPH rates of fluid particle i (Sec. 2.1: Eq. nslag, the
+ * linear EOS of Eq. eos-water, the printed operators <div U>, <grad p> and
+ * <lap U>), the foil of the hydrostatic comparison. The state stays
+ * (x, U, phi) with rho = rho(phi) and p = p(phi) by the EOS; since
+ * d(phi) = c^2 d(rho)/rho, Drho/Dt = -rho div U is Dphi/Dt = -c^2 div U:
+ *   DU/Dt   = -(1/rho_i) sum (p_i + p_j) grad_i W_ij V_j + 2 nu Lambda + Pi + G(t)
+ *   Dphi/Dt = -c^2 sum (U_j - U_i).grad_i W_ij V_j
+ *   Pi      = -sum m_j Pi_ij grad_i W_ij, m_j = rho_j V_j,
+ *   Pi_ij   = -alpha h C0 (U_ij.x_ij) / (rho_ij (|x_ij|^2 + 0.01 h^2)) when
+ *             U_ij.x_ij < 0, else 0; U_ij = U_i - U_j, x_ij = x_i - x_j,
+ *             rho_ij = (rho_i + rho_j)/2 (artificial viscosity, Monaghan's form)
+ * with Lambda the Laplacian sum of pair_sums_one (fluid neighbours).
+ * ------------------------------------------------------------------------- */
+static void conventional_rates_one(const orc_config* c, int64_t n, const double* x, const double* u,
+                                   const double* phi, const double* vol, const uint8_t* type,
+                                   const csr_t* nb, int64_t i, const double* G, double* dudt,
+                                   double* dphidt) {
+  int d = c->dim;
+  double h = c->h_over_dx * c->dx;
+  double rho_i = eos_density(c, phi[i]), p_i = eos_pressure(c, phi[i]);
+  double gp[3] = {0, 0, 0}, lam[3] = {0, 0, 0}, av[3] = {0, 0, 0}, divu = 0.0;
+  for (int64_t e = nb->row[i]; e < nb->row[i + 1]; ++e) {
+    int64_t j = nb->col[e];
+    double rij[3] = {0, 0, 0}, r2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+      rij[k] = x[k * n + j] - x[k * n + i];
+      r2 += rij[k] * rij[k];
+    }
+    double r = sqrt(r2);
+    double dwdr = kernel_dwdr(d, h, r);
+    double gw[3] = {0, 0, 0}; /* grad_i W_ij = dW/dr (x_i - x_j) / r */
+    for (int k = 0; k < d; ++k) gw[k] = dwdr * (-rij[k]) / r;
+    double vj = vol[j];
+    double rho_j = eos_density(c, phi[j]), p_j = eos_pressure(c, phi[j]);
+    double rgw = 0.0, uijxij = 0.0;
+    for (int k = 0; k < d; ++k) {
+      rgw += rij[k] * gw[k];
+      /* (U_i - U_j).(x_i - x_j) */
+      uijxij += (u[k * n + i] - u[k * n + j]) * (-rij[k]);
+    }
+    double pi_ij = 0.0;
+    if (uijxij < 0.0) {
+      double rho_bar = 0.5 * (rho_i + rho_j);
+      pi_ij = -c->art_alpha * h * c->c0 * uijxij / (rho_bar * (r2 + 0.01 * h * h));
+    }
+    for (int k = 0; k < d; ++k) {
+      double duk = u[k * n + j] - u[k * n + i];
+      gp[k] += (p_i + p_j) * gw[k] * vj;
+      divu += duk * gw[k] * vj;
+      if (type[j] == FLUID) lam[k] += duk * rgw / r2 * vj;
+      av[k] += rho_j * vj * pi_ij * gw[k];
+    }
+  }
+  for (int k = 0; k < d; ++k) {
+    double visc = c->use_visc ? 2.0 * c->nu * lam[k] : 0.0;
+    dudt[k] = -gp[k] / rho_i + visc - av[k] + G[k];
+  }
+  *dphidt = -eos_c2(c, phi[i]) * divu;
+}
+
 static int volumes(const orc_config* c, int64_t n, const double* phi, const double* mass,
                    double* vol) {
   for (int64_t i = 0; i < n; ++i) {
@@ -672,9 +735,18 @@ int orc_stage_rates(const orc_config* c, int64_t n, const double* x, double* u, 
         lambda[i] = 0.0;
         continue;
       }
-      double s[ORC_NSUMS];
-      pair_sums_one(c, n, x, u, phi, vol, type, &nb, i, s);
-      int e = rates_from_sums(c, phi[i], s, umax, G, a, &dp, sh, &lam);
+      int e = ORC_OK;
+      if (c->scheme == 1) {
+        conventional_rates_one(c, n, x, u, phi, vol, type, &nb, i, G, a, &dp);
+        for (int k = 0; k < d; ++k) sh[k] = 0.0;
+        for (int k = 0; k < d; ++k)
+          if (!isfinite(a[k])) e = ORC_E_NAN;
+        if (!isfinite(dp)) e = ORC_E_NAN;
+      } else {
+        double s[ORC_NSUMS];
+        pair_sums_one(c, n, x, u, phi, vol, type, &nb, i, s);
+        e = rates_from_sums(c, phi[i], s, umax, G, a, &dp, sh, &lam);
+      }
       if (e < err) err = e;
       for (int k = 0; k < d; ++k) { dudt[k * n + i] = a[k]; dushift[k * n + i] = sh[k]; }
       dphidt[i] = dp;

@@ -16,6 +16,8 @@
  *   time integration .. SSP-RK2 stages and the three-condition time step
  *   walls ............. Sec. 2.4, Eq. (phiBn) and the slip velocity condition
  *   neighbours ........ Sec. 3, Eqs. (hashid), (ixyz), Algorithm 1 (d <= 2h)
+ *   conventional foil . Sec. 2.1, Eq. (nslag), Eq. (eos-water), the printed operators
+ *                        <div U>, <grad p>, <lap U>; artificial viscosity (Monaghan form)
  *
  * Layouts: positions, velocities and normals are structure-of-arrays,
  * component k of particle i at [k*n + i]. Types: 0 fluid, 1 dummy (wall).
@@ -61,6 +63,11 @@ typedef struct {
   double umax_override;    /* >= 0: U_max used by shifting in orc_stage_rates (an input
                               when rates are evaluated on a patch of a larger scene);
                               < 0: computed from the particles */
+  int scheme;              /* 0: well-balanced WCSPH (Eq. sph); 1: conventional WCSPH
+                              (Eq. nslag with the printed operators and artificial
+                              viscosity), the foil of the hydrostatic comparison; it
+                              takes no delta-SPH, shifting or TIC */
+  double art_alpha;        /* artificial-viscosity coefficient of the conventional scheme */
 } orc_config;
 
 /* Number of doubles per particle written by orc_pair_sums:
