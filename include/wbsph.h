@@ -101,7 +101,18 @@ typedef struct {
   wbsph_free_fn free;
   void* alloc_ctx;
   double water_height;      /* free-surface height H of the hydrostatic split (mixed path) */
+  int scheme;               /* WBSPH_SCHEME_WB (default): the well-balanced scheme, Eq. (sph);
+                               WBSPH_SCHEME_CONVENTIONAL: conventional WCSPH (Sec. 2.1, Eq. nslag
+                               with the printed operators, Eq. eos-water) plus artificial
+                               viscosity, the foil of the hydrostatic comparison (Sec. 4.1).
+                               The conventional scheme runs in FP64 with delta-SPH, shifting
+                               and TIC off; anything else is WBSPH_E_INVAL. */
+  double art_alpha;         /* conventional scheme: artificial-viscosity coefficient alpha of
+                               Pi_ij = -alpha h C0 (U_ij.x_ij) / (rho_ij (r^2 + 0.01 h^2)) for
+                               approaching pairs (default 0.02) */
 } wbsph_config;
+
+typedef enum { WBSPH_SCHEME_WB = 0, WBSPH_SCHEME_CONVENTIONAL = 1 } wbsph_scheme;
 
 typedef struct {
   int64_t n, n_fluid, n_dummy;

@@ -59,6 +59,9 @@ struct Params {
   int64_t ncells;
   double water_height;
   double phs0;  // |G| H: hydrostatic potential at height zero (phi_hs = G.x + |G| H)
+  int scheme;          // 0 well-balanced, 1 conventional WCSPH (the hydrostatic foil)
+  double art_ahc0;     // conventional scheme: alpha h C0 of the artificial viscosity
+  double avis_eps2;    // 0.01 h^2
 };
 
 // Device arrays of one particle-state buffer.
@@ -83,6 +86,8 @@ struct Work {
   double* lambda;    // n
   double* Lmat;      // 3n (2D) or 6n (3D): L of the last FP64 pair pass (upper triangle, SoA)
   double* vol;       // n
+  double* rho;       // n: densities of the stage (conventional scheme only)
+  double* pres;      // n: pressures of the stage (conventional scheme only)
   double* volc;      // n: 5 alpha / h^2 * V, so that -W'(r)/r V = volc (1 - q/2)^3
   float4* xf;        // n: FP32 copy of positions (.w = type) for the candidate prefilter
   uint32_t* key;     // n: sorted cell keys
@@ -135,6 +140,9 @@ void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n,
                       int stage2, cudaStream_t st);
 int pair_list_kmax(int dim);
 void launch_lambda_fp64(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st);
+// ---- pair_conventional.cu ----
+void launch_pair_conventional(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
+                              int stage2, cudaStream_t st);
 void launch_nbr_list(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid, cudaStream_t st,
                      bool exact);
 void launch_rk_stage(const Params& p, const State& s, const Work& w, int64_t n, int stage,

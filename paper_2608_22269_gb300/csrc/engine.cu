@@ -215,6 +215,9 @@ static int derive_params(wbsph_s* h) {
   p.fixed_dt = c.fixed_dt;
   p.water_height = c.water_height;
   p.phs0 = std::sqrt(c.g[0] * c.g[0] + c.g[1] * c.g[1] + c.g[2] * c.g[2]) * c.water_height;
+  p.scheme = c.scheme;
+  p.art_ahc0 = c.art_alpha * p.h * c.c0;
+  p.avis_eps2 = 0.01 * p.h * p.h;
   int64_t ncells = 1;
   for (int k = 0; k < 3; ++k) {
     int64_t m = 1;
@@ -283,6 +286,11 @@ static int validate(const wbsph_config* c, wbsph_s* h) {
     if (!(c->domain_max[k] > c->domain_min[k])) return fail(h, WBSPH_E_INVAL, "empty domain on axis %d", k);
   if ((c->alloc == nullptr) != (c->free == nullptr))
     return fail(h, WBSPH_E_INVAL, "alloc and free hooks must be given together");
+  if (c->scheme != WBSPH_SCHEME_WB && c->scheme != WBSPH_SCHEME_CONVENTIONAL)
+    return fail(h, WBSPH_E_INVAL, "unknown scheme");
+  if (c->scheme == WBSPH_SCHEME_CONVENTIONAL &&
+      (c->precision != WBSPH_FP64 || c->use_delta || c->use_pst || c->use_tic || !(c->art_alpha >= 0)))
+    return fail(h, WBSPH_E_INVAL, "the conventional scheme runs in FP64 without delta-SPH, shifting or TIC");
   return WBSPH_OK;
 }
 
@@ -306,6 +314,8 @@ extern "C" int wbsph_config_default(wbsph_config* cfg, int dim) {
   cfg->tait_gamma = 7.0;
   for (int k = 0; k < 3; ++k) cfg->domain_max[k] = 1.0;
   cfg->precision = WBSPH_FP64;
+  cfg->scheme = WBSPH_SCHEME_WB;
+  cfg->art_alpha = 0.02;
   return WBSPH_OK;
 }
 
@@ -360,6 +370,7 @@ static int allocate(wbsph_s* h, int64_t n) {
   Work& w = h->W;
   w.dudt = D(d * nn); w.dushift = D(d * nn); w.dphidt = D(nn); w.lambda = D(nn); w.vol = D(nn);
   w.volc = D(nn);
+  if (h->cfg.scheme == WBSPH_SCHEME_CONVENTIONAL) { w.rho = D(nn); w.pres = D(nn); }
   w.Lmat = D((size_t)(d == 3 ? 6 : 3) * nn);
   w.xf = (float4*)dev_alloc(h, nn * sizeof(float4));
   w.key = U32(nn); w.key_alt = U32(nn); w.perm = U32(nn); w.perm_alt = U32(nn);
@@ -541,6 +552,7 @@ static int rates(wbsph_s* h, int stage2) {
   {
     ProfScope ps(h, WBSPH_K_PAIR);
     if (mixed) launch_pair_mixed(h->P, h->A, h->W, n, h->nf, stage2, st);
+    else if (h->P.scheme == WBSPH_SCHEME_CONVENTIONAL) launch_pair_conventional(h->P, h->A, h->W, n, h->nf, stage2, st);
     else launch_pair_fp64(h->P, h->A, h->W, n, h->nf, stage2, st);
   }
   h->launches += (n ? 1 : 0) + (h->nd ? 1 : 0) + (stage2 ? 0 : 1) + (h->nf ? 2 : 0);

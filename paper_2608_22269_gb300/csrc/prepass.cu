@@ -102,8 +102,14 @@ __global__ void __launch_bounds__(PRE_THREADS) k_volumes_umax(Params p, State s,
   if (i < n) {
     if (s.type[i] == kFluid)
       for (int k = 0; k < p.dim; ++k) umax2 += s.u[k * n + i] * s.u[k * n + i];
-    double v = s.mass[i] / eos_density(p, s.phi[i]);
+    const double rho = eos_density(p, s.phi[i]);
+    double v = s.mass[i] / rho;
     w.vol[i] = v;
+    if (p.scheme == 1) {  // the conventional scheme's density and pressure (EOS)
+      w.rho[i] = rho;
+      w.pres[i] = p.eos == 0 ? p.c0sq * (rho - p.rho0)
+                             : p.rho0 * p.c0sq / p.gamma * (pow(rho / p.rho0, p.gamma) - 1.0);
+    }
     w.volc[i] = p.neg_dwdr_over_r_coef * v;  // -W'(r)/r V = volc (1 - q/2)^3
     if (!isfinite(v)) atomicOr(w.status, kStatNaN);
   }

@@ -68,7 +68,7 @@ def default_params(dim: int, dx: float, c0: float, **kw) -> dict:
              use_delta=0, use_pst=0, use_tic=0, use_visc=1,
              eos=0, tait_gamma=7.0,
              domain_min=[0.0, 0.0, 0.0], domain_max=[1.0, 1.0, 1.0],
-             force_amp=[0.0, 0.0, 0.0], force_period=0.0, fixed_dt=0.0)
+             force_amp=[0.0, 0.0, 0.0], force_period=0.0, fixed_dt=0.0, scheme=0, art_alpha=0.02)
     p.update(kw)
     return p
 

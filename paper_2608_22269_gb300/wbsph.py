@@ -49,7 +49,8 @@ class Config(C.Structure):
                 ("force_amp", C.c_double * 3), ("force_period", C.c_double),
                 ("fixed_dt", C.c_double), ("precision", C.c_int), ("device", C.c_int),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("water_height", C.c_double)]
+                ("alloc_ctx", C.c_void_p), ("water_height", C.c_double), ("scheme", C.c_int),
+                ("art_alpha", C.c_double)]
 
 
 class Stats(C.Structure):

@@ -61,6 +61,16 @@ def test_create_rejects_bad_configs_without_a_gpu(lib):
     cfg.eos = 0
     cfg.domain_max[0] = cfg.domain_min[0]
     assert L.wbsph_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    cfg.domain_max[0] = 1.0
+    assert cfg.scheme == 0 and cfg.art_alpha == 0.02
+    cfg.scheme = 2
+    assert L.wbsph_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    # the conventional foil: FP64 only, no delta-SPH, shifting or TIC
+    cfg.scheme = 1
+    assert L.wbsph_create(ctypes.byref(cfg), ctypes.byref(h)) == -1  # defaults have them on
+    cfg.use_delta = cfg.use_pst = cfg.use_tic = 0
+    cfg.precision = 1
+    assert L.wbsph_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
     assert L.wbsph_step(None, 1) == -1
 
 
