@@ -40,10 +40,11 @@ class Config(C.Structure):
                 ("domain_min", C.c_double * 3), ("domain_max", C.c_double * 3),
                 ("force_amp", C.c_double * 3), ("force_period", C.c_double),
                 ("fixed_dt", C.c_double), ("umax_override", C.c_double),
-                ("scheme", C.c_int), ("art_alpha", C.c_double)]
+                ("scheme", C.c_int), ("art_alpha", C.c_double), ("wall_bc", C.c_int),
+                ("body_u", C.c_double * 3)]
 
 # parameters with defaults when a parameter set does not name them
-_DEFAULTS = {"umax_override": -1.0, "scheme": 0, "art_alpha": 0.02}
+_DEFAULTS = {"umax_override": -1.0, "scheme": 0, "art_alpha": 0.02, "wall_bc": 0, "body_u": [0.0, 0.0, 0.0]}
 
 
 _lock = threading.Lock()

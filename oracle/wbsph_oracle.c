@@ -22,6 +22,7 @@
 
 #define FLUID 0
 #define DUMMY 1
+#define BODY 2
 
 static const double PI = 3.14159265358979323846;
 
@@ -44,6 +45,7 @@ static int valid_config(const orc_config* c) {
     if (!(c->domain_max[k] > c->domain_min[k])) return 0;
   if (c->scheme != 0 && c->scheme != 1) return 0;
   if (c->scheme == 1 && (c->use_delta || c->use_pst || c->use_tic || c->art_alpha < 0)) return 0;
+  if (c->wall_bc != 0 && c->wall_bc != 1) return 0;
   return 1;
 }
 
@@ -415,12 +417,15 @@ static void small_inverse(int d, const double* a, double* inv, double* det) {
 }
 
 /* ---------------------------------------------------------------------------
- * Dummy wall particles (Sec. 2.4): each dummy takes the potential of its
- * nearest fluid particle f within 2h shifted by the body force, Eq. (phiBn),
- * phi_d = phi_f + G . (x_d - x_f), and the slip velocity
- * U_d = U_f - (U_f . n_d) n_d. Ties in distance go to the smallest index;
- * a dummy with no fluid particle within 2h keeps its values (it then lies in
- * no fluid particle's support).
+ * Wall particles (Sec. 2.4): each dummy (and body) particle takes the
+ * potential of its nearest fluid particle f within 2h shifted by the body
+ * force, Eq. (phiBn), phi_d = phi_f + G . (x_d - x_f), and with the wall
+ * velocity U_w (zero for fixed walls, body_u for body particles) the slip
+ * velocity U_d = U_f - ((U_f - U_w) . n_d) n_d (the paper's choice, stated
+ * there for a fixed wall) or the no-slip velocity of Eq. (velBn),
+ * U_d = 2 U_w - U_f. Ties in distance go to the smallest index; a wall
+ * particle with no fluid particle within 2h keeps its values (it then lies
+ * in no fluid particle's support).
  * ------------------------------------------------------------------------- */
 static int dummy_update_csr(const orc_config* c, int64_t n, const double* x, double* u,
                             double* phi, const uint8_t* type, const double* normal, double t,
@@ -430,7 +435,7 @@ static int dummy_update_csr(const orc_config* c, int64_t n, const double* x, dou
   body_force(c, t, G);
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
-    if (type[i] != DUMMY) continue;
+    if (type[i] == FLUID) continue;
     int64_t best = -1;
     double best_r2 = 0.0;
     for (int64_t e = nb->row[i]; e < nb->row[i + 1]; ++e) {
@@ -444,13 +449,19 @@ static int dummy_update_csr(const orc_config* c, int64_t n, const double* x, dou
       if (best < 0 || r2 < best_r2) { best = j; best_r2 = r2; }
     }
     if (best < 0) continue;
+    double uw[3] = {0.0, 0.0, 0.0};
+    if (type[i] == BODY)
+      for (int k = 0; k < d; ++k) uw[k] = c->body_u[k];
     double gdot = 0.0, un = 0.0;
     for (int k = 0; k < d; ++k) {
       gdot += G[k] * (x[k * n + i] - x[k * n + best]);
-      un += u[k * n + best] * normal[k * n + i];
+      un += (u[k * n + best] - uw[k]) * normal[k * n + i];
     }
     phi[i] = phi[best] + gdot;
-    for (int k = 0; k < d; ++k) u[k * n + i] = u[k * n + best] - un * normal[k * n + i];
+    for (int k = 0; k < d; ++k) {
+      if (c->wall_bc == 1) u[k * n + i] = 2.0 * uw[k] - u[k * n + best];
+      else u[k * n + i] = u[k * n + best] - un * normal[k * n + i];
+    }
   }
   return ORC_OK;
 }
@@ -520,7 +531,7 @@ static void pair_sums_one(const orc_config* c, int64_t n, const double* x, const
       S[a] += 2.0 * (phistar - phi[i]) * gw[a] * vj;
       C[a] += (phi[j] + phi[i]) * gw[a] * vj;
       P[a] += shift * gw[a] * vj;
-      if (type[j] == FLUID) Lam[a] += (u[a * n + j] - u[a * n + i]) * rgw / r2 * vj;
+      if (type[j] == FLUID || c->wall_bc == 1) Lam[a] += (u[a * n + j] - u[a * n + i]) * rgw / r2 * vj;
     }
     D += 2.0 * (phi[j] - phi[i]) * rgw / r2 * vj;
   }
@@ -583,7 +594,7 @@ static void conventional_rates_one(const orc_config* c, int64_t n, const double*
       double duk = u[k * n + j] - u[k * n + i];
       gp[k] += (p_i + p_j) * gw[k] * vj;
       divu += duk * gw[k] * vj;
-      if (type[j] == FLUID) lam[k] += duk * rgw / r2 * vj;
+      if (type[j] == FLUID || c->wall_bc == 1) lam[k] += duk * rgw / r2 * vj;
       av[k] += rho_j * vj * pi_ij * gw[k];
     }
   }
@@ -766,6 +777,10 @@ int orc_time_step(const orc_config* c, int64_t n, const double* u, const uint8_t
   if (!valid_config(c) || n < 0) return ORC_E_INVAL;
   if (c->fixed_dt > 0) { *dt = c->fixed_dt; return ORC_OK; }
   double umax = fluid_umax(c, n, u, type);
+  double ub = 0.0; /* the prescribed body speed also bounds the step */
+  for (int k = 0; k < c->dim; ++k) ub += c->body_u[k] * c->body_u[k];
+  ub = sqrt(ub);
+  if (ub > umax) umax = ub;
   double t = c->dx / (c->c0 + umax);
   if (c->nu > 0) {
     double td = c->dx * c->dx / (2.0 * c->nu);
@@ -816,6 +831,8 @@ int orc_step(const orc_config* c, int64_t n, double* x, double* u, double* phi,
     rc = orc_stage_rates(c, n, x, u, phi, mass, type, normal, *t, ra, rp, rs, rl, NULL);
     if (rc) goto done;
     for (int64_t i = 0; i < n; ++i) {
+      if (type[i] == BODY) /* prescribed rigid translation, the same SSP-RK2 update */
+        for (int k = 0; k < d; ++k) x[k * n + i] = x0[k * n + i] + dt * c->body_u[k];
       if (type[i] != FLUID) continue;
       for (int k = 0; k < d; ++k) {
         x[k * n + i] = x0[k * n + i] + dt * (u0[k * n + i] + rs[k * n + i]);
@@ -827,6 +844,8 @@ int orc_step(const orc_config* c, int64_t n, double* x, double* u, double* phi,
     rc = orc_stage_rates(c, n, x, u, phi, mass, type, normal, *t + dt, ra, rp, rs, rl, NULL);
     if (rc) goto done;
     for (int64_t i = 0; i < n; ++i) {
+      if (type[i] == BODY)
+        for (int k = 0; k < d; ++k) x[k * n + i] = 0.5 * x0[k * n + i] + 0.5 * (x[k * n + i] + dt * c->body_u[k]);
       if (type[i] != FLUID) continue;
       for (int k = 0; k < d; ++k) {
         double x1 = x[k * n + i], u1 = u[k * n + i];

@@ -20,7 +20,8 @@
  *                        <div U>, <grad p>, <lap U>; artificial viscosity (Monaghan form)
  *
  * Layouts: positions, velocities and normals are structure-of-arrays,
- * component k of particle i at [k*n + i]. Types: 0 fluid, 1 dummy (wall).
+ * component k of particle i at [k*n + i]. Types: 0 fluid, 1 dummy (fixed wall),
+ * 2 body (a wall particle translating with the prescribed velocity body_u).
  * Every function returns 0 on success or a negative ORC_E_* code.
  */
 #ifndef WBSPH_ORACLE_H
@@ -68,6 +69,11 @@ typedef struct {
                               viscosity), the foil of the hydrostatic comparison; it
                               takes no delta-SPH, shifting or TIC */
   double art_alpha;        /* artificial-viscosity coefficient of the conventional scheme */
+  int wall_bc;             /* 0: slip walls (Sec. 2.4, the paper's choice); 1: no-slip walls,
+                              Eq. (velBn) U_d = 2 U_w - U_f, with the viscous interaction of
+                              fluid particles with wall particles included */
+  double body_u[3];        /* velocity of the moving wall particles (type 2): they translate
+                              rigidly with it, and it is their wall velocity U_w */
 } orc_config;
 
 /* Number of doubles per particle written by orc_pair_sums:

@@ -27,6 +27,7 @@ import numpy as np
 
 FLUID = 0
 DUMMY = 1
+BODY = 2  # wall particles of a rigid body translating with params["body_u"]
 
 
 @dataclasses.dataclass
@@ -68,7 +69,8 @@ def default_params(dim: int, dx: float, c0: float, **kw) -> dict:
              use_delta=0, use_pst=0, use_tic=0, use_visc=1,
              eos=0, tait_gamma=7.0,
              domain_min=[0.0, 0.0, 0.0], domain_max=[1.0, 1.0, 1.0],
-             force_amp=[0.0, 0.0, 0.0], force_period=0.0, fixed_dt=0.0, scheme=0, art_alpha=0.02)
+             force_amp=[0.0, 0.0, 0.0], force_period=0.0, fixed_dt=0.0, scheme=0, art_alpha=0.02,
+             wall_bc=0, body_u=[0.0, 0.0, 0.0])
     p.update(kw)
     return p
 
@@ -261,6 +263,43 @@ def sloshing_3d(dx=0.00769, tank=(4.0, 2.0, 2.0), depth=1.0, amp=0.01, period=1.
     kw.setdefault("use_tic", 1)
     return box_tank(3, tank, dx, lambda g_: g_[2] < depth, depth, name="sloshing_3d",
                     force_amp=[amp, 0.0, 0.0], force_period=period, **kw)
+
+
+def moving_body(dim: int = 2, dx: float = 0.01, tank=(1.0, 0.6), depth: float = 0.4,
+                body=(0.12, 0.12), center=(0.3, 0.2), body_u=(0.5, 0.0), **kw) -> Scene:
+    """A rigid rectangular (box-shaped in 3D) body of wall particles (type
+    BODY) translating with the prescribed velocity ``body_u`` through a tank
+    of water at rest: the tank of ``box_tank`` with the water up to ``depth``,
+    the body a solid block of lattice points (the fluid there removed), each
+    body particle's normal pointing out of the block towards its nearest face
+    (averaged over equally near faces). ``tank``, ``body``, ``center`` and
+    ``body_u`` have ``dim`` entries; the vertical axis is the last."""
+    tank, body, center, body_u = (tuple(v[:dim]) for v in (tank, body, center, body_u))
+    sc = box_tank(dim, tank, dx, lambda g_: g_[dim - 1] < depth, depth, name="moving_body",
+                  body_u=list(body_u) + [0.0] * (3 - dim), **kw)
+    lo = np.array([c - b / 2 for c, b in zip(center, body)])[:, None]
+    hi = np.array([c + b / 2 for c, b in zip(center, body)])[:, None]
+    inside = np.all((sc.x >= lo) & (sc.x <= hi), axis=0)
+    in_fluid = inside & (sc.type == FLUID)
+    keep = ~inside | (sc.type != FLUID)
+    bx = sc.x[:, in_fluid]
+    # outward normal: towards the nearest face(s) of the block
+    dist = np.concatenate([bx - lo, hi - bx])  # 2 dim rows: distance to each face
+    dmin = dist.min(axis=0)
+    near = np.isclose(dist, dmin[None, :], rtol=0, atol=1e-9 * dx)
+    sign = np.concatenate([-np.ones((dim, 1)), np.ones((dim, 1))])
+    nrm = np.zeros((dim, bx.shape[1]))
+    for k in range(2 * dim):
+        nrm[k % dim] += np.where(near[k], sign[k, 0], 0.0)
+    nrm /= np.sqrt((nrm * nrm).sum(axis=0))[None, :]
+    x = np.concatenate([sc.x[:, keep], bx], axis=1)
+    typ = np.concatenate([sc.type[keep], np.full(bx.shape[1], BODY, dtype=np.uint8)])
+    normal = np.concatenate([sc.normal[:, keep], nrm], axis=1)
+    u = np.zeros_like(x)
+    u[:, typ == BODY] = np.asarray(body_u, dtype=np.float64)[:, None]
+    phi = np.concatenate([sc.phi[keep], _hydrostatic_phi(bx, dim, 9.81, depth)])
+    return Scene(sc.params, np.ascontiguousarray(x), u, np.ascontiguousarray(phi), typ,
+                 np.ascontiguousarray(normal), "moving_body", depth)
 
 
 def jitter(scene: Scene, amount: float, seed: int = 2026, fluid_only: bool = True) -> Scene:
