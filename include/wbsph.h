@@ -110,6 +110,13 @@ typedef struct {
   double art_alpha;         /* conventional scheme: artificial-viscosity coefficient alpha of
                                Pi_ij = -alpha h C0 (U_ij.x_ij) / (rho_ij (r^2 + 0.01 h^2)) for
                                approaching pairs (default 0.02) */
+  int wall_bc;              /* 0 (default): slip walls, U_d = U_f - ((U_f - U_w).n_d) n_d, viscous
+                               interaction with fluid neighbours only (the paper's choice,
+                               Sec. 2.4); 1: no-slip walls, U_d = 2 U_w - U_f (Eq. velBn), wall
+                               particles included in the viscous sum */
+  double body_u[3];         /* velocity of the body particles (type 2): they translate rigidly
+                               with it and it is their wall velocity U_w (fixed walls: U_w = 0);
+                               its magnitude also bounds the time step */
 } wbsph_config;
 
 typedef enum { WBSPH_SCHEME_WB = 0, WBSPH_SCHEME_CONVENTIONAL = 1 } wbsph_scheme;
@@ -141,7 +148,7 @@ int wbsph_create(const wbsph_config* cfg, wbsph_handle* out);
 
 /* Load n particles (Sec. 2.4: fluid and dummy). x, u, normal: dim*n SoA;
  * phi: n; mass: n or NULL (then m = rho(phi) dx^dim, the initial density
- * times the particle volume); type: n bytes (0 fluid, 1 dummy); normal may
+ * times the particle volume); type: n bytes (0 fluid, 1 dummy wall, 2 body wall); normal may
  * be NULL when there are no dummies. Sets t = 0. */
 int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, const double* u,
                         const double* phi, const double* mass, const uint8_t* type,

@@ -12,6 +12,7 @@ namespace wbsph {
 
 constexpr int kFluid = 0;
 constexpr int kDummy = 1;
+constexpr int kBody = 2;  // wall particle of the rigid body translating with Params::body_u
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 // Device status word bits (read by the host at synchronising calls).
@@ -62,6 +63,9 @@ struct Params {
   int scheme;          // 0 well-balanced, 1 conventional WCSPH (the hydrostatic foil)
   double art_ahc0;     // conventional scheme: alpha h C0 of the artificial viscosity
   double avis_eps2;    // 0.01 h^2
+  int wall_bc;         // 0 slip walls, 1 no-slip walls (Eq. velBn)
+  double body_u[3];    // velocity of the body particles
+  double body_speed;   // |body_u|: bounds the time step
 };
 
 // Device arrays of one particle-state buffer.

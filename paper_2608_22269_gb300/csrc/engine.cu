@@ -216,6 +216,13 @@ static int derive_params(wbsph_s* h) {
   p.water_height = c.water_height;
   p.phs0 = std::sqrt(c.g[0] * c.g[0] + c.g[1] * c.g[1] + c.g[2] * c.g[2]) * c.water_height;
   p.scheme = c.scheme;
+  p.wall_bc = c.wall_bc;
+  p.body_speed = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    p.body_u[k] = k < c.dim ? c.body_u[k] : 0.0;
+    p.body_speed += p.body_u[k] * p.body_u[k];
+  }
+  p.body_speed = std::sqrt(p.body_speed);
   p.art_ahc0 = c.art_alpha * p.h * c.c0;
   p.avis_eps2 = 0.01 * p.h * p.h;
   int64_t ncells = 1;
@@ -288,6 +295,7 @@ static int validate(const wbsph_config* c, wbsph_s* h) {
     return fail(h, WBSPH_E_INVAL, "alloc and free hooks must be given together");
   if (c->scheme != WBSPH_SCHEME_WB && c->scheme != WBSPH_SCHEME_CONVENTIONAL)
     return fail(h, WBSPH_E_INVAL, "unknown scheme");
+  if (c->wall_bc != 0 && c->wall_bc != 1) return fail(h, WBSPH_E_INVAL, "wall_bc must be 0 (slip) or 1 (no-slip)");
   if (c->scheme == WBSPH_SCHEME_CONVENTIONAL &&
       (c->precision != WBSPH_FP64 || c->use_delta || c->use_pst || c->use_tic || !(c->art_alpha >= 0)))
     return fail(h, WBSPH_E_INVAL, "the conventional scheme runs in FP64 without delta-SPH, shifting or TIC");
@@ -444,13 +452,13 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
   for (int64_t i = 0; i < n; ++i) {
     const uint8_t v = ty[i];
     nf += v == 0;
-    nd += v == 1;
-    bad += v > 1;
+    nd += v == 1 || v == 2;  // wall particles: fixed dummies and body particles
+    bad += v > 2;
   }
   if (bad) {
     int64_t i = 0;
-    while (ty[i] <= 1) ++i;
-    return fail(h, WBSPH_E_INVAL, "particle %lld has type %d (0 fluid, 1 dummy)", (long long)i, ty[i]);
+    while (ty[i] <= 2) ++i;
+    return fail(h, WBSPH_E_INVAL, "particle %lld has type %d (0 fluid, 1 dummy, 2 body)", (long long)i, ty[i]);
   }
   if (nd > 0 && !normal) return fail(h, WBSPH_E_INVAL, "dummy particles need normals");
   h->loaded = false;

@@ -379,12 +379,13 @@ void launch_cell_bounds(const Params& p, const Work& w, int64_t n, cudaStream_t 
 // pass runs over fluid particles only).
 // ---------------------------------------------------------------------------
 constexpr int CMP_THREADS = 1024;
+constexpr uint8_t kAnyWall = 255;  // `want` of the compaction: every non-fluid particle
 
 __global__ void __launch_bounds__(CMP_THREADS) k_count_type(const uint8_t* __restrict__ type, int64_t n,
                                                            uint8_t want, uint32_t* __restrict__ cnt) {
   __shared__ uint32_t wsum[CMP_THREADS / 32];
   int64_t i = blockIdx.x * (int64_t)CMP_THREADS + threadIdx.x;
-  bool f = i < n && type[i] == want;
+  bool f = i < n && (want == kAnyWall ? type[i] != kFluid : type[i] == want);
   unsigned b = __ballot_sync(0xffffffffu, f);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(b);
   __syncthreads();
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(CMP_THREADS) k_write_type(const uint8_t* __res
   __shared__ uint32_t wsum[CMP_THREADS / 32];
   int64_t i = blockIdx.x * (int64_t)CMP_THREADS + threadIdx.x;
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  bool f = i < n && type[i] == want;
+  bool f = i < n && (want == kAnyWall ? type[i] != kFluid : type[i] == want);
   unsigned b = __ballot_sync(0xffffffffu, f);
   if (lane == 0) wsum[warp] = __popc(b);
   __syncthreads();
@@ -436,9 +437,9 @@ void launch_fluid_list(const Params& p, const State& s, const Work& w, int64_t n
   *launches += 3;
   if (compact) {
     k_cell_lower_bounds<<<(unsigned)div_up(p.ncells + 1, 256), 256, 0, st>>>(w.fkey, nf, p.ncells, w.fcell_lb);
-    k_count_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kDummy, w.block_cnt);
+    k_count_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, kAnyWall, w.block_cnt);
     k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(w.block_cnt, nb);
-    k_write_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, (uint8_t)kDummy, w.block_cnt, w.dummy_list,
+    k_write_type<<<(unsigned)nb, CMP_THREADS, 0, st>>>(s.type, n, kAnyWall, w.block_cnt, w.dummy_list,
                                                         nullptr, nullptr, nullptr, nullptr);
     *launches += 4;
   }

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(128) k_pair_conventional(Params p, State s, Wo
     double pij = 0.0;
     if (dun < 0.0) pij = -p.art_ahc0 * dun / (0.5 * (rho_i + w.rho[j]) * (r2 + p.avis_eps2));
     const double rho_j = w.rho[j];
-    const bool fluid_j = s.type[j] == kFluid;
+    const bool fluid_j = p.wall_bc || s.type[j] == kFluid;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       gp[c] += pp * g * r[c];

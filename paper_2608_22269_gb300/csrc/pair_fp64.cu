@@ -20,7 +20,8 @@ namespace wbsph {
 //   M  += (U_j - U_i) (x) g r             (continuity, corrected in the epilogue)
 //   C  += (phi_i + phi_j) g r             (conservative gradient, TIC branch)
 //   D  += (phi_j - phi_i) g               (delta-SPH: (x_j-x_i).grad W/|r|^2 V_j = g)
-//   Lam+= (U_j - U_i) g, fluid j only     (Laplacian operator, Sec. 2.1/2.4)
+//   Lam+= (U_j - U_i) g, fluid j only     (Laplacian operator, Sec. 2.1/2.4;
+//                                          every j with no-slip walls)
 //   P  += [1 + R (W_ij / W(dx))^n] g r    (shifting)
 // ---------------------------------------------------------------------------
 constexpr int PAIR_THREADS = 128;
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, 4)
       for (int e = 0; e < DIM; ++e) M[c * DIM + e] = fma(du[c], gr[e], M[c * DIM + e]);
     }
     D = fma(dphi, g, D);
-    if (s.type[j] == kFluid) {
+    if (p.wall_bc || s.type[j] == kFluid) {
 #pragma unroll
       for (int c = 0; c < DIM; ++c) Lam[c] = fma(du[c], g, Lam[c]);
     }

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
       for (int d2 = 0; d2 < DIM; ++d2) M[c * DIM + d2].add(du[c] * gr[d2]);
     }
     D.add(dphi * g);
-    if (Bjw > 0.f) {
+    if (Bjw > 0.f || p.wall_bc) {
 #pragma unroll
       for (int c = 0; c < DIM; ++c) Lam[c].add(du[c] * g);
     }

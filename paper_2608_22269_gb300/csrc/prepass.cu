@@ -84,13 +84,20 @@ __global__ void __launch_bounds__(DUM_THREADS) k_dummy_update(Params p, State s,
   }
   if (!active || best == kEmpty) return;
   double fs = forcing_factor(p, stage_time(w, stage2));
+  // wall velocity U_w: zero for fixed walls, body_u for body particles; slip
+  // U_d = U_f - ((U_f - U_w).n) n, or no-slip U_d = 2 U_w - U_f (Eq. velBn)
+  const bool body = s.type[i] == kBody;
   double gdot = 0.0, un = 0.0;
   for (int k = 0; k < p.dim; ++k) {
+    const double uw = body ? p.body_u[k] : 0.0;
     gdot += (p.g[k] + p.force_amp[k] * fs) * (s.x[k * n + i] - s.x[k * n + best]);
-    un += s.u[k * n + best] * s.normal[k * n + i];
+    un += (s.u[k * n + best] - uw) * s.normal[k * n + i];
   }
   s.phi[i] = s.phi[best] + gdot;
-  for (int k = 0; k < p.dim; ++k) s.u[k * n + i] = s.u[k * n + best] - un * s.normal[k * n + i];
+  for (int k = 0; k < p.dim; ++k) {
+    const double uw = body ? p.body_u[k] : 0.0;
+    s.u[k * n + i] = p.wall_bc == 1 ? 2.0 * uw - s.u[k * n + best] : s.u[k * n + best] - un * s.normal[k * n + i];
+  }
 }
 
 constexpr int PRE_THREADS = 256;
@@ -144,6 +151,7 @@ void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, i
 // Time step (Sec. 2.3): CFL * min(dx/(C0 + U_max), dx^2/(2 nu), sqrt(2 dx/|G|)).
 __global__ void k_time_step(Params p, Work w) {
   double umax = sqrt(__longlong_as_double((long long)*w.umax_bits));
+  if (p.body_speed > umax) umax = p.body_speed;  // a prescribed body also bounds the step
   double dt;
   if (p.fixed_dt > 0) {
     dt = p.fixed_dt;
@@ -199,7 +207,7 @@ __device__ __forceinline__ bool mx_nonfinite(double x) {
 // volume V = m / rho(phi) in FP32 (it only enters the FP32 pair sums); and the
 // packed FP32 copies read by the pair pass:
 //   A[i] = (x - cell origin, phi - phi_hs(x)), B[i] = (U, V) with V < 0 marking
-//   dummy particles (the Laplacian operator takes fluid neighbours only),
+//   wall particles (with slip walls the Laplacian operator takes fluid neighbours only),
 //   C[i] = cell coordinates packed 11/11/10 bits.
 // w.vol receives V widened to FP64.
 constexpr int MXP_THREADS = 256;

@@ -16,6 +16,7 @@ __global__ void k_rk_stage(Params p, State s, Work w, int64_t n, int stage) {
   if (stage == 2 && i == 0) w.scalars[0] = w.scalars[0] + dt;
   if (i >= n) return;
   bool fluid = s.type[i] == kFluid;
+  const bool body = s.type[i] == kBody;  // prescribed rigid translation, the same SSP-RK2 update
   if (stage == 1) {
     for (int k = 0; k < p.dim; ++k) {
       double x0 = s.x[k * n + i], u0 = s.u[k * n + i];
@@ -24,11 +25,16 @@ __global__ void k_rk_stage(Params p, State s, Work w, int64_t n, int stage) {
       if (fluid) {
         s.x[k * n + i] = x0 + dt * (u0 + w.dushift[k * n + i]);
         s.u[k * n + i] = u0 + dt * w.dudt[k * n + i];
+      } else if (body) {
+        s.x[k * n + i] = x0 + dt * p.body_u[k];
       }
     }
     double ph0 = s.phi[i];
     s.phi0[i] = ph0;
     if (fluid) s.phi[i] = ph0 + dt * w.dphidt[i];
+  } else if (body) {
+    for (int k = 0; k < p.dim; ++k)
+      s.x[k * n + i] = 0.5 * s.x0[k * n + i] + 0.5 * (s.x[k * n + i] + dt * p.body_u[k]);
   } else if (fluid) {
     for (int k = 0; k < p.dim; ++k) {
       double x1 = s.x[k * n + i], u1 = s.u[k * n + i];

@@ -50,7 +50,7 @@ class Config(C.Structure):
                 ("fixed_dt", C.c_double), ("precision", C.c_int), ("device", C.c_int),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("water_height", C.c_double), ("scheme", C.c_int),
-                ("art_alpha", C.c_double)]
+                ("art_alpha", C.c_double), ("wall_bc", C.c_int), ("body_u", C.c_double * 3)]
 
 
 class Stats(C.Structure):
