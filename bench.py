@@ -7,7 +7,7 @@ update) over the synthetic scene named by --workload, inputs resident in HBM.
 Prints ONE JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload dam3d|slosh3d] [--precision fp64|mixed]
+                  [--workload dam3d|slosh3d] [--precision fp64|mixed|df64]
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 project) on the host cores, on a bounded sample of the same workload.
@@ -49,6 +49,19 @@ FLOPS_PER_PAIR_MIXED_2D = 118
 # 1987 MHz): FP64 5.93e11 DFMA/s = 1.186 TFLOP/s; FP32 3.62e13 FFMA/s = 72.4
 FP64_PEAK_TFLOPS = 1.186
 FP32_PEAK_TFLOPS = 72.4
+# FP32 instructions of one pair in the double-float pass, all terms on (each
+# FADD, FMUL or FFMA is one operation on the FP32 pipe; two-sum 6, fast
+# two-sum 3, double-float product 8, raw product 4, accumulate 11): offsets 9,
+# |r|^2 31, 1/|r| 17, |r| 8, 1 - q/2 7, kernel factor 24, velocity
+# differences 24, g r 24, normal velocity 39, potential terms 27, L 90, S 45,
+# M 135, K 33, C 53, D 15, Lambda 45, shifting 96 (3D)
+OPS_PER_PAIR_DF_3D = 722
+OPS_PER_PAIR_DF_2D = 488
+# FP32 instruction rate of the FP32 pipe (one FFMA counts once)
+FP32_PEAK_TOPS = FP32_PEAK_TFLOPS / 2
+PRECISIONS = ("fp64", "mixed", "df64")
+DTYPES = {"fp64": "f64", "mixed": "f32 (Kahan-compensated sums) + f64 epilogue",
+          "df64": "f32x2 (double-float sums) + f64 epilogue"}
 
 WORKLOADS = {
     "dam3d": dict(
@@ -251,27 +264,33 @@ def time_path(scene, precision, args, world, local):
                  "sp0": sp0, "sp1": sp1, "clocks": clk.summary()}
 
 
-def pair_roofline(m, dim, nf, mixed, workload):
+def pair_roofline(m, dim, nf, precision, workload):
     pair_ms, pair_n = m["prof"]["pair"]
     pairs = m["sp1"]["pairs"] - m["sp0"]["pairs"]
     per_launch = pairs / max(pair_n, 1)
     avg_ms = pair_ms / max(pair_n, 1)
-    if mixed:
+    unit, pipe = "TFLOP/s", "FP64"
+    if precision == "mixed":
         fpp = FLOPS_PER_PAIR_MIXED_3D if dim == 3 else FLOPS_PER_PAIR_MIXED_2D
         flops = per_launch * fpp + nf * 600
-        peak, kernel, src = FP32_PEAK_TFLOPS, "k_pair_mixed<%d>" % dim, "pair_mixed.cu"
+        peak, kernel, src, pipe = FP32_PEAK_TFLOPS, "k_pair_mixed<%d>" % dim, "pair_mixed.cu", "FP32"
+    elif precision == "df64":
+        # FP32 operations of the pair terms only (the FP64 epilogue runs on the other pipe)
+        fpp = OPS_PER_PAIR_DF_3D if dim == 3 else OPS_PER_PAIR_DF_2D
+        flops = per_launch * fpp
+        peak, kernel, src, pipe = FP32_PEAK_TOPS, "k_pair_df<%d>" % dim, "pair_df64.cu", "FP32"
+        unit = "Top/s (FP32 instructions)"
     else:
         fpp = FLOPS_PER_PAIR_3D if dim == 3 else FLOPS_PER_PAIR_2D
         flops = per_launch * fpp + nf * FLOPS_EPILOGUE_3D
         peak, kernel, src = FP64_PEAK_TFLOPS, "k_pair_fp64<%d>" % dim, "pair_fp64.cu"
     achieved = flops / (avg_ms / 1e3) / 1e12
-    key = ("pair_mixed_" if mixed else "pair_fp64_") + workload
+    key = "pair_%s_%s" % (precision, workload)
     total = sum(v[0] for v in m["prof"].values())
     return {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 4), "peak": peak,
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "unit": unit, "frac": round(achieved / peak, 4),
             "traffic": profile_traffic(src, key),
-            "peak_source": ("measured %s FMA throughput of this GB300 (profiles/fp64_alu_peak.md)"
-                            % ("FP32" if mixed else "FP64")),
+            "peak_source": "measured %s FMA throughput of this GB300 (profiles/fp64_alu_peak.md)" % pipe,
             "pairs_per_launch": int(per_launch), "flops_per_pair": fpp,
             "avg_launch_ms": round(avg_ms, 4), "share_of_step": round(pair_ms / max(total, 1e-9), 4)}
 
@@ -431,10 +450,11 @@ def run_ours(args):
     dim = scene.params["dim"]
     nf = scene.n_fluid
     setup_s = time.perf_counter() - t_setup
-    primary_mixed = args.precision == "mixed"
-    sim, m = time_path(scene, wbsph.MIXED if primary_mixed else wbsph.FP64, args, world, local)
+    prec_code = {"fp64": wbsph.FP64, "mixed": wbsph.MIXED, "df64": wbsph.DF64}
+    primary = args.precision
+    sim, m = time_path(scene, prec_code[primary], args, world, local)
     value = weak_scaling_value(nf * args.steps, world, m["ms"] / 1e3)
-    roofline = pair_roofline(m, dim, nf, primary_mixed, args.workload)
+    roofline = pair_roofline(m, dim, nf, primary, args.workload)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -471,7 +491,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(m["ms"] / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[primary],
         "data": "synthetic",
         "config": {"workload": wl["desc"], "precision": args.precision, "n_fluid": nf,
                    "n_total": scene.n, "dim": dim,
@@ -489,26 +509,31 @@ def run_ours(args):
         "setup_s": round(setup_s, 1),
     }
     if not args.no_paths:
-        # the other precision on the same workload, and errors at this size
-        other = wbsph.FP64 if primary_mixed else wbsph.MIXED
-        sim2, m2 = time_path(scene, other, args, world, local)
-        v2 = nf * args.steps * world / (m2["ms"] / 1e3)
-        paths = {("fp64" if primary_mixed else "mixed"): {
-            "value": round(v2, 1), "ms_per_step": round(m2["ms"] / args.steps, 4),
-            "roofline": pair_roofline(m2, dim, nf, not primary_mixed, args.workload),
-            "hbm_frac": round(v2 / world * bytes_ps / (hbm * 1e9), 5)}}
+        # the other precisions on the same workload, and their errors at this
+        # size against the FP64 path on one common state
+        sims, paths = {primary: sim}, {}
+        for other in PRECISIONS:
+            if other == primary:
+                continue
+            sims[other], m2 = time_path(scene, prec_code[other], args, world, local)
+            v2 = nf * args.steps * world / (m2["ms"] / 1e3)
+            paths[other] = {"value": round(v2, 1), "ms_per_step": round(m2["ms"] / args.steps, 4),
+                            "dtype": DTYPES[other],
+                            "roofline": pair_roofline(m2, dim, nf, other, args.workload),
+                            "hbm_frac": round(v2 / world * bytes_ps / (hbm * 1e9), 5)}
         if rank == 0:
-            fp64 = sim2 if primary_mixed else sim
-            mixed = sim if primary_mixed else sim2
-            st = {k: mixed.get(k) for k in ("x", "u", "phi")}
-            fp64.set_particles(st["x"], st["u"], st["phi"], scene.type, scene.normal,
-                               mixed.get("mass"))
+            fp64 = sims["fp64"]
+            st = {k: fp64.get(k) for k in ("x", "u", "phi", "mass")}
+            line["error"] = {}
             fp64.eval_rates()
-            mixed.eval_rates()
-            diff = rates_diff(mixed, fp64, scene)
-            line["error"] = {"mixed_vs_fp64": diff,
-                             "fp64_vs_oracle": "within 1e-12 (tests/test_gpu_fullsize.py samples this workload)",
-                             "measure": "max|a-b| / max(max|b|, natural scale) over fluid particles"}
+            for other in ("mixed", "df64"):
+                o = sims[other]
+                o.set_particles(st["x"], st["u"], st["phi"], scene.type, scene.normal, st["mass"])
+                o.eval_rates()
+                line["error"][other + "_vs_fp64"] = rates_diff(o, fp64, scene)
+            line["error"].update({
+                "fp64_vs_oracle": "within 1e-12 (tests/test_gpu_fullsize.py samples this workload)",
+                "measure": "max|a-b| / max(max|b|, natural scale) over fluid particles"})
         if rank == 0:
             for key, dim in (("surrogate", 2), ("surrogate_3d", 3)):
                 try:
@@ -516,7 +541,9 @@ def run_ours(args):
                 except Exception as exc:  # the plain paths above are the headline; report, do not abort
                     paths[key] = {"error": f"{type(exc).__name__}: {exc}"}
         line["paths"] = paths
-        sim2.close()
+        for k, s2 in sims.items():
+            if k != primary:
+                s2.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = wl["sample"]()
         v, steps, secs, cores = cpu_baseline(sample)
@@ -562,7 +589,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dam3d", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true",
                     help="skip the second precision and the surrogate paths")

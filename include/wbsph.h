@@ -54,7 +54,20 @@ typedef enum {
   WBSPH_E_NOSYM = -10     /* feature not built into this library */
 } wbsph_status;
 
-typedef enum { WBSPH_FP64 = 0, WBSPH_MIXED = 1 } wbsph_precision;
+/* Arithmetic of the pair pass (the state x, U, phi is FP64 in every mode):
+ *  WBSPH_FP64  FP64 pair sums, the full potential (the reference arithmetic).
+ *  WBSPH_MIXED FP32 pair sums with Kahan compensation on cell-relative
+ *              offsets and the hydrostatic split phi - phi_hs (Eq. eqSol),
+ *              FP64 epilogue: about 1e-5 of the field scale.
+ *  WBSPH_DF64  double-float pair sums (pairs of FP32, about 48 bits) on
+ *              offsets in cell units and the same hydrostatic split, FP64
+ *              epilogue, the exact FP64 neighbour lists: FP64-level results
+ *              on the FP32 pipe.
+ * MIXED and DF64 need grids of at most 2048 x 2048 x 1024 cells
+ * (WBSPH_E_INVAL at the first stage otherwise) and set the domain status
+ * when a particle has moved more than half a cell since the last neighbour
+ * build (DF64). */
+typedef enum { WBSPH_FP64 = 0, WBSPH_MIXED = 1, WBSPH_DF64 = 2 } wbsph_precision;
 typedef enum { WBSPH_HOST = 0, WBSPH_DEVICE = 1 } wbsph_where;
 
 typedef enum {
@@ -100,7 +113,7 @@ typedef struct {
   wbsph_alloc_fn alloc;     /* NULL: cudaMallocAsync on cuda_stream */
   wbsph_free_fn free;
   void* alloc_ctx;
-  double water_height;      /* free-surface height H of the hydrostatic split (mixed path) */
+  double water_height;      /* free-surface height H of the hydrostatic split (mixed, df64) */
   int scheme;               /* WBSPH_SCHEME_WB (default): the well-balanced scheme, Eq. (sph);
                                WBSPH_SCHEME_CONVENTIONAL: conventional WCSPH (Sec. 2.1, Eq. nslag
                                with the printed operators, Eq. eos-water) plus artificial

@@ -66,6 +66,8 @@ struct Params {
   int wall_bc;         // 0 slip walls, 1 no-slip walls (Eq. velBn)
   double body_u[3];    // velocity of the body particles
   double body_speed;   // |body_u|: bounds the time step
+  float df_c0[2];      // double-float path: C0 and R_pst (alpha / W(dx))^4 as hi + lo
+  float df_pst_Ra4[2];
 };
 
 // Device arrays of one particle-state buffer.
@@ -112,10 +114,13 @@ struct Work {
   unsigned long long* pairs;  // [0]: neighbour pairs summed by pair passes (units of work)
   uint32_t* nbr;     // kmax * n_fluid: candidate lists, k-major (nbr[k * nf + gi])
   uint32_t* nbr_cnt; // n_fluid: candidates per fluid particle
-  float4* packA;     // n: mixed path, (cell-relative offset, phi - phi_hs) in FP32
-  float4* packB;     // n: mixed path, (U, +-V) in FP32
-  uint32_t* packC;   // n: mixed path, cell coordinates packed 11/11/10 bits
-  double* cell_origin;  // mixed path: domain_min[k] + i R for the cells of axis k, axes one after
+  float4* packA;     // n: mixed path, (cell-relative offset, phi - phi_hs) in FP32;
+                     //    double-float path, high parts of (offset / R, phi - phi_hs)
+  float4* packB;     // n: mixed path, (U, +-V) in FP32; double-float path, high parts of (U, +-volc)
+  uint32_t* packC;   // n: mixed and double-float paths, cell coordinates packed 11/11/10 bits
+  float4* packAl;    // n: double-float path, low parts of packA (packA/packB hold the high parts)
+  float4* packBl;    // n: double-float path, low parts of packB
+  double* cell_origin;  // mixed and double-float paths: domain_min[k] + i R for the cells of axis k, axes one after
                         // another (nc[0] + nc[1] + nc[2] entries)
 };
 
@@ -144,6 +149,10 @@ void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n,
                       int stage2, cudaStream_t st);
 int pair_list_kmax(int dim);
 void launch_lambda_fp64(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st);
+// ---- pair_df64.cu ----
+int launch_pack_df(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
+void launch_pair_df(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
+                    cudaStream_t st);
 // ---- pair_conventional.cu ----
 void launch_pair_conventional(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
                               int stage2, cudaStream_t st);

@@ -197,6 +197,14 @@ static int derive_params(wbsph_s* h) {
     p.pst_R_a4 = c.pst_R * a2 * a2;
   }
   p.pst_n = c.pst_n;
+  {
+    // double-float constants: hi = the nearest float, lo = the nearest float to the rest
+    const float c0h = (float)c.c0, pah = (float)p.pst_R_a4;
+    p.df_c0[0] = c0h;
+    p.df_c0[1] = (float)(c.c0 - (double)c0h);
+    p.df_pst_Ra4[0] = pah;
+    p.df_pst_Ra4[1] = (float)(p.pst_R_a4 - (double)pah);
+  }
   p.rho0 = c.rho0;
   p.c0 = c.c0;
   p.c0sq = c.c0 * c.c0;
@@ -287,7 +295,7 @@ static int validate(const wbsph_config* c, wbsph_s* h) {
   if (c->nu < 0 || !(c->cfl > 0)) return fail(h, WBSPH_E_INVAL, "nu >= 0 and cfl > 0 required");
   if (c->eos != 0 && c->eos != 1) return fail(h, WBSPH_E_INVAL, "eos must be 0 or 1");
   if (c->eos == 1 && !(c->tait_gamma > 1)) return fail(h, WBSPH_E_INVAL, "tait_gamma must exceed 1");
-  if (c->precision != WBSPH_FP64 && c->precision != WBSPH_MIXED)
+  if (c->precision != WBSPH_FP64 && c->precision != WBSPH_MIXED && c->precision != WBSPH_DF64)
     return fail(h, WBSPH_E_INVAL, "unknown precision");
   for (int k = 0; k < c->dim; ++k)
     if (!(c->domain_max[k] > c->domain_min[k])) return fail(h, WBSPH_E_INVAL, "empty domain on axis %d", k);
@@ -403,9 +411,13 @@ static int allocate(wbsph_s* h, int64_t n) {
     w.nbr_cnt = U32(nfl);
   }
   h->field_tmp = D(d * nn);
-  if (h->cfg.precision == WBSPH_MIXED) {
+  if (h->cfg.precision == WBSPH_MIXED || h->cfg.precision == WBSPH_DF64) {
     w.packA = (float4*)dev_alloc(h, nn * sizeof(float4));
     w.packB = (float4*)dev_alloc(h, nn * sizeof(float4));
+    if (h->cfg.precision == WBSPH_DF64) {
+      w.packAl = (float4*)dev_alloc(h, nn * sizeof(float4));
+      w.packBl = (float4*)dev_alloc(h, nn * sizeof(float4));
+    }
     w.packC = U32(nn);
     const size_t no = (size_t)h->P.nc[0] + h->P.nc[1] + h->P.nc[2];
     w.cell_origin = D(no);
@@ -539,14 +551,20 @@ static int rates(wbsph_s* h, int stage2) {
   const int64_t n = h->n;
   cudaStream_t st = h->stream;
   const bool mixed = h->cfg.precision == WBSPH_MIXED;
+  const bool dfp = h->cfg.precision == WBSPH_DF64;
   {
     // dummy walls, then V and U_max (FP64 path) or V, U_max and the packed
-    // FP32 copies in one kernel (mixed path)
+    // FP32 copies in one kernel (mixed path); the double-float path packs
+    // its hi/lo copies after the FP64 volumes
     ProfScope ps(h, WBSPH_K_PREPASS);
     launch_prepass(h->P, h->A, h->W, n, h->nd, stage2, st, !mixed);
     if (mixed) {
       int rc = launch_prepass_mixed(h->P, h->A, h->W, n, st);
       if (rc) return fail(h, rc, "mixed path: grid too large for packed cell coordinates");
+    }
+    if (dfp) {
+      int rc = launch_pack_df(h->P, h->A, h->W, n, st);
+      if (rc) return fail(h, rc, "df64 path: grid too large for packed cell coordinates");
     }
   }
   if (!stage2) {
@@ -560,10 +578,11 @@ static int rates(wbsph_s* h, int stage2) {
   {
     ProfScope ps(h, WBSPH_K_PAIR);
     if (mixed) launch_pair_mixed(h->P, h->A, h->W, n, h->nf, stage2, st);
+    else if (dfp) launch_pair_df(h->P, h->A, h->W, n, h->nf, stage2, st);
     else if (h->P.scheme == WBSPH_SCHEME_CONVENTIONAL) launch_pair_conventional(h->P, h->A, h->W, n, h->nf, stage2, st);
     else launch_pair_fp64(h->P, h->A, h->W, n, h->nf, stage2, st);
   }
-  h->launches += (n ? 1 : 0) + (h->nd ? 1 : 0) + (stage2 ? 0 : 1) + (h->nf ? 2 : 0);
+  h->launches += (n ? 1 : 0) + (h->nd ? 1 : 0) + (stage2 ? 0 : 1) + (h->nf ? 2 : 0) + (dfp && n ? 1 : 0);
   return check_launch(h, "stage rates");
 }
 

@@ -19,7 +19,7 @@ OK = 0
 ERRORS = {-1: "WBSPH_E_INVAL", -2: "WBSPH_E_NOMEM", -3: "WBSPH_E_CUDA", -4: "WBSPH_E_DOMAIN",
           -5: "WBSPH_E_SINGULAR", -6: "WBSPH_E_NAN", -7: "WBSPH_E_TIMEOUT", -8: "WBSPH_E_STATE",
           -9: "WBSPH_E_CAPACITY", -10: "WBSPH_E_NOSYM"}
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 HOST, DEVICE = 0, 1
 FIELDS = {"x": 0, "u": 1, "phi": 2, "rho": 3, "p": 4, "dudt": 5, "dphidt": 6, "dushift": 7,
           "lambda": 8, "mass": 9, "vol": 10}

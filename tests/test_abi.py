@@ -71,6 +71,11 @@ def test_create_rejects_bad_configs_without_a_gpu(lib):
     cfg.use_delta = cfg.use_pst = cfg.use_tic = 0
     cfg.precision = 1
     assert L.wbsph_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    cfg.precision = 2  # the double-float path runs the well-balanced scheme only
+    assert L.wbsph_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    cfg.scheme = 0
+    cfg.precision = 3  # FP64 = 0, MIXED = 1, DF64 = 2
+    assert L.wbsph_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
     assert L.wbsph_step(None, 1) == -1
 
 
