@@ -149,7 +149,7 @@ void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n,
                       int stage2, cudaStream_t st);
 int pair_list_kmax(int dim);
 void launch_lambda_fp64(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st);
-// ---- pair_df64.cu ----
+// ---- prepass.cu (double-float pack) and pair_df64.cu ----
 int launch_pack_df(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
 void launch_pair_df(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
                     cudaStream_t st);

@@ -20,70 +20,14 @@
 //  * The same exact FP64 neighbour lists as the FP64 pass, so both passes
 //    sum over the same pairs.
 // The shifting sum is split as P = K + P', P' = sum (f - 1) grad W V, so only
-// the shifting correction needs a separate accumulator.
+// the shifting correction needs a separate accumulator. The packed hi/lo
+// copies it reads are written per particle by k_pack_df (prepass.cu).
 #include "../../include/wbsph.h"
 #include "common.cuh"
 #include "df64.cuh"
 #include "physics.cuh"
 
 namespace wbsph {
-
-// ---- per-particle packing (after the FP64 prepass: dummy walls, V, volc, U_max) ----
-//   A  = (o_hi, phi'_hi)   Al = (o_lo, phi'_lo)
-//   B  = (U_hi, volc_hi)   Bl = (U_lo, volc_lo)   volc negated (both parts) for wall particles
-//   C  = cell coordinates packed 11/11/10 bits
-// with o = (x - cell origin) / R and o_hi = o rounded to a multiple of 2^-23;
-// |o| < 1.5 is required (a particle may drift only a fraction of a cell
-// from the cell of its last neighbour build), else the domain bit is set.
-constexpr int DFP_THREADS = 256;
-
-__global__ void __launch_bounds__(DFP_THREADS) k_pack_df(Params p, State s, Work w, int64_t n) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t key = w.key[i];
-  const uint32_t nx = (uint32_t)p.nc[0], ny = (uint32_t)p.nc[1];
-  const uint32_t ic[3] = {key % nx, (key / nx) % ny, key / (nx * ny)};
-  float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
-  float bh[4] = {0.f, 0.f, 0.f, 0.f}, bl[4] = {0.f, 0.f, 0.f, 0.f};
-  double phs = p.phs0;
-  bool bad = false, off = false;
-  const double* org = w.cell_origin;  // origins of axis 0, then 1, then 2
-  for (int k = 0; k < p.dim; ++k) {
-    const double xk = s.x[k * n + i], uk = s.u[k * n + i];
-    bad |= !isfinite(xk) || !isfinite(uk);
-    const double o = (xk - org[ic[k]]) / p.R;
-    org += p.nc[k];
-    off |= !(fabs(o) < 1.5);
-    const double q = rint(o * 8388608.0) * (1.0 / 8388608.0);  // multiple of 2^-23
-    ah[k] = (float)q;
-    al[k] = (float)(o - q);
-    bh[k] = (float)uk;
-    bl[k] = (float)(uk - (double)bh[k]);
-    if (p.g[k] != 0.0) phs = fma(p.g[k], xk, phs);
-  }
-  const double phi = s.phi[i];
-  bad |= !isfinite(phi);
-  const double ph = phi - phs;
-  ah[3] = (float)ph;
-  al[3] = (float)(ph - (double)ah[3]);
-  const double v = s.type[i] == kFluid ? w.volc[i] : -w.volc[i];
-  bh[3] = (float)v;
-  bl[3] = (float)(v - (double)bh[3]);
-  if (bad) atomicOr(w.status, kStatNaN);
-  if (off) atomicOr(w.status, kStatDomain);
-  w.packA[i] = make_float4(ah[0], ah[1], ah[2], ah[3]);
-  w.packAl[i] = make_float4(al[0], al[1], al[2], al[3]);
-  w.packB[i] = make_float4(bh[0], bh[1], bh[2], bh[3]);
-  w.packBl[i] = make_float4(bl[0], bl[1], bl[2], bl[3]);
-  w.packC[i] = ic[0] | (ic[1] << 11) | (ic[2] << 22);
-}
-
-int launch_pack_df(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st) {
-  if (n == 0) return 0;
-  if (p.nc[0] > 2048 || p.nc[1] > 2048 || p.nc[2] > 1024) return WBSPH_E_INVAL;
-  k_pack_df<<<(unsigned)div_up(n, DFP_THREADS), DFP_THREADS, 0, st>>>(p, s, w, n);
-  return 0;
-}
 
 // ---------------------------------------------------------------------------
 // Double-float pair pass over fluid particles (one lane per particle i), in
@@ -102,6 +46,41 @@ constexpr int DF_THREADS = 128;
 #ifndef WBSPH_DF_MIN_BLOCKS
 #define WBSPH_DF_MIN_BLOCKS 3  // resident blocks per SM the register budget is sized for
 #endif
+#ifndef WBSPH_DF_RING
+#define WBSPH_DF_RING 2  // list entries of each lane in flight (shared-memory ring)
+#endif
+constexpr int DF_RING = WBSPH_DF_RING;
+
+// Asynchronous global -> shared copies (cp.async, cached in L1), one group
+// per list entry; a thread waits only for its own groups.
+__device__ __forceinline__ void df_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void df_cp4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void df_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void df_wait_ring() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(DF_RING - 1) : "memory");
+}
+
+// FP64 value of a float, widened exactly on the IEEE fields with integer
+// instructions (the FP64 pipe keeps only the additions of the epilogue);
+// zero and subnormal floats give zero (below 2^-126, far under the
+// accuracy of any sum here), infinities and NaN stay non-finite.
+__device__ __forceinline__ double df_f2d(float v) {
+  const unsigned b = __float_as_uint(v), e = (b >> 23) & 0xFFu;
+  if (e == 0u) return 0.0;
+  const unsigned ed = e == 0xFFu ? 0x7FFu : e + (1023u - 127u);
+  return __hiloint2double((int)((b & 0x80000000u) | (ed << 20) | ((b & 0x7FFFFFu) >> 3)), (int)(b << 29));
+}
+
+// hi + lo of a double-float in FP64: one rounding of the exact sum
+__device__ __forceinline__ double df_val(df a) { return df_f2d(a.hi) + df_f2d(a.lo); }
 
 template <int DIM>
 __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
@@ -146,11 +125,34 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
   unsigned npairs = 0;
   const int maxc = __reduce_max_sync(0xffffffffu, cnt);
   const uint32_t* lst = w.nbr + gi;
+  // The packed data of list entries k + 1 .. k + DF_RING - 1 is gathered
+  // (cp.async into this lane's slots of a shared-memory ring) while entry k
+  // is summed, so the gathers do not hold registers and their latency is
+  // covered by the arithmetic of the entries before them.
+  __shared__ float4 ringA[DF_RING * DF_THREADS], ringAl[DF_RING * DF_THREADS];
+  __shared__ float4 ringB[DF_RING * DF_THREADS], ringBl[DF_RING * DF_THREADS];
+  __shared__ uint32_t ringC[DF_RING * DF_THREADS];
+  const int tid = threadIdx.x;
+  auto fetch = [&](int k, uint32_t j) {  // entry k (< cnt), neighbour j, into slot k % DF_RING
+    const int q = (k % DF_RING) * DF_THREADS + tid;
+    df_cp16(&ringA[q], A + j);
+    df_cp16(&ringAl[q], Al + j);
+    df_cp16(&ringB[q], B + j);
+    df_cp16(&ringBl[q], Bl + j);
+    df_cp4(&ringC[q], Cc + j);
+  };
+#pragma unroll
+  for (int k = 0; k < DF_RING; ++k) {  // one group per entry (empty past the list)
+    if (k < cnt) fetch(k, __ldg(lst + (int64_t)k * nf));
+    df_commit();
+  }
+  uint32_t jn = DF_RING < cnt ? __ldg(lst + (int64_t)DF_RING * nf) : 0u;  // next entry to fetch
   for (int k = 0; k < maxc; ++k) {
     if (k >= cnt) continue;
-    const uint32_t j = __ldg(lst + (int64_t)k * nf);
-    const float4 Aj = __ldg(A + j), Alj = __ldg(Al + j), Bj = __ldg(B + j), Blj = __ldg(Bl + j);
-    const uint32_t cj = __ldg(Cc + j);
+    df_wait_ring();  // entry k's group has landed; the later ones may still be in flight
+    const int q = (k % DF_RING) * DF_THREADS + tid;
+    const float4 Aj = ringA[q], Alj = ringAl[q], Bj = ringB[q], Blj = ringBl[q];
+    const uint32_t cj = ringC[q];
     ++npairs;  // every list entry is an exact neighbour (k_nbr_list applies the FP64 test)
     // r / R: the high part (cell offset plus a difference of multiples of
     // 2^-23, below 2 in magnitude) is exact; the low parts round once
@@ -177,7 +179,6 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
       }
       r2 = df_fast_two_sum(hi, lo);
     }
-    if (!(r2.hi > 0.f)) continue;
     // R / |r|: FP32 estimate, a Newton-Raphson step y <- y (3 - r2 y^2) / 2 in
     // FP32 and one in double-float, y <- y + (y/2)(1 - r2 y^2), with the
     // residual 1 - r2 y^2 (near 2^-23) formed from exact products
@@ -206,6 +207,16 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
     du[0] = df_sub_raw({Bj.x, Blj.x}, ui[0]);
     du[1] = df_sub_raw({Bj.y, Blj.y}, ui[1]);
     if (DIM == 3) du[DIM - 1] = df_sub_raw({Bj.z, Blj.z}, ui[DIM - 1]);
+    const df phij = {Aj.w, Alj.w};
+    const df dphi = df_sub_raw(phij, phii);
+    // the slot is refilled with entry k + DF_RING only after every value
+    // read from it has been used above
+    if (k + DF_RING < cnt) {
+      fetch(k + DF_RING, jn);
+      if (k + DF_RING + 1 < cnt) jn = __ldg(lst + (int64_t)(k + DF_RING + 1) * nf);
+    }
+    df_commit();
+    if (!(r2.hi > 0.f)) continue;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) gr[c] = df_mul(g, r[c]);
     // (U_j - U_i).r / |r|
@@ -220,8 +231,6 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
       }
       dun = df_mul(df_norm(pd), inv);
     }
-    const df phij = {Aj.w, Alj.w};
-    const df dphi = df_sub_raw(phij, phii);
     df rs = dphi;  // phi'_j - phi'_i - C0 (U_j - U_i).r/|r|: 2 (phi* - phi_i) of Eq. lfsover
     df_acc(rs, df_neg(df_mul(c0, dun)));
     if (DIM == 2) {
@@ -285,7 +294,7 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
   const double R = p.R, R2 = R * R;
   double Ld[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-  for (int k = 0; k < NL; ++k) Ld[k] = R2 * df_to_double(L[k]);
+  for (int k = 0; k < NL; ++k) Ld[k] = R2 * df_val(L[k]);
   bool tic_branch = false;
   if (p.use_tic) {
     const float lf = DIM == 2 ? lambda_min_2f((float)Ld[0], (float)Ld[1], (float)Ld[2])
@@ -304,7 +313,7 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
   for (int k = 0; k < NL; ++k) w.Lmat[k * n + i] = Ld[k];
   double Kd[DIM];
 #pragma unroll
-  for (int c = 0; c < DIM; ++c) Kd[c] = R * df_to_double(K[c]);
+  for (int c = 0; c < DIM; ++c) Kd[c] = R * df_val(K[c]);
   const double fs = forcing_factor(p, stage_time(w, stage2));
   double acc[DIM], divu = 0.0;
   if (tic_branch) {
@@ -321,42 +330,47 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
       double lg = 0.0;
 #pragma unroll
       for (int e = 0; e < DIM; ++e) lg = fma(Lm[c][e], p.g[e], lg);
-      const double gradphi = R * df_to_double(Cs[c]) + 2.0 * phs * Kd[c] + lg;
+      const double gradphi = R * df_val(Cs[c]) + 2.0 * phs * Kd[c] + lg;
       acc[c] = -gradphi + p.g[c] + p.force_amp[c] * fs;
-      divu += R * df_to_double(M[c * DIM + c]);
+      divu += R * df_val(M[c * DIM + c]);
     }
   } else {
     // grad phi = L^-1 S' + G, so -grad phi + G(t) = -L^-1 S' + A omega^2 sin(omega t)
     double inv[DIM][DIM];
     const bool ok = sym_inverse<DIM>(Ld, inv);
     if (!ok) atomicOr(w.status, kStatSingular);
+    // the factor R of S' = R Sh and M = R Mh is applied to the contractions
+    double Sd[DIM];
+#pragma unroll
+    for (int e = 0; e < DIM; ++e) Sd[e] = df_val(S[e]);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       double gs = 0.0;
 #pragma unroll
       for (int e = 0; e < DIM; ++e) {
-        gs = fma(inv[c][e], R * df_to_double(S[e]), gs);
-        divu = fma(inv[c][e], R * df_to_double(M[c * DIM + e]), divu);
+        gs = fma(inv[c][e], Sd[e], gs);
+        divu = fma(inv[c][e], df_val(M[c * DIM + e]), divu);
       }
       // a singular L zeroes the inverse: grad phi = 0, as in the FP64 pass
-      acc[c] = -gs + (ok ? 0.0 : p.g[c]) + p.force_amp[c] * fs;
+      acc[c] = -R * gs + (ok ? 0.0 : p.g[c]) + p.force_amp[c] * fs;
     }
+    divu *= R;
   }
   const double umax = sqrt(__longlong_as_double((long long)*w.umax_bits));
   bool bad = false;
   double dstar[DIM], dn2 = 0.0, gk = 0.0;
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
-    const double visc = p.use_visc ? 2.0 * p.nu * df_to_double(Lam[c]) : 0.0;
+    const double visc = p.use_visc ? 2.0 * p.nu * df_val(Lam[c]) : 0.0;
     const double a = acc[c] + visc;
     w.dudt[c * n + i] = a;
     bad |= !isfinite(a);
-    const double P = p.use_pst ? Kd[c] + R * df_to_double(Pp[c]) : 0.0;
+    const double P = p.use_pst ? Kd[c] + R * df_val(Pp[c]) : 0.0;
     dstar[c] = -2.0 * p.h * umax * P;
     dn2 += dstar[c] * dstar[c];
     gk = fma(p.g[c], Kd[c], gk);
   }
-  const double diff = p.use_delta ? p.delta_h_c0 * (2.0 * (df_to_double(D) + gk)) : 0.0;
+  const double diff = p.use_delta ? p.delta_h_c0 * (2.0 * (df_val(D) + gk)) : 0.0;
   const double dphidt = -eos_c2(p, s.phi[i]) * divu + diff;
   w.dphidt[i] = dphidt;
   bad |= !isfinite(dphidt);

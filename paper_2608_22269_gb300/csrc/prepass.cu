@@ -1,6 +1,7 @@
 // prepass.cu -- per-stage work before the pair pass: the dummy wall update
-// (Sec. 2.4), particle volumes and U_max, the time step (Sec. 2.3), and the
-// packed FP32 copies of the mixed path.
+// (Sec. 2.4), particle volumes and U_max, the time step (Sec. 2.3), the
+// packed FP32 copies of the mixed path and the hi/lo copies of the
+// double-float path.
 #include "../../include/wbsph.h"
 #include "common.cuh"
 #include "neighbor_iter.cuh"
@@ -278,6 +279,76 @@ int launch_prepass_mixed(const Params& p, const State& s, const Work& w, int64_t
   if (p.nc[0] > 2048 || p.nc[1] > 2048 || p.nc[2] > 1024) return WBSPH_E_INVAL;
   k_prepass_mixed<<<(unsigned)div_up(n, MXP_THREADS), MXP_THREADS, 0, st>>>(p, s, w, n, w.packA, w.packB,
                                                                             w.packC);
+  return 0;
+}
+
+// ---- pack of the double-float path, per particle (after the FP64 prepass:
+// dummy walls, V, volc, U_max) ----
+//   A  = (o_hi, phi'_hi)   Al = (o_lo, phi'_lo)
+//   B  = (U_hi, volc_hi)   Bl = (U_lo, volc_lo)   volc negated (both parts) for wall particles
+//   C  = cell coordinates packed 11/11/10 bits
+// o = (x - cell origin) / R in cell units. o_hi is o rounded to a multiple of
+// 2^-23 by adding and subtracting 1.5 * 2^29 (its ulp is 2^-23, exact for
+// |o| < 2^28), an FP32 number for |o| < 2; |o| < 1.5 is required (a
+// particle may drift half a cell out of the cell of its last neighbour
+// build), else the domain bit is set. The other hi parts are the nearest
+// FP32 numbers; each lo part is the FP64 remainder (exact: Sterbenz's
+// lemma) rounded to FP32. The moves between FP64 and FP32 are integer
+// instructions, so the FP64 pipe only does the additions.
+constexpr int DFP_THREADS = 256;
+
+__device__ __forceinline__ void df_split(double v, float& hi, float& lo) {
+  hi = mx_d2f(v);
+  lo = mx_d2f(v - mx_f2d(hi));
+}
+
+__global__ void __launch_bounds__(DFP_THREADS) k_pack_df(Params p, State s, Work w, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t key = w.key[i];
+  const uint32_t nx = (uint32_t)p.nc[0], ny = (uint32_t)p.nc[1];
+  const uint32_t ic[3] = {key % nx, (key / nx) % ny, key / (nx * ny)};
+  float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+  float bh[4] = {0.f, 0.f, 0.f, 0.f}, bl[4] = {0.f, 0.f, 0.f, 0.f};
+  constexpr double kRound23 = 805306368.0;  // 1.5 * 2^29
+  double phs = p.phs0;
+  bool bad = false, off = false;
+  const double* org = w.cell_origin;  // origins of axis 0, then 1, then 2
+  for (int k = 0; k < p.dim; ++k) {
+    const double xk = s.x[k * n + i], uk = s.u[k * n + i];
+    bad |= mx_nonfinite(xk) | mx_nonfinite(uk);
+    const double o = (xk - __ldg(org + ic[k])) * p.inv_two_h;  // 1 / R
+    org += p.nc[k];
+    off |= !(fabs(o) < 1.5);
+    const double q = __dsub_rn(__dadd_rn(o, kRound23), kRound23);  // multiple of 2^-23
+    ah[k] = mx_d2f(q);                            // exact
+    al[k] = mx_d2f(o - q);
+    df_split(uk, bh[k], bl[k]);
+    if (p.g[k] != 0.0) phs = fma(p.g[k], xk, phs);
+  }
+  const double phi = s.phi[i];
+  bad |= mx_nonfinite(phi);
+  df_split(phi - phs, ah[3], al[3]);
+  df_split(w.volc[i], bh[3], bl[3]);
+  if (s.type[i] != kFluid) {
+    bh[3] = -bh[3];
+    bl[3] = -bl[3];
+  }
+  if (bad) atomicOr(w.status, kStatNaN);
+  if (off) atomicOr(w.status, kStatDomain);
+  w.packA[i] = make_float4(ah[0], ah[1], ah[2], ah[3]);
+  w.packAl[i] = make_float4(al[0], al[1], al[2], al[3]);
+  w.packB[i] = make_float4(bh[0], bh[1], bh[2], bh[3]);
+  w.packBl[i] = make_float4(bl[0], bl[1], bl[2], bl[3]);
+  w.packC[i] = ic[0] | (ic[1] << 11) | (ic[2] << 22);
+}
+
+// Double-float pack (after the FP64 prepass); fails when the grid is too
+// large for the packed cell coordinates (11/11/10 bits).
+int launch_pack_df(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st) {
+  if (n == 0) return 0;
+  if (p.nc[0] > 2048 || p.nc[1] > 2048 || p.nc[2] > 1024) return WBSPH_E_INVAL;
+  k_pack_df<<<(unsigned)div_up(n, DFP_THREADS), DFP_THREADS, 0, st>>>(p, s, w, n);
   return 0;
 }
 
