@@ -23,8 +23,8 @@ checks cover it.
 
 Bit-exact: cell keys and sort order of the whole scene; neighbour rows of
 the sampled particles. Within 1e-12 of the natural scale: FP64 rates and
-fields. The mixed path and the surrogate are held to the tolerances of their
-small-size tests.
+fields, and the same for the double-float path. The mixed path and the
+surrogate are held to the tolerances of their small-size tests.
 """
 import types
 
@@ -124,10 +124,9 @@ def test_full_size_neighbour_rows_bitexact(name):
     sim.close()
 
 
-@pytest.mark.parametrize("name", sorted(FULL))
-def test_full_size_stage_rates_sampled(name):
+def _stage_rates_sampled(name, precision):
     sc = _scene(name)
-    sim = _sim(sc)
+    sim = _sim(sc, precision)
     sim.eval_rates()
     smp = sample_fluid(sc, 64)
     idx, loc, r = _stage_oracle(sc, smp, _umax(sc))
@@ -149,20 +148,22 @@ def test_full_size_stage_rates_sampled(name):
     if dl.size:
         errs["u_dummy"] = scaled_err(sim.get("u")[:, d[near]], r["u"][:, dl], sk["u"])
         errs["phi_dummy"] = scaled_err(sim.get("phi")[d[near]], r["phi"][dl], sk["phi"])
-    print(name, "samples", smp.size, "patch", idx.size, "dummies", int(near.sum()), errs)
+    print(name, "precision", precision, "samples", smp.size, "patch", idx.size, "dummies",
+          int(near.sum()), errs)
     for k, v in errs.items():
         assert v <= TOL, (k, v)
     sim.close()
 
 
 @pytest.mark.parametrize("name", sorted(FULL))
-def test_full_size_step_sampled(name):
-    """One SSP-RK2 step replayed from the captured CUDA graph: a first step
-    captures it, the state is reloaded (same counts, so the graph is kept)
-    and the second step replays it. Shifting off (see the module note)."""
+def test_full_size_stage_rates_sampled(name):
+    _stage_rates_sampled(name, 0)
+
+
+def _step_sampled(name, precision):
     sc = _scene(name, use_pst=0)
     p = sc.params
-    sim = _sim(sc)
+    sim = _sim(sc, precision)
     sim.step(1)
     sim.set_scene(sc)
     sim.step(1)
@@ -178,10 +179,33 @@ def test_full_size_step_sampled(name):
     errs = {"x": scaled_err(sim.get("x")[:, smp], ref.x[:, loc], sk["x"]),
             "u": scaled_err(sim.get("u")[:, smp], ref.u[:, loc], sk["u"]),
             "phi": scaled_err(sim.get("phi")[smp], ref.phi[loc], sk["phi"])}
-    print(name, "samples", smp.size, "patch", idx.size, errs)
+    print(name, "precision", precision, "samples", smp.size, "patch", idx.size, errs)
     for k, v in errs.items():
         assert v <= TOL, (k, v)
     sim.close()
+
+
+@pytest.mark.parametrize("name", sorted(FULL))
+def test_full_size_step_sampled(name):
+    """One SSP-RK2 step replayed from the captured CUDA graph: a first step
+    captures it, the state is reloaded (same counts, so the graph is kept)
+    and the second step replays it. Shifting off (see the module note)."""
+    _step_sampled(name, 0)
+
+
+@pytest.mark.parametrize("name", ["dam3d_1.2M", "slosh3d_17.6M", "gauss2d_250k"])
+def test_full_size_df64_stage_rates_sampled(name):
+    """The double-float pass at full size, held to the FP64 bar: the same
+    sampled rates against the same oracle patches."""
+    from paper_2608_22269_gb300 import wbsph
+    _stage_rates_sampled(name, wbsph.DF64)
+
+
+def test_full_size_df64_step_sampled():
+    """One double-float SSP-RK2 step of the 1.2M dam break, replayed from
+    its captured CUDA graph, against the oracle patches."""
+    from paper_2608_22269_gb300 import wbsph
+    _step_sampled("dam3d_1.2M", wbsph.DF64)
 
 
 @pytest.mark.parametrize("name", ["dam3d_1.2M", "slosh3d_17.6M", "gauss2d_250k"])
