@@ -123,3 +123,29 @@ def test_cell_key_estimate_error_bound(lo, hi, R):
     m = np.float32(2 * E * 1.001)
     ok = (fr > m) & (fr < 1 - m)
     assert np.array_equal(np.floor(qf[ok]).astype(np.int64), np.floor(q64[ok]).astype(np.int64))
+
+
+def test_double_float_offsets_subtract_exactly():
+    """The double-float pack stores o = (x - cell origin) / R with a high part
+    rounded to a multiple of 2^-23 (add and subtract 1.5 * 2^29 in FP64). For
+    |o| < 1.5 that high part is an FP32 number, and for every pair closer than
+    R the pair pass's FP32 evaluation (cell offset) + (o_hi,j - o_hi,i) is
+    exact, so r / R is rounded only in its low parts. Emulated with IEEE FP32
+    and FP64 operations on random offsets, including the drift to |o| < 1.5."""
+    rng = np.random.default_rng(11)
+    o = rng.uniform(-1.5, 1.5, size=(2, 400_000))
+    o[:, :64] = [[-1.5 + 2.0 ** -40], [1.5 - 2.0 ** -30]]  # near the ends of the range
+    c = 1.5 * 2.0 ** 29
+    q = (o + c) - c
+    assert np.all(np.abs(o - q) <= 2.0 ** -24)
+    assert np.all(np.abs(q * 2.0 ** 23 - np.rint(q * 2.0 ** 23)) == 0)
+    hi = q.astype(np.float32)
+    assert np.array_equal(hi.astype(np.float64), q)  # the high parts are FP32 numbers
+    dc = rng.integers(-1, 2, size=o.shape[1]).astype(np.float32)
+    diff = hi[1] - hi[0]  # FP32 subtraction
+    rhat = dc + diff      # FP32 addition
+    exact = dc.astype(np.float64) + (q[1] - q[0])
+    near = np.abs(exact) <= 1.0 + 2.0 ** -22  # pairs within R (plus the low-part slack)
+    assert near.sum() > 50_000
+    assert np.array_equal(diff[near].astype(np.float64), (q[1] - q[0])[near])
+    assert np.array_equal(rhat[near].astype(np.float64), exact[near])
