@@ -37,34 +37,12 @@ __device__ __forceinline__ df df_two_prod(float a, float b) {
   return {p, __fmaf_rn(a, b, -p)};
 }
 
-__device__ __forceinline__ df df_make(float a) { return {a, 0.f}; }
-
-// a + b (the accurate double-word sum: relative error below 3 u^2, u = 2^-24)
-__device__ __forceinline__ df df_add(df a, df b) {
-  const df s = df_two_sum(a.hi, b.hi);
-  const df t = df_two_sum(a.lo, b.lo);
-  const df v = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-  return df_fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
-}
-
-__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
-
-// a * b (double-word times double-word with FMA: relative error below 5 u^2)
+// a * b (double-word times double-word with FMA, renormalised: relative error a few u^2)
 __device__ __forceinline__ df df_mul(df a, df b) {
   const df p = df_two_prod(a.hi, b.hi);
   const float t = __fmaf_rn(a.lo, b.hi, __fmul_rn(a.hi, b.lo));
   return df_fast_two_sum(p.hi, __fadd_rn(p.lo, t));
 }
-
-// a * b with b an FP32 number (relative error below 2 u^2)
-__device__ __forceinline__ df df_mul_f(df a, float b) {
-  const df p = df_two_prod(a.hi, b);
-  return df_fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
-}
-
-// a * b + c
-__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
 
 // a * b as (fl(a.hi b.hi), the rest): the exact product of the high parts
 // plus the two cross terms, not renormalised. Neither operand needs to be
@@ -91,6 +69,8 @@ __device__ __forceinline__ df df_sub_raw(df a, df b) {
   const df s = df_two_sum(a.hi, -b.hi);
   return {s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo))};
 }
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 
 // the double nearest to hi + lo (exact: both are FP32)
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
