@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_edge_mlp_tc(const bf16* __res
   // bit b: parity of mbarrier b's next phase (0, 1: MMA per accumulator;
   // 2 + s: TMA arrival of slot s)
   uint32_t phases = 0u;
-  auto wait_slot = [&](int ac) -> bool {  // bounded; every thread gets the CTA's verdict
+  auto wait_slot = [&](int ac) -> bool {  // bounded; every thread gets the CTA's decision
     bool w_ok = mbar_wait(smem_u32(mbar + ac), (phases >> ac) & 1u);
     phases ^= 1u << ac;
     return __syncthreads_and(w_ok) != 0;

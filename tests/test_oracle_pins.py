@@ -401,3 +401,47 @@ def test_results_independent_of_thread_count(monkeypatch):
     b = oracle.State(sc)
     b.step(2)
     assert np.array_equal(a.x, b.x) and np.array_equal(a.phi, b.phi)
+
+
+def test_dam_break_follows_the_ritter_solution():
+    """A dynamic run pinned to a closed form: the collapse of a water column
+    (a = 0.3 m wide, H = 0.2 m high) on a dry, slip floor, the flow of the
+    dam-breaking case of Sec. 4 before it meets an obstacle. Ritter's
+    shallow-water solution for an instantaneous dry-bed dam break gives the
+    depth h/H = (2 - xi)^2 / 9 for -1 <= xi <= 2, xi = (x - a) / (sqrt(gH) t):
+    h = 4H/9 and u = (2/3) sqrt(gH) at the dam line, so the volume (per unit
+    width) that has crossed it grows as (8/27) H sqrt(gH) t, and the front is
+    at xi = 2. Checked on the oracle's run:
+      - crossed volume (particle area beyond x = a) at t sqrt(g/H) = 1 and 2:
+        between 0.92 and 1.02 of (8/27) H sqrt(gH) t (the release from rest
+        lags the instantaneous solution a little); a gravity scale off by
+        20 % moves it to 0.88 or 1.06;
+      - depth profile (particle area per unit width) at t sqrt(g/H) = 2 within
+        0.08 H of Ritter's over -0.25 <= xi <= 1.25: ahead of the wave
+        reflected from the back wall (it reaches the wall at t sqrt(g/H) =
+        a/H) and behind the front tip, where the shallow-water model fails;
+      - the front lags the ideal front (xi = 2) but has passed xi = 1."""
+    dx, H, a, g = 0.01, 0.2, 0.3, 9.81
+    sc = S.dam_break_2d(dx=dx, width=1.6, column=(a, H))
+    st = oracle.State(sc)
+    ratios = []
+    for T in (1.0, 2.0):
+        while st.t * np.sqrt(g / H) < T:
+            st.step(10)
+        x = st.x[:, sc.type == 0]
+        crossed = np.count_nonzero(x[0] > a) * dx * dx
+        ratios.append(crossed / (8.0 / 27.0 * H * np.sqrt(g * H) * st.t))
+    ct = np.sqrt(g * H) * st.t
+    bw = 0.05
+    centres = np.arange(bw / 2, 1.2, bw)
+    depth = np.array([np.count_nonzero(np.abs(x[0] - c) < bw / 2) for c in centres]) * dx * dx / bw
+    xi = (centres - a) / ct
+    ritter = H * (2.0 - xi) ** 2 / 9.0
+    band = (xi >= -0.25) & (xi <= 1.25)
+    assert band.sum() >= 8
+    err = np.abs(depth[band] - ritter[band]).max() / H
+    front = (np.quantile(x[0], 0.995) - a) / ct
+    print(f"crossed volume / Ritter {ratios}, max |h - h_Ritter| / H = {err:.3f}, front xi = {front:.2f}")
+    assert all(0.92 <= r <= 1.02 for r in ratios)
+    assert err <= 0.08
+    assert 1.0 < front < 2.0
