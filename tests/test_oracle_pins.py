@@ -445,3 +445,41 @@ def test_dam_break_follows_the_ritter_solution():
     assert all(0.92 <= r <= 1.02 for r in ratios)
     assert err <= 0.08
     assert 1.0 < front < 2.0
+
+
+def test_sloshing_first_mode_period():
+    """A second dynamic run pinned to a closed form: the standing wave of the
+    sloshing workload. Linear water-wave theory gives the first sloshing mode
+    of a tank of length L and depth d the frequency w^2 = g k tanh(k d),
+    k = pi / L. The oracle runs a 2D tank (L = 0.4 m, d = 0.2 m, every
+    stabiliser on) released from rest with the surface of that mode,
+    d + A cos(k x), A = 0.01 m, and hydrostatic potential below it. The
+    mode's amplitude is the projection of the particle area on cos(k x);
+    its first and third zero crossings are one period apart, which must be
+    within 3 % of 2 pi / w (the run gives 0.5 %; a gravity scale off by 10 %
+    moves the period by 5 %)."""
+    dx, L, d, A, g = 0.01, 0.4, 0.2, 0.01, 9.81
+    k = math.pi / L
+    period = 2.0 * math.pi / math.sqrt(g * k * math.tanh(k * d))
+
+    def eta(x):
+        return d + A * np.cos(k * x)
+
+    sc = S.box_tank(2, (L, 0.4), dx, lambda gr: gr[1] < eta(gr[0]), d, name="slosh2d",
+                    use_delta=1, use_pst=1, use_tic=1)
+    f = sc.type == 0
+    sc.phi[f] = g * (eta(sc.x[0, f]) - sc.x[1, f])
+    st = oracle.State(sc)
+    ts, amp = [], []
+    while st.t < 1.3 * period:
+        st.step(5)
+        ts.append(st.t)
+        amp.append((2.0 / L) * dx * dx * np.cos(k * st.x[0, f]).sum())
+    ts, amp = np.array(ts), np.array(amp)
+    assert amp[0] > 0.8 * A
+    s = np.nonzero(amp[:-1] * amp[1:] < 0)[0]
+    crossings = ts[s] + (ts[s + 1] - ts[s]) * amp[s] / (amp[s] - amp[s + 1])
+    assert crossings.size >= 3
+    measured = crossings[2] - crossings[0]
+    print(f"first-mode period {measured:.4f} s, linear theory {period:.4f} s")
+    assert abs(measured / period - 1.0) <= 0.03
