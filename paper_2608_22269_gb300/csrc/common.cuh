@@ -140,24 +140,34 @@ void launch_count_neighbors(const Params& p, const State& s, const Work& w, int6
 void launch_fill_neighbors(const Params& p, const State& s, const Work& w, int64_t n,
                            const int64_t* row_ptr_by_oid, int32_t* cols, cudaStream_t st);
 
-// ---- launchers (pair_fp64.cu) ----
+// ---- prepass.cu ----
 // Dummy walls, then (volumes = true) V = m / rho and U_max of the stage.
 void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int64_t nd,
                     int stage2, cudaStream_t st, bool volumes = true);
 void launch_time_step(const Params& p, const Work& w, cudaStream_t st);
-void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid,
-                      int stage2, cudaStream_t st);
-int pair_list_kmax(int dim);
-void launch_lambda_fp64(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st);
-// ---- prepass.cu (double-float pack) and pair_df64.cu ----
+// Mixed path: V, U_max and the packed FP32 copies; WBSPH_E_INVAL when the
+// grid exceeds the packed cell word (2048 x 2048 x 1024 cells).
+int launch_prepass_mixed(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
+// Double-float path: the hi/lo copies (after launch_prepass); the same grid limit.
 int launch_pack_df(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
-void launch_pair_df(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
-                    cudaStream_t st);
-// ---- pair_conventional.cu ----
-void launch_pair_conventional(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
-                              int stage2, cudaStream_t st);
+
+// ---- lists.cu ----
+int pair_list_kmax(int dim);
 void launch_nbr_list(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid, cudaStream_t st,
                      bool exact);
+
+// ---- pair passes: pair_fp64.cu, pair_mixed.cu, pair_df64.cu, pair_conventional.cu ----
+void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid,
+                      int stage2, cudaStream_t st);
+void launch_lambda_fp64(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st);
+void launch_pair_mixed(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
+                       cudaStream_t st);
+void launch_pair_df(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
+                    cudaStream_t st);
+void launch_pair_conventional(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
+                              int stage2, cudaStream_t st);
+
+// ---- update.cu ----
 void launch_rk_stage(const Params& p, const State& s, const Work& w, int64_t n, int stage,
                      cudaStream_t st);
 void launch_field(const Params& p, const State& s, const Work& w, int64_t n, int field,

@@ -23,10 +23,7 @@ using namespace wbsph;
 
 namespace wbsph {
 void launch_mass(const Params& p, const double* phi, double* mass, int64_t n, cudaStream_t st);
-int launch_prepass_mixed(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
 void launch_wait_probe(unsigned* status, uint32_t limit, cudaStream_t st);
-void launch_pair_mixed(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
-                       cudaStream_t st);
 }
 
 struct ProfEvent {
