@@ -143,7 +143,11 @@ def make_config(params: dict, precision: int = FP64, stream=None, device: int = 
 
 class Sim:
     """One simulation handle. ``params`` is a scene parameter dict; device
-    memory comes from PyTorch's caching allocator on the current stream."""
+    memory comes from PyTorch's caching allocator on the current stream.
+    ``precision`` selects the pair pass: FP64, MIXED (FP32 sums with Kahan
+    compensation, about 1e-5 of the field scale) or DF64 (double-float sums
+    on the FP32 pipe, within 1e-12 like FP64); ``water_height`` is the H of
+    the hydrostatic split phi_hs = G.x + |G| H that MIXED and DF64 use."""
 
     def __init__(self, params: dict, precision: int = FP64, water_height: float = 0.0,
                  device: int = 0, use_torch_allocator: bool = True, stream=None):
