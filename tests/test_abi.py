@@ -149,3 +149,75 @@ def test_double_float_offsets_subtract_exactly():
     assert near.sum() > 50_000
     assert np.array_equal(diff[near].astype(np.float64), (q[1] - q[0])[near])
     assert np.array_equal(rhat[near].astype(np.float64), exact[near])
+
+
+def _f32(x):
+    return np.float32(x)
+
+
+def _fma32(a, b, c):
+    """fmaf emulated through FP64: exact for the two-product residual
+    a*b - fl(a*b); elsewhere (the cross terms of a product) within one extra
+    rounding of a low part, far below the bounds checked here."""
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _two_sum(a, b):
+    s = _f32(a + b)
+    bb = _f32(s - a)
+    return s, _f32(_f32(a - _f32(s - bb)) + _f32(b - bb))
+
+
+def _fast_two_sum(a, b):
+    s = _f32(a + b)
+    return s, _f32(b - _f32(s - a))
+
+
+def _df_mul(a, b):
+    p = _f32(a[0] * b[0])
+    e = _fma32(a[0], b[0], -p)
+    t = np.float32(np.float64(a[1]) * np.float64(b[0]) + np.float64(_f32(a[0] * b[1])))
+    return _fast_two_sum(p, _f32(e + t))
+
+
+def _df_acc(acc, v):
+    s = _two_sum(acc[0], v[0])
+    return _fast_two_sum(s[0], _f32(s[1] + _f32(acc[1] + v[1])))
+
+
+def test_double_float_primitives_meet_their_error_bounds():
+    """The double-float arithmetic of the df64 pair pass, emulated operation
+    by operation in IEEE FP32 as the device helpers write it, against exact
+    rational arithmetic: two-sum is exact; the product has a relative error
+    of a few u^2 (u = 2^-24); a running sum of 100 terms of mixed sign stays
+    within a few u^2 of the sum of the magnitudes. These bounds are what make
+    the double-float pass agree with FP64 to ~1e-13 of a field's scale."""
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(3)
+    u2 = Fr(1, 2 ** 48)
+
+    def split(x):
+        hi = np.float32(x)
+        return hi, np.float32(x - np.float64(hi))
+
+    def val(d):
+        return Fr(float(d[0])) + Fr(float(d[1]))
+
+    for _ in range(300):
+        a, b = (np.float32(v) for v in rng.normal(size=2) * 10.0 ** rng.integers(-3, 4, size=2))
+        s = _two_sum(a, b)
+        assert Fr(float(s[0])) + Fr(float(s[1])) == Fr(float(a)) + Fr(float(b))
+    for _ in range(300):
+        x, y = split(rng.normal() * 7.0), split(rng.normal() * 0.3)
+        exact = val(x) * val(y)
+        err = abs(val(_df_mul(x, y)) - exact)
+        assert err <= 6 * u2 * abs(exact)
+    for _ in range(20):
+        terms = [split(v) for v in rng.normal(size=100) * 10.0 ** rng.integers(-2, 3, size=100)]
+        acc = (np.float32(0.0), np.float32(0.0))
+        exact, mag = Fr(0), Fr(0)
+        for t in terms:
+            acc = _df_acc(acc, t)
+            exact += val(t)
+            mag += abs(val(t))
+        assert abs(val(acc) - exact) <= 4 * u2 * mag
