@@ -483,3 +483,40 @@ def test_sloshing_first_mode_period():
     measured = crossings[2] - crossings[0]
     print(f"first-mode period {measured:.4f} s, linear theory {period:.4f} s")
     assert abs(measured / period - 1.0) <= 0.03
+
+
+def test_tank_forcing_is_the_frame_acceleration():
+    """The forced tank of the sloshing workload is simulated in the tank's
+    frame: a displacement X(t) = A sin(w t) along x adds the frame
+    acceleration -X''(t) to the body force. A lone fluid particle has no
+    pressure or viscous terms, so its rate is exactly G - X''(t), checked at
+    several times against a central difference of X(t) (not the oracle's own
+    formula). Released from rest at t = 0 it then follows
+    x(t) = x0 + A w t - A sin(w t), and y under G alone; the SSP-RK2 run over
+    one period with a fixed step must match it within the method's
+    second-order error. (2D, coarse dx: a lone particle's motion does not
+    depend on h, and the fall of 11 m needs a tall grid.)"""
+    A, period = 0.01, 1.5
+    w = 2.0 * math.pi / period
+    p = S.default_params(2, 0.1, 30.0, use_tic=1, force_amp=[A, 0.0, 0.0], force_period=period,
+                         domain_min=[-2.0, -15.0, 0.0], domain_max=[2.0, 2.0, 1.0])
+    x0 = np.array([[0.3], [0.2]])
+    typ, nrm = np.zeros(1, np.uint8), np.zeros((2, 1))
+
+    def X(t):
+        return A * math.sin(w * t)
+
+    hd = 1e-4
+    for t in (0.1, 0.37, 0.9, 1.2):
+        r = oracle.stage_rates(p, x0, np.zeros((2, 1)), np.zeros(1), np.ones(1), typ, nrm, t=t)
+        frame = -(X(t + hd) - 2.0 * X(t) + X(t - hd)) / (hd * hd)
+        assert r["dudt"][0, 0] == pytest.approx(frame, rel=1e-6, abs=1e-9)
+        assert r["dudt"][1, 0] == -9.81
+    dt = 1e-3
+    sc = S.Scene(dict(p, fixed_dt=dt), x0.copy(), np.zeros((2, 1)), np.zeros(1), typ, nrm)
+    st = oracle.State(sc).step(int(round(period / dt)))
+    t = st.t
+    assert t == pytest.approx(period, rel=1e-12)
+    want_x = x0[0, 0] + A * w * t - A * math.sin(w * t)
+    assert abs(st.x[0, 0] - want_x) <= 10.0 * (w * dt) ** 2 * A
+    assert st.x[1, 0] == pytest.approx(x0[1, 0] - 0.5 * 9.81 * t * t, abs=1e-9)
