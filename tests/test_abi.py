@@ -1,6 +1,9 @@
 """Host-side checks of the C-ABI library: it builds for sm_103a, loads, and
 exports every function that include/wbsph.h declares (no compute calls);
-and the error bound that the cell-key kernel's FP32 fast path relies on."""
+configuration validation; and, emulated in IEEE arithmetic on the host, the
+numerical arguments the kernels rely on: the error bound of the cell-key
+kernel's FP32 fast path, the exact high-part offset differences of the
+double-float pack, and the error bounds of the double-float primitives."""
 import ctypes
 import os
 import re

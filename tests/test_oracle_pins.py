@@ -3,7 +3,8 @@
 Each test names the passage of the paper it pins. None of them re-types the
 oracle's own formulas: they use quadrature, brute force, library routines,
 closed-form consequences (linear exactness, lattice symmetry, an energy
-identity) or values printed in the paper.
+identity), values printed in the paper, or closed-form flows that a run must
+approach (Ritter's dam break, linear sloshing, a forced frame).
 """
 import json
 import math
