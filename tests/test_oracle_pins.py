@@ -282,6 +282,119 @@ def test_shifting_direction_and_clamp():
     assert np.isclose(nrm.max(), 0.15)
 
 
+def _three_particle_cloud(n_exp):
+    """Three fluid particles at rest, phi = 0, G = 0, h = 1 exactly (dx = 0.5,
+    h/dx = 2): i at the origin, j at (0.6, 0.8) (q = 1), k at (-0.25, 0)
+    (q = 0.25); j and k are neighbours of i (and of each other, |x_j - x_k| =
+    1.17 < 2h). Every particle's volume is V = m / rho0 = 0.125."""
+    p = S.default_params(2, 0.5, 20.0, h_over_dx=2.0, g=[0.0, 0.0, 0.0], use_pst=1, use_tic=1,
+                         pst_n=float(n_exp), domain_min=[-2.0, -2.0, 0.0],
+                         domain_max=[2.0, 2.0, 1.0])
+    x = np.array([[0.0, 0.6, -0.25], [0.0, 0.8, 0.0]])
+    z = np.zeros((2, 3))
+    m = np.full(3, 0.125 * p["rho0"])
+    return p, x, z, m
+
+
+@pytest.mark.parametrize("n_exp,R", [(4, 0.2), (3, 0.2), (4, 0.5)])
+def test_shifting_magnitude_hand_computed(n_exp, R):
+    """Particle shifting (Sec. 2.3), the unclamped magnitude, against numbers
+    worked by hand from Eq. (c2kernel). In 2D with h = 1 the kernel is
+    W(q) = a (1 - q/2)^4 (2q + 1), a = 7 / (4 pi), and dW/dr = -5 a q (1 - q/2)^3:
+      j (q = 1):    dW/dr = -5a/8,            grad_i W_ij = a (0.375, 0.5),
+                    W(1) / W(dx) = (3a/16) / (81a/128) = 8/27;
+      k (q = 1/4):  dW/dr = -5a (1/4)(7/8)^3 = -(1715/2048) a,
+                    grad_i W_ik = (-(1715/2048) a, 0),
+                    W(1/4) / W(dx) = ((7/8)^4 (3/2)) / ((3/4)^4 2) = 2401/1728.
+    With V = 1/8 and U_max = 2:
+      dU*_i = -2 h U_max V sum_j [1 + R ratio_j^n] grad_i W_ij,
+    |dU*_i| = 0.33 < U_max / 2, so the clamp is inactive and dU_i = dU*_i.
+    Catches a dropped or doubled factor 2, h replaced by dx (a factor 2 here),
+    a wrong U_max or V factor, a sign error, and R or n misapplied (the two
+    neighbours' ratios differ, 0.30 and 1.39, so their weights move apart)."""
+    p, x, z, m = _three_particle_cloud(n_exp)
+    p = dict(p, pst_R=R)
+    r = oracle.stage_rates(p, x, z, np.zeros(3), m, np.zeros(3, np.uint8), z, umax=2.0)
+    a = 7.0 / (4.0 * math.pi)
+    fj = 1.0 + R * (8.0 / 27.0) ** n_exp
+    fk = 1.0 + R * (2401.0 / 1728.0) ** n_exp
+    P = 0.125 * (fj * a * np.array([0.375, 0.5]) + fk * a * np.array([-1715.0 / 2048.0, 0.0]))
+    want = -2.0 * 1.0 * 2.0 * P
+    assert np.linalg.norm(want) < 1.0                       # clamp inactive by construction
+    assert np.abs(r["dushift"][:, 0] - want).max() <= 1e-14 * np.abs(want).max(), (
+        r["dushift"][:, 0], want)
+
+
+def test_shifting_clamp_hand_computed():
+    """Same cloud with U_max = 2 and V = 1 (eight times the volume): the
+    unclamped vector would exceed U_max / 2 = 1, so dU_i has length exactly 1
+    along dU*_i (Sec. 2.3, the min of the two lengths)."""
+    p, x, z, m = _three_particle_cloud(4)
+    r = oracle.stage_rates(p, x, z, np.zeros(3), 8.0 * m, np.zeros(3, np.uint8), z, umax=2.0)
+    a = 7.0 / (4.0 * math.pi)
+    fj = 1.0 + 0.2 * (8.0 / 27.0) ** 4
+    fk = 1.0 + 0.2 * (2401.0 / 1728.0) ** 4
+    dus = -4.0 * (fj * a * np.array([0.375, 0.5]) + fk * a * np.array([-1715.0 / 2048.0, 0.0]))
+    assert np.linalg.norm(dus) > 1.0
+    want = dus / np.linalg.norm(dus)
+    assert np.abs(r["dushift"][:, 0] - want).max() <= 1e-14
+
+
+# -- conservative (TIC) gradient (Sec. 2.3) ---------------------------------------------------
+
+@pytest.mark.parametrize("dim,n_side", [(2, 20), (3, 10)])
+def test_conservative_gradient_on_lattice_is_L_b(dim, n_side):
+    """The conservative gradient C_i = sum_j (phi_j + phi_i) grad_i W_ij V_j of
+    the TIC switch (Sec. 2.3) for phi = a + b.x on a perfect lattice: at an
+    interior particle the lattice is point-symmetric, so sum_j grad_i W_ij V_j
+    = 0 and C_i = sum_j (b.(x_j - x_i)) grad_i W_ij V_j = L_i^T b = L_i b, and
+    with L = c I (lattice symmetry, c = tr L / d) C_i = c b, to 1e-13 |b|
+    (1e-13 |a| / h with a constant a in phi, which must not change it: the
+    rounding of the vanishing 2 phi_i sum grad W V scales with |phi_i|). Catches a factor 2, a sign error,
+    a dropped V_j and a sum that uses phi_i alone; the (phi_j + phi_i) sign of
+    the pair is pinned by the antisymmetry test below and the surface test
+    that follows."""
+    sc = S.lattice_cloud(dim, n_side)
+    p = sc.params
+    rng = np.random.default_rng(12)
+    b = rng.normal(size=dim) * 4.0
+    ctr = np.argmin(((sc.x - sc.x.mean(axis=1, keepdims=True)) ** 2).sum(0))
+    for a0 in (0.0, 37.5):
+        phi = a0 + b @ sc.x
+        m = np.full(sc.n, p["rho0"] * p["dx"] ** dim)
+        m = m * oracle.density(p, phi) / p["rho0"]          # every V_j = dx^d
+        s = oracle.pair_sums(p, sc.x, sc.u, phi, m, sc.type)
+        L = s[ctr, :9].reshape(3, 3)[:dim, :dim]
+        c = np.trace(L) / dim
+        C = s[ctr, 21:21 + dim]
+        # rounding of the vanishing 2 phi_i sum grad W V scales with |phi_i| / h
+        tol = 1e-13 * max(np.abs(b).max(), a0 / (p["h_over_dx"] * p["dx"]))
+        assert np.abs(C - L @ b).max() <= tol
+        assert np.abs(C - c * b).max() <= tol
+        assert 0.9 < c < 1.1
+
+
+def test_conservative_gradient_constant_part_at_a_surface():
+    """At a particle with an incomplete support, adding a constant a to phi
+    changes C_i by 2 a sum_j grad_i W_ij V_j, and that sum is the shifting sum
+    P_i taken with R = 0 (pinned by hand above). With (phi_j - phi_i) in place
+    of (phi_j + phi_i) the change would be zero; with phi_j alone, a P_i."""
+    sc = S.lattice_cloud(2, 12, jitter_amount=0.15, seed=4)
+    p = dict(sc.params, pst_R=0.0)
+    rng = np.random.default_rng(6)
+    phi = rng.normal(size=sc.n)
+    m = oracle.mass(p, phi)
+    s0 = oracle.pair_sums(p, sc.x, sc.u, phi, m, sc.type)
+    a0 = 3.25
+    m1 = m * oracle.density(p, phi + a0) / oracle.density(p, phi)   # same volumes
+    s1 = oracle.pair_sums(p, sc.x, sc.u, phi + a0, m1, sc.type)
+    dC = s1[:, 21:23] - s0[:, 21:23]
+    P = s0[:, 25:27]
+    edge = np.linalg.norm(P, axis=1) > 1e-3 * np.linalg.norm(P, axis=1).max()
+    assert edge.sum() > 20
+    assert np.abs(dC - 2.0 * a0 * P).max() <= 1e-12 * np.abs(2.0 * a0 * P).max()
+
+
 # -- walls (Sec. 2.4) ------------------------------------------------------------------------
 
 def test_dummy_potential_is_hydrostatic_and_velocity_slips():
@@ -345,6 +458,27 @@ def test_open_tank_stays_at_rest_100_steps(eos):
     l2, um = st.l2_velocity()
     assert um <= 1e-12
     assert l2 <= _golden()["hydrostatic_l2_wbsph"]["range"][1]
+
+
+def test_l2_velocity_measure_hand_computed():
+    """The L2 spurious-velocity measure of Sec. 4.1, sqrt(sum |U_j|^2 V_j / sum V_j)
+    over fluid particles, on three fluid particles and one dummy worked by
+    hand: |U|^2 = 25, 0, 1 with V = 1, 2, 1 (the first at phi = C0^2 ln 2, so
+    rho = 2 rho0 and its mass is 2 rho0 V), giving sqrt(26 / 4); the dummy
+    (|U| = 100, V = 5) is excluded, and max |U| = 5. Catches a missing square
+    root, unweighted or unnormalised sums, V taken as m / rho0, and dummies
+    counted."""
+    p = S.default_params(2, 0.01, 20.0)
+    u = np.array([[3.0, 0.0, 1.0, 100.0], [4.0, 0.0, 0.0, 0.0]])
+    phi = np.array([p["c0"] ** 2 * math.log(2.0), 0.0, 0.0, 0.0])
+    rho0 = p["rho0"]
+    m = np.array([2.0 * rho0 * 1.0, rho0 * 2.0, rho0 * 1.0, rho0 * 5.0])
+    typ = np.array([0, 0, 0, 1], np.uint8)
+    sc = S.Scene(p, np.zeros((2, 4)), u, phi, typ, np.zeros((2, 4)))
+    st = oracle.State(sc, mass_override=m)
+    l2, um = st.l2_velocity()
+    assert l2 == pytest.approx(math.sqrt(6.5), rel=1e-14)
+    assert um == 5.0
 
 
 # -- SSP-RK2 and the time step (Sec. 2.3) -----------------------------------------------------
