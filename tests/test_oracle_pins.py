@@ -481,6 +481,96 @@ def test_l2_velocity_measure_hand_computed():
     assert um == 5.0
 
 
+def _rate_jacobian(sc):
+    """Jacobian of the oracle's stage rates of the fluid state (x, U, phi) at
+    the scene's state, by central differences, in scaled variables (x / dx,
+    U / C0, phi / C0^2, time in dx / C0, so that eigenvalues come in C0 / dx).
+    Column and row blocks: x (d blocks), U (d blocks), phi, each nf long."""
+    p = sc.params
+    f = np.nonzero(sc.type == 0)[0]
+    d, dx, c0 = p["dim"], p["dx"], p["c0"]
+    m = oracle.mass(p, sc.phi)
+    scale = [dx] * d + [c0] * d + [c0 * c0]
+
+    def F(x, u, phi):
+        r = oracle.stage_rates(p, x, u, phi, m, sc.type, sc.normal)
+        return np.concatenate([u[:, f].ravel() / dx, r["dudt"][:, f].ravel() / c0,
+                               r["dphidt"][f] / (c0 * c0)]) * (dx / c0)
+
+    J = np.zeros(((2 * d + 1) * f.size,) * 2)
+    eps, col = 1e-6, 0
+    for blk in range(2 * d + 1):
+        for i in f:
+            y = [sc.x.copy(), sc.u.copy(), sc.phi.copy()]
+            arr, k = (y[0], blk) if blk < d else ((y[1], blk - d) if blk < 2 * d else (y[2], None))
+            idx = (k, i) if k is not None else i
+            arr[idx] += eps * scale[blk]
+            fp = F(*y)
+            arr[idx] -= 2 * eps * scale[blk]
+            J[:, col] = (fp - F(*y)) / (2 * eps)
+            col += 1
+    return J, f, m
+
+
+def test_open_tank_surface_mode_is_an_instability_of_the_printed_scheme():
+    """Pins the reading on free-surface stability (stabilisers off, Sec. 4.1).
+    Linearised about the hydrostatic state, the oracle's discrete operator of
+    an open tank (0.2 x 0.1 m, dx = 0.01, linear EOS) has a real eigenvalue
+    mu > 0: a surface particle's excess potential pushes it into the fluid
+    through the differential gradient of Eq. (parGrad) (the air side is
+    missing from its support), which compresses it further. On the particle's
+    own (U, phi) block the coupling is dU/dt = a dphi - C0 B dU and
+    dphi/dt = C0^2 a.dU, whose growing root is
+      mu_1 = C0 [sqrt(b^2 + 4 k^2) - b] / 2,  k^2 = |a|^2, b = a^.B a^
+    (in scaled units), positive for any Riemann coefficient b. (Next to a wall
+    the slip condition couples the particle to its dummies and the two
+    coupling vectors differ a little; k^2 is then their product.) Checked:
+      - mu_1 is the growing eigenvalue of each surface particle's own block
+        (within 2 %, exact away from the walls);
+      - mu_max is real and within 3 % of the largest one-particle mu_1;
+      - its eigenvector lives on the surface particles (lambda_min < 0.75);
+      - the same tank with a lid has no eigenvalue above rounding;
+      - the oracle's own run from rest grows, between steps 200 and 300, by
+        the SSP-RK2 amplification 1 + z + z^2 / 2, z = mu_max dt, within 1 %.
+    This is why the 200-step bound of the hydrostatic tank holds with a lid
+    only: the open tank passes 1e-12 after about 110 steps."""
+    sc = S.hydrostatic_tank_2d(dx=0.01, width=0.2, depth=0.1, eos=0)
+    J, f, m = _rate_jacobian(sc)
+    nf = f.size
+    ev, vec = np.linalg.eig(J)
+    top = int(np.argmax(ev.real))
+    mu = ev[top]
+    assert mu.real > 0.5 and abs(mu.imag) < 1e-6 * mu.real
+    r = oracle.stage_rates(sc.params, sc.x, sc.u, sc.phi, m, sc.type, sc.normal)
+    surf = r["lam"][f] < 0.75
+    w = (np.abs(vec[:, top]) ** 2).reshape(5, nf).sum(0)
+    assert w[surf].sum() >= 0.95 * w.sum()
+    mu1 = []
+    for i in np.nonzero(surf)[0]:
+        idx = [2 * nf + i, 3 * nf + i, 4 * nf + i]          # U_x, U_y, phi of particle i
+        B = J[np.ix_(idx, idx)]
+        a, g, Rm = B[:2, 2], B[2, :2], -B[:2, :2]           # g = a away from the walls
+        ah = a / np.linalg.norm(a)
+        b, k2 = ah @ Rm @ ah, a @ g
+        mu1.append((math.sqrt(b * b + 4 * k2) - b) / 2)
+        assert mu1[-1] == pytest.approx(np.linalg.eigvals(B).real.max(), rel=2e-2)
+    assert mu.real == pytest.approx(max(mu1), rel=0.03)
+    lid = S.hydrostatic_tank_2d(dx=0.01, width=0.2, depth=0.1, eos=0, lid=True)
+    Jl, _, _ = _rate_jacobian(lid)
+    assert np.linalg.eigvals(Jl).real.max() < 1e-8
+    st = oracle.State(sc)
+    um = []
+    for _ in range(300):
+        st.step(1)
+        um.append(st.l2_velocity()[1])
+    z = mu.real * sc.params["cfl"]                           # dt = CFL dx / C0 at rest
+    growth = (um[299] / um[199]) ** (1.0 / 100)
+    print(f"mu_max = {mu.real:.4f} C0/dx, one-particle {max(mu1):.4f}, growth per step "
+          f"{growth:.4f} vs SSP-RK2 {1 + z + z * z / 2:.4f}")
+    assert growth == pytest.approx(1 + z + z * z / 2, rel=0.01)
+    assert um[99] < 1e-12 < um[149]
+
+
 # -- SSP-RK2 and the time step (Sec. 2.3) -----------------------------------------------------
 
 def test_lone_particle_falls_exactly():
