@@ -281,15 +281,22 @@ const char* wbsph_surrogate_last_error(wbsph_surrogate s);
  * position, the input index (the same result as wbsph_build_neighbors +
  * wbsph_get_cell_keys on particles loaded in that order). The grid comes
  * from h's configuration; h needs no wbsph_set_particles, and the handle's
- * stream is used and synchronised before returning.
+ * stream is used and synchronised before returning. The call runs on h's
+ * device and restores the caller's current device before it returns.
+ * The pointers are not checked beyond NULL: x must hold dim*n doubles and
+ * each output n 32-bit words, all on h's device (the Python binding checks
+ * this on the tensors before calling).
  * Scratch lives in a file-scope device array sized for WBSPH_NOALLOC_MAX_N
  * particles (4.3 MB, held by every GPU that loads the library until
  * the process exits); larger n returns WBSPH_E_CAPACITY. The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) for
- * that device, so make that first call before any stream capture. All calls
- * share the array: calls that overlap on the GPU (other threads or streams)
- * race and must be serialised by the caller. Returns WBSPH_E_DOMAIN if a
- * particle lies outside the domain. */
+ * that device and keeps it until the process exits, so a device reset
+ * (cudaDeviceReset) after that first call is not supported. The call
+ * synchronises its stream and reads the status word back to the host, so it
+ * must not be called while that stream is being captured into a CUDA graph.
+ * All calls share the array: calls that overlap on the GPU (other threads or
+ * streams) race and must be serialised by the caller. Returns WBSPH_E_DOMAIN
+ * if a particle lies outside the domain. */
 #define WBSPH_NOALLOC_MAX_N 524288
 int wbsph_sort_cells_noalloc(wbsph_handle h, const double* x, int64_t n, uint32_t* keys_sorted,
                              uint32_t* ids_sorted);

@@ -53,6 +53,9 @@ int scratch_address(int dev, uint32_t** out) {
   return WBSPH_OK;
 }
 
+int sort_on_device(wbsph_handle h, int dev, const double* x, int64_t n, uint32_t* keys_sorted,
+                   uint32_t* ids_sorted);
+
 }  // namespace
 
 extern "C" int wbsph_sort_cells_noalloc(wbsph_handle h, const double* x, int64_t n,
@@ -66,10 +69,24 @@ extern "C" int wbsph_sort_cells_noalloc(wbsph_handle h, const double* x, int64_t
   if (!x || !keys_sorted || !ids_sorted) return handle_fail(h, WBSPH_E_INVAL, "null pointer");
   int dev = handle_device(h);
   if (dev < 0 || dev >= kMaxDevices) return handle_fail(h, WBSPH_E_INVAL, "device ordinal out of range");
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    return handle_fail(h, WBSPH_E_CUDA, "cudaGetDevice failed");
+  }
   if (cudaSetDevice(dev) != cudaSuccess) {
     cudaGetLastError();
     return handle_fail(h, WBSPH_E_CUDA, "cudaSetDevice failed");
   }
+  int rc = sort_on_device(h, dev, x, n, keys_sorted, ids_sorted);
+  if (prev != dev) cudaSetDevice(prev);  // the caller's current device, as it was
+  return rc;
+}
+
+namespace {
+
+int sort_on_device(wbsph_handle h, int dev, const double* x, int64_t n, uint32_t* keys_sorted,
+                   uint32_t* ids_sorted) {
   uint32_t* base = nullptr;
   if (scratch_address(dev, &base) != WBSPH_OK)
     return handle_fail(h, WBSPH_E_CUDA, "cudaGetSymbolAddress of the scratch array failed");
@@ -106,3 +123,5 @@ extern "C" int wbsph_sort_cells_noalloc(wbsph_handle h, const double* x, int64_t
   if (status & kStatDomain) return handle_fail(h, WBSPH_E_DOMAIN, "a particle is outside the domain");
   return WBSPH_OK;
 }
+
+}  // namespace

@@ -270,8 +270,12 @@ class Sim:
 
     def sort_cells_noalloc(self, x, keys_sorted, ids_sorted):
         """wbsph_sort_cells_noalloc on device tensors: x (dim, n) float64,
-        keys_sorted / ids_sorted (n,) 32-bit. Allocates no device memory."""
-        n = int(x.shape[1])
+        keys_sorted / ids_sorted (n,) 32-bit. Allocates no device memory.
+        The arguments are checked (check_noalloc_args) before the call, since
+        the library receives bare pointers and cannot check them."""
+        torch = self._torch
+        n = check_noalloc_args(x, keys_sorted, ids_sorted, self.dim,
+                               torch.device("cuda", self.device))
         cur = self._torch.cuda.current_stream(self.device)
         self.stream.wait_stream(cur)
         self._check(self.lib.wbsph_sort_cells_noalloc(self.h, _ptr(x), n, _ptr(keys_sorted),
@@ -292,6 +296,52 @@ class Sim:
         cnt = (C.c_int64 * len(KERNEL_CLASSES))()
         self._check(self.lib.wbsph_get_profile(self.h, ms, cnt, int(reset)))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def check_noalloc_args(x, keys_sorted, ids_sorted, dim: int, device) -> int:
+    """Argument checks of wbsph_sort_cells_noalloc, done on the tensors'
+    metadata before any pointer reaches the library: x must be a contiguous
+    float64 tensor of shape (dim, n) on ``device``; keys_sorted and ids_sorted
+    contiguous 32-bit integer tensors of at least n elements on the same
+    device, not overlapping each other or x. A float32 or transposed x would
+    make the key kernel read past the end of x, and a short output would make
+    the sort write past its end. Returns n; raises WbsphError(WBSPH_E_INVAL)."""
+    import torch
+
+    def bad(msg):
+        raise WbsphError(-1, f"sort_cells_noalloc: {msg}")
+
+    for name, t in (("x", x), ("keys_sorted", keys_sorted), ("ids_sorted", ids_sorted)):
+        if not isinstance(t, torch.Tensor):
+            bad(f"{name} must be a torch tensor")
+        if t.device != torch.device(device):
+            bad(f"{name} is on {t.device}, the handle's device is {device}")
+        if not t.is_contiguous():
+            bad(f"{name} must be contiguous")
+    if x.dtype != torch.float64:
+        bad(f"x must be float64, got {x.dtype}")
+    if x.dim() != 2 or int(x.shape[0]) != int(dim):
+        bad(f"x must have shape ({dim}, n), got {tuple(x.shape)}")
+    n = int(x.shape[1])
+    u32 = getattr(torch, "uint32", None)
+    for name, t in (("keys_sorted", keys_sorted), ("ids_sorted", ids_sorted)):
+        if t.dtype not in (torch.int32,) + ((u32,) if u32 is not None else ()):
+            bad(f"{name} must be a 32-bit integer tensor, got {t.dtype}")
+        if t.numel() < n:
+            bad(f"{name} holds {t.numel()} elements, {n} are needed")
+
+    def span(t, count):
+        return t.data_ptr(), t.data_ptr() + count * t.element_size()
+
+    spans = {"x": span(x, x.numel()), "keys_sorted": span(keys_sorted, n),
+             "ids_sorted": span(ids_sorted, n)}
+    names = list(spans)
+    for a in range(3):
+        for b in range(a + 1, 3):
+            (a0, a1), (b0, b1) = spans[names[a]], spans[names[b]]
+            if n > 0 and a0 < b1 and b0 < a1:
+                bad(f"{names[a]} and {names[b]} overlap")
+    return n
 
 
 # ---------------------------------------------------------------------------

@@ -39,6 +39,46 @@ def test_binding_lists_the_same_symbols():
     assert sorted(wbsph.SYMBOLS) == _declared()
 
 
+def test_noalloc_arguments_are_checked_before_the_call():
+    """The binding of wbsph_sort_cells_noalloc checks every tensor before a
+    pointer reaches the library (which cannot check bare pointers): each bad
+    argument raises WbsphError(WBSPH_E_INVAL) from the tensors' metadata
+    alone, so no kernel is launched. Run here on CPU tensors against a CPU
+    'device'; the device mismatch is checked against cuda:0."""
+    import torch
+    from paper_2608_22269_gb300 import wbsph
+    cpu = torch.device("cpu")
+    n, dim = 100, 3
+    x = torch.zeros(dim, n, dtype=torch.float64)
+    k = torch.zeros(n, dtype=torch.int32)
+    i = torch.zeros(n, dtype=torch.int32)
+    assert wbsph.check_noalloc_args(x, k, i, dim, cpu) == n
+    big = torch.zeros(2 * n, dtype=torch.int32)
+    assert wbsph.check_noalloc_args(x, big[:n], big[n:], dim, cpu) == n
+    bad_cases = {
+        "float32 x": (x.float(), k, i),
+        "transposed x": (x.t(), k, i),
+        "(n, dim) x": (x.t().contiguous(), k, i),
+        "wrong dim": (torch.zeros(2, n, dtype=torch.float64), k, i),
+        "1-D x": (torch.zeros(dim * n, dtype=torch.float64), k, i),
+        "short keys": (x, k[:n - 1], i),
+        "short ids": (x, k, i[:n - 1]),
+        "int64 keys": (x, k.long(), i),
+        "float ids": (x, k, i.float()),
+        "strided keys": (x, big[::2], i),
+        "keys alias ids": (x, k, k),
+        "overlapping outputs": (x, big[:n], big[n - 1:2 * n - 1]),
+        "keys inside x": (x, x.view(torch.int32)[0, :n], i),
+        "numpy keys": (x, k.numpy(), i),
+    }
+    for what, (xx, kk, ii) in bad_cases.items():
+        with pytest.raises(wbsph.WbsphError) as ei:
+            wbsph.check_noalloc_args(xx, kk, ii, dim, cpu)
+        assert ei.value.code == -1, what
+    with pytest.raises(wbsph.WbsphError):
+        wbsph.check_noalloc_args(x, k, i, dim, torch.device("cuda", 0))
+
+
 def test_status_strings_and_config_defaults(lib):
     from paper_2608_22269_gb300 import wbsph
     L = wbsph.load()

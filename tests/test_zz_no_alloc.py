@@ -52,6 +52,45 @@ def test_noalloc_sort_equals_regular_build_on_consecutive_calls():
     assert sim_big.stats()["device_bytes"] == 0
 
 
+@pytest.mark.parametrize("dim,n,side,passes", [(2, 3000, 0.2, 1), (3, 400_000, 1.1, 3)])
+def test_noalloc_sort_odd_pass_counts(dim, n, side, passes):
+    """Grids of at most 256 cells (one 8-bit radix pass) and of more than
+    65,536 cells (three passes): with an odd pass count the sorted keys end in
+    the static scratch array and are copied to the caller's buffers. Bit for
+    bit against the regular build, twice in a row."""
+    from paper_2608_22269_gb300 import wbsph
+    sc = S.random_box(n, dim, side=side, dx=0.01, seed=40 + dim)
+    R = 2.0 * sc.params["h_over_dx"] * sc.params["dx"]
+    ncells = int(np.prod([int(np.floor(side / R)) + 1 for _ in range(dim)]))
+    bits = max(1, int(np.ceil(np.log2(ncells))))
+    assert (bits + 7) // 8 == passes, (ncells, bits)
+    ref = _regular(sc)
+    sim = wbsph.Sim(sc.params)
+    for _ in range(2):
+        keys, ids = _noalloc(sim, sc)
+        assert np.array_equal(keys, ref[0])
+        assert np.array_equal(ids, ref[1])
+
+
+def test_noalloc_sort_rejects_bad_tensors_before_the_call():
+    """A float32 x, a transposed x or a short output raises before any pointer
+    reaches the library; the handle stays usable."""
+    import torch
+    from paper_2608_22269_gb300 import wbsph
+    sc = S.random_box(5000, 3, side=0.3, dx=0.01, seed=5)
+    sim = wbsph.Sim(sc.params)
+    x = torch.from_numpy(sc.x).cuda()
+    k = torch.empty(sc.n, dtype=torch.int32, device="cuda")
+    i = torch.empty(sc.n, dtype=torch.int32, device="cuda")
+    for bad in [(x.float(), k, i), (x.t(), k, i), (x, k[:-1], i), (x, k, k), (x.cpu(), k, i)]:
+        with pytest.raises(wbsph.WbsphError) as ei:
+            sim.sort_cells_noalloc(*bad)
+        assert ei.value.code == -1
+    ref = _regular(sc)
+    keys, ids = _noalloc(sim, sc)
+    assert np.array_equal(keys, ref[0]) and np.array_equal(ids, ref[1])
+
+
 def test_noalloc_sort_rejects_sizes_beyond_its_limit():
     import torch
     from paper_2608_22269_gb300 import wbsph
