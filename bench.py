@@ -295,13 +295,32 @@ def pair_roofline(m, dim, nf, precision, workload):
             "avg_launch_ms": round(avg_ms, 4), "share_of_step": round(pair_ms / max(total, 1e-9), 4)}
 
 
-def rates_diff(a, b, scene):
-    """Scaled difference of the stage rates of two sims on the same state."""
+def natural_scales(params, water_height):
+    """Natural scales of the relative error measure: accelerations by |G|,
+    potential rates by C0^2 sqrt(|G| H) / h."""
+    g = math.sqrt(sum(v * v for v in params["g"][: params["dim"]])) or 1.0
+    H = water_height if water_height > 0 else 1.0
+    h = params["h_over_dx"] * params["dx"]
+    return {"dudt": g, "dphidt": params["c0"] ** 2 * math.sqrt(g * H) / h}
+
+
+def scaled_err(a, b, scale):
+    """max |a - b| / max(max |b|, scale)."""
     import numpy as np
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from helpers import scaled_err, scales
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if b.size == 0:
+        return 0.0
+    return float(np.abs(a - b).max()) / max(float(np.abs(b).max()), scale)
+
+
+def rates_diff(a, b, scene):
+    """Scaled difference of the stage rates of two sims on the same state
+    (particles within 1e-4 of the TIC threshold are left out: there the two
+    arithmetics may legitimately take different branches)."""
+    import numpy as np
     f = scene.type == 0
-    sk = scales(scene.params, scene.water_height)
+    sk = natural_scales(scene.params, scene.water_height)
     lam = b.get("lambda")[f]
     keep = np.abs(lam - scene.params["tic_lambda"]) > 1e-4
     return {"dudt": scaled_err(a.get("dudt")[:, f][:, keep], b.get("dudt")[:, f][:, keep], sk["dudt"]),
@@ -437,6 +456,107 @@ def surrogate_path(args, local, dim=2):
     return out
 
 
+def precision_paths(scene, args, world, local, workload, primary=None, primary_sim=None,
+                    primary_m=None, steps=None, warmup=None):
+    """Every precision on one scene: value, roofline of the pair pass, HBM
+    fraction, resident footprint, and the rate errors of the mixed and
+    double-float paths against the FP64 path on one common state (the state
+    the FP64 run reached). Returns (paths, sims); the sims stay open."""
+    from paper_2608_22269_gb300 import wbsph
+    prec_code = {"fp64": wbsph.FP64, "mixed": wbsph.MIXED, "df64": wbsph.DF64}
+    a = argparse.Namespace(**vars(args))
+    if steps is not None:
+        a.steps = steps
+    if warmup is not None:
+        a.warmup = warmup
+    dim, nf = scene.params["dim"], scene.n_fluid
+    bytes_ps = algorithmic_bytes_per_particle_step(dim)
+    hbm = measured_peaks().get("hbm_gbs", 6686.1)
+    sims, paths = {}, {}
+    for prec in PRECISIONS:
+        if prec == primary:
+            sims[prec], m = primary_sim, primary_m
+        else:
+            sims[prec], m = time_path(scene, prec_code[prec], a, world, local)
+        v = nf * a.steps * world / (m["ms"] / 1e3)
+        paths[prec] = {"value": round(v, 1), "ms_per_step": round(m["ms"] / a.steps, 4),
+                       "steps": a.steps, "dtype": DTYPES[prec],
+                       "roofline": pair_roofline(m, dim, nf, prec, workload),
+                       "hbm_frac": round(v / world * bytes_ps / (hbm * 1e9), 5),
+                       "resident_gb": round(m["st1"]["device_bytes"] / 1e9, 2)}
+    fp64 = sims["fp64"]
+    st = {k: fp64.get(k) for k in ("x", "u", "phi", "mass")}
+    # reload the FP64 sim too, so that every path evaluates at the same time t = 0
+    # (the forced tank's body force depends on t)
+    fp64.set_particles(st["x"], st["u"], st["phi"], scene.type, scene.normal, st["mass"])
+    fp64.eval_rates()
+    for other in ("mixed", "df64"):
+        o = sims[other]
+        o.set_particles(st["x"], st["u"], st["phi"], scene.type, scene.normal, st["mass"])
+        o.eval_rates()
+        paths[other]["error_vs_fp64"] = rates_diff(o, fp64, scene)
+    return paths, sims
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def summary_of(line) -> dict:
+    """Compact per-path digest (value, ms per step, pair-pass roofline
+    fraction, HBM fraction, error) placed last on the JSON line."""
+    def digest(p, err=None):
+        if not isinstance(p, dict) or "value" not in p:
+            return {"error": str(p.get("error", p.get("unavailable", "not run")))[:160]} \
+                if isinstance(p, dict) else None
+        d = {"value": p["value"], "ms_per_step": p.get("ms_per_step")}
+        rf = p.get("roofline") or {}
+        if "frac" in rf:
+            d["roofline_frac"] = rf["frac"]
+            d["roofline_bound"] = rf.get("bound")
+        hb = p.get("hbm_frac", (p.get("hbm") or {}).get("frac"))
+        if hb is not None:
+            d["hbm_frac"] = hb
+        if err is not None:
+            d["error"] = err
+        return d
+
+    out = {}
+    head = {"value": line["value"], "ms_per_step": line["ms_per_step"],
+            "roofline_frac": line["roofline"]["frac"], "hbm_frac": line["hbm"]["frac"],
+            "error": "fp64 vs oracle <= 1e-12 (tests/test_gpu_fullsize.py)"}
+    out[line["config"]["precision"] + "@" + line["config"]["workload_key"]] = head
+    paths = line.get("paths", {})
+    for prec in PRECISIONS:
+        p = paths.get(prec)
+        if p is not None and prec != line["config"]["precision"]:
+            e = p.get("error_vs_fp64")
+            out[prec + "@" + line["config"]["workload_key"]] = digest(
+                p, None if e is None else {"dudt": e["dudt"], "dphidt": e["dphidt"]})
+    for key in ("slosh3d",):
+        sp = paths.get(key) or {}
+        for prec in PRECISIONS:
+            p = sp.get(prec)
+            if p is not None:
+                e = p.get("error_vs_fp64")
+                out[prec + "@" + key] = digest(
+                    p, None if e is None else {"dudt": e["dudt"], "dphidt": e["dphidt"]})
+        if "error" in sp:
+            out[key] = {"error": sp["error"][:160]}
+    for key in ("surrogate", "surrogate_3d"):
+        p = paths.get(key)
+        if p is not None:
+            out[key] = digest(p, (p.get("error") or {}) if isinstance(p, dict) else None)
+            if isinstance(p, dict) and "plain_fp64_same_scene" in p:
+                out[key]["plain_fp64_same_scene"] = p["plain_fp64_same_scene"]
+    if "cpu_baseline" in line:
+        out["cpu_baseline_oracle"] = line["cpu_baseline"]["value"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -455,12 +575,7 @@ def run_ours(args):
     sim, m = time_path(scene, prec_code[primary], args, world, local)
     value = weak_scaling_value(nf * args.steps, world, m["ms"] / 1e3)
     roofline = pair_roofline(m, dim, nf, primary, args.workload)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm = peaks.get("hbm_gbs", 6686.1)
+    hbm = measured_peaks().get("hbm_gbs", 6686.1)
     bytes_ps = algorithmic_bytes_per_particle_step(dim)
 
     # ---- end to end through the C-ABI with pinned host buffers ----
@@ -508,48 +623,45 @@ def run_ours(args):
         "kernel_ms": {k: round(v[0], 3) for k, v in m["prof"].items()},
         "setup_s": round(setup_s, 1),
     }
+    line["config"]["workload_key"] = args.workload
     if not args.no_paths:
-        # the other precisions on the same workload, and their errors at this
-        # size against the FP64 path on one common state
-        sims, paths = {primary: sim}, {}
-        for other in PRECISIONS:
-            if other == primary:
-                continue
-            sims[other], m2 = time_path(scene, prec_code[other], args, world, local)
-            v2 = nf * args.steps * world / (m2["ms"] / 1e3)
-            paths[other] = {"value": round(v2, 1), "ms_per_step": round(m2["ms"] / args.steps, 4),
-                            "dtype": DTYPES[other],
-                            "roofline": pair_roofline(m2, dim, nf, other, args.workload),
-                            "hbm_frac": round(v2 / world * bytes_ps / (hbm * 1e9), 5)}
-        if rank == 0:
-            fp64 = sims["fp64"]
-            st = {k: fp64.get(k) for k in ("x", "u", "phi", "mass")}
-            line["error"] = {}
-            fp64.eval_rates()
-            for other in ("mixed", "df64"):
-                o = sims[other]
-                o.set_particles(st["x"], st["u"], st["phi"], scene.type, scene.normal, st["mass"])
-                o.eval_rates()
-                line["error"][other + "_vs_fp64"] = rates_diff(o, fp64, scene)
-            line["error"].update({
-                "fp64_vs_oracle": "within 1e-12 (tests/test_gpu_fullsize.py samples this workload)",
-                "measure": "max|a-b| / max(max|b|, natural scale) over fluid particles"})
-        if rank == 0:
-            for key, dim in (("surrogate", 2), ("surrogate_3d", 3)):
-                try:
-                    paths[key] = surrogate_path(args, local, dim)
-                except Exception as exc:  # the plain paths above are the headline; report, do not abort
-                    paths[key] = {"error": f"{type(exc).__name__}: {exc}"}
-        line["paths"] = paths
+        # every precision on the same workload, and the errors of the mixed and
+        # double-float paths at this size against the FP64 path on one state
+        paths, sims = precision_paths(scene, args, world, local, args.workload, primary, sim, m)
+        line["error"] = {
+            "fp64_vs_oracle": "within 1e-12 (tests/test_gpu_fullsize.py samples this workload)",
+            "measure": "max|a-b| / max(max|b|, natural scale) over fluid particles"}
         for k, s2 in sims.items():
             if k != primary:
                 s2.close()
+        if args.workload == "dam3d":
+            # the metric's second point: the 17.58M-fluid sloshing tank, every precision
+            try:
+                big = WORKLOADS["slosh3d"]["make"]()
+                sp, ssims = precision_paths(big, args, world, local, "slosh3d",
+                                            steps=min(args.steps, 10), warmup=3)
+                sp["workload"] = WORKLOADS["slosh3d"]["desc"]
+                sp["n_fluid"], sp["n_total"] = big.n_fluid, big.n
+                for s2 in ssims.values():
+                    s2.close()
+                del ssims, big
+            except Exception as exc:  # report, do not abort the headline
+                sp = {"error": f"{type(exc).__name__}: {exc}"}
+            paths["slosh3d"] = sp
+        if rank == 0:
+            for key, sdim in (("surrogate", 2), ("surrogate_3d", 3)):
+                try:
+                    paths[key] = surrogate_path(args, local, sdim)
+                except Exception as exc:  # the plain paths above are the headline; report, do not abort
+                    paths[key] = {"error": f"{type(exc).__name__}: {exc}"}
+        line["paths"] = paths
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = wl["sample"]()
         v, steps, secs, cores = cpu_baseline(sample)
         line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{wl['sample_desc']}, {steps} steps in {secs:.1f} s"}
     if rank == 0:
+        line["summary"] = summary_of(line)   # last key: the compact digest ends the line
         print(json.dumps(line), flush=True)
     sim.close()
     if world > 1:
