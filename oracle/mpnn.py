@@ -3,23 +3,32 @@
 Plain PyTorch CPU float64 statement of the network that the CUDA surrogate
 kernels evaluate in BF16 with FP32 accumulation; gradients come from
 autograd of this forward and are pinned by central finite differences in
-the tests. Only the tests may import this module.
+the tests. Only the tests may import this module. The paper has no learned
+part: this network is the surrogate of the pair pass that the rollouts use
+between plain re-anchoring steps.
 
 Network (dimension d, hidden H = 64, three message-passing layers):
-  node input  f_i = normalised (U_i, rho_i/rho0 - 1, phi_i, dummy flag)   (d + 3)
-  edge input  g_ij = ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U, (phi_j - phi_i)/s_phi)
-              for receiver i, sender j (2d + 2; s = the node-feature scales)
+  hydrostatic split  phi'_i = phi_i - phi_hs(x_i), phi_hs(x) = G.x + |G| H
+                     (G the constant body force, H the scene's water height;
+                     the same split as the mixed path), so that at rest the
+                     potential input carries only the departure from balance
+  node input  f_i = (U_i, rho_i/rho0 - 1, phi'_i) minus node_mean over
+              node_std, then the dummy flag                              (d + 3)
+  edge input  g_ij = ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U, (phi'_j - phi'_i)/s_phi)
+              for receiver i, sender j (2d + 2; s_U, s_phi the edge scales)
   MLP(x) = W2 silu(W1 x + b1) + b2 (weights stored input-major: x @ W)
-  h = MLP_node_enc(f), e = MLP_edge_enc(g)
-  per layer: e <- e + MLP_e([e_ij, h_i, h_j]);  a_i = sum_j e_ij;  h <- h + MLP_n([h_i, a_i])
+  h = MLP_enc(f)
+  per layer: m_i = sum_j MLP_e([g_ij, h_i, h_j]);  h <- h + MLP_n([h_i, m_i])
   output y_i = MLP_dec(h_i)  (d + 1: normalised DU/Dt and Dphi/Dt)
-Edges: every fluid receiver i with every particle j within 2h (dummies only
-send). Loss: mean over fluid particles and output components of the squared
-difference to the normalised targets.
+No state is kept per edge: every layer's messages are formed from the edge
+inputs g_ij and the node states. Edges: every fluid receiver i with every
+particle j within 2h (dummies only send). Loss: mean over fluid particles and
+output components of the squared difference to the normalised targets.
 
 Flat parameter layout (shared with the CUDA library): blocks in the order
-node encoder, edge encoder, (edge MLP, node MLP) per layer, decoder; each
-block W1 [in][H], b1 [H], W2 [H][out], b2 [out], row-major.
+node encoder, (edge MLP, node MLP) per layer, decoder; each block W1 [in][H],
+b1 [H], W2 [H][out], b2 [out], row-major; the edge MLP's W1 rows are the
+2d + 2 edge inputs, then h_i (64 rows), then h_j (64 rows).
 """
 from __future__ import annotations
 
@@ -32,9 +41,9 @@ LAYERS = 3
 
 def block_dims(dim: int, hidden: int = HIDDEN, layers: int = LAYERS):
     fn, fe, fo = dim + 3, 2 * dim + 2, dim + 1
-    dims = [("enc_n", fn, hidden), ("enc_e", fe, hidden)]
+    dims = [("enc_n", fn, hidden)]
     for l in range(layers):
-        dims += [(f"mp{l}_e", 3 * hidden, hidden), (f"mp{l}_n", 2 * hidden, hidden)]
+        dims += [(f"mp{l}_e", fe + 2 * hidden, hidden), (f"mp{l}_n", 2 * hidden, hidden)]
     dims.append(("dec", hidden, fo))
     return dims
 
@@ -57,13 +66,17 @@ def unflatten(theta: torch.Tensor, dim: int, hidden: int = HIDDEN, layers: int =
 
 def init_params(dim: int, seed: int = 0, hidden: int = HIDDEN, layers: int = LAYERS) -> np.ndarray:
     """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases; the last
-    layer of every processor MLP is scaled by 0.1 so residual updates start small."""
+    layer of every processor MLP is scaled by 0.1 so that the residual updates
+    start small (the edge MLP's by a further 1/8: its outputs are summed over
+    the receiver's neighbours)."""
     rng = np.random.default_rng(seed)
     parts = []
     for name, i, o in block_dims(dim, hidden, layers):
         s1, s2 = 1.0 / np.sqrt(i), 1.0 / np.sqrt(hidden)
         if name.startswith("mp"):
             s2 *= 0.1
+        if name.endswith("_e"):
+            s2 /= 8.0
         parts += [rng.uniform(-s1, s1, i * hidden), np.zeros(hidden),
                   rng.uniform(-s2, s2, hidden * o), np.zeros(o)]
     return np.concatenate(parts).astype(np.float32)
@@ -78,26 +91,34 @@ def forward(theta, dim, node_in, recv, send, edge_in, hidden=HIDDEN, layers=LAYE
     """node_in (N, d+3), recv/send (E,) int64, edge_in (E, 2d+2) -> (N, d+1)."""
     P = unflatten(theta, dim, hidden, layers)
     h = _mlp(node_in, P["enc_n"])
-    e = _mlp(edge_in, P["enc_e"])
     for l in range(layers):
-        e = e + _mlp(torch.cat([e, h[recv], h[send]], dim=1), P[f"mp{l}_e"])
-        agg = torch.zeros(h.shape, dtype=h.dtype).index_add(0, recv, e)
-        h = h + _mlp(torch.cat([h, agg], dim=1), P[f"mp{l}_n"])
+        msg = _mlp(torch.cat([edge_in, h[recv], h[send]], dim=1), P[f"mp{l}_e"])
+        m = torch.zeros(h.shape, dtype=h.dtype).index_add(0, recv, msg)
+        h = h + _mlp(torch.cat([h, m], dim=1), P[f"mp{l}_n"])
     return _mlp(h, P["dec"])
 
 
-def graph_and_features(params, x, u, phi, typ, node_mean, node_std, row=None, col=None):
+def hydrostatic_potential(params, x, water_height):
+    """phi_hs(x) = G.x + |G| H with the constant body force G of the scene."""
+    d = int(params["dim"])
+    g = np.asarray(params["g"][:d], dtype=np.float64)
+    return g @ np.asarray(x, dtype=np.float64)[:d] + np.linalg.norm(g) * water_height
+
+
+def graph_and_features(params, x, u, phi, typ, node_mean, node_std, edge_std, water_height,
+                       row=None, col=None):
     """Edges and network inputs of a particle state, by the definitions above.
 
     u and phi are the stage's values (wall particles after their update from
     the nearest fluid particle); row/col is the oracle's neighbour CSR of x
     (computed here when None). Receivers are the fluid particles in ascending
     index, each with its neighbours within 2h in ascending index as senders.
-    Node inputs: (U, rho/rho0 - 1, phi) minus node_mean over node_std, then the
-    dummy flag; edge inputs: ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U,
-    (phi_j - phi_i)/s_phi) with s the node_std entries. Both are rounded to
-    BF16, the precision the network reads them in. Returns recv, send (int64),
-    node_in (N, d + 3) and edge_in (E, 2d + 2) as float64."""
+    Node inputs: (U, rho/rho0 - 1, phi') minus node_mean over node_std, then
+    the dummy flag; edge inputs: ((x_j - x_i)/h, |x_j - x_i|/h,
+    (U_j - U_i)/s_U, (phi'_j - phi'_i)/s_phi) with (s_U, s_phi) = edge_std.
+    Both are rounded to BF16, the precision the network reads them in.
+    Returns recv, send (int64), node_in (N, d + 3) and edge_in (E, 2d + 2) as
+    float64."""
     from . import oracle as O
     d = int(params["dim"])
     x = np.asarray(x, dtype=np.float64)
@@ -106,6 +127,7 @@ def graph_and_features(params, x, u, phi, typ, node_mean, node_std, row=None, co
     typ = np.asarray(typ)
     mean = np.asarray(node_mean, dtype=np.float64)
     std = np.asarray(node_std, dtype=np.float64)
+    es = np.asarray(edge_std, dtype=np.float64)
     if row is None:
         row, col = O.neighbors(params, x)
     fl = np.nonzero(typ == 0)[0]
@@ -117,11 +139,12 @@ def graph_and_features(params, x, u, phi, typ, node_mean, node_std, row=None, co
     send = np.asarray(col, dtype=np.int64)[start + within]
     h = params["h_over_dx"] * params["dx"]
     rho = O.density(params, phi)
-    raw = np.r_[u[:d], (rho / params["rho0"] - 1.0)[None], phi[None]]
+    phip = phi - hydrostatic_potential(params, x, water_height)
+    raw = np.r_[u[:d], (rho / params["rho0"] - 1.0)[None], phip[None]]
     node_in = np.c_[((raw - mean[:d + 2, None]) / std[:d + 2, None]).T, (typ != 0).astype(np.float64)]
     r = x[:d, send] - x[:d, recv]
     edge_in = np.c_[(r / h).T, np.sqrt((r * r).sum(axis=0)) / h,
-                    ((u[:d, send] - u[:d, recv]) / std[:d, None]).T, (phi[send] - phi[recv]) / std[d + 1]]
+                    ((u[:d, send] - u[:d, recv]) / es[0]).T, (phip[send] - phip[recv]) / es[1]]
     return (recv, send, bf16_round(node_in).astype(np.float64),
             bf16_round(edge_in).astype(np.float64))
 

@@ -3,8 +3,10 @@
 The reference's gradients come from autograd of its forward; they are
 pinned by central finite differences. Its forward is pinned by properties
 fixed by the definition: permutation equivariance, batching additivity of
-disjoint graphs, independence of absolute position, and an isolated
-receiver reducing to the encoder-processor-decoder chain without messages.
+disjoint graphs, an isolated receiver reducing to the encoder-processor-
+decoder chain without messages, a layer's message sum taken apart edge by
+edge, and the hydrostatic split of its inputs (a state at rest gives zero
+potential differences on every edge).
 """
 import numpy as np
 import pytest
@@ -90,7 +92,42 @@ def test_isolated_receiver_has_no_messages():
 def test_parameter_count_and_layout():
     assert mpnn.num_params(2) == mpnn.init_params(2).size
     P = mpnn.unflatten(torch.zeros(mpnn.num_params(3), dtype=torch.float64), 3)
-    assert P["mp0_e"][0].shape == (192, 64) and P["dec"][2].shape == (64, 4)
+    assert P["mp0_e"][0].shape == (8 + 128, 64) and P["dec"][2].shape == (64, 4)
+    assert P["enc_n"][0].shape == (6, 64) and "enc_e" not in P
+    # 2D: encoder 5*64+64+64*64+64, per layer edge (6+128)*64+64+64*64+64 and
+    # node 128*64+64+64*64+64, decoder 64*64+64+64*3+3
+    assert mpnn.num_params(2) == 4544 + 3 * (12800 + 12416) + 4355
+
+
+def test_message_sum_taken_apart_edge_by_edge():
+    """One layer's aggregate m_i = sum_j MLP_e([g_ij, h_i, h_j]), evaluated
+    here edge by edge with explicit loops and numpy for a one-layer network:
+    the decoder input must equal h + MLP_n([h, m]). Catches a wrong sender or
+    receiver gather, a missing sum or a residual on the messages."""
+    dim = 2
+    node, recv, send, edge = _graph(n=9, dim=dim, seed=11, deg=3)
+    theta = mpnn.init_params(dim, seed=7, layers=1).astype(np.float64)
+    theta += np.random.default_rng(8).normal(scale=0.1, size=theta.shape)
+    P = {k: tuple(t.numpy() for t in v)
+         for k, v in mpnn.unflatten(torch.as_tensor(theta), dim, layers=1).items()}
+
+    def silu(z):
+        return z / (1.0 + np.exp(-z))
+
+    def mlp(x, p):
+        return silu(x @ p[0] + p[1]) @ p[2] + p[3]
+
+    h = mlp(node, P["enc_n"])
+    m = np.zeros_like(h)
+    for e in range(recv.size):
+        i, j = recv[e], send[e]
+        m[i] += mlp(np.concatenate([edge[e], h[i], h[j]]), P["mp0_e"])
+    h1 = h + mlp(np.concatenate([h, m], axis=1), P["mp0_n"])
+    want = mlp(h1, P["dec"])
+    with torch.no_grad():
+        got = mpnn.forward(torch.as_tensor(theta), dim, torch.as_tensor(node), torch.as_tensor(recv),
+                           torch.as_tensor(send), torch.as_tensor(edge), layers=1).numpy()
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12)
 
 
 def test_graph_and_features_by_hand():
@@ -101,24 +138,46 @@ def test_graph_and_features_by_hand():
     import math
 
     from paper_2608_22269_gb300 import scenes as S
-    p = S.default_params(2, dx=0.1, c0=10.0)
+    p = S.default_params(2, dx=0.1, c0=10.0)                  # G = (0, -9.81)
     x = np.array([[0.5, 0.6, 0.5, 0.9], [0.5, 0.5, 0.3, 0.5]])
     u = np.array([[0.1, -0.2, 0.05, 0.0], [0.3, 0.0, -0.1, 0.0]])
     phi = np.array([2.0, 1.5, 4.0, 0.0])
     typ = np.array([0, 0, 1, 0], dtype=np.uint8)
     mean = np.array([0.1, -0.1, 0.0, 1.0], dtype=np.float32)
     std = np.array([0.5, 0.25, 0.001, 2.0], dtype=np.float32)
-    recv, send, node_in, edge_in = mpnn.graph_and_features(p, x, u, phi, typ, mean, std)
+    estd = np.array([0.4, 0.8], dtype=np.float32)
+    H = 0.7                                                    # water height of the split
+    recv, send, node_in, edge_in = mpnn.graph_and_features(p, x, u, phi, typ, mean, std, estd, H)
     assert recv.tolist() == [0, 0, 1, 1] and send.tolist() == [1, 2, 0, 2]
     h = 0.13
     m, sd = mean.astype(np.float64), std.astype(np.float64)  # the FP32 values the library holds
+    es = estd.astype(np.float64)
+    # phi' = phi - (G.x + |G| H) = phi - 9.81 (H - y)
+    phip = [phi[k] - 9.81 * (H - x[1, k]) for k in range(4)]
     for k in range(4):
         rho = 1000.0 * math.exp(phi[k] / 100.0)  # linear EOS, C0 = 10
         want = [(u[0, k] - m[0]) / sd[0], (u[1, k] - m[1]) / sd[1], (rho / 1000.0 - 1.0) / sd[2],
-                (phi[k] - m[3]) / sd[3], 1.0 if k == 2 else 0.0]
+                (phip[k] - m[3]) / sd[3], 1.0 if k == 2 else 0.0]
         assert np.array_equal(node_in[k], mpnn.bf16_round(np.array(want)).astype(np.float64))
     for e, (i, j) in enumerate([(0, 1), (0, 2), (1, 0), (1, 2)]):
         rx, ry = x[0, j] - x[0, i], x[1, j] - x[1, i]
-        want = [rx / h, ry / h, math.hypot(rx, ry) / h, (u[0, j] - u[0, i]) / sd[0],
-                (u[1, j] - u[1, i]) / sd[1], (phi[j] - phi[i]) / sd[3]]
+        want = [rx / h, ry / h, math.hypot(rx, ry) / h, (u[0, j] - u[0, i]) / es[0],
+                (u[1, j] - u[1, i]) / es[0], (phip[j] - phip[i]) / es[1]]
         assert np.allclose(edge_in[e], mpnn.bf16_round(np.array(want)), rtol=0, atol=1e-12), e
+
+
+def test_hydrostatic_state_has_no_potential_differences():
+    """At rest with phi = G.x + |G| H (the hydrostatic state of Eq. eqSol as
+    the scenes write it) every edge's potential input vanishes and every
+    node's phi' is zero, whatever the positions: the split removes the
+    hydrostatic part exactly (up to the rounding of phi itself)."""
+    from paper_2608_22269_gb300 import scenes as S
+    sc = S.jitter(S.dam_break_2d(dx=0.02, width=0.8, column=(0.3, 0.2)), 0.2, seed=3)
+    f = sc.type == 0
+    phi = 9.81 * (sc.water_height - sc.x[1])               # at the jittered positions
+    mean = np.zeros(4, np.float32)
+    std = np.ones(4, np.float32)
+    recv, send, node_in, edge_in = mpnn.graph_and_features(sc.params, sc.x, sc.u, phi, sc.type, mean,
+                                                           std, np.ones(2, np.float32), sc.water_height)
+    assert recv.size > 1000
+    assert np.abs(edge_in[:, 5]).max() <= 1e-14 and np.abs(node_in[f, 3]).max() <= 1e-14
