@@ -213,14 +213,24 @@ int wbsph_get_profile(wbsph_handle h, double* ms, int64_t* launches, int reset);
 
 /* ---- learned surrogate (the paper has no learned part) ----------------
  * A message-passing network over the same neighbour lists predicts the
- * stage rates (DU/Dt, Dphi/Dt) of fluid particles from node features
- * (U, rho/rho0 - 1, phi, dummy flag) and edge features (r/h, |r|/h and the
- * differences of U and phi scaled by the node-feature scales). Three
- * layers, hidden width 64, BF16 weights and activations, FP32 accumulation
- * on the tensor cores; trained on the GPU against the plain FP64 rates of
- * the states it is shown. Parameters are a flat FP32 vector: blocks node
- * encoder, edge encoder, (edge MLP, node MLP) per layer, decoder; each
- * W1 [in][64], b1 [64], W2 [64][out], b2 [out], row-major. */
+ * stage rates (DU/Dt, Dphi/Dt) of fluid particles. Node inputs: (U,
+ * rho/rho0 - 1, phi') normalised, and a dummy flag, with the hydrostatic
+ * split phi' = phi - phi_hs(x), phi_hs = G.x + |G| H (H the handle's water
+ * height, as the mixed path); edge inputs: ((x_j - x_i)/h, |x_j - x_i|/h,
+ * (U_j - U_i)/s_U, (phi'_j - phi'_i)/s_phi). Per layer the message of
+ * receiver i is m_i = sum_j MLP_e([g_ij, h_i, h_j]) and h_i += MLP_n([h_i,
+ * m_i]); nothing is kept per edge, so inference allocates per node only.
+ * Three layers, hidden width 64, BF16 weights and activations, FP32
+ * accumulation on the tensor cores (tcgen05); trained on the GPU against
+ * the plain FP64 rates of the states it is shown. Parameters are a flat
+ * FP32 vector: blocks node encoder, (edge MLP, node MLP) per layer,
+ * decoder; each W1 [in][64], b1 [64], W2 [64][out], b2 [out], row-major;
+ * the edge MLP's W1 rows are the 2 dim + 2 edge inputs, then h_i, then h_j.
+ * This interface departs from a load-from-file / train-from-a-directory
+ * pair: parameters and normalisation are set from host arrays, and
+ * training is one step at a time on a state the caller loads, so that the
+ * caller owns files, datasets and schedules. */
+enum { WBSPH_SURROGATE_NETWORK = 0, WBSPH_SURROGATE_FROZEN = 1 };
 typedef struct wbsph_surrogate_s* wbsph_surrogate;
 typedef struct {
   int dim;            /* 2 or 3 */
@@ -242,9 +252,16 @@ int64_t wbsph_surrogate_num_params(wbsph_surrogate s);
 /* host FP32 arrays of wbsph_surrogate_num_params() values */
 int wbsph_surrogate_set_params(wbsph_surrogate s, const float* params);
 int wbsph_surrogate_get_params(wbsph_surrogate s, float* params);
-/* node mean/std: dim+2 values (U, rho/rho0-1, phi); output mean/std: dim+1 */
+/* node mean/std: dim+2 values (U, rho/rho0-1, phi'); edge_std: 2 values
+ * (s_U, s_phi) of the edge inputs; output mean/std: dim+1. Host arrays. */
 int wbsph_surrogate_set_normalization(wbsph_surrogate s, const float* node_mean, const float* node_std,
-                                      const float* out_mean, const float* out_std);
+                                      const float* edge_std, const float* out_mean, const float* out_std);
+/* WBSPH_SURROGATE_NETWORK (default): the network predicts the rates.
+ * WBSPH_SURROGATE_FROZEN: a control for measuring what the network gains:
+ * surrogate stages reuse, per particle, the rates of the last plain stage of
+ * the rollout (wbsph_step_surrogate only; train, eval and debug need the
+ * network mode and return WBSPH_E_STATE otherwise). */
+int wbsph_surrogate_set_mode(wbsph_surrogate s, int mode);
 /* One training step on the sim's current state: plain FP64 rates as targets,
  * forward, MSE loss on normalised outputs, backward, Adam with rate lr.
  * Synchronises; *loss (nullable) receives the loss before the update. */
@@ -263,9 +280,10 @@ int wbsph_surrogate_debug(wbsph_surrogate s, wbsph_handle h, int64_t* n_edges, u
                           uint32_t* send_ids, float* edge_feat, float* node_feat, uint32_t* fluid_ids,
                           float* out, float* grad, double* loss);
 /* Advance nsteps SSP-RK2 steps with surrogate rates; every anchor_every-th
- * step is a plain FP64 step, and at each anchor the surrogate's DU/Dt is
- * compared with the plain one on the same state (relative L2 over fluid).
- * If it exceeds tau the next window runs plain (fallback). Synchronises. */
+ * step, starting with the first, is a plain FP64 step (an anchor), and at
+ * each anchor the surrogate's DU/Dt is compared with the plain one on the
+ * same state (relative L2 over fluid). If it exceeds tau the next window
+ * runs plain (fallback). anchor_every = 0: no anchors. Synchronises. */
 int wbsph_step_surrogate(wbsph_handle h, wbsph_surrogate s, int64_t nsteps, int anchor_every, double tau,
                          wbsph_anchor_stats* stats);
 void wbsph_surrogate_destroy(wbsph_surrogate s);

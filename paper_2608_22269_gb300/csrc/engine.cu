@@ -900,6 +900,10 @@ int surrogate_loss(wbsph_surrogate s, const Params& p, const State& st, const Wo
                    cudaStream_t cs, int train, float lr, double* loss_out, const float* dout_override,
                    float* grad_out);
 int64_t surrogate_edges(wbsph_surrogate s);
+int surrogate_stage_launches(wbsph_surrogate s, int64_t nf);
+int surrogate_mode(wbsph_surrogate s);
+int surrogate_plain_rates(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n, int64_t nf,
+                          int64_t n_ids, cudaStream_t cs);
 const float* surrogate_out(wbsph_surrogate s);
 const uint32_t* surrogate_recv(wbsph_surrogate s);
 const uint32_t* surrogate_send(wbsph_surrogate s);
@@ -932,11 +936,10 @@ static int surrogate_stage(wbsph_s* h, wbsph_surrogate s, int stage2) {
     ProfScope ps(h, WBSPH_K_PAIR);
     rc = surrogate_stage_rates(s, h->P, h->A, h->W, h->n, h->nf, st);
   }
-  // prepass (dummy update, volumes), time step, and the surrogate stage's 22
-  // kernels: neighbour lists, row-pointer scan (3), graph fill, node features,
-  // two encoders, 3 x (node projections, edge MLP, aggregation, node MLP),
-  // decoder, rates
-  h->launches += (h->n ? (h->nd ? 2 : 1) : 0) + (stage2 ? 0 : 1) + (h->nf ? 22 : 0);
+  // prepass (dummy update, volumes), time step, and the surrogate stage's
+  // kernels (network: neighbour lists, node inputs, encoder, one fused
+  // kernel per layer, decoder, rates; frozen-rates control: one)
+  h->launches += (h->n ? (h->nd ? 2 : 1) : 0) + (stage2 ? 0 : 1) + surrogate_stage_launches(s, h->nf);
   if (rc) return fail(h, rc, "surrogate stage failed");
   return check_launch(h, "surrogate stage");
 }
@@ -1035,21 +1038,29 @@ extern "C" int wbsph_step_surrogate(wbsph_handle h, wbsph_surrogate s, int64_t n
   double* ref = nullptr;  // copy of the surrogate DU/Dt at an anchor, then error sums
   CK(cudaMallocAsync((void**)&ref, ((size_t)d * (h->n > 0 ? h->n : 1) + 2) * sizeof(double), h->stream));
   int64_t plain_until = -1;
+  bool have_plain = false;  // a plain stage has run (the frozen-rates control needs one)
   for (int64_t k = 0; k < nsteps && !rc; ++k) {
-    bool anchor = anchor_every > 0 && (k + 1) % anchor_every == 0;
+    bool anchor = anchor_every > 0 && k % anchor_every == 0;
     bool plain = anchor || k < plain_until;
+    // the frozen-rates control has nothing to compare before its first plain stage
+    bool compare = anchor && (have_plain || surrogate_mode(s) != WBSPH_SURROGATE_FROZEN);
     if ((rc = build(h, false))) break;
-    if (anchor) {
+    if (compare) {
       // surrogate rates at this state, kept for the comparison with the plain ones
       if ((rc = surrogate_stage(h, s, 0))) break;
       CK(cudaMemcpyAsync(ref, h->W.dudt, (size_t)d * h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     }
     if (plain) {
       if ((rc = rates(h, 0))) break;
+      if ((rc = surrogate_plain_rates(s, h->P, h->A, h->W, h->n, h->nf, h->n, h->stream))) {
+        rc = fail(h, rc, "surrogate: keeping the plain rates failed");
+        break;
+      }
+      have_plain = true;
     } else {
       if ((rc = surrogate_stage(h, s, 0))) break;
     }
-    if (anchor) {
+    if (compare) {
       double sums[2] = {0, 0};
       launch_rel_err(h->P, h->W, h->n, h->nf, ref, ref + (size_t)d * h->n, h->stream);
       CK(cudaMemcpyAsync(sums, ref + (size_t)d * h->n, 16, cudaMemcpyDeviceToHost, h->stream));

@@ -1,16 +1,18 @@
-// mpnn.cu -- BF16 message-passing surrogate of the pair pass: graph over the
-// same neighbour lists, fused two-layer MLP kernels on the tensor cores
-// (mma.sync m16n8k16, BF16 operands, FP32 accumulation) for inference and
-// training, segment sums, loss, Adam, and the surrogate stage rates.
+// mpnn.cu -- BF16 message-passing surrogate of the pair pass: the network
+// over the same neighbour lists, one fused tcgen05 kernel per message-passing
+// layer (inference and training forward), mma.sync MLP kernels for the node
+// encoder, the decoder and every backward pass, loss, Adam, and the
+// surrogate stage rates.
 //
 // Network (the paper has no learned part): node input f_i = normalised
-// (U_i, rho_i/rho0 - 1, phi_i) plus a dummy flag; edge input
-// ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U, (phi_j - phi_i)/s_phi) for
-// every fluid receiver i and every particle j within 2h (s = node scales); MLP(x) = W2 silu(W1 x + b1) + b2; node and edge encoders,
-// three layers of e <- e + MLP_e([e, h_i, h_j]), a_i = sum_j e_ij,
-// h <- h + MLP_n([h, a]), and a decoder to normalised (DU/Dt, Dphi/Dt).
-// Flat parameter layout: blocks node encoder, edge encoder, (edge MLP,
-// node MLP) per layer, decoder; each block W1 [in][64], b1, W2 [64][out], b2.
+// (U_i, rho_i/rho0 - 1, phi'_i) plus a dummy flag, phi' = phi - phi_hs(x);
+// edge input g_ij = ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U,
+// (phi'_j - phi'_i)/s_phi) for every fluid receiver i and every particle j
+// within 2h; MLP(x) = W2 silu(W1 x + b1) + b2; a node encoder, three layers
+// of m_i = sum_j MLP_e([g_ij, h_i, h_j]), h <- h + MLP_n([h, m]), and a
+// decoder to normalised (DU/Dt, Dphi/Dt). Flat parameter layout: blocks node
+// encoder, (edge MLP, node MLP) per layer, decoder; each block W1 [in][64],
+// b1, W2 [64][out], b2.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -122,26 +124,40 @@ struct MlpArgs {
   // gather sources
   const bf16* in;            // DIRECT: [rows][FEAT]; LIST: node table [n][64]
   const uint32_t* list;      // LIST: row -> node
-  const bf16* e;             // EDGE: [E][64]
+  const bf16* e;             // EDGE: edge inputs [E][8]
   const bf16* h;             // EDGE, NODE: [n][64]
   const uint32_t* recv;      // EDGE
   const uint32_t* send;      // EDGE
   const bf16* agg;           // NODE: [n][64]
   int kin, nout;             // true widths
+  int kg;                    // EDGE: edge inputs (2d + 2) at the head of the padded row [g | h_i | h_j]
   const bf16* w1; const float* b1; const bf16* w2; const float* b2;  // block parameters
   // forward outputs
   bf16* out_bf;              // [rows][64] (+ residual for EDGE/NODE)
   float* out_f;              // [rows][nout] (decoder)
   // backward
   const float* dout;         // [rows][nout] incoming gradient (EDGE/NODE/DIRECT: [rows][64])
-  float* din_row;            // EDGE: de_in, NODE: dh_in ([rows][64], = dout + dX[0:64])
-  float* dh;                 // EDGE: atomics into [n][64]; LIST: writes dh[list[row]]
+  float* din_row;            // NODE: dh_in ([rows][64], = dout + dX[0:64])
+  float* dh;                 // EDGE: atomics into [n][64] (h_i and h_j); LIST: writes dh[list[row]]
   float* dagg;               // NODE: [rows][64]
   float* gw1; float* gb1; float* gw2; float* gb2;  // FP32 parameter gradients
 };
 
 __device__ __forceinline__ int64_t arg_rows(const MlpArgs& a) {
   return a.rows_dev ? (int64_t)*a.rows_dev : a.rows;
+}
+
+// Padded input width of the edge MLP: the edge inputs padded to 16, h_i, h_j.
+constexpr int EDGE_KP = 16 + 2 * HID;
+
+// Row of the block's W1 (flat parameters) that multiplies padded input
+// column k, or -1 for a padding column. The edge MLP's W1 rows are the kg
+// edge inputs, then h_i and h_j; its padded input puts the edge inputs in
+// columns 0 .. 15.
+template <int MODE>
+__device__ __forceinline__ int param_row(const MlpArgs& a, int k) {
+  if (MODE == MODE_EDGE) return k < 16 ? (k < a.kg ? k : -1) : a.kg + (k - 16);
+  return k < a.kin ? k : -1;
 }
 
 // Gather of input element pair (k, k+1) of row `row` (KP padded width).
@@ -153,9 +169,9 @@ __device__ __forceinline__ uint32_t gather_pair(const MlpArgs& a, int64_t row, i
   } else if (MODE == MODE_LIST) {
     return *reinterpret_cast<const uint32_t*>(a.in + (int64_t)a.list[row] * HID + k);
   } else if (MODE == MODE_EDGE) {
-    if (k < HID) return *reinterpret_cast<const uint32_t*>(a.e + row * HID + k);
-    if (k < 2 * HID) return *reinterpret_cast<const uint32_t*>(a.h + (int64_t)a.recv[row] * HID + k - HID);
-    return *reinterpret_cast<const uint32_t*>(a.h + (int64_t)a.send[row] * HID + k - 2 * HID);
+    if (k < 16) return k < FEAT ? *reinterpret_cast<const uint32_t*>(a.e + row * FEAT + k) : 0u;
+    if (k < 16 + HID) return *reinterpret_cast<const uint32_t*>(a.h + (int64_t)a.recv[row] * HID + k - 16);
+    return *reinterpret_cast<const uint32_t*>(a.h + (int64_t)a.send[row] * HID + k - 16 - HID);
   } else {
     if (k < HID) return *reinterpret_cast<const uint32_t*>(a.h + row * HID + k);
     return *reinterpret_cast<const uint32_t*>(a.agg + row * HID + k - HID);
@@ -223,11 +239,7 @@ __device__ __forceinline__ const bf16* chunk_src(const MlpArgs& a, int64_t row, 
                                                  const uint32_t* I) {
   if (MODE == MODE_DIRECT) return a.in + row * FEAT;  // only chunk 0 carries data
   if (MODE == MODE_LIST) return a.in + (int64_t)I[r] * HID + c8 * 8;
-  if (MODE == MODE_EDGE) {
-    if (c8 < 8) return a.e + row * HID + c8 * 8;
-    if (c8 < 16) return a.h + (int64_t)I[r] * HID + (c8 - 8) * 8;
-    return a.h + (int64_t)I[TILE + r] * HID + (c8 - 16) * 8;
-  }
+  static_assert(MODE != MODE_EDGE, "the edge MLP runs forward in the fused layer kernel");
   if (c8 < 8) return a.h + row * HID + c8 * 8;
   return a.agg + row * HID + (c8 - 8) * 8;
 }
@@ -357,7 +369,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
         for (int hq = 0; hq < 2; ++hq) {
           int r = m0 + g + hq * 8, o = nt * 8 + 2 * t;
           float v0 = acc2[nt][2 * hq] + B2[o], v1 = acc2[nt][2 * hq + 1] + B2[o + 1];
-          if (MODE == MODE_EDGE || MODE == MODE_NODE) {
+          if (MODE == MODE_NODE) {
             __nv_bfloat162 res = *reinterpret_cast<const __nv_bfloat162*>(X + r * S::LDX + o);
             v0 += __bfloat162float(res.x);
             v1 += __bfloat162float(res.y);
@@ -380,99 +392,16 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Node projections for the split edge MLP. The first layer of the edge MLP
-// acts on [e_ij, h_i, h_j], so z1 = e_ij W1e + h_i W1r + h_j W1s + b1 with
-// W1 = [W1e; W1r; W1s] (64 rows each): the two node terms are computed once
-// per node here, P_i = [h_i W1r + b1 | h_i W1s] (BF16, FP32 accumulation), and
-// the edge kernel gathers them instead of h, leaving a 64-wide GEMM per edge.
-// ---------------------------------------------------------------------------
-constexpr int PJ_LD = HID + 8, PJ_LDO = 2 * HID + 8;
-
-__global__ void __launch_bounds__(MLP_THREADS) k_node_proj(const bf16* __restrict__ h, int64_t n,
-                                                           const bf16* __restrict__ w1, const float* __restrict__ b1,
-                                                           bf16* __restrict__ P) {
-  __shared__ __align__(16) bf16 Bt[2 * HID * PJ_LD];  // Bt[o][k] = W1[64 + k][o] | W1[128 + k][o - 64]
-  __shared__ __align__(16) bf16 At[TILE * PJ_LD];
-  __shared__ __align__(16) bf16 Ot[TILE * PJ_LDO];
-  for (int idx = threadIdx.x; idx < 2 * HID * HID; idx += MLP_THREADS) {
-    int o = idx / HID, k = idx % HID;
-    Bt[o * PJ_LD + k] = w1[(int64_t)(HID + (o >= HID ? HID : 0) + k) * HID + (o % HID)];
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int m0 = warp * 16;
-  for (int64_t tile = blockIdx.x; tile * TILE < n; tile += gridDim.x) {
-    const int64_t row0 = tile * TILE;
-    __syncthreads();  // Bt staged / At and Ot free
-    for (int idx = threadIdx.x; idx < TILE * (HID / 8); idx += MLP_THREADS) {
-      int r = idx / (HID / 8), c8 = idx % (HID / 8);
-      int64_t row = row0 + r;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (row < n) v = *reinterpret_cast<const uint4*>(h + row * HID + c8 * 8);
-      *reinterpret_cast<uint4*>(At + r * PJ_LD + c8 * 8) = v;
-    }
-    __syncthreads();
-    float acc[16][4];
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-    for (int kt = 0; kt < HID / 16; ++kt) {
-      uint32_t af[4];
-      ldsm_a(af, At, PJ_LD, m0, kt * 16);
-#pragma unroll
-      for (int nt = 0; nt < 16; nt += 2) {
-        uint32_t bq[4];
-        ldsm_b2(bq, Bt, PJ_LD, kt * 16, nt * 8);
-        mma16816(acc[nt], af, bq);
-        mma16816(acc[nt + 1], af, bq + 2);
-      }
-    }
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-      int c = nt * 8 + 2 * t;
-      // the first-layer bias rides on the receiver half
-      const float c0 = nt < 8 ? __ldg(b1 + c) : 0.f, c1 = nt < 8 ? __ldg(b1 + c + 1) : 0.f;
-      *reinterpret_cast<__nv_bfloat162*>(Ot + (m0 + g) * PJ_LDO + c) =
-          __floats2bfloat162_rn(acc[nt][0] + c0, acc[nt][1] + c1);
-      *reinterpret_cast<__nv_bfloat162*>(Ot + (m0 + g + 8) * PJ_LDO + c) =
-          __floats2bfloat162_rn(acc[nt][2] + c0, acc[nt][3] + c1);
-    }
-    __syncwarp();
-    // the warp's 16 rows of 256 bytes, 16-byte chunks
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int idx = q * 32 + lane, r = m0 + (idx >> 4), c16 = idx & 15;
-      int64_t row = row0 + r;
-      if (row < n)
-        *reinterpret_cast<uint4*>(P + row * 2 * HID + c16 * 8) = *reinterpret_cast<const uint4*>(Ot + r * PJ_LDO + c16 * 8);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Edge MLP of a message-passing layer on the 5th-generation tensor cores
-// (tcgen05). Per tile of 128 edges:
-//   z1 = e W1e + P_recv + P_send + b1    (64 x 64 GEMM, node terms from k_node_proj)
-//   e' = e + silu(z1) W2 + b2            (64 x 64 GEMM)
-// Operands sit in shared memory in the K-major 128-byte-swizzled layout the
-// tensor core reads through matrix descriptors (row r of 64 BF16 = 128 B at
-// r * 128, 16-byte chunk c stored at chunk c ^ (r % 8); 8-row groups 1024 B
-// apart); the FP32 accumulators live in tensor memory (TMEM, 64 columns per
-// tile in flight, lane = tile row) and are read back by the warp that owns
+// tcgen05 helpers. Operands sit in shared memory in the K-major
+// 128-byte-swizzled layout the tensor core reads through matrix descriptors
+// (row r of 64 BF16 = 128 B at r * 128, 16-byte chunk c stored at chunk
+// c ^ (r % 8); 8-row groups 1024 B apart); FP32 accumulators live in tensor
+// memory (TMEM: lane = operand row) and are read back by the warp that owns
 // those 32 lanes. One thread issues the MMAs and their commit to an
-// mbarrier; every wait on an mbarrier is bounded and a timeout is reported
-// through the error word.
+// mbarrier; every wait on an mbarrier is bounded.
 // ---------------------------------------------------------------------------
 constexpr int TC_ROWS = 128;
-constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TILE_BYTES = TC_ROWS * 128;        // 128 rows x 64 BF16
-#ifndef WBSPH_TC_SLOTS
-#define WBSPH_TC_SLOTS 2
-#endif
-// tiles in flight per CTA (operand slots of 2 x 16 KB each)
-constexpr int TC_SLOTS = WBSPH_TC_SLOTS;
-static_assert(TC_SLOTS >= 2 && TC_SLOTS <= 8, "slot count");
-constexpr size_t TC_SMEM_BYTES =
-    1024 + 2 * TC_SLOTS * TC_TILE_BYTES + 3 * 8192 + 2 * 64 * 4 + 128;  // slots, W, biases, barriers
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16,
@@ -505,28 +434,6 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// all 64 FP32 columns of this thread's TMEM lane in one load and one wait
-__device__ __forceinline__ void tc_ld64(uint32_t taddr, float v[64]) {
-  uint32_t r[64];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // bounded wait for the mbarrier phase `parity`; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit = TC_WAIT_LIMIT) {
   for (uint32_t it = 0; it < limit; ++it) {
@@ -540,27 +447,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
   }
   return false;
 }
-
-// TMA: 2D tile load into shared memory, completing on an mbarrier with a
-// byte count; 2D tile store from shared memory in a bulk group.
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(x), "r"(y), "r"(src)
-               : "memory");
-  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void tma_store_read_wait() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-__device__ __forceinline__ void tma_store_wait() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 
 // Check of the bounded wait itself: one thread waits on an mbarrier that
 // nothing arrives on; when the limit runs out it reports a timeout through the
@@ -581,296 +467,436 @@ __device__ __forceinline__ float silu_tanh(float z) {
   return fmaf(h, th, h);
 }
 
-// Modes. TC_EDGE: the edge MLP above. TC_ENC: an encoder MLP on rows of 8
-// BF16 input features (K = 16, zero padded): z1 = f W1 + b1,
-// out = silu(z1) W2 + b2, no projections, no residual. TC_NODE: the node MLP
-// of a layer, h' = h + silu([h, a] W1 + b1) W2 + b2 (K = 128: the h tile and
-// the aggregate tile are the two 64-wide K blocks of the first GEMM).
+// ---------------------------------------------------------------------------
+// Edge inputs of the network for receiver i and sender j, from the per-node
+// FP32 packs A = (x, y, z, phi') and B = (U, 0) (phi' = phi - phi_hs):
+// ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U, (phi'_j - phi'_i)/s_phi),
+// 2d + 2 values rounded to BF16 and zero padded to 8 (one 16-byte row). The
+// fused layer kernel and the training graph both form them here, so that
+// the backward sees exactly the inputs of the forward.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 edge_features(int dim, float4 ai, float4 bi, float4 aj, float4 bj,
+                                               float inv_h, float inv_su, float inv_sphi) {
+  const float rx = aj.x - ai.x, ry = aj.y - ai.y, rz = aj.z - ai.z;  // z = 0 in 2D
+  const float rn = sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+  float f[8];
+  if (dim == 3) {
+    f[0] = rx * inv_h; f[1] = ry * inv_h; f[2] = rz * inv_h; f[3] = rn * inv_h;
+    f[4] = (bj.x - bi.x) * inv_su; f[5] = (bj.y - bi.y) * inv_su; f[6] = (bj.z - bi.z) * inv_su;
+    f[7] = (aj.w - ai.w) * inv_sphi;
+  } else {
+    f[0] = rx * inv_h; f[1] = ry * inv_h; f[2] = rn * inv_h;
+    f[3] = (bj.x - bi.x) * inv_su; f[4] = (bj.y - bi.y) * inv_su; f[5] = (aj.w - ai.w) * inv_sphi;
+    f[6] = 0.f; f[7] = 0.f;
+  }
+  uint4 v;
+  v.x = pack2(__float2bfloat16(f[0]), __float2bfloat16(f[1]));
+  v.y = pack2(__float2bfloat16(f[2]), __float2bfloat16(f[3]));
+  v.z = pack2(__float2bfloat16(f[4]), __float2bfloat16(f[5]));
+  v.w = pack2(__float2bfloat16(f[6]), __float2bfloat16(f[7]));
+  return v;
+}
+
+// 16 FP32 columns of this thread's TMEM lane (32x32b shape), one wait
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// named barrier of one receiver group (256 threads), plain and with an AND vote
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "n"(256) : "memory");
+}
+__device__ __forceinline__ bool group_bar_and(int id, bool v) {
+  uint32_t res;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(res)
+      : "r"((uint32_t)v), "r"(id), "n"(256)
+      : "memory");
+  return res != 0;
+}
+
+__device__ __forceinline__ uint32_t bf2_u32(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
+__device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterpret_cast<__nv_bfloat162*>(&v); }
+
+// ---------------------------------------------------------------------------
+// One message-passing layer, fused, on tcgen05:
+//   m_i = sum_j MLP_e([g_ij, h_i, h_j]) = (sum_j silu(z_ij)) W2 + n_i b2,
+//   z_ij = g_ij W_g + h_i W_r + h_j W_s + b1,   h'_i = h_i + MLP_n([h_i, m_i]).
+// The second layer of the message MLP is linear, so it is applied once per
+// receiver after the sum; the per-edge work is the first layer, its SiLU and
+// the sum, and nothing per edge is ever written to memory.
 //
-// Pipeline over the CTA's tiles: TC_SLOTS operand slots (tile i in slot
-// i % TC_SLOTS), each with its own e tile, sender-projection tile (which
-// then holds silu(z1)) and TMA mbarrier, and two TMEM accumulators of 64
-// columns with their MMA mbarriers (tile i in accumulator i % 2). Iteration
-// i runs: epilogue 1 of tile i, MMA2 of tile i issued, MMA1 of tile i+1
-// issued (its loads were issued TC_SLOTS - 1 iterations earlier), epilogue
-// 2 and store of tile i, loads of tile i + TC_SLOTS into tile i's slot. So
-// each tile's GEMMs run while the other tile's epilogues do, and the loads
-// of TC_SLOTS - 1 tiles are in flight.
-// (The explicit minimum of one block lets the compiler keep the edge mode's
-// receiver projections and accumulator values in registers without spills.)
-enum { TC_EDGE = 0, TC_ENC = 1, TC_NODE = 2 };
+// A CTA runs MS_GROUPS independent groups of 256 threads; a group owns a
+// tile of 128 receivers (fluid particles in sorted order, one TMEM lane and
+// one smem operand row each; then tiles of wall particles, which receive no
+// messages). Warp w of a group serves lanes 32 (w % 4) .. + 31 and the
+// accumulator column half w / 4, so each thread holds 32 of the receiver's 64
+// running sums in registers. The group walks the receivers' k-major
+// neighbour lists, step k taking the k-th neighbour of every receiver:
+//   - gather (step k + 1, one step ahead): h_j rows by cp.async into a
+//     128-byte-swizzled K-major tile, the sender's FP32 packs into registers
+//     and from them the 16-wide edge-input row (K padded to 16);
+//   - one thread issues D = G W_g/2 + H W_s/2 (five K = 16 MMAs, M = 128,
+//     N = 64, BF16 in, FP32 in TMEM), double-buffered in TMEM and smem;
+//   - epilogue: u = D + P_r/2 (P_r = h_i W_r + b1, from one MMA at the tile
+//     start, held as BF16 pairs), silu(2u) = u + u tanh(u) with the packed
+//     BF16 hardware tanh, summed in FP32 for the receivers that have a k-th
+//     neighbour (the weights were halved on staging: exact in BF16).
+// At the end of the tile the sums (BF16) go through W2 on the tensor core,
+// the node MLP's two GEMMs follow (K = 128 from the h_i and m_i tiles), and
+// h'_i is written. Every mbarrier wait is bounded; a timeout is voted over
+// the group, reported through the status word, and ends the group's work.
+// ---------------------------------------------------------------------------
+constexpr int MS_GROUPS = 2;
+constexpr int MS_GROUP_THREADS = 256;
+constexpr int MS_THREADS = MS_GROUPS * MS_GROUP_THREADS;
+constexpr uint32_t MS_W_BYTES = 8192;  // [64][64] BF16 weight tile, K-major swizzled
+constexpr int MS_NW = 7;
+constexpr size_t MS_SMEM_BYTES = 1024 + MS_NW * MS_W_BYTES + 256 * 4 + (size_t)MS_GROUPS * 4 * TC_TILE_BYTES + 128;
 
-template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_edge_mlp_tc(const bf16* __restrict__ e_in, bf16* __restrict__ e_out,
-                                                           int64_t E, const uint32_t* __restrict__ recv,
-                                                           const uint32_t* __restrict__ send,
-                                                           const bf16* __restrict__ P, const bf16* __restrict__ w1,
-                                                           int kin, const float* __restrict__ b1g,
-                                                           const bf16* __restrict__ w2,
-                                                           const float* __restrict__ b2g, unsigned* err,
-                                                           const __grid_constant__ CUtensorMap tm_a,
-                                                           const __grid_constant__ CUtensorMap tm_b,
-                                                           const __grid_constant__ CUtensorMap tm_out) {
-  // tm_a: rows of e_in (edge, node: h) and tm_b: rows of the aggregates (node),
-  // tm_out: rows of e_out; [rows][64] BF16, 128-row boxes, 128-byte swizzle.
-  // The encoder mode (8-feature rows) gathers and stores with plain loads.
-  constexpr bool ENC = MODE == TC_ENC, NODE = MODE == TC_NODE, EDGE = MODE == TC_EDGE;
-  extern __shared__ unsigned char tc_raw[];
-  unsigned char* base = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);  // 1024-byte aligned
-  // slot s: e (or h) tile at s * 32 KB; sender projections (or aggregates),
-  // then silu(z1), at s * 32 KB + 16 KB
-  unsigned char* B1 = base + 2 * TC_SLOTS * TC_TILE_BYTES;  // W1[0:64]^T [n][k]
-  unsigned char* B2 = B1 + 8192;                 // W2^T [n][k]
-  unsigned char* B1b = B2 + 8192;                // W1[64:128]^T [n][k] (node MLP)
-  float* b2 = reinterpret_cast<float*>(B1b + 8192);
-  float* b1 = b2 + 64;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(b1 + 64);  // MMA completion, one per accumulator
-  uint64_t* lbar = mbar + 2;                               // TMA tile arrival, one per slot
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(lbar + TC_SLOTS);
-  auto Et = [&](int sl) { return base + sl * 2 * TC_TILE_BYTES; };
-  auto Pt = [&](int sl) { return base + sl * 2 * TC_TILE_BYTES + TC_TILE_BYTES; };
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+struct MsgArgs {
+  int64_t nf, nd;
+  const uint32_t* fluid_list;
+  const uint32_t* dummy_list;
+  const uint32_t* nbr;      // k-major exact neighbour lists of the fluid particles
+  const uint32_t* nbr_cnt;
+  const float4* packA;      // (x, y, z, phi') per node
+  const float4* packB;      // (U, 0) per node
+  const bf16* h_in;         // [n][64]
+  bf16* h_out;              // [n][64]
+  bf16* m_out;              // [n][64] message sums (training), or null
+  const bf16* we_w1; const float* we_b1; const bf16* we_w2; const float* we_b2;  // edge MLP
+  const bf16* wn_w1; const float* wn_b1; const bf16* wn_w2; const float* wn_b2;  // node MLP
+  int dim, kg;              // kg = 2d + 2 edge inputs
+  float inv_h, inv_su, inv_sphi;
+  unsigned* status;
+};
 
-  // weights (K-major swizzled), biases, barriers, tensor memory
-  for (int idx = t; idx < 64 * 64; idx += TC_THREADS) {
-    int n = idx >> 6, k = idx & 63;
-    uint32_t off = sw128(n, k >> 3) + (k & 7) * 2;
-    *reinterpret_cast<bf16*>(B1 + off) = k < kin ? w1[k * HID + n] : __float2bfloat16(0.f);
-    *reinterpret_cast<bf16*>(B2 + off) = w2[k * HID + n];
-    if (NODE) *reinterpret_cast<bf16*>(B1b + off) = w1[(HID + k) * HID + n];
+__global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
+  extern __shared__ unsigned char ms_raw[];
+  unsigned char* base = ms_raw + ((1024u - (smem_u32(ms_raw) & 1023u)) & 1023u);  // 1024-byte aligned
+  enum { WG = 0, WS = 1, WR = 2, WE2 = 3, WH = 4, WM = 5, WN2 = 6 };
+  unsigned char* W = base;
+  float* bias = reinterpret_cast<float*>(W + MS_NW * MS_W_BYTES);  // b1/2 | b2 (edge) | b1 | b2 (node)
+  unsigned char* tiles = reinterpret_cast<unsigned char*>(bias + 256);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tiles + (size_t)MS_GROUPS * 4 * TC_TILE_BYTES);
+  int* wmax = reinterpret_cast<int*>(mbar + 2 * MS_GROUPS);  // per-warp neighbour-count maxima
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(wmax + 16);
+  const int t = threadIdx.x;
+
+  // weights (K-major, 128-byte swizzle, [n][k] = W[k][n]); the first layer
+  // of the edge MLP halved; its input rows: kg edge inputs, h_i, h_j
+  const bf16 zero = __float2bfloat16(0.f);
+  auto half = [](bf16 v) { return __float2bfloat16(0.5f * __bfloat162float(v)); };
+  for (int idx = t; idx < 64 * 64; idx += MS_THREADS) {
+    const int n = idx >> 6, k = idx & 63;
+    const uint32_t off = sw128(n, k >> 3) + (k & 7) * 2;
+    auto put = [&](int w, bf16 v) { *reinterpret_cast<bf16*>(W + w * MS_W_BYTES + off) = v; };
+    put(WG, k < a.kg ? half(a.we_w1[k * HID + n]) : zero);
+    put(WR, half(a.we_w1[(a.kg + k) * HID + n]));
+    put(WS, half(a.we_w1[(a.kg + HID + k) * HID + n]));
+    put(WE2, a.we_w2[k * HID + n]);
+    put(WH, a.wn_w1[k * HID + n]);
+    put(WM, a.wn_w1[(HID + k) * HID + n]);
+    put(WN2, a.wn_w2[k * HID + n]);
   }
   if (t < 64) {
-    b2[t] = b2g[t];
-    b1[t] = EDGE ? 0.f : b1g[t];  // the edge MLP's b1 rides on the receiver projections
+    bias[t] = 0.5f * a.we_b1[t];
+    bias[64 + t] = a.we_b2[t];
+    bias[128 + t] = a.wn_b1[t];
+    bias[192 + t] = a.wn_b2[t];
   }
   if (t == 0) {
-    for (int k = 0; k < 2 + TC_SLOTS; ++k)
+    for (int k = 0; k < 2 * MS_GROUPS; ++k)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + k)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(smem_u32(tslot))
+  if (t < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "n"(128 * MS_GROUPS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;  // slot s accumulator: columns 64 s .. 64 s + 63
-  const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
-  const uint64_t dB1 = tc_desc(smem_u32(B1)), dB2 = tc_desc(smem_u32(B2)), dB1b = tc_desc(smem_u32(B1b));
-  const int64_t ntiles = div_up(E, TC_ROWS);
-  const int64_t stride = gridDim.x;
+  const uint32_t tmem = *tslot;
 
-  // gathers of tile `tile` into slot `sl`: e rows (or features) and sender
-  // projections of the warp's 32 rows. Edge rows: lane l moves 16-byte chunk
-  // l % 8 of row 4 k + l / 8, so each instruction covers 4 whole rows
-  // (512 contiguous bytes of e); `sd` is the sender of this thread's row.
-  auto issue = [&](int64_t tile, int sl, uint32_t sd) {
-    unsigned char* Ae = Et(sl);
-    if (ENC) {  // row t: 8 features, then zeros up to K = 16
-      const int64_t row = tile * TC_ROWS + t;
-      const bool valid = tile < ntiles && row < E;
-      cp_async16(Ae + sw128(t, 0), e_in + (valid ? row : 0) * FEAT, valid);
-      cp_async16(Ae + sw128(t, 1), e_in, false);
-    } else {
-      // e (or h) tile, and the aggregate tile of a node MLP, by TMA (rows past
-      // the end read as zeros); the store of the tile held here before must
-      // have finished reading it
-      if (t == 0 && tile < ntiles) {
-        tma_store_read_wait();
-        mbar_expect_tx(smem_u32(lbar + sl), NODE ? 2 * TC_TILE_BYTES : TC_TILE_BYTES);
-        tma_load_2d(smem_u32(Ae), &tm_a, 0, (int)(tile * TC_ROWS), smem_u32(lbar + sl));
-        if (NODE) tma_load_2d(smem_u32(Pt(sl)), &tm_b, 0, (int)(tile * TC_ROWS), smem_u32(lbar + sl));
-      }
-      if (EDGE) {  // sender projections: lane l moves chunk l % 8 of row 4 k + l / 8
-        const int c = lane & 7;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int rl = k * 4 + (lane >> 3), r = warp * 32 + rl;
-          const uint32_t sdr = __shfl_sync(0xffffffffu, sd, rl);
-          const int64_t row = tile * TC_ROWS + r;
-          const bool valid = tile < ntiles && row < E;
-          cp_async16(Pt(sl) + sw128(r, c), P + (int64_t)(valid ? sdr : 0u) * 2 * HID + HID + c * 8, valid);
-        }
-      }
-    }
-    cp_async_commit();
-  };
-  auto index_of = [&](const uint32_t* a, int64_t tile) -> uint32_t {
-    const int64_t row = tile * TC_ROWS + t;
-    return (EDGE && tile < ntiles && row < E) ? __ldg(a + row) : 0u;
-  };
-  // receiver projections (+ b1) of this thread's row, in registers, one tile ahead
-  uint4 pr[8];
-  auto load_pr = [&](uint32_t rv) {
-    if (EDGE) {
-      const uint4* prg = reinterpret_cast<const uint4*>(P + (int64_t)rv * 2 * HID);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) pr[c] = __ldg(prg + c);
-    }
-  };
-  // accumulator ac (TMEM columns 64 ac .. 64 ac + 63) of the tile in slot sl
-  auto mma1 = [&](int sl, int ac) {  // z1 = e W1e (or f W1, or [h, a] W1)
-    tc_fence_after();
-    const uint64_t dA = tc_desc(smem_u32(Et(sl)));
-#pragma unroll
-    for (int k = 0; k < (ENC ? 1 : 4); ++k) tc_mma(tmem + 64 * ac, dA + 2 * k, dB1 + 2 * k, k > 0);
-    if (NODE) {  // second K block: the aggregates
-      const uint64_t dA2 = tc_desc(smem_u32(Pt(sl)));
-#pragma unroll
-      for (int k = 0; k < 4; ++k) tc_mma(tmem + 64 * ac, dA2 + 2 * k, dB1b + 2 * k, 1u);
-    }
-    tc_commit(smem_u32(mbar + ac));
-  };
-  auto mma2 = [&](int sl, int ac) {  // z2 = silu(z1) W2, same columns
-    tc_fence_after();
-    const uint64_t dA = tc_desc(smem_u32(Pt(sl)));
-#pragma unroll
-    for (int k = 0; k < 4; ++k) tc_mma(tmem + 64 * ac, dA + 2 * k, dB2 + 2 * k, k > 0);
-    tc_commit(smem_u32(mbar + ac));
-  };
-  // bit b: parity of mbarrier b's next phase (0, 1: MMA per accumulator;
-  // 2 + s: TMA arrival of slot s)
-  uint32_t phases = 0u;
-  auto wait_slot = [&](int ac) -> bool {  // bounded; every thread gets the CTA's decision
-    bool w_ok = mbar_wait(smem_u32(mbar + ac), (phases >> ac) & 1u);
-    phases ^= 1u << ac;
-    return __syncthreads_and(w_ok) != 0;
-  };
-  // this thread's gathers of slot sl are complete and the slot's TMA tiles
-  // have arrived (bounded wait); followed by a CTA barrier. In the prologue
-  // all TC_SLOTS slots are in flight, later TC_SLOTS - 1 of them.
-  auto wait_loads = [&](int sl, bool prologue) -> bool {
-    if (prologue) cp_async_wait<TC_SLOTS - 1>(); else cp_async_wait<TC_SLOTS - 2>();
-    bool w_ok = true;
-    if (!ENC) {
-      w_ok = mbar_wait(smem_u32(lbar + sl), (phases >> (2 + sl)) & 1u);
-      phases ^= 1u << (2 + sl);
-    }
-    fence_async_smem();  // gathered tiles are read by the tensor core
-    tc_fence_before();
-    return __syncthreads_and(w_ok) != 0;
-  };
-
-  int64_t tile = blockIdx.x;
-  // prologue: gathers of the first TC_SLOTS tiles, MMA1 of the first
-#pragma unroll
-  for (int q = 0; q < TC_SLOTS; ++q) issue(tile + q * stride, q, index_of(send, tile + q * stride));
-  load_pr(index_of(recv, tile));
-  uint32_t rv_n1 = index_of(recv, tile + stride);                // receiver indices of the next tile
-  uint32_t sd_nx = index_of(send, tile + TC_SLOTS * stride);     // senders of the next tile to gather
+  const int g = t / MS_GROUP_THREADS, lt = t % MS_GROUP_THREADS, lw = lt >> 5, lane = t & 31;
+  const int q = lw & 3, ch = lw >> 2;   // lane quarter, column half
+  const int r = q * 32 + lane;          // receiver row = TMEM lane
+  const int bar_id = 1 + g;
+  const bool leader = lt == 0;
+  const uint32_t D0 = tmem + 128u * g, D1 = D0 + 64u;
+  const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + 32u * ch;
+  unsigned char* G0 = tiles + (size_t)g * 4 * TC_TILE_BYTES;
+  unsigned char* G1 = G0 + TC_TILE_BYTES;
+  unsigned char* H0 = G1 + TC_TILE_BYTES;
+  unsigned char* H1 = H0 + TC_TILE_BYTES;
+  uint64_t* mb = mbar + 2 * g;
+  const uint64_t dW[MS_NW] = {tc_desc(smem_u32(W)), tc_desc(smem_u32(W + MS_W_BYTES)),
+                              tc_desc(smem_u32(W + 2 * MS_W_BYTES)), tc_desc(smem_u32(W + 3 * MS_W_BYTES)),
+                              tc_desc(smem_u32(W + 4 * MS_W_BYTES)), tc_desc(smem_u32(W + 5 * MS_W_BYTES)),
+                              tc_desc(smem_u32(W + 6 * MS_W_BYTES))};
+  const float* b1h = bias;
+  const float* b2e = bias + 64;
+  const float* b1n = bias + 128;
+  const float* b2n = bias + 192;
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  uint32_t ph = 0u;  // parity of the next phase of mb[0], mb[1]
   bool ok = true;
-  if (tile < ntiles) {
-    ok = wait_loads(0, true);
-    if (ok && t == 0) mma1(0, 0);
-  }
-
-  for (int it = 0; tile < ntiles; ++it, tile += stride) {
-    const int ac = it & 1;              // accumulator of this tile
-    const int sl = it % TC_SLOTS;       // operand slot of this tile
-    const int sn = (it + 1) % TC_SLOTS; // and of the next one
-    const int64_t row0 = tile * TC_ROWS;
-    unsigned char* A = Et(sl);
-    unsigned char* PS = Pt(sl);
-    if (!wait_slot(ac)) { ok = false; break; }  // MMA1 of this tile
+  auto wait_mma = [&](int b) {
+    const bool w_ok = mbar_wait(smem_u32(mb + b), (ph >> b) & 1u);
+    ph ^= 1u << b;
+    ok = ok && w_ok;
     tc_fence_after();
-    // ---- silu(z1 + P_recv + P_send) (or + b1) -> PS, in place, BF16 swizzled ----
-    {
-      float va[64];
-      tc_ld64(t_lane + 64 * ac, va);
+  };
+  // this thread's half of a 64-wide BF16 row: 16-byte chunks ch*4 .. ch*4+3 of row r
+  auto copy_row_half = [&](unsigned char* T, const bf16* src, bool valid) {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const float* v = va + 8 * c;
-        uint4 o;
-        uint32_t* o32 = reinterpret_cast<uint32_t*>(&o);
-        if (!EDGE) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int col = c * 8 + 2 * j;
-            __nv_bfloat162 a2 = __floats2bfloat162_rn(silu_tanh(v[2 * j] + b1[col]),
-                                                      silu_tanh(v[2 * j + 1] + b1[col + 1]));
-            o32[j] = *reinterpret_cast<uint32_t*>(&a2);
-          }
-        } else {
-          uint4 ps = *reinterpret_cast<const uint4*>(PS + sw128(t, c));
-          const __nv_bfloat162* r2 = reinterpret_cast<const __nv_bfloat162*>(&pr[c]);
-          const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(&ps);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            float2 fr = __bfloat1622float2(r2[j]), fs = __bfloat1622float2(s2[j]);
-            __nv_bfloat162 a2 = __floats2bfloat162_rn(silu_tanh(v[2 * j] + fr.x + fs.x),
-                                                      silu_tanh(v[2 * j + 1] + fr.y + fs.y));
-            o32[j] = *reinterpret_cast<uint32_t*>(&a2);
-          }
-        }
-        *reinterpret_cast<uint4*>(PS + sw128(t, c)) = o;
-      }
-    }
-    fence_async_smem();  // silu(z1) is read by the tensor core
+    for (int c = 0; c < 4; ++c) cp_async16(T + sw128(r, ch * 4 + c), src + (ch * 4 + c) * 8, valid);
+  };
+  auto sync_operands = [&]() -> bool {  // smem operands written by the group -> tensor core
+    cp_async_wait<0>();
+    fence_async_smem();
     tc_fence_before();
-    __syncthreads();
-    if (t == 0) mma2(sl, ac);
-    load_pr(rv_n1);  // next tile's receiver projections
-    rv_n1 = index_of(recv, tile + 2 * stride);
-    // ---- MMA1 of the next tile (its gathers were issued TC_SLOTS - 1 iterations ago) ----
-    if (tile + stride < ntiles) {
-      if (!wait_loads(sn, false)) { ok = false; break; }
-      if (t == 0) mma1(sn, ac ^ 1);
-    }
-    if (!wait_slot(ac)) { ok = false; break; }  // MMA2 of this tile
-    tc_fence_after();
-    // ---- e' = e + z2 + b2, in place into the e tile ----
-    {
-      float va[64];
-      tc_ld64(t_lane + 64 * ac, va);
+    ok = group_bar_and(bar_id, ok);
+    return ok;
+  };
+  auto mma_k64 = [&](uint32_t d, const unsigned char* A, int w, bool accumulate) {
+    const uint64_t dA = tc_desc(smem_u32(A));
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const float* v = va + 8 * c;
-        uint4 ev = make_uint4(0u, 0u, 0u, 0u);  // residual (none for an encoder)
-        if (!ENC) ev = *reinterpret_cast<const uint4*>(A + sw128(t, c));
-        const __nv_bfloat162* e2 = reinterpret_cast<const __nv_bfloat162*>(&ev);
-        uint4 o;
-        uint32_t* o32 = reinterpret_cast<uint32_t*>(&o);
+    for (int kk = 0; kk < 4; ++kk) tc_mma(d, dA + 2 * kk, dW[w] + 2 * kk, (accumulate || kk > 0) ? 1u : 0u);
+  };
+  auto mma_step = [&](uint32_t d, const unsigned char* Gb, const unsigned char* Hb) {
+    tc_mma(d, tc_desc(smem_u32(Gb)), dW[WG], 0u);
+    mma_k64(d, Hb, WS, true);
+  };
+
+  const int64_t ntf = div_up(a.nf, 128), ntd = div_up(a.nd, 128), ntiles = ntf + ntd;
+  const int64_t gstride = (int64_t)gridDim.x * MS_GROUPS;
+  for (int64_t tile = (int64_t)blockIdx.x * MS_GROUPS + g; ok && tile < ntiles; tile += gstride) {
+    const bool fluid = tile < ntf;
+    const int64_t row0 = fluid ? tile * 128 : (tile - ntf) * 128;
+    const int64_t gi = row0 + r;
+    const bool valid = gi < (fluid ? a.nf : a.nd);
+    const uint32_t node = valid ? __ldg((fluid ? a.fluid_list : a.dummy_list) + gi) : 0u;
+    const int cnt = (valid && fluid) ? (int)__ldg(a.nbr_cnt + gi) : 0;
+    // longest list of the tile
+    const int wm = __reduce_max_sync(0xffffffffu, cnt);
+    if (lane == 0) wmax[g * 8 + lw] = wm;
+    group_bar(bar_id);
+    int kmax = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int col = c * 8 + 2 * j;
-          float2 fe = __bfloat1622float2(e2[j]);
-          __nv_bfloat162 a2 = __floats2bfloat162_rn(v[2 * j] + b2[col] + fe.x,
-                                                    v[2 * j + 1] + b2[col + 1] + fe.y);
-          o32[j] = *reinterpret_cast<uint32_t*>(&a2);
+    for (int w = 0; w < 8; ++w) kmax = max(kmax, wmax[g * 8 + w]);
+    const bool msg = kmax > 0;
+    float acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+    if (msg) {
+      const float4 ai = ch == 0 ? __ldg(a.packA + node) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 bi = ch == 0 ? __ldg(a.packB + node) : make_float4(0.f, 0.f, 0.f, 0.f);
+      // h_i rows (for P_r) into G1, step 0 into G0 / H0
+      copy_row_half(G1, a.h_in + (int64_t)node * HID, valid);
+      uint32_t jn = cnt > 0 ? __ldg(a.nbr + gi) : 0u;
+      copy_row_half(H0, a.h_in + (int64_t)jn * HID, cnt > 0);
+      cp_async_commit();
+      if (ch == 0) {
+        uint4 f = zero4;
+        if (cnt > 0)
+          f = edge_features(a.dim, ai, bi, __ldg(a.packA + jn), __ldg(a.packB + jn), a.inv_h, a.inv_su,
+                            a.inv_sphi);
+        *reinterpret_cast<uint4*>(G0 + sw128(r, 0)) = f;
+        *reinterpret_cast<uint4*>(G0 + sw128(r, 1)) = zero4;
+      }
+      jn = cnt > 1 ? __ldg(a.nbr + a.nf + gi) : 0u;
+      if (!sync_operands()) break;
+      if (leader) {
+        tc_fence_after();
+        mma_k64(D1, G1, WR, false);  // P_r / 2 = h_i W_r / 2
+        tc_commit(smem_u32(mb + 1));
+      }
+      wait_mma(1);
+      uint32_t pr[16];  // (P_r + b1) / 2 of this thread's 32 columns, BF16 pairs
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        float v[16];
+        tc_ld16(D1 + lane_off + 16 * hh, v);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const int col = 32 * ch + 16 * hh + 2 * p;
+          pr[8 * hh + p] = bf2_u32(__floats2bfloat162_rn(v[2 * p] + b1h[col], v[2 * p + 1] + b1h[col + 1]));
         }
-        *reinterpret_cast<uint4*>(A + sw128(t, c)) = o;
       }
-    }
-    if (ENC) {
-      __syncwarp();
-      // the warp's 32 output rows, 4 whole rows (512 B) per store instruction
+      if (leader) {
+        mma_step(D0, G0, H0);
+        tc_commit(smem_u32(mb + 0));
+      }
+      for (int k = 0; k < kmax; ++k) {
+        const int b = k & 1;
+        unsigned char* Gn = b ? G0 : G1;
+        unsigned char* Hn = b ? H0 : H1;
+        const bool more = k + 1 < kmax, act1 = k + 1 < cnt;
+        float4 aj = make_float4(0.f, 0.f, 0.f, 0.f), bj = aj;
+        if (more) {  // step k + 1: h_j rows in flight, sender packs into registers
+          copy_row_half(Hn, a.h_in + (int64_t)jn * HID, act1);
+          cp_async_commit();
+          if (ch == 0 && act1) {
+            aj = __ldg(a.packA + jn);
+            bj = __ldg(a.packB + jn);
+          }
+        }
+        const uint32_t jnn = k + 2 < cnt ? __ldg(a.nbr + (int64_t)(k + 2) * a.nf + gi) : 0u;
+        // epilogue of step k
+        wait_mma(b);
+        const bool act = k < cnt;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int r = warp * 32 + k * 4 + (lane >> 3), c = lane & 7;
-        const int64_t row = row0 + r;
-        if (row < E)
-          *reinterpret_cast<uint4*>(e_out + row * HID + c * 8) = *reinterpret_cast<const uint4*>(A + sw128(r, c));
+        for (int hh = 0; hh < 2; ++hh) {
+          float v[16];
+          tc_ld16((b ? D1 : D0) + lane_off + 16 * hh, v);
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const __nv_bfloat162 u = __hadd2(__floats2bfloat162_rn(v[2 * p], v[2 * p + 1]), u32_bf2(pr[8 * hh + p]));
+            uint32_t th;
+            asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(bf2_u32(u)));
+            const float2 s = __bfloat1622float2(__hfma2(u, u32_bf2(th), u));
+            if (act) {
+              acc[16 * hh + 2 * p] += s.x;
+              acc[16 * hh + 2 * p + 1] += s.y;
+            }
+          }
+        }
+        if (more && ch == 0) {
+          uint4 f = zero4;
+          if (act1) f = edge_features(a.dim, ai, bi, aj, bj, a.inv_h, a.inv_su, a.inv_sphi);
+          *reinterpret_cast<uint4*>(Gn + sw128(r, 0)) = f;
+          *reinterpret_cast<uint4*>(Gn + sw128(r, 1)) = zero4;
+        }
+        if (!sync_operands()) break;
+        if (more && leader) {
+          tc_fence_after();
+          mma_step(b ? D0 : D1, Gn, Hn);
+          tc_commit(smem_u32(mb + (b ^ 1)));
+        }
+        jn = jnn;
       }
-      __syncwarp();
-    } else {  // the whole tile by one TMA store (rows past the end are not written)
-      fence_async_smem();
-      __syncthreads();
-      if (t == 0) tma_store_2d(&tm_out, 0, (int)row0, smem_u32(A));
+      if (!ok) break;
+      // m_i = (sum_j silu(z_ij)) W2 + n_i b2: the sums (BF16) to G0, one GEMM
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint4 o;
+        o.x = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 0], acc[8 * c + 1]));
+        o.y = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 2], acc[8 * c + 3]));
+        o.z = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 4], acc[8 * c + 5]));
+        o.w = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 6], acc[8 * c + 7]));
+        *reinterpret_cast<uint4*>(G0 + sw128(r, ch * 4 + c)) = o;
+      }
+      copy_row_half(H1, a.h_in + (int64_t)node * HID, valid);  // h_i again, for the node MLP
+      cp_async_commit();
+      if (!sync_operands()) break;
+      if (leader) {
+        tc_fence_after();
+        mma_k64(D0, G0, WE2, false);
+        tc_commit(smem_u32(mb + 0));
+      }
+      wait_mma(0);
+      const float fc = (float)cnt;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        float v[16];
+        tc_ld16(D0 + lane_off + 16 * hh, v);
+        uint32_t o[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const int col = 32 * ch + 16 * hh + 2 * p;
+          o[p] = bf2_u32(__floats2bfloat162_rn(fmaf(fc, b2e[col], v[2 * p]), fmaf(fc, b2e[col + 1], v[2 * p + 1])));
+        }
+        const uint4 o0 = make_uint4(o[0], o[1], o[2], o[3]), o1 = make_uint4(o[4], o[5], o[6], o[7]);
+        *reinterpret_cast<uint4*>(H0 + sw128(r, ch * 4 + 2 * hh)) = o0;
+        *reinterpret_cast<uint4*>(H0 + sw128(r, ch * 4 + 2 * hh + 1)) = o1;
+        if (a.m_out && valid) {
+          uint4* mo = reinterpret_cast<uint4*>(a.m_out + (int64_t)node * HID + 32 * ch + 16 * hh);
+          mo[0] = o0;
+          mo[1] = o1;
+        }
+      }
+    } else {  // no messages: m = 0, h_i into H1
+#pragma unroll
+      for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(H0 + sw128(r, ch * 4 + c)) = zero4;
+      copy_row_half(H1, a.h_in + (int64_t)node * HID, valid);
+      cp_async_commit();
     }
-    // ---- gathers of the tile TC_SLOTS ahead into this slot (its e and silu(z1) tiles are free) ----
-    issue(tile + TC_SLOTS * stride, sl, sd_nx);
-    sd_nx = index_of(send, tile + (TC_SLOTS + 1) * stride);
+    // node MLP: z = [h_i, m_i] W1 + b1 (K = 128), h' = h_i + silu(z) W2 + b2
+    if (!sync_operands()) break;
+    if (leader) {
+      tc_fence_after();
+      mma_k64(D1, H1, WH, false);
+      mma_k64(D1, H0, WM, true);
+      tc_commit(smem_u32(mb + 1));
+    }
+    wait_mma(1);
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      float v[16];
+      tc_ld16(D1 + lane_off + 16 * hh, v);
+      uint32_t o[8];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const int col = 32 * ch + 16 * hh + 2 * p;
+        o[p] = bf2_u32(__floats2bfloat162_rn(silu_tanh(v[2 * p] + b1n[col]), silu_tanh(v[2 * p + 1] + b1n[col + 1])));
+      }
+      *reinterpret_cast<uint4*>(G1 + sw128(r, ch * 4 + 2 * hh)) = make_uint4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<uint4*>(G1 + sw128(r, ch * 4 + 2 * hh + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+    }
+    if (!sync_operands()) break;
+    if (leader) {
+      tc_fence_after();
+      mma_k64(D0, G1, WN2, false);
+      tc_commit(smem_u32(mb + 0));
+    }
+    wait_mma(0);
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      float v[16];
+      tc_ld16(D0 + lane_off + 16 * hh, v);
+      uint32_t o[8];
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        const uint4 hv = *reinterpret_cast<const uint4*>(H1 + sw128(r, ch * 4 + 2 * hh + cc));
+        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int pp = 4 * cc + p, col = 32 * ch + 16 * hh + 2 * pp;
+          const float2 hf = __bfloat1622float2(u32_bf2(hw[p]));
+          o[pp] = bf2_u32(__floats2bfloat162_rn(hf.x + v[2 * pp] + b2n[col], hf.y + v[2 * pp + 1] + b2n[col + 1]));
+        }
+      }
+      if (valid) {
+        uint4* ho = reinterpret_cast<uint4*>(a.h_out + (int64_t)node * HID + 32 * ch + 16 * hh);
+        ho[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        ho[1] = make_uint4(o[4], o[5], o[6], o[7]);
+      }
+    }
+    tc_fence_before();
+    ok = group_bar_and(bar_id, ok);  // H1 and TMEM reads done before the next tile's writes
   }
-  cp_async_wait<0>();  // gathers issued for tiles past the end
-  if (t == 0) tma_store_wait();
-  if (!ok && t == 0) atomicOr(err, (unsigned)kStatTimeout);
+  cp_async_wait<0>();
+  if (!ok && (t % MS_GROUP_THREADS) == 0) atomicOr(a.status, (unsigned)kStatTimeout);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (t < 32) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(128 * MS_GROUPS)
+                 : "memory");
   }
 }
 
@@ -912,7 +938,8 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd(MlpArgs a) {
   const bf16 zero = __float2bfloat16(0.f);
   for (int idx = threadIdx.x; idx < HID * KP; idx += MLP_THREADS) {
     int c = idx / KP, k = idx % KP;
-    bf16 v = k < a.kin ? a.w1[k * HID + c] : zero;
+    const int pr = param_row<MODE>(a, k);
+    bf16 v = pr >= 0 ? a.w1[pr * HID + c] : zero;
     W1t[c * S::LDX + k] = v;
     W1r[k * S::LDW1 + c] = v;
   }
@@ -1020,14 +1047,14 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd(MlpArgs a) {
         for (int q = 0; q < 4; ++q) {
           int r = m0 + g + (q >> 1) * 8, k = nt * 8 + 2 * t + (q & 1);
           int64_t row = row0 + r;
-          if (row >= rows || k >= a.kin) continue;
+          if (row >= rows || param_row<MODE>(a, k) < 0) continue;
           float v = dx[q];
           if (MODE == MODE_LIST) {
             a.dh[(int64_t)a.list[row] * HID + k] = v;
-          } else if (MODE == MODE_EDGE) {
-            if (k < HID) a.din_row[row * HID + k] = a.dout[row * HID + k] + v;
-            else if (k < 2 * HID) atomicAdd(&a.dh[(int64_t)a.recv[row] * HID + k - HID], v);
-            else atomicAdd(&a.dh[(int64_t)a.send[row] * HID + k - 2 * HID], v);
+          } else if (MODE == MODE_EDGE) {  // edge inputs take no gradient; h_i, h_j scatter
+            if (k < 16) continue;
+            if (k < 16 + HID) atomicAdd(&a.dh[(int64_t)a.recv[row] * HID + k - 16], v);
+            else atomicAdd(&a.dh[(int64_t)a.send[row] * HID + k - 16 - HID], v);
           } else {  // MODE_NODE
             if (k < HID) a.din_row[row * HID + k] = a.dout[row * HID + k] + v;
             else a.dagg[row * HID + k - HID] = v;
@@ -1074,7 +1101,10 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd(MlpArgs a) {
     }
     __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < a.kin * HID; idx += MLP_THREADS) atomicAdd(&a.gw1[idx], gW1[idx]);
+  for (int idx = threadIdx.x; idx < KP * HID; idx += MLP_THREADS) {
+    const int pr = param_row<MODE>(a, idx / HID);
+    if (pr >= 0) atomicAdd(&a.gw1[pr * HID + idx % HID], gW1[idx]);
+  }
   for (int idx = threadIdx.x; idx < HID * a.nout; idx += MLP_THREADS) {
     int c = idx / a.nout, o = idx % a.nout;
     atomicAdd(&a.gw2[idx], gW2[c * NP + o]);
@@ -1084,122 +1114,76 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd(MlpArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Graph, features, aggregation, loss, optimiser
+// Graph, features, loss, optimiser
 // ---------------------------------------------------------------------------
-// FP32 value of a double by truncating its IEEE fields with integer
-// instructions (magnitudes below 2^-126 give zero; no infinities arise
-// here). Feature inputs are rounded to BF16 afterwards, so truncation is
-// immaterial, and the FP64 pipe stays free.
-__device__ __forceinline__ float d2f_fields(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const unsigned e = (hi >> 20) & 0x7FFu;
-  if (e <= 1023u - 127u) return 0.f;
-  return __uint_as_float((hi & 0x80000000u) | ((e - (1023u - 127u)) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+// Node inputs and packs. Node input (BF16, 8 wide): (U, rho/rho0 - 1, phi')
+// minus the mean over the std, then the dummy flag, with the hydrostatic
+// split phi' = phi - phi_hs(x), phi_hs = G.x + |G| H (FP64, like the mixed
+// path). Packs (FP32) for the edge inputs: A = (x, y, z, phi'), B = (U, 0).
+__global__ void k_sg_nodes(Params p, State s, int64_t n, const float* mean, const float* stdv, bf16* nf_out,
+                           float4* packA, float4* packB) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double phs = p.phs0, xs[3] = {0.0, 0.0, 0.0}, us[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < p.dim; ++d) {
+    xs[d] = s.x[d * n + i];
+    us[d] = s.u[d * n + i];
+    phs = fma(p.g[d], xs[d], phs);
+  }
+  const double phip = s.phi[i] - phs;
+  float v[FEAT] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int d = 0; d < p.dim; ++d) v[d] = (float)us[d];
+  v[p.dim] = (float)(eos_density(p, s.phi[i]) / p.rho0 - 1.0);
+  v[p.dim + 1] = (float)phip;
+  for (int k = 0; k < p.dim + 2; ++k) v[k] = (v[k] - mean[k]) / stdv[k];
+  v[p.dim + 2] = s.type[i] == kFluid ? 0.f : 1.f;
+  uint4 o;
+  o.x = pack2(__float2bfloat16(v[0]), __float2bfloat16(v[1]));
+  o.y = pack2(__float2bfloat16(v[2]), __float2bfloat16(v[3]));
+  o.z = pack2(__float2bfloat16(v[4]), __float2bfloat16(v[5]));
+  o.w = pack2(__float2bfloat16(v[6]), __float2bfloat16(v[7]));
+  *reinterpret_cast<uint4*>(nf_out + i * FEAT) = o;
+  packA[i] = make_float4((float)xs[0], (float)xs[1], (float)xs[2], (float)phip);
+  packB[i] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
 }
 
-// Edges and edge features. A warp covers the receivers g0 .. g0 + 31 and
-// the contiguous range of their edges; lane l takes edges l, l + 32, ... of
-// that range, finds its receiver by a binary search over the lanes' row
-// starts, and receives the receiver's data by shuffle: every store of
-// recv, send and the 16-byte feature rows is coalesced.
-__global__ void k_sg_fill(Params p, State s, Work w, int64_t n, int64_t nf, const uint32_t* row_ptr,
-                          uint32_t* recv, uint32_t* send, bf16* efeat, const float* node_std) {
+// Training graph: edges (receiver, sender) in CSR order by receiver and
+// their inputs (edge_features, the same function the fused layer uses), for
+// the backward pass. A warp covers the receivers g0 .. g0 + 31 and the
+// contiguous range of their edges; lane l takes edges l, l + 32, ... of that
+// range and finds its receiver by a binary search over the lanes' row
+// starts, so every store of recv, send and the 16-byte input rows coalesces.
+__global__ void k_sg_fill(int dim, Work w, int64_t nf, const uint32_t* row_ptr, const float4* packA,
+                          const float4* packB, float inv_h, float inv_su, float inv_sphi, uint32_t* recv,
+                          uint32_t* send, bf16* efeat) {
   const int lane = threadIdx.x & 31;
   const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane;
   if (g0 >= nf) return;  // whole warps leave together
   const int64_t gl = g0 + lane;
   const uint32_t start = row_ptr[gl < nf ? gl : nf];  // row_ptr holds nf + 1 entries
-  const uint32_t e_end = __shfl_sync(0xffffffffu, start, 31) +
-                         (g0 + 31 < nf ? w.nbr_cnt[g0 + 31] : 0u);  // end of the last receiver's row
+  const uint32_t e_end = __shfl_sync(0xffffffffu, start, 31) + (g0 + 31 < nf ? w.nbr_cnt[g0 + 31] : 0u);
   const uint32_t e_beg = __shfl_sync(0xffffffffu, start, 0);
-  const float inv_h = (float)(1.0 / p.h);
-  float inv_su[3] = {0.f, 0.f, 0.f};
-  for (int d = 0; d < p.dim; ++d) inv_su[d] = 1.f / node_std[d];
-  const float inv_sphi = 1.f / node_std[p.dim + 1];
-  // this lane's receiver: FP32 position, velocity and potential narrowed on
-  // the IEEE fields (BF16 features need no FP64 arithmetic)
-  uint32_t i_l = 0u;
-  float4 x_l = make_float4(0.f, 0.f, 0.f, 0.f);
-  float u_l[3] = {0.f, 0.f, 0.f}, phi_l = 0.f;
-  if (gl < nf) {
-    i_l = w.fluid_list[gl];
-    x_l = w.xf[i_l];
-    for (int d = 0; d < p.dim; ++d) u_l[d] = d2f_fields(s.u[d * n + i_l]);
-    phi_l = d2f_fields(s.phi[i_l]);
-  }
   for (uint32_t e0 = e_beg; e0 < e_end; e0 += 32) {
     const uint32_t e = e0 + (uint32_t)lane;
-    // receiver lane r: the last lane whose row starts at or before e
-    int r = 0;
+    int r = 0;  // receiver lane: the last lane whose row starts at or before e
 #pragma unroll
     for (int step = 16; step; step >>= 1) {
       const uint32_t st_c = __shfl_sync(0xffffffffu, start, r + step);
       if (r + step < 32 && g0 + r + step < nf && st_c <= e) r += step;
     }
-    const uint32_t i = __shfl_sync(0xffffffffu, i_l, r);
-    const float xi = __shfl_sync(0xffffffffu, x_l.x, r), yi = __shfl_sync(0xffffffffu, x_l.y, r),
-                zi = __shfl_sync(0xffffffffu, x_l.z, r);
-    float ui[3];
-    for (int d = 0; d < 3; ++d) ui[d] = __shfl_sync(0xffffffffu, u_l[d], r);
-    const float phii = __shfl_sync(0xffffffffu, phi_l, r);
     const uint32_t st_r = __shfl_sync(0xffffffffu, start, r);
     if (e >= e_end) continue;
-    const uint32_t k = e - st_r;
-    const uint32_t j = w.nbr[(int64_t)k * nf + g0 + r];  // every list entry is an exact neighbour
-    const float4 xj = __ldg(&w.xf[j]);
-    const float rv[3] = {xj.x - xi, xj.y - yi, xj.z - zi};
+    const uint32_t i = w.fluid_list[g0 + r];
+    const uint32_t j = w.nbr[(int64_t)(e - st_r) * nf + g0 + r];  // every list entry is an exact neighbour
     recv[e] = i;
     send[e] = j;
-    // features (r/h, |r|/h, dU/s_U, dphi/s_phi), zero padded to 8, one 16-byte store
-    float f[FEAT] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float r2 = 0.f;
-    for (int d = 0; d < p.dim; ++d) {
-      f[d] = rv[d] * inv_h;
-      r2 = fmaf(rv[d], rv[d], r2);
-      f[p.dim + 1 + d] = (d2f_fields(s.u[d * n + j]) - ui[d]) * inv_su[d];
-    }
-    f[p.dim] = sqrtf(r2) * inv_h;
-    f[2 * p.dim + 1] = (d2f_fields(s.phi[j]) - phii) * inv_sphi;
-    uint4 v;
-    v.x = pack2(__float2bfloat16(f[0]), __float2bfloat16(f[1]));
-    v.y = pack2(__float2bfloat16(f[2]), __float2bfloat16(f[3]));
-    v.z = pack2(__float2bfloat16(f[4]), __float2bfloat16(f[5]));
-    v.w = pack2(__float2bfloat16(f[6]), __float2bfloat16(f[7]));
-    *reinterpret_cast<uint4*>(efeat + (int64_t)e * FEAT) = v;
+    *reinterpret_cast<uint4*>(efeat + (int64_t)e * FEAT) =
+        edge_features(dim, __ldg(packA + i), __ldg(packB + i), __ldg(packA + j), __ldg(packB + j), inv_h, inv_su,
+                      inv_sphi);
   }
 }
 
-// node features: (U, rho/rho0 - 1, phi) normalised by (mean, std), dummy flag
-__global__ void k_sg_nodes(Params p, State s, int64_t n, const float* mean, const float* stdv, bf16* nf_out) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float v[FEAT] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int d = 0; d < p.dim; ++d) v[d] = (float)s.u[d * n + i];
-  double rho = eos_density(p, s.phi[i]);
-  v[p.dim] = (float)(rho / p.rho0 - 1.0);
-  v[p.dim + 1] = (float)s.phi[i];
-  for (int k = 0; k < p.dim + 2; ++k) v[k] = (v[k] - mean[k]) / stdv[k];
-  v[p.dim + 2] = s.type[i] == kFluid ? 0.f : 1.f;
-  for (int k = 0; k < FEAT; ++k) nf_out[i * FEAT + k] = __float2bfloat16(v[k]);
-}
-
-// a_i = sum of the receiver's edge states (fluid rows; other nodes keep zero)
-__global__ void k_sg_aggregate(const uint32_t* fluid_list, int64_t nf, const uint32_t* row_ptr,
-                               const bf16* e, bf16* agg) {
-  int64_t gi = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
-  int lane = threadIdx.x & 31;
-  if (gi >= nf) return;
-  uint32_t i = fluid_list[gi];
-  float s0 = 0.f, s1 = 0.f;
-  for (uint32_t k = row_ptr[gi]; k < row_ptr[gi + 1]; ++k) {
-    __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162*>(e + (int64_t)k * HID)[lane];
-    s0 += __bfloat162float(v.x);
-    s1 += __bfloat162float(v.y);
-  }
-  reinterpret_cast<__nv_bfloat162*>(agg + (int64_t)i * HID)[lane] = __floats2bfloat162_rn(s0, s1);
-}
-
-// de_e += dagg_recv(e)
+// de_e = dm_recv(e): the gradient of a receiver's message sum reaches each of its edges
 __global__ void k_sg_aggregate_bwd(const uint32_t* fluid_list, int64_t nf, const uint32_t* row_ptr,
                                    const float* dagg_rows, float* de) {
   int64_t gi = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
@@ -1207,13 +1191,7 @@ __global__ void k_sg_aggregate_bwd(const uint32_t* fluid_list, int64_t nf, const
   if (gi >= nf) return;
   uint32_t i = fluid_list[gi];
   float2 g = reinterpret_cast<const float2*>(dagg_rows + (int64_t)i * HID)[lane];
-  for (uint32_t k = row_ptr[gi]; k < row_ptr[gi + 1]; ++k) {
-    float2* p2 = reinterpret_cast<float2*>(de + (int64_t)k * HID) + lane;
-    float2 v = *p2;
-    v.x += g.x;
-    v.y += g.y;
-    *p2 = v;
-  }
+  for (uint32_t k = row_ptr[gi]; k < row_ptr[gi + 1]; ++k) reinterpret_cast<float2*>(de + (int64_t)k * HID)[lane] = g;
 }
 
 // normalised targets from the plain rates; loss and its gradient (fluid rows)
@@ -1250,6 +1228,28 @@ __global__ void k_sg_rates(int dim, Work w, int64_t n, int64_t nf, const float* 
   w.dphidt[i] = (double)out[gi * no + dim] * tstd[dim] + tmean[dim];
 }
 
+// Control of the gain test: the rates of the last plain stage of a rollout,
+// kept per particle (by original id) and replayed in later stages.
+__global__ void k_frozen_store(int dim, Work w, const uint32_t* oid, int64_t n, int64_t nf, double* frozen,
+                               int64_t cap) {
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gi >= nf) return;
+  const uint32_t i = w.fluid_list[gi], o = oid[i];
+  for (int d = 0; d < dim; ++d) frozen[d * cap + o] = w.dudt[d * n + i];
+  frozen[dim * cap + o] = w.dphidt[i];
+}
+__global__ void k_frozen_rates(int dim, Work w, const uint32_t* oid, int64_t n, int64_t nf, const double* frozen,
+                               int64_t cap) {
+  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gi >= nf) return;
+  const uint32_t i = w.fluid_list[gi], o = oid[i];
+  for (int d = 0; d < dim; ++d) {
+    w.dudt[d * n + i] = frozen[d * cap + o];
+    w.dushift[d * n + i] = 0.0;
+  }
+  w.dphidt[i] = frozen[dim * cap + o];
+}
+
 __global__ void k_adam(int64_t np, float* p, const float* g, float* m, float* v, float lr, float b1,
                        float b2, float eps, float c1, float c2, bf16* pb) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1281,21 +1281,31 @@ struct Block {
 // ---------------------------------------------------------------------------
 struct wbsph_surrogate_s {
   wbsph_surrogate_config cfg;
-  int dim = 2, layers = 3;
+  int dim = 2, layers = 3, mode = WBSPH_SURROGATE_NETWORK;
   std::vector<Block> blocks;
   int64_t np = 0;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   bf16* pb = nullptr;
-  float* norm = nullptr;  // node mean[8], node std[8], target mean[4], target std[4]
+  float* norm = nullptr;  // node mean[8], node std[8], target mean[4], target std[4], edge std[2]
+  float edge_std[2] = {1.f, 1.f};
   int64_t adam_t = 0;
-  // graph and activations, sized on demand
-  int64_t cap_n = 0, cap_nf = 0, cap_e = 0;
+  // node buffers (inference and training), sized on demand
+  int64_t cap_n = 0, cap_nf = 0;
+  bf16* nfeat = nullptr;
+  float4 *packA = nullptr, *packB = nullptr;
+  std::vector<bf16*> hs;
+  float* out = nullptr;
+  // training: the graph, message sums and gradients
+  int64_t cap_tn = 0, cap_e = 0;
   uint32_t *row_ptr = nullptr, *recv = nullptr, *send = nullptr, *scan_tmp = nullptr;
-  bf16 *efeat = nullptr, *nfeat = nullptr, *proj = nullptr;
-  std::vector<bf16*> hs, es, aggs;
-  float *out = nullptr, *dout = nullptr, *dh = nullptr, *de = nullptr, *dagg = nullptr;
+  bf16* efeat = nullptr;
+  std::vector<bf16*> ms;
+  float *dout = nullptr, *dh = nullptr, *de = nullptr, *dagg = nullptr;
   double* loss = nullptr;
   int64_t E = 0;
+  // frozen-rates control: rates by original id
+  double* frozen = nullptr;
+  int64_t cap_frozen = 0;
   std::string err;
 };
 
@@ -1306,6 +1316,7 @@ int sfail(wbsph_surrogate s, int code, const char* msg) {
   return code;
 }
 
+// flat layout: node encoder, (edge MLP, node MLP) per layer, decoder
 void build_blocks(wbsph_surrogate s) {
   int d = s->dim;
   int64_t off = 0;
@@ -1319,9 +1330,8 @@ void build_blocks(wbsph_surrogate s) {
     s->blocks.push_back(b);
   };
   add(d + 3, HID);
-  add(2 * d + 2, HID);
   for (int l = 0; l < s->layers; ++l) {
-    add(3 * HID, HID);
+    add(2 * d + 2 + 2 * HID, HID);
     add(2 * HID, HID);
   }
   add(HID, d + 1);
@@ -1343,55 +1353,61 @@ void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
+void free_train(wbsph_surrogate s) {
+  dfree(s->row_ptr); dfree(s->recv); dfree(s->send); dfree(s->efeat); dfree(s->scan_tmp);
+  for (auto* q : s->ms) dfree(q);
+  s->ms.clear();
+  dfree(s->dout); dfree(s->dh); dfree(s->de); dfree(s->dagg);
+  s->row_ptr = s->recv = s->send = s->scan_tmp = nullptr;
+  s->efeat = nullptr;
+  s->dout = s->dh = s->de = s->dagg = nullptr;
+  s->cap_tn = s->cap_e = 0;
+}
+
 void free_graph(wbsph_surrogate s) {
-  dfree(s->row_ptr); dfree(s->recv); dfree(s->send); dfree(s->efeat); dfree(s->nfeat);
-  dfree(s->proj); dfree(s->scan_tmp);
-  s->proj = nullptr;
-  s->scan_tmp = nullptr;
+  free_train(s);
+  dfree(s->nfeat); dfree(s->packA); dfree(s->packB); dfree(s->out);
   for (auto* q : s->hs) dfree(q);
-  for (auto* q : s->es) dfree(q);
-  for (auto* q : s->aggs) dfree(q);
-  s->hs.clear(); s->es.clear(); s->aggs.clear();
-  dfree(s->out); dfree(s->dout); dfree(s->dh); dfree(s->de); dfree(s->dagg);
-  s->row_ptr = s->recv = s->send = nullptr;
-  s->efeat = s->nfeat = nullptr;
-  s->out = s->dout = s->dh = s->de = s->dagg = nullptr;
-  s->cap_n = s->cap_nf = s->cap_e = 0;
+  s->hs.clear();
+  s->nfeat = nullptr;
+  s->packA = s->packB = nullptr;
+  s->out = nullptr;
+  s->cap_n = s->cap_nf = 0;
 }
 
 int ensure_nodes(wbsph_surrogate s, int64_t n, int64_t nf) {
   if (n <= s->cap_n && nf <= s->cap_nf) return WBSPH_OK;
   free_graph(s);
   s->cap_n = n; s->cap_nf = nf;
-  bool ok = dalloc(&s->row_ptr, nf + 1) && dalloc(&s->nfeat, n * FEAT) &&
-            dalloc(&s->out, nf * 4) && dalloc(&s->dout, nf * 4) && dalloc(&s->dh, n * HID) &&
-            dalloc(&s->dagg, n * HID) && dalloc(&s->proj, n * 2 * HID) &&
-            dalloc(&s->scan_tmp, (size_t)scan_scratch_words(nf + 1));
+  bool ok = dalloc(&s->nfeat, n * FEAT) && dalloc(&s->packA, n) && dalloc(&s->packB, n) && dalloc(&s->out, nf * 4);
   for (int l = 0; ok && l <= s->layers; ++l) {
     bf16* q = nullptr;
     ok = dalloc(&q, n * HID);
     s->hs.push_back(q);
-    if (ok && l < s->layers) {
-      ok = dalloc(&q, n * HID);
-      s->aggs.push_back(q);
-    }
   }
   return ok ? WBSPH_OK : sfail(s, WBSPH_E_NOMEM, "surrogate node buffers");
+}
+
+int ensure_train_nodes(wbsph_surrogate s, int64_t n, int64_t nf) {
+  if (n <= s->cap_tn && nf <= s->cap_nf && s->row_ptr) return WBSPH_OK;
+  free_train(s);
+  s->cap_tn = n;
+  bool ok = dalloc(&s->row_ptr, s->cap_nf + 1) && dalloc(&s->dout, s->cap_nf * 4) && dalloc(&s->dh, n * HID) &&
+            dalloc(&s->dagg, n * HID) && dalloc(&s->scan_tmp, (size_t)scan_scratch_words(s->cap_nf + 1));
+  for (int l = 0; ok && l < s->layers; ++l) {
+    bf16* q = nullptr;
+    ok = dalloc(&q, n * HID);
+    s->ms.push_back(q);
+  }
+  return ok ? WBSPH_OK : sfail(s, WBSPH_E_NOMEM, "surrogate training buffers");
 }
 
 int ensure_edges(wbsph_surrogate s, int64_t E) {
   if (E <= s->cap_e) return WBSPH_OK;
   dfree(s->recv); dfree(s->send); dfree(s->efeat); dfree(s->de);
-  for (auto* q : s->es) dfree(q);
-  s->es.clear();
   int64_t cap = E + E / 4 + 1024;
   bool ok = dalloc(&s->recv, cap) && dalloc(&s->send, cap) && dalloc(&s->efeat, cap * FEAT) &&
             dalloc(&s->de, cap * HID);
-  for (int l = 0; ok && l <= s->layers; ++l) {
-    bf16* q = nullptr;
-    ok = dalloc(&q, cap * HID);
-    s->es.push_back(q);
-  }
   s->cap_e = ok ? cap : 0;
   return ok ? WBSPH_OK : sfail(s, WBSPH_E_NOMEM, "surrogate edge buffers");
 }
@@ -1422,84 +1438,6 @@ void launch_bwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
   k_mlp_bwd<MODE, KP, NP><<<grid, MLP_THREADS, sm, st>>>(a);
 }
 
-// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
-// query (no link-time dependency on libcuda)
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    else
-      cudaGetLastError();
-  }
-  return fn;
-}
-
-// TMA map of a [rows][64] BF16 row-major array: 128-row boxes, 128-byte swizzle
-// (the tensor core's K-major operand layout), zero fill past the last row.
-static bool rows_map(CUtensorMap* m, const bf16* base, int64_t rows) {
-  auto fn = tensor_map_encoder();
-  if (!fn || rows <= 0 || rows > 0x7FFFFFFF) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)HID, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)HID * sizeof(bf16)};
-  cuuint32_t box[2] = {(cuuint32_t)HID, (cuuint32_t)TC_ROWS};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// in: rows of e (edge), 8-feature rows (encoder) or h (node); P: projections
-// (edge) or aggregates (node); out: [rows][64]. Returns false when a TMA map
-// cannot be built (the caller reports it).
-template <int MODE>
-bool launch_tc(const bf16* in, bf16* out, int64_t rows, const uint32_t* recv, const uint32_t* send,
-               const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
-  if (rows <= 0) return true;
-  static int sms = 0, per_sm = 1;
-  if (!sms) {
-    int dev = 0, smem_sm = 0, reserved = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    cudaFuncSetAttribute(k_edge_mlp_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES);
-    // all of the unified L1/shared storage as shared memory; the persistent
-    // grid holds as many CTAs per SM as their shared memory allows (two with
-    // two slots), at most four (their TMEM columns then fill the 512)
-    cudaFuncSetAttribute(k_edge_mlp_tc<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    per_sm = smem_sm > 0 ? smem_sm / (int)(TC_SMEM_BYTES + (size_t)reserved) : 1;
-    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
-    if (sms <= 0) sms = 152;
-  }
-  CUtensorMap ma, mb, mo;
-  memset(&ma, 0, sizeof ma);
-  memset(&mb, 0, sizeof mb);
-  memset(&mo, 0, sizeof mo);
-  if (MODE != TC_ENC) {
-    if (!rows_map(&ma, in, rows) || !rows_map(&mo, out, rows)) return false;
-    if (MODE == TC_NODE && !rows_map(&mb, P, rows)) return false;
-  }
-  int64_t tiles = div_up(rows, TC_ROWS);
-  int grid = (int)(tiles < (int64_t)per_sm * sms ? tiles : (int64_t)per_sm * sms);
-  k_edge_mlp_tc<MODE><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(in, out, rows, recv, send, P, blk.w1, blk.kin,
-                                                               blk.b1, blk.w2, blk.b2, status, ma, mb, mo);
-  return true;
-}
-
-// Edge MLP of one layer on tcgen05: persistent CTAs, 2 per SM (83 KB of
-// shared memory and 128 TMEM columns each).
-bool launch_edge_tc(const bf16* e_in, bf16* e_out, int64_t E, const uint32_t* recv, const uint32_t* send,
-                    const bf16* P, const MlpArgs& blk, unsigned* status, cudaStream_t st) {
-  return launch_tc<TC_EDGE>(e_in, e_out, E, recv, send, P, blk, status, st);
-}
-
 MlpArgs block_args(wbsph_surrogate s, int bi) {
   const Block& b = s->blocks[bi];
   MlpArgs a;
@@ -1511,10 +1449,51 @@ MlpArgs block_args(wbsph_surrogate s, int bi) {
   return a;
 }
 
-// Graph of the sim's current state (candidate lists must be built).
-int build_graph(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n,
-                int64_t nf, cudaStream_t cs) {
-  int rc = ensure_nodes(s, n, nf);
+// One fused message-passing layer (k_message_tc): persistent CTAs, one per
+// SM (186 KB of shared memory and 256 TMEM columns each), two receiver
+// groups per CTA.
+void launch_message(wbsph_surrogate s, const Params& p, const Work& w, int64_t nf, int64_t nd, int l,
+                    const bf16* h_in, bf16* h_out, bf16* m_out, cudaStream_t st) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+    cudaFuncSetAttribute(k_message_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MS_SMEM_BYTES);
+  }
+  const Block& be = s->blocks[1 + 2 * l];
+  const Block& bn = s->blocks[2 + 2 * l];
+  MsgArgs a;
+  memset(&a, 0, sizeof a);
+  a.nf = nf; a.nd = nd;
+  a.fluid_list = w.fluid_list; a.dummy_list = w.dummy_list; a.nbr = w.nbr; a.nbr_cnt = w.nbr_cnt;
+  a.packA = s->packA; a.packB = s->packB;
+  a.h_in = h_in; a.h_out = h_out; a.m_out = m_out;
+  a.we_w1 = s->pb + be.w1; a.we_b1 = s->p + be.b1; a.we_w2 = s->pb + be.w2; a.we_b2 = s->p + be.b2;
+  a.wn_w1 = s->pb + bn.w1; a.wn_b1 = s->p + bn.b1; a.wn_w2 = s->pb + bn.w2; a.wn_b2 = s->p + bn.b2;
+  a.dim = p.dim; a.kg = 2 * p.dim + 2;
+  a.inv_h = (float)(1.0 / p.h);
+  a.inv_su = 1.f / s->edge_std[0];
+  a.inv_sphi = 1.f / s->edge_std[1];
+  a.status = w.status;
+  const int64_t tiles = div_up(nf, 128) + div_up(nd, 128);
+  if (tiles == 0) return;
+  const int64_t want = div_up(tiles, MS_GROUPS);
+  const int grid = (int)(want < sms ? want : sms);
+  k_message_tc<<<grid, MS_THREADS, MS_SMEM_BYTES, st>>>(a);
+}
+
+// node inputs and packs of the sim's current state (wall particles updated)
+void node_inputs(wbsph_surrogate s, const Params& p, const State& st, int64_t n, cudaStream_t cs) {
+  if (n > 0)
+    k_sg_nodes<<<(unsigned)div_up(n, 256), 256, 0, cs>>>(p, st, n, s->norm, s->norm + 8, s->nfeat, s->packA,
+                                                         s->packB);
+}
+
+// Training graph of the sim's current state (neighbour lists built).
+int build_graph(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t cs) {
+  int rc = ensure_train_nodes(s, n, nf);
   if (rc) return rc;
   // edges of receiver gi = its neighbour list (exact neighbours, built by k_nbr_list)
   if (nf > 0) cudaMemcpyAsync(s->row_ptr, w.nbr_cnt, nf * 4, cudaMemcpyDeviceToDevice, cs);
@@ -1527,67 +1506,55 @@ int build_graph(wbsph_surrogate s, const Params& p, const State& st, const Work&
   rc = ensure_edges(s, E);
   if (rc) return rc;
   if (nf > 0)
-    k_sg_fill<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p, st, w, n, nf, s->row_ptr, s->recv, s->send, s->efeat,
-                                                         s->norm + 8);
-  k_sg_nodes<<<(unsigned)div_up(n > 0 ? n : 1, 256), 256, 0, cs>>>(p, st, n, s->norm, s->norm + 8, s->nfeat);
+    k_sg_fill<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, nf, s->row_ptr, s->packA, s->packB,
+                                                         (float)(1.0 / p.h), 1.f / s->edge_std[0],
+                                                         1.f / s->edge_std[1], s->recv, s->send, s->efeat);
   return WBSPH_OK;
 }
 
-int forward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream_t cs) {
-  const int64_t E = s->E;
-  int L = s->layers;
-  // node and edge encoders (tcgen05, K = 16)
-  const char* tma_err = "TMA tensor map of the surrogate activations could not be built";
-  launch_tc<TC_ENC>(s->nfeat, s->hs[0], n, nullptr, nullptr, nullptr, block_args(s, 0), w.status, cs);
-  launch_tc<TC_ENC>(s->efeat, s->es[0], E, nullptr, nullptr, nullptr, block_args(s, 1), w.status, cs);
-  const int pgrid = (int)(div_up(n > 0 ? n : 1, TILE) < 152 * 4 ? div_up(n > 0 ? n : 1, TILE) : 152 * 4);
+// encoder, layers, decoder; with `train` the message sums of every layer are kept
+int forward(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, int64_t nf, bool train, cudaStream_t cs) {
+  const int L = s->layers;
+  {  // node encoder (rows of 8 inputs)
+    MlpArgs a = block_args(s, 0);
+    a.rows = n; a.in = s->nfeat; a.out_bf = s->hs[0];
+    launch_fwd<MODE_DIRECT, 16, 64>(a, n, cs);
+  }
   for (int l = 0; l < L; ++l) {
-    MlpArgs a = block_args(s, 2 + 2 * l);
-    k_node_proj<<<pgrid, MLP_THREADS, 0, cs>>>(s->hs[l], n, a.w1, a.b1, s->proj);
-    if (!launch_edge_tc(s->es[l], s->es[l + 1], E, s->recv, s->send, s->proj, a, w.status, cs))
-      return sfail(s, WBSPH_E_CUDA, tma_err);
-    cudaMemsetAsync(s->aggs[l], 0, (size_t)n * HID * 2, cs);
-    if (nf > 0)
-      k_sg_aggregate<<<(unsigned)div_up(nf, 4), 128, 0, cs>>>(w.fluid_list, nf, s->row_ptr, s->es[l + 1], s->aggs[l]);
-    // node MLP (tcgen05): h_{l+1} = h_l + MLP_n([h_l, a_l])
-    if (!launch_tc<TC_NODE>(s->hs[l], s->hs[l + 1], n, nullptr, nullptr, s->aggs[l], block_args(s, 3 + 2 * l),
-                       w.status, cs))
-      return sfail(s, WBSPH_E_CUDA, tma_err);
+    bf16* m_out = train ? s->ms[l] : nullptr;
+    if (m_out) cudaMemsetAsync(m_out, 0, (size_t)n * HID * 2, cs);  // rows of wall particles stay zero
+    launch_message(s, p, w, nf, n - nf, l, s->hs[l], s->hs[l + 1], m_out, cs);
   }
   {  // decoder over fluid rows
-    MlpArgs a = block_args(s, 2 + 2 * L);
+    MlpArgs a = block_args(s, 1 + 2 * L);
     a.rows = nf; a.in = s->hs[L]; a.list = w.fluid_list; a.out_f = s->out;
     launch_fwd<MODE_LIST, 64, 16>(a, nf, cs);
   }
   return WBSPH_OK;
 }
 
-void backward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStream_t cs) {
+void backward(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t cs) {
   const int64_t E = s->E;
-  int L = s->layers;
+  const int L = s->layers;
   cudaMemsetAsync(s->g, 0, (size_t)s->np * 4, cs);
   cudaMemsetAsync(s->dh, 0, (size_t)n * HID * 4, cs);
-  cudaMemsetAsync(s->de, 0, (size_t)E * HID * 4 + 4, cs);
   {  // decoder: dh_L[fluid] = dX
-    MlpArgs a = block_args(s, 2 + 2 * L);
+    MlpArgs a = block_args(s, 1 + 2 * L);
     a.rows = nf; a.in = s->hs[L]; a.list = w.fluid_list; a.dout = s->dout; a.dh = s->dh;
     launch_bwd<MODE_LIST, 64, 16>(a, nf, cs);
   }
   for (int l = L - 1; l >= 0; --l) {
-    MlpArgs b = block_args(s, 3 + 2 * l);  // node MLP: dh_l = dh_{l+1} + dX[:64], dagg = dX[64:]
-    b.rows = n; b.h = s->hs[l]; b.agg = s->aggs[l]; b.dout = s->dh; b.din_row = s->dh; b.dagg = s->dagg;
+    MlpArgs b = block_args(s, 2 + 2 * l);  // node MLP: dh_l = dh_{l+1} + dX[:64], dm = dX[64:]
+    b.rows = n; b.h = s->hs[l]; b.agg = s->ms[l]; b.dout = s->dh; b.din_row = s->dh; b.dagg = s->dagg;
     launch_bwd<MODE_NODE, 128, 64>(b, n, cs);
     if (nf > 0)
       k_sg_aggregate_bwd<<<(unsigned)div_up(nf, 4), 128, 0, cs>>>(w.fluid_list, nf, s->row_ptr, s->dagg, s->de);
-    MlpArgs a = block_args(s, 2 + 2 * l);  // edge MLP: de_l = de_{l+1} + dX[:64], dh += scatter
-    a.rows = E; a.e = s->es[l]; a.h = s->hs[l]; a.recv = s->recv; a.send = s->send;
-    a.dout = s->de; a.din_row = s->de; a.dh = s->dh;
-    launch_bwd<MODE_EDGE, 192, 64>(a, E, cs);
+    MlpArgs a = block_args(s, 1 + 2 * l);  // edge MLP on [g, h_i, h_j]: dh += scatter of dX[16:]
+    a.rows = E; a.e = s->efeat; a.h = s->hs[l]; a.recv = s->recv; a.send = s->send; a.kg = 2 * p.dim + 2;
+    a.dout = s->de; a.dh = s->dh;
+    launch_bwd<MODE_EDGE, EDGE_KP, 64>(a, E, cs);
   }
-  {  // encoders: weight gradients only
-    MlpArgs a = block_args(s, 1);
-    a.rows = E; a.in = s->efeat; a.dout = s->de;
-    launch_bwd<MODE_DIRECT, 16, 64>(a, E, cs);
+  {  // node encoder: weight gradients only
     MlpArgs b = block_args(s, 0);
     b.rows = n; b.in = s->nfeat; b.dout = s->dh;
     launch_bwd<MODE_DIRECT, 16, 64>(b, n, cs);
@@ -1596,17 +1563,50 @@ void backward(wbsph_surrogate s, const Work& w, int64_t n, int64_t nf, cudaStrea
 
 }  // namespace
 
-// Called by the engine for a surrogate stage: graph over the candidate lists,
-// forward pass, de-normalised rates into the stage rate arrays.
+// Called by the engine for a surrogate stage: node inputs, forward pass,
+// de-normalised rates into the stage rate arrays (or, in the frozen-rates
+// control mode, the rates kept from the last plain stage).
 namespace wbsph {
 int surrogate_stage_rates(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n,
                           int64_t nf, cudaStream_t cs) {
+  if (s->mode == WBSPH_SURROGATE_FROZEN) {
+    if (!s->frozen) return sfail(s, WBSPH_E_STATE, "frozen-rates mode has no stored rates");
+    if (nf > 0)
+      k_frozen_rates<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, st.oid, n, nf, s->frozen, s->cap_frozen);
+    return WBSPH_OK;
+  }
   launch_nbr_list(p, st, w, n, nf, cs, true);
-  int rc = build_graph(s, p, st, w, n, nf, cs);
+  int rc = ensure_nodes(s, n, nf);
   if (rc) return rc;
-  if ((rc = forward(s, w, n, nf, cs))) return rc;
+  node_inputs(s, p, st, n, cs);
+  if ((rc = forward(s, p, w, n, nf, false, cs))) return rc;
   if (nf > 0)
     k_sg_rates<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, n, nf, s->out, s->norm + 16, s->norm + 20);
+  return WBSPH_OK;
+}
+
+int surrogate_mode(wbsph_surrogate s) { return s->mode; }
+
+// Kernel launches of one surrogate stage (surrogate_stage_rates).
+int surrogate_stage_launches(wbsph_surrogate s, int64_t nf) {
+  if (nf == 0) return 0;
+  if (s->mode == WBSPH_SURROGATE_FROZEN) return 1;
+  return 1 + 1 + 1 + s->layers + 1 + 1;  // lists, node inputs, encoder, layers, decoder, rates
+}
+
+// The rates of a plain stage of a rollout (fluid particles): kept by the
+// frozen-rates control; nothing in network mode.
+int surrogate_plain_rates(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n, int64_t nf,
+                          int64_t n_ids, cudaStream_t cs) {
+  if (s->mode != WBSPH_SURROGATE_FROZEN || nf == 0) return WBSPH_OK;
+  if (n_ids > s->cap_frozen) {
+    dfree(s->frozen);
+    s->frozen = nullptr;
+    s->cap_frozen = 0;
+    if (!dalloc(&s->frozen, (size_t)(p.dim + 1) * n_ids)) return sfail(s, WBSPH_E_NOMEM, "frozen rates");
+    s->cap_frozen = n_ids;
+  }
+  k_frozen_store<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, st.oid, n, nf, s->frozen, s->cap_frozen);
   return WBSPH_OK;
 }
 
@@ -1615,17 +1615,20 @@ int surrogate_stage_rates(wbsph_surrogate s, const Params& p, const State& st, c
 int surrogate_loss(wbsph_surrogate s, const Params& p, const State& st, const Work& w, int64_t n, int64_t nf,
                    cudaStream_t cs, int train, float lr, double* loss_out, const float* dout_override,
                    float* grad_out) {
+  if (s->mode != WBSPH_SURROGATE_NETWORK) return sfail(s, WBSPH_E_STATE, "loss needs the network mode");
   launch_nbr_list(p, st, w, n, nf, cs, true);
-  int rc = build_graph(s, p, st, w, n, nf, cs);
+  int rc = ensure_nodes(s, n, nf);
   if (rc) return rc;
-  if ((rc = forward(s, w, n, nf, cs))) return rc;
+  node_inputs(s, p, st, n, cs);
+  if ((rc = build_graph(s, p, w, n, nf, cs))) return rc;
+  if ((rc = forward(s, p, w, n, nf, true, cs))) return rc;
   cudaMemsetAsync(s->loss, 0, 8, cs);
   if (nf > 0)
     k_sg_loss<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, n, nf, s->out, s->norm + 16, s->norm + 20,
                                                           s->dout, s->loss);
   if (dout_override)
     cudaMemcpyAsync(s->dout, dout_override, (size_t)nf * (p.dim + 1) * 4, cudaMemcpyHostToDevice, cs);
-  if (train || grad_out) backward(s, w, n, nf, cs);
+  if (train || grad_out) backward(s, p, w, n, nf, cs);
   if (grad_out) cudaMemcpyAsync(grad_out, s->g, (size_t)s->np * 4, cudaMemcpyDeviceToHost, cs);
   if (train) {
     s->adam_t += 1;
@@ -1706,6 +1709,7 @@ extern "C" void wbsph_surrogate_destroy(wbsph_surrogate s) {
   cudaDeviceSynchronize();
   free_graph(s);
   dfree(s->p); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->pb); dfree(s->norm); dfree(s->loss);
+  dfree(s->frozen);
   delete s;
 }
 
@@ -1730,9 +1734,9 @@ extern "C" int wbsph_surrogate_get_params(wbsph_surrogate s, float* params) {
 }
 
 extern "C" int wbsph_surrogate_set_normalization(wbsph_surrogate s, const float* node_mean,
-                                                 const float* node_std, const float* out_mean,
-                                                 const float* out_std) {
-  if (!s || !node_mean || !node_std || !out_mean || !out_std) return WBSPH_E_INVAL;
+                                                 const float* node_std, const float* edge_std,
+                                                 const float* out_mean, const float* out_std) {
+  if (!s || !node_mean || !node_std || !edge_std || !out_mean || !out_std) return WBSPH_E_INVAL;
   std::vector<float> nrm(32, 0.f);
   int fn = s->dim + 2, fo = s->dim + 1;
   for (int k = 0; k < 8; ++k) nrm[8 + k] = 1.f;
@@ -1747,8 +1751,21 @@ extern "C" int wbsph_surrogate_set_normalization(wbsph_surrogate s, const float*
     nrm[16 + k] = out_mean[k];
     nrm[20 + k] = out_std[k];
   }
+  for (int k = 0; k < 2; ++k) {
+    if (!(edge_std[k] > 0)) return sfail(s, WBSPH_E_INVAL, "edge scales must be positive");
+    nrm[24 + k] = edge_std[k];
+    s->edge_std[k] = edge_std[k];
+  }
   cudaSetDevice(s->cfg.device);
   return cudaMemcpy(s->norm, nrm.data(), 32 * 4, cudaMemcpyHostToDevice) == cudaSuccess ? WBSPH_OK : WBSPH_E_CUDA;
+}
+
+extern "C" int wbsph_surrogate_set_mode(wbsph_surrogate s, int mode) {
+  if (!s) return WBSPH_E_INVAL;
+  if (mode != WBSPH_SURROGATE_NETWORK && mode != WBSPH_SURROGATE_FROZEN)
+    return sfail(s, WBSPH_E_INVAL, "unknown surrogate mode");
+  s->mode = mode;
+  return WBSPH_OK;
 }
 
 extern "C" const char* wbsph_surrogate_last_error(wbsph_surrogate s) { return s ? s->err.c_str() : "null"; }

@@ -89,11 +89,22 @@ def _load_state(sim, sc, st):
     sim.set_particles(x, u, phi, sc.type, sc.normal)
 
 
+def hydrostatic_potential(params, x, water_height):
+    """phi_hs(x) = G.x + |G| H: the split of the potential that the network's
+    inputs use (the constant body force G of the scene)."""
+    d = int(params["dim"])
+    g = np.asarray(params["g"][:d], dtype=np.float64)
+    return g @ np.asarray(x)[:d] + np.linalg.norm(g) * water_height
+
+
 def normalisation(data, samples=20, seed=0):
-    """Means and standard deviations of the node features (U, rho/rho0 - 1,
-    phi) and of the plain rates (DU/Dt, Dphi/Dt) over sampled frames."""
+    """Means and standard deviations of the node inputs (U, rho/rho0 - 1,
+    phi'), the scales of the edge inputs (RMS over edges of the velocity and
+    potential differences), and the means and deviations of the plain rates
+    (DU/Dt, Dphi/Dt), over sampled frames. Returns (node_mean, node_std,
+    edge_std, out_mean, out_std)."""
     rng = np.random.default_rng(seed)
-    feats, outs = [], []
+    feats, outs, du, dp = [], [], [], []
     for _ in range(samples):
         sc, states = data[rng.integers(len(data))]
         st = states[rng.integers(len(states))]
@@ -102,15 +113,24 @@ def normalisation(data, samples=20, seed=0):
         sim.eval_rates()
         f = sc.type == 0
         rho = sim.get("rho")
-        d = sc.params["dim"]
-        feats.append(np.r_[st[1][:, f], (rho[f] / sc.params["rho0"] - 1.0)[None], st[2][None, f]])
+        u, phi = sim.get("u"), sim.get("phi")          # wall particles after their update
+        phip = phi - hydrostatic_potential(sc.params, st[0], sc.water_height)
+        feats.append(np.r_[u[:, f], (rho[f] / sc.params["rho0"] - 1.0)[None], phip[None, f]])
         outs.append(np.r_[sim.get("dudt")[:, f], sim.get("dphidt")[None, f]])
+        row, col = sim.neighbors()
+        recv = np.repeat(np.arange(sc.n), np.diff(row))
+        keep = f[recv]
+        recv, send = recv[keep], col[keep].astype(np.int64)
+        du.append((u[:, send] - u[:, recv]).ravel())
+        dp.append(phip[send] - phip[recv])
         sim.close()
     F = np.concatenate(feats, axis=1)
     O = np.concatenate(outs, axis=1)
     fs = np.maximum(F.std(1), 1e-6)
     os_ = np.maximum(O.std(1), 1e-6)
-    return F.mean(1), fs, O.mean(1), os_
+    es = np.array([max(float(np.sqrt(np.mean(np.concatenate(du) ** 2))), 1e-6),
+                   max(float(np.sqrt(np.mean(np.concatenate(dp) ** 2))), 1e-6)])
+    return F.mean(1), fs, es, O.mean(1), os_
 
 
 def train(sur: "wbsph.Surrogate", data, iters=2000, lr=1e-3, seed=1, log=print, log_every=200):
@@ -146,10 +166,19 @@ def gravity_only_params(dim, out_mean, out_std, g):
     return from_flat
 
 
-def wbsph_num_params(dim, hidden=64, layers=3):
+def block_dims(dim, hidden=64, layers=3):
+    """(name, inputs, outputs) of the parameter blocks in their flat order:
+    node encoder, (edge MLP, node MLP) per layer, decoder."""
     fn, fe, fo = dim + 3, 2 * dim + 2, dim + 1
-    blocks = [(fn, hidden), (fe, hidden)] + [(3 * hidden, hidden), (2 * hidden, hidden)] * layers + [(hidden, fo)]
-    return sum(i * hidden + hidden + hidden * o + o for i, o in blocks)
+    blocks = [("enc", fn, hidden)]
+    for _ in range(layers):
+        blocks += [("edge", fe + 2 * hidden, hidden), ("node", 2 * hidden, hidden)]
+    blocks.append(("dec", hidden, fo))
+    return blocks
+
+
+def wbsph_num_params(dim, hidden=64, layers=3):
+    return sum(i * hidden + hidden + hidden * o + o for _, i, o in block_dims(dim, hidden, layers))
 
 
 def rollout_error(sc, sur, nsteps, anchor_every=10, tau=0.1):
@@ -180,15 +209,17 @@ def rollout_error(sc, sur, nsteps, anchor_every=10, tau=0.1):
 
 
 def save(path, sur, norm, meta):
-    np.savez(path, params=sur.get_params(), node_mean=norm[0], node_std=norm[1], out_mean=norm[2],
-             out_std=norm[3], meta=np.frombuffer(str(meta).encode(), dtype=np.uint8))
+    np.savez(path, params=sur.get_params(), node_mean=norm[0], node_std=norm[1], edge_std=norm[2],
+             out_mean=norm[3], out_std=norm[4], meta=np.frombuffer(str(meta).encode(), dtype=np.uint8))
 
 
 def load(path, dim=2):
+    """Network and normalisation (node_mean, node_std, edge_std, out_mean,
+    out_std) from a file written by save()."""
     z = np.load(path)
     sur = wbsph.Surrogate(dim)
     sur.set_params(z["params"])
-    norm = (z["node_mean"], z["node_std"], z["out_mean"], z["out_std"])
+    norm = (z["node_mean"], z["node_std"], z["edge_std"], z["out_mean"], z["out_std"])
     sur.set_normalization(*norm)
     return sur, norm
 
@@ -239,7 +270,7 @@ def main(argv=None):
     inf = float("inf")
     rep["trained"] = rollout_error(held, sur, args.eval_steps, tau=inf)
     grav = wbsph.Surrogate(dim)
-    grav.set_params(gravity_only_params(dim, norm[2], norm[3], held.params["g"]))
+    grav.set_params(gravity_only_params(dim, norm[3], norm[4], held.params["g"]))
     grav.set_normalization(*norm)
     rep["gravity_only"] = rollout_error(held, grav, args.eval_steps, tau=inf)
     untrained = wbsph.Surrogate(dim)
@@ -259,19 +290,18 @@ def init_params_2d(seed=0, hidden=64, layers=3):
 
 
 def init_params(dim, seed=0, hidden=64, layers=3):
-    """Uniform(+-1/sqrt(fan_in)) weights, zero biases, processor output
-    layers scaled by 0.1 (small residual updates at the start)."""
+    """Uniform(+-1/sqrt(fan_in)) weights, zero biases; the output layers of
+    the processor MLPs scaled by 0.1 (small residual updates at the start),
+    the edge MLP's by a further 1/8 (its outputs are summed over the
+    receiver's neighbours)."""
     rng = np.random.default_rng(seed)
-    fn, fe, fo = dim + 3, 2 * dim + 2, dim + 1
-    blocks = [("n", fn, hidden), ("e", fe, hidden)]
-    for _ in range(layers):
-        blocks += [("mp", 3 * hidden, hidden), ("mp", 2 * hidden, hidden)]
-    blocks.append(("dec", hidden, fo))
     parts = []
-    for name, i, o in blocks:
+    for name, i, o in block_dims(dim, hidden, layers):
         s1, s2 = 1.0 / math.sqrt(i), 1.0 / math.sqrt(hidden)
-        if name == "mp":
+        if name in ("edge", "node"):
             s2 *= 0.1
+        if name == "edge":
+            s2 /= 8.0
         parts += [rng.uniform(-s1, s1, i * hidden), np.zeros(hidden), rng.uniform(-s2, s2, hidden * o),
                   np.zeros(o)]
     return np.concatenate(parts).astype(np.float32)

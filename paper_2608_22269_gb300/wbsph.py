@@ -357,9 +357,11 @@ class AnchorStats(C.Structure):
                 ("fallbacks", C.c_int64), ("last_rel_err", C.c_double), ("max_rel_err", C.c_double)]
 
 
+SURROGATE_NETWORK, SURROGATE_FROZEN = 0, 1
 SURROGATE_SYMBOLS = ["wbsph_surrogate_config_default", "wbsph_surrogate_create",
                      "wbsph_surrogate_num_params", "wbsph_surrogate_set_params",
                      "wbsph_surrogate_get_params", "wbsph_surrogate_set_normalization",
+                     "wbsph_surrogate_set_mode",
                      "wbsph_surrogate_train_step", "wbsph_surrogate_eval", "wbsph_surrogate_predict",
                      "wbsph_surrogate_debug", "wbsph_step_surrogate", "wbsph_surrogate_destroy",
                      "wbsph_surrogate_last_error"]
@@ -376,7 +378,8 @@ def _load_surrogate(L):
         "wbsph_surrogate_num_params": (i64, [P]),
         "wbsph_surrogate_set_params": (I, [P, P]),
         "wbsph_surrogate_get_params": (I, [P, P]),
-        "wbsph_surrogate_set_normalization": (I, [P, P, P, P, P]),
+        "wbsph_surrogate_set_normalization": (I, [P, P, P, P, P, P]),
+        "wbsph_surrogate_set_mode": (I, [P, I]),
         "wbsph_surrogate_train_step": (I, [P, P, F, P]),
         "wbsph_surrogate_eval": (I, [P, P, P]),
         "wbsph_surrogate_predict": (I, [P, P]),
@@ -439,9 +442,17 @@ class Surrogate:
         self._check(self.lib.wbsph_surrogate_get_params(self.h, _ptr(out)))
         return out
 
-    def set_normalization(self, node_mean, node_std, out_mean, out_std):
-        a = [np.ascontiguousarray(v, dtype=np.float32) for v in (node_mean, node_std, out_mean, out_std)]
+    def set_normalization(self, node_mean, node_std, edge_std, out_mean, out_std):
+        """Scales of the inputs and outputs: node (dim + 2 means and stds of
+        U, rho/rho0 - 1, phi'), edge (s_U, s_phi) and output (dim + 1)."""
+        a = [np.ascontiguousarray(v, dtype=np.float32)
+             for v in (node_mean, node_std, edge_std, out_mean, out_std)]
         self._check(self.lib.wbsph_surrogate_set_normalization(self.h, *[_ptr(v) for v in a]))
+
+    def set_mode(self, mode):
+        """SURROGATE_NETWORK, or SURROGATE_FROZEN: the control whose surrogate
+        stages replay the rates of the rollout's last plain stage."""
+        self._check(self.lib.wbsph_surrogate_set_mode(self.h, int(mode)))
 
     def train_step(self, sim, lr):
         loss = C.c_double()

@@ -241,7 +241,7 @@ def test_full_size_surrogate_sampled():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     z = np.load(os.path.join(root, "paper_2608_22269_gb300", "data", "surrogate_2d.npz"))
     sur, norm = SG.load(os.path.join(root, "paper_2608_22269_gb300", "data", "surrogate_2d.npz"), 2)
-    nm, ns, om, osd = (np.asarray(a, dtype=np.float32) for a in norm)
+    nm, ns, es, om, osd = (np.asarray(a, dtype=np.float32) for a in norm)
     sc = _scene("dam2d_249k")
     p = sc.params
     sim = _sim(sc)
@@ -251,7 +251,7 @@ def test_full_size_surrogate_sampled():
     smp = sample_fluid(sc, 32, seed=21)
     idx, loc = _patch(sc, smp, 6.0 * _h(p) + 0.05 * p["dx"])
     recv, send, node_in, edge_in = mpnn.graph_and_features(p, sc.x[:, idx], u[:, idx], phi[idx],
-                                                           sc.type[idx], nm, ns)
+                                                           sc.type[idx], nm, ns, es, sc.water_height)
     th = mpnn.round_weights_bf16(z["params"], 2)
     out = mpnn.forward_np(th, 2, node_in, recv, send, edge_in)[loc]
     ref = out * osd + om

@@ -28,9 +28,10 @@ def _state(dim=2, seed=3, dx2=0.01):
 
 def _setup(sc, seed=1):
     """Sim and network of a state. The normalisation comes from the oracle's
-    stage rates of the same state (host inputs only); returns the sim, the
-    surrogate, the FP32 parameters, the output normalisation and the oracle
-    rates (with the dummies' updated U and phi)."""
+    stage rates and graph of the same state (host inputs only); returns the
+    sim, the surrogate, the FP32 parameters, the normalisation (node mean,
+    node std, edge std, output mean, output std) and the oracle rates (with
+    the dummies' updated U and phi)."""
     from paper_2608_22269_gb300 import wbsph
     dim = sc.params["dim"]
     sim = wbsph.Sim(sc.params, water_height=sc.water_height)
@@ -40,14 +41,25 @@ def _setup(sc, seed=1):
     theta = theta + np.random.default_rng(seed).normal(scale=0.02, size=theta.size).astype(np.float32)
     sur.set_params(theta)
     f = sc.type == 0
-    node_mean = np.r_[sc.u[:, f].mean(1), 0.0, sc.phi[f].mean()].astype(np.float32)
-    node_std = np.r_[sc.u[:, f].std(1), 1e-3, sc.phi[f].std()].astype(np.float32)
     r = oracle.stage_rates(sc.params, sc.x, sc.u, sc.phi, oracle.mass(sc.params, sc.phi), sc.type,
                            sc.normal)
+    phip = r["phi"] - mpnn.hydrostatic_potential(sc.params, sc.x, sc.water_height)
+    node_mean = np.r_[sc.u[:, f].mean(1), 0.0, phip[f].mean()].astype(np.float32)
+    node_std = np.r_[sc.u[:, f].std(1), 1e-3, phip[f].std()].astype(np.float32)
+    _, _, _, e1 = mpnn.graph_and_features(sc.params, sc.x, r["u"], r["phi"], sc.type, node_mean, node_std,
+                                          np.ones(2, np.float32), sc.water_height)
+    edge_std = np.array([np.sqrt(np.mean(e1[:, dim + 1:2 * dim + 1] ** 2)),
+                         np.sqrt(np.mean(e1[:, 2 * dim + 1] ** 2))], np.float32)
     a = np.r_[r["dudt"][:, f], r["dphidt"][None, f]]
     out_mean, out_std = a.mean(1).astype(np.float32), a.std(1).astype(np.float32)
-    sur.set_normalization(node_mean, node_std, out_mean, out_std)
-    return sim, sur, theta, (node_mean, node_std, out_mean, out_std), r
+    norm = (node_mean, node_std, edge_std, out_mean, out_std)
+    sur.set_normalization(*norm)
+    return sim, sur, theta, norm, r
+
+
+def _graph(sc, r, norm):
+    return mpnn.graph_and_features(sc.params, sc.x, r["u"], r["phi"], sc.type, norm[0], norm[1], norm[2],
+                                   sc.water_height)
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -56,11 +68,11 @@ def test_forward_and_gradient_match_fp64_reference(dim):
     oracle's own graph and features of the same state, with the oracle's
     rates as targets."""
     sc = _state(dim)
-    sim, sur, theta, (nm, ns, om, osd), r = _setup(sc)
+    sim, sur, theta, norm, r = _setup(sc)
+    om, osd = norm[3], norm[4]
     dbg = sur.debug(sim)
     n = sc.n
-    recv, send, node_in, edge_in = mpnn.graph_and_features(sc.params, sc.x, r["u"], r["phi"], sc.type,
-                                                           nm, ns)
+    recv, send, node_in, edge_in = _graph(sc, r, norm)
     th = mpnn.round_weights_bf16(theta, dim)
     out = mpnn.forward_np(th, dim, node_in, recv, send, edge_in)
     fid = dbg["fluid_ids"].astype(np.int64)
@@ -93,10 +105,9 @@ def test_graph_and_edge_features_follow_the_positions(dim, dx2):
     15,000-fluid case spans several chunks of the row-pointer scan and
     hundreds of 128-edge tiles."""
     sc = _state(dim, dx2=dx2)
-    sim, sur, theta, (nm, ns, _, _), r = _setup(sc)
+    sim, sur, theta, norm, r = _setup(sc)
     dbg = sur.debug(sim)
-    recv, send, node_in, edge_in = mpnn.graph_and_features(sc.params, sc.x, r["u"], r["phi"], sc.type,
-                                                           nm, ns)
+    recv, send, node_in, edge_in = _graph(sc, r, norm)
     ref = dict(zip(zip(recv.tolist(), send.tolist()), range(recv.size)))
     got = list(zip(dbg["recv"].tolist(), dbg["send"].tolist()))
     assert len(got) == len(ref) and set(got) == set(ref)
@@ -132,3 +143,32 @@ def test_anchored_rollout_bookkeeping():
     assert st2["fallbacks"] >= 1 and st2["plain_steps"] > st2["anchors"]
     x = sim.get("x")
     assert np.all(np.isfinite(x))
+
+
+def test_frozen_rates_control_replays_the_last_plain_rates():
+    """The gain test's control A: in the frozen-rates mode a surrogate stage
+    gives every fluid particle, bit for bit, the plain rates it had at the
+    rollout's last plain stage (kept by original id, so the reorder of the
+    neighbour build does not matter). The first step of a rollout is plain
+    (an anchor); the mode has nothing to replay before it."""
+    from paper_2608_22269_gb300 import wbsph
+    sc = _state(2, seed=7)
+    sim, sur, _, _, _ = _setup(sc, seed=4)
+    ref = wbsph.Sim(sc.params, water_height=sc.water_height)
+    ref.set_scene(sc)
+    ref.eval_rates()
+    want_a, want_p = ref.get("dudt"), ref.get("dphidt")
+    sur.set_mode(wbsph.SURROGATE_FROZEN)
+    with pytest.raises(wbsph.WbsphError):
+        sur.predict(sim)                      # nothing kept yet
+    st = sur.step(sim, 3, anchor_every=10, tau=1e9)
+    assert st["plain_steps"] == 1 and st["surrogate_steps"] == 2
+    sur.predict(sim)
+    f = sc.type == 0
+    assert np.array_equal(sim.get("dudt")[:, f], want_a[:, f])
+    assert np.array_equal(sim.get("dphidt")[f], want_p[f])
+    assert np.all(sim.get("dushift")[:, f] == 0.0)
+    with pytest.raises(wbsph.WbsphError):
+        sur.eval(sim)                         # the loss needs the network
+    sur.set_mode(wbsph.SURROGATE_NETWORK)
+    assert np.isfinite(sur.eval(sim))
