@@ -218,14 +218,16 @@ int wbsph_get_profile(wbsph_handle h, double* ms, int64_t* launches, int reset);
  * split phi' = phi - phi_hs(x), phi_hs = G.x + |G| H (H the handle's water
  * height, as the mixed path); edge inputs: ((x_j - x_i)/h, |x_j - x_i|/h,
  * (U_j - U_i)/s_U, (phi'_j - phi'_i)/s_phi). Per layer the message of
- * receiver i is m_i = sum_j MLP_e([g_ij, h_i, h_j]) and h_i += MLP_n([h_i,
+ * receiver i is m_i = sum_j MLP_e([g_ij, h_i, h_j[:32]]) (a sender
+ * contributes the first 32 of its 64 state features) and h_i += MLP_n([h_i,
  * m_i]); nothing is kept per edge, so inference allocates per node only.
  * Three layers, hidden width 64, BF16 weights and activations, FP32
  * accumulation on the tensor cores (tcgen05); trained on the GPU against
  * the plain FP64 rates of the states it is shown. Parameters are a flat
  * FP32 vector: blocks node encoder, (edge MLP, node MLP) per layer,
  * decoder; each W1 [in][64], b1 [64], W2 [64][out], b2 [out], row-major;
- * the edge MLP's W1 rows are the 2 dim + 2 edge inputs, then h_i, then h_j.
+ * the edge MLP's W1 rows are the 2 dim + 2 edge inputs, then h_i (64), then
+ * h_j[:32].
  * This interface departs from a load-from-file / train-from-a-directory
  * pair: parameters and normalisation are set from host arrays, and
  * training is one step at a time on a state the caller loads, so that the

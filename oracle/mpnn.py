@@ -18,7 +18,8 @@ Network (dimension d, hidden H = 64, three message-passing layers):
               for receiver i, sender j (2d + 2; s_U, s_phi the edge scales)
   MLP(x) = W2 silu(W1 x + b1) + b2 (weights stored input-major: x @ W)
   h = MLP_enc(f)
-  per layer: m_i = sum_j MLP_e([g_ij, h_i, h_j]);  h <- h + MLP_n([h_i, m_i])
+  per layer: m_i = sum_j MLP_e([g_ij, h_i, h_j[:32]]);  h <- h + MLP_n([h_i, m_i])
+  (a sender contributes the first 32 of its 64 state features)
   output y_i = MLP_dec(h_i)  (d + 1: normalised DU/Dt and Dphi/Dt)
 No state is kept per edge: every layer's messages are formed from the edge
 inputs g_ij and the node states. Edges: every fluid receiver i with every
@@ -28,7 +29,7 @@ output components of the squared difference to the normalised targets.
 Flat parameter layout (shared with the CUDA library): blocks in the order
 node encoder, (edge MLP, node MLP) per layer, decoder; each block W1 [in][H],
 b1 [H], W2 [H][out], b2 [out], row-major; the edge MLP's W1 rows are the
-2d + 2 edge inputs, then h_i (64 rows), then h_j (64 rows).
+2d + 2 edge inputs, then h_i (64 rows), then h_j[:32] (32 rows).
 """
 from __future__ import annotations
 
@@ -37,13 +38,14 @@ import torch
 
 HIDDEN = 64
 LAYERS = 3
+SEND = 32   # sender features in a message
 
 
 def block_dims(dim: int, hidden: int = HIDDEN, layers: int = LAYERS):
     fn, fe, fo = dim + 3, 2 * dim + 2, dim + 1
     dims = [("enc_n", fn, hidden)]
     for l in range(layers):
-        dims += [(f"mp{l}_e", fe + 2 * hidden, hidden), (f"mp{l}_n", 2 * hidden, hidden)]
+        dims += [(f"mp{l}_e", fe + hidden + SEND, hidden), (f"mp{l}_n", 2 * hidden, hidden)]
     dims.append(("dec", hidden, fo))
     return dims
 
@@ -92,7 +94,7 @@ def forward(theta, dim, node_in, recv, send, edge_in, hidden=HIDDEN, layers=LAYE
     P = unflatten(theta, dim, hidden, layers)
     h = _mlp(node_in, P["enc_n"])
     for l in range(layers):
-        msg = _mlp(torch.cat([edge_in, h[recv], h[send]], dim=1), P[f"mp{l}_e"])
+        msg = _mlp(torch.cat([edge_in, h[recv], h[send][:, :SEND]], dim=1), P[f"mp{l}_e"])
         m = torch.zeros(h.shape, dtype=h.dtype).index_add(0, recv, msg)
         h = h + _mlp(torch.cat([h, m], dim=1), P[f"mp{l}_n"])
     return _mlp(h, P["dec"])

@@ -9,7 +9,7 @@
 // edge input g_ij = ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U,
 // (phi'_j - phi'_i)/s_phi) for every fluid receiver i and every particle j
 // within 2h; MLP(x) = W2 silu(W1 x + b1) + b2; a node encoder, three layers
-// of m_i = sum_j MLP_e([g_ij, h_i, h_j]), h <- h + MLP_n([h, m]), and a
+// of m_i = sum_j MLP_e([g_ij, h_i, h_j[:32]]), h <- h + MLP_n([h, m]), and a
 // decoder to normalised (DU/Dt, Dphi/Dt). Flat parameter layout: blocks node
 // encoder, (edge MLP, node MLP) per layer, decoder; each block W1 [in][64],
 // b1, W2 [64][out], b2.
@@ -130,7 +130,7 @@ struct MlpArgs {
   const uint32_t* send;      // EDGE
   const bf16* agg;           // NODE: [n][64]
   int kin, nout;             // true widths
-  int kg;                    // EDGE: edge inputs (2d + 2) at the head of the padded row [g | h_i | h_j]
+  int kg;                    // EDGE: edge inputs (2d + 2) at the head of the padded row [g | h_i | h_j[:32]]
   const bf16* w1; const float* b1; const bf16* w2; const float* b2;  // block parameters
   // forward outputs
   bf16* out_bf;              // [rows][64] (+ residual for EDGE/NODE)
@@ -138,7 +138,7 @@ struct MlpArgs {
   // backward
   const float* dout;         // [rows][nout] incoming gradient (EDGE/NODE/DIRECT: [rows][64])
   float* din_row;            // NODE: dh_in ([rows][64], = dout + dX[0:64])
-  float* dh;                 // EDGE: atomics into [n][64] (h_i and h_j); LIST: writes dh[list[row]]
+  float* dh;                 // EDGE: atomics into [n][64] (h_i and h_j[:32]); LIST: writes dh[list[row]]
   float* dagg;               // NODE: [rows][64]
   float* gw1; float* gb1; float* gw2; float* gb2;  // FP32 parameter gradients
 };
@@ -147,13 +147,15 @@ __device__ __forceinline__ int64_t arg_rows(const MlpArgs& a) {
   return a.rows_dev ? (int64_t)*a.rows_dev : a.rows;
 }
 
-// Padded input width of the edge MLP: the edge inputs padded to 16, h_i, h_j.
-constexpr int EDGE_KP = 16 + 2 * HID;
+// Padded input width of the edge MLP: the edge inputs padded to 16, h_i and
+// the sender's first 32 features (the message's sender part).
+constexpr int EDGE_SEND = 32;
+constexpr int EDGE_KP = 16 + HID + EDGE_SEND;
 
 // Row of the block's W1 (flat parameters) that multiplies padded input
 // column k, or -1 for a padding column. The edge MLP's W1 rows are the kg
-// edge inputs, then h_i and h_j; its padded input puts the edge inputs in
-// columns 0 .. 15.
+// edge inputs, then h_i (64) and h_j[:32]; its padded input puts the edge
+// inputs in columns 0 .. 15.
 template <int MODE>
 __device__ __forceinline__ int param_row(const MlpArgs& a, int k) {
   if (MODE == MODE_EDGE) return k < 16 ? (k < a.kg ? k : -1) : a.kg + (k - 16);
@@ -208,6 +210,12 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, boo
   unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   int n = valid ? 16 : 0;
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n));
+}
+// the same, cached in L1 (rows that neighbouring receivers gather again)
+__device__ __forceinline__ void cp_async16_ca(void* smem_dst, const void* gsrc, bool valid) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  int n = valid ? 16 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
@@ -510,16 +518,42 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// named barrier of one receiver group (256 threads), plain and with an AND vote
-__device__ __forceinline__ void group_bar(int id) {
-  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "n"(256) : "memory");
+// 32 FP32 columns of this thread's TMEM lane, issued without waiting; the
+// values may be used only after tc_wait_ld on the same registers (which ties
+// them to the wait)
+__device__ __forceinline__ void tc_ld32_nowait(uint32_t taddr, uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
 }
+__device__ __forceinline__ void tc_wait_ld(uint32_t r[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
+// named barrier of one receiver group (THREADS threads), plain and with an AND vote
+template <int THREADS>
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "n"(THREADS) : "memory");
+}
+template <int THREADS>
 __device__ __forceinline__ bool group_bar_and(int id, bool v) {
   uint32_t res;
   asm volatile(
       "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}\n"
       : "=r"(res)
-      : "r"((uint32_t)v), "r"(id), "n"(256)
+      : "r"((uint32_t)v), "r"(id), "n"(THREADS)
       : "memory");
   return res != 0;
 }
@@ -529,11 +563,14 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 
 // ---------------------------------------------------------------------------
 // One message-passing layer, fused, on tcgen05:
-//   m_i = sum_j MLP_e([g_ij, h_i, h_j]) = (sum_j silu(z_ij)) W2 + n_i b2,
-//   z_ij = g_ij W_g + h_i W_r + h_j W_s + b1,   h'_i = h_i + MLP_n([h_i, m_i]).
+//   m_i = sum_j MLP_e([g_ij, h_i, h_j[:SEND]]) = (sum_j silu(z_ij)) W2 + n_i b2,
+//   z_ij = g_ij W_g + h_i W_r + h_j[:SEND] W_s + b1,   h'_i = h_i + MLP_n([h_i, m_i]).
 // The second layer of the message MLP is linear, so it is applied once per
 // receiver after the sum; the per-edge work is the first layer, its SiLU and
-// the sum, and nothing per edge is ever written to memory.
+// the sum, and nothing per edge is ever written to memory. A sender
+// contributes the first SEND = 32 of its 64 state features, so a gathered
+// row is 64 B: the layer is bound by the gathers (a row and a 32-byte pack
+// per edge, from L2), and halving the row halves that traffic.
 //
 // A CTA runs MS_GROUPS independent groups of 256 threads; a group owns a
 // tile of 128 receivers (fluid particles in sorted order, one TMEM lane and
@@ -542,10 +579,11 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 // accumulator column half w / 4, so each thread holds 32 of the receiver's 64
 // running sums in registers. The group walks the receivers' k-major
 // neighbour lists, step k taking the k-th neighbour of every receiver:
-//   - gather (step k + 1, one step ahead): h_j rows by cp.async into a
-//     128-byte-swizzled K-major tile, the sender's FP32 packs into registers
-//     and from them the 16-wide edge-input row (K padded to 16);
-//   - one thread issues D = G W_g/2 + H W_s/2 (five K = 16 MMAs, M = 128,
+//   - gather (step k + 1, one step ahead): the sender rows by cp.async into a
+//     128-byte-swizzled K-major tile, the sender's FP32 pack (32 B: x, phi',
+//     U) into registers and from it the 16-wide edge-input row (K padded to
+//     16);
+//   - one thread issues D = G W_g/2 + H W_s/2 (three K = 16 MMAs, M = 128,
 //     N = 64, BF16 in, FP32 in TMEM), double-buffered in TMEM and smem;
 //   - epilogue: u = D + P_r/2 (P_r = h_i W_r + b1, from one MMA at the tile
 //     start, held as BF16 pairs), silu(2u) = u + u tanh(u) with the packed
@@ -556,6 +594,7 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 // h'_i is written. Every mbarrier wait is bounded; a timeout is voted over
 // the group, reported through the status word, and ends the group's work.
 // ---------------------------------------------------------------------------
+constexpr int SEND = 32;            // sender features in a message (the first SEND of h_j)
 constexpr int MS_GROUPS = 2;
 constexpr int MS_GROUP_THREADS = 256;
 constexpr int MS_THREADS = MS_GROUPS * MS_GROUP_THREADS;
@@ -569,8 +608,7 @@ struct MsgArgs {
   const uint32_t* dummy_list;
   const uint32_t* nbr;      // k-major exact neighbour lists of the fluid particles
   const uint32_t* nbr_cnt;
-  const float4* packA;      // (x, y, z, phi') per node
-  const float4* packB;      // (U, 0) per node
+  const float4* pack;       // per node: (x, y, z, phi'), (U, 0)
   const bf16* h_in;         // [n][64]
   bf16* h_out;              // [n][64]
   bf16* m_out;              // [n][64] message sums (training), or null
@@ -603,7 +641,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
     auto put = [&](int w, bf16 v) { *reinterpret_cast<bf16*>(W + w * MS_W_BYTES + off) = v; };
     put(WG, k < a.kg ? half(a.we_w1[k * HID + n]) : zero);
     put(WR, half(a.we_w1[(a.kg + k) * HID + n]));
-    put(WS, half(a.we_w1[(a.kg + HID + k) * HID + n]));
+    put(WS, k < SEND ? half(a.we_w1[(a.kg + HID + k) * HID + n]) : zero);
     put(WE2, a.we_w2[k * HID + n]);
     put(WH, a.wn_w1[k * HID + n]);
     put(WM, a.wn_w1[(HID + k) * HID + n]);
@@ -665,11 +703,16 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) cp_async16(T + sw128(r, ch * 4 + c), src + (ch * 4 + c) * 8, valid);
   };
+  // the sender's first SEND features (64 B, chunks 0..3 of the row): two chunks per column half
+  auto copy_send = [&](unsigned char* T, const bf16* src, bool valid) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) cp_async16(T + sw128(r, ch * 2 + c), src + (ch * 2 + c) * 8, valid);
+  };
   auto sync_operands = [&]() -> bool {  // smem operands written by the group -> tensor core
     cp_async_wait<0>();
     fence_async_smem();
     tc_fence_before();
-    ok = group_bar_and(bar_id, ok);
+    ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);
     return ok;
   };
   auto mma_k64 = [&](uint32_t d, const unsigned char* A, int w, bool accumulate) {
@@ -679,7 +722,9 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
   };
   auto mma_step = [&](uint32_t d, const unsigned char* Gb, const unsigned char* Hb) {
     tc_mma(d, tc_desc(smem_u32(Gb)), dW[WG], 0u);
-    mma_k64(d, Hb, WS, true);
+    const uint64_t dA = tc_desc(smem_u32(Hb));
+#pragma unroll
+    for (int kk = 0; kk < SEND / 16; ++kk) tc_mma(d, dA + 2 * kk, dW[WS] + 2 * kk, 1u);
   };
 
   const int64_t ntf = div_up(a.nf, 128), ntd = div_up(a.nd, 128), ntiles = ntf + ntd;
@@ -694,7 +739,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
     // longest list of the tile
     const int wm = __reduce_max_sync(0xffffffffu, cnt);
     if (lane == 0) wmax[g * 8 + lw] = wm;
-    group_bar(bar_id);
+    group_bar<MS_GROUP_THREADS>(bar_id);
     int kmax = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) kmax = max(kmax, wmax[g * 8 + w]);
@@ -703,17 +748,17 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
 #pragma unroll
     for (int c = 0; c < 32; ++c) acc[c] = 0.f;
     if (msg) {
-      const float4 ai = ch == 0 ? __ldg(a.packA + node) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 bi = ch == 0 ? __ldg(a.packB + node) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 ai = ch == 0 ? __ldg(a.pack + 2 * node) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 bi = ch == 0 ? __ldg(a.pack + 2 * node + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
       // h_i rows (for P_r) into G1, step 0 into G0 / H0
       copy_row_half(G1, a.h_in + (int64_t)node * HID, valid);
       uint32_t jn = cnt > 0 ? __ldg(a.nbr + gi) : 0u;
-      copy_row_half(H0, a.h_in + (int64_t)jn * HID, cnt > 0);
+      copy_send(H0, a.h_in + (int64_t)jn * HID, cnt > 0);
       cp_async_commit();
       if (ch == 0) {
         uint4 f = zero4;
         if (cnt > 0)
-          f = edge_features(a.dim, ai, bi, __ldg(a.packA + jn), __ldg(a.packB + jn), a.inv_h, a.inv_su,
+          f = edge_features(a.dim, ai, bi, __ldg(a.pack + 2 * jn), __ldg(a.pack + 2 * jn + 1), a.inv_h, a.inv_su,
                             a.inv_sphi);
         *reinterpret_cast<uint4*>(G0 + sw128(r, 0)) = f;
         *reinterpret_cast<uint4*>(G0 + sw128(r, 1)) = zero4;
@@ -748,11 +793,11 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
         const bool more = k + 1 < kmax, act1 = k + 1 < cnt;
         float4 aj = make_float4(0.f, 0.f, 0.f, 0.f), bj = aj;
         if (more) {  // step k + 1: h_j rows in flight, sender packs into registers
-          copy_row_half(Hn, a.h_in + (int64_t)jn * HID, act1);
+          copy_send(Hn, a.h_in + (int64_t)jn * HID, act1);
           cp_async_commit();
           if (ch == 0 && act1) {
-            aj = __ldg(a.packA + jn);
-            bj = __ldg(a.packB + jn);
+            aj = __ldg(a.pack + 2 * jn);
+            bj = __ldg(a.pack + 2 * jn + 1);
           }
         }
         const uint32_t jnn = k + 2 < cnt ? __ldg(a.nbr + (int64_t)(k + 2) * a.nf + gi) : 0u;
@@ -887,7 +932,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
       }
     }
     tc_fence_before();
-    ok = group_bar_and(bar_id, ok);  // H1 and TMEM reads done before the next tile's writes
+    ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);  // H1 and TMEM reads done before the next tile's writes
   }
   cp_async_wait<0>();
   if (!ok && (t % MS_GROUP_THREADS) == 0) atomicOr(a.status, (unsigned)kStatTimeout);
@@ -1119,9 +1164,9 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd(MlpArgs a) {
 // Node inputs and packs. Node input (BF16, 8 wide): (U, rho/rho0 - 1, phi')
 // minus the mean over the std, then the dummy flag, with the hydrostatic
 // split phi' = phi - phi_hs(x), phi_hs = G.x + |G| H (FP64, like the mixed
-// path). Packs (FP32) for the edge inputs: A = (x, y, z, phi'), B = (U, 0).
+// path). Pack (FP32, 32 B per node) for the edge inputs: (x, y, z, phi') and (U, 0).
 __global__ void k_sg_nodes(Params p, State s, int64_t n, const float* mean, const float* stdv, bf16* nf_out,
-                           float4* packA, float4* packB) {
+                           float4* pack) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double phs = p.phs0, xs[3] = {0.0, 0.0, 0.0}, us[3] = {0.0, 0.0, 0.0};
@@ -1143,8 +1188,8 @@ __global__ void k_sg_nodes(Params p, State s, int64_t n, const float* mean, cons
   o.z = pack2(__float2bfloat16(v[4]), __float2bfloat16(v[5]));
   o.w = pack2(__float2bfloat16(v[6]), __float2bfloat16(v[7]));
   *reinterpret_cast<uint4*>(nf_out + i * FEAT) = o;
-  packA[i] = make_float4((float)xs[0], (float)xs[1], (float)xs[2], (float)phip);
-  packB[i] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
+  pack[2 * i] = make_float4((float)xs[0], (float)xs[1], (float)xs[2], (float)phip);
+  pack[2 * i + 1] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
 }
 
 // Training graph: edges (receiver, sender) in CSR order by receiver and
@@ -1153,8 +1198,8 @@ __global__ void k_sg_nodes(Params p, State s, int64_t n, const float* mean, cons
 // contiguous range of their edges; lane l takes edges l, l + 32, ... of that
 // range and finds its receiver by a binary search over the lanes' row
 // starts, so every store of recv, send and the 16-byte input rows coalesces.
-__global__ void k_sg_fill(int dim, Work w, int64_t nf, const uint32_t* row_ptr, const float4* packA,
-                          const float4* packB, float inv_h, float inv_su, float inv_sphi, uint32_t* recv,
+__global__ void k_sg_fill(int dim, Work w, int64_t nf, const uint32_t* row_ptr, const float4* pack,
+                          float inv_h, float inv_su, float inv_sphi, uint32_t* recv,
                           uint32_t* send, bf16* efeat) {
   const int lane = threadIdx.x & 31;
   const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane;
@@ -1178,8 +1223,8 @@ __global__ void k_sg_fill(int dim, Work w, int64_t nf, const uint32_t* row_ptr, 
     recv[e] = i;
     send[e] = j;
     *reinterpret_cast<uint4*>(efeat + (int64_t)e * FEAT) =
-        edge_features(dim, __ldg(packA + i), __ldg(packB + i), __ldg(packA + j), __ldg(packB + j), inv_h, inv_su,
-                      inv_sphi);
+        edge_features(dim, __ldg(pack + 2 * i), __ldg(pack + 2 * i + 1), __ldg(pack + 2 * j), __ldg(pack + 2 * j + 1),
+                      inv_h, inv_su, inv_sphi);
   }
 }
 
@@ -1292,7 +1337,7 @@ struct wbsph_surrogate_s {
   // node buffers (inference and training), sized on demand
   int64_t cap_n = 0, cap_nf = 0;
   bf16* nfeat = nullptr;
-  float4 *packA = nullptr, *packB = nullptr;
+  float4* pack = nullptr;  // per node: (x, y, z, phi'), (U, 0)
   std::vector<bf16*> hs;
   float* out = nullptr;
   // training: the graph, message sums and gradients
@@ -1331,7 +1376,7 @@ void build_blocks(wbsph_surrogate s) {
   };
   add(d + 3, HID);
   for (int l = 0; l < s->layers; ++l) {
-    add(2 * d + 2 + 2 * HID, HID);
+    add(2 * d + 2 + HID + EDGE_SEND, HID);
     add(2 * HID, HID);
   }
   add(HID, d + 1);
@@ -1366,11 +1411,11 @@ void free_train(wbsph_surrogate s) {
 
 void free_graph(wbsph_surrogate s) {
   free_train(s);
-  dfree(s->nfeat); dfree(s->packA); dfree(s->packB); dfree(s->out);
+  dfree(s->nfeat); dfree(s->pack); dfree(s->out);
   for (auto* q : s->hs) dfree(q);
   s->hs.clear();
   s->nfeat = nullptr;
-  s->packA = s->packB = nullptr;
+  s->pack = nullptr;
   s->out = nullptr;
   s->cap_n = s->cap_nf = 0;
 }
@@ -1379,7 +1424,7 @@ int ensure_nodes(wbsph_surrogate s, int64_t n, int64_t nf) {
   if (n <= s->cap_n && nf <= s->cap_nf) return WBSPH_OK;
   free_graph(s);
   s->cap_n = n; s->cap_nf = nf;
-  bool ok = dalloc(&s->nfeat, n * FEAT) && dalloc(&s->packA, n) && dalloc(&s->packB, n) && dalloc(&s->out, nf * 4);
+  bool ok = dalloc(&s->nfeat, n * FEAT) && dalloc(&s->pack, 2 * n) && dalloc(&s->out, nf * 4);
   for (int l = 0; ok && l <= s->layers; ++l) {
     bf16* q = nullptr;
     ok = dalloc(&q, n * HID);
@@ -1449,6 +1494,9 @@ MlpArgs block_args(wbsph_surrogate s, int bi) {
   return a;
 }
 
+// Messages of one layer (k_message_tc): persistent CTAs, one per SM (226 KB
+// of shared memory and 256 TMEM columns each, 512 threads), two receiver
+// groups per CTA. Writes m_i of the fluid particles into m_out.
 // One fused message-passing layer (k_message_tc): persistent CTAs, one per
 // SM (186 KB of shared memory and 256 TMEM columns each), two receiver
 // groups per CTA.
@@ -1468,7 +1516,7 @@ void launch_message(wbsph_surrogate s, const Params& p, const Work& w, int64_t n
   memset(&a, 0, sizeof a);
   a.nf = nf; a.nd = nd;
   a.fluid_list = w.fluid_list; a.dummy_list = w.dummy_list; a.nbr = w.nbr; a.nbr_cnt = w.nbr_cnt;
-  a.packA = s->packA; a.packB = s->packB;
+  a.pack = s->pack;
   a.h_in = h_in; a.h_out = h_out; a.m_out = m_out;
   a.we_w1 = s->pb + be.w1; a.we_b1 = s->p + be.b1; a.we_w2 = s->pb + be.w2; a.we_b2 = s->p + be.b2;
   a.wn_w1 = s->pb + bn.w1; a.wn_b1 = s->p + bn.b1; a.wn_w2 = s->pb + bn.w2; a.wn_b2 = s->p + bn.b2;
@@ -1487,8 +1535,7 @@ void launch_message(wbsph_surrogate s, const Params& p, const Work& w, int64_t n
 // node inputs and packs of the sim's current state (wall particles updated)
 void node_inputs(wbsph_surrogate s, const Params& p, const State& st, int64_t n, cudaStream_t cs) {
   if (n > 0)
-    k_sg_nodes<<<(unsigned)div_up(n, 256), 256, 0, cs>>>(p, st, n, s->norm, s->norm + 8, s->nfeat, s->packA,
-                                                         s->packB);
+    k_sg_nodes<<<(unsigned)div_up(n, 256), 256, 0, cs>>>(p, st, n, s->norm, s->norm + 8, s->nfeat, s->pack);
 }
 
 // Training graph of the sim's current state (neighbour lists built).
@@ -1506,7 +1553,7 @@ int build_graph(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, in
   rc = ensure_edges(s, E);
   if (rc) return rc;
   if (nf > 0)
-    k_sg_fill<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, nf, s->row_ptr, s->packA, s->packB,
+    k_sg_fill<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, nf, s->row_ptr, s->pack,
                                                          (float)(1.0 / p.h), 1.f / s->edge_std[0],
                                                          1.f / s->edge_std[1], s->recv, s->send, s->efeat);
   return WBSPH_OK;
@@ -1549,7 +1596,7 @@ void backward(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, int6
     launch_bwd<MODE_NODE, 128, 64>(b, n, cs);
     if (nf > 0)
       k_sg_aggregate_bwd<<<(unsigned)div_up(nf, 4), 128, 0, cs>>>(w.fluid_list, nf, s->row_ptr, s->dagg, s->de);
-    MlpArgs a = block_args(s, 1 + 2 * l);  // edge MLP on [g, h_i, h_j]: dh += scatter of dX[16:]
+    MlpArgs a = block_args(s, 1 + 2 * l);  // edge MLP on [g, h_i, h_j[:32]]: dh += scatter of dX[16:]
     a.rows = E; a.e = s->efeat; a.h = s->hs[l]; a.recv = s->recv; a.send = s->send; a.kg = 2 * p.dim + 2;
     a.dout = s->de; a.dh = s->dh;
     launch_bwd<MODE_EDGE, EDGE_KP, 64>(a, E, cs);

@@ -171,8 +171,8 @@ def block_dims(dim, hidden=64, layers=3):
     node encoder, (edge MLP, node MLP) per layer, decoder."""
     fn, fe, fo = dim + 3, 2 * dim + 2, dim + 1
     blocks = [("enc", fn, hidden)]
-    for _ in range(layers):
-        blocks += [("edge", fe + 2 * hidden, hidden), ("node", 2 * hidden, hidden)]
+    for _ in range(layers):  # the edge MLP reads the edge inputs, h_i and the sender's first 32 features
+        blocks += [("edge", fe + hidden + 32, hidden), ("node", 2 * hidden, hidden)]
     blocks.append(("dec", hidden, fo))
     return blocks
 
@@ -181,31 +181,149 @@ def wbsph_num_params(dim, hidden=64, layers=3):
     return sum(i * hidden + hidden + hidden * o + o for _, i, o in block_dims(dim, hidden, layers))
 
 
-def rollout_error(sc, sur, nsteps, anchor_every=10, tau=0.1):
-    """Run the plain FP64 rollout and a surrogate rollout from the same state;
-    return position RMS / dx, velocity RMS error and the anchor statistics."""
-    ref = wbsph.Sim(sc.params, water_height=sc.water_height)
-    ref.set_scene(sc)
-    t0 = time.time()
-    ref.step(nsteps)
-    ref.sync()
-    t_plain = time.time() - t0
+def comparison_step(sc):
+    """A fixed time step for rollout comparisons: CFL dx / (C0 + 2 sqrt(g H)),
+    the adaptive step of the method once the dam-break front runs at its
+    shallow-water speed 2 sqrt(g H) (so it stays stable for the whole run)."""
+    p = sc.params
+    g = float(np.linalg.norm(np.asarray(p["g"][: p["dim"]])))
+    return p["cfl"] * p["dx"] / (p["c0"] + 2.0 * math.sqrt(g * sc.water_height))
+
+
+def _fixed(sc, dt):
+    s2 = sc.copy()
+    s2.params = dict(sc.params, fixed_dt=float(dt))
+    return s2
+
+
+def _pos_rms(a, b, sc):
+    f = sc.type == 0
+    return float(np.sqrt(((a[:, f] - b[:, f]) ** 2).sum(0).mean()) / sc.params["dx"])
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def rollout_error(sc, sur, nsteps, anchor_every=10, tau=0.1, dt=None, ref_x=None):
+    """Run the plain FP64 rollout (unless its final positions ref_x are given)
+    and a surrogate rollout from the same state, both with the fixed step dt
+    when given; return position RMS / dx, the anchor statistics and the wall
+    times."""
+    if dt is not None:
+        sc = _fixed(sc, dt)
+    out = {}
+    if ref_x is None:
+        ref = wbsph.Sim(sc.params, water_height=sc.water_height)
+        ref.set_scene(sc)
+        _, out["wall_plain_s"] = _timed(lambda: (ref.step(nsteps), ref.sync()))
+        ref_x = ref.get("x")
+        ref.close()
     sim = wbsph.Sim(sc.params, water_height=sc.water_height)
     sim.set_scene(sc)
-    t0 = time.time()
-    stats = sur.step(sim, nsteps, anchor_every=anchor_every, tau=tau)
-    t_sur = time.time() - t0
-    f = sc.type == 0
-    dx = sc.params["dx"]
-    ex = ref.get("x")[:, f] - sim.get("x")[:, f]
-    eu = ref.get("u")[:, f] - sim.get("u")[:, f]
-    out = {"pos_rms_over_dx": float(np.sqrt((ex ** 2).sum(0).mean()) / dx),
-           "vel_rms": float(np.sqrt((eu ** 2).sum(0).mean())),
-           "vel_scale": float(np.sqrt((ref.get("u")[:, f] ** 2).sum(0).mean())),
-           "anchors": stats, "wall_plain_s": t_plain, "wall_surrogate_s": t_sur}
-    ref.close()
+    stats, out["wall_surrogate_s"] = _timed(lambda: sur.step(sim, nsteps, anchor_every=anchor_every, tau=tau))
+    out["pos_rms_over_dx"] = _pos_rms(ref_x, sim.get("x"), sc)
+    out["anchors"] = stats
     sim.close()
     return out
+
+
+def _checkpointed(sc, advance, checkpoints):
+    """Positions of a rollout at the checkpoint step counts; advance(sim, k)
+    runs k more steps. A run that fails (non-finite state) gives None from
+    there on."""
+    sim = wbsph.Sim(sc.params, water_height=sc.water_height)
+    sim.set_scene(sc)
+    out, done, failed = [], 0, None
+    for c in checkpoints:
+        if failed is None:
+            try:
+                advance(sim, c - done)
+                done = c
+                x = sim.get("x")
+                if not np.all(np.isfinite(x)):
+                    raise wbsph.WbsphError(-6, "non-finite positions")
+                out.append(x)
+                continue
+            except wbsph.WbsphError as exc:
+                failed = f"step <= {c}: {exc}"
+        out.append(None)
+    sim.close()
+    return out, failed
+
+
+def gain_report(held, sur, norm, steps=400, anchor_every=10, seed=7, log=print, every=50):
+    """What the trained network gains over the method without it, on a
+    held-out scene, every rollout with the same fixed step and the same
+    anchoring (a plain FP64 step every anchor_every steps, starting with the
+    first; no fallback). Position RMS / dx against the plain FP64 rollout at
+    every `every` steps up to `steps`, for:
+      trained    the trained network;
+      frozen     control A: the rates of the last plain step, replayed;
+      gravity    control B: a network predicting (G, 0);
+      untrained  the initial weights;
+      coarse     the plain FP64 method alone with its step enlarged so that it
+                 spends the trained rollout's wall-clock time on the same
+                 physical time (equal wall clock; compared at the end).
+    A rollout that leaves the finite range is recorded as diverged (inf)."""
+    dim = held.params["dim"]
+    dt = comparison_step(held)
+    sc = _fixed(held, dt)
+    cps = list(range(every, steps + 1, every))
+    inf = float("inf")
+    rep = {"steps": steps, "dt": dt, "anchor_every": anchor_every, "checkpoints": cps}
+    # wall clock of the plain and the trained rollouts (after a warm-up of each)
+    for warm in range(2):
+        ref = wbsph.Sim(sc.params, water_height=sc.water_height)
+        ref.set_scene(sc)
+        _, t_plain = _timed(lambda: (ref.step(steps if warm else 2), ref.sync()))
+        ref_end = ref.get("x")
+        ref.close()
+        sim = wbsph.Sim(sc.params, water_height=sc.water_height)
+        sim.set_scene(sc)
+        sur.set_mode(wbsph.SURROGATE_NETWORK)
+        _, t_sur = _timed(lambda: sur.step(sim, steps if warm else 2, anchor_every=anchor_every, tau=inf))
+        sim.close()
+    rep["wall_plain_s"], rep["wall_trained_s"] = t_plain, t_sur
+    ref_x, _ = _checkpointed(sc, lambda s, k: (s.step(k), s.sync()), cps)
+
+    def errors(xs):
+        return [_pos_rms(r, x, sc) if x is not None else inf for r, x in zip(ref_x, xs)]
+
+    def run(net, mode=wbsph.SURROGATE_NETWORK):
+        net.set_mode(mode)
+        xs, failed = _checkpointed(sc, lambda s, k: net.step(s, k, anchor_every=anchor_every, tau=inf), cps)
+        net.set_mode(wbsph.SURROGATE_NETWORK)
+        e = errors(xs)
+        return {"pos_rms_over_dx": e[-1], "history": e, "diverged": failed}
+
+    rep["trained"] = run(sur)
+    rep["frozen"] = run(sur, wbsph.SURROGATE_FROZEN)
+    grav = wbsph.Surrogate(dim)
+    grav.set_params(gravity_only_params(dim, norm[3], norm[4], held.params["g"]))
+    grav.set_normalization(*norm)
+    rep["gravity"] = run(grav)
+    grav.close()
+    untrained = wbsph.Surrogate(dim)
+    untrained.set_params(init_params(dim, seed=seed))
+    untrained.set_normalization(*norm)
+    rep["untrained"] = run(untrained)
+    untrained.close()
+    speedup = t_plain / t_sur
+    m = max(1, int(round(steps / speedup)))
+    xc, failed = _checkpointed(_fixed(sc, steps * dt / m), lambda s, k: (s.step(k), s.sync()), [m])
+    rep["coarse"] = {"pos_rms_over_dx": _pos_rms(ref_end, xc[0], sc) if xc[0] is not None else inf,
+                     "steps": m, "dt": steps * dt / m, "cfl": sc.params["cfl"] * steps / m,
+                     "speedup_of_trained": speedup, "diverged": failed}
+    if log:
+        log("gain: " + ", ".join(f"{k} {rep[k]['pos_rms_over_dx']:.4f}" for k in
+                                 ("trained", "frozen", "gravity", "untrained", "coarse")))
+    return rep
 
 
 def save(path, sur, norm, meta):
@@ -233,8 +351,8 @@ def main(argv=None):
     ap.add_argument("--report", default=None, help="JSON report path")
     ap.add_argument("--trajectories", type=int, default=200)
     ap.add_argument("--particles", type=int, default=50_000)
-    ap.add_argument("--t-end", type=float, default=0.2)
-    ap.add_argument("--frames", type=int, default=20)
+    ap.add_argument("--t-end", type=float, default=0.4)
+    ap.add_argument("--frames", type=int, default=40)
     ap.add_argument("--iters", type=int, default=30000)
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--seed", type=int, default=7)
@@ -242,17 +360,27 @@ def main(argv=None):
     ap.add_argument("--concurrent", type=int, default=16, help="trajectories generated at once")
     ap.add_argument("--dim", type=int, default=2, choices=(2, 3))
     ap.add_argument("--dx3", type=float, default=0.0084, help="particle spacing of the 3D scenes")
+    ap.add_argument("--eval-only", default=None, help="skip training: evaluate the weights in this file")
     args = ap.parse_args(argv)
     dim = args.dim
     if dim == 2:
         scene_fn = lambda w, h: dam_scene(w, h, args.particles)  # noqa: E731
     else:
         scene_fn = lambda w, h: dam_scene_3d(w, h, args.dx3)  # noqa: E731
+    if args.eval_only:
+        sur, norm = load(args.eval_only, dim)
+        rep = gain_report(scene_fn(0.55, 0.35), sur, norm, args.eval_steps, seed=args.seed)
+        print(json.dumps(rep))
+        if args.report:
+            with open(args.report, "w") as fh:
+                json.dump(rep, fh, indent=1)
+        return
     t0 = time.time()
     data = generate(args.trajectories, args.particles, args.t_end, args.frames, args.seed,
                     concurrent=args.concurrent, scene_fn=scene_fn)
     t_gen = time.time() - t0
     norm = normalisation(data)
+    print("normalisation", [np.round(np.asarray(v), 5).tolist() for v in norm], flush=True)
     sur = wbsph.Surrogate(dim)
     theta0 = init_params(dim, seed=args.seed)
     sur.set_params(theta0)
@@ -266,18 +394,8 @@ def main(argv=None):
     # gain test on a held-out column, same anchoring for every variant
     held = scene_fn(0.55, 0.35)
     rep = {"meta": meta, "gen_s": t_gen, "train_s": t_train,
-           "loss_first": float(np.mean(hist[:50])), "loss_last": float(np.mean(hist[-50:]))}
-    inf = float("inf")
-    rep["trained"] = rollout_error(held, sur, args.eval_steps, tau=inf)
-    grav = wbsph.Surrogate(dim)
-    grav.set_params(gravity_only_params(dim, norm[3], norm[4], held.params["g"]))
-    grav.set_normalization(*norm)
-    rep["gravity_only"] = rollout_error(held, grav, args.eval_steps, tau=inf)
-    untrained = wbsph.Surrogate(dim)
-    untrained.set_params(theta0)
-    untrained.set_normalization(*norm)
-    rep["untrained"] = rollout_error(held, untrained, args.eval_steps, tau=inf)
-    rep["trained_with_fallback"] = rollout_error(held, sur, args.eval_steps, tau=0.5)
+           "loss_first": float(np.mean(hist[:50])), "loss_last": float(np.mean(hist[-50:])),
+           "gain": gain_report(held, sur, norm, args.eval_steps, seed=args.seed)}
     print(json.dumps(rep))
     if args.report:
         with open(args.report, "w") as fh:

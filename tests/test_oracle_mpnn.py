@@ -92,18 +92,19 @@ def test_isolated_receiver_has_no_messages():
 def test_parameter_count_and_layout():
     assert mpnn.num_params(2) == mpnn.init_params(2).size
     P = mpnn.unflatten(torch.zeros(mpnn.num_params(3), dtype=torch.float64), 3)
-    assert P["mp0_e"][0].shape == (8 + 128, 64) and P["dec"][2].shape == (64, 4)
+    assert P["mp0_e"][0].shape == (8 + 64 + 32, 64) and P["dec"][2].shape == (64, 4)
     assert P["enc_n"][0].shape == (6, 64) and "enc_e" not in P
-    # 2D: encoder 5*64+64+64*64+64, per layer edge (6+128)*64+64+64*64+64 and
+    # 2D: encoder 5*64+64+64*64+64, per layer edge (6+64+32)*64+64+64*64+64 and
     # node 128*64+64+64*64+64, decoder 64*64+64+64*3+3
-    assert mpnn.num_params(2) == 4544 + 3 * (12800 + 12416) + 4355
+    assert mpnn.num_params(2) == 4544 + 3 * (10752 + 12416) + 4355
 
 
 def test_message_sum_taken_apart_edge_by_edge():
-    """One layer's aggregate m_i = sum_j MLP_e([g_ij, h_i, h_j]), evaluated
-    here edge by edge with explicit loops and numpy for a one-layer network:
-    the decoder input must equal h + MLP_n([h, m]). Catches a wrong sender or
-    receiver gather, a missing sum or a residual on the messages."""
+    """One layer's aggregate m_i = sum_j MLP_e([g_ij, h_i, h_j[:32]]),
+    evaluated here edge by edge with explicit loops and numpy for a one-layer
+    network: the decoder input must equal h + MLP_n([h, m]). Catches a wrong
+    sender or receiver gather, a missing sum, a residual on the messages and
+    the wrong half of the sender's state."""
     dim = 2
     node, recv, send, edge = _graph(n=9, dim=dim, seed=11, deg=3)
     theta = mpnn.init_params(dim, seed=7, layers=1).astype(np.float64)
@@ -121,7 +122,7 @@ def test_message_sum_taken_apart_edge_by_edge():
     m = np.zeros_like(h)
     for e in range(recv.size):
         i, j = recv[e], send[e]
-        m[i] += mlp(np.concatenate([edge[e], h[i], h[j]]), P["mp0_e"])
+        m[i] += mlp(np.concatenate([edge[e], h[i], h[j][:32]]), P["mp0_e"])
     h1 = h + mlp(np.concatenate([h, m], axis=1), P["mp0_n"])
     want = mlp(h1, P["dec"])
     with torch.no_grad():
