@@ -179,6 +179,26 @@ int wbsph_eval_rates(wbsph_handle h);
  * stage). Asynchronous: errors surface at the next synchronising call. */
 int wbsph_step(wbsph_handle h, int64_t nsteps);
 
+/* One SSP-RK2 stage (Sec. 2.3) of a subdomain of a domain decomposition:
+ * neighbour build, dummy walls at the stage's time, volumes, pair pass and
+ * the stage's update, for every particle of the handle (the caller keeps
+ * the results of the particles it owns and discards its ghosts'). The caller
+ * gives the values that span subdomains: t, the time at the start of the
+ * step (stage 2 runs at t + dt); umax, the stage's maximum fluid speed over
+ * the whole domain (shifting; for stage 1 also the time step); dt > 0 the
+ * step's time step, or dt <= 0 to compute it from umax in stage 1 (the
+ * three-condition step) and to keep stage 1's in stage 2. Stage 2 must follow
+ * stage 1 with no set_particles between (wbsph_update_particles may refresh
+ * the ghosts). Asynchronous; WBSPH_E_STATE out of order. */
+int wbsph_stage(wbsph_handle h, int stage, double t, double dt, double umax);
+
+/* Overwrite x, U and phi of `count` particles identified by their index in
+ * the last wbsph_set_particles input (host arrays; x and u SoA dim*count).
+ * Between the stages of a domain decomposition this brings the ghosts to the
+ * stage-1 state their owners computed. Synchronises the stream. */
+int wbsph_update_particles(wbsph_handle h, int64_t count, const uint32_t* ids, const double* x,
+                           const double* u, const double* phi);
+
 /* Wait for the handle's stream and read the device status word. */
 int wbsph_sync(wbsph_handle h);
 

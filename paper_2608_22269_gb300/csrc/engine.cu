@@ -56,6 +56,11 @@ struct wbsph_s {
   int64_t prof_cnt[WBSPH_K_COUNT] = {0};
   double* field_tmp = nullptr;       // device: a field in the caller's order, on its way to the host
   unsigned* status_host = nullptr;   // pinned host copy of the status word
+  // distributed stages (wbsph_stage): host values copied to the device, the
+  // last stage run since set_particles, and whether a time step is in place
+  double dist_host[3] = {0.0, 0.0, 0.0};
+  int dist_stage = 0;
+  double dist_dt = 0.0;
 };
 
 static const char* kStatusNames[] = {"ok", "invalid argument", "out of device memory",
@@ -509,6 +514,8 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
   if (where == WBSPH_HOST) CK(cudaStreamSynchronize(h->stream));
   h->steps = 0;
   h->steps_since_load = 0;
+  h->dist_stage = 0;
+  h->dist_dt = 0.0;
   h->loaded = true;
   return WBSPH_OK;
 }
@@ -544,30 +551,34 @@ static int build(wbsph_s* h, bool with_base) {
   return check_launch(h, "neighbour build");
 }
 
-static int rates(wbsph_s* h, int stage2) {
+// dummy walls, then V and U_max (FP64 path) or V, U_max and the packed FP32
+// copies in one kernel (mixed path); the double-float path packs its hi/lo
+// copies after the FP64 volumes
+static int prepass(wbsph_s* h, int stage2) {
   const int64_t n = h->n;
   cudaStream_t st = h->stream;
   const bool mixed = h->cfg.precision == WBSPH_MIXED;
   const bool dfp = h->cfg.precision == WBSPH_DF64;
-  {
-    // dummy walls, then V and U_max (FP64 path) or V, U_max and the packed
-    // FP32 copies in one kernel (mixed path); the double-float path packs
-    // its hi/lo copies after the FP64 volumes
-    ProfScope ps(h, WBSPH_K_PREPASS);
-    launch_prepass(h->P, h->A, h->W, n, h->nd, stage2, st, !mixed);
-    if (mixed) {
-      int rc = launch_prepass_mixed(h->P, h->A, h->W, n, st);
-      if (rc) return fail(h, rc, "mixed path: grid too large for packed cell coordinates");
-    }
-    if (dfp) {
-      int rc = launch_pack_df(h->P, h->A, h->W, n, st);
-      if (rc) return fail(h, rc, "df64 path: grid too large for packed cell coordinates");
-    }
+  ProfScope ps(h, WBSPH_K_PREPASS);
+  launch_prepass(h->P, h->A, h->W, n, h->nd, stage2, st, !mixed);
+  if (mixed) {
+    int rc = launch_prepass_mixed(h->P, h->A, h->W, n, st);
+    if (rc) return fail(h, rc, "mixed path: grid too large for packed cell coordinates");
   }
-  if (!stage2) {
-    ProfScope ps(h, WBSPH_K_OTHER);
-    launch_time_step(h->P, h->W, st);
+  if (dfp) {
+    int rc = launch_pack_df(h->P, h->A, h->W, n, st);
+    if (rc) return fail(h, rc, "df64 path: grid too large for packed cell coordinates");
   }
+  h->launches += (n ? 1 : 0) + (h->nd ? 1 : 0) + (dfp && n ? 1 : 0);
+  return WBSPH_OK;
+}
+
+// neighbour lists and the pair pass of the configured precision and scheme
+static void pair_pass(wbsph_s* h, int stage2) {
+  const int64_t n = h->n;
+  cudaStream_t st = h->stream;
+  const bool mixed = h->cfg.precision == WBSPH_MIXED;
+  const bool dfp = h->cfg.precision == WBSPH_DF64;
   {
     ProfScope ps(h, WBSPH_K_NLIST);
     launch_nbr_list(h->P, h->A, h->W, n, h->nf, st, !mixed);
@@ -579,7 +590,18 @@ static int rates(wbsph_s* h, int stage2) {
     else if (h->P.scheme == WBSPH_SCHEME_CONVENTIONAL) launch_pair_conventional(h->P, h->A, h->W, n, h->nf, stage2, st);
     else launch_pair_fp64(h->P, h->A, h->W, n, h->nf, stage2, st);
   }
-  h->launches += (n ? 1 : 0) + (h->nd ? 1 : 0) + (stage2 ? 0 : 1) + (h->nf ? 2 : 0) + (dfp && n ? 1 : 0);
+  h->launches += h->nf ? 2 : 0;
+}
+
+static int rates(wbsph_s* h, int stage2) {
+  int rc = prepass(h, stage2);
+  if (rc) return rc;
+  if (!stage2) {
+    ProfScope ps(h, WBSPH_K_OTHER);
+    launch_time_step(h->P, h->W, h->stream);
+    h->launches += 1;
+  }
+  pair_pass(h, stage2);
   return check_launch(h, "stage rates");
 }
 
@@ -597,6 +619,102 @@ extern "C" int wbsph_eval_rates(wbsph_handle h) {
   int rc = build(h, false);
   if (rc) return rc;
   return rates(h, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Stages of a domain decomposition: one SSP-RK2 stage with the step's start
+// time, its time step and the stage's U_max (over all fluid particles of all
+// subdomains) given by the caller, and an update of selected particles (the
+// ghosts a neighbouring subdomain owns) between the stages.
+// ---------------------------------------------------------------------------
+__global__ void k_inverse_oid(const uint32_t* oid, int64_t n, uint32_t* inv) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) inv[oid[i]] = (uint32_t)i;
+}
+
+__global__ void k_scatter_state(int dim, State s, int64_t n, const uint32_t* inv, const uint32_t* ids, int64_t count,
+                                const double* xs, const double* us, const double* phis) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int64_t i = inv[ids[k]];
+  for (int d = 0; d < dim; ++d) {
+    s.x[d * n + i] = xs[d * count + k];
+    s.u[d * n + i] = us[d * count + k];
+  }
+  s.phi[i] = phis[k];
+}
+
+extern "C" int wbsph_stage(wbsph_handle h, int stage, double t, double dt, double umax) {
+  if (!h) return WBSPH_E_INVAL;
+  if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
+  if (stage != 1 && stage != 2) return fail(h, WBSPH_E_INVAL, "stage must be 1 or 2");
+  if (!std::isfinite(t) || !std::isfinite(dt) || !(umax >= 0.0) || !std::isfinite(umax))
+    return fail(h, WBSPH_E_INVAL, "bad time, time step or U_max");
+  if (stage == 2 && h->dist_stage != 1) return fail(h, WBSPH_E_STATE, "stage 2 needs a stage 1 first");
+  CK(cudaSetDevice(h->cfg.device));
+  drop_graph(h);  // builds outside a captured step
+  cudaStream_t st = h->stream;
+  const int stage2 = stage == 2;
+  h->dist_host[0] = t;
+  h->dist_host[1] = dt;
+  const double u2 = umax * umax;
+  memcpy(&h->dist_host[2], &u2, sizeof u2);
+  CK(cudaMemcpyAsync(h->W.scalars, h->dist_host, (dt > 0.0 ? 2 : 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+  int rc = build(h, stage2);
+  if (rc) return rc;
+  if ((rc = prepass(h, stage2))) return rc;
+  // the stage's U_max of the whole domain (shifting, and the time step below)
+  CK(cudaMemcpyAsync(h->W.umax_bits, &h->dist_host[2], 8, cudaMemcpyHostToDevice, st));
+  if (!stage2 && !(dt > 0.0)) {
+    ProfScope ps(h, WBSPH_K_OTHER);
+    launch_time_step(h->P, h->W, st);
+    h->launches += 1;
+  } else if (stage2 && !(dt > 0.0) && h->dist_dt <= 0.0) {
+    return fail(h, WBSPH_E_STATE, "no time step for stage 2");
+  }
+  pair_pass(h, stage2);
+  {
+    ProfScope ps(h, WBSPH_K_UPDATE);
+    launch_rk_stage(h->P, h->A, h->W, h->n, stage, st);
+    h->launches += 1;
+  }
+  h->dist_stage = stage;
+  h->dist_dt = 1.0;  // a time step is in place on the device
+  if (stage2) ++h->steps;
+  return check_launch(h, "distributed stage");
+}
+
+extern "C" int wbsph_update_particles(wbsph_handle h, int64_t count, const uint32_t* ids, const double* x,
+                                      const double* u, const double* phi) {
+  if (!h) return WBSPH_E_INVAL;
+  if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
+  if (count < 0 || count > h->n) return fail(h, WBSPH_E_INVAL, "bad particle count");
+  if (count == 0) return WBSPH_OK;
+  if (!ids || !x || !u || !phi) return fail(h, WBSPH_E_INVAL, "null array");
+  for (int64_t k = 0; k < count; ++k)
+    if ((int64_t)ids[k] >= h->n) return fail(h, WBSPH_E_INVAL, "particle id %lld out of range", (long long)ids[k]);
+  CK(cudaSetDevice(h->cfg.device));
+  cudaStream_t st = h->stream;
+  const int d = h->cfg.dim;
+  const int64_t n = h->n;
+  uint32_t *inv = nullptr, *dids = nullptr;
+  double* vals = nullptr;
+  CK(cudaMallocAsync((void**)&inv, (size_t)n * 4, st));
+  CK(cudaMallocAsync((void**)&dids, (size_t)count * 4, st));
+  CK(cudaMallocAsync((void**)&vals, (size_t)count * (2 * d + 1) * sizeof(double), st));
+  CK(cudaMemcpyAsync(dids, ids, (size_t)count * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(vals, x, (size_t)count * d * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(vals + (size_t)count * d, u, (size_t)count * d * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(vals + (size_t)count * 2 * d, phi, (size_t)count * sizeof(double), cudaMemcpyHostToDevice, st));
+  k_inverse_oid<<<(unsigned)div_up(n, 256), 256, 0, st>>>(h->A.oid, n, inv);
+  k_scatter_state<<<(unsigned)div_up(count, 256), 256, 0, st>>>(d, h->A, n, inv, dids, count, vals,
+                                                               vals + (size_t)count * d, vals + (size_t)count * 2 * d);
+  h->launches += 2;
+  CK(cudaStreamSynchronize(st));  // the host arrays may be reused when this returns
+  cudaFreeAsync(inv, st);
+  cudaFreeAsync(dids, st);
+  cudaFreeAsync(vals, st);
+  return check_launch(h, "update_particles");
 }
 
 // One SSP-RK2 step as a launch sequence (no host synchronisation).

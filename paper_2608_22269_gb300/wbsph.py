@@ -31,7 +31,7 @@ SYMBOLS = ["wbsph_config_default", "wbsph_create", "wbsph_set_particles", "wbsph
            "wbsph_eval_rates", "wbsph_step", "wbsph_sync", "wbsph_get_fields",
            "wbsph_get_cell_keys", "wbsph_get_neighbors", "wbsph_get_stats", "wbsph_set_profiling",
            "wbsph_get_profile", "wbsph_destroy", "wbsph_last_error", "wbsph_status_string",
-           "wbsph_sort_cells_noalloc", "wbsph_test_bounded_wait"]
+           "wbsph_sort_cells_noalloc", "wbsph_test_bounded_wait", "wbsph_stage", "wbsph_update_particles"]
 NOALLOC_MAX_N = 524288
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -104,6 +104,8 @@ def load(build_if_missing: bool = False):
         "wbsph_status_string": (C.c_char_p, [I]),
         "wbsph_sort_cells_noalloc": (I, [P, P, i64, P, P]),
         "wbsph_test_bounded_wait": (I, [P, i64]),
+        "wbsph_stage": (I, [P, I, C.c_double, C.c_double, C.c_double]),
+        "wbsph_update_particles": (I, [P, i64, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -234,6 +236,19 @@ class Sim:
 
     def sync(self):
         self._check(self.lib.wbsph_sync(self.h))
+
+    def stage(self, stage, t, dt, umax):
+        """One SSP-RK2 stage of a subdomain (wbsph_stage): t the step's start
+        time, dt the time step (<= 0: from umax in stage 1, kept in stage 2),
+        umax the stage's maximum fluid speed over the whole domain."""
+        self._check(self.lib.wbsph_stage(self.h, int(stage), float(t), float(dt), float(umax)))
+
+    def update_particles(self, ids, x, u, phi):
+        """Overwrite x, U, phi of the particles with these input indices
+        (wbsph_update_particles; host arrays, x and u of shape (dim, count))."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        x, u, phi = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, u, phi))
+        self._check(self.lib.wbsph_update_particles(self.h, ids.size, _ptr(ids), _ptr(x), _ptr(u), _ptr(phi)))
 
     def get(self, field: str, out=None):
         """Field in the caller's original order: numpy (host) unless ``out``
