@@ -328,45 +328,48 @@ def rates_diff(a, b, scene):
             "excluded_tic_boundary": int((~keep).sum())}
 
 
-def surrogate_flops_per_stage(dim, n, nf, E, hidden=64, layers=3):
+def surrogate_flops_per_stage(dim, n, nf, E, hidden=64, layers=3, send=32):
     """Dense-contraction FLOPs of one surrogate stage (2 per multiply-add), as
-    the kernels run it: node and edge encoders (inputs padded to 16), per
-    layer the node projections (64 -> 128), the edge MLP on the 64-wide edge
-    state (64 -> 64 -> 64) and the node MLP (128 -> 64 -> 64), and the decoder
-    on fluid rows (64 -> 64 -> 16 padded)."""
+    the kernels run them: the node encoder (inputs padded to 16), per layer
+    the per-edge first layer of the message MLP on the edge inputs (K = 16)
+    and the sender's first 32 features (K = 32), and per node the receiver
+    term (64 x 64), the message MLP's second layer on the sums (64 x 64) and
+    the node MLP (128 -> 64 -> 64), and the decoder on fluid rows (64 -> 64
+    -> 16 padded)."""
     H = hidden
-    enc = 2 * (n + E) * (16 * H + H * H)
-    per_layer = 2 * (n * H * 2 * H + E * (H * H + H * H) + n * (2 * H * H + H * H))
+    enc = 2 * n * (16 * H + H * H)
+    per_layer = 2 * (E * (16 + send) * H + nf * (H * H + H * H) + n * (2 * H * H + H * H))
     dec = 2 * nf * (H * H + H * 16)
     return enc + layers * per_layer + dec
 
 
 def surrogate_bytes_per_stage(n, nf, E, hidden=64, layers=3):
-    """Algorithmic HBM bytes of one surrogate stage (BF16 activations): the
-    graph fill (list entry read, receiver/sender/features written), node and
-    edge encoders (8 features in, a 64-wide row out), per layer the node
-    projections (h in, 128-wide row out), the edge MLP (edge state in and
-    out; the gathered projections are L2 traffic), the aggregation (edge
-    states in, a row out) and the node MLP (h and aggregate in, h out), and
-    the decoder on fluid rows."""
+    """Algorithmic HBM bytes of one surrogate stage: the neighbour lists
+    (written once, 4 B per entry, read by every layer), the node inputs and
+    packs (state in, 16 + 32 B out per node), per layer the node states (h
+    in, h' out: 2 x 128 B per node; the per-edge gathers of sender rows and
+    packs are reuse served by L2, not additional algorithmic bytes) and the
+    decoder (h in, outputs out, fluid rows)."""
     row = 2 * hidden
-    fill = E * (4 + 8 + 16)
-    enc = (n + E) * (16 + row)
-    per_layer = n * (row + 2 * row) + E * 2 * row + (E * row + n * row) + n * 3 * row
+    lists = E * 4 * (1 + layers)
+    inputs = n * (8 * 8 + 16 + 32)
+    per_layer = n * 2 * row
     dec = nf * (row + 16)
-    return fill + enc + layers * per_layer + dec
+    return lists + inputs + layers * per_layer + dec
 
 
-def surrogate_path(args, local, dim=2):
-    """Surrogate rollouts with a plain FP64 re-anchoring step every 10 steps,
-    timed against the plain FP64 rollout of the same scene; error = position
-    RMS / dx against that plain rollout. 2D: the configs' inference case (dam
-    break, column 0.6 x 0.3 m, dx = 0.00085 m, 249,218 fluid particles). 3D:
-    the 3D dam break of the headline (1,208,207 fluid particles) with the
-    network trained on its half-size replicas. The timed rollout keeps the
-    surrogate between anchors (tau = inf); the fallback rule (tau = 0.1: a
-    window whose anchor error exceeds tau runs plain) is reported from a
-    second, untimed rollout."""
+def surrogate_path(args, local, dim=2, scene=None):
+    """Surrogate rollouts with a plain FP64 re-anchoring step every 10 steps
+    (the first step of the rollout is one), timed against the plain FP64
+    rollout of the same scene; error = position RMS / dx against that plain
+    rollout. 2D: the configs' inference case (dam break, column 0.6 x 0.3 m,
+    dx = 0.00085 m, 249,218 fluid particles). 3D: the 3D dam break of the
+    headline (1,208,207 fluid particles) with the network trained on its
+    half-size replicas, or (scene = "slosh3d") the 17.58M-fluid sloshing tank
+    with the same network. The timed rollout keeps the surrogate between
+    anchors (tau = inf); the fallback rule (tau = 0.1: a window whose anchor
+    error exceeds tau runs plain) is reported from a second, untimed
+    rollout."""
     import numpy as np
     import torch
 
@@ -381,11 +384,16 @@ def surrogate_path(args, local, dim=2):
         sc = scenes.dam_break_2d(dx=0.00085, width=2.0, wall=0.6, column=(0.6, 0.3))
         desc = ("2D dam break, column 0.6x0.3 m in a 2.0 m basin, dx=0.00085 m "
                 f"({sc.n_fluid:,} fluid), FP64 anchor every 10 steps, no fallback (tau = inf)")
+    elif scene == "slosh3d":
+        sc = scenes.sloshing_3d()
+        desc = ("3D sloshing tank 4.0x2.0x2.0 m, depth 1.0 m, dx=0.00769 m "
+                f"({sc.n_fluid:,} fluid), 3D network, FP64 anchor every 10 steps, no fallback (tau = inf)")
     else:
         sc = scenes.dam_break_3d(dx=0.0084)
         desc = ("3D dam break, box 3.2x1.0x1.0 m, column 1.2x1.0x0.6 m, dx=0.0084 m "
                 f"({sc.n_fluid:,} fluid), FP64 anchor every 10 steps, no fallback (tau = inf)")
-    K = max(args.steps, 10)
+    K = max(args.steps, 10) if scene != "slosh3d" else 10
+    warm = args.warmup if scene != "slosh3d" else 3
     inf = float("inf")
 
     def timed(fn):
@@ -397,26 +405,33 @@ def surrogate_path(args, local, dim=2):
 
     plain = wbsph.Sim(sc.params, water_height=sc.water_height, device=local)
     plain.set_scene(sc)
-    plain.step(args.warmup)
+    plain.step(warm)
     plain.sync()
     t_plain = timed(lambda: (plain.step(K), plain.sync()))
     sim = wbsph.Sim(sc.params, water_height=sc.water_height, device=local)
     sim.set_scene(sc)
-    sur.step(sim, args.warmup, anchor_every=10, tau=inf)
-    sim.set_profiling(True)
-    sim.profile(reset=True)
+    sur.step(sim, warm, anchor_every=10, tau=inf)
     stats = {}
     t_sur = timed(lambda: stats.update(sur.step(sim, K, anchor_every=10, tau=inf)))
-    prof = sim.profile(reset=True)
     f = sc.type == 0
     err = float(np.sqrt(((plain.get("x")[:, f] - sim.get("x")[:, f]) ** 2).sum(0).mean()) / sc.params["dx"])
-    # one surrogate stage alone: graph build and network, CUDA events in the library
+    plain.close()
+    # one surrogate stage alone (CUDA events in the library) and one plain
+    # stage of the same state; edges = the pairs of that plain stage (the
+    # surrogate's graph is the same exact neighbour lists)
     st = sim.stats()
     n, nf = st["n"], st["n_fluid"]
-    E = sur.edges(sim)
+    sur.predict(sim)
+    sim.set_profiling(True)
     sim.profile(reset=True)
     sur.predict(sim)
     stage_ms = sim.profile(reset=True)["pair"][0]
+    p0 = sim.stats()["pairs"]
+    sim.eval_rates()
+    prof = sim.profile(reset=True)
+    plain_stage_ms = prof["pair"][0] + prof["nlist"][0]
+    sim.set_profiling(False)
+    E = int(sim.stats()["pairs"] - p0)
     flops = surrogate_flops_per_stage(dim, n, nf, E)
     peak = 1925.2
     try:
@@ -431,28 +446,31 @@ def surrogate_path(args, local, dim=2):
     except (OSError, ValueError, KeyError):
         pass
     gbs = sbytes / (stage_ms / 1e3) / 1e9
+    sim.close()
     fb_sim = wbsph.Sim(sc.params, water_height=sc.water_height, device=local)
     fb_sim.set_scene(sc)
     fb = sur.step(fb_sim, K, anchor_every=10, tau=0.1)
+    fb_sim.close()
     out = {"workload": desc,
            "value": round(sc.n_fluid * K / t_sur, 1), "unit": UNIT,
            "plain_fp64_same_scene": round(sc.n_fluid * K / t_plain, 1),
            "ms_per_step": round(t_sur * 1e3 / K, 3), "steps": K,
            "anchors": stats, "error": {"pos_rms_over_dx_vs_plain": err,
                                         "max_anchor_rel_l2_dudt": stats.get("max_rel_err")},
-           "stage": {"ms": round(stage_ms, 3), "edges": E, "nodes": n,
-                     "network_gflop": round(flops / 1e9, 2)},
-           "roofline": {"bound": "tensor", "kernel": "surrogate stage (graph + all MLP kernels)",
+           "stage": {"ms": round(stage_ms, 3), "plain_fp64_stage_ms": round(plain_stage_ms, 3), "edges": E,
+                     "nodes": n, "network_gflop": round(flops / 1e9, 2)},
+           "roofline": {"bound": "tensor", "kernel": "surrogate stage (lists, inputs and all network kernels)",
                         "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                         "frac": round(achieved / peak, 4), "traffic": None,
                         "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"},
            "hbm": {"algorithmic_bytes_per_stage": int(sbytes), "achieved_gbs": round(gbs, 1),
                    "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4),
-                   "note": "the stage is bound by data movement: ~45 FLOP/B against a ~290 FLOP/B ridge"},
+                   "bytes_per_fluid_particle": round(sbytes / max(nf, 1), 1),
+                   "note": "nothing per edge reaches memory; the stage is bound by the per-edge gathers of "
+                           "sender rows (64 B) and packs (32 B) served by L2"},
            "with_fallback_tau_0.1": fb,
            "weights": f"paper_2608_22269_gb300/data/{name} (trained on the GPU by this library)"}
-    for o in (plain, sim, fb_sim, sur):
-        o.close()
+    sur.close()
     return out
 
 
@@ -546,12 +564,15 @@ def summary_of(line) -> dict:
                     p, None if e is None else {"dudt": e["dudt"], "dphidt": e["dphidt"]})
         if "error" in sp:
             out[key] = {"error": sp["error"][:160]}
-    for key in ("surrogate", "surrogate_3d"):
+    for key in ("surrogate", "surrogate_3d", "surrogate_slosh3d"):
         p = paths.get(key)
         if p is not None:
             out[key] = digest(p, (p.get("error") or {}) if isinstance(p, dict) else None)
             if isinstance(p, dict) and "plain_fp64_same_scene" in p:
                 out[key]["plain_fp64_same_scene"] = p["plain_fp64_same_scene"]
+                stg = p.get("stage", {})
+                out[key]["stage_ms"] = stg.get("ms")
+                out[key]["plain_stage_ms"] = stg.get("plain_fp64_stage_ms")
     if "cpu_baseline" in line:
         out["cpu_baseline_oracle"] = line["cpu_baseline"]["value"]
     return out
@@ -649,9 +670,10 @@ def run_ours(args):
                 sp = {"error": f"{type(exc).__name__}: {exc}"}
             paths["slosh3d"] = sp
         if rank == 0:
-            for key, sdim in (("surrogate", 2), ("surrogate_3d", 3)):
+            for key, sdim, ssc in (("surrogate", 2, None), ("surrogate_3d", 3, None),
+                                   ("surrogate_slosh3d", 3, "slosh3d")):
                 try:
-                    paths[key] = surrogate_path(args, local, sdim)
+                    paths[key] = surrogate_path(args, local, sdim, ssc)
                 except Exception as exc:  # the plain paths above are the headline; report, do not abort
                     paths[key] = {"error": f"{type(exc).__name__}: {exc}"}
         line["paths"] = paths

@@ -21,7 +21,8 @@ enum : unsigned {
   kStatSingular = 2u,   // singular renormalisation matrix on the corrected branch
   kStatNaN = 4u,        // non-finite rate or state
   kStatOverflow = 8u,   // neighbour list chunk bookkeeping overflow
-  kStatTimeout = 16u    // bounded device wait gave up
+  kStatTimeout = 16u,   // bounded device wait gave up
+  kStatSkin = 32u       // a particle may move further in a stage than the reused lists allow
 };
 
 // Numerical parameters, derived once on the host from the configuration and
@@ -49,7 +50,17 @@ struct Params {
   float nearest_band_r2;          // FP32 band around the FP32 minimum that holds the exact nearest
   float inner_r2;                 // FP32 r^2 at or below it (and > 0): an exact neighbour, no FP64 test
   double domain_min[3], domain_max[3];
-  double R;                       // cell size 2h
+  double R;                       // cell size: 2h, plus skin_max on the mixed path
+  // Mixed path: the candidate lists of stage 1 are kept for stage 2. They
+  // hold every pair within 2h + delta, delta = 3 dt U* (U* = max(U_max,
+  // |body_u|)), twice the largest move of a particle in stage 1 (U0 plus a
+  // shift clamped to U_max/2, times dt), so that every pair within 2h at the
+  // stage-2 positions is listed; cells are widened by skin_max >= delta so
+  // that the listed pairs and the wall update's nearest fluid particle stay
+  // in adjacent cells without a new sort.
+  int skin;                       // 1: lists kept for stage 2 (mixed path)
+  double skin_max;                // largest delta the cells allow
+  double skin_e;                  // FP32 rounding margin of a list distance
   // cell keys: FP32 estimate of (x - min)/R, trusted where its fractional
   // part is more than key_margin from a cell boundary (exact FP64 otherwise)
   float key_min_f[3];             // domain_min rounded to FP32
@@ -109,7 +120,7 @@ struct Work {
   uint32_t* block_cnt;   // scratch for scans
   uint32_t* hist;        // radix histograms
   unsigned long long* umax_bits;  // [0]: max |U|^2 over fluid (bits of a non-negative double)
-  double* scalars;   // [0] t, [1] dt, [2] U_max of the current stage
+  double* scalars;   // [0] t, [1] dt, [2] unused, [3] FP32 candidate threshold of the kept lists
   unsigned* status;  // device status word
   unsigned long long* pairs;  // [0]: neighbour pairs summed by pair passes (units of work)
   uint32_t* nbr;     // kmax * n_fluid: candidate lists, k-major (nbr[k * nf + gi])
@@ -144,7 +155,9 @@ void launch_fill_neighbors(const Params& p, const State& s, const Work& w, int64
 // Dummy walls, then (volumes = true) V = m / rho and U_max of the stage.
 void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int64_t nd,
                     int stage2, cudaStream_t st, bool volumes = true);
-void launch_time_step(const Params& p, const Work& w, cudaStream_t st);
+// keep_lists: also the radius of the mixed path's kept lists (and the check
+// that the widened cells hold it)
+void launch_time_step(const Params& p, const Work& w, cudaStream_t st, bool keep_lists = false);
 // Mixed path: V, U_max and the packed FP32 copies; WBSPH_E_INVAL when the
 // grid exceeds the packed cell word (2048 x 2048 x 1024 cells).
 int launch_prepass_mixed(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
@@ -153,8 +166,10 @@ int launch_pack_df(const Params& p, const State& s, const Work& w, int64_t n, cu
 
 // ---- lists.cu ----
 int pair_list_kmax(int dim);
+// exact: FP64 neighbour sets (FP64 path, surrogate graph); skin: the mixed
+// path's lists of stage 1, kept for stage 2 (radius 2h + delta)
 void launch_nbr_list(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid, cudaStream_t st,
-                     bool exact);
+                     bool exact, bool skin = false);
 
 // ---- pair passes: pair_fp64.cu, pair_mixed.cu, pair_df64.cu, pair_conventional.cu ----
 void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n, int64_t n_fluid,
@@ -172,5 +187,10 @@ void launch_rk_stage(const Params& p, const State& s, const Work& w, int64_t n, 
                      cudaStream_t st);
 void launch_field(const Params& p, const State& s, const Work& w, int64_t n, int field,
                   double* out, cudaStream_t st);
+// FP32 position copies (xf, and xff of the fluid particles) brought to the
+// current positions of the fluid and body particles, in the order of the
+// last neighbour build (mixed path, stage 2 without a new build)
+void launch_refresh_xf(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int64_t nd,
+                       cudaStream_t st);
 
 }  // namespace wbsph

@@ -44,8 +44,17 @@ struct wbsph_s {
   bool loaded = false;
   bool alloc_failed = false;
   bool use_graphs = true;            // replay captured steps (caller stream only)
-  cudaGraphExec_t graph_exec = nullptr;
-  int64_t graph_launches = 0;        // kernels in the captured step
+  // Captured steps, each with the buffer pointers it starts from and leaves
+  // behind. A step of the FP64 and double-float paths sorts twice and
+  // leaves every pointer where it found it, so one graph serves every step;
+  // a mixed-path step sorts once, so its pointers alternate between two
+  // states and a graph is kept for each.
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    State a0{}, b0{}, a1{}, b1{};
+    Work w0{}, w1{};
+    int64_t launches = 0;              // kernels in the captured step
+  } graphs[2];
   int64_t steps_since_load = 0;
   bool capturing = false;
   int64_t n_alloc = -1;  // particle count the buffers were sized for
@@ -187,6 +196,16 @@ static int derive_params(wbsph_s* h) {
   p.two_h = 2.0 * p.h;
   p.four_h2 = p.two_h * p.two_h;
   p.R = p.two_h;
+  // Mixed path: lists kept for stage 2 (see Params::skin). The cells are
+  // widened by the largest skin that a flow at Mach 0.3 needs at this CFL
+  // number: a particle moves at most 1.5 dt U_max in stage 1 and
+  // dt <= CFL dx / (C0 + U_max).
+  p.skin = c.precision == WBSPH_MIXED ? 1 : 0;
+  if (p.skin) {
+    const double mach = 0.3;
+    p.skin_max = 3.0 * c.cfl * c.dx * mach / (1.0 + mach);
+    p.R = p.two_h + p.skin_max;
+  }
   p.alpha = c.dim == 2 ? 7.0 / (4.0 * kPi * p.h * p.h) : 21.0 / (16.0 * kPi * p.h * p.h * p.h);
   p.neg_dwdr_over_r_coef = 5.0 * p.alpha / (p.h * p.h);
   p.inv_two_h = 1.0 / p.two_h;
@@ -270,6 +289,8 @@ static int derive_params(wbsph_s* h) {
   const double u24 = std::ldexp(1.0, -24);
   double e = 2.0 * std::sqrt((double)c.dim) * (2.0 * X + 2.0 * p.two_h) * u24;
   double thr = (p.two_h + e) * (p.two_h + e) * (1.0 + 16.0 * u24);
+  // the same margin for distances up to 2h + skin_max (kept lists)
+  p.skin_e = 2.0 * std::sqrt((double)c.dim) * (2.0 * X + 2.0 * (p.two_h + p.skin_max)) * u24;
   float tf = (float)thr;
   if ((double)tf < thr) tf = std::nextafter(tf, INFINITY);
   p.prefilter_r2 = tf;
@@ -523,9 +544,6 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
 // Neighbour build for the current positions (stage 2 also carries y^n).
 static int build(wbsph_s* h, bool with_base) {
   const int64_t n = h->n;
-  // an odd number of builds outside a captured step would desynchronise
-  // the buffer pointers baked into a captured graph
-  if (h->graph_exec && !h->capturing) drop_graph(h);
   if (n == 0) return WBSPH_OK;
   cudaStream_t st = h->stream;
   {
@@ -573,15 +591,20 @@ static int prepass(wbsph_s* h, int stage2) {
   return WBSPH_OK;
 }
 
-// neighbour lists and the pair pass of the configured precision and scheme
-static void pair_pass(wbsph_s* h, int stage2) {
+// neighbour lists and the pair pass of the configured precision and scheme;
+// lists: LISTS_STAGE builds them for this stage, LISTS_KEEP builds the
+// mixed path's kept lists (radius 2h + delta), LISTS_REUSE uses those of
+// stage 1
+enum { LISTS_STAGE = 0, LISTS_KEEP = 1, LISTS_REUSE = 2 };
+static void pair_pass(wbsph_s* h, int stage2, int lists = LISTS_STAGE) {
   const int64_t n = h->n;
   cudaStream_t st = h->stream;
   const bool mixed = h->cfg.precision == WBSPH_MIXED;
   const bool dfp = h->cfg.precision == WBSPH_DF64;
-  {
+  if (lists != LISTS_REUSE) {
     ProfScope ps(h, WBSPH_K_NLIST);
-    launch_nbr_list(h->P, h->A, h->W, n, h->nf, st, !mixed);
+    launch_nbr_list(h->P, h->A, h->W, n, h->nf, st, !mixed, lists == LISTS_KEEP);
+    h->launches += h->nf ? 1 : 0;
   }
   {
     ProfScope ps(h, WBSPH_K_PAIR);
@@ -590,7 +613,7 @@ static void pair_pass(wbsph_s* h, int stage2) {
     else if (h->P.scheme == WBSPH_SCHEME_CONVENTIONAL) launch_pair_conventional(h->P, h->A, h->W, n, h->nf, stage2, st);
     else launch_pair_fp64(h->P, h->A, h->W, n, h->nf, stage2, st);
   }
-  h->launches += h->nf ? 2 : 0;
+  h->launches += h->nf ? 1 : 0;
 }
 
 static int rates(wbsph_s* h, int stage2) {
@@ -721,6 +744,31 @@ extern "C" int wbsph_update_particles(wbsph_handle h, int64_t count, const uint3
 static int enqueue_step(wbsph_s* h) {
   int rc = build(h, false);
   if (rc) return rc;
+  if (h->P.skin) {
+    // mixed path: one build per step; stage 2 keeps the sorted order, the
+    // cells and the lists of stage 1 (2h + delta), with the FP32 position
+    // copies brought to the stage-1 positions for the wall update's scan
+    if ((rc = prepass(h, 0))) return rc;
+    {
+      ProfScope ps(h, WBSPH_K_OTHER);
+      launch_time_step(h->P, h->W, h->stream, true);
+      h->launches += 1;
+    }
+    pair_pass(h, 0, LISTS_KEEP);
+    {
+      ProfScope ps(h, WBSPH_K_UPDATE);
+      launch_rk_stage(h->P, h->A, h->W, h->n, 1, h->stream);
+      launch_refresh_xf(h->P, h->A, h->W, h->n, h->nf, h->nd, h->stream);
+    }
+    if ((rc = prepass(h, 1))) return rc;
+    pair_pass(h, 1, LISTS_REUSE);
+    {
+      ProfScope ps(h, WBSPH_K_UPDATE);
+      launch_rk_stage(h->P, h->A, h->W, h->n, 2, h->stream);
+    }
+    h->launches += 3;
+    return check_launch(h, "step");
+  }
   rc = rates(h, 0);
   if (rc) return rc;
   {
@@ -740,43 +788,57 @@ static int enqueue_step(wbsph_s* h) {
 }
 
 static void drop_graph(wbsph_s* h) {
-  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
-  h->graph_exec = nullptr;
-  h->graph_launches = 0;
+  for (auto& g : h->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = wbsph_s::StepGraph{};
+  }
 }
 
-// A step's launch sequence is periodic in the buffer pointers: every swap
-// (state buffers per stage, sort buffers per pass) happens an even number of
-// times per step, so one captured step replays correctly any number of times.
-static int capture_step(wbsph_s* h) {
-  drop_graph(h);
+// the captured step that starts from the current buffer pointers, if any
+static wbsph_s::StepGraph* find_graph(wbsph_s* h) {
+  for (auto& g : h->graphs)
+    if (g.exec && !memcmp(&g.a0, &h->A, sizeof(State)) && !memcmp(&g.b0, &h->B, sizeof(State)) &&
+        !memcmp(&g.w0, &h->W, sizeof(Work)))
+      return &g;
+  return nullptr;
+}
+
+// Capture one step from the current buffer pointers into a free graph slot
+// (both slots in use: both dropped first). The enqueue leaves the host's
+// pointers where the step leaves them; the graph is launched next.
+static int capture_step(wbsph_s* h, wbsph_s::StepGraph** out) {
+  wbsph_s::StepGraph* g = !h->graphs[0].exec ? &h->graphs[0] : !h->graphs[1].exec ? &h->graphs[1] : nullptr;
+  if (!g) {
+    drop_graph(h);
+    g = &h->graphs[0];
+  }
   int64_t l0 = h->launches;
-  const State a0 = h->A;
-  const Work w0 = h->W;
-  cudaGraph_t g = nullptr;
+  g->a0 = h->A; g->b0 = h->B; g->w0 = h->W;
+  cudaGraph_t cg = nullptr;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   h->capturing = true;
   int rc = enqueue_step(h);
   h->capturing = false;
-  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &cg);
   if (rc || e != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
+    if (cg) cudaGraphDestroy(cg);
     cudaGetLastError();
+    h->A = g->a0; h->B = g->b0; h->W = g->w0;  // nothing ran
+    *g = wbsph_s::StepGraph{};
     return rc ? rc : fail(h, WBSPH_E_CUDA, "step capture: %s", cudaGetErrorString(e));
   }
-  if (h->A.x != a0.x || h->W.key != w0.key || h->W.perm != w0.perm) {
-    cudaGraphDestroy(g);
-    return fail(h, WBSPH_E_STATE, "step is not pointer-periodic; graph replay disabled");
-  }
-  e = cudaGraphInstantiate(&h->graph_exec, g, 0);
-  cudaGraphDestroy(g);
+  e = cudaGraphInstantiate(&g->exec, cg, 0);
+  cudaGraphDestroy(cg);
   if (e != cudaSuccess) {
-    h->graph_exec = nullptr;
     cudaGetLastError();
+    h->A = g->a0; h->B = g->b0; h->W = g->w0;
+    *g = wbsph_s::StepGraph{};
     return fail(h, WBSPH_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
   }
-  h->graph_launches = h->launches - l0;
+  g->a1 = h->A; g->b1 = h->B; g->w1 = h->W;
+  g->launches = h->launches - l0;
   h->launches = l0;
+  *out = g;
   return WBSPH_OK;
 }
 
@@ -793,14 +855,16 @@ extern "C" int wbsph_step(wbsph_handle h, int64_t nsteps) {
   bool graphs = h->use_graphs && h->stream != nullptr && !h->prof && h->n > 0;
   for (int64_t s = 0; s < nsteps; ++s) {
     int rc;
-    if (graphs && (h->graph_exec || h->steps_since_load > 0)) {
-      if (!h->graph_exec && capture_step(h) != WBSPH_OK) {
+    wbsph_s::StepGraph* g = graphs ? find_graph(h) : nullptr;
+    if (graphs && (g || h->steps_since_load > 0)) {
+      if (!g && capture_step(h, &g) != WBSPH_OK) {
         h->use_graphs = false;
         graphs = false;
         rc = enqueue_step(h);
       } else {
-        CK(cudaGraphLaunch(h->graph_exec, h->stream));
-        h->launches += h->graph_launches;
+        CK(cudaGraphLaunch(g->exec, h->stream));
+        h->A = g->a1; h->B = g->b1; h->W = g->w1;
+        h->launches += g->launches;
         rc = check_launch(h, "graph step");
       }
     } else {
@@ -825,6 +889,12 @@ static int read_status(wbsph_s* h) {
 
 static int decode_status(wbsph_s* h, unsigned s) {
   if (!s) return WBSPH_OK;
+  // the kept lists of the mixed path no longer covered every pair: what
+  // followed is not the method, whatever else went wrong after it
+  if (s & kStatSkin)
+    return fail(h, WBSPH_E_CAPACITY,
+                "a particle can move more than the neighbour-list skin in one stage (mixed path: flow above "
+                "Mach 0.3 at this CFL number, or a fixed time step that is too long)");
   // a non-finite value also sends positions out of the domain: report it first
   if (s & kStatNaN) return fail(h, WBSPH_E_NAN, "non-finite rate or state value");
   if (s & kStatSingular) return fail(h, WBSPH_E_SINGULAR, "singular renormalisation matrix (TIC off)");

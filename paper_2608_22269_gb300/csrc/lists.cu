@@ -13,7 +13,9 @@ namespace wbsph {
 //    candidates inside the inner bound; the rest of the candidates that pass
 //    the conservative prefilter (a thin band near 2h) take the exact FP64 test.
 //  otherwise (mixed path): every candidate that passes the FP32 prefilter;
-//    the mixed pair pass applies its own FP32 test.
+//    the mixed pair pass applies its own FP32 test. With `skin` the
+//    prefilter radius is 2h + delta (device scalar of the time step), and
+//    the same lists serve both stages of the step.
 // Lists are staged per warp in shared memory so the global stores are
 // coalesced rows.
 // ---------------------------------------------------------------------------
@@ -21,7 +23,7 @@ constexpr int LIST_THREADS = 64;
 
 template <int DIM, bool EXACT>
 __global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, State s, Work w, int64_t n, int64_t nf,
-                                                         int kmax, int ks) {
+                                                         int kmax, int ks, int skin) {
   extern __shared__ float4 smem_f4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4* stage = smem_f4 + warp * 32;
@@ -35,7 +37,9 @@ __global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, State s, Wo
   const float4 xs = active ? w.xf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   int cnt = 0, nband = 0;
   constexpr uint32_t kBand = 0x80000000u;  // entry still needs the exact test
-  warp_scan_candidates<DIM>(p, all_particles(w), active, i, key, xs, stage, sidx, [&](uint32_t j, float r2f, float) {
+  // kept lists (mixed path, stage 1): every candidate within 2h + delta
+  const float pre_r2 = (!EXACT && skin) ? __double2float_ru(w.scalars[3]) : p.prefilter_r2;
+  warp_scan_candidates_r<DIM>(p, all_particles(w), active, i, key, xs, pre_r2, stage, sidx, [&](uint32_t j, float r2f, float) {
     // neighbour test of Algorithm 1: FP32 decides inside the inner bound;
     // candidates in the rounding band near 2h (and at r_f = 0) are flagged
     // for the exact FP64 test below
@@ -91,7 +95,7 @@ int pair_list_kmax(int dim) { return dim == 3 ? 128 : 48; }
 static int pair_list_stage(int dim) { return dim == 3 ? WBSPH_LIST_STAGE_3D : 48; }
 
 void launch_nbr_list(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, cudaStream_t st,
-                     bool exact) {
+                     bool exact, bool skin) {
   if (nf == 0) return;
   int kmax = pair_list_kmax(p.dim);
   int ks = pair_list_stage(p.dim);
@@ -108,11 +112,11 @@ void launch_nbr_list(const Params& p, const State& s, const Work& w, int64_t n, 
   }
   unsigned blocks = (unsigned)div_up(nf, LIST_THREADS);
   if (p.dim == 3) {
-    if (exact) k_nbr_list<3, true><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
-    else k_nbr_list<3, false><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
+    if (exact) k_nbr_list<3, true><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks, 0);
+    else k_nbr_list<3, false><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks, skin ? 1 : 0);
   } else {
-    if (exact) k_nbr_list<2, true><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
-    else k_nbr_list<2, false><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks);
+    if (exact) k_nbr_list<2, true><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks, 0);
+    else k_nbr_list<2, false><<<blocks, LIST_THREADS, sm, st>>>(p, s, w, n, nf, kmax, ks, skin ? 1 : 0);
   }
 }
 

@@ -1494,9 +1494,6 @@ MlpArgs block_args(wbsph_surrogate s, int bi) {
   return a;
 }
 
-// Messages of one layer (k_message_tc): persistent CTAs, one per SM (226 KB
-// of shared memory and 256 TMEM columns each, 512 threads), two receiver
-// groups per CTA. Writes m_i of the fluid particles into m_out.
 // One fused message-passing layer (k_message_tc): persistent CTAs, one per
 // SM (186 KB of shared memory and 256 TMEM columns each), two receiver
 // groups per CTA.

@@ -150,7 +150,7 @@ void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, i
 }
 
 // Time step (Sec. 2.3): CFL * min(dx/(C0 + U_max), dx^2/(2 nu), sqrt(2 dx/|G|)).
-__global__ void k_time_step(Params p, Work w) {
+__global__ void k_time_step(Params p, Work w, int keep_lists) {
   double umax = sqrt(__longlong_as_double((long long)*w.umax_bits));
   if (p.body_speed > umax) umax = p.body_speed;  // a prescribed body also bounds the step
   double dt;
@@ -171,10 +171,19 @@ __global__ void k_time_step(Params p, Work w) {
     dt = p.cfl * t;
   }
   w.scalars[1] = dt;
+  if (p.skin && keep_lists) {
+    // lists kept for stage 2: a particle moves at most dt (U_max + U_max/2)
+    // (or dt |body_u|) in stage 1, so pairs within 2h at stage 2 lie within
+    // 2h + delta at stage 1; the margin covers the rounding of the move
+    const double delta = 3.0 * dt * umax * (1.0 + 1e-6);
+    if (delta > p.skin_max) atomicOr(w.status, kStatSkin);
+    const double rl = p.two_h + delta + p.skin_e;
+    w.scalars[3] = rl * rl * (1.0 + 16.0 * 5.9604644775390625e-08);
+  }
 }
 
-void launch_time_step(const Params& p, const Work& w, cudaStream_t st) {
-  k_time_step<<<1, 1, 0, st>>>(p, w);
+void launch_time_step(const Params& p, const Work& w, cudaStream_t st, bool keep_lists) {
+  k_time_step<<<1, 1, 0, st>>>(p, w, keep_lists ? 1 : 0);
 }
 
 // FP32 value of a finite double, rounded to nearest (ties away from zero) on

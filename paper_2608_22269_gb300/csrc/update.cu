@@ -50,6 +50,37 @@ void launch_rk_stage(const Params& p, const State& s, const Work& w, int64_t n, 
   k_rk_stage<<<(unsigned)div_up(n > 0 ? n : 1, 256), 256, 0, st>>>(p, s, w, n, stage);
 }
 
+// FP32 position copies of the moved particles (fluid and body) at their
+// current positions, in the sorted order of the last neighbour build: xf for
+// the candidate tests, xff for the wall update's scan over fluid particles.
+__global__ void k_refresh_xf(int dim, State s, Work w, int64_t n, int64_t nf, int64_t nd, int compact) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  auto pos = [&](uint32_t i) {
+    float4 f = make_float4(0.f, 0.f, 0.f, (float)s.type[i]);
+    f.x = (float)s.x[i];
+    f.y = (float)s.x[n + i];
+    if (dim == 3) f.z = (float)s.x[2 * n + i];
+    return f;
+  };
+  if (t < nf) {
+    const uint32_t i = w.fluid_list[t];
+    const float4 f = pos(i);
+    w.xf[i] = f;
+    if (compact) w.xff[t] = f;
+  }
+  if (t < nd) {
+    const uint32_t i = w.dummy_list[t];
+    if (s.type[i] == kBody) w.xf[i] = pos(i);
+  }
+}
+
+void launch_refresh_xf(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int64_t nd,
+                       cudaStream_t st) {
+  const int64_t m = nf > nd ? nf : nd;
+  if (m == 0) return;
+  k_refresh_xf<<<(unsigned)div_up(m, 256), 256, 0, st>>>(p.dim, s, w, n, nf, nd, nd > 0 && w.dummy_list ? 1 : 0);
+}
+
 // ---------------------------------------------------------------------------
 // Field output in original order: out[k n + oid[i]] = field[k n + i].
 // ---------------------------------------------------------------------------

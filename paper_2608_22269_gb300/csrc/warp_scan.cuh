@@ -87,7 +87,7 @@ struct CandSource {
 };
 
 // f(j, r2f, type_j) is called for every candidate j != self of the lane's
-// particle with FP32 squared distance r2f <= prefilter_r2 (type_j from the .w
+// particle with FP32 squared distance r2f <= pre_r2 (type_j from the .w
 // component of the FP32 position copy). `stage` holds 32 float4 and `sidx`
 // 32 indices of this warp; the positions are staged as four arrays of 32
 // (x, y, z, type) so that pairs of candidates load as one 64-bit word. All
@@ -99,9 +99,9 @@ struct CandSource {
 // into registers while the current ones are tested: no partially filled
 // batches at row ends, and the gather latency overlaps the tests.
 template <int DIM, class F>
-__device__ __forceinline__ void warp_scan_candidates(const Params& p, const CandSource& src, bool active,
-                                                     uint32_t self, uint32_t key, float4 xs,
-                                                     float4* stage, uint32_t* sidx, F&& f) {
+__device__ __forceinline__ void warp_scan_candidates_r(const Params& p, const CandSource& src, bool active,
+                                                       uint32_t self, uint32_t key, float4 xs, float pre_r2,
+                                                       float4* stage, uint32_t* sidx, F&& f) {
   constexpr int NR = DIM == 3 ? 9 : 3;
   const int lane = threadIdx.x & 31;
   LaneCell c = lane_cell(p, active ? key : 0u);
@@ -161,7 +161,7 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Cand
     const bool fin = isfinite(xs.x) && isfinite(xs.y) && isfinite(xs.z);
     const float qx = fin ? xs.x : -INFINITY, qy = fin ? xs.y : -INFINITY, qz = fin ? xs.z : -INFINITY;
     const unsigned long long px = f32x2_pack(qx, qx), py = f32x2_pack(qy, qy), pz = f32x2_pack(qz, qz);
-    const unsigned long long pre2 = f32x2_pack(p.prefilter_r2, p.prefilter_r2);
+    const unsigned long long pre2 = f32x2_pack(pre_r2, pre_r2);
     for (uint32_t c0 = 0; c0 < total; c0 += 32) {
       // slots past the stream hold a point at infinity, which no test passes
       sx[lane] = nxt.x;
@@ -180,8 +180,8 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Cand
       if (in_g) {
         // independent tests of all 32 staged candidates, then the hits in
         // order. Four candidates per 16-byte broadcast load, two per paired
-        // instruction; candidate k fails r2 <= prefilter_r2 exactly when the
-        // difference prefilter_r2 - r2 is negative (it is never rounded to
+        // instruction; candidate k fails r2 <= pre_r2 exactly when the
+        // difference pre_r2 - r2 is negative (it is never rounded to
         // zero), so its sign bit is shifted into bit k of the miss mask.
         unsigned miss = 0u;
         const ulonglong2* s4 = reinterpret_cast<const ulonglong2*>(sx);
@@ -215,6 +215,14 @@ __device__ __forceinline__ void warp_scan_candidates(const Params& p, const Cand
       __syncwarp();
     }
   }
+}
+
+// The scan with the candidate threshold of Algorithm 1's test (prefilter_r2).
+template <int DIM, class F>
+__device__ __forceinline__ void warp_scan_candidates(const Params& p, const CandSource& src, bool active,
+                                                     uint32_t self, uint32_t key, float4 xs,
+                                                     float4* stage, uint32_t* sidx, F&& f) {
+  warp_scan_candidates_r<DIM>(p, src, active, self, key, xs, p.prefilter_r2, stage, sidx, static_cast<F&&>(f));
 }
 
 // Candidates = all particles in sorted order.

@@ -122,16 +122,62 @@ def test_mixed_lone_particle_falls_exactly():
     assert abs(x[1] - (0.2 + t - 0.5 * 9.81 * t * t)) < 1e-13
 
 
+def _mixed_cell(p):
+    """Cell size of the mixed path: 2h widened by the skin of its kept lists,
+    3 CFL dx 0.3 / 1.3 (the move of two particles in one stage at Mach 0.3)."""
+    return 2.0 * p["h_over_dx"] * p["dx"] + 3.0 * p["cfl"] * p["dx"] * 0.3 / 1.3
+
+
 def test_mixed_rejects_grids_beyond_its_packed_cell_coordinates():
     """The mixed path packs cell coordinates in 11/11/10 bits: a grid with
     more than 2048 cells on an axis is refused at the first step with
     WBSPH_E_INVAL (the FP64 path has no such limit)."""
     from paper_2608_22269_gb300 import wbsph
-    p = S.default_params(2, 0.01, 30.0, domain_min=[-5, -50, 0], domain_max=[5, 5, 1])
+    p = S.default_params(2, 0.01, 30.0, domain_min=[-5, -60, 0], domain_max=[5, 5, 1])
     sc = S.Scene(p, np.array([[0.1], [0.2]]), np.zeros((2, 1)), np.zeros(1), np.zeros(1, np.uint8),
                  np.zeros((2, 1)))
-    assert int(np.floor(55.0 / (2 * 1.3 * 0.01))) + 1 > 2048
+    assert int(np.floor(65.0 / _mixed_cell(p))) + 1 > 2048
     sim = _sim(sc)
     with pytest.raises(wbsph.WbsphError) as ei:
         sim.step(1)
     assert ei.value.code == -1
+
+
+def test_mixed_kept_lists_in_a_fast_flow():
+    """The mixed step sorts once and keeps stage 1's lists (radius 2h +
+    3 dt U_max) for stage 2. In a flow thrown at 2.5 m/s (Mach 0.14), where
+    particles move furthest between the stages, four steps stay as close to
+    the oracle as two steps of the slow case above: a pair missing from the
+    kept lists would show at the 1e-3 level."""
+    sc = S.jitter(S.dam_break_2d(dx=0.01, width=0.8, column=(0.4, 0.25)), 0.3, seed=3)
+    f = sc.type == 0
+    sc.u[0, f] = 2.5
+    sc.u[1, f] = 0.5 * np.random.default_rng(1).normal(size=f.sum())
+    sim = _sim(sc)
+    sim.step(4)
+    st = oracle.State(sc)
+    st.step(4)
+    sk = scales(sc.params, sc.water_height)
+    ex = scaled_err(sim.get("x"), st.x, sk["x"])
+    eu = scaled_err(sim.get("u"), st.u, sk["u"])
+    ep = scaled_err(sim.get("phi"), st.phi, sk["phi"])
+    print(f"fast flow: x {ex:.2e} u {eu:.2e} phi {ep:.2e}")
+    assert ex <= 1e-9 and eu <= 1e-6 and ep <= 1e-6
+
+
+def test_mixed_kept_lists_report_a_move_beyond_the_skin():
+    """A fixed time step that lets a particle move further in one stage than
+    the widened cells allow (3 dt U > 3 CFL dx 0.3 / 1.3) is reported as
+    WBSPH_E_CAPACITY at the next synchronising call."""
+    from paper_2608_22269_gb300 import wbsph
+    sc = S.dam_break_2d(dx=0.01, width=0.8, column=(0.4, 0.25))
+    f = sc.type == 0
+    sc.u[0, f] = 2.0
+    p = dict(sc.params, fixed_dt=5e-4)
+    assert 3 * 5e-4 * 2.0 > _mixed_cell(p) - 2.0 * p["h_over_dx"] * p["dx"]
+    sim = wbsph.Sim(p, precision=wbsph.MIXED, water_height=sc.water_height)
+    sim.set_scene(sc)
+    with pytest.raises(wbsph.WbsphError) as ei:
+        sim.step(1)
+        sim.sync()
+    assert ei.value.code == -9 and "skin" in str(ei.value)
