@@ -578,17 +578,25 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 // messages). Warp w of a group serves lanes 32 (w % 4) .. + 31 and the
 // accumulator column half w / 4, so each thread holds 32 of the receiver's 64
 // running sums in registers. The group walks the receivers' k-major
-// neighbour lists, step k taking the k-th neighbour of every receiver:
-//   - gather (step k + 1, one step ahead): the sender rows by cp.async into a
-//     128-byte-swizzled K-major tile, the sender's FP32 pack (32 B: x, phi',
-//     U) into registers and from it the 16-wide edge-input row (K padded to
-//     16);
-//   - one thread issues D = G W_g/2 + H W_s/2 (three K = 16 MMAs, M = 128,
-//     N = 64, BF16 in, FP32 in TMEM), double-buffered in TMEM and smem;
-//   - epilogue: u = D + P_r/2 (P_r = h_i W_r + b1, from one MMA at the tile
-//     start, held as BF16 pairs), silu(2u) = u + u tanh(u) with the packed
-//     BF16 hardware tanh, summed in FP32 for the receivers that have a k-th
-//     neighbour (the weights were halved on staging: exact in BF16).
+// neighbour lists, step k taking the k-th neighbour of every receiver, as a
+// three-deep software pipeline (iteration k):
+//   - gathers for step k + 2: the sender rows by cp.async into the K-major
+//     128-byte-swizzled ring slot (k + 2) % 4, and the sender's FP32 pack
+//     (32 B: x, phi', U) into registers;
+//   - the 16-wide edge-input row of step k + 1 (K padded to 16) from the
+//     pack loaded one iteration earlier;
+//   - once the group's operands of step k + 1 are in place, one thread
+//     issues D = G W_g/2 + H W_s/2 for it (three K = 16 MMAs, M = 128,
+//     N = 64, BF16 in, FP32 in TMEM, two accumulators alternating);
+//   - the epilogue of step k runs while that MMA executes: u = D + P_r/2
+//     (P_r = h_i W_r + b1, from one MMA at the tile start, held as BF16
+//     pairs), silu(2u) = u + u tanh(u) with the packed BF16 hardware tanh,
+//     summed in FP32 for the receivers that have a k-th neighbour (the
+//     weights were halved on staging: exact in BF16).
+// The MMA latency hides behind the epilogue and the gather latency behind
+// two steps; one group barrier per step. The ring lives in three tiles per
+// group (edge inputs of four steps in one tile, sender rows of two steps in
+// each of the others), which leaves room for both groups in 158 KB.
 // At the end of the tile the sums (BF16) go through W2 on the tensor core,
 // the node MLP's two GEMMs follow (K = 128 from the h_i and m_i tiles), and
 // h'_i is written. Every mbarrier wait is bounded; a timeout is voted over
@@ -600,7 +608,9 @@ constexpr int MS_GROUP_THREADS = 256;
 constexpr int MS_THREADS = MS_GROUPS * MS_GROUP_THREADS;
 constexpr uint32_t MS_W_BYTES = 8192;  // [64][64] BF16 weight tile, K-major swizzled
 constexpr int MS_NW = 7;
-constexpr size_t MS_SMEM_BYTES = 1024 + MS_NW * MS_W_BYTES + 256 * 4 + (size_t)MS_GROUPS * 4 * TC_TILE_BYTES + 128;
+constexpr int MS_TILES = 3;            // per group: the edge-input ring, two sender-row tiles
+constexpr size_t MS_SMEM_BYTES =
+    1024 + MS_NW * MS_W_BYTES + 256 * 4 + (size_t)MS_GROUPS * MS_TILES * TC_TILE_BYTES + 128;
 
 struct MsgArgs {
   int64_t nf, nd;
@@ -626,7 +636,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
   unsigned char* W = base;
   float* bias = reinterpret_cast<float*>(W + MS_NW * MS_W_BYTES);  // b1/2 | b2 (edge) | b1 | b2 (node)
   unsigned char* tiles = reinterpret_cast<unsigned char*>(bias + 256);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tiles + (size_t)MS_GROUPS * 4 * TC_TILE_BYTES);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tiles + (size_t)MS_GROUPS * MS_TILES * TC_TILE_BYTES);
   int* wmax = reinterpret_cast<int*>(mbar + 2 * MS_GROUPS);  // per-warp neighbour-count maxima
   uint32_t* tslot = reinterpret_cast<uint32_t*>(wmax + 16);
   const int t = threadIdx.x;
@@ -664,32 +674,41 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tslot;
 
   const int g = t / MS_GROUP_THREADS, lt = t % MS_GROUP_THREADS, lw = lt >> 5, lane = t & 31;
   const int q = lw & 3, ch = lw >> 2;   // lane quarter, column half
   const int r = q * 32 + lane;          // receiver row = TMEM lane
   const int bar_id = 1 + g;
   const bool leader = lt == 0;
+  // Per group: T0 holds the edge-input rows of four neighbour steps (step s
+  // in K block s % 4: 16-byte chunk 2 (s % 4), and chunk 2 (s % 4) + 1 zero,
+  // the K padding); T1 and T2 hold the sender rows of steps s % 4 = 0, 1 and
+  // 2, 3 (32 features = chunks 4 (s % 2) .. 4 (s % 2) + 3). Outside the
+  // neighbour loop T1 and T2 serve as 64-wide row tiles.
+  unsigned char* T0 = tiles + (size_t)g * MS_TILES * TC_TILE_BYTES;
+  unsigned char* T1 = T0 + TC_TILE_BYTES;
+  unsigned char* T2 = T1 + TC_TILE_BYTES;
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  if (ch == 0) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) *reinterpret_cast<uint4*>(T0 + sw128(r, 2 * s + 1)) = zero4;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
   const uint32_t D0 = tmem + 128u * g, D1 = D0 + 64u;
   const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + 32u * ch;
-  unsigned char* G0 = tiles + (size_t)g * 4 * TC_TILE_BYTES;
-  unsigned char* G1 = G0 + TC_TILE_BYTES;
-  unsigned char* H0 = G1 + TC_TILE_BYTES;
-  unsigned char* H1 = H0 + TC_TILE_BYTES;
   uint64_t* mb = mbar + 2 * g;
   const uint64_t dW[MS_NW] = {tc_desc(smem_u32(W)), tc_desc(smem_u32(W + MS_W_BYTES)),
                               tc_desc(smem_u32(W + 2 * MS_W_BYTES)), tc_desc(smem_u32(W + 3 * MS_W_BYTES)),
                               tc_desc(smem_u32(W + 4 * MS_W_BYTES)), tc_desc(smem_u32(W + 5 * MS_W_BYTES)),
                               tc_desc(smem_u32(W + 6 * MS_W_BYTES))};
+  const uint64_t dT0 = tc_desc(smem_u32(T0)), dT1 = tc_desc(smem_u32(T1)), dT2 = tc_desc(smem_u32(T2));
   const float* b1h = bias;
   const float* b2e = bias + 64;
   const float* b1n = bias + 128;
   const float* b2n = bias + 192;
-  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
   uint32_t ph = 0u;  // parity of the next phase of mb[0], mb[1]
   bool ok = true;
   auto wait_mma = [&](int b) {
@@ -703,10 +722,11 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) cp_async16(T + sw128(r, ch * 4 + c), src + (ch * 4 + c) * 8, valid);
   };
-  // the sender's first SEND features (64 B, chunks 0..3 of the row): two chunks per column half
-  auto copy_send = [&](unsigned char* T, const bf16* src, bool valid) {
+  // the sender's first SEND features (64 B) into ring slot s: two chunks per column half
+  auto copy_send = [&](int s, const bf16* src, bool valid) {
+    unsigned char* T = (s & 2) ? T2 : T1;
 #pragma unroll
-    for (int c = 0; c < 2; ++c) cp_async16(T + sw128(r, ch * 2 + c), src + (ch * 2 + c) * 8, valid);
+    for (int c = 0; c < 2; ++c) cp_async16(T + sw128(r, 4 * (s & 1) + ch * 2 + c), src + (ch * 2 + c) * 8, valid);
   };
   auto sync_operands = [&]() -> bool {  // smem operands written by the group -> tensor core
     cp_async_wait<0>();
@@ -715,14 +735,14 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
     ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);
     return ok;
   };
-  auto mma_k64 = [&](uint32_t d, const unsigned char* A, int w, bool accumulate) {
-    const uint64_t dA = tc_desc(smem_u32(A));
+  auto mma_k64 = [&](uint32_t d, uint64_t dA, int w, bool accumulate) {
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) tc_mma(d, dA + 2 * kk, dW[w] + 2 * kk, (accumulate || kk > 0) ? 1u : 0u);
   };
-  auto mma_step = [&](uint32_t d, const unsigned char* Gb, const unsigned char* Hb) {
-    tc_mma(d, tc_desc(smem_u32(Gb)), dW[WG], 0u);
-    const uint64_t dA = tc_desc(smem_u32(Hb));
+  // D = G W_g/2 + H W_s/2 of ring slot s
+  auto mma_step = [&](uint32_t d, int s) {
+    tc_mma(d, dT0 + 2 * s, dW[WG], 0u);
+    const uint64_t dA = ((s & 2) ? dT2 : dT1) + 4 * (s & 1);
 #pragma unroll
     for (int kk = 0; kk < SEND / 16; ++kk) tc_mma(d, dA + 2 * kk, dW[WS] + 2 * kk, 1u);
   };
@@ -750,25 +770,33 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
     if (msg) {
       const float4 ai = ch == 0 ? __ldg(a.pack + 2 * node) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 bi = ch == 0 ? __ldg(a.pack + 2 * node + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-      // h_i rows (for P_r) into G1, step 0 into G0 / H0
-      copy_row_half(G1, a.h_in + (int64_t)node * HID, valid);
-      uint32_t jn = cnt > 0 ? __ldg(a.nbr + gi) : 0u;
-      copy_send(H0, a.h_in + (int64_t)jn * HID, cnt > 0);
+      // h_i rows (for P_r) into T2, the sender rows of steps 0 and 1 into slots 0 and 1
+      const uint32_t j0 = cnt > 0 ? __ldg(a.nbr + gi) : 0u;
+      const uint32_t j1 = cnt > 1 ? __ldg(a.nbr + a.nf + gi) : 0u;
+      uint32_t jn2 = cnt > 2 ? __ldg(a.nbr + 2 * a.nf + gi) : 0u;
+      copy_row_half(T2, a.h_in + (int64_t)node * HID, valid);
+      copy_send(0, a.h_in + (int64_t)j0 * HID, cnt > 0);
+      copy_send(1, a.h_in + (int64_t)j1 * HID, cnt > 1);
       cp_async_commit();
+      float4 aj1 = make_float4(0.f, 0.f, 0.f, 0.f), bj1 = aj1;
       if (ch == 0) {
         uint4 f = zero4;
         if (cnt > 0)
-          f = edge_features(a.dim, ai, bi, __ldg(a.pack + 2 * jn), __ldg(a.pack + 2 * jn + 1), a.inv_h, a.inv_su,
+          f = edge_features(a.dim, ai, bi, __ldg(a.pack + 2 * j0), __ldg(a.pack + 2 * j0 + 1), a.inv_h, a.inv_su,
                             a.inv_sphi);
-        *reinterpret_cast<uint4*>(G0 + sw128(r, 0)) = f;
-        *reinterpret_cast<uint4*>(G0 + sw128(r, 1)) = zero4;
+        *reinterpret_cast<uint4*>(T0 + sw128(r, 0)) = f;
+        if (cnt > 1) {
+          aj1 = __ldg(a.pack + 2 * j1);
+          bj1 = __ldg(a.pack + 2 * j1 + 1);
+        }
       }
-      jn = cnt > 1 ? __ldg(a.nbr + a.nf + gi) : 0u;
       if (!sync_operands()) break;
       if (leader) {
         tc_fence_after();
-        mma_k64(D1, G1, WR, false);  // P_r / 2 = h_i W_r / 2
+        mma_k64(D1, dT2, WR, false);  // P_r / 2 = h_i W_r / 2
         tc_commit(smem_u32(mb + 1));
+        mma_step(D0, 0);
+        tc_commit(smem_u32(mb + 0));
       }
       wait_mma(1);
       uint32_t pr[16];  // (P_r + b1) / 2 of this thread's 32 columns, BF16 pairs
@@ -782,25 +810,37 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
           pr[8 * hh + p] = bf2_u32(__floats2bfloat162_rn(v[2 * p] + b1h[col], v[2 * p + 1] + b1h[col + 1]));
         }
       }
-      if (leader) {
-        mma_step(D0, G0, H0);
-        tc_commit(smem_u32(mb + 0));
-      }
+      // Step k: the sender rows of step k + 2 go out, the edge inputs of step
+      // k + 1 are formed, and once every thread's operands of step k + 1 are
+      // in place its MMA is issued; the epilogue of step k then runs while
+      // that MMA executes.
       for (int k = 0; k < kmax; ++k) {
-        const int b = k & 1;
-        unsigned char* Gn = b ? G0 : G1;
-        unsigned char* Hn = b ? H0 : H1;
-        const bool more = k + 1 < kmax, act1 = k + 1 < cnt;
-        float4 aj = make_float4(0.f, 0.f, 0.f, 0.f), bj = aj;
-        if (more) {  // step k + 1: h_j rows in flight, sender packs into registers
-          copy_send(Hn, a.h_in + (int64_t)jn * HID, act1);
-          cp_async_commit();
-          if (ch == 0 && act1) {
-            aj = __ldg(a.pack + 2 * jn);
-            bj = __ldg(a.pack + 2 * jn + 1);
-          }
+        const bool more1 = k + 1 < kmax, act1 = k + 1 < cnt;
+        const bool more2 = k + 2 < kmax, act2 = k + 2 < cnt;
+        if (more2) copy_send((k + 2) & 3, a.h_in + (int64_t)jn2 * HID, act2);
+        cp_async_commit();
+        float4 aj2 = make_float4(0.f, 0.f, 0.f, 0.f), bj2 = aj2;
+        if (ch == 0 && act2) {
+          aj2 = __ldg(a.pack + 2 * jn2);
+          bj2 = __ldg(a.pack + 2 * jn2 + 1);
         }
-        const uint32_t jnn = k + 2 < cnt ? __ldg(a.nbr + (int64_t)(k + 2) * a.nf + gi) : 0u;
+        const uint32_t jn3 = k + 3 < cnt ? __ldg(a.nbr + (int64_t)(k + 3) * a.nf + gi) : 0u;
+        if (more1 && ch == 0) {
+          uint4 f = zero4;
+          if (act1) f = edge_features(a.dim, ai, bi, aj1, bj1, a.inv_h, a.inv_su, a.inv_sphi);
+          *reinterpret_cast<uint4*>(T0 + sw128(r, 2 * ((k + 1) & 3))) = f;
+        }
+        cp_async_wait<1>();  // the rows of step k + 1 (issued one step ago)
+        fence_async_smem();
+        tc_fence_before();
+        ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);
+        if (!ok) break;
+        const int b = k & 1;
+        if (more1 && leader) {
+          tc_fence_after();
+          mma_step(b ? D0 : D1, (k + 1) & 3);
+          tc_commit(smem_u32(mb + (b ^ 1)));
+        }
         // epilogue of step k
         wait_mma(b);
         const bool act = k < cnt;
@@ -820,22 +860,13 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
             }
           }
         }
-        if (more && ch == 0) {
-          uint4 f = zero4;
-          if (act1) f = edge_features(a.dim, ai, bi, aj, bj, a.inv_h, a.inv_su, a.inv_sphi);
-          *reinterpret_cast<uint4*>(Gn + sw128(r, 0)) = f;
-          *reinterpret_cast<uint4*>(Gn + sw128(r, 1)) = zero4;
-        }
-        if (!sync_operands()) break;
-        if (more && leader) {
-          tc_fence_after();
-          mma_step(b ? D0 : D1, Gn, Hn);
-          tc_commit(smem_u32(mb + (b ^ 1)));
-        }
-        jn = jnn;
+        aj1 = aj2;
+        bj1 = bj2;
+        jn2 = jn3;
       }
       if (!ok) break;
-      // m_i = (sum_j silu(z_ij)) W2 + n_i b2: the sums (BF16) to G0, one GEMM
+      cp_async_wait<0>();
+      // m_i = (sum_j silu(z_ij)) W2 + n_i b2: the sums (BF16) to T1, one GEMM
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         uint4 o;
@@ -843,14 +874,14 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
         o.y = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 2], acc[8 * c + 3]));
         o.z = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 4], acc[8 * c + 5]));
         o.w = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 6], acc[8 * c + 7]));
-        *reinterpret_cast<uint4*>(G0 + sw128(r, ch * 4 + c)) = o;
+        *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + c)) = o;
       }
-      copy_row_half(H1, a.h_in + (int64_t)node * HID, valid);  // h_i again, for the node MLP
+      copy_row_half(T2, a.h_in + (int64_t)node * HID, valid);  // h_i again, for the node MLP
       cp_async_commit();
       if (!sync_operands()) break;
       if (leader) {
         tc_fence_after();
-        mma_k64(D0, G0, WE2, false);
+        mma_k64(D0, dT1, WE2, false);
         tc_commit(smem_u32(mb + 0));
       }
       wait_mma(0);
@@ -866,26 +897,27 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
           o[p] = bf2_u32(__floats2bfloat162_rn(fmaf(fc, b2e[col], v[2 * p]), fmaf(fc, b2e[col + 1], v[2 * p + 1])));
         }
         const uint4 o0 = make_uint4(o[0], o[1], o[2], o[3]), o1 = make_uint4(o[4], o[5], o[6], o[7]);
-        *reinterpret_cast<uint4*>(H0 + sw128(r, ch * 4 + 2 * hh)) = o0;
-        *reinterpret_cast<uint4*>(H0 + sw128(r, ch * 4 + 2 * hh + 1)) = o1;
+        // T1 (the sums) was read by the completed MMA: m_i overwrites it
+        *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + 2 * hh)) = o0;
+        *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + 2 * hh + 1)) = o1;
         if (a.m_out && valid) {
           uint4* mo = reinterpret_cast<uint4*>(a.m_out + (int64_t)node * HID + 32 * ch + 16 * hh);
           mo[0] = o0;
           mo[1] = o1;
         }
       }
-    } else {  // no messages: m = 0, h_i into H1
+    } else {  // no messages: m = 0 into T1, h_i into T2
 #pragma unroll
-      for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(H0 + sw128(r, ch * 4 + c)) = zero4;
-      copy_row_half(H1, a.h_in + (int64_t)node * HID, valid);
+      for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + c)) = zero4;
+      copy_row_half(T2, a.h_in + (int64_t)node * HID, valid);
       cp_async_commit();
     }
     // node MLP: z = [h_i, m_i] W1 + b1 (K = 128), h' = h_i + silu(z) W2 + b2
     if (!sync_operands()) break;
     if (leader) {
       tc_fence_after();
-      mma_k64(D1, H1, WH, false);
-      mma_k64(D1, H0, WM, true);
+      mma_k64(D1, dT2, WH, false);
+      mma_k64(D1, dT1, WM, true);
       tc_commit(smem_u32(mb + 1));
     }
     wait_mma(1);
@@ -899,13 +931,14 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
         const int col = 32 * ch + 16 * hh + 2 * p;
         o[p] = bf2_u32(__floats2bfloat162_rn(silu_tanh(v[2 * p] + b1n[col]), silu_tanh(v[2 * p + 1] + b1n[col + 1])));
       }
-      *reinterpret_cast<uint4*>(G1 + sw128(r, ch * 4 + 2 * hh)) = make_uint4(o[0], o[1], o[2], o[3]);
-      *reinterpret_cast<uint4*>(G1 + sw128(r, ch * 4 + 2 * hh + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+      // T1 (m_i) was read by the completed MMA: the hidden layer overwrites it
+      *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + 2 * hh)) = make_uint4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + 2 * hh + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
     }
     if (!sync_operands()) break;
     if (leader) {
       tc_fence_after();
-      mma_k64(D0, G1, WN2, false);
+      mma_k64(D0, dT1, WN2, false);
       tc_commit(smem_u32(mb + 0));
     }
     wait_mma(0);
@@ -916,7 +949,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
       uint32_t o[8];
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
-        const uint4 hv = *reinterpret_cast<const uint4*>(H1 + sw128(r, ch * 4 + 2 * hh + cc));
+        const uint4 hv = *reinterpret_cast<const uint4*>(T2 + sw128(r, ch * 4 + 2 * hh + cc));
         const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -932,7 +965,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
       }
     }
     tc_fence_before();
-    ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);  // H1 and TMEM reads done before the next tile's writes
+    ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);  // T2 and TMEM reads done before the next tile's writes
   }
   cp_async_wait<0>();
   if (!ok && (t % MS_GROUP_THREADS) == 0) atomicOr(a.status, (unsigned)kStatTimeout);
@@ -1495,7 +1528,7 @@ MlpArgs block_args(wbsph_surrogate s, int bi) {
 }
 
 // One fused message-passing layer (k_message_tc): persistent CTAs, one per
-// SM (186 KB of shared memory and 256 TMEM columns each), two receiver
+// SM (158 KB of shared memory and 256 TMEM columns each), two receiver
 // groups per CTA.
 void launch_message(wbsph_surrogate s, const Params& p, const Work& w, int64_t nf, int64_t nd, int l,
                     const bf16* h_in, bf16* h_out, bf16* m_out, cudaStream_t st) {

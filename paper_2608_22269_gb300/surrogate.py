@@ -354,7 +354,7 @@ def main(argv=None):
     ap.add_argument("--t-end", type=float, default=0.4)
     ap.add_argument("--frames", type=int, default=40)
     ap.add_argument("--iters", type=int, default=30000)
-    ap.add_argument("--lr", type=float, default=5e-4)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--eval-steps", type=int, default=400)
     ap.add_argument("--concurrent", type=int, default=16, help="trajectories generated at once")
