@@ -15,6 +15,8 @@
 // delta-SPH sums are rebuilt from phi' sums in FP64:
 //   C = C' + 2 phi_hs,i K + L G,   D = D' + G.K,   K = sum grad W V.
 // The state (x, U, phi) stays FP64; only the pair sums run in FP32.
+#include <type_traits>
+
 #include "../../include/wbsph.h"
 #include "common.cuh"
 #include "physics.cuh"
@@ -22,6 +24,12 @@
 namespace wbsph {
 
 // Kahan-compensated FP32 accumulator: s + (-c) carries the running sum.
+// The terms of list entries 2m and 2m + 1 enter as one compensated step:
+// defer() parks the first in the compensation (one subtraction), add()
+// folds it in with the second (y = v - c takes both), so the compensated
+// update costs 2.5 operations per term instead of 4. The parked term adds
+// one FP32 rounding of its own magnitude per pair of terms, where plain
+// Kahan has none; the compensation of the running sum is unchanged.
 struct Kahan {
   float s, c;
   __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
@@ -31,8 +39,14 @@ struct Kahan {
     c = (t - s) - y;
     s = t;
   }
+  __device__ __forceinline__ void defer(float v) { c -= v; }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
+template <bool FULL>
+__device__ __forceinline__ void kacc(Kahan& a, float v) {
+  if constexpr (FULL) a.add(v);
+  else a.defer(v);
+}
 
 constexpr int MX_THREADS = 128;
 #ifndef WBSPH_MX_MIN_BLOCKS
@@ -115,8 +129,11 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
     mx_commit();
   }
   uint32_t jn = MX_RING < cnt ? __ldg(lst + (int64_t)MX_RING * nf) : 0u;  // next entry to fetch
-  for (int k = 0; k < maxc; ++k) {
-    if (k >= cnt) continue;
+  // entry k of the lists; terms of even k are parked (defer), odd k
+  // completes the compensated step of the pair (add)
+  auto entry = [&](int k, auto odd) {
+    constexpr bool FULL = decltype(odd)::value;
+    if (k >= cnt) return;
     mx_wait_ring();  // entry k's group has landed; the later ones may still be in flight
     const int q = (k % MX_RING) * MX_THREADS + t;
     const float4 Aj = ringA[q], Bj = ringB[q];
@@ -139,7 +156,7 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
       if (k + MX_RING + 1 < cnt) jn = __ldg(lst + (int64_t)(k + MX_RING + 1) * nf);
     }
     mx_commit();
-    if (!(r2 <= four_h2 && r2 > 0.f)) continue;  // the neighbour test in FP32
+    if (!(r2 <= four_h2 && r2 > 0.f)) return;  // the neighbour test in FP32
     ++npairs;
     float inv_r = rsqrtf(r2);
     float rr = r2 * inv_r;
@@ -153,23 +170,23 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
 #pragma unroll
     for (int c = 0; c < DIM; ++c) gr[c] = g * r[c];
     if (DIM == 2) {
-      L[0].add(r[0] * gr[0]); L[1].add(r[0] * gr[1]); L[2].add(r[1] * gr[1]);
+      kacc<FULL>(L[0], r[0] * gr[0]); kacc<FULL>(L[1], r[0] * gr[1]); kacc<FULL>(L[2], r[1] * gr[1]);
     } else {
-      L[0].add(r[0] * gr[0]); L[1].add(r[0] * gr[1]); L[2].add(r[0] * gr[DIM - 1]);
-      L[3].add(r[1] * gr[1]); L[4].add(r[1] * gr[DIM - 1]); L[5].add(r[DIM - 1] * gr[DIM - 1]);
+      kacc<FULL>(L[0], r[0] * gr[0]); kacc<FULL>(L[1], r[0] * gr[1]); kacc<FULL>(L[2], r[0] * gr[DIM - 1]);
+      kacc<FULL>(L[3], r[1] * gr[1]); kacc<FULL>(L[4], r[1] * gr[DIM - 1]); kacc<FULL>(L[5], r[DIM - 1] * gr[DIM - 1]);
     }
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-      S[c].add(rs * gr[c]);
-      Cs[c].add(sphi * gr[c]);
-      K[c].add(gr[c]);
+      kacc<FULL>(S[c], rs * gr[c]);
+      kacc<FULL>(Cs[c], sphi * gr[c]);
+      kacc<FULL>(K[c], gr[c]);
 #pragma unroll
-      for (int d2 = 0; d2 < DIM; ++d2) M[c * DIM + d2].add(du[c] * gr[d2]);
+      for (int d2 = 0; d2 < DIM; ++d2) kacc<FULL>(M[c * DIM + d2], du[c] * gr[d2]);
     }
-    D.add(dphi * g);
+    kacc<FULL>(D, dphi * g);
     if (Bjw > 0.f || p.wall_bc) {
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) Lam[c].add(du[c] * g);
+      for (int c = 0; c < DIM; ++c) kacc<FULL>(Lam[c], du[c] * g);
     }
     if (p.use_pst) {
       float q21 = fmaf(rr, two_over_h, 1.f);
@@ -177,8 +194,12 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
       float r4 = (ratio * ratio) * (ratio * ratio);
       float f = fmaf(pst_R, r4, 1.f);
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) P[c].add(f * gr[c]);
+      for (int c = 0; c < DIM; ++c) kacc<FULL>(P[c], f * gr[c]);
     }
+  };
+  for (int k = 0; k < maxc; k += 2) {
+    entry(k, std::false_type{});
+    if (k + 1 < maxc) entry(k + 1, std::true_type{});
   }
   unsigned wp = __reduce_add_sync(0xffffffffu, npairs);
   if (lane == 0 && wp) atomicAdd(w.pairs, (unsigned long long)wp);
