@@ -42,9 +42,11 @@ FLOPS_PER_PAIR_2D = 74
 # per fluid particle: eigenvalue, 3x3 inverse, contractions and rates
 FLOPS_EPILOGUE_3D = 260
 # FP32 flops of one pair in the mixed pass: 78 for the pair terms and
-# 124 for the Kahan-compensated updates of 31 accumulators (4 each)
-FLOPS_PER_PAIR_MIXED_3D = 202
-FLOPS_PER_PAIR_MIXED_2D = 118
+# 77.5 for the Kahan-compensated updates of 31 accumulators (two
+# consecutive terms share one 4-operation step after a 1-operation park:
+# 2.5 each); 2D: 46 and 18 accumulators
+FLOPS_PER_PAIR_MIXED_3D = 155.5
+FLOPS_PER_PAIR_MIXED_2D = 91
 # measured FMA throughput of this GB300 (independent FMA chains, 152 SMs at
 # 1987 MHz): FP64 5.93e11 DFMA/s = 1.186 TFLOP/s; FP32 3.62e13 FFMA/s = 72.4
 FP64_PEAK_TFLOPS = 1.186

@@ -50,7 +50,7 @@ typedef enum {
   WBSPH_E_NAN = -6,       /* a non-finite rate or state value */
   WBSPH_E_TIMEOUT = -7,   /* a bounded device-side wait gave up */
   WBSPH_E_STATE = -8,     /* call out of order (e.g. step before set_particles) */
-  WBSPH_E_CAPACITY = -9,  /* output capacity too small / neighbour list overflow */
+  WBSPH_E_CAPACITY = -9,  /* output capacity too small / neighbour list overflow / list skin exceeded */
   WBSPH_E_NOSYM = -10     /* feature not built into this library */
 } wbsph_status;
 
@@ -61,12 +61,18 @@ typedef enum {
  *              FP64 epilogue: about 1e-5 of the field scale.
  *  WBSPH_DF64  double-float pair sums (pairs of FP32, about 48 bits) on
  *              offsets in cell units and the same hydrostatic split, FP64
- *              epilogue, the exact FP64 neighbour lists: FP64-level results
- *              on the FP32 pipe.
- * MIXED and DF64 need grids of at most 2048 x 2048 x 1024 cells
- * (WBSPH_E_INVAL at the first stage otherwise) and set the domain status
- * when a particle has moved more than half a cell since the last neighbour
- * build (DF64). */
+ *              epilogue, Algorithm 1's exact FP64 neighbour test: FP64-level
+ *              results on the FP32 pipe.
+ * MIXED and DF64 sort once per step: stage 1 lists every pair within
+ * 2h + 3 dt U* (U* = max(U_max, |body_u|), twice the largest move of a
+ * particle in stage 1) and stage 2 reuses those lists with its own
+ * neighbour test. Their cells are 2h + 3 CFL dx 0.3 / 1.3 wide (the skin of
+ * a flow at Mach 0.3); a step whose skin would be wider (a faster flow, or
+ * a fixed time step too long) returns WBSPH_E_CAPACITY at the next
+ * synchronising call. They need grids of at most 2048 x 2048 x 1024 cells
+ * (WBSPH_E_INVAL at the first stage otherwise), and DF64 sets the domain
+ * status when a particle has moved more than half a cell since the last
+ * neighbour build. */
 typedef enum { WBSPH_FP64 = 0, WBSPH_MIXED = 1, WBSPH_DF64 = 2 } wbsph_precision;
 typedef enum { WBSPH_HOST = 0, WBSPH_DEVICE = 1 } wbsph_where;
 
@@ -175,8 +181,9 @@ int wbsph_build_neighbors(wbsph_handle h);
  * update, volumes, pair pass (Eq. sph). State is not advanced. */
 int wbsph_eval_rates(wbsph_handle h);
 
-/* Advance nsteps SSP-RK2 steps (two stages each, neighbours rebuilt per
- * stage). Asynchronous: errors surface at the next synchronising call. */
+/* Advance nsteps SSP-RK2 steps (two stages each; FP64 rebuilds the
+ * neighbours per stage, MIXED and DF64 once per step, see wbsph_precision).
+ * Asynchronous: errors surface at the next synchronising call. */
 int wbsph_step(wbsph_handle h, int64_t nsteps);
 
 /* One SSP-RK2 stage (Sec. 2.3) of a subdomain of a domain decomposition:

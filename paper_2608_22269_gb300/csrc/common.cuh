@@ -50,15 +50,16 @@ struct Params {
   float nearest_band_r2;          // FP32 band around the FP32 minimum that holds the exact nearest
   float inner_r2;                 // FP32 r^2 at or below it (and > 0): an exact neighbour, no FP64 test
   double domain_min[3], domain_max[3];
-  double R;                       // cell size: 2h, plus skin_max on the mixed path
-  // Mixed path: the candidate lists of stage 1 are kept for stage 2. They
+  double R;                       // cell size: 2h, plus skin_max on the mixed and double-float paths
+  double inv_R;                   // 1 / R
+  // Mixed and double-float paths: the candidate lists of stage 1 are kept for stage 2. They
   // hold every pair within 2h + delta, delta = 3 dt U* (U* = max(U_max,
   // |body_u|)), twice the largest move of a particle in stage 1 (U0 plus a
   // shift clamped to U_max/2, times dt), so that every pair within 2h at the
   // stage-2 positions is listed; cells are widened by skin_max >= delta so
   // that the listed pairs and the wall update's nearest fluid particle stay
   // in adjacent cells without a new sort.
-  int skin;                       // 1: lists kept for stage 2 (mixed path)
+  int skin;                       // 1: lists kept for stage 2 (mixed and double-float paths)
   double skin_max;                // largest delta the cells allow
   double skin_e;                  // FP32 rounding margin of a list distance
   // cell keys: FP32 estimate of (x - min)/R, trusted where its fractional
@@ -79,6 +80,8 @@ struct Params {
   double body_speed;   // |body_u|: bounds the time step
   float df_c0[2];      // double-float path: C0 and R_pst (alpha / W(dx))^4 as hi + lo
   float df_pst_Ra4[2];
+  float df_4h2_R2[2];  // double-float path: (2h / R)^2 as hi + lo (kept lists' exact test)
+  float df_R_2h[2];    // double-float path: R / 2h as hi + lo (1 when the cells are 2h wide)
 };
 
 // Device arrays of one particle-state buffer.
@@ -177,8 +180,10 @@ void launch_pair_fp64(const Params& p, const State& s, const Work& w, int64_t n,
 void launch_lambda_fp64(const Params& p, const Work& w, int64_t n, int64_t nf, cudaStream_t st);
 void launch_pair_mixed(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
                        cudaStream_t st);
+// kept: the lists are the kept lists of radius 2h + delta (the pass applies
+// the exact test); otherwise every entry is an exact neighbour
 void launch_pair_df(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
-                    cudaStream_t st);
+                    cudaStream_t st, bool kept = false);
 void launch_pair_conventional(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf,
                               int stage2, cudaStream_t st);
 

@@ -196,16 +196,17 @@ static int derive_params(wbsph_s* h) {
   p.two_h = 2.0 * p.h;
   p.four_h2 = p.two_h * p.two_h;
   p.R = p.two_h;
-  // Mixed path: lists kept for stage 2 (see Params::skin). The cells are
-  // widened by the largest skin that a flow at Mach 0.3 needs at this CFL
-  // number: a particle moves at most 1.5 dt U_max in stage 1 and
-  // dt <= CFL dx / (C0 + U_max).
-  p.skin = c.precision == WBSPH_MIXED ? 1 : 0;
+  // Mixed and double-float paths: lists kept for stage 2 (see
+  // Params::skin). The cells are widened by the largest skin that a flow at
+  // Mach 0.3 needs at this CFL number: a particle moves at most 1.5 dt U_max
+  // in stage 1 and dt <= CFL dx / (C0 + U_max).
+  p.skin = (c.precision == WBSPH_MIXED || c.precision == WBSPH_DF64) ? 1 : 0;
   if (p.skin) {
     const double mach = 0.3;
     p.skin_max = 3.0 * c.cfl * c.dx * mach / (1.0 + mach);
     p.R = p.two_h + p.skin_max;
   }
+  p.inv_R = 1.0 / p.R;
   p.alpha = c.dim == 2 ? 7.0 / (4.0 * kPi * p.h * p.h) : 21.0 / (16.0 * kPi * p.h * p.h * p.h);
   p.neg_dwdr_over_r_coef = 5.0 * p.alpha / (p.h * p.h);
   p.inv_two_h = 1.0 / p.two_h;
@@ -225,6 +226,14 @@ static int derive_params(wbsph_s* h) {
     p.df_c0[1] = (float)(c.c0 - (double)c0h);
     p.df_pst_Ra4[0] = pah;
     p.df_pst_Ra4[1] = (float)(p.pst_R_a4 - (double)pah);
+    const double t4 = p.four_h2 / (p.R * p.R);
+    const float t4h = (float)t4;
+    p.df_4h2_R2[0] = t4h;
+    p.df_4h2_R2[1] = (float)(t4 - (double)t4h);
+    const double rs = p.R / p.two_h;
+    const float rsh = (float)rs;
+    p.df_R_2h[0] = rsh;
+    p.df_R_2h[1] = (float)(rs - (double)rsh);
   }
   p.rho0 = c.rho0;
   p.c0 = c.c0;
@@ -602,14 +611,16 @@ static void pair_pass(wbsph_s* h, int stage2, int lists = LISTS_STAGE) {
   const bool mixed = h->cfg.precision == WBSPH_MIXED;
   const bool dfp = h->cfg.precision == WBSPH_DF64;
   if (lists != LISTS_REUSE) {
+    // exact lists for the FP64 path, and for the double-float path unless
+    // they are kept lists (then its pass applies the exact test)
     ProfScope ps(h, WBSPH_K_NLIST);
-    launch_nbr_list(h->P, h->A, h->W, n, h->nf, st, !mixed, lists == LISTS_KEEP);
+    launch_nbr_list(h->P, h->A, h->W, n, h->nf, st, !mixed && lists == LISTS_STAGE, lists == LISTS_KEEP);
     h->launches += h->nf ? 1 : 0;
   }
   {
     ProfScope ps(h, WBSPH_K_PAIR);
     if (mixed) launch_pair_mixed(h->P, h->A, h->W, n, h->nf, stage2, st);
-    else if (dfp) launch_pair_df(h->P, h->A, h->W, n, h->nf, stage2, st);
+    else if (dfp) launch_pair_df(h->P, h->A, h->W, n, h->nf, stage2, st, lists != LISTS_STAGE);
     else if (h->P.scheme == WBSPH_SCHEME_CONVENTIONAL) launch_pair_conventional(h->P, h->A, h->W, n, h->nf, stage2, st);
     else launch_pair_fp64(h->P, h->A, h->W, n, h->nf, stage2, st);
   }
@@ -745,9 +756,10 @@ static int enqueue_step(wbsph_s* h) {
   int rc = build(h, false);
   if (rc) return rc;
   if (h->P.skin) {
-    // mixed path: one build per step; stage 2 keeps the sorted order, the
-    // cells and the lists of stage 1 (2h + delta), with the FP32 position
-    // copies brought to the stage-1 positions for the wall update's scan
+    // mixed and double-float paths: one build per step; stage 2 keeps the
+    // sorted order, the cells and the lists of stage 1 (2h + delta), with
+    // the FP32 position copies brought to the stage-1 positions for the wall
+    // update's scan
     if ((rc = prepass(h, 0))) return rc;
     {
       ProfScope ps(h, WBSPH_K_OTHER);
@@ -889,12 +901,12 @@ static int read_status(wbsph_s* h) {
 
 static int decode_status(wbsph_s* h, unsigned s) {
   if (!s) return WBSPH_OK;
-  // the kept lists of the mixed path no longer covered every pair: what
+  // the kept lists no longer covered every pair: what
   // followed is not the method, whatever else went wrong after it
   if (s & kStatSkin)
     return fail(h, WBSPH_E_CAPACITY,
-                "a particle can move more than the neighbour-list skin in one stage (mixed path: flow above "
-                "Mach 0.3 at this CFL number, or a fixed time step that is too long)");
+                "a particle can move more than the neighbour-list skin in one stage (mixed and double-float "
+                "paths: flow above Mach 0.3 at this CFL number, or a fixed time step that is too long)");
   // a non-finite value also sends positions out of the domain: report it first
   if (s & kStatNaN) return fail(h, WBSPH_E_NAN, "non-finite rate or state value");
   if (s & kStatSingular) return fail(h, WBSPH_E_SINGULAR, "singular renormalisation matrix (TIC off)");

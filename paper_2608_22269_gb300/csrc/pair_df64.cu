@@ -24,6 +24,7 @@
 // copies it reads are written per particle by k_pack_df (prepass.cu).
 #include "../../include/wbsph.h"
 #include "common.cuh"
+#include "neighbor_iter.cuh"
 #include "df64.cuh"
 #include "physics.cuh"
 
@@ -84,7 +85,7 @@ __device__ __forceinline__ double df_val(df a) { return df_f2d(a.hi) + df_f2d(a.
 
 template <int DIM>
 __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
-    k_pair_df(Params p, State s, Work w, int64_t n, int64_t nf, int stage2) {
+    k_pair_df(Params p, State s, Work w, int64_t n, int64_t nf, int stage2, int kept) {
   const int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool active = gi < nf;
   const uint32_t i = active ? w.fluid_list[gi] : 0u;
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
   __shared__ float4 ringA[DF_RING * DF_THREADS], ringAl[DF_RING * DF_THREADS];
   __shared__ float4 ringB[DF_RING * DF_THREADS], ringBl[DF_RING * DF_THREADS];
   __shared__ uint32_t ringC[DF_RING * DF_THREADS];
+  __shared__ uint32_t ringJ[DF_RING * DF_THREADS];  // the entry itself, for the exact test of kept lists
   const int tid = threadIdx.x;
   auto fetch = [&](int k, uint32_t j) {  // entry k (< cnt), neighbour j, into slot k % DF_RING
     const int q = (k % DF_RING) * DF_THREADS + tid;
@@ -140,6 +142,7 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
     df_cp16(&ringB[q], B + j);
     df_cp16(&ringBl[q], Bl + j);
     df_cp4(&ringC[q], Cc + j);
+    ringJ[q] = j;
   };
 #pragma unroll
   for (int k = 0; k < DF_RING; ++k) {  // one group per entry (empty past the list)
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
     const int q = (k % DF_RING) * DF_THREADS + tid;
     const float4 Aj = ringA[q], Alj = ringAl[q], Bj = ringB[q], Blj = ringBl[q];
     const uint32_t cj = ringC[q];
-    ++npairs;  // every list entry is an exact neighbour (k_nbr_list applies the FP64 test)
+    const uint32_t jj = ringJ[q];
     // r / R: the high part (cell offset plus a difference of multiples of
     // 2^-23, below 2 in magnitude) is exact; the low parts round once
     df r[DIM];
@@ -194,7 +197,9 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
       e = __fmaf_rn(-r2.lo, yy.hi, e);
       inv = df_fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), e));
     }
-    const df rr = df_mul(r2, inv);  // |r| / R = q / 2
+    // q / 2 = |r| / (2h) = (|r| / R) (R / 2h); R / 2h = 1 unless the cells
+    // are widened for kept lists (then the product rounds once more)
+    const df rr = df_mul(df_mul(r2, inv), df{p.df_R_2h[0], p.df_R_2h[1]});
     df t = df_fast_two_sum(1.f, -rr.hi);
     t = df_fast_two_sum(t.hi, __fsub_rn(t.lo, rr.lo));  // 1 - q/2
     const df t2 = df_mul(t, t);
@@ -216,7 +221,21 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
       if (k + DF_RING + 1 < cnt) jn = __ldg(lst + (int64_t)(k + DF_RING + 1) * nf);
     }
     df_commit();
-    if (!(r2.hi > 0.f)) continue;
+    if (kept) {
+      // kept lists (radius 2h + delta): Algorithm 1's test. The double-float
+      // |r/R|^2 is within ~1e-13 of the FP64 one, so outside a band of 1e-12
+      // around (2h/R)^2 it decides as the FP64 test would; inside the band,
+      // and near r = 0, the FP64 test itself decides
+      const float dd = __fadd_rn(__fsub_rn(r2.hi, p.df_4h2_R2[0]), __fsub_rn(r2.lo, p.df_4h2_R2[1]));
+      bool nb;
+      if (dd < -1e-12f && r2.hi > 1e-6f) nb = true;
+      else if (dd > 1e-12f) nb = false;
+      else nb = exact_neighbor(p, s.x, n, i, jj);
+      if (!nb) continue;
+    } else if (!(r2.hi > 0.f)) {
+      continue;
+    }
+    ++npairs;  // an exact neighbour (exact lists: k_nbr_list applied the FP64 test)
 #pragma unroll
     for (int c = 0; c < DIM; ++c) gr[c] = df_mul(g, r[c]);
     // (U_j - U_i).r / |r|
@@ -387,11 +406,11 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
 }
 
 void launch_pair_df(const Params& p, const State& s, const Work& w, int64_t n, int64_t nf, int stage2,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool kept) {
   if (nf == 0) return;
   const unsigned blocks = (unsigned)div_up(nf, DF_THREADS);
-  if (p.dim == 2) k_pair_df<2><<<blocks, DF_THREADS, 0, st>>>(p, s, w, n, nf, stage2);
-  else k_pair_df<3><<<blocks, DF_THREADS, 0, st>>>(p, s, w, n, nf, stage2);
+  if (p.dim == 2) k_pair_df<2><<<blocks, DF_THREADS, 0, st>>>(p, s, w, n, nf, stage2, kept ? 1 : 0);
+  else k_pair_df<3><<<blocks, DF_THREADS, 0, st>>>(p, s, w, n, nf, stage2, kept ? 1 : 0);
 }
 
 }  // namespace wbsph

@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(DFP_THREADS) k_pack_df(Params p, State s, Work
   for (int k = 0; k < p.dim; ++k) {
     const double xk = s.x[k * n + i], uk = s.u[k * n + i];
     bad |= mx_nonfinite(xk) | mx_nonfinite(uk);
-    const double o = (xk - __ldg(org + ic[k])) * p.inv_two_h;  // 1 / R
+    const double o = (xk - __ldg(org + ic[k])) * p.inv_R;
     org += p.nc[k];
     off |= !(fabs(o) < 1.5);
     const double q = __dsub_rn(__dadd_rn(o, kRound23), kRound23);  // multiple of 2^-23

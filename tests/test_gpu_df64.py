@@ -184,8 +184,12 @@ def test_df64_wall_particles_only():
 
 
 def test_df64_rejects_grids_beyond_its_packed_cell_coordinates():
+    """More than 2048 cells on an axis (cells of 2h plus the kept lists'
+    skin, 3 CFL dx 0.3 / 1.3): refused with WBSPH_E_INVAL."""
     from paper_2608_22269_gb300 import wbsph
-    p = S.default_params(2, 0.01, 30.0, domain_min=[-5, -50, 0], domain_max=[5, 5, 1])
+    p = S.default_params(2, 0.01, 30.0, domain_min=[-5, -60, 0], domain_max=[5, 5, 1])
+    R = 2.0 * p["h_over_dx"] * p["dx"] + 3.0 * p["cfl"] * p["dx"] * 0.3 / 1.3
+    assert int(np.floor(65.0 / R)) + 1 > 2048
     sc = S.Scene(p, np.array([[0.1], [0.2]]), np.zeros((2, 1)), np.zeros(1), np.zeros(1, np.uint8),
                  np.zeros((2, 1)))
     sim = _sim(sc)
@@ -195,7 +199,9 @@ def test_df64_rejects_grids_beyond_its_packed_cell_coordinates():
 
 
 def test_df64_counts_the_same_pairs_as_fp64():
-    """Both passes walk the exact FP64 lists: the same pair count."""
+    """The double-float step keeps stage 1's lists (radius 2h + 3 dt U*) for
+    stage 2 and applies Algorithm 1's test in the pass; the FP64 step builds
+    exact lists per stage. Both count the same pairs."""
     from paper_2608_22269_gb300 import wbsph
     sc = SMALL[2][1]()
     a = _sim(sc)
@@ -204,3 +210,22 @@ def test_df64_counts_the_same_pairs_as_fp64():
     b.set_scene(sc)
     b.step(1)
     assert a.stats()["pairs"] == b.stats()["pairs"] > 0
+
+
+def test_df64_kept_lists_in_a_fast_flow():
+    """Particles thrown at 2.5 m/s (Mach 0.14) move furthest between the
+    stages; the kept lists and the pass's exact test still give the oracle's
+    fields within the FP64 bar after four steps."""
+    sc = S.jitter(S.dam_break_2d(dx=0.01, width=0.8, column=(0.4, 0.25)), 0.3, seed=3)
+    f = sc.type == 0
+    sc.u[0, f] = 2.5
+    sc.u[1, f] = 0.5 * np.random.default_rng(1).normal(size=f.sum())
+    sim = _sim(sc)
+    sim.step(4)
+    st = oracle.State(sc)
+    st.step(4)
+    sk = scales(sc.params, sc.water_height)
+    _check({"x": scaled_err(sim.get("x"), st.x, sk["x"]),
+            "u": scaled_err(sim.get("u"), st.u, sk["u"]),
+            "phi": scaled_err(sim.get("phi"), st.phi, sk["phi"]),
+            "dudt": scaled_err(sim.get("dudt")[:, f], st.dudt[:, f], sk["dudt"])}, "fast flow x4")
