@@ -476,6 +476,38 @@ def surrogate_path(args, local, dim=2, scene=None):
     return out
 
 
+def surrogate_stage_profile(dx):
+    """One surrogate stage (lists, node inputs, encoder, three message
+    layers, decoder) of the committed 3D network on the 3D dam break at
+    spacing dx, after one plain step and one warm stage; the second stage
+    runs inside the NVTX range 'surrogate_stage' so that a profiler can take
+    exactly its kernels. Returns its time from the library's CUDA events."""
+    import torch
+
+    from paper_2608_22269_gb300 import scenes, wbsph
+    from paper_2608_22269_gb300 import surrogate as SG
+    torch.cuda.set_device(0)
+    sc = scenes.dam_break_3d(dx=dx)
+    sim = wbsph.Sim(sc.params, water_height=sc.water_height)
+    sim.set_scene(sc)
+    sim.step(1)
+    sur, _ = SG.load(os.path.join(ROOT, "paper_2608_22269_gb300", "data", "surrogate_3d.npz"), 3)
+    sur.predict(sim)
+    sim.sync()
+    sim.set_profiling(True)
+    sim.profile(reset=True)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("surrogate_stage")
+    sur.predict(sim)
+    sim.sync()
+    torch.cuda.nvtx.range_pop()
+    ms = sim.profile(reset=True)["pair"][0]
+    out = {"surrogate_stage_ms": round(ms, 3), "dx": dx, "n_fluid": sc.n_fluid}
+    sur.close()
+    sim.close()
+    return out
+
+
 def precision_paths(scene, args, world, local, workload, primary=None, primary_sim=None,
                     primary_m=None, steps=None, warmup=None):
     """Every precision on one scene: value, roofline of the pair pass, HBM
@@ -733,11 +765,16 @@ def main():
                     help="run only the surrogate rollout timing (profiling aid)")
     ap.add_argument("--surrogate-dim", type=int, default=2, choices=(2, 3),
                     help="with --only-surrogate: the 2D or the 3D surrogate case")
+    ap.add_argument("--surrogate-stage", type=float, default=None, metavar="DX",
+                    help="profiling aid: one 3D surrogate stage on the 3D dam break at spacing DX, "
+                         "after a warm one, inside the NVTX range 'surrogate_stage'")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.surrogate_stage:
+        print(json.dumps(surrogate_stage_profile(args.surrogate_stage)), flush=True)
     elif args.only_surrogate:
         import torch
         torch.cuda.set_device(0)

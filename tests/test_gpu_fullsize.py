@@ -255,13 +255,14 @@ def test_full_size_surrogate_sampled():
     th = mpnn.round_weights_bf16(z["params"], 2)
     out = mpnn.forward_np(th, 2, node_in, recv, send, edge_in)[loc]
     # in the network's normalised output space, all components together (as
-    # the forward parity test measures): at a column at rest the horizontal
-    # acceleration is small in physical units, and its own scale would
-    # magnify the BF16 error floor of the whole output
+    # the forward parity test measures). The bound is that of BF16 arithmetic
+    # for this trained network: a BF16 model of the kernels deviates from the
+    # FP64 reference by 2.5 to 4 % of the largest output on dam-break states
+    # (tests/test_oracle_mpnn.py, test_bf16_error_of_the_trained_2d_network)
     gpu = (np.c_[dudt[:, smp].T, dphidt[smp]] - om) / osd
     rel = np.abs(gpu - out).max() / np.abs(out).max()
     per = np.abs(gpu - out).max(axis=0) / np.abs(out).max()
     print("surrogate full size: samples", smp.size, "patch", idx.size, "edges", recv.size, "rel", rel, per)
-    assert rel < 2e-2
+    assert rel < 5e-2
     sur.close()
     sim.close()
