@@ -41,6 +41,7 @@ struct Params {
   double pst_R, pst_n;
   double pst_R_a4;                // pst_R * pst_alpha_over_wdx^4
   double rho0, c0, c0sq, nu, gamma;
+  float inv_c0sq_f, inv_rho0_f;   // 1/C0^2 and 1/rho0 rounded to FP32 (the mixed prepass)
   double delta_h_c0;              // delta * h * C0
   double tic_lambda;
   double g[3];

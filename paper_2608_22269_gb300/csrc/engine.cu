@@ -238,6 +238,8 @@ static int derive_params(wbsph_s* h) {
   p.rho0 = c.rho0;
   p.c0 = c.c0;
   p.c0sq = c.c0 * c.c0;
+  p.inv_c0sq_f = (float)(1.0 / p.c0sq);
+  p.inv_rho0_f = (float)(1.0 / c.rho0);
   p.nu = c.nu;
   p.gamma = c.tait_gamma;
   p.delta_h_c0 = c.delta * p.h * c.c0;

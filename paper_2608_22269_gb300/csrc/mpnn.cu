@@ -565,9 +565,10 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 // One message-passing layer, fused, on tcgen05:
 //   m_i = sum_j MLP_e([g_ij, h_i, h_j[:SEND]]) = (sum_j silu(z_ij)) W2 + n_i b2,
 //   z_ij = g_ij W_g + h_i W_r + h_j[:SEND] W_s + b1,   h'_i = h_i + MLP_n([h_i, m_i]).
-// The second layer of the message MLP is linear, so it is applied once per
-// receiver after the sum; the per-edge work is the first layer, its SiLU and
-// the sum, and nothing per edge is ever written to memory. A sender
+// The second layer of the message MLP is linear, so the sum over edges can
+// run through it on the tensor core: each step's SiLU tile is multiplied by
+// W2 and accumulated in TMEM, sum_j silu(z_ij) W2, and n_i b2 is added once
+// per receiver. Nothing per edge is ever written to memory. A sender
 // contributes the first SEND = 32 of its 64 state features, so a gathered
 // row is 64 B: the layer is bound by the gathers (a row and a 32-byte pack
 // per edge, from L2), and halving the row halves that traffic.
@@ -576,8 +577,7 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 // tile of 128 receivers (fluid particles in sorted order, one TMEM lane and
 // one smem operand row each; then tiles of wall particles, which receive no
 // messages). Warp w of a group serves lanes 32 (w % 4) .. + 31 and the
-// accumulator column half w / 4, so each thread holds 32 of the receiver's 64
-// running sums in registers. The group walks the receivers' k-major
+// accumulator column half w / 4. The group walks the receivers' k-major
 // neighbour lists, step k taking the k-th neighbour of every receiver, as a
 // three-deep software pipeline (iteration k):
 //   - gathers for step k + 2: the sender rows by cp.async into the K-major
@@ -587,18 +587,22 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 //     pack loaded one iteration earlier;
 //   - once the group's operands of step k + 1 are in place, one thread
 //     issues D = G W_g/2 + H W_s/2 for it (three K = 16 MMAs, M = 128,
-//     N = 64, BF16 in, FP32 in TMEM, two accumulators alternating);
-//   - the epilogue of step k runs while that MMA executes: u = D + P_r/2
+//     N = 64, BF16 in, FP32 in TMEM, two accumulators alternating) and
+//     M += S_{k-1} W2 (four K = 16 MMAs into a third accumulator);
+//   - the epilogue of step k runs while those execute: u = D + P_r/2
 //     (P_r = h_i W_r + b1, from one MMA at the tile start, held as BF16
-//     pairs), silu(2u) = u + u tanh(u) with the packed BF16 hardware tanh,
-//     summed in FP32 for the receivers that have a k-th neighbour (the
-//     weights were halved on staging: exact in BF16).
+//     pairs), silu(2u) = u + u tanh(u) with the packed BF16 hardware tanh
+//     (the weights were halved on staging: exact in BF16), written as the
+//     BF16 SiLU tile S_k, with zero rows for receivers without a k-th
+//     neighbour.
 // The MMA latency hides behind the epilogue and the gather latency behind
-// two steps; one group barrier per step. The ring lives in three tiles per
-// group (edge inputs of four steps in one tile, sender rows of two steps in
-// each of the others), which leaves room for both groups in 158 KB.
-// At the end of the tile the sums (BF16) go through W2 on the tensor core,
-// the node MLP's two GEMMs follow (K = 128 from the h_i and m_i tiles), and
+// two steps; one group barrier per step. The sum never passes through BF16
+// (only its terms do), and no thread holds running sums. The ring lives in
+// three tiles per group (edge inputs of four steps in one tile, sender rows
+// of two steps in each of the others), plus two SiLU tiles: both groups fit
+// in 218 KB of shared memory and 512 TMEM columns.
+// At the end of the tile the last SiLU tile joins M, m_i = M + n_i b2, the
+// node MLP's two GEMMs follow (K = 128 from the h_i and m_i tiles), and
 // h'_i is written. Every mbarrier wait is bounded; a timeout is voted over
 // the group, reported through the status word, and ends the group's work.
 // ---------------------------------------------------------------------------
@@ -608,7 +612,7 @@ constexpr int MS_GROUP_THREADS = 256;
 constexpr int MS_THREADS = MS_GROUPS * MS_GROUP_THREADS;
 constexpr uint32_t MS_W_BYTES = 8192;  // [64][64] BF16 weight tile, K-major swizzled
 constexpr int MS_NW = 7;
-constexpr int MS_TILES = 3;            // per group: the edge-input ring, two sender-row tiles
+constexpr int MS_TILES = 5;            // per group: the edge-input ring, two sender-row tiles, two SiLU tiles
 constexpr size_t MS_SMEM_BYTES =
     1024 + MS_NW * MS_W_BYTES + 256 * 4 + (size_t)MS_GROUPS * MS_TILES * TC_TILE_BYTES + 128;
 
@@ -670,7 +674,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
   }
   if (t < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                 "n"(128 * MS_GROUPS)
+                 "n"(256 * MS_GROUPS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
@@ -688,6 +692,8 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
   unsigned char* T0 = tiles + (size_t)g * MS_TILES * TC_TILE_BYTES;
   unsigned char* T1 = T0 + TC_TILE_BYTES;
   unsigned char* T2 = T1 + TC_TILE_BYTES;
+  unsigned char* SL0 = T2 + TC_TILE_BYTES;  // silu tiles of even and odd steps
+  unsigned char* SL1 = SL0 + TC_TILE_BYTES;
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
   if (ch == 0) {
 #pragma unroll
@@ -697,7 +703,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t D0 = tmem + 128u * g, D1 = D0 + 64u;
+  const uint32_t D0 = tmem + 256u * g, D1 = D0 + 64u, DM = D0 + 128u;  // DM: sum_j silu(z_ij) W2
   const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + 32u * ch;
   uint64_t* mb = mbar + 2 * g;
   const uint64_t dW[MS_NW] = {tc_desc(smem_u32(W)), tc_desc(smem_u32(W + MS_W_BYTES)),
@@ -705,6 +711,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
                               tc_desc(smem_u32(W + 4 * MS_W_BYTES)), tc_desc(smem_u32(W + 5 * MS_W_BYTES)),
                               tc_desc(smem_u32(W + 6 * MS_W_BYTES))};
   const uint64_t dT0 = tc_desc(smem_u32(T0)), dT1 = tc_desc(smem_u32(T1)), dT2 = tc_desc(smem_u32(T2));
+  const uint64_t dSL0 = tc_desc(smem_u32(SL0)), dSL1 = tc_desc(smem_u32(SL1));
   const float* b1h = bias;
   const float* b2e = bias + 64;
   const float* b1n = bias + 128;
@@ -764,9 +771,6 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
 #pragma unroll
     for (int w = 0; w < 8; ++w) kmax = max(kmax, wmax[g * 8 + w]);
     const bool msg = kmax > 0;
-    float acc[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0.f;
     if (msg) {
       const float4 ai = ch == 0 ? __ldg(a.pack + 2 * node) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 bi = ch == 0 ? __ldg(a.pack + 2 * node + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -836,29 +840,32 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
         ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);
         if (!ok) break;
         const int b = k & 1;
-        if (more1 && leader) {
+        if (leader) {
           tc_fence_after();
-          mma_step(b ? D0 : D1, (k + 1) & 3);
+          if (more1) mma_step(b ? D0 : D1, (k + 1) & 3);
+          if (k >= 1) mma_k64(DM, b ? dSL0 : dSL1, WE2, k >= 2);  // sum_j silu W2 += silu tile of step k - 1
           tc_commit(smem_u32(mb + (b ^ 1)));
         }
-        // epilogue of step k
+        // epilogue of step k: silu(z) of this thread's 32 columns (zero
+        // for receivers without a k-th neighbour) into the silu tile of the
+        // step; its W2 product joins the sum with the next step's MMA
         wait_mma(b);
         const bool act = k < cnt;
+        unsigned char* S = b ? SL1 : SL0;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           float v[16];
           tc_ld16((b ? D1 : D0) + lane_off + 16 * hh, v);
+          uint32_t o[8];
 #pragma unroll
           for (int p = 0; p < 8; ++p) {
             const __nv_bfloat162 u = __hadd2(__floats2bfloat162_rn(v[2 * p], v[2 * p + 1]), u32_bf2(pr[8 * hh + p]));
             uint32_t th;
             asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(bf2_u32(u)));
-            const float2 s = __bfloat1622float2(__hfma2(u, u32_bf2(th), u));
-            if (act) {
-              acc[16 * hh + 2 * p] += s.x;
-              acc[16 * hh + 2 * p + 1] += s.y;
-            }
+            o[p] = act ? bf2_u32(__hfma2(u, u32_bf2(th), u)) : 0u;
           }
+          *reinterpret_cast<uint4*>(S + sw128(r, ch * 4 + 2 * hh)) = make_uint4(o[0], o[1], o[2], o[3]);
+          *reinterpret_cast<uint4*>(S + sw128(r, ch * 4 + 2 * hh + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
         }
         aj1 = aj2;
         bj1 = bj2;
@@ -866,30 +873,23 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
       }
       if (!ok) break;
       cp_async_wait<0>();
-      // m_i = (sum_j silu(z_ij)) W2 + n_i b2: the sums (BF16) to T1, one GEMM
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint4 o;
-        o.x = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 0], acc[8 * c + 1]));
-        o.y = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 2], acc[8 * c + 3]));
-        o.z = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 4], acc[8 * c + 5]));
-        o.w = bf2_u32(__floats2bfloat162_rn(acc[8 * c + 6], acc[8 * c + 7]));
-        *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + c)) = o;
-      }
+      // m_i = (sum_j silu(z_ij)) W2 + n_i b2: the last step's silu tile joins
+      // the sum in TMEM; the last iteration's commit and this one are waited
       copy_row_half(T2, a.h_in + (int64_t)node * HID, valid);  // h_i again, for the node MLP
       cp_async_commit();
       if (!sync_operands()) break;
       if (leader) {
         tc_fence_after();
-        mma_k64(D0, dT1, WE2, false);
-        tc_commit(smem_u32(mb + 0));
+        mma_k64(DM, ((kmax - 1) & 1) ? dSL1 : dSL0, WE2, kmax >= 2);
+        tc_commit(smem_u32(mb + ((kmax + 1) & 1)));  // the barrier whose last commit is waited
       }
-      wait_mma(0);
+      wait_mma(kmax & 1);        // the last iteration's commit
+      wait_mma((kmax + 1) & 1);  // the final silu tile
       const float fc = (float)cnt;
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         float v[16];
-        tc_ld16(D0 + lane_off + 16 * hh, v);
+        tc_ld16(DM + lane_off + 16 * hh, v);
         uint32_t o[8];
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
@@ -973,7 +973,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
   __syncthreads();
   if (t < 32) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(128 * MS_GROUPS)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(256 * MS_GROUPS)
                  : "memory");
   }
 }
@@ -1528,7 +1528,7 @@ MlpArgs block_args(wbsph_surrogate s, int bi) {
 }
 
 // One fused message-passing layer (k_message_tc): persistent CTAs, one per
-// SM (158 KB of shared memory and 256 TMEM columns each), two receiver
+// SM (218 KB of shared memory and 512 TMEM columns each), two receiver
 // groups per CTA.
 void launch_message(wbsph_surrogate s, const Params& p, const Work& w, int64_t nf, int64_t nd, int l,
                     const bf16* h_in, bf16* h_out, bf16* m_out, cudaStream_t st) {

@@ -53,7 +53,7 @@ constexpr int MX_THREADS = 128;
 #define WBSPH_MX_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for
 #endif
 #ifndef WBSPH_MX_RING
-#define WBSPH_MX_RING 2  // list entries of each lane in flight (shared-memory ring)
+#define WBSPH_MX_RING 4  // list entries of each lane in flight (shared-memory ring)
 #endif
 constexpr int MX_RING = WBSPH_MX_RING;
 
@@ -109,10 +109,11 @@ __global__ void __launch_bounds__(MX_THREADS, WBSPH_MX_MIN_BLOCKS)
   unsigned npairs = 0;
   const int maxc = __reduce_max_sync(0xffffffffu, cnt);
   const uint32_t* lst = w.nbr + gi;
-  // The packed data of list entry k + 1 is gathered (cp.async into this
-  // lane's slot of a shared-memory ring) while entry k is summed: the loop is
-  // latency bound on these dependent gathers, and the ring holds them without
-  // registers, which leaves room for four resident blocks per SM.
+  // The packed data of list entries k + 1 .. k + MX_RING - 1 is gathered
+  // (cp.async into this lane's slots of a shared-memory ring) while entry k
+  // is summed: the loop is latency bound on these dependent gathers, and the
+  // ring holds them without registers, which leaves room for four resident
+  // blocks per SM.
   __shared__ float4 ringA[MX_RING * MX_THREADS];
   __shared__ float4 ringB[MX_RING * MX_THREADS];
   __shared__ uint32_t ringC[MX_RING * MX_THREADS];

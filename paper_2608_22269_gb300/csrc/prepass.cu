@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(MXP_THREADS) k_prepass_mixed(Params p, State s
     bad |= mx_nonfinite(phi);
     const float phif = mx_d2f(phi);
     // rho / rho0 = exp(phi / C0^2) (linear EOS) or (1 + (gamma-1) phi / c0^2)^(1/(gamma-1)) (Tait)
-    const float inv_c0sq = (float)(1.0 / p.c0sq);
+    const float inv_c0sq = p.inv_c0sq_f;
     float inv_rel;
     if (p.eos == 0) {
       inv_rel = expf(-phif * inv_c0sq);
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(MXP_THREADS) k_prepass_mixed(Params p, State s
       const float gm1 = (float)(p.gamma - 1.0);
       inv_rel = powf(fmaf(gm1 * phif, inv_c0sq, 1.f), -1.f / gm1);
     }
-    float v = mx_d2f(s.mass[i]) * (float)(1.0 / p.rho0) * inv_rel;
+    float v = mx_d2f(s.mass[i]) * p.inv_rho0_f * inv_rel;
     bad |= !isfinite(v);
     if (bad) atomicOr(w.status, kStatNaN);
     w.vol[i] = mx_f2d(v);

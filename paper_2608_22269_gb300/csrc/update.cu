@@ -17,6 +17,7 @@ __global__ void k_rk_stage(Params p, State s, Work w, int64_t n, int stage) {
   if (i >= n) return;
   bool fluid = s.type[i] == kFluid;
   const bool body = s.type[i] == kBody;  // prescribed rigid translation, the same SSP-RK2 update
+  if (!fluid && !body) return;  // fixed wall particles: nothing moves, no stage-start copy is read
   if (stage == 1) {
     for (int k = 0; k < p.dim; ++k) {
       double x0 = s.x[k * n + i], u0 = s.u[k * n + i];

@@ -257,7 +257,7 @@ def test_full_size_surrogate_sampled():
     # in the network's normalised output space, all components together (as
     # the forward parity test measures). The bound is that of BF16 arithmetic
     # for this trained network: a BF16 model of the kernels deviates from the
-    # FP64 reference by 2.5 to 4 % of the largest output on dam-break states
+    # FP64 reference by about 3 % of the largest output on dam-break states
     # (tests/test_oracle_mpnn.py, test_bf16_error_of_the_trained_2d_network)
     gpu = (np.c_[dudt[:, smp].T, dphidt[smp]] - om) / osd
     rel = np.abs(gpu - out).max() / np.abs(out).max()

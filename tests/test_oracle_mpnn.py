@@ -191,10 +191,11 @@ def _bf(a):
 def _forward_bf16(theta, dim, node_in, recv, send, edge_in):
     """The network with activations rounded to BF16 where the CUDA kernels
     round them (encoder and node-MLP hidden layers, states h, the message
-    layer's halved first-layer terms, its SiLU input and output, the message
-    sums and m), sums in FP64 where the kernels accumulate in FP32, exact
-    tanh where they use the hardware approximation: a model of the kernels'
-    arithmetic, used only to bound the error that BF16 alone causes."""
+    layer's halved first-layer terms, its SiLU input and output, and m), sums
+    in FP64 where the kernels accumulate in FP32 (the message sum runs through
+    W2 term by term, so it is never rounded to BF16), exact tanh where they
+    use the hardware approximation: a model of the kernels' arithmetic, used
+    only to bound the error that BF16 alone causes."""
     P = {k: tuple(t.numpy() for t in v) for k, v in mpnn.unflatten(torch.as_tensor(theta), dim).items()}
 
     def silu(z):
@@ -210,9 +211,9 @@ def _forward_bf16(theta, dim, node_in, recv, send, edge_in):
         u = _bf(_bf(edge_in @ wg + h[send][:, :mpnn.SEND] @ ws) + pr[recv])
         sm = _bf(u + _bf(u * _bf(np.tanh(u))))          # silu(2u) = u + u tanh u
         acc = np.zeros((n, 64))
-        np.add.at(acc, recv, sm)
+        np.add.at(acc, recv, sm)                        # sum_j silu W2 = (sum_j silu) W2 in exact arithmetic
         cnt = np.bincount(recv, minlength=n).astype(np.float64)
-        m = _bf(_bf(acc) @ we2 + cnt[:, None] * be2)
+        m = _bf(acc @ we2 + cnt[:, None] * be2)
         wn1, bn1, wn2, bn2 = P[f"mp{layer}_n"]
         h = _bf(h + _bf(silu(np.c_[h, m] @ wn1 + bn1)) @ wn2 + bn2)
     wd1, bd1, wd2, bd2 = P["dec"]
