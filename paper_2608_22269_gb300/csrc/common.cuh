@@ -156,6 +156,8 @@ void launch_fill_neighbors(const Params& p, const State& s, const Work& w, int64
                            const int64_t* row_ptr_by_oid, int32_t* cols, cudaStream_t st);
 
 // ---- prepass.cu ----
+// U_max^2 of the fluid particles alone (after launch_prepass without volumes)
+void launch_umax(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st);
 // Dummy walls, then (volumes = true) V = m / rho and U_max of the stage.
 void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int64_t nd,
                     int stage2, cudaStream_t st, bool volumes = true);

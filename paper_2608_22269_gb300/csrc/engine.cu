@@ -1122,12 +1122,14 @@ static int check_pair(wbsph_s* h, wbsph_surrogate s) {
   return WBSPH_OK;
 }
 
-// Surrogate stage: dummy walls, volumes, [time step], surrogate rates.
+// Surrogate stage: dummy walls, U_max, [time step], surrogate rates. The
+// network reads no volumes, so none are formed.
 static int surrogate_stage(wbsph_s* h, wbsph_surrogate s, int stage2) {
   cudaStream_t st = h->stream;
   {
     ProfScope ps(h, WBSPH_K_PREPASS);
-    launch_prepass(h->P, h->A, h->W, h->n, h->nd, stage2, st);
+    launch_prepass(h->P, h->A, h->W, h->n, h->nd, stage2, st, false);
+    launch_umax(h->P, h->A, h->W, h->n, st);
   }
   if (!stage2) {
     ProfScope ps(h, WBSPH_K_OTHER);
@@ -1138,7 +1140,7 @@ static int surrogate_stage(wbsph_s* h, wbsph_surrogate s, int stage2) {
     ProfScope ps(h, WBSPH_K_PAIR);
     rc = surrogate_stage_rates(s, h->P, h->A, h->W, h->n, h->nf, st);
   }
-  // prepass (dummy update, volumes), time step, and the surrogate stage's
+  // prepass (dummy update, U_max), time step, and the surrogate stage's
   // kernels (network: neighbour lists, node inputs, encoder, one fused
   // kernel per layer, decoder, rates; frozen-rates control: one)
   h->launches += (h->n ? (h->nd ? 2 : 1) : 0) + (stage2 ? 0 : 1) + surrogate_stage_launches(s, h->nf);

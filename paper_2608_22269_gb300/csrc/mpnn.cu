@@ -211,12 +211,6 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, boo
   int n = valid ? 16 : 0;
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n));
 }
-// the same, cached in L1 (rows that neighbouring receivers gather again)
-__device__ __forceinline__ void cp_async16_ca(void* smem_dst, const void* gsrc, bool valid) {
-  unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  int n = valid ? 16 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n));
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
@@ -729,11 +723,14 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) cp_async16(T + sw128(r, ch * 4 + c), src + (ch * 4 + c) * 8, valid);
   };
-  // the sender's first SEND features (64 B) into ring slot s: two chunks per column half
+  // the sender's first SEND features (64 B) into ring slot s, all four chunks
+  // by the thread of column half 1 (the other thread forms the edge inputs)
   auto copy_send = [&](int s, const bf16* src, bool valid) {
     unsigned char* T = (s & 2) ? T2 : T1;
+    if (ch == 1) {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) cp_async16(T + sw128(r, 4 * (s & 1) + ch * 2 + c), src + (ch * 2 + c) * 8, valid);
+      for (int c = 0; c < 4; ++c) cp_async16(T + sw128(r, 4 * (s & 1) + c), src + c * 8, valid);
+    }
   };
   auto sync_operands = [&]() -> bool {  // smem operands written by the group -> tensor core
     cp_async_wait<0>();
@@ -1211,7 +1208,15 @@ __global__ void k_sg_nodes(Params p, State s, int64_t n, const float* mean, cons
   const double phip = s.phi[i] - phs;
   float v[FEAT] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int d = 0; d < p.dim; ++d) v[d] = (float)us[d];
-  v[p.dim] = (float)(eos_density(p, s.phi[i]) / p.rho0 - 1.0);
+  // rho/rho0 - 1 in FP32 (the input is rounded to BF16): expm1 of phi/C0^2
+  // (linear EOS) or the Tait power minus one
+  const float phf = (float)s.phi[i];
+  if (p.eos == 0) {
+    v[p.dim] = expm1f(phf * p.inv_c0sq_f);
+  } else {
+    const float gm1 = (float)(p.gamma - 1.0);
+    v[p.dim] = powf(fmaf(gm1 * phf, p.inv_c0sq_f, 1.f), 1.f / gm1) - 1.f;
+  }
   v[p.dim + 1] = (float)phip;
   for (int k = 0; k < p.dim + 2; ++k) v[k] = (v[k] - mean[k]) / stdv[k];
   v[p.dim + 2] = s.type[i] == kFluid ? 0.f : 1.f;
@@ -1490,16 +1495,22 @@ int ensure_edges(wbsph_surrogate s, int64_t E) {
   return ok ? WBSPH_OK : sfail(s, WBSPH_E_NOMEM, "surrogate edge buffers");
 }
 
+// Persistent grid of every block that fits at once (the tile loop strides by
+// the grid, so blocks beyond the resident ones would start late).
 template <int MODE, int KP, int NP>
 void launch_fwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
   size_t sm = FwdSmem<MODE, KP, NP>::bytes;
-  static bool attr = false;
-  if (!attr) {
+  static int resident = 0;
+  if (!resident) {
     cudaFuncSetAttribute(k_mlp_fwd<MODE, KP, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_fwd<MODE, KP, NP>, MLP_THREADS, sm);
+    resident = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 4);
   }
   int64_t tiles = div_up(max_rows > 0 ? max_rows : 1, TILE);
-  int grid = (int)(tiles < 152 * 4 ? tiles : 152 * 4);
+  int grid = (int)(tiles < resident ? tiles : resident);
   k_mlp_fwd<MODE, KP, NP><<<grid, MLP_THREADS, sm, st>>>(a);
 }
 

@@ -137,6 +137,32 @@ __global__ void __launch_bounds__(PRE_THREADS) k_volumes_umax(Params p, State s,
   }
 }
 
+// U_max^2 over fluid particles alone (surrogate stages, which need no
+// volumes); the block max and one atomic per block as in k_volumes_umax.
+__global__ void __launch_bounds__(PRE_THREADS) k_umax(Params p, State s, Work w, int64_t n) {
+  __shared__ unsigned long long red[PRE_THREADS / 32];
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double umax2 = 0.0;
+  if (i < n && s.type[i] == kFluid)
+    for (int k = 0; k < p.dim; ++k) umax2 += s.u[k * n + i] * s.u[k * n + i];
+  unsigned long long b = __double_as_longlong(umax2);
+  for (int off = 16; off; off >>= 1) {
+    unsigned long long o = __shfl_xor_sync(0xffffffffu, b, off);
+    b = o > b ? o : b;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = 0;
+    for (int k = 0; k < PRE_THREADS / 32; ++k) m = red[k] > m ? red[k] : m;
+    if (m) atomicMax(w.umax_bits, m);
+  }
+}
+
+void launch_umax(const Params& p, const State& s, const Work& w, int64_t n, cudaStream_t st) {
+  if (n > 0) k_umax<<<(unsigned)div_up(n, PRE_THREADS), PRE_THREADS, 0, st>>>(p, s, w, n);
+}
+
 void launch_prepass(const Params& p, const State& s, const Work& w, int64_t n, int64_t nd,
                     int stage2, cudaStream_t st, bool volumes) {
   cudaMemsetAsync(w.umax_bits, 0, sizeof(unsigned long long), st);
