@@ -135,6 +135,11 @@ struct MlpArgs {
   // forward outputs
   bf16* out_bf;              // [rows][64] (+ residual for EDGE/NODE)
   float* out_f;              // [rows][nout] (decoder)
+  // decoder of a stage: the de-normalised rates straight into the work arrays
+  // (row = fluid index, list[row] = sorted index), with out_f left unwritten
+  double* r_dudt; double* r_dphidt; double* r_shift;  // [dim][n], [n], [dim][n]
+  const float* r_mean; const float* r_std;            // target mean and std
+  int64_t r_n;                                        // particles (array stride)
   // backward
   const float* dout;         // [rows][nout] incoming gradient (EDGE/NODE/DIRECT: [rows][64])
   float* din_row;            // NODE: dh_in ([rows][64], = dout + dX[0:64])
@@ -354,7 +359,26 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpArgs a) {
       }
     }
     __syncwarp();
-    if (a.out_f) {  // decoder: FP32 outputs, few columns
+    if (a.r_dudt) {  // decoder of a stage: rates (shifting velocity zero), few columns
+      const int dim = a.nout - 1;
+#pragma unroll
+      for (int nt = 0; nt < NP / 8; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int r = m0 + g + (q >> 1) * 8, o = nt * 8 + 2 * t + (q & 1);
+          int64_t row = row0 + r;
+          if (row < rows && o < a.nout) {
+            const int64_t i = a.list[row];
+            const double v = (double)(acc2[nt][q] + B2[o]) * a.r_std[o] + a.r_mean[o];
+            if (o < dim) {
+              a.r_dudt[o * a.r_n + i] = v;
+              a.r_shift[o * a.r_n + i] = 0.0;
+            } else {
+              a.r_dphidt[i] = v;
+            }
+          }
+        }
+    } else if (a.out_f) {  // decoder: FP32 outputs, few columns
 #pragma unroll
       for (int nt = 0; nt < NP / 8; ++nt)
 #pragma unroll
@@ -625,6 +649,7 @@ struct MsgArgs {
   int dim, kg;              // kg = 2d + 2 edge inputs
   float inv_h, inv_su, inv_sphi;
   unsigned* status;
+  int* tile_ctr;            // tiles handed out beyond the first one of each group (zeroed per launch)
 };
 
 __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
@@ -637,6 +662,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
   uint64_t* mbar = reinterpret_cast<uint64_t*>(tiles + (size_t)MS_GROUPS * MS_TILES * TC_TILE_BYTES);
   int* wmax = reinterpret_cast<int*>(mbar + 2 * MS_GROUPS);  // per-warp neighbour-count maxima
   uint32_t* tslot = reinterpret_cast<uint32_t*>(wmax + 16);
+  int* tnext = reinterpret_cast<int*>(tslot + 1);  // each group's next tile
   const int t = threadIdx.x;
 
   // weights (K-major, 128-byte swizzle, [n][k] = W[k][n]); the first layer
@@ -753,7 +779,10 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
 
   const int64_t ntf = div_up(a.nf, 128), ntd = div_up(a.nd, 128), ntiles = ntf + ntd;
   const int64_t gstride = (int64_t)gridDim.x * MS_GROUPS;
-  for (int64_t tile = (int64_t)blockIdx.x * MS_GROUPS + g; ok && tile < ntiles; tile += gstride) {
+  // the first tile of a group by its index, the following ones from a global
+  // counter: fluid tiles (many steps) and wall tiles (none) even out over
+  // the groups
+  for (int64_t tile = (int64_t)blockIdx.x * MS_GROUPS + g; ok && tile < ntiles;) {
     const bool fluid = tile < ntf;
     const int64_t row0 = fluid ? tile * 128 : (tile - ntf) * 128;
     const int64_t gi = row0 + r;
@@ -961,8 +990,10 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
         ho[1] = make_uint4(o[4], o[5], o[6], o[7]);
       }
     }
+    if (leader) tnext[g] = (int)gstride + atomicAdd(a.tile_ctr, 1);
     tc_fence_before();
     ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);  // T2 and TMEM reads done before the next tile's writes
+    tile = tnext[g];
   }
   cp_async_wait<0>();
   if (!ok && (t % MS_GROUP_THREADS) == 0) atomicOr(a.status, (unsigned)kStatTimeout);
@@ -1297,20 +1328,6 @@ __global__ void k_sg_loss(int dim, Work w, int64_t n, int64_t nf, const float* o
   if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l / (double)(nf * no));
 }
 
-// de-normalised outputs -> stage rates (shifting velocity zero)
-__global__ void k_sg_rates(int dim, Work w, int64_t n, int64_t nf, const float* out, const float* tmean,
-                           const float* tstd) {
-  int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gi >= nf) return;
-  uint32_t i = w.fluid_list[gi];
-  int no = dim + 1;
-  for (int o = 0; o < dim; ++o) {
-    w.dudt[o * n + i] = (double)out[gi * no + o] * tstd[o] + tmean[o];
-    w.dushift[o * n + i] = 0.0;
-  }
-  w.dphidt[i] = (double)out[gi * no + dim] * tstd[dim] + tmean[dim];
-}
-
 // Control of the gain test: the rates of the last plain stage of a rollout,
 // kept per particle (by original id) and replayed in later stages.
 __global__ void k_frozen_store(int dim, Work w, const uint32_t* oid, int64_t n, int64_t nf, double* frozen,
@@ -1389,6 +1406,7 @@ struct wbsph_surrogate_s {
   // frozen-rates control: rates by original id
   double* frozen = nullptr;
   int64_t cap_frozen = 0;
+  int* tile_ctr = nullptr;  // dynamic tile counter of the fused layer
   std::string err;
 };
 
@@ -1566,10 +1584,12 @@ void launch_message(wbsph_surrogate s, const Params& p, const Work& w, int64_t n
   a.inv_su = 1.f / s->edge_std[0];
   a.inv_sphi = 1.f / s->edge_std[1];
   a.status = w.status;
+  a.tile_ctr = s->tile_ctr;
   const int64_t tiles = div_up(nf, 128) + div_up(nd, 128);
   if (tiles == 0) return;
   const int64_t want = div_up(tiles, MS_GROUPS);
   const int grid = (int)(want < sms ? want : sms);
+  cudaMemsetAsync(s->tile_ctr, 0, sizeof(int), st);
   k_message_tc<<<grid, MS_THREADS, MS_SMEM_BYTES, st>>>(a);
 }
 
@@ -1601,7 +1621,10 @@ int build_graph(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, in
 }
 
 // encoder, layers, decoder; with `train` the message sums of every layer are kept
-int forward(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, int64_t nf, bool train, cudaStream_t cs) {
+// to_rates: the decoder writes the stage rates (DU/Dt, Dphi/Dt, zero
+// shifting) into the work arrays instead of the normalised outputs
+int forward(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, int64_t nf, bool train, cudaStream_t cs,
+            bool to_rates = false) {
   const int L = s->layers;
   {  // node encoder (rows of 8 inputs)
     MlpArgs a = block_args(s, 0);
@@ -1616,6 +1639,10 @@ int forward(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, int64_
   {  // decoder over fluid rows
     MlpArgs a = block_args(s, 1 + 2 * L);
     a.rows = nf; a.in = s->hs[L]; a.list = w.fluid_list; a.out_f = s->out;
+    if (to_rates) {
+      a.r_dudt = w.dudt; a.r_dphidt = w.dphidt; a.r_shift = w.dushift;
+      a.r_mean = s->norm + 16; a.r_std = s->norm + 20; a.r_n = n;
+    }
     launch_fwd<MODE_LIST, 64, 16>(a, nf, cs);
   }
   return WBSPH_OK;
@@ -1667,10 +1694,7 @@ int surrogate_stage_rates(wbsph_surrogate s, const Params& p, const State& st, c
   int rc = ensure_nodes(s, n, nf);
   if (rc) return rc;
   node_inputs(s, p, st, n, cs);
-  if ((rc = forward(s, p, w, n, nf, false, cs))) return rc;
-  if (nf > 0)
-    k_sg_rates<<<(unsigned)div_up(nf, 128), 128, 0, cs>>>(p.dim, w, n, nf, s->out, s->norm + 16, s->norm + 20);
-  return WBSPH_OK;
+  return forward(s, p, w, n, nf, false, cs, true);
 }
 
 int surrogate_mode(wbsph_surrogate s) { return s->mode; }
@@ -1679,7 +1703,7 @@ int surrogate_mode(wbsph_surrogate s) { return s->mode; }
 int surrogate_stage_launches(wbsph_surrogate s, int64_t nf) {
   if (nf == 0) return 0;
   if (s->mode == WBSPH_SURROGATE_FROZEN) return 1;
-  return 1 + 1 + 1 + s->layers + 1 + 1;  // lists, node inputs, encoder, layers, decoder, rates
+  return 1 + 1 + 1 + s->layers + 1;  // lists, node inputs, encoder, layers, decoder (writes the rates)
 }
 
 // The rates of a plain stage of a rollout (fluid particles): kept by the
@@ -1774,7 +1798,7 @@ extern "C" int wbsph_surrogate_create(const wbsph_surrogate_config* c, wbsph_sur
   s->layers = c->layers;
   build_blocks(s);
   bool ok = dalloc(&s->p, s->np) && dalloc(&s->g, s->np) && dalloc(&s->m, s->np) && dalloc(&s->v, s->np) &&
-            dalloc(&s->pb, s->np) && dalloc(&s->norm, 32) && dalloc(&s->loss, 1);
+            dalloc(&s->pb, s->np) && dalloc(&s->norm, 32) && dalloc(&s->loss, 1) && dalloc(&s->tile_ctr, 1);
   if (!ok) {
     wbsph_surrogate_destroy(s);
     return WBSPH_E_NOMEM;
@@ -1798,6 +1822,7 @@ extern "C" void wbsph_surrogate_destroy(wbsph_surrogate s) {
   free_graph(s);
   dfree(s->p); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->pb); dfree(s->norm); dfree(s->loss);
   dfree(s->frozen);
+  dfree(s->tile_ctr);
   delete s;
 }
 
