@@ -111,7 +111,16 @@ __device__ __forceinline__ void ldsm_b2(uint32_t r[4], const bf16* s, int ld, in
   ldsm_x4(r, s + (n0 + (lane & 7) + ((lane >> 4) << 3)) * ld + k0 + (((lane >> 3) & 1) << 3));
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+// silu(z) = z sigmoid(z) = h + h tanh(h), h = z / 2, with the hardware tanh
+// approximation (one special-function operation instead of an exponential
+// and a division; absolute error ~1e-3 |z|, below the BF16 rounding of the
+// result)
+__device__ __forceinline__ float silu(float z) {
+  const float h = 0.5f * z;
+  float th;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(h));
+  return fmaf(h, th, h);
+}
 __device__ __forceinline__ float silu_grad(float z) {
   float s = 1.f / (1.f + __expf(-z));
   return s * (1.f + z * (1.f - s));
@@ -484,14 +493,6 @@ __global__ void k_wait_probe(unsigned* status, uint32_t limit) {
   if (!mbar_wait(mb, 0u, limit)) atomicOr(status, (unsigned)kStatTimeout);
 }
 
-// silu(z) = z sigmoid(z) = z (1 + tanh(z / 2)) / 2 with the hardware tanh
-// approximation (one special-function op instead of an exponential and a
-// reciprocal; absolute error ~1e-3 |z|, below the BF16 rounding of the result)
-__device__ __forceinline__ float silu_tanh(float z) {
-  float h = 0.5f * z, th;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(h));
-  return fmaf(h, th, h);
-}
 
 // ---------------------------------------------------------------------------
 // Edge inputs of the network for receiver i and sender j, from the per-node
@@ -955,7 +956,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
 #pragma unroll
       for (int p = 0; p < 8; ++p) {
         const int col = 32 * ch + 16 * hh + 2 * p;
-        o[p] = bf2_u32(__floats2bfloat162_rn(silu_tanh(v[2 * p] + b1n[col]), silu_tanh(v[2 * p + 1] + b1n[col + 1])));
+        o[p] = bf2_u32(__floats2bfloat162_rn(silu(v[2 * p] + b1n[col]), silu(v[2 * p + 1] + b1n[col + 1])));
       }
       // T1 (m_i) was read by the completed MMA: the hidden layer overwrites it
       *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + 2 * hh)) = make_uint4(o[0], o[1], o[2], o[3]);
