@@ -5,9 +5,11 @@
 //   keys -> radix sort -> gather (reorder) -> cell bounds -> fluid list   (Sec. 3)
 //   prepass: dummy walls (Sec. 2.4), volumes, U_max
 //   [s = 1] time step from U_max of y^n
-//   fused FP64 pair pass + epilogue (Eq. sph)
+//   neighbour lists, fused pair pass + epilogue (Eq. sph)
 //   RK stage update
-// with no host synchronisation inside a step.
+// with no host synchronisation inside a step. The mixed and double-float
+// paths sort once per step: stage 2 keeps stage 1's order, cells and lists
+// (built with radius 2h + 3 dt U*, on cells widened for that skin).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
