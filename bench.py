@@ -54,11 +54,11 @@ FP32_PEAK_TFLOPS = 72.4
 # FP32 instructions of one pair in the double-float pass, all terms on (each
 # FADD, FMUL or FFMA is one operation on the FP32 pipe; two-sum 6, fast
 # two-sum 3, double-float product 8, raw product 4, accumulate 11): offsets 9,
-# |r|^2 31, 1/|r| 17, |r| 8, 1 - q/2 7, kernel factor 24, velocity
-# differences 24, g r 24, normal velocity 39, potential terms 27, L 90, S 45,
-# M 135, K 33, C 53, D 15, Lambda 45, shifting 96 (3D)
-OPS_PER_PAIR_DF_3D = 722
-OPS_PER_PAIR_DF_2D = 488
+# |r|^2 31, 1/|r| 17, q/2 16 (|r|/R times R/2h), 1 - q/2 7, kernel factor
+# 12, velocity differences 24, g r 12, normal velocity 39, potential terms 23,
+# L 90, S 45, M 135, K 33, C 53, D 15, Lambda 45, shifting 76 (3D)
+OPS_PER_PAIR_DF_3D = 682
+OPS_PER_PAIR_DF_2D = 452
 # FP32 instruction rate of the FP32 pipe (one FFMA counts once)
 FP32_PEAK_TOPS = FP32_PEAK_TFLOPS / 2
 PRECISIONS = ("fp64", "mixed", "df64")

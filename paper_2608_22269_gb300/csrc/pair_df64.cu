@@ -202,12 +202,15 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
     const df rr = df_mul(df_mul(r2, inv), df{p.df_R_2h[0], p.df_R_2h[1]});
     df t = df_fast_two_sum(1.f, -rr.hi);
     t = df_fast_two_sum(t.hi, __fsub_rn(t.lo, rr.lo));  // 1 - q/2
-    const df t2 = df_mul(t, t);
-    const df t3 = df_mul(t2, t);
+    // products that only feed other products or running sums stay
+    // unrenormalised (df_mul_raw: the exact product of the high parts and the
+    // cross terms; the next product or sum absorbs the unnormalised low part)
+    const df t2 = df_mul_raw(t, t);
+    const df t3 = df_mul_raw(t2, t);
     df vj = {Bj.w, Blj.w};
     const bool jfluid = vj.hi > 0.f;
     if (!jfluid) vj = df_neg(vj);
-    const df g = df_mul(t3, vj);
+    const df g = df_mul_raw(t3, vj);
     df gr[DIM], du[DIM];
     du[0] = df_sub_raw({Bj.x, Blj.x}, ui[0]);
     du[1] = df_sub_raw({Bj.y, Blj.y}, ui[1]);
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
     }
     ++npairs;  // an exact neighbour (exact lists: k_nbr_list applied the FP64 test)
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) gr[c] = df_mul(g, r[c]);
+    for (int c = 0; c < DIM; ++c) gr[c] = df_mul_raw(g, r[c]);
     // (U_j - U_i).r / |r|
     df dun;
     {
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
       dun = df_mul(df_norm(pd), inv);
     }
     df rs = dphi;  // phi'_j - phi'_i - C0 (U_j - U_i).r/|r|: 2 (phi* - phi_i) of Eq. lfsover
-    df_acc(rs, df_neg(df_mul(c0, dun)));
+    df_acc(rs, df_neg(df_mul_raw(c0, dun)));
     if (DIM == 2) {
       df_acc(L[0], df_mul_raw(r[0], gr[0]));
       df_acc(L[1], df_mul_raw(r[0], gr[1]));
@@ -289,11 +292,11 @@ __global__ void __launch_bounds__(DF_THREADS, WBSPH_DF_MIN_BLOCKS)
       // W_ij / W(dx) = (alpha / W(dx)) v, v = t^4 (2q + 1), 2q + 1 = 4 |r|/R + 1
       const df q4 = df_two_sum(1.f, __fmul_rn(4.f, rr.hi));
       const df q21 = df_fast_two_sum(q4.hi, __fmaf_rn(4.f, rr.lo, q4.lo));
-      const df v = df_mul(df_mul(t2, t2), q21);
+      const df v = df_mul_raw(df_mul_raw(t2, t2), q21);
       df fm1;  // f - 1 = R_pst (W_ij / W(dx))^n
       if (pst4) {
-        const df v2 = df_mul(v, v);
-        fm1 = df_mul(df_mul(v2, v2), pra4);
+        const df v2 = df_mul_raw(v, v);
+        fm1 = df_mul_raw(df_mul_raw(v2, v2), pra4);
       } else {
         fm1 = df_from_double(p.pst_R * pow(p.pst_alpha_over_wdx * df_to_double(v), p.pst_n));
       }
