@@ -589,8 +589,9 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 // W2 and accumulated in TMEM, sum_j silu(z_ij) W2, and n_i b2 is added once
 // per receiver. Nothing per edge is ever written to memory. A sender
 // contributes the first SEND = 32 of its 64 state features, so a gathered
-// row is 64 B: the layer is bound by the gathers (a row and a 32-byte pack
-// per edge, from L2), and halving the row halves that traffic.
+// row is 64 B, plus a 32-byte pack per edge, from L2. The layer is bound by
+// its per-step chain (gathers, barrier, MMA, epilogue), not by bytes or by
+// the tensor core.
 //
 // A CTA runs MS_GROUPS independent groups of 256 threads; a group owns a
 // tile of 128 receivers (fluid particles in sorted order, one TMEM lane and
@@ -600,8 +601,9 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 // neighbour lists, step k taking the k-th neighbour of every receiver, as a
 // three-deep software pipeline (iteration k):
 //   - gathers for step k + 2: the sender rows by cp.async into the K-major
-//     128-byte-swizzled ring slot (k + 2) % 4, and the sender's FP32 pack
-//     (32 B: x, phi', U) into registers;
+//     128-byte-swizzled ring slot (k + 2) % 4 (by the row's column-half-1
+//     thread), and the sender's FP32 pack (32 B: x, phi', U) into registers
+//     (by the column-half-0 thread, which forms the edge inputs);
 //   - the 16-wide edge-input row of step k + 1 (K padded to 16) from the
 //     pack loaded one iteration earlier;
 //   - once the group's operands of step k + 1 are in place, one thread
@@ -622,8 +624,10 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 // in 218 KB of shared memory and 512 TMEM columns.
 // At the end of the tile the last SiLU tile joins M, m_i = M + n_i b2, the
 // node MLP's two GEMMs follow (K = 128 from the h_i and m_i tiles), and
-// h'_i is written. Every mbarrier wait is bounded; a timeout is voted over
-// the group, reported through the status word, and ends the group's work.
+// h'_i is written. A group's first tile is fixed by its index; the next
+// ones come from a global counter. Every mbarrier wait is bounded; a timeout
+// is voted over the group, reported through the status word, and ends the
+// group's work.
 // ---------------------------------------------------------------------------
 constexpr int SEND = 32;            // sender features in a message (the first SEND of h_j)
 constexpr int MS_GROUPS = 2;
