@@ -537,46 +537,6 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 32 FP32 columns of this thread's TMEM lane, issued without waiting; the
-// values may be used only after tc_wait_ld on the same registers (which ties
-// them to the wait)
-__device__ __forceinline__ void tc_ld32_nowait(uint32_t taddr, uint32_t r[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tc_wait_ld(uint32_t r[32]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-               :
-               : "memory");
-}
-
-// named barrier of one receiver group (THREADS threads), plain and with an AND vote
-template <int THREADS>
-__device__ __forceinline__ void group_bar(int id) {
-  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "n"(THREADS) : "memory");
-}
-template <int THREADS>
-__device__ __forceinline__ bool group_bar_and(int id, bool v) {
-  uint32_t res;
-  asm volatile(
-      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(res)
-      : "r"((uint32_t)v), "r"(id), "n"(THREADS)
-      : "memory");
-  return res != 0;
-}
-
 __device__ __forceinline__ uint32_t bf2_u32(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
 __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterpret_cast<__nv_bfloat162*>(&v); }
 
@@ -584,60 +544,53 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 // One message-passing layer, fused, on tcgen05:
 //   m_i = sum_j MLP_e([g_ij, h_i, h_j[:SEND]]) = (sum_j silu(z_ij)) W2 + n_i b2,
 //   z_ij = g_ij W_g + h_i W_r + h_j[:SEND] W_s + b1,   h'_i = h_i + MLP_n([h_i, m_i]).
-// The second layer of the message MLP is linear, so the sum over edges can
-// run through it on the tensor core: each step's SiLU tile is multiplied by
-// W2 and accumulated in TMEM, sum_j silu(z_ij) W2, and n_i b2 is added once
-// per receiver. Nothing per edge is ever written to memory. A sender
-// contributes the first SEND = 32 of its 64 state features, so a gathered
-// row is 64 B, plus a 32-byte pack per edge, from L2. The layer is bound by
-// its per-step chain (gathers, barrier, MMA, epilogue), not by bytes or by
-// the tensor core.
+// The second layer of the message MLP is linear, so it is applied once per
+// receiver, to the sum of the receiver's SiLU rows, rather than once per
+// edge. Nothing per edge is ever written to memory. A sender contributes
+// the first SEND = 32 of its 64 state features, so a gathered row is 64 B,
+// plus a 32-byte pack per edge, from L2.
 //
-// A CTA runs MS_GROUPS independent groups of 256 threads; a group owns a
-// tile of 128 receivers (fluid particles in sorted order, one TMEM lane and
-// one smem operand row each; then tiles of wall particles, which receive no
-// messages). Warp w of a group serves lanes 32 (w % 4) .. + 31 and the
-// accumulator column half w / 4. The group walks the receivers' k-major
-// neighbour lists, step k taking the k-th neighbour of every receiver, as a
-// three-deep software pipeline (iteration k):
-//   - gathers for step k + 2: the sender rows by cp.async into the K-major
-//     128-byte-swizzled ring slot (k + 2) % 4 (by the row's column-half-1
-//     thread), and the sender's FP32 pack (32 B: x, phi', U) into registers
-//     (by the column-half-0 thread, which forms the edge inputs);
-//   - the 16-wide edge-input row of step k + 1 (K padded to 16) from the
-//     pack loaded one iteration earlier;
-//   - once the group's operands of step k + 1 are in place, one thread
-//     issues D = G W_g/2 + H W_s/2 for it (three K = 16 MMAs, M = 128,
-//     N = 64, BF16 in, FP32 in TMEM, two accumulators alternating) and
-//     M += S_{k-1} W2 (four K = 16 MMAs into a third accumulator);
-//   - the epilogue of step k runs while those execute: u = D + P_r/2
-//     (P_r = h_i W_r + b1, from one MMA at the tile start, held as BF16
-//     pairs), silu(2u) = u + u tanh(u) with the packed BF16 hardware tanh
-//     (the weights were halved on staging: exact in BF16), written as the
-//     BF16 SiLU tile S_k, with zero rows for receivers without a k-th
-//     neighbour.
-// The MMA latency hides behind the epilogue and the gather latency behind
-// two steps; one group barrier per step. The sum never passes through BF16
-// (only its terms do), and no thread holds running sums. The ring lives in
-// three tiles per group (edge inputs of four steps in one tile, sender rows
-// of two steps in each of the others), plus two SiLU tiles: both groups fit
-// in 218 KB of shared memory and 512 TMEM columns.
-// At the end of the tile the last SiLU tile joins M, m_i = M + n_i b2, the
-// node MLP's two GEMMs follow (K = 128 from the h_i and m_i tiles), and
-// h'_i is written. A group's first tile is fixed by its index; the next
-// ones come from a global counter. Every mbarrier wait is bounded; a timeout
-// is voted over the group, reported through the status word, and ends the
-// group's work.
+// A tile is 128 receivers (fluid particles in sorted order, one TMEM lane and
+// one shared-memory operand row each; then tiles of wall particles, which
+// receive no messages). Step k of a tile takes the k-th entry of every
+// receiver's k-major neighbour list. One CTA per SM, split into roles that
+// hand off through mbarriers (no CTA-wide barrier inside the loop):
+//   - gather: two groups of four warps, for the even and the odd steps;
+//     thread r fills row r. Per step, the 16-wide edge-input row goes into a
+//     slot of an 8-deep operand ring. It is formed from the FP32 packs of
+//     receiver and sender, prefetched two of the group's steps ahead (the
+//     neighbour index three). The sender's first SEND features go into the
+//     slot by cp.async. A slot is announced on its "full" barrier once the
+//     thread's copies into it have landed. The announcement of a copy group
+//     waits until three newer groups are in flight, so that no thread blocks
+//     on a fresh copy. Group 0 also writes the tile record (counts, node ids,
+//     longest list, tile index), group 1 the tile's h_i rows.
+//   - MMA: one thread. Per tile it issues P_r / 2 = h_i W_r / 2. Per step it
+//     issues D = G W_g/2 + H W_s/2 into a ring of four TMEM accumulators:
+//     three K = 16 MMAs, M = 128, N = 64, BF16 in, FP32 out. Per tile it
+//     then issues the W2 product of the summed SiLU rows and the node MLP's
+//     two GEMMs.
+//   - epilogue: eight warps; thread (r, ch) holds TMEM lane r and the
+//     accumulator column half ch.
+//       Per step: u = D + (P_r + b1)/2 in BF16, then silu(2u) = u + u tanh(u)
+//       with the packed BF16 hardware tanh (the first-layer weights were
+//       halved on staging, exactly, in BF16). The result is added in FP32
+//       to 32 running sums; receivers without a k-th neighbour add nothing.
+//       At the end of the tile: the sums go to shared memory as BF16 high
+//       and low parts (s = hi + lo to about 2^-17 relative), and the tensor
+//       core forms (hi + lo) W2. m_i = that + n_i b2 is rounded to BF16.
+//       Then z = [h_i, m_i] W1 + b1, the hidden layer silu(z), and
+//       h'_i = h_i + silu(z) W2 + b2.
+// The terms of a receiver's message sum are its BF16-rounded SiLU rows; the
+// sum is rounded once, at the end. A CTA's first tile is fixed by its index;
+// the following ones come from a counter shared by all CTAs, so that CTAs
+// that drew long fluid tiles take fewer. Every mbarrier wait is bounded. A
+// timeout in any role ends all roles and is reported through the status
+// word.
 // ---------------------------------------------------------------------------
-constexpr int SEND = 32;            // sender features in a message (the first SEND of h_j)
-constexpr int MS_GROUPS = 2;
-constexpr int MS_GROUP_THREADS = 256;
-constexpr int MS_THREADS = MS_GROUPS * MS_GROUP_THREADS;
+constexpr int SEND = 32;               // sender features in a message (the first SEND of h_j)
 constexpr uint32_t MS_W_BYTES = 8192;  // [64][64] BF16 weight tile, K-major swizzled
 constexpr int MS_NW = 7;
-constexpr int MS_TILES = 5;            // per group: the edge-input ring, two sender-row tiles, two SiLU tiles
-constexpr size_t MS_SMEM_BYTES =
-    1024 + MS_NW * MS_W_BYTES + 256 * 4 + (size_t)MS_GROUPS * MS_TILES * TC_TILE_BYTES + 128;
 
 struct MsgArgs {
   int64_t nf, nd;
@@ -654,8 +607,60 @@ struct MsgArgs {
   int dim, kg;              // kg = 2d + 2 edge inputs
   float inv_h, inv_su, inv_sphi;
   unsigned* status;
-  int* tile_ctr;            // tiles handed out beyond the first one of each group (zeroed per launch)
+  int* tile_ctr;            // tiles handed out beyond each CTA's first (zeroed per launch)
 };
+
+constexpr int MS_NS = 8;                       // operand ring slots
+constexpr int MS_ND = 4;                       // step accumulators in TMEM
+constexpr int MS_GATHER = 128, MS_EPI = 256;   // threads of one gather group, of the epilogue
+constexpr int MS_THREADS = 2 * MS_GATHER + MS_EPI + 32;
+constexpr int MS_NTILES = 2 + 4 + 2 + 2;       // edge inputs, sender rows, h_i (x2), sum hi / m_i / hidden, sum lo
+constexpr int MS_INFO = 128 * 2 + 4;           // ints per tile record: cnt[128], node[128], kmax, tile
+// mbarriers (full: the producer is done with it; free: the consumer is)
+enum {
+  WB_SFULL = 0, WB_SFREE = WB_SFULL + MS_NS,                   // operand ring slots: gather -> MMA
+  WB_DFULL = WB_SFREE + MS_NS, WB_DFREE = WB_DFULL + MS_ND,    // step accumulators: MMA -> epilogue
+  WB_HFULL = WB_DFREE + MS_ND, WB_HFREE = WB_HFULL + 2,         // h_i tiles, by tile parity
+  WB_IFULL = WB_HFREE + 2, WB_IFREE = WB_IFULL + 2,             // tile records, by tile parity
+  WB_PR = WB_IFREE + 2, WB_HL = WB_PR + 1, WB_DM = WB_HL + 1,   // P_r; summed SiLU rows; their W2 product
+  WB_M = WB_DM + 1, WB_Z = WB_M + 1, WB_ZT = WB_Z + 1, WB_O = WB_ZT + 1,  // node MLP operands and products
+  WB_TILE = WB_O + 1,                                           // the tile index, within gather group 0
+  WB_FIN = WB_TILE + 2, WB_COUNT = WB_FIN + 1                   // the last MMA, before TMEM is released
+};
+constexpr size_t MS_SMEM_BYTES = 1024 + MS_NW * MS_W_BYTES + 256 * 4 + (size_t)MS_NTILES * TC_TILE_BYTES +
+                                 2 * MS_INFO * 4 + WB_COUNT * 8 + 16;
+
+__device__ __forceinline__ void ms_arrive(uint32_t mbar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+// bounded wait on the phase `parity`; gives up early once another role has aborted
+__device__ __forceinline__ bool ms_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 1023u) == 1023u && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+// the same wait, decided for the whole warp (the roles that use it run
+// warp-collective instructions after it, so a warp never splits on a timeout)
+__device__ __forceinline__ bool ms_wait_warp(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
+  return __all_sync(0xffffffffu, ms_wait(mbar, parity, abort_flag));
+}
+
+// (a0, a1) += the two BF16 halves of w (low, high), FP32 adds with BF16 operands
+__device__ __forceinline__ void add_bf16x2_f32(float& a0, float& a1, uint32_t w) {
+  asm("{\n.reg .b16 lo, hi;\nmov.b32 {lo, hi}, %2;\nadd.rn.f32.bf16 %0, lo, %0;\nadd.rn.f32.bf16 %1, hi, %1;\n}\n"
+      : "+f"(a0), "+f"(a1)
+      : "r"(w));
+}
 
 __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
   extern __shared__ unsigned char ms_raw[];
@@ -663,12 +668,16 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
   enum { WG = 0, WS = 1, WR = 2, WE2 = 3, WH = 4, WM = 5, WN2 = 6 };
   unsigned char* W = base;
   float* bias = reinterpret_cast<float*>(W + MS_NW * MS_W_BYTES);  // b1/2 | b2 (edge) | b1 | b2 (node)
-  unsigned char* tiles = reinterpret_cast<unsigned char*>(bias + 256);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tiles + (size_t)MS_GROUPS * MS_TILES * TC_TILE_BYTES);
-  int* wmax = reinterpret_cast<int*>(mbar + 2 * MS_GROUPS);  // per-warp neighbour-count maxima
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(wmax + 16);
-  int* tnext = reinterpret_cast<int*>(tslot + 1);  // each group's next tile
-  const int t = threadIdx.x;
+  unsigned char* TG = reinterpret_cast<unsigned char*>(bias + 256);  // edge inputs: slots 0-3, 4-7
+  unsigned char* TH = TG + 2 * TC_TILE_BYTES;    // sender rows, two slots per tile
+  unsigned char* THI = TH + 4 * TC_TILE_BYTES;   // h_i rows, by tile parity
+  unsigned char* TM = THI + 2 * TC_TILE_BYTES;   // sum_j silu (high part), m_i, the node MLP's hidden layer
+  unsigned char* TL = TM + TC_TILE_BYTES;        // sum_j silu (low part)
+  int* info = reinterpret_cast<int*>(TL + TC_TILE_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(info + 2 * MS_INFO);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + WB_COUNT);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
   // weights (K-major, 128-byte swizzle, [n][k] = W[k][n]); the first layer
   // of the edge MLP halved; its input rows: kg edge inputs, h_i, h_j
@@ -692,322 +701,427 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
     bias[128 + t] = a.wn_b1[t];
     bias[192 + t] = a.wn_b2[t];
   }
+  // the K padding chunk of every edge-input slot stays zero
+  for (int idx = t; idx < 128 * MS_NS; idx += MS_THREADS) {
+    const int r = idx / MS_NS, s = idx % MS_NS;
+    *reinterpret_cast<uint4*>(TG + (s >> 2) * TC_TILE_BYTES + sw128(r, 2 * (s & 3) + 1)) =
+        make_uint4(0u, 0u, 0u, 0u);
+  }
   if (t == 0) {
-    for (int k = 0; k < 2 * MS_GROUPS; ++k)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + k)) : "memory");
+    *abort_flag = 0;
+    auto init = [&](int i, uint32_t count) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar + i)), "r"(count) : "memory");
+    };
+    for (int s = 0; s < MS_NS; ++s) { init(WB_SFULL + s, MS_GATHER); init(WB_SFREE + s, 1); }
+    for (int d = 0; d < MS_ND; ++d) { init(WB_DFULL + d, 1); init(WB_DFREE + d, MS_EPI); }
+    for (int i = 0; i < 2; ++i) {
+      init(WB_HFULL + i, MS_GATHER); init(WB_HFREE + i, MS_EPI);
+      init(WB_IFULL + i, MS_GATHER); init(WB_IFREE + i, MS_EPI);
+    }
+    init(WB_PR, 1); init(WB_HL, MS_EPI); init(WB_DM, 1);
+    init(WB_M, MS_EPI); init(WB_Z, 1); init(WB_ZT, MS_EPI); init(WB_O, 1);
+    init(WB_TILE, 1); init(WB_TILE + 1, 1); init(WB_FIN, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (t < 32) {
+  if (warp == 16) {  // the MMA warp owns the TMEM allocation
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                 "n"(256 * MS_GROUPS)
+                 "n"(512)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-  }
-
-  const int g = t / MS_GROUP_THREADS, lt = t % MS_GROUP_THREADS, lw = lt >> 5, lane = t & 31;
-  const int q = lw & 3, ch = lw >> 2;   // lane quarter, column half
-  const int r = q * 32 + lane;          // receiver row = TMEM lane
-  const int bar_id = 1 + g;
-  const bool leader = lt == 0;
-  // Per group: T0 holds the edge-input rows of four neighbour steps (step s
-  // in K block s % 4: 16-byte chunk 2 (s % 4), and chunk 2 (s % 4) + 1 zero,
-  // the K padding); T1 and T2 hold the sender rows of steps s % 4 = 0, 1 and
-  // 2, 3 (32 features = chunks 4 (s % 2) .. 4 (s % 2) + 3). Outside the
-  // neighbour loop T1 and T2 serve as 64-wide row tiles.
-  unsigned char* T0 = tiles + (size_t)g * MS_TILES * TC_TILE_BYTES;
-  unsigned char* T1 = T0 + TC_TILE_BYTES;
-  unsigned char* T2 = T1 + TC_TILE_BYTES;
-  unsigned char* SL0 = T2 + TC_TILE_BYTES;  // silu tiles of even and odd steps
-  unsigned char* SL1 = SL0 + TC_TILE_BYTES;
-  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-  if (ch == 0) {
-#pragma unroll
-    for (int s = 0; s < 4; ++s) *reinterpret_cast<uint4*>(T0 + sw128(r, 2 * s + 1)) = zero4;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t D0 = tmem + 256u * g, D1 = D0 + 64u, DM = D0 + 128u;  // DM: sum_j silu(z_ij) W2
-  const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + 32u * ch;
-  uint64_t* mb = mbar + 2 * g;
-  const uint64_t dW[MS_NW] = {tc_desc(smem_u32(W)), tc_desc(smem_u32(W + MS_W_BYTES)),
-                              tc_desc(smem_u32(W + 2 * MS_W_BYTES)), tc_desc(smem_u32(W + 3 * MS_W_BYTES)),
-                              tc_desc(smem_u32(W + 4 * MS_W_BYTES)), tc_desc(smem_u32(W + 5 * MS_W_BYTES)),
-                              tc_desc(smem_u32(W + 6 * MS_W_BYTES))};
-  const uint64_t dT0 = tc_desc(smem_u32(T0)), dT1 = tc_desc(smem_u32(T1)), dT2 = tc_desc(smem_u32(T2));
-  const uint64_t dSL0 = tc_desc(smem_u32(SL0)), dSL1 = tc_desc(smem_u32(SL1));
-  const float* b1h = bias;
-  const float* b2e = bias + 64;
-  const float* b1n = bias + 128;
-  const float* b2n = bias + 192;
-  uint32_t ph = 0u;  // parity of the next phase of mb[0], mb[1]
-  bool ok = true;
-  auto wait_mma = [&](int b) {
-    const bool w_ok = mbar_wait(smem_u32(mb + b), (ph >> b) & 1u);
-    ph ^= 1u << b;
-    ok = ok && w_ok;
-    tc_fence_after();
-  };
-  // this thread's half of a 64-wide BF16 row: 16-byte chunks ch*4 .. ch*4+3 of row r
-  auto copy_row_half = [&](unsigned char* T, const bf16* src, bool valid) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) cp_async16(T + sw128(r, ch * 4 + c), src + (ch * 4 + c) * 8, valid);
-  };
-  // the sender's first SEND features (64 B) into ring slot s, all four chunks
-  // by the thread of column half 1 (the other thread forms the edge inputs)
-  auto copy_send = [&](int s, const bf16* src, bool valid) {
-    unsigned char* T = (s & 2) ? T2 : T1;
-    if (ch == 1) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) cp_async16(T + sw128(r, 4 * (s & 1) + c), src + c * 8, valid);
-    }
-  };
-  auto sync_operands = [&]() -> bool {  // smem operands written by the group -> tensor core
-    cp_async_wait<0>();
-    fence_async_smem();
-    tc_fence_before();
-    ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);
-    return ok;
-  };
-  auto mma_k64 = [&](uint32_t d, uint64_t dA, int w, bool accumulate) {
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) tc_mma(d, dA + 2 * kk, dW[w] + 2 * kk, (accumulate || kk > 0) ? 1u : 0u);
-  };
-  // D = G W_g/2 + H W_s/2 of ring slot s
-  auto mma_step = [&](uint32_t d, int s) {
-    tc_mma(d, dT0 + 2 * s, dW[WG], 0u);
-    const uint64_t dA = ((s & 2) ? dT2 : dT1) + 4 * (s & 1);
-#pragma unroll
-    for (int kk = 0; kk < SEND / 16; ++kk) tc_mma(d, dA + 2 * kk, dW[WS] + 2 * kk, 1u);
-  };
-
+  // TMEM columns: step accumulators 0-255, (sum_j silu) W2 256, P_r 320, node MLP z 384 and output 448
+  const uint32_t TD = tmem, TDM = tmem + 256u, TPR = tmem + 320u, TZ = tmem + 384u, TO = tmem + 448u;
+  auto B = [&](int i) { return smem_u32(bar + i); };
   const int64_t ntf = div_up(a.nf, 128), ntd = div_up(a.nd, 128), ntiles = ntf + ntd;
-  const int64_t gstride = (int64_t)gridDim.x * MS_GROUPS;
-  // the first tile of a group by its index, the following ones from a global
-  // counter: fluid tiles (many steps) and wall tiles (none) even out over
-  // the groups
-  for (int64_t tile = (int64_t)blockIdx.x * MS_GROUPS + g; ok && tile < ntiles;) {
-    const bool fluid = tile < ntf;
-    const int64_t row0 = fluid ? tile * 128 : (tile - ntf) * 128;
-    const int64_t gi = row0 + r;
-    const bool valid = gi < (fluid ? a.nf : a.nd);
-    const uint32_t node = valid ? __ldg((fluid ? a.fluid_list : a.dummy_list) + gi) : 0u;
-    const int cnt = (valid && fluid) ? (int)__ldg(a.nbr_cnt + gi) : 0;
-    // longest list of the tile
-    const int wm = __reduce_max_sync(0xffffffffu, cnt);
-    if (lane == 0) wmax[g * 8 + lw] = wm;
-    group_bar<MS_GROUP_THREADS>(bar_id);
-    int kmax = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) kmax = max(kmax, wmax[g * 8 + w]);
-    const bool msg = kmax > 0;
-    if (msg) {
-      const float4 ai = ch == 0 ? __ldg(a.pack + 2 * node) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 bi = ch == 0 ? __ldg(a.pack + 2 * node + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-      // h_i rows (for P_r) into T2, the sender rows of steps 0 and 1 into slots 0 and 1
-      const uint32_t j0 = cnt > 0 ? __ldg(a.nbr + gi) : 0u;
-      const uint32_t j1 = cnt > 1 ? __ldg(a.nbr + a.nf + gi) : 0u;
-      uint32_t jn2 = cnt > 2 ? __ldg(a.nbr + 2 * a.nf + gi) : 0u;
-      copy_row_half(T2, a.h_in + (int64_t)node * HID, valid);
-      copy_send(0, a.h_in + (int64_t)j0 * HID, cnt > 0);
-      copy_send(1, a.h_in + (int64_t)j1 * HID, cnt > 1);
-      cp_async_commit();
-      float4 aj1 = make_float4(0.f, 0.f, 0.f, 0.f), bj1 = aj1;
-      if (ch == 0) {
-        uint4 f = zero4;
-        if (cnt > 0)
-          f = edge_features(a.dim, ai, bi, __ldg(a.pack + 2 * j0), __ldg(a.pack + 2 * j0 + 1), a.inv_h, a.inv_su,
-                            a.inv_sphi);
-        *reinterpret_cast<uint4*>(T0 + sw128(r, 0)) = f;
-        if (cnt > 1) {
-          aj1 = __ldg(a.pack + 2 * j1);
-          bj1 = __ldg(a.pack + 2 * j1 + 1);
-        }
-      }
-      if (!sync_operands()) break;
-      if (leader) {
-        tc_fence_after();
-        mma_k64(D1, dT2, WR, false);  // P_r / 2 = h_i W_r / 2
-        tc_commit(smem_u32(mb + 1));
-        mma_step(D0, 0);
-        tc_commit(smem_u32(mb + 0));
-      }
-      wait_mma(1);
-      uint32_t pr[16];  // (P_r + b1) / 2 of this thread's 32 columns, BF16 pairs
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        float v[16];
-        tc_ld16(D1 + lane_off + 16 * hh, v);
-#pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const int col = 32 * ch + 16 * hh + 2 * p;
-          pr[8 * hh + p] = bf2_u32(__floats2bfloat162_rn(v[2 * p] + b1h[col], v[2 * p + 1] + b1h[col + 1]));
-        }
-      }
-      // Step k: the sender rows of step k + 2 go out, the edge inputs of step
-      // k + 1 are formed, and once every thread's operands of step k + 1 are
-      // in place its MMA is issued; the epilogue of step k then runs while
-      // that MMA executes.
-      for (int k = 0; k < kmax; ++k) {
-        const bool more1 = k + 1 < kmax, act1 = k + 1 < cnt;
-        const bool more2 = k + 2 < kmax, act2 = k + 2 < cnt;
-        if (more2) copy_send((k + 2) & 3, a.h_in + (int64_t)jn2 * HID, act2);
-        cp_async_commit();
-        float4 aj2 = make_float4(0.f, 0.f, 0.f, 0.f), bj2 = aj2;
-        if (ch == 0 && act2) {
-          aj2 = __ldg(a.pack + 2 * jn2);
-          bj2 = __ldg(a.pack + 2 * jn2 + 1);
-        }
-        const uint32_t jn3 = k + 3 < cnt ? __ldg(a.nbr + (int64_t)(k + 3) * a.nf + gi) : 0u;
-        if (more1 && ch == 0) {
-          uint4 f = zero4;
-          if (act1) f = edge_features(a.dim, ai, bi, aj1, bj1, a.inv_h, a.inv_su, a.inv_sphi);
-          *reinterpret_cast<uint4*>(T0 + sw128(r, 2 * ((k + 1) & 3))) = f;
-        }
-        cp_async_wait<1>();  // the rows of step k + 1 (issued one step ago)
+
+  if (warp < 8) {
+    // ---- gather: two groups of four warps, even and odd steps; thread r of
+    // a group fills row r of its steps' operand slots. Group 0 also writes
+    // the tile record, group 1 the h_i rows. A slot (or h_i tile) is
+    // announced once this thread's copies into it have landed: the
+    // announcement of a copy group waits until QD newer groups are in
+    // flight, so that no thread blocks on a fresh copy. A thread's
+    // unannounced groups then span fewer than 2 QD < MS_NS steps, so the MMA
+    // never waits for a slot whose announcement waits for a slot to free.
+    constexpr int QD = 3;
+    const int grp = warp >> 2, r = t & 127;
+    uint32_t q0 = 0, q1 = 0, q2 = 0;  // barriers of the copy groups in flight, oldest first
+    int nq = 0;
+    auto announce_oldest = [&]() {
+      ms_arrive(q0);
+      q0 = q1;
+      q1 = q2;
+      --nq;
+    };
+    auto push = [&](uint32_t mb) {  // after the commit of the group that fills mb
+      if (nq == QD) {
+        cp_async_wait<QD>();
         fence_async_smem();
-        tc_fence_before();
-        ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);
-        if (!ok) break;
-        const int b = k & 1;
-        if (leader) {
-          tc_fence_after();
-          if (more1) mma_step(b ? D0 : D1, (k + 1) & 3);
-          if (k >= 1) mma_k64(DM, b ? dSL0 : dSL1, WE2, k >= 2);  // sum_j silu W2 += silu tile of step k - 1
-          tc_commit(smem_u32(mb + (b ^ 1)));
+        announce_oldest();
+      }
+      (nq == 0 ? q0 : nq == 1 ? q1 : q2) = mb;
+      ++nq;
+    };
+    auto flush_to = [&](int keep) {  // announce all but the newest `keep` groups
+      if (nq <= keep) return;
+      if (keep <= 0) cp_async_wait<0>();
+      else if (keep == 1) cp_async_wait<1>();
+      else cp_async_wait<2>();
+      fence_async_smem();
+      while (nq > keep) announce_oldest();
+    };
+    uint32_t gs0 = 0;      // index of the tile's first step in this CTA
+    int prev_groups = QD;  // copy groups of this thread in the previous tile
+    int64_t next = blockIdx.x;  // thread 0: this CTA's next tile (the first by the CTA's index,
+                                // then from a counter shared by all CTAs)
+    bool ok = true;
+    for (int it = 0;; ++it) {
+      const int tb = it & 1;
+      int* inf = info + tb * MS_INFO;
+      // this thread's groups of tile it - 2 are announced before waiting for its end
+      flush_to(min(prev_groups, QD));
+      int groups = 0;
+      int64_t tile, gi;
+      int cnt, kmax;
+      uint32_t node;
+      bool valid;
+      if (grp == 0) {
+        if (!(ok = ms_wait_warp(B(WB_IFREE + tb), ((it >> 1) & 1) ^ 1, abort_flag))) break;
+        if (t == 0) {
+          inf[257] = (int)(next < ntiles ? next : ntiles);
+          ms_arrive(B(WB_TILE + tb));
+          if (next < ntiles) next = (int64_t)gridDim.x + atomicAdd(a.tile_ctr, 1);
         }
-        // epilogue of step k: silu(z) of this thread's 32 columns (zero
-        // for receivers without a k-th neighbour) into the silu tile of the
-        // step; its W2 product joins the sum with the next step's MMA
-        wait_mma(b);
-        const bool act = k < cnt;
-        unsigned char* S = b ? SL1 : SL0;
+        if (!(ok = ms_wait_warp(B(WB_TILE + tb), (it >> 1) & 1, abort_flag))) break;
+        tile = inf[257];
+        if (tile >= ntiles) {  // the end, for every role
+          ms_arrive(B(WB_IFULL + tb));
+          break;
+        }
+        const bool fluid = tile < ntf;
+        const int64_t row0 = (fluid ? tile : tile - ntf) * 128, rows = fluid ? a.nf : a.nd;
+        gi = row0 + r;
+        valid = gi < rows;
+        node = valid ? __ldg((fluid ? a.fluid_list : a.dummy_list) + gi) : 0u;
+        cnt = (valid && fluid) ? (int)__ldg(a.nbr_cnt + gi) : 0;
+        // the tile's longest list
+        int km = 0;
+        if (fluid) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int64_t g2 = row0 + 32 * c + lane;
+            if (g2 < rows) km = max(km, (int)__ldg(a.nbr_cnt + g2));
+          }
+        }
+        kmax = __reduce_max_sync(0xffffffffu, km);
+        inf[r] = cnt;
+        inf[128 + r] = (int)node;
+        if (r == 0) inf[256] = kmax;
+        ms_arrive(B(WB_IFULL + tb));
+      } else {
+        if (!(ok = ms_wait_warp(B(WB_IFULL + tb), (it >> 1) & 1, abort_flag))) break;
+        tile = inf[257];
+        if (tile >= ntiles) break;
+        cnt = inf[r];
+        node = (uint32_t)inf[128 + r];
+        kmax = inf[256];
+        const bool fluid = tile < ntf;
+        gi = (fluid ? tile : tile - ntf) * 128 + r;
+        valid = gi < (fluid ? a.nf : a.nd);
+        if (!(ok = ms_wait_warp(B(WB_HFREE + tb), ((it >> 1) & 1) ^ 1, abort_flag))) break;
+        unsigned char* T = THI + tb * TC_TILE_BYTES;
+        const bf16* src = a.h_in + (int64_t)node * HID;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) cp_async16(T + sw128(r, c), src + c * 8, valid);
+        cp_async_commit();
+        push(B(WB_HFULL + tb));
+        groups = 1;
+      }
+      // this group's tile steps k0, k0 + 2, ...
+      const int k0 = (int)((gs0 ^ (uint32_t)grp) & 1u);
+      if (k0 < kmax) {
+        const float4 ai = __ldg(a.pack + 2 * node), bi = __ldg(a.pack + 2 * node + 1);
+        // neighbour indices three of the group's steps ahead, packs two
+        uint32_t j0 = k0 < cnt ? __ldg(a.nbr + (int64_t)k0 * a.nf + gi) : 0u;
+        uint32_t j1 = k0 + 2 < cnt ? __ldg(a.nbr + (int64_t)(k0 + 2) * a.nf + gi) : 0u;
+        uint32_t j2 = k0 + 4 < cnt ? __ldg(a.nbr + (int64_t)(k0 + 4) * a.nf + gi) : 0u;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 aj0 = z4, bj0 = z4, aj1 = z4, bj1 = z4;
+        if (k0 < cnt) { aj0 = __ldg(a.pack + 2 * j0); bj0 = __ldg(a.pack + 2 * j0 + 1); }
+        if (k0 + 2 < cnt) { aj1 = __ldg(a.pack + 2 * j1); bj1 = __ldg(a.pack + 2 * j1 + 1); }
+        for (int k = k0; k < kmax; k += 2) {
+          const uint32_t gs = gs0 + (uint32_t)k;
+          const int s = (int)(gs % MS_NS);
+          const uint32_t j3 = k + 6 < cnt ? __ldg(a.nbr + (int64_t)(k + 6) * a.nf + gi) : 0u;
+          float4 aj2 = z4, bj2 = z4;
+          if (k + 4 < cnt) { aj2 = __ldg(a.pack + 2 * j2); bj2 = __ldg(a.pack + 2 * j2 + 1); }
+          const bool act = k < cnt;
+          uint4 f = make_uint4(0u, 0u, 0u, 0u);
+          if (act) f = edge_features(a.dim, ai, bi, aj0, bj0, a.inv_h, a.inv_su, a.inv_sphi);
+          if (!(ok = ms_wait_warp(B(WB_SFREE + s), (uint32_t)((gs / MS_NS) & 1) ^ 1u, abort_flag))) break;
+          *reinterpret_cast<uint4*>(TG + (s >> 2) * TC_TILE_BYTES + sw128(r, 2 * (s & 3))) = f;
+          {
+            unsigned char* T = TH + (s >> 1) * TC_TILE_BYTES;
+            const bf16* src = a.h_in + (int64_t)j0 * HID;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cp_async16(T + sw128(r, 4 * (s & 1) + c), src + c * 8, act);
+          }
+          cp_async_commit();
+          push(B(WB_SFULL + s));
+          ++groups;
+          j0 = j1; j1 = j2; j2 = j3;
+          aj0 = aj1; bj0 = bj1; aj1 = aj2; bj1 = bj2;
+        }
+        if (!ok) break;
+      }
+      gs0 += (uint32_t)kmax;
+      prev_groups = groups;
+    }
+    if (ok) flush_to(0);
+    cp_async_wait<0>();
+  } else if (warp < 16) {
+    // ---- epilogue: row r (TMEM lane), column half ch ----
+    const int ew = warp - 8;
+    const int q = ew & 3, ch = ew >> 2, r = q * 32 + lane;
+    const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + 32u * ch;
+    const float* b1h = bias;
+    const float* b2e = bias + 64;
+    const float* b1n = bias + 128;
+    const float* b2n = bias + 192;
+    uint32_t gs = 0;
+    int nmsg = 0;
+    bool ok = true;
+    for (int it = 0;; ++it) {
+      const int tb = it & 1;
+      if (!(ok = ms_wait_warp(B(WB_IFULL + tb), (it >> 1) & 1, abort_flag))) break;
+      const int* inf = info + tb * MS_INFO;
+      const int64_t tile = inf[257];
+      if (tile >= ntiles) break;
+      const int cnt = inf[r];
+      const uint32_t node = (uint32_t)inf[128 + r];
+      const int kmax = inf[256];
+      const bool fluid = tile < ntf;
+      const bool valid = (fluid ? tile : tile - ntf) * 128 + r < (fluid ? a.nf : a.nd);
+      if (kmax > 0) {
+        if (!(ok = ms_wait_warp(B(WB_PR), nmsg & 1, abort_flag))) break;
+        tc_fence_after();
+        uint32_t pr[16];  // (P_r + b1) / 2 of this thread's 32 columns, BF16 pairs
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           float v[16];
-          tc_ld16((b ? D1 : D0) + lane_off + 16 * hh, v);
+          tc_ld16(TPR + lane_off + 16 * hh, v);
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const int col = 32 * ch + 16 * hh + 2 * p;
+            pr[8 * hh + p] = bf2_u32(__floats2bfloat162_rn(v[2 * p] + b1h[col], v[2 * p + 1] + b1h[col + 1]));
+          }
+        }
+        float acc[32];  // sum_j silu(z_ij) of this thread's 32 columns
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+        for (int k = 0; k < kmax; ++k, ++gs) {
+          const int d = (int)(gs % MS_ND);
+          if (!(ok = ms_wait_warp(B(WB_DFULL + d), (uint32_t)((gs / MS_ND) & 1), abort_flag))) break;
+          tc_fence_after();
+          const bool act = k < cnt;
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            float v[16];
+            tc_ld16(TD + 64u * d + lane_off + 16 * hh, v);
+            if (hh == 1) {
+              tc_fence_before();
+              ms_arrive(B(WB_DFREE + d));
+            }
+            if (act) {
+#pragma unroll
+              for (int p = 0; p < 8; ++p) {
+                const __nv_bfloat162 u =
+                    __hadd2(__floats2bfloat162_rn(v[2 * p], v[2 * p + 1]), u32_bf2(pr[8 * hh + p]));
+                uint32_t th;
+                asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(bf2_u32(u)));
+                add_bf16x2_f32(acc[16 * hh + 2 * p], acc[16 * hh + 2 * p + 1], bf2_u32(__hfma2(u, u32_bf2(th), u)));
+              }
+            }
+          }
+        }
+        if (!ok) break;
+        // the sums as BF16 high and low parts, the operands of their W2 product
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t oh[8], ol[8];
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const float s0 = acc[16 * hh + 2 * p], s1 = acc[16 * hh + 2 * p + 1];
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(s0, s1);
+            const float2 hf = __bfloat1622float2(h2);
+            oh[p] = bf2_u32(h2);
+            ol[p] = bf2_u32(__floats2bfloat162_rn(s0 - hf.x, s1 - hf.y));
+          }
+          *reinterpret_cast<uint4*>(TM + sw128(r, ch * 4 + 2 * hh)) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
+          *reinterpret_cast<uint4*>(TM + sw128(r, ch * 4 + 2 * hh + 1)) = make_uint4(oh[4], oh[5], oh[6], oh[7]);
+          *reinterpret_cast<uint4*>(TL + sw128(r, ch * 4 + 2 * hh)) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+          *reinterpret_cast<uint4*>(TL + sw128(r, ch * 4 + 2 * hh + 1)) = make_uint4(ol[4], ol[5], ol[6], ol[7]);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        ms_arrive(B(WB_HL));
+        // m_i = (sum_j silu(z_ij)) W2 + n_i b2
+        if (!(ok = ms_wait_warp(B(WB_DM), nmsg & 1, abort_flag))) break;
+        tc_fence_after();
+        ++nmsg;
+        const float fc = (float)cnt;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          float v[16];
+          tc_ld16(TDM + lane_off + 16 * hh, v);
           uint32_t o[8];
 #pragma unroll
           for (int p = 0; p < 8; ++p) {
-            const __nv_bfloat162 u = __hadd2(__floats2bfloat162_rn(v[2 * p], v[2 * p + 1]), u32_bf2(pr[8 * hh + p]));
-            uint32_t th;
-            asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(bf2_u32(u)));
-            o[p] = act ? bf2_u32(__hfma2(u, u32_bf2(th), u)) : 0u;
+            const int col = 32 * ch + 16 * hh + 2 * p;
+            o[p] = bf2_u32(
+                __floats2bfloat162_rn(fmaf(fc, b2e[col], v[2 * p]), fmaf(fc, b2e[col + 1], v[2 * p + 1])));
           }
-          *reinterpret_cast<uint4*>(S + sw128(r, ch * 4 + 2 * hh)) = make_uint4(o[0], o[1], o[2], o[3]);
-          *reinterpret_cast<uint4*>(S + sw128(r, ch * 4 + 2 * hh + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+          const uint4 o0 = make_uint4(o[0], o[1], o[2], o[3]), o1 = make_uint4(o[4], o[5], o[6], o[7]);
+          *reinterpret_cast<uint4*>(TM + sw128(r, ch * 4 + 2 * hh)) = o0;
+          *reinterpret_cast<uint4*>(TM + sw128(r, ch * 4 + 2 * hh + 1)) = o1;
+          if (a.m_out && valid) {
+            uint4* mo = reinterpret_cast<uint4*>(a.m_out + (int64_t)node * HID + 32 * ch + 16 * hh);
+            mo[0] = o0;
+            mo[1] = o1;
+          }
         }
-        aj1 = aj2;
-        bj1 = bj2;
-        jn2 = jn3;
+      } else {  // no messages: m_i = 0
+#pragma unroll
+        for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(TM + sw128(r, ch * 4 + c)) = make_uint4(0u, 0u, 0u, 0u);
       }
-      if (!ok) break;
-      cp_async_wait<0>();
-      // m_i = (sum_j silu(z_ij)) W2 + n_i b2: the last step's silu tile joins
-      // the sum in TMEM; the last iteration's commit and this one are waited
-      copy_row_half(T2, a.h_in + (int64_t)node * HID, valid);  // h_i again, for the node MLP
-      cp_async_commit();
-      if (!sync_operands()) break;
-      if (leader) {
-        tc_fence_after();
-        mma_k64(DM, ((kmax - 1) & 1) ? dSL1 : dSL0, WE2, kmax >= 2);
-        tc_commit(smem_u32(mb + ((kmax + 1) & 1)));  // the barrier whose last commit is waited
-      }
-      wait_mma(kmax & 1);        // the last iteration's commit
-      wait_mma((kmax + 1) & 1);  // the final silu tile
-      const float fc = (float)cnt;
+      fence_async_smem();
+      tc_fence_before();
+      ms_arrive(B(WB_M));
+      // node MLP: z = [h_i, m_i] W1 + b1, hidden layer silu(z) into TM
+      if (!(ok = ms_wait_warp(B(WB_Z), it & 1, abort_flag))) break;
+      tc_fence_after();
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         float v[16];
-        tc_ld16(DM + lane_off + 16 * hh, v);
+        tc_ld16(TZ + lane_off + 16 * hh, v);
         uint32_t o[8];
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
           const int col = 32 * ch + 16 * hh + 2 * p;
-          o[p] = bf2_u32(__floats2bfloat162_rn(fmaf(fc, b2e[col], v[2 * p]), fmaf(fc, b2e[col + 1], v[2 * p + 1])));
+          o[p] = bf2_u32(__floats2bfloat162_rn(silu(v[2 * p] + b1n[col]), silu(v[2 * p + 1] + b1n[col + 1])));
         }
-        const uint4 o0 = make_uint4(o[0], o[1], o[2], o[3]), o1 = make_uint4(o[4], o[5], o[6], o[7]);
-        // T1 (the sums) was read by the completed MMA: m_i overwrites it
-        *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + 2 * hh)) = o0;
-        *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + 2 * hh + 1)) = o1;
-        if (a.m_out && valid) {
-          uint4* mo = reinterpret_cast<uint4*>(a.m_out + (int64_t)node * HID + 32 * ch + 16 * hh);
-          mo[0] = o0;
-          mo[1] = o1;
-        }
+        *reinterpret_cast<uint4*>(TM + sw128(r, ch * 4 + 2 * hh)) = make_uint4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<uint4*>(TM + sw128(r, ch * 4 + 2 * hh + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
       }
-    } else {  // no messages: m = 0 into T1, h_i into T2
-#pragma unroll
-      for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + c)) = zero4;
-      copy_row_half(T2, a.h_in + (int64_t)node * HID, valid);
-      cp_async_commit();
-    }
-    // node MLP: z = [h_i, m_i] W1 + b1 (K = 128), h' = h_i + silu(z) W2 + b2
-    if (!sync_operands()) break;
-    if (leader) {
+      fence_async_smem();
+      tc_fence_before();
+      ms_arrive(B(WB_ZT));
+      // h'_i = h_i + silu(z) W2 + b2
+      if (!(ok = ms_wait_warp(B(WB_O), it & 1, abort_flag))) break;
       tc_fence_after();
-      mma_k64(D1, dT2, WH, false);
-      mma_k64(D1, dT1, WM, true);
-      tc_commit(smem_u32(mb + 1));
-    }
-    wait_mma(1);
+      const unsigned char* HI = THI + tb * TC_TILE_BYTES;
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      float v[16];
-      tc_ld16(D1 + lane_off + 16 * hh, v);
-      uint32_t o[8];
+      for (int hh = 0; hh < 2; ++hh) {
+        float v[16];
+        tc_ld16(TO + lane_off + 16 * hh, v);
+        uint32_t o[8];
 #pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        const int col = 32 * ch + 16 * hh + 2 * p;
-        o[p] = bf2_u32(__floats2bfloat162_rn(silu(v[2 * p] + b1n[col]), silu(v[2 * p + 1] + b1n[col + 1])));
-      }
-      // T1 (m_i) was read by the completed MMA: the hidden layer overwrites it
-      *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + 2 * hh)) = make_uint4(o[0], o[1], o[2], o[3]);
-      *reinterpret_cast<uint4*>(T1 + sw128(r, ch * 4 + 2 * hh + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
-    }
-    if (!sync_operands()) break;
-    if (leader) {
-      tc_fence_after();
-      mma_k64(D0, dT1, WN2, false);
-      tc_commit(smem_u32(mb + 0));
-    }
-    wait_mma(0);
+        for (int cc = 0; cc < 2; ++cc) {
+          const uint4 hv = *reinterpret_cast<const uint4*>(HI + sw128(r, ch * 4 + 2 * hh + cc));
+          const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      float v[16];
-      tc_ld16(D0 + lane_off + 16 * hh, v);
-      uint32_t o[8];
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const uint4 hv = *reinterpret_cast<const uint4*>(T2 + sw128(r, ch * 4 + 2 * hh + cc));
-        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const int pp = 4 * cc + p, col = 32 * ch + 16 * hh + 2 * pp;
-          const float2 hf = __bfloat1622float2(u32_bf2(hw[p]));
-          o[pp] = bf2_u32(__floats2bfloat162_rn(hf.x + v[2 * pp] + b2n[col], hf.y + v[2 * pp + 1] + b2n[col + 1]));
+          for (int p = 0; p < 4; ++p) {
+            const int pp = 4 * cc + p, col = 32 * ch + 16 * hh + 2 * pp;
+            const float2 hf = __bfloat1622float2(u32_bf2(hw[p]));
+            o[pp] = bf2_u32(
+                __floats2bfloat162_rn(hf.x + v[2 * pp] + b2n[col], hf.y + v[2 * pp + 1] + b2n[col + 1]));
+          }
+        }
+        if (valid) {
+          uint4* ho = reinterpret_cast<uint4*>(a.h_out + (int64_t)node * HID + 32 * ch + 16 * hh);
+          ho[0] = make_uint4(o[0], o[1], o[2], o[3]);
+          ho[1] = make_uint4(o[4], o[5], o[6], o[7]);
         }
       }
-      if (valid) {
-        uint4* ho = reinterpret_cast<uint4*>(a.h_out + (int64_t)node * HID + 32 * ch + 16 * hh);
-        ho[0] = make_uint4(o[0], o[1], o[2], o[3]);
-        ho[1] = make_uint4(o[4], o[5], o[6], o[7]);
-      }
+      tc_fence_before();
+      ms_arrive(B(WB_HFREE + tb));
+      ms_arrive(B(WB_IFREE + tb));
     }
-    if (leader) tnext[g] = (int)gstride + atomicAdd(a.tile_ctr, 1);
-    tc_fence_before();
-    ok = group_bar_and<MS_GROUP_THREADS>(bar_id, ok);  // T2 and TMEM reads done before the next tile's writes
-    tile = tnext[g];
+  } else if (lane == 0) {
+    // ---- the MMA thread ----
+    const uint64_t dW[MS_NW] = {tc_desc(smem_u32(W)), tc_desc(smem_u32(W + MS_W_BYTES)),
+                                tc_desc(smem_u32(W + 2 * MS_W_BYTES)), tc_desc(smem_u32(W + 3 * MS_W_BYTES)),
+                                tc_desc(smem_u32(W + 4 * MS_W_BYTES)), tc_desc(smem_u32(W + 5 * MS_W_BYTES)),
+                                tc_desc(smem_u32(W + 6 * MS_W_BYTES))};
+    auto mma_k64 = [&](uint32_t d, uint64_t dA, int w, bool accumulate) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) tc_mma(d, dA + 2 * kk, dW[w] + 2 * kk, (accumulate || kk > 0) ? 1u : 0u);
+    };
+    const uint64_t dTG = tc_desc(smem_u32(TG)), dTH = tc_desc(smem_u32(TH));
+    const uint64_t dTHI = tc_desc(smem_u32(THI)), dTM = tc_desc(smem_u32(TM));
+    constexpr uint64_t tile16 = TC_TILE_BYTES >> 4;  // descriptor address step of one tile
+    const uint64_t dTL = tc_desc(smem_u32(TL));
+    uint32_t gs = 0;
+    int it = 0, nmsg = 0;
+    bool ok = true;
+    for (;; ++it) {
+      const int tb = it & 1;
+      if (!(ok = ms_wait(B(WB_IFULL + tb), (it >> 1) & 1, abort_flag))) break;
+      if (info[tb * MS_INFO + 257] >= ntiles) break;
+      const int kmax = info[tb * MS_INFO + 256];
+      if (!(ok = ms_wait(B(WB_HFULL + tb), (it >> 1) & 1, abort_flag))) break;
+      tc_fence_after();
+      const uint64_t dHI = dTHI + tb * tile16;
+      if (kmax > 0) {
+        mma_k64(TPR, dHI, WR, false);  // P_r / 2 = h_i W_r / 2
+        tc_commit(B(WB_PR));
+        for (int k = 0; k < kmax; ++k, ++gs) {
+          const int s = (int)(gs % MS_NS), d = (int)(gs % MS_ND);
+          if (!(ok = ms_wait(B(WB_SFULL + s), (uint32_t)((gs / MS_NS) & 1), abort_flag))) break;
+          if (!(ok = ms_wait(B(WB_DFREE + d), (uint32_t)((gs / MS_ND) & 1) ^ 1u, abort_flag))) break;
+          tc_fence_after();
+          const uint32_t dd = TD + 64u * d;
+          tc_mma(dd, dTG + (s >> 2) * tile16 + 2 * (s & 3), dW[WG], 0u);
+          const uint64_t dA = dTH + (s >> 1) * tile16 + 4 * (s & 1);
+#pragma unroll
+          for (int kk = 0; kk < SEND / 16; ++kk) tc_mma(dd, dA + 2 * kk, dW[WS] + 2 * kk, 1u);
+          tc_commit(B(WB_DFULL + d));
+          tc_commit(B(WB_SFREE + s));
+        }
+        if (!ok) break;
+        // (sum_j silu) W2 from the high and low parts
+        if (!(ok = ms_wait(B(WB_HL), nmsg & 1, abort_flag))) break;
+        ++nmsg;
+        tc_fence_after();
+        mma_k64(TDM, dTM, WE2, false);
+        mma_k64(TDM, dTL, WE2, true);
+        tc_commit(B(WB_DM));
+      }
+      // node MLP: z = [h_i, m_i] W1 + b1, then the output layer
+      if (!(ok = ms_wait(B(WB_M), it & 1, abort_flag))) break;
+      tc_fence_after();
+      mma_k64(TZ, dHI, WH, false);
+      mma_k64(TZ, dTM, WM, true);
+      tc_commit(B(WB_Z));
+      if (!(ok = ms_wait(B(WB_ZT), it & 1, abort_flag))) break;
+      tc_fence_after();
+      mma_k64(TO, dTM, WN2, false);
+      tc_commit(B(WB_O));
+    }
+    // every MMA issued has completed before TMEM is released
+    tc_commit(B(WB_FIN));
+    mbar_wait(B(WB_FIN), 0u);
   }
-  cp_async_wait<0>();
-  if (!ok && (t % MS_GROUP_THREADS) == 0) atomicOr(a.status, (unsigned)kStatTimeout);
   tc_fence_before();
   __syncthreads();
-  if (t < 32) {
+  if (t == 0 && *abort_flag) atomicOr(a.status, (unsigned)kStatTimeout);
+  if (warp == 16) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(256 * MS_GROUPS)
-                 : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(512) : "memory");
   }
 }
 
@@ -1520,8 +1634,9 @@ int ensure_edges(wbsph_surrogate s, int64_t E) {
 
 // Persistent grid of every block that fits at once (the tile loop strides by
 // the grid, so blocks beyond the resident ones would start late).
+// returns the launch's error, which a later runtime call could otherwise consume
 template <int MODE, int KP, int NP>
-void launch_fwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
+cudaError_t launch_fwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
   size_t sm = FwdSmem<MODE, KP, NP>::bytes;
   static int resident = 0;
   if (!resident) {
@@ -1535,6 +1650,7 @@ void launch_fwd(const MlpArgs& a, int64_t max_rows, cudaStream_t st) {
   int64_t tiles = div_up(max_rows > 0 ? max_rows : 1, TILE);
   int grid = (int)(tiles < resident ? tiles : resident);
   k_mlp_fwd<MODE, KP, NP><<<grid, MLP_THREADS, sm, st>>>(a);
+  return cudaGetLastError();
 }
 
 template <int MODE, int KP, int NP>
@@ -1562,10 +1678,10 @@ MlpArgs block_args(wbsph_surrogate s, int bi) {
 }
 
 // One fused message-passing layer (k_message_tc): persistent CTAs, one per
-// SM (218 KB of shared memory and 512 TMEM columns each), two receiver
-// groups per CTA.
-void launch_message(wbsph_surrogate s, const Params& p, const Work& w, int64_t nf, int64_t nd, int l,
-                    const bf16* h_in, bf16* h_out, bf16* m_out, cudaStream_t st) {
+// SM (221 KB of shared memory and 512 TMEM columns each); returns the
+// launch's error.
+cudaError_t launch_message(wbsph_surrogate s, const Params& p, const Work& w, int64_t nf, int64_t nd, int l,
+                           const bf16* h_in, bf16* h_out, bf16* m_out, cudaStream_t st) {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -1591,11 +1707,11 @@ void launch_message(wbsph_surrogate s, const Params& p, const Work& w, int64_t n
   a.status = w.status;
   a.tile_ctr = s->tile_ctr;
   const int64_t tiles = div_up(nf, 128) + div_up(nd, 128);
-  if (tiles == 0) return;
-  const int64_t want = div_up(tiles, MS_GROUPS);
-  const int grid = (int)(want < sms ? want : sms);
+  if (tiles == 0) return cudaSuccess;
+  const int grid = (int)(tiles < sms ? tiles : sms);
   cudaMemsetAsync(s->tile_ctr, 0, sizeof(int), st);
   k_message_tc<<<grid, MS_THREADS, MS_SMEM_BYTES, st>>>(a);
+  return cudaGetLastError();
 }
 
 // node inputs and packs of the sim's current state (wall particles updated)
@@ -1634,12 +1750,14 @@ int forward(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, int64_
   {  // node encoder (rows of 8 inputs)
     MlpArgs a = block_args(s, 0);
     a.rows = n; a.in = s->nfeat; a.out_bf = s->hs[0];
-    launch_fwd<MODE_DIRECT, 16, 64>(a, n, cs);
+    const cudaError_t e = launch_fwd<MODE_DIRECT, 16, 64>(a, n, cs);
+    if (e != cudaSuccess) return sfail(s, WBSPH_E_CUDA, cudaGetErrorString(e));
   }
   for (int l = 0; l < L; ++l) {
     bf16* m_out = train ? s->ms[l] : nullptr;
     if (m_out) cudaMemsetAsync(m_out, 0, (size_t)n * HID * 2, cs);  // rows of wall particles stay zero
-    launch_message(s, p, w, nf, n - nf, l, s->hs[l], s->hs[l + 1], m_out, cs);
+    const cudaError_t e = launch_message(s, p, w, nf, n - nf, l, s->hs[l], s->hs[l + 1], m_out, cs);
+    if (e != cudaSuccess) return sfail(s, WBSPH_E_CUDA, cudaGetErrorString(e));
   }
   {  // decoder over fluid rows
     MlpArgs a = block_args(s, 1 + 2 * L);
@@ -1648,7 +1766,8 @@ int forward(wbsph_surrogate s, const Params& p, const Work& w, int64_t n, int64_
       a.r_dudt = w.dudt; a.r_dphidt = w.dphidt; a.r_shift = w.dushift;
       a.r_mean = s->norm + 16; a.r_std = s->norm + 20; a.r_n = n;
     }
-    launch_fwd<MODE_LIST, 64, 16>(a, nf, cs);
+    const cudaError_t e = launch_fwd<MODE_LIST, 64, 16>(a, nf, cs);
+    if (e != cudaSuccess) return sfail(s, WBSPH_E_CUDA, cudaGetErrorString(e));
   }
   return WBSPH_OK;
 }

@@ -192,10 +192,11 @@ def _forward_bf16(theta, dim, node_in, recv, send, edge_in):
     """The network with activations rounded to BF16 where the CUDA kernels
     round them (encoder and node-MLP hidden layers, states h, the message
     layer's halved first-layer terms, its SiLU input and output, and m), sums
-    in FP64 where the kernels accumulate in FP32 (the message sum runs through
-    W2 term by term, so it is never rounded to BF16), exact tanh where they
-    use the hardware approximation: a model of the kernels' arithmetic, used
-    only to bound the error that BF16 alone causes."""
+    in FP64 where the kernels accumulate in FP32 (the message sum is kept in
+    FP32 and enters W2 as a BF16 high and low part, so it is never rounded to
+    BF16), exact tanh where they use the hardware approximation: a model of
+    the kernels' arithmetic, used only to bound the error that BF16 alone
+    causes."""
     P = {k: tuple(t.numpy() for t in v) for k, v in mpnn.unflatten(torch.as_tensor(theta), dim).items()}
 
     def silu(z):
