@@ -469,8 +469,9 @@ def surrogate_path(args, local, dim=2, scene=None):
            "hbm": {"algorithmic_bytes_per_stage": int(sbytes), "achieved_gbs": round(gbs, 1),
                    "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4),
                    "bytes_per_fluid_particle": round(sbytes / max(nf, 1), 1),
-                   "note": "nothing per edge reaches memory; the stage is bound by the per-edge gathers of "
-                           "sender rows (64 B) and packs (32 B) served by L2"},
+                   "note": "nothing per edge reaches memory; the per-edge gathers of sender rows (64 B) and "
+                           "packs (32 B) are served by L2, and the layer is bound by the latency of its "
+                           "gather, MMA and epilogue chains"},
            "with_fallback_tau_0.1": fb,
            "weights": f"paper_2608_22269_gb300/data/{name} (trained on the GPU by this library)"}
     sur.close()
