@@ -97,6 +97,56 @@ def test_forward_and_gradient_match_fp64_reference(dim):
     assert cos > 0.9999 and reln < 1e-2
 
 
+def _with_spray(seed=3):
+    """A 2D dam break with a block of isolated fluid particles above the
+    free surface, away from the walls: spaced 2.1h apart, none has a
+    neighbour within 2h. Sorted by cell they fill consecutive rows of the
+    fluid order, more than two 128-receiver tiles' worth, so at least one
+    tile of the fused layer holds only receivers without messages."""
+    sc = S.jitter(S.dam_break_2d(dx=0.01, width=1.6, column=(0.3, 0.2)), 0.15, seed=seed)
+    p = sc.params
+    h = p["h_over_dx"] * p["dx"]
+    gx, gy = np.meshgrid(np.arange(0.36, 1.56, 2.1 * h), np.arange(0.26, 0.58, 2.1 * h))
+    xs = np.vstack([gx.ravel(), gy.ravel()])
+    m = xs.shape[1]
+    f = sc.type == 0
+    rng = np.random.default_rng(seed)
+    x = np.concatenate([sc.x[:, f], xs, sc.x[:, ~f]], axis=1)
+    u = np.concatenate([0.3 * rng.normal(size=(2, f.sum())), 0.3 * rng.normal(size=(2, m)),
+                        sc.u[:, ~f]], axis=1)
+    phi = np.concatenate([sc.phi[f] + 0.1 * rng.normal(size=f.sum()), np.zeros(m), sc.phi[~f]])
+    typ = np.concatenate([sc.type[f], np.zeros(m, np.uint8), sc.type[~f]])
+    normal = np.concatenate([sc.normal[:, f], np.zeros((2, m)), sc.normal[:, ~f]], axis=1)
+    return S.Scene(sc.params, np.ascontiguousarray(x), np.ascontiguousarray(u), np.ascontiguousarray(phi),
+                   typ, np.ascontiguousarray(normal), "dam break with spray", sc.water_height), m
+
+
+def test_forward_with_isolated_receivers_matches_fp64_reference():
+    """Receivers without neighbours take m_i = 0 (the empty message sum and
+    no n_i b2 term). The fused layer meets them inside tiles with messages
+    (a zero count beside longer lists) and as whole tiles whose longest list
+    is empty (the node MLP alone); both must agree with the FP64 reference."""
+    sc, m = _with_spray()
+    sim, sur, theta, norm, r = _setup(sc)
+    dbg = sur.debug(sim)
+    recv, send, node_in, edge_in = _graph(sc, r, norm)
+    th = mpnn.round_weights_bf16(theta, 2)
+    out = mpnn.forward_np(th, 2, node_in, recv, send, edge_in)
+    fid = dbg["fluid_ids"].astype(np.int64)
+    isolated = np.ones(sc.n, bool)
+    isolated[recv] = False
+    iso = isolated[fid]                      # in the kernel's receiver order
+    assert iso.sum() >= m
+    full = [t for t in range(iso.size // 128) if iso[128 * t:128 * t + 128].all()]
+    assert full, "no tile of receivers without messages"
+    ref = out[fid]
+    err = np.abs(dbg["out"] - ref)
+    scale = np.abs(ref).max()
+    print("forward rel err", err.max() / scale, "isolated", err[iso].max() / scale, "empty tiles", len(full))
+    assert err.max() <= 2e-2 * scale
+    assert err[iso].max() <= 2e-2 * scale
+
+
 @pytest.mark.parametrize("dim,dx2", [(2, 0.01), (3, 0.01), (2, 0.002)])
 def test_graph_and_edge_features_follow_the_positions(dim, dx2):
     """Edges: every fluid receiver with every particle within 2h, the exact
