@@ -561,10 +561,11 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 //     receiver and sender, prefetched two of the group's steps ahead (the
 //     neighbour index three). The sender's first SEND features go into the
 //     slot by cp.async. A slot is announced on its "full" barrier once the
-//     thread's copies into it have landed. The announcement of a copy group
-//     waits until three newer groups are in flight, so that no thread blocks
-//     on a fresh copy. Group 0 also writes the tile record (counts, node ids,
-//     longest list, tile index), group 1 the tile's h_i rows.
+//     thread's copies into it have landed. A thread announces its slots
+//     three at a time, under one proxy fence, once a fourth copy group is in
+//     flight: the fence is the costly part, and no thread blocks on a fresh
+//     copy. Group 0 also writes the tile record (counts, node ids, longest
+//     list, tile index), group 1 the tile's h_i rows.
 //   - MMA: one thread. Per tile it issues P_r / 2 = h_i W_r / 2. Per step it
 //     issues D = G W_g/2 + H W_s/2 into a ring of four TMEM accumulators:
 //     three K = 16 MMAs, M = 128, N = 64, BF16 in, FP32 out. Per tile it
@@ -742,10 +743,11 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
     // ---- gather: two groups of four warps, even and odd steps; thread r of
     // a group fills row r of its steps' operand slots. Group 0 also writes
     // the tile record, group 1 the h_i rows. A slot (or h_i tile) is
-    // announced once this thread's copies into it have landed: the
-    // announcement of a copy group waits until QD newer groups are in
-    // flight, so that no thread blocks on a fresh copy. A thread's
-    // unannounced groups then span fewer than 2 QD < MS_NS steps, so the MMA
+    // announced once this thread's copies into it have landed. When a copy
+    // group is committed with QD unannounced ones before it, those QD are
+    // announced together: one wait for all but the newest group, one proxy
+    // fence, QD arrivals. A thread waits for a free slot with at most QD
+    // unannounced groups, spanning fewer than 2 QD < MS_NS steps, so the MMA
     // never waits for a slot whose announcement waits for a slot to free.
     constexpr int QD = 3;
     const int grp = warp >> 2, r = t & 127;
@@ -759,8 +761,10 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
     };
     auto push = [&](uint32_t mb) {  // after the commit of the group that fills mb
       if (nq == QD) {
-        cp_async_wait<QD>();
+        cp_async_wait<1>();
         fence_async_smem();
+        announce_oldest();
+        announce_oldest();
         announce_oldest();
       }
       (nq == 0 ? q0 : nq == 1 ? q1 : q2) = mb;
