@@ -500,12 +500,15 @@ __global__ void k_wait_probe(unsigned* status, uint32_t limit) {
 // ((x_j - x_i)/h, |x_j - x_i|/h, (U_j - U_i)/s_U, (phi'_j - phi'_i)/s_phi),
 // 2d + 2 values rounded to BF16 and zero padded to 8 (one 16-byte row). The
 // fused layer kernel and the training graph both form them here, so that
-// the backward sees exactly the inputs of the forward.
+// the backward sees exactly the inputs of the forward. |x_j - x_i| takes the
+// hardware's approximate square root: its error of a few FP32 units in the
+// last place changes the BF16 feature only next to a BF16 rounding boundary.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint4 edge_features(int dim, float4 ai, float4 bi, float4 aj, float4 bj,
                                                float inv_h, float inv_su, float inv_sphi) {
   const float rx = aj.x - ai.x, ry = aj.y - ai.y, rz = aj.z - ai.z;  // z = 0 in 2D
-  const float rn = sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+  float rn;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rn) : "f"(fmaf(rx, rx, fmaf(ry, ry, rz * rz))));
   float f[8];
   if (dim == 3) {
     f[0] = rx * inv_h; f[1] = ry * inv_h; f[2] = rz * inv_h; f[3] = rn * inv_h;
@@ -853,6 +856,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
         uint32_t j0 = k0 < cnt ? __ldg(a.nbr + (int64_t)k0 * a.nf + gi) : 0u;
         uint32_t j1 = k0 + 2 < cnt ? __ldg(a.nbr + (int64_t)(k0 + 2) * a.nf + gi) : 0u;
         uint32_t j2 = k0 + 4 < cnt ? __ldg(a.nbr + (int64_t)(k0 + 4) * a.nf + gi) : 0u;
+        const uint32_t* nb6 = a.nbr + (int64_t)(k0 + 6) * a.nf + gi;  // entry k + 6 of this row
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 aj0 = z4, bj0 = z4, aj1 = z4, bj1 = z4;
         if (k0 < cnt) { aj0 = __ldg(a.pack + 2 * j0); bj0 = __ldg(a.pack + 2 * j0 + 1); }
@@ -860,7 +864,8 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
         for (int k = k0; k < kmax; k += 2) {
           const uint32_t gs = gs0 + (uint32_t)k;
           const int s = (int)(gs % MS_NS);
-          const uint32_t j3 = k + 6 < cnt ? __ldg(a.nbr + (int64_t)(k + 6) * a.nf + gi) : 0u;
+          const uint32_t j3 = k + 6 < cnt ? __ldg(nb6) : 0u;
+          nb6 += 2 * a.nf;
           float4 aj2 = z4, bj2 = z4;
           if (k + 4 < cnt) { aj2 = __ldg(a.pack + 2 * j2); bj2 = __ldg(a.pack + 2 * j2 + 1); }
           const bool act = k < cnt;
