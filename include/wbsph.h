@@ -349,12 +349,16 @@ int wbsph_sort_cells_noalloc(wbsph_handle h, const double* x, int64_t n, uint32_
                              uint32_t* ids_sorted);
 
 /* Check of the bounded device waits (failure detection without a GPU fault):
- * launches one thread that waits, with at most `limit` polls, on an mbarrier
- * that nothing arrives on, the same bounded wait the surrogate's tcgen05
- * kernels use for their MMA and TMA completions. When the limit runs out the
- * thread sets the status word and returns; the call then synchronises and
- * returns WBSPH_E_TIMEOUT (the status stays set until the next
- * wbsph_set_particles). The context stays usable. Requires loaded particles. */
+ * launches two warps that use the waits of the surrogate's fused layer. The
+ * first waits, with at most `limit` polls (1 .. 2^20), on an mbarrier that
+ * nothing arrives on, and raises the block's abort flag when the limit runs
+ * out. The second waits on another such mbarrier with a 64 times longer
+ * limit and must leave as soon as it sees the flag, as the layer's roles
+ * do when one of them times out. Only when both happen does the probe set
+ * the status word; the call then synchronises and returns WBSPH_E_TIMEOUT
+ * (the status stays set until the next wbsph_set_particles), else
+ * WBSPH_OK. The context stays usable. Requires loaded particles; a limit
+ * out of range returns WBSPH_E_INVAL. */
 int wbsph_test_bounded_wait(wbsph_handle h, int64_t limit);
 
 void wbsph_destroy(wbsph_handle h);

@@ -922,7 +922,7 @@ static int decode_status(wbsph_s* h, unsigned s) {
 extern "C" int wbsph_test_bounded_wait(wbsph_handle h, int64_t limit) {
   if (!h) return WBSPH_E_INVAL;
   if (!h->loaded) return fail(h, WBSPH_E_STATE, "set_particles first");
-  if (limit < 1 || limit > (int64_t)0xFFFFFFFF) return fail(h, WBSPH_E_INVAL, "limit out of range");
+  if (limit < 1 || limit > ((int64_t)1 << 20)) return fail(h, WBSPH_E_INVAL, "limit out of range (1 .. 2^20)");
   CK(cudaSetDevice(h->cfg.device));
   launch_wait_probe(h->W.status, (uint32_t)limit, h->stream);
   int rc = check_launch(h, "wait probe");

@@ -483,15 +483,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
   return false;
 }
 
-// Check of the bounded wait itself: one thread waits on an mbarrier that
-// nothing arrives on; when the limit runs out it reports a timeout through the
-// status word, as the MLP kernels do, and the kernel ends normally.
-__global__ void k_wait_probe(unsigned* status, uint32_t limit) {
-  __shared__ uint64_t bar;
-  const uint32_t mb = smem_u32(&bar);
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
-  if (!mbar_wait(mb, 0u, limit)) atomicOr(status, (unsigned)kStatTimeout);
-}
 
 
 // ---------------------------------------------------------------------------
@@ -638,25 +629,65 @@ __device__ __forceinline__ void ms_arrive(uint32_t mbar) {
   asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
 }
 // bounded wait on the phase `parity`; gives up early once another role has aborted
-__device__ __forceinline__ bool ms_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+// (`polls`, when given, receives the number of polls made)
+__device__ __forceinline__ bool ms_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag,
+                                        uint32_t limit = TC_WAIT_LIMIT, uint32_t* polls = nullptr) {
+  bool ok = false;
+  uint32_t it = 0;
+  for (; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(mbar), "r"(parity)
         : "memory");
-    if (done) return true;
-    if ((it & 1023u) == 1023u && *abort_flag) return false;
+    if (done) {
+      ok = true;
+      break;
+    }
+    if ((it & 1023u) == 1023u && *abort_flag) break;
   }
-  *abort_flag = 1;
-  return false;
+  if (polls) *polls = it;
+  if (!ok && it == limit) *abort_flag = 1;
+  return ok;
 }
 
 // the same wait, decided for the whole warp (the roles that use it run
 // warp-collective instructions after it, so a warp never splits on a timeout)
-__device__ __forceinline__ bool ms_wait_warp(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
-  return __all_sync(0xffffffffu, ms_wait(mbar, parity, abort_flag));
+__device__ __forceinline__ bool ms_wait_warp(uint32_t mbar, uint32_t parity, volatile int* abort_flag,
+                                             uint32_t limit = TC_WAIT_LIMIT, uint32_t* polls = nullptr) {
+  return __all_sync(0xffffffffu, ms_wait(mbar, parity, abort_flag, limit, polls));
+}
+
+// Check of the fused layer's bounded waits (failure detection without a GPU
+// fault). Warp 0 waits, for at most `limit` polls, on an mbarrier that
+// nothing arrives on; when the limit runs out it raises the CTA's abort
+// flag. Warp 1 waits on a second such mbarrier with a limit 64 times as long
+// (at most 2^26 polls) and must leave as soon as it sees the flag, as every
+// role of the layer leaves when another role times out. The timeout is
+// reported through the status word only when both happened: warp 0 timed
+// out, and warp 1 left on the flag before its own limit. The kernel ends
+// normally either way.
+__global__ void k_wait_probe(unsigned* status, uint32_t limit) {
+  __shared__ uint64_t bar[2];
+  __shared__ int abort_flag;
+  __shared__ uint32_t polls1;
+  const int t = threadIdx.x, warp = t >> 5;
+  if (t == 0) {
+    for (int i = 0; i < 2; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + i)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_flag = 0;
+    polls1 = 0;
+  }
+  __syncthreads();
+  const uint64_t l1 = (uint64_t)limit * 64u;
+  const uint32_t limit1 = l1 < (1u << 26) ? (uint32_t)l1 : (1u << 26);
+  uint32_t polls = 0;
+  ms_wait_warp(smem_u32(bar + warp), 0u, &abort_flag, warp == 0 ? limit : limit1, &polls);
+  if (warp == 1 && (t & 31) == 0) polls1 = polls;
+  __syncthreads();
+  if (t == 0 && abort_flag && polls1 < limit1) atomicOr(status, (unsigned)kStatTimeout);
 }
 
 // (a0, a1) += the two BF16 halves of w (low, high), FP32 adds with BF16 operands
@@ -1894,7 +1925,7 @@ int surrogate_loss(wbsph_surrogate s, const Params& p, const State& st, const Wo
 int64_t surrogate_edges(wbsph_surrogate s) { return s->E; }
 
 void launch_wait_probe(unsigned* status, uint32_t limit, cudaStream_t st) {
-  k_wait_probe<<<1, 1, 0, st>>>(status, limit);
+  k_wait_probe<<<1, 64, 0, st>>>(status, limit);
 }
 const float* surrogate_out(wbsph_surrogate s) { return s->out; }
 const uint32_t* surrogate_recv(wbsph_surrogate s) { return s->recv; }

@@ -300,7 +300,8 @@ class Sim:
 
     def test_bounded_wait(self, limit=4096):
         """Run the bounded-wait check (wbsph_test_bounded_wait); raises
-        WbsphError(WBSPH_E_TIMEOUT) when the wait gave up as designed."""
+        WbsphError(WBSPH_E_TIMEOUT) when the first wait gave up and the
+        second left on the abort flag, as designed."""
         self._check(self.lib.wbsph_test_bounded_wait(self.h, int(limit)))
 
     def set_profiling(self, on=True):

@@ -270,15 +270,22 @@ def test_restart_from_fields_continues_the_run():
 
 
 def test_bounded_device_wait_reports_timeout_and_context_survives():
-    """A device wait that nothing satisfies gives up after its limit and
-    reports WBSPH_E_TIMEOUT through the status word (no trap, no fault); the
-    same handle then reloads and steps normally."""
+    """A device wait that nothing satisfies gives up after its limit, and a
+    second warp's wait (64 times the limit) leaves on the abort flag it
+    raises, as the fused layer's roles do; together they report
+    WBSPH_E_TIMEOUT through the status word (no trap, no fault). The same
+    handle then reloads and steps normally. A limit out of range is refused
+    before any launch."""
     from paper_2608_22269_gb300 import wbsph
     sc = S.dam_break_2d(dx=0.02, width=1.0, column=(0.3, 0.2))
     sim = _sim(sc)
     with pytest.raises(wbsph.WbsphError) as ei:
         sim.test_bounded_wait(4096)
     assert ei.value.code == -7
+    for bad in (0, (1 << 20) + 1):
+        with pytest.raises(wbsph.WbsphError) as ei:
+            sim.test_bounded_wait(bad)
+        assert ei.value.code == -1
     sim.set_scene(sc)
     sim.step(2)
     sim.sync()
