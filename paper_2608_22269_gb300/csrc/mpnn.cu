@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar + i)), "r"(count) : "memory");
     };
     for (int s = 0; s < MS_NS; ++s) { init(WB_SFULL + s, MS_GATHER); init(WB_SFREE + s, 1); }
-    for (int d = 0; d < MS_ND; ++d) { init(WB_DFULL + d, 1); init(WB_DFREE + d, MS_EPI); }
+    for (int d = 0; d < MS_ND; ++d) { init(WB_DFULL + d, 1); init(WB_DFREE + d, MS_EPI / 32); }
     for (int i = 0; i < 2; ++i) {
       init(WB_HFULL + i, MS_GATHER); init(WB_HFREE + i, MS_EPI);
       init(WB_IFULL + i, MS_GATHER); init(WB_IFREE + i, MS_EPI);
@@ -972,9 +972,9 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
           for (int hh = 0; hh < 2; ++hh) {
             float v[16];
             tc_ld16(TD + 64u * d + lane_off + 16 * hh, v);
-            if (hh == 1) {
+            if (hh == 1) {  // both loads complete (warp-collective waits): one arrival for the warp
               tc_fence_before();
-              ms_arrive(B(WB_DFREE + d));
+              if (lane == 0) ms_arrive(B(WB_DFREE + d));
             }
             if (act) {
 #pragma unroll
