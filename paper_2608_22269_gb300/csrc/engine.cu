@@ -496,12 +496,22 @@ extern "C" int wbsph_set_particles(wbsph_handle h, int64_t n, const double* x, c
     CK(cudaStreamSynchronize(h->stream));
     ty = ty_copy.data();
   }
+  // fluid (0), wall (1 fixed dummy, 2 body) and invalid counts; 16-bit sums
+  // over blocks of 4096 let the compiler vectorise the byte compares
   int64_t nf = 0, nd = 0, bad = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    const uint8_t v = ty[i];
-    nf += v == 0;
-    nd += v == 1 || v == 2;  // wall particles: fixed dummies and body particles
-    bad += v > 2;
+  for (int64_t s = 0; s < n; s += 4096) {
+    const int64_t m = n - s < 4096 ? n - s : 4096;
+    const uint8_t* q = ty + s;
+    uint16_t f16 = 0, d16 = 0, b16 = 0;
+    for (int64_t i = 0; i < m; ++i) {
+      const uint8_t v = q[i];
+      f16 += (uint16_t)(v == 0);
+      d16 += (uint16_t)((uint8_t)(v - 1) < 2);
+      b16 += (uint16_t)(v > 2);
+    }
+    nf += f16;
+    nd += d16;
+    bad += b16;
   }
   if (bad) {
     int64_t i = 0;
