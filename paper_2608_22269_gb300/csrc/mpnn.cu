@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
         uint32_t j0 = k0 < cnt ? __ldg(a.nbr + (int64_t)k0 * a.nf + gi) : 0u;
         uint32_t j1 = k0 + 2 < cnt ? __ldg(a.nbr + (int64_t)(k0 + 2) * a.nf + gi) : 0u;
         uint32_t j2 = k0 + 4 < cnt ? __ldg(a.nbr + (int64_t)(k0 + 4) * a.nf + gi) : 0u;
-        const uint32_t* nb6 = a.nbr + (int64_t)(k0 + 6) * a.nf + gi;  // entry k + 6 of this row
+        int64_t o6 = (int64_t)(k0 + 6) * a.nf + gi;  // offset of this row's entry k + 6
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 aj0 = z4, bj0 = z4, aj1 = z4, bj1 = z4;
         if (k0 < cnt) { aj0 = __ldg(a.pack + 2 * j0); bj0 = __ldg(a.pack + 2 * j0 + 1); }
@@ -895,8 +895,8 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
         for (int k = k0; k < kmax; k += 2) {
           const uint32_t gs = gs0 + (uint32_t)k;
           const int s = (int)(gs % MS_NS);
-          const uint32_t j3 = k + 6 < cnt ? __ldg(nb6) : 0u;
-          nb6 += 2 * a.nf;
+          const uint32_t j3 = k + 6 < cnt ? __ldg(a.nbr + o6) : 0u;
+          o6 += 2 * a.nf;
           float4 aj2 = z4, bj2 = z4;
           if (k + 4 < cnt) { aj2 = __ldg(a.pack + 2 * j2); bj2 = __ldg(a.pack + 2 * j2 + 1); }
           const bool act = k < cnt;

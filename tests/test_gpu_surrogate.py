@@ -147,6 +147,50 @@ def test_forward_with_isolated_receivers_matches_fp64_reference():
     assert err[iso].max() <= 2e-2 * scale
 
 
+def _thinned(seed=4):
+    """A 2D tank whose fluid is a block of every other lattice point in each
+    direction, away from the walls: spaced 2 dx = 1.54 h apart, a receiver
+    has at most its four axis neighbours within 2h (the diagonals lie at
+    2.18 h), so every 128-receiver tile of the fused layer has a list of at
+    most four steps."""
+    sc = S.dam_break_2d(dx=0.01, width=1.6, column=(1.2, 0.4))
+    dx = sc.params["dx"]
+    f = sc.type == 0
+    ij = np.rint((sc.x - dx / 2) / dx).astype(np.int64)
+    block = (sc.x[0] > 0.3) & (sc.x[0] < 1.3) & (sc.x[1] > 0.1)
+    keep = ~f | ((ij[0] % 2 == 0) & (ij[1] % 2 == 0) & block)
+    rng = np.random.default_rng(seed)
+    u, phi = sc.u[:, keep].copy(), sc.phi[keep].copy()
+    fl = sc.type[keep] == 0
+    u[:, fl] = 0.3 * rng.normal(size=(2, fl.sum()))
+    phi[fl] += 0.1 * rng.normal(size=fl.sum())
+    return S.Scene(sc.params, np.ascontiguousarray(sc.x[:, keep]), np.ascontiguousarray(u),
+                   np.ascontiguousarray(phi), np.ascontiguousarray(sc.type[keep]),
+                   np.ascontiguousarray(sc.normal[:, keep]), "thinned block", sc.water_height)
+
+
+def test_forward_on_short_lists_matches_fp64_reference():
+    """Tiles whose longest list is at most four steps: each holds a full
+    tile's worth of per-tile work (P_r, the node MLP) for few neighbour
+    steps, and the gather announces its copies at tile starts rather than
+    three at a time. The forward must match the FP64 reference."""
+    sc = _thinned()
+    sim, sur, theta, norm, r = _setup(sc)
+    dbg = sur.debug(sim)
+    recv, send, node_in, edge_in = _graph(sc, r, norm)
+    th = mpnn.round_weights_bf16(theta, 2)
+    out = mpnn.forward_np(th, 2, node_in, recv, send, edge_in)
+    fid = dbg["fluid_ids"].astype(np.int64)
+    cnt = np.bincount(recv, minlength=sc.n)[fid]           # list lengths in the kernel's order
+    kmax = [int(cnt[128 * t:128 * t + 128].max()) for t in range((cnt.size + 127) // 128)]
+    short = sum(k <= 4 for k in kmax)
+    assert len(kmax) >= 3 and short == len(kmax), kmax
+    ref = out[fid]
+    err = np.abs(dbg["out"] - ref).max() / np.abs(ref).max()
+    print("forward rel err", err, "tiles", len(kmax), "longest lists", kmax)
+    assert err < 2e-2
+
+
 @pytest.mark.parametrize("dim,dx2", [(2, 0.01), (3, 0.01), (2, 0.002)])
 def test_graph_and_edge_features_follow_the_positions(dim, dx2):
     """Edges: every fluid receiver with every particle within 2h, the exact
