@@ -152,11 +152,15 @@ class Sim:
     the hydrostatic split phi_hs = G.x + |G| H that MIXED and DF64 use."""
 
     def __init__(self, params: dict, precision: int = FP64, water_height: float = 0.0,
-                 device: int = 0, use_torch_allocator: bool = True, stream=None):
+                 device: int = 0, use_torch_allocator: bool = True, stream=None, allocator=None):
         """The handle works on its own CUDA stream (a new torch stream unless
         ``stream`` is given), so that its steps can be replayed as CUDA
         graphs; the binding orders that stream against torch's current
-        stream wherever device tensors are exchanged."""
+        stream wherever device tensors are exchanged. ``allocator``, a pair
+        of callables (alloc(size) -> device address or 0, free(address)),
+        replaces the device allocator (the C-ABI's alloc/free hooks); an
+        address of 0 is an allocation failure, which the library reports as
+        WBSPH_E_NOMEM."""
         import torch
         self._torch = torch
         self.lib = load()
@@ -165,7 +169,20 @@ class Sim:
         self.stream = stream if stream is not None else torch.cuda.Stream(device)
         cfg = make_config(params, precision, C.c_void_p(self.stream.cuda_stream), device,
                           water_height)
-        if use_torch_allocator:
+        if allocator is not None:
+            user_alloc, user_free = allocator
+
+            def _alloc(size, stream, ctx):
+                return int(user_alloc(int(size))) or None
+
+            def _free(ptr, stream, ctx):
+                user_free(int(ptr))
+
+            self._alloc_cb = ALLOC_FN(_alloc)
+            self._free_cb = FREE_FN(_free)
+            cfg.alloc = self._alloc_cb
+            cfg.free = self._free_cb
+        elif use_torch_allocator:
             def _alloc(size, stream, ctx):
                 return torch.cuda.caching_allocator_alloc(int(size), device, self.stream)
 

@@ -295,6 +295,50 @@ def test_bounded_device_wait_reports_timeout_and_context_survives():
     assert scaled_err(sim.get("x"), st.x, sk["x"]) <= TOL
 
 
+def test_allocation_failure_is_reported_and_the_handle_recovers():
+    """Fault injection on the host (no GPU fault): the caller's allocator
+    refuses one request during set_particles. The call returns
+    WBSPH_E_NOMEM and the handle holds no particle set (a step is refused
+    with WBSPH_E_STATE). The next set_particles, whose requests all
+    succeed, gives a handle that steps to oracle parity, and every block the
+    library took is back with the allocator once the handle is closed."""
+    import torch
+    from paper_2608_22269_gb300 import wbsph
+    sc = S.dam_break_2d(dx=0.02, width=1.0, column=(0.3, 0.2))
+    stream = torch.cuda.Stream()
+    live, calls = {}, [0]
+
+    def alloc(size):
+        calls[0] += 1
+        if calls[0] == 5:
+            return 0
+        p = torch.cuda.caching_allocator_alloc(size, 0, stream)
+        live[p] = size
+        return p
+
+    def free(p):
+        del live[p]
+        torch.cuda.caching_allocator_delete(p)
+
+    sim = wbsph.Sim(sc.params, water_height=sc.water_height, stream=stream, allocator=(alloc, free))
+    with pytest.raises(wbsph.WbsphError) as ei:
+        sim.set_scene(sc)
+    assert ei.value.code == -2
+    with pytest.raises(wbsph.WbsphError) as ei:
+        sim.step(1)
+    assert ei.value.code == -8
+    sim.set_scene(sc)
+    sim.step(2)
+    sim.sync()
+    st = oracle.State(sc)
+    st.step(2)
+    sk = scales(sc.params, sc.water_height)
+    assert scaled_err(sim.get("x"), st.x, sk["x"]) <= TOL
+    assert calls[0] > 5 and live
+    sim.close()
+    assert not live
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_wall_particles_only(precision):
     """No fluid at all: the dummy update finds no fluid within 2h and leaves
