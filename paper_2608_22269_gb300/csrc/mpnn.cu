@@ -225,6 +225,12 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, boo
   int n = valid ? 16 : 0;
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n));
 }
+// the same copy, cached in L1 as well (rows that neighbouring receivers read again)
+__device__ __forceinline__ void cp_async16_ca(void* smem_dst, const void* gsrc, bool valid) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  int n = valid ? 16 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
@@ -908,7 +914,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_message_tc(const MsgArgs a) {
             unsigned char* T = TH + (s >> 1) * TC_TILE_BYTES;
             const bf16* src = a.h_in + (int64_t)j0 * HID;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) cp_async16(T + sw128(r, 4 * (s & 1) + c), src + c * 8, act);
+            for (int c = 0; c < 4; ++c) cp_async16_ca(T + sw128(r, 4 * (s & 1) + c), src + c * 8, act);
           }
           cp_async_commit();
           push(B(WB_SFULL + s));
