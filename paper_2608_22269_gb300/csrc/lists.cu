@@ -85,12 +85,14 @@ __global__ void __launch_bounds__(LIST_THREADS) k_nbr_list(Params p, State s, Wo
 int pair_list_kmax(int dim) { return dim == 3 ? 128 : 48; }
 
 // List entries per lane staged in shared memory (the rest are stored
-// directly, uncoalesced): 80 holds the candidates of most particles of 3D
-// lattices at h = 1.3 dx (about 75) and leaves room for 20 resident warps
-// per SM, which this latency-bound kernel needs more than coalesced stores
-// of the few entries beyond.
+// directly, uncoalesced). A 3D list holds about 75 exact neighbours (h =
+// 1.3 dx) or 90 kept candidates; staging 48 of them leaves room for about
+// 34 resident warps per SM, and this latency-bound kernel gains more from
+// those warps than it loses on the uncoalesced stores of the entries beyond
+// (against 80 staged entries and 18 warps: mixed step 2.96 -> 2.86 ms, FP64
+// step 23.66 -> 23.54 ms on the 1.21M-particle dam break).
 #ifndef WBSPH_LIST_STAGE_3D
-#define WBSPH_LIST_STAGE_3D 80
+#define WBSPH_LIST_STAGE_3D 48
 #endif
 static int pair_list_stage(int dim) { return dim == 3 ? WBSPH_LIST_STAGE_3D : 48; }
 
