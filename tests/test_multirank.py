@@ -4,7 +4,6 @@ throughput counts the units of every rank."""
 import os
 import socket
 
-import pytest
 import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
