@@ -560,7 +560,8 @@ __device__ __forceinline__ __nv_bfloat162 u32_bf2(uint32_t v) { return *reinterp
 //     slot of an 8-deep operand ring. It is formed from the FP32 packs of
 //     receiver and sender, prefetched two of the group's steps ahead (the
 //     neighbour index three). The sender's first SEND features go into the
-//     slot by cp.async. A slot is announced on its "full" barrier once the
+//     slot by cp.async, through L1 (neighbouring receivers read the same rows
+//     over a tile's steps). A slot is announced on its "full" barrier once the
 //     thread's copies into it have landed. A thread announces its slots
 //     three at a time, under one proxy fence, once a fourth copy group is in
 //     flight: the fence is the costly part, and no thread blocks on a fresh
