@@ -170,6 +170,18 @@ def test_df64_lone_particle_falls_exactly():
     assert abs(x[1] - (0.2 + t - 0.5 * 9.81 * t * t)) < 1e-13
 
 
+def test_df64_empty_set_steps():
+    """No particles: the single-sort step (one eager, then the captured
+    graphs) launches nothing that needs a particle and reports n = 0."""
+    p = S.default_params(2, 0.01, 30.0, use_tic=1, domain_min=[-5, -20, 0], domain_max=[5, 5, 1])
+    empty = S.Scene(p, np.zeros((2, 0)), np.zeros((2, 0)), np.zeros(0), np.zeros(0, np.uint8),
+                    np.zeros((2, 0)))
+    sim = _sim(empty)
+    sim.step(3)
+    sim.sync()
+    assert sim.stats()["n"] == 0
+
+
 def test_df64_wall_particles_only():
     sc = S.dam_break_2d(dx=0.02, width=1.0, column=(0.3, 0.2))
     walls = sc.type != 0

@@ -122,6 +122,33 @@ def test_mixed_lone_particle_falls_exactly():
     assert abs(x[1] - (0.2 + t - 0.5 * 9.81 * t * t)) < 1e-13
 
 
+def test_mixed_empty_set_steps():
+    """No particles: the single-sort step (one eager, then the captured
+    graphs) launches nothing that needs a particle and reports n = 0."""
+    p = S.default_params(2, 0.01, 30.0, use_tic=1, domain_min=[-5, -20, 0], domain_max=[5, 5, 1])
+    empty = S.Scene(p, np.zeros((2, 0)), np.zeros((2, 0)), np.zeros(0), np.zeros(0, np.uint8),
+                    np.zeros((2, 0)))
+    sim = _sim(empty)
+    sim.step(3)
+    sim.sync()
+    assert sim.stats()["n"] == 0
+
+
+def test_mixed_wall_particles_only():
+    """Walls and no fluid: no kept lists and no pair pass; the walls keep
+    their positions and, with no fluid particle to copy, their phi."""
+    sc = S.dam_break_2d(dx=0.02, width=1.0, column=(0.3, 0.2))
+    walls = sc.type != 0
+    only = S.Scene(dict(sc.params), sc.x[:, walls].copy(), sc.u[:, walls].copy(), sc.phi[walls].copy(),
+                   sc.type[walls].copy(), sc.normal[:, walls].copy())
+    sim = _sim(only)
+    sim.step(2)
+    sim.sync()
+    assert sim.stats()["n_fluid"] == 0
+    assert np.array_equal(sim.get("x"), only.x)
+    assert np.array_equal(sim.get("phi"), only.phi)
+
+
 def _mixed_cell(p):
     """Cell size of the mixed path: 2h widened by the skin of its kept lists,
     3 CFL dx 0.3 / 1.3 (the move of two particles in one stage at Mach 0.3)."""

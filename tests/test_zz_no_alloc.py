@@ -101,3 +101,25 @@ def test_noalloc_sort_rejects_sizes_beyond_its_limit():
     with pytest.raises(wbsph.WbsphError) as ei:
         sim.sort_cells_noalloc(x, k, k.clone())
     assert ei.value.code == -9 and "WBSPH_NOALLOC_MAX_N" in str(ei.value)
+
+
+@pytest.mark.parametrize("dim,side", [(2, 1.0), (3, 1.1)])
+def test_noalloc_sort_at_its_size_limit(dim, side):
+    """Exactly WBSPH_NOALLOC_MAX_N particles, the largest input accepted: the
+    static scratch is used to its last element. 2D: two radix passes; 3D:
+    more than 65,536 cells, three passes, so the result ends in the scratch
+    and is copied out. Bit for bit against the regular build. An empty input
+    then returns at once and leaves its outputs as they were."""
+    import torch
+    from paper_2608_22269_gb300 import wbsph
+    sc = S.random_box(wbsph.NOALLOC_MAX_N, dim, side=side, dx=0.01, seed=60 + dim, on_faces=False)
+    ref = _regular(sc)
+    sim = wbsph.Sim(sc.params)
+    keys, ids = _noalloc(sim, sc)
+    assert np.array_equal(keys, ref[0])
+    assert np.array_equal(ids, ref[1])
+    x0 = torch.empty((dim, 0), dtype=torch.float64, device="cuda")
+    k0 = torch.full((4,), 7, dtype=torch.int32, device="cuda")
+    i0 = torch.full((4,), 7, dtype=torch.int32, device="cuda")
+    sim.sort_cells_noalloc(x0, k0, i0)
+    assert int(k0.min()) == 7 and int(k0.max()) == 7 and int(i0.min()) == 7 and int(i0.max()) == 7
