@@ -53,6 +53,13 @@ typedef enum {
   WBSPH_E_CAPACITY = -9,  /* output capacity too small / neighbour list overflow / list skin exceeded */
   WBSPH_E_NOSYM = -10     /* feature not built into this library */
 } wbsph_status;
+/* Conditions found on the device during a step are returned by the next
+ * synchronising call. When several were flagged, the neighbour-list ones
+ * come first (WBSPH_E_CAPACITY: a move beyond the skin of kept lists, or a
+ * list overflow, more than 48 entries for a particle in 2D or 128 in 3D),
+ * because every sum after them left pairs out; then WBSPH_E_NAN,
+ * WBSPH_E_SINGULAR, WBSPH_E_DOMAIN and WBSPH_E_TIMEOUT. set_particles
+ * clears them. */
 
 /* Arithmetic of the pair pass (the state x, U, phi is FP64 in every mode):
  *  WBSPH_FP64  FP64 pair sums, the full potential (the reference arithmetic).

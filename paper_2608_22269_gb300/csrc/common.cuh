@@ -20,7 +20,7 @@ enum : unsigned {
   kStatDomain = 1u,     // particle outside the grid
   kStatSingular = 2u,   // singular renormalisation matrix on the corrected branch
   kStatNaN = 4u,        // non-finite rate or state
-  kStatOverflow = 8u,   // neighbour list chunk bookkeeping overflow
+  kStatOverflow = 8u,   // a neighbour list had more entries than it holds
   kStatTimeout = 16u,   // bounded device wait gave up
   kStatSkin = 32u       // a particle may move further in a stage than the reused lists allow
 };

@@ -921,12 +921,17 @@ static int decode_status(wbsph_s* h, unsigned s) {
     return fail(h, WBSPH_E_CAPACITY,
                 "a particle can move more than the neighbour-list skin in one stage (mixed and double-float "
                 "paths: flow above Mach 0.3 at this CFL number, or a fixed time step that is too long)");
+  // so did a list that overflowed: its particle's sums left pairs out
+  if (s & kStatOverflow)
+    return fail(h, WBSPH_E_CAPACITY,
+                "neighbour list overflow: a particle has more neighbours (or kept candidates) than a list "
+                "holds (48 in 2D, 128 in 3D); the particle spacing is far below dx");
   // a non-finite value also sends positions out of the domain: report it first
   if (s & kStatNaN) return fail(h, WBSPH_E_NAN, "non-finite rate or state value");
   if (s & kStatSingular) return fail(h, WBSPH_E_SINGULAR, "singular renormalisation matrix (TIC off)");
   if (s & kStatDomain) return fail(h, WBSPH_E_DOMAIN, "a particle left the domain");
   if (s & kStatTimeout) return fail(h, WBSPH_E_TIMEOUT, "a bounded device wait gave up");
-  return fail(h, WBSPH_E_CAPACITY, "neighbour list overflow");
+  return fail(h, WBSPH_E_CUDA, "unexpected device status word 0x%x", s);
 }
 
 extern "C" int wbsph_test_bounded_wait(wbsph_handle h, int64_t limit) {

@@ -192,6 +192,31 @@ def test_lone_particle_and_empty_set():
     assert ei.value.code == -5
 
 
+@pytest.mark.parametrize("dim,n_dense,n_sparse,side,precision", [
+    (2, 2000, 250, 0.2, 0), (2, 2000, 250, 0.2, 1), (2, 2000, 250, 0.2, 2), (3, 4000, 600, 0.1, 0)])
+def test_list_overflow_is_reported_and_the_handle_recovers(dim, n_dense, n_sparse, side, precision):
+    """Particles packed far below dx: about 106 neighbours per particle in 2D
+    (a list holds 48) and about 290 in 3D (a list holds 128). The lists stop
+    at their capacity and the rates are not the method's, so the next
+    synchronising call returns WBSPH_E_CAPACITY naming the overflow, ahead
+    of anything the truncated sums may have caused. Loading a sparse set
+    (about 13 and 44 neighbours) clears it: the rates are then finite."""
+    from paper_2608_22269_gb300 import wbsph
+    dense = S.random_box(n_dense, dim, side=side, dx=0.01, seed=70 + dim, on_faces=False)
+    sparse = S.random_box(n_sparse, dim, side=side, dx=0.01, seed=80 + dim, on_faces=False)
+    p = dict(dense.params, use_tic=1)
+    sim = wbsph.Sim(p, precision=precision)
+    sim.set_particles(dense.x, dense.u, dense.phi, dense.type, dense.normal)
+    with pytest.raises(wbsph.WbsphError) as ei:
+        sim.eval_rates()
+        sim.sync()
+    assert ei.value.code == -9 and "overflow" in str(ei.value)
+    sim.set_particles(sparse.x, sparse.u, sparse.phi, sparse.type, sparse.normal)
+    sim.eval_rates()
+    sim.sync()
+    assert np.isfinite(sim.get("dudt")).all() and np.isfinite(sim.get("dphidt")).all()
+
+
 def test_error_paths():
     from paper_2608_22269_gb300 import wbsph
     sc = S.dam_break_2d(dx=0.02, width=1.0, column=(0.3, 0.2))
