@@ -5,6 +5,10 @@ sample of the benchmark's scene, and prints the same line as the library's
 arm with "impl": "reference", a cpu_baseline describing the run and an e2e
 block with no host-device traffic. Under torchrun only rank 0 runs it; the
 other ranks exit 0 without work. Fewer than three warm-up steps are refused.
+The host arithmetic behind the library arm's line is pinned on hand-computed
+cases: the pair pass's roofline (flops per launch over the average launch
+time, against the measured peak) and the summary of the clock samples taken
+during the timed region (median clock, throttle reasons seen).
 """
 import json
 import os
@@ -56,3 +60,51 @@ def test_reference_arm_runs_on_rank_zero_only():
 def test_fewer_than_three_warmup_steps_are_refused(impl):
     r = _bench("--impl", impl, "--steps", "1", "--warmup", "2", timeout=120)
     assert r.returncode == 2 and "--warmup must be at least 3" in r.stderr
+
+
+def test_pair_roofline_arithmetic():
+    """Two launches of 10 ms over 2e8 listed pairs: 1e8 pairs per launch.
+    FP64: 110 flops a pair, 1.1e10 flops in 10 ms = 1.1 TFLOP/s, against the
+    measured 1.186. Mixed: 155.5 flops, 1.555 TFLOP/s against 72.4. Double
+    float: 682 FP32 instructions, 6.82 Top/s against 36.2. The pair pass's
+    share is its 20 ms of the 30 ms profiled."""
+    sys.path.insert(0, ROOT)
+    import bench
+    m = {"prof": {"pair": (20.0, 2), "nlist": (6.0, 2), "other": (4.0, 7)},
+         "sp0": {"pairs": 5}, "sp1": {"pairs": 5 + 2 * 10**8}}
+    for prec, achieved, peak in [("fp64", 1.1, 1.186), ("mixed", 1.555, 72.4), ("df64", 6.82, 36.2)]:
+        r = bench.pair_roofline(m, 3, 0, prec, "dam3d")
+        assert r["pairs_per_launch"] == 10**8 and r["avg_launch_ms"] == 10.0
+        assert r["achieved"] == pytest.approx(achieved, rel=1e-4)
+        assert r["peak"] == pytest.approx(peak)
+        assert r["frac"] == pytest.approx(achieved / peak, abs=1e-4)
+        assert r["share_of_step"] == pytest.approx(2 / 3, abs=1e-4)
+        assert r["bound"] == "alu"
+
+
+def test_clock_samples_are_summarised_with_their_throttle_reasons(tmp_path):
+    """nvidia-smi rows (SM MHz, max MHz, power, reasons word, then the four
+    reasons): the median SM clock, the first row's maximum, the largest
+    power reading, and every reason seen active in any row. Rows that do not
+    start with a number (a header, an error line) are skipped."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = ["clocks.current.sm [MHz], clocks.max.sm [MHz], ...",
+            "2070, 2070, 510.25, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "1980, 2070, 1398.50, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "2055, 2070, [N/A], 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+            "Unable to determine the device handle"]
+    p = tmp_path / "clocks.csv"
+    p.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.path = str(p)
+    s = cs.summary()
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["power_w_max"] == pytest.approx(1398.5)
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert not p.exists()
+    empty = bench.ClockSampler(0)
+    q = tmp_path / "none.csv"
+    q.write_text("")
+    empty.path = str(q)
+    assert empty.summary()["reasons"] == ["no samples"]
