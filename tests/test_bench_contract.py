@@ -108,3 +108,25 @@ def test_clock_samples_are_summarised_with_their_throttle_reasons(tmp_path):
     q.write_text("")
     empty.path = str(q)
     assert empty.summary()["reasons"] == ["no samples"]
+
+
+def test_algorithmic_bytes_and_error_measure():
+    """HBM bytes per fluid particle-step, per stage: keys (8d + 4), three
+    16-byte sort passes (48), the reorder read and write (2 (24d + 18)), the
+    pair pass's reads and writes (16 (2d + 2)) and the update (16 (2d + 1));
+    two stages: 3D 2 x 496 = 992, 2D 2 x 376 = 752. The bench's error measure
+    is the tests' max |a - b| / max(max |b|, scale), and an empty field has
+    no error."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from tests.helpers import scaled_err
+    assert bench.algorithmic_bytes_per_particle_step(3) == 992
+    assert bench.algorithmic_bytes_per_particle_step(2) == 752
+    rng = np.random.default_rng(3)
+    for scale in (1e-3, 1.0, 1e3):
+        a, b = rng.normal(size=(3, 50)), rng.normal(size=(3, 50))
+        assert bench.scaled_err(a, b, scale) == scaled_err(a, b, scale)
+    assert bench.scaled_err(np.zeros(0), np.zeros(0), 1.0) == 0.0
+    assert bench.scaled_err([1.0, 2.0], [1.0, 4.0], 1.0) == 0.5
+    assert bench.scaled_err([1.0, 2.0], [1.0, 2.5], 10.0) == 0.05
