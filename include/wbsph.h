@@ -209,7 +209,10 @@ int wbsph_stage(wbsph_handle h, int stage, double t, double dt, double umax);
 /* Overwrite x, U and phi of `count` particles identified by their index in
  * the last wbsph_set_particles input (host arrays; x and u SoA dim*count).
  * Between the stages of a domain decomposition this brings the ghosts to the
- * stage-1 state their owners computed. Synchronises the stream. */
+ * stage-1 state their owners computed. The ids must be distinct: for an id
+ * given twice, which of its two rows is written is unspecified. An id not
+ * below the particle count returns WBSPH_E_INVAL before anything is
+ * written. Synchronises the stream. */
 int wbsph_update_particles(wbsph_handle h, int64_t count, const uint32_t* ids, const double* x,
                            const double* u, const double* phi);
 

@@ -262,9 +262,9 @@ class Sim:
 
     def update_particles(self, ids, x, u, phi):
         """Overwrite x, U, phi of the particles with these input indices
-        (wbsph_update_particles; host arrays, x and u of shape (dim, count))."""
-        ids = np.ascontiguousarray(ids, dtype=np.uint32)
-        x, u, phi = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, u, phi))
+        (wbsph_update_particles; host arrays, x and u of shape (dim, count)).
+        The arguments are checked (check_update_args) before the call."""
+        ids, x, u, phi = check_update_args(ids, x, u, phi, self.dim, self.n)
         self._check(self.lib.wbsph_update_particles(self.h, ids.size, _ptr(ids), _ptr(x), _ptr(u), _ptr(phi)))
 
     def get(self, field: str, out=None):
@@ -329,6 +329,34 @@ class Sim:
         cnt = (C.c_int64 * len(KERNEL_CLASSES))()
         self._check(self.lib.wbsph_get_profile(self.h, ms, cnt, int(reset)))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def check_update_args(ids, x, u, phi, dim: int, n: int):
+    """Argument checks of wbsph_update_particles, on the host arrays before
+    the call (the library reads count rows of each array through bare
+    pointers): ids a one-dimensional integer array of distinct indices in
+    [0, n), n the particle count of the last set_particles; x and u of shape
+    (dim, count), phi of shape (count,). Returns the arrays as the library
+    takes them (contiguous uint32 ids, float64 fields); raises
+    WbsphError(WBSPH_E_INVAL)."""
+    def bad(msg):
+        raise WbsphError(-1, f"update_particles: {msg}")
+
+    ids = np.asarray(ids)
+    if ids.ndim != 1:
+        bad(f"ids must be one-dimensional, got shape {ids.shape}")
+    if ids.size and not np.issubdtype(ids.dtype, np.integer):
+        bad(f"ids must be integers, got {ids.dtype}")
+    count = int(ids.size)
+    if count and (int(ids.min()) < 0 or int(ids.max()) >= n):
+        bad(f"ids must lie in [0, {n})")
+    if np.unique(ids).size != count:
+        bad("ids must be distinct")
+    x, u, phi = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, u, phi))
+    for name, a, shape in (("x", x, (dim, count)), ("u", u, (dim, count)), ("phi", phi, (count,))):
+        if a.shape != shape:
+            bad(f"{name} must have shape {shape}, got {a.shape}")
+    return np.ascontiguousarray(ids, dtype=np.uint32), x, u, phi
 
 
 def check_noalloc_args(x, keys_sorted, ids_sorted, dim: int, device) -> int:

@@ -59,6 +59,11 @@ class OracleBackend:
         return {"x": self.x, "u": self.u, "phi": self.phi, "mass": self.m}[field].copy()
 
     def update(self, ids, x, u, phi):
+        # the argument contract of the library's wbsph_update_particles, so
+        # the slab driver's ghost refresh is held to it on CPU ranks too
+        from paper_2608_22269_gb300.wbsph import check_update_args
+        ids, x, u, phi = check_update_args(ids, x, u, phi, self.x.shape[0], self.x.shape[1])
+        ids = ids.astype(np.int64)
         self.x[:, ids], self.u[:, ids], self.phi[ids] = x, u, phi
 
     def dt(self):

@@ -79,6 +79,38 @@ def test_noalloc_arguments_are_checked_before_the_call():
         wbsph.check_noalloc_args(x, k, i, dim, torch.device("cuda", 0))
 
 
+def test_update_arguments_are_checked_before_the_call():
+    """The binding of wbsph_update_particles checks the host arrays before
+    the library reads count rows of each through bare pointers: ids distinct
+    integers in [0, n), x and u (dim, count), phi (count,). Each bad argument
+    raises WbsphError(WBSPH_E_INVAL); a good call returns the arrays as the
+    library takes them, and an empty update passes."""
+    from paper_2608_22269_gb300 import wbsph
+    n, dim = 50, 2
+    ids = np.array([3, 0, 49, 7])
+    x, u, phi = np.zeros((dim, 4)), np.ones((dim, 4)), np.arange(4.0)
+    i2, x2, u2, p2 = wbsph.check_update_args(ids, x, u, phi, dim, n)
+    assert i2.dtype == np.uint32 and i2.flags.c_contiguous and list(i2) == [3, 0, 49, 7]
+    assert x2.shape == (dim, 4) and u2.dtype == np.float64 and p2.shape == (4,)
+    e = wbsph.check_update_args([], np.zeros((dim, 0)), np.zeros((dim, 0)), np.zeros(0), dim, n)
+    assert e[0].size == 0
+    bad_cases = {
+        "repeated id": ([3, 0, 3, 7], x, u, phi),
+        "negative id": ([3, -1, 4, 7], x, u, phi),
+        "id = n": ([3, 0, 50, 7], x, u, phi),
+        "float ids": (ids.astype(float), x, u, phi),
+        "2-D ids": (ids.reshape(2, 2), x, u, phi),
+        "x of (count, dim)": (ids, x.T, u, phi),
+        "short u": (ids, x, u[:, :3], phi),
+        "long phi": (ids, x, u, np.arange(5.0)),
+        "x of another dim": (ids, np.zeros((3, 4)), u, phi),
+    }
+    for what, args in bad_cases.items():
+        with pytest.raises(wbsph.WbsphError) as ei:
+            wbsph.check_update_args(*args, dim, n)
+        assert ei.value.code == -1, what
+
+
 def test_status_strings_and_config_defaults(lib):
     from paper_2608_22269_gb300 import wbsph
     L = wbsph.load()
